@@ -1,0 +1,27 @@
+"""FP64 CPU oracle for the Split-SPCP hot path (Driggs, Becker, Aravkin, arXiv 1702.02241).
+
+TEST INFRASTRUCTURE ONLY.  This package is a plain, slow, obviously-correct NumPy
+implementation of what the CUDA path computes.  Only ``tests/``, ``__graft_entry__.smoke()``
+and the ``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import it.  The
+product (``paper_1702_02241_gb300``) never imports it and shares no code with it; the one
+shared module is the seeded input generator ``paper_1702_02241_gb300.gen``, which holds no
+arithmetic of the method.
+
+Modules and the passages they follow:
+
+* ``core``        -- Huber value/derivative (Sec. 1 "Marginalization in S", Sec. 3.2), the
+                     factored objective Eq. (Thm5) / Eq. (7) with the optional mask of Sec. 6.2,
+                     its gradient (Sec. 3.2), the sparse part S.
+* ``lbfgs``       -- L-BFGS with memory 10 (Sec. 5.1, Table 1) and a strong-Wolfe line search
+                     (the paper is silent on the line search; Nocedal & Wright Alg. 3.5/3.6).
+* ``certificate`` -- the convergence certificate of Sec. 3.4 (the four-term ||E||_F, the
+                     QR + small-SVD route of its footnote, the distance bound F_bound).
+* ``convex``      -- proximal gradient / FISTA with singular-value thresholding on Eq. (4)
+                     (Sec. 1 notes proximal methods apply but need an SVD): reference solutions
+                     on tiny instances.
+* ``sketch``      -- randomized-SVD initialisation U0 = U_k S^1/2, V0 = V_k S^1/2 (Sec. 4.2).
+
+Every function is pinned by ``tests/test_oracle_*.py`` against something other than itself:
+brute-force minimisation, finite differences, closed-form SVT solutions, the explicit
+subdifferential construction, planted recovery.
+"""

@@ -1,0 +1,129 @@
+"""Computable convergence certificate of Sec. 3.4, float64.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring): never imported by the product.
+
+Given a factored point L = U V^T, Sec. 3.4 builds an element E of the subdifferential of
+lam_L ||L||_* + phi(L) of smallest Frobenius norm reachable from the SVD of L:
+
+  L = [U1 U2] diag(Sigma1, 0) [V1 V2]^T        (U1, V1: the r directions with sigma > 0)
+  U1, V1 from thin QR of U and V and an SVD of the small k x k R_U R_V^T (footnote of Sec. 3.4)
+  D = P_Omega(clip(U V^T - X, +-lam_S))        (gradient of phi, Sec. 3.2)
+  ||E||_F^2 = t1 + t2 + t3 + t4 with
+    t1 = || lam_L I + U1^T D V1 ||_F^2
+    t2 = || U1^T D ||_F^2 - || U1^T D V1 ||_F^2        (= || U1^T D V2 ||_F^2)
+    t3 = || D V1 ||_F^2   - || U1^T D V1 ||_F^2        (= || U2^T D V1 ||_F^2)
+    t4 = min_{||W'|| <= lam_L} || U2^T D V2 + W' ||_F^2 = sum_i (sigma_i(P_U1perp D P_V1perp) - lam_L)_+^2
+
+Readings of the paper taken here (each is pinned by a test):
+* The printed first block is "I - U1^T D V1"; expanding U~^T (Z + D) V~ with Z in the
+  nuclear-norm subdifferential gives "I + U1^T D V1" (at the optimum D = -U1 V1^T on the
+  range of L).  The sign of the W' block does not matter (the ball is symmetric).
+* The paper sets lam_L = 1 "for convenience"; for general lam_L the nuclear-norm
+  subgradient is scaled by lam_L (t1 uses lam_L I, t4 thresholds at lam_L), and
+  cert_rel = cert / lam_L is the scale-free number that is compared against 1e-4.
+* The numerical rank r counts singular values of L above tau * sigma_1 (tau = 1e-8).
+* Distance bound: ||L - L*||_F <= ||L||_F + F_bound / lam_L with
+  F_bound = min(F(0) = phi(0), best objective seen), and the optimality-gap bound
+  F(L) - F* <= cert * (||L||_F + F_bound / lam_L).
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+
+from . import core
+
+TAU = 1e-8
+
+
+@dataclasses.dataclass
+class Cert:
+    cert: float
+    cert_rel: float
+    t1: float
+    t2: float
+    t3: float
+    t4: float
+    rank_r: int
+    normL_F: float
+    F: float
+    F_bound: float
+    gap_bound: float
+    sigma_perp: np.ndarray  # leading singular values of P_U1perp D P_V1perp that were computed
+
+
+def range_bases(U, V, tau=TAU):
+    """U1, V1, Sigma1 of L = U V^T via thin QR and the SVD of R_U R_V^T (footnote, Sec. 3.4)."""
+    U = np.asarray(U, np.float64)
+    V = np.asarray(V, np.float64)
+    QU, RU = np.linalg.qr(U)
+    QV, RV = np.linalg.qr(V)
+    Ur, s, Vrt = np.linalg.svd(RU @ RV.T)
+    r = int(np.sum(s > tau * s[0])) if s.size and s[0] > 0 else 0
+    return QU @ Ur[:, :r], QV @ Vrt[:r].T, s[:r]
+
+
+def perp_singular_values(D, U1, V1, lam_L, method="auto", k_s=32):
+    """Singular values of P_U1perp D P_V1perp that can exceed lam_L, largest first.
+
+    Small problems: all of them, from a dense SVD of the explicit projected matrix.
+    Large problems: the leading k_s from scipy's svds on a LinearOperator, doubling k_s
+    until the smallest one returned is below lam_L.
+    """
+    m, n = D.shape
+    if method == "auto":
+        method = "dense" if m * n <= 4_000_000 else "svds"
+    if method == "dense":
+        M = D - U1 @ (U1.T @ D)
+        M = M - (M @ V1) @ V1.T
+        return np.linalg.svd(M, compute_uv=False)
+    from scipy.sparse.linalg import LinearOperator, svds
+
+    def mv(x):
+        x = x - V1 @ (V1.T @ x)
+        y = D @ x
+        return y - U1 @ (U1.T @ y)
+
+    def rmv(y):
+        y = y - U1 @ (U1.T @ y)
+        x = D.T @ y
+        return x - V1 @ (V1.T @ x)
+
+    op = LinearOperator((m, n), matvec=mv, rmatvec=rmv, matmat=mv, rmatmat=rmv, dtype=np.float64)
+    while True:
+        kk = min(k_s, min(m, n) - 1)
+        s = svds(op, k=kk, return_singular_vectors=False, tol=1e-10,
+                 random_state=np.random.default_rng(0))
+        s = np.sort(s)[::-1]
+        if s[-1] < lam_L or kk >= min(m, n) - 1:
+            return s
+        k_s *= 2
+
+
+def certificate(X, mask, U, V, lam_L, lam_S, F_best=None, tau=TAU, t4_method="auto"):
+    """The Sec. 3.4 certificate at L = U V^T, with the paper's term formulas."""
+    U = np.asarray(U, np.float64)
+    V = np.asarray(V, np.float64)
+    R = core.residual(X, U, V)
+    D = core.D_of_R(R, mask, lam_S)
+    U1, V1, s1 = range_bases(U, V, tau)
+    r = s1.size
+    DV1 = D @ V1
+    UtD = U1.T @ D
+    B = U1.T @ DV1
+    nB = float(np.sum(B * B))
+    t1 = float(np.sum((lam_L * np.eye(r) + B) ** 2))
+    t2 = float(np.sum(UtD * UtD)) - nB
+    t3 = float(np.sum(DV1 * DV1)) - nB
+    sp = perp_singular_values(D, U1, V1, lam_L, t4_method)
+    t4 = float(np.sum(np.maximum(sp - lam_L, 0.0) ** 2))
+    cert = float(np.sqrt(max(t1 + t2 + t3 + t4, 0.0)))
+    F = 0.5 * lam_L * (np.sum(U * U) + np.sum(V * V)) + core.phi_of_R(R, mask, lam_S)
+    F0 = core.phi_of_R(-np.asarray(X, np.float64), mask, lam_S)
+    F_bound = min(F0, F if F_best is None else min(F, F_best))
+    normL = float(np.sqrt(np.sum(s1 ** 2)))
+    gap = cert * (normL + F_bound / lam_L)
+    return Cert(cert=cert, cert_rel=cert / lam_L, t1=t1, t2=t2, t3=t3, t4=t4, rank_r=r,
+                normL_F=normL, F=float(F), F_bound=float(F_bound), gap_bound=float(gap),
+                sigma_perp=sp)
