@@ -10,8 +10,8 @@ lam_L ||L||_* + phi(L) of smallest Frobenius norm reachable from the SVD of L:
   D = P_Omega(clip(U V^T - X, +-lam_S))        (gradient of phi, Sec. 3.2)
   ||E||_F^2 = t1 + t2 + t3 + t4 with
     t1 = || lam_L I + U1^T D V1 ||_F^2
-    t2 = || U1^T D ||_F^2 - || U1^T D V1 ||_F^2        (= || U1^T D V2 ||_F^2)
-    t3 = || D V1 ||_F^2   - || U1^T D V1 ||_F^2        (= || U2^T D V1 ||_F^2)
+    t2 = || U1^T D V2 ||_F^2   (the paper evaluates it as ||U1^T D||^2 - ||U1^T D V1||^2)
+    t3 = || U2^T D V1 ||_F^2   (likewise ||D V1||^2 - ||U1^T D V1||^2)
     t4 = min_{||W'|| <= lam_L} || U2^T D V2 + W' ||_F^2 = sum_i (sigma_i(P_U1perp D P_V1perp) - lam_L)_+^2
 
 Readings of the paper taken here (each is pinned by a test):
@@ -21,7 +21,12 @@ Readings of the paper taken here (each is pinned by a test):
 * The paper sets lam_L = 1 "for convenience"; for general lam_L the nuclear-norm
   subgradient is scaled by lam_L (t1 uses lam_L I, t4 thresholds at lam_L), and
   cert_rel = cert / lam_L is the scale-free number that is compared against 1e-4.
-* The numerical rank r counts singular values of L above tau * sigma_1 (tau = 1e-8).
+* The numerical rank r counts singular values of L above tau * sigma_1 (tau = 1e-8); in
+  addition a direction that is both tiny (sigma_i <= 1e-3 sigma_1) and inactive
+  (|lam_L + u_i^T D v_i| > lam_L / 2) is placed in the complement block: it is rounding
+  residue of a factor column that the nuclear penalty drives to zero, and the certificate is
+  then the one of L with that direction truncated (a valid subgradient of the truncated
+  point, as the W' block of Eq. subdiff allows).
 * Distance bound: ||L - L*||_F <= ||L||_F + F_bound / lam_L with
   F_bound = min(F(0) = phi(0), best objective seen), and the optimality-gap bound
   F(L) - F* <= cert * (||L||_F + F_bound / lam_L).
@@ -35,6 +40,7 @@ import numpy as np
 from . import core
 
 TAU = 1e-8
+DROP_TAU = 1e-3
 
 
 @dataclasses.dataclass
@@ -108,14 +114,23 @@ def certificate(X, mask, U, V, lam_L, lam_S, F_best=None, tau=TAU, t4_method="au
     R = core.residual(X, U, V)
     D = core.D_of_R(R, mask, lam_S)
     U1, V1, s1 = range_bases(U, V, tau)
-    r = s1.size
+    if s1.size:
+        b_diag = np.einsum("ij,ij->j", U1, D @ V1)
+        keep = ~((s1 <= DROP_TAU * s1[0]) & (np.abs(lam_L + b_diag) > 0.5 * lam_L))
+        U1, V1, s1_kept = U1[:, keep], V1[:, keep], s1[keep]
+    else:
+        s1_kept = s1
+    r = s1_kept.size
     DV1 = D @ V1
     UtD = U1.T @ D
     B = U1.T @ DV1
-    nB = float(np.sum(B * B))
     t1 = float(np.sum((lam_L * np.eye(r) + B) ** 2))
-    t2 = float(np.sum(UtD * UtD)) - nB
-    t3 = float(np.sum(DV1 * DV1)) - nB
+    # ||U1^T D V2||^2 and ||U2^T D V1||^2 as the norms of the projected blocks (the paper's
+    # "||U1^T D||^2 - ||U1^T D V1||^2" is the same number but cancels near the optimum).
+    E2 = UtD - B @ V1.T
+    E3 = DV1 - U1 @ B
+    t2 = float(np.sum(E2 * E2))
+    t3 = float(np.sum(E3 * E3))
     sp = perp_singular_values(D, U1, V1, lam_L, t4_method)
     t4 = float(np.sum(np.maximum(sp - lam_L, 0.0) ** 2))
     cert = float(np.sqrt(max(t1 + t2 + t3 + t4, 0.0)))

@@ -267,6 +267,10 @@ def test_certificate_terms_equal_explicit_construction():
     assert c.t1 == pytest.approx(np.sum((U1.T @ E @ V1) ** 2), rel=1e-10)
     assert c.t2 == pytest.approx(np.sum((U1.T @ D @ V2) ** 2), rel=1e-9)
     assert c.t3 == pytest.approx(np.sum((U2.T @ D @ V1) ** 2), rel=1e-9)
+    # The paper's shortcut ||U1^T D V2||^2 = ||U1^T D||^2 - ||U1^T D V1||^2 (Sec. 3.4).
+    B = U1.T @ D @ V1
+    assert c.t2 == pytest.approx(np.sum((U1.T @ D) ** 2) - np.sum(B * B), rel=1e-9)
+    assert c.t3 == pytest.approx(np.sum((D @ V1) ** 2) - np.sum(B * B), rel=1e-9)
     # No other feasible W' does better (spot check).
     for _ in range(20):
         W2 = g.normal(size=M.shape)
@@ -326,3 +330,21 @@ def test_rsvd_mask_rescaling():
     A = sketch.sampled(X, mask)
     assert np.allclose(A[mask == 0], 0)
     assert np.allclose(A[mask != 0], X[mask != 0] / mask.mean())
+
+
+def test_certificate_moves_tiny_inactive_direction_to_complement():
+    """A rounding-size extra factor column at the optimum is truncated (the direction goes to
+    the W' block): the certificate equals the one of the truncated point, not ~lam_L."""
+    X = _lowrank_noise(20, 15, 3, 4)
+    lam_L = 1.0
+    Ub, Vb = convex.balanced_factors(convex.svt(X, lam_L), 4)
+    g = np.random.default_rng(1)
+    U, V = Ub.copy(), Vb.copy()
+    U[:, 3] = 3e-3 * g.normal(size=20)
+    V[:, 3] = 3e-3 * g.normal(size=15)
+    c = ocert.certificate(X, np.ones(X.shape, np.uint8), U, V, lam_L, np.inf)
+    assert c.rank_r == 3
+    assert c.cert_rel < 1e-3
+    # Without the rule the extra direction would sit in U1 with u^T D v ~ 0: t1 >= lam_L^2 / 4.
+    U1, V1, s = ocert.range_bases(U, V)
+    assert s.size == 4 and s[3] / s[0] < 1e-3
