@@ -1,0 +1,196 @@
+/*
+ * rpca.h -- C ABI of the GB300 (sm_103a) Split-SPCP engine.
+ *
+ * Method: Driggs, Becker, Aravkin, "Adapting Regularized Low-Rank Models for Parallel
+ * Architectures" (arXiv 1702.02241).  The engine minimises the smooth non-convex RPCA
+ * objective of Eq. (Thm5) / Eq. (7),
+ *
+ *     F(U, V) = lam_L/2 (||U||_F^2 + ||V||_F^2) + sum_{(i,j) in Omega} psi_{lam_S}((U V^T - X)_ij),
+ *
+ * where psi is the Huber function left by marginalising the l1-penalised sparse part S
+ * (Sec. 1, "Marginalization in S"), Omega the observed entries (Sec. 6.2), with L-BFGS of
+ * memory 10 (Sec. 5.1), and checks optimality with the computable certificate of Sec. 3.4.
+ *
+ * Conventions for every entry point:
+ *   - Matrices are column-major float32 in DEVICE memory unless stated otherwise.  X is
+ *     m x n with leading dimension ldx >= m; U is m x k (ld m); V is n x k (ld n).
+ *   - X and the mask are BORROWED: they must stay valid and unchanged until rpca_destroy.
+ *     U, V, gU, gV and all other matrix arguments are caller-owned device buffers.
+ *   - Work is ordered on the CUDA stream given to rpca_create; calls that return host
+ *     scalars or structs (f, rpca_result, rpca_cert) synchronise that stream.
+ *   - Every entry returns an rpca_status and never aborts; rpca_last_error() gives a
+ *     message for the last failure on a context.  A context is not thread-safe: serialise
+ *     calls on one context.
+ *   - Any CUDA error (including a device wait that gave up, see RPCA_ETIMEOUT) is reported,
+ *     never hidden; there is no CPU fallback.
+ */
+#ifndef RPCA_H
+#define RPCA_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define RPCA_API __attribute__((visibility("default")))
+#else
+#define RPCA_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rpca_ctx rpca_ctx; /* opaque, owned by the library */
+
+typedef enum {
+  RPCA_OK = 0,
+  RPCA_EINVAL = -1,       /* bad argument (sizes, k, lambdas, null pointers, non-finite observed X) */
+  RPCA_ENOMEM = -2,       /* device allocation failed */
+  RPCA_ECUDA = -3,        /* CUDA runtime/driver error */
+  RPCA_ENOTCONV = -4,     /* solver stopped (iteration cap, line-search failure) above cert_tol */
+  RPCA_ETIMEOUT = -5,     /* a bounded device wait gave up; results are invalid */
+  RPCA_EUNSUPPORTED = -6  /* combination not compiled (e.g. k > 16) */
+} rpca_status;
+
+typedef enum { RPCA_F32 = 0, RPCA_BF16 = 1, RPCA_FP8E4M3 = 2 } rpca_dtype;
+
+typedef enum {
+  RPCA_INIT_SKETCH = 0, /* randomized SVD of A*(X): U0 = U_k S^1/2, V0 = V_k S^1/2 (Sec. 4.2) */
+  RPCA_INIT_RANDOM = 1, /* iid N(0, 1e-2) factors from the seeded device generator */
+  RPCA_INIT_LEARNED = 2,
+  RPCA_INIT_USER = 3    /* start from the U, V passed to rpca_solve */
+} rpca_init_kind;
+
+typedef struct {
+  int lbfgs_mem;         /* L-BFGS memory (10, Sec. 5.1); 1..32 */
+  int max_iter;          /* iteration cap of rpca_solve */
+  double cert_tol;       /* stop when cert_rel <= cert_tol (1e-4) */
+  int cert_every;        /* evaluate the certificate every cert_every iterations (0 = only at the end) */
+  int init;              /* rpca_init_kind */
+  uint64_t seed;         /* seed of the device generator (sketch, random init) */
+  rpca_dtype x_dtype;    /* storage of X inside the engine (RPCA_F32 only in this build) */
+  int refine_fp32;       /* reserved for the reduced-precision form */
+  double timeout_s;      /* wall-clock limit of rpca_solve (0 = none) */
+  double gtol;           /* also stop when ||grad F||_F <= gtol * max(1, |F|) (0 = off) */
+  int sketch_oversample; /* rSVD oversampling p (10) */
+  int sketch_power;      /* rSVD power iterations q (2) */
+} rpca_options;
+
+typedef struct {
+  double cert;     /* ||E||_F, E in the subdifferential of lam_L ||L||_* + phi(L) at L = U V^T */
+  double cert_rel; /* cert / lam_L, compared against cert_tol */
+  double t1, t2, t3, t4; /* the four terms of ||E||_F^2 (Sec. 3.4) */
+  double normL_F;  /* ||U V^T||_F */
+  double F;        /* F(U, V) */
+  double F_bound;  /* min(F(0), best F seen by this context) */
+  double gap_bound;/* cert * (||L||_F + F_bound / lam_L) >= F(L) - F* */
+  int rank_r;      /* numerical rank of U V^T (singular values > 1e-8 sigma_1) */
+  int krylov_steps;/* block Lanczos steps used for t4 */
+  double sigma1_perp; /* largest singular value of P_U1perp D P_V1perp found */
+} rpca_cert;
+
+typedef struct {
+  double F;        /* final objective */
+  int iters;       /* L-BFGS iterations */
+  int evals;       /* objective/gradient evaluations (one pass over X each) */
+  int cert_evals;  /* certificate evaluations */
+  double seconds;  /* wall time of rpca_solve */
+  rpca_cert cert;  /* certificate at the returned point */
+  rpca_status status;
+} rpca_result;
+
+/* Fills *opt with the defaults named in the comments above. */
+RPCA_API void rpca_default_options(rpca_options *opt);
+
+/*
+ * Creates a solver context for X (m x n, device, column-major, ldx >= m; ldx * 4 must be a
+ * multiple of 16 bytes and X 16-byte aligned, as the tiled TMA copies require), an optional
+ * observation mask (device uint8, m x n column-major with ldmask >= m, nonzero = observed,
+ * NULL = all observed; Sec. 6.2), factor rank k (1..16), lambda_L > 0 and lambda_S > 0
+ * (lambda_S = +inf gives plain least squares, phi = 1/2 ||P_Omega(L - X)||^2).
+ * opt may be NULL (defaults).  cuda_stream is a cudaStream_t (NULL = legacy default stream).
+ * Checks that every observed X entry is finite (RPCA_EINVAL otherwise).  Allocates the
+ * context's device workspaces (partial-sum buffers, L-BFGS history of 2 * mem (m + n) k
+ * floats, certificate buffers) and packs the mask into a bitmap it owns.
+ */
+RPCA_API rpca_status rpca_create(rpca_ctx **out, int64_t m, int64_t n, const float *X, int64_t ldx,
+                        const uint8_t *mask, int64_t ldmask, int k, double lambda_L, double lambda_S,
+                        const rpca_options *opt, void *cuda_stream);
+
+/*
+ * One evaluation of F and its gradient at (U, V) (Eq. Thm5; gradient of phi from Sec. 3.2
+ * through L = U V^T):  gU = D V + lam_L U,  gV = D^T U + lam_L V,  D = P_Omega(clip(U V^T - X)).
+ * One pass over X.  f is a HOST pointer (may be NULL; the call then does not synchronise);
+ * gU (m x k) and gV (n x k) are required device buffers.  The objective is summed in float64.
+ */
+RPCA_API rpca_status rpca_fg(rpca_ctx *c, const float *U, const float *V, double *f, float *gU, float *gV);
+
+/*
+ * Products with the clipped residual D = P_Omega(clip(U V^T - X, +-lam_S)) at (U, V):
+ *   DBv = D Bv  (m x b, device),   DtBu = D^T Bu  (n x b, device),
+ * for 1 <= b <= 8, with Bv n x b and Bu m x b (device, column-major).  These are the matrix products the
+ * certificate's spectral term needs (Sec. 3.4); one pass over X for both.
+ */
+RPCA_API rpca_status rpca_apply(rpca_ctx *c, const float *U, const float *V, int b, const float *Bv,
+                       const float *Bu, float *DBv, float *DtBu);
+
+/*
+ * Randomized-SVD initialisation (Sec. 4.2): U0 = U_k S^1/2, V0 = V_k S^1/2 from a rank
+ * k + p sketch of A*(X) (observed entries, rescaled by 1/p_hat when masked) with q power
+ * iterations.  Omega is an optional device n x (k + p) Gaussian test matrix; NULL draws
+ * one from the context's seeded device generator.  Writes U (m x k) and V (n x k).
+ */
+RPCA_API rpca_status rpca_init_sketch(rpca_ctx *c, const float *Omega, float *U, float *V);
+
+/*
+ * Minimises F with L-BFGS (memory opt.lbfgs_mem, Sec. 5.1) and a strong-Wolfe line search,
+ * all on the device (direction, line search and its decisions are kernels inside a CUDA
+ * graph; the host only polls a status word between graph launches).  U, V: in = the start
+ * point when opt.init == RPCA_INIT_USER, out = the solution.  Stops at cert_rel <= cert_tol
+ * (certificate every cert_every iterations), max_iter, gtol, or timeout.  res may be NULL.
+ * Returns RPCA_OK when the certificate tolerance was met, RPCA_ENOTCONV otherwise.
+ */
+RPCA_API rpca_status rpca_solve(rpca_ctx *c, float *U, float *V, rpca_result *res);
+
+/*
+ * The convergence certificate of Sec. 3.4 at L = U V^T: one pass over X for F and the
+ * gradient terms, small float64 factorisations on the device for t1..t3, and block
+ * Lanczos (passes over X through rpca_apply's kernel) for the spectral term t4.
+ */
+RPCA_API rpca_status rpca_certificate(rpca_ctx *c, const float *U, const float *V, rpca_cert *out);
+
+/* Releases the context and every buffer it owns (not X or the mask). NULL is allowed. */
+RPCA_API void rpca_destroy(rpca_ctx *c);
+
+/* Message of the last failure on c (or of the last failed rpca_create when c is NULL). */
+RPCA_API const char *rpca_last_error(const rpca_ctx *c);
+
+/*
+ * Launch configuration the planner picked for the fused kernel of this context
+ * (which = 0: objective/gradient; 1, 2: the certificate's and the sketch's products).
+ * out[0..7] = {rows per lane R, consumer warps per CTA, row blocks, column splits,
+ * columns per CTA, threads per CTA, dynamic shared memory bytes, CTAs per SM}.
+ * The planner can be overridden with the environment variable RPCA_PLAN="warps,splits".
+ */
+RPCA_API rpca_status rpca_plan_info(const rpca_ctx *c, int which, int64_t *out);
+
+/*
+ * Instrumentation (tracing).  rpca_profile(c, 1) starts recording: CUDA events bracket every
+ * launch of the fused objective/gradient kernel and of its finalize kernel issued outside a
+ * CUDA graph, on the context's stream, and every kernel the library issues is counted
+ * (kernels inside a solver graph launch are counted from the iterations and line-search
+ * trials it ran).  rpca_profile(c, 0) stops.  rpca_profile_read fills out[0..5] with
+ * {fused-kernel launches timed, their total milliseconds, finalize launches timed, their
+ * total milliseconds, kernels launched, CUDA-graph launches} since recording started; it
+ * synchronises the stream.
+ */
+RPCA_API rpca_status rpca_profile(rpca_ctx *c, int enable);
+RPCA_API rpca_status rpca_profile_read(rpca_ctx *c, double *out);
+
+/* Library version string. */
+RPCA_API const char *rpca_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RPCA_H */

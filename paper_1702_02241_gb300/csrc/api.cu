@@ -1,0 +1,730 @@
+// C ABI: context creation, launch planning, one-pass objective/gradient and D-products.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <utility>
+#include <vector>
+#include <new>
+
+#include "ctx.h"
+#include "fg_kernel.cuh"
+
+namespace rpca {
+
+static thread_local std::string g_create_err;
+
+rpca_status set_err(rpca_ctx* c, rpca_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  else g_create_err = msg;
+  return s;
+}
+
+rpca_status cuda_err(rpca_ctx* c, cudaError_t e, const char* what) {
+  std::string msg = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+  return set_err(c, e == cudaErrorMemoryAllocation ? RPCA_ENOMEM : RPCA_ECUDA, msg);
+}
+
+#define RPCA_CUDA(c, call)                              \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return cuda_err((c), e_, #call); \
+  } while (0)
+
+// Reads (and clears) the device status word; call after a synchronise.
+rpca_status check_dev_err(rpca_ctx* c) {
+  int h = 0;
+  RPCA_CUDA(c, cudaMemcpyAsync(&h, c->ws.err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  RPCA_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (h != 0) {
+    RPCA_CUDA(c, cudaMemsetAsync(c->ws.err, 0, sizeof(int), c->stream));
+    char buf[128];
+    snprintf(buf, sizeof buf, "a bounded device wait gave up (status bits 0x%x); results are invalid", h);
+    return set_err(c, RPCA_ETIMEOUT, buf);
+  }
+  return RPCA_OK;
+}
+
+// ---- kernel variant table ----------------------------------------------------------------
+static FgVariant g_same[17][2];
+static FgVariant g_apply[3][2];
+static std::once_flag g_once;
+
+static void init_tables() {
+  std::call_once(g_once, [] {
+    memset(g_same, 0, sizeof g_same);
+    memset(g_apply, 0, sizeof g_apply);
+    fg_register_same_small(g_same);
+    fg_register_same_large(g_same);
+    fg_register_apply(g_apply);
+  });
+}
+
+const FgVariant* fg_variant(int K, int B, bool same, bool masked) {
+  init_tables();
+  if (same) {
+    if (K < 1 || K > 16 || B != K) return nullptr;
+    return g_same[K][masked ? 1 : 0].fn ? &g_same[K][masked ? 1 : 0] : nullptr;
+  }
+  int slot = -1;
+  if (K == 0 && B == 16) slot = 0;
+  if (K == 8 && B == 8) slot = 1;
+  if (K == 16 && B == 8) slot = 2;
+  if (slot < 0) return nullptr;
+  return &g_apply[slot][masked ? 1 : 0];
+}
+
+// ---- TMA descriptors -----------------------------------------------------------------------
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+static rpca_status make_tmap(rpca_ctx* c, CUtensorMap* map, CUtensorMapDataType dt, const void* base, int64_t d0,
+                             int64_t d1, int64_t stride_bytes, int b0, int b1) {
+  auto fn = encode_fn();
+  if (!fn) return set_err(c, RPCA_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  cuuint64_t dims[2] = {(cuuint64_t)d0, (cuuint64_t)d1};
+  cuuint64_t strides[1] = {(cuuint64_t)stride_bytes};
+  cuuint32_t box[2] = {(cuuint32_t)b0, (cuuint32_t)b1};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = fn(map, dt, 2, const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    char buf[160];
+    snprintf(buf, sizeof buf, "cuTensorMapEncodeTiled failed (%d) for dims %lld x %lld, box %d x %d", (int)r,
+             (long long)d0, (long long)d1, b0, b1);
+    return set_err(c, RPCA_ECUDA, buf);
+  }
+  return RPCA_OK;
+}
+
+// Raises a kernel's dynamic shared-memory limit to at least `bytes` (never lowers it, so
+// plans made earlier stay launchable).  False when the device cannot provide that much.
+static bool allow_smem(const void* fn, size_t bytes) {
+  static std::mutex mu;
+  static const void* fns[64];
+  static size_t lim[64];
+  static int nf = 0;
+  std::lock_guard<std::mutex> lock(mu);
+  int i = 0;
+  while (i < nf && fns[i] != fn) ++i;
+  if (i < nf && lim[i] >= bytes) return true;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (i == nf && nf < 64) fns[nf++] = fn;
+  if (i < 64) lim[i] = bytes;
+  return true;
+}
+
+// ---- autotuner support ----------------------------------------------------------------------
+struct PlanKey {
+  int dev, m, n;
+  int64_t ldx;
+  int K, B;
+  bool same, masked;
+  bool operator<(const PlanKey& o) const {
+    return std::tie(dev, m, n, ldx, K, B, same, masked) < std::tie(o.dev, o.m, o.n, o.ldx, o.K, o.B, o.same, o.masked);
+  }
+};
+static std::mutex g_cache_mu;
+static std::map<PlanKey, std::pair<int, int>> g_plan_cache;
+
+static bool plan_cache_get(const PlanKey& k, int* wc, int* ncs) {
+  std::lock_guard<std::mutex> lock(g_cache_mu);
+  auto it = g_plan_cache.find(k);
+  if (it == g_plan_cache.end()) return false;
+  *wc = it->second.first;
+  *ncs = it->second.second;
+  return true;
+}
+static void plan_cache_put(const PlanKey& k, int wc, int ncs) {
+  std::lock_guard<std::mutex> lock(g_cache_mu);
+  g_plan_cache[k] = {wc, ncs};
+}
+static bool autotune_enabled() {
+  const char* e = getenv("RPCA_AUTOTUNE");
+  return !(e && e[0] == '0');
+}
+
+static rpca_status size_workspace(rpca_ctx* c, const FgPlan& P);
+
+// Tensor maps for a chosen configuration.
+static rpca_status finish_plan(rpca_ctx* c, FgPlan* q) {
+  rpca_status s = make_tmap(c, &q->tmX, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, c->X, c->m, c->n, c->ldx * 4, 32 * q->R,
+                            FG_BJ);
+  if (s != RPCA_OK) return s;
+  if (q->masked) {
+    s = make_tmap(c, &q->tmM, CU_TENSOR_MAP_DATA_TYPE_UINT32, c->bits, c->wpad, c->n, (int64_t)c->wpad * 4,
+                  q->WC * q->R, FG_BJ);
+    if (s != RPCA_OK) return s;
+  } else {
+    q->tmM = q->tmX;
+  }
+  return RPCA_OK;
+}
+
+// Average duration of the fused kernel alone for configuration q (zero factors: the pass
+// over X and the arithmetic are the same as for any factors), CUDA events on the stream.
+static rpca_status time_plan(rpca_ctx* c, const FgPlan& q, double* ms) {
+  rpca_status s = size_workspace(c, q);
+  if (s != RPCA_OK) return s;
+  const int w = std::max(q.K, q.B);
+  float* z = nullptr;
+  RPCA_CUDA(c, cudaMalloc(&z, sizeof(float) * (size_t)(c->m + c->n) * std::max(w, 1)));
+  RPCA_CUDA(c, cudaMemsetAsync(z, 0, sizeof(float) * (size_t)(c->m + c->n) * std::max(w, 1), c->stream));
+  FgArgs a;
+  memset(&a, 0, sizeof a);
+  a.m = c->m;
+  a.n = c->n;
+  a.mpad = c->mpad;
+  a.U = z;
+  a.V = z + (size_t)c->m * w;
+  a.BU = z;
+  a.BV = z + (size_t)c->m * w;
+  a.lam_S = std::isinf(c->lam_S) ? INFINITY : (float)c->lam_S;
+  a.nrb = q.nrb;
+  a.ncs = q.ncs;
+  a.BN = q.BN;
+  a.PU = c->ws.PU;
+  a.PV = c->ws.PV;
+  a.Ppsi = c->ws.Ppsi;
+  a.err = c->ws.err;
+  void* args[] = {(void*)&q.tmX, (void*)&q.tmM, (void*)&a};
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaError_t e = cudaLaunchKernel(q.var->fn, dim3(q.nrb * q.ncs), dim3(q.threads), args, q.smem, c->stream);
+  const int reps = 3;
+  if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
+  for (int i = 0; i < reps && e == cudaSuccess; ++i)
+    e = cudaLaunchKernel(q.var->fn, dim3(q.nrb * q.ncs), dim3(q.threads), args, q.smem, c->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  float t = 0;
+  if (e == cudaSuccess) cudaEventElapsedTime(&t, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(z);
+  count_launches(c, reps + 1);
+  if (e != cudaSuccess) return cuda_err(c, e, "timing a launch configuration");
+  *ms = t / reps;
+  return check_dev_err(c);
+}
+
+// ---- launch planning -----------------------------------------------------------------------
+// Chooses consumer warps per CTA (WC) and the column split (ncs, BN).  A time model ranks
+// the configurations that fit (whole waves of tiles at full bandwidth, a partly filled last
+// wave costing at least half a wave, plus the write and re-read of the partial sums); the
+// six best are then timed on the device and the fastest is kept (cached per shape in this
+// process).  RPCA_PLAN="warps,splits" forces one configuration; RPCA_AUTOTUNE=0 keeps the
+// model's choice without timing.
+static rpca_status make_plan(rpca_ctx* c, FgPlan* P, int K, int B, bool same) {
+  const bool masked = c->bits != nullptr;
+  const FgVariant* v = fg_variant(K, B, same, masked);
+  if (!v) return set_err(c, RPCA_EUNSUPPORTED, "no compiled kernel for this factor rank");
+  const int KV = same ? K : K + B;
+  const int JB = v->J * B;
+  double best = 1e300;
+  std::vector<std::pair<double, FgPlan>> cands;
+  int force_wc = 0, force_ncs = 0, n_smem = 0, n_attr = 0, n_occ = 0, n_try = 0;
+  cudaError_t last_occ = cudaSuccess;
+  if (const char* env = getenv("RPCA_PLAN")) sscanf(env, "%d,%d", &force_wc, &force_ncs);
+  for (int WC : {8, 4, 2}) {
+    if (force_wc && WC != force_wc) continue;
+    const int BM = WC * 32 * v->R;
+    const int nrb = (c->m + BM - 1) / BM;
+    if (WC > 2 && BM / 2 >= c->m) continue;  // a smaller CTA covers the rows
+    const int maxsplit = std::max(1, (c->n + FG_BJ - 1) / FG_BJ);
+    int last_ncs = -1;
+    for (int ncs_req = 1; ncs_req <= std::min(maxsplit, 256); ++ncs_req) {
+      int BN = (c->n + ncs_req - 1) / ncs_req;
+      BN = (BN + FG_BJ - 1) / FG_BJ * FG_BJ;
+      const int ncs = (c->n + BN - 1) / BN;
+      if (ncs == last_ncs) continue;
+      if (force_ncs && ncs != force_ncs) continue;
+      last_ncs = ncs;
+      const FgSmem L = fg_smem_layout(WC, v->R, masked, BN, KV, JB);
+      ++n_try;
+      if (L.total > c->max_smem) {
+        ++n_smem;
+        continue;
+      }
+      const int threads = (WC + 1) * 32;
+      if (!allow_smem(v->fn, L.total)) {
+        ++n_attr;
+        continue;
+      }
+      int cps = 0;
+      cudaError_t oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cps, v->fn, threads, L.total);
+      if (oe != cudaSuccess || cps < 1) {
+        if (oe != cudaSuccess) last_occ = oe;
+        cudaGetLastError();
+        ++n_occ;
+        continue;
+      }
+      const double slots = (double)c->nsm * cps;
+      const double tiles = (double)nrb * ncs;
+      const double tile_bytes = (double)BM * BN * 4.0 * (masked ? 33.0 / 32.0 : 1.0);
+      const double full_waves = std::floor(tiles / slots);
+      const double rem = tiles - full_waves * slots;
+      double t = full_waves * slots * tile_bytes;
+      if (rem > 0) t += std::max(rem, 0.5 * slots) * tile_bytes;
+      t += 2.0 * 4.0 * ((double)ncs * c->mpad * B + (double)nrb * c->n * B);
+      FgPlan cand;
+      cand.valid = true;
+      cand.var = v;
+      cand.K = K;
+      cand.B = B;
+      cand.same = same;
+      cand.masked = masked;
+      cand.R = v->R;
+      cand.WC = WC;
+      cand.nrb = nrb;
+      cand.ncs = ncs;
+      cand.BN = BN;
+      cand.threads = threads;
+      cand.smem = L.total;
+      cand.cps = cps;
+      cands.push_back({t, cand});
+      if (t < best) best = t;
+    }
+  }
+  if (cands.empty()) {
+    char buf[256];
+    snprintf(buf, sizeof buf,
+             "no launch configuration for K=%d B=%d (m=%d n=%d): %d tried, %d over %zu B of shared memory, "
+             "%d refused the smem attribute, %d with zero occupancy (%s)",
+             K, B, c->m, c->n, n_try, n_smem, c->max_smem, n_attr, n_occ, cudaGetErrorName(last_occ));
+    return set_err(c, RPCA_EUNSUPPORTED, buf);
+  }
+  std::sort(cands.begin(), cands.end(),
+            [](const std::pair<double, FgPlan>& a, const std::pair<double, FgPlan>& b) { return a.first < b.first; });
+  const int64_t N = (int64_t)(c->m + c->n) * B;
+  for (auto& cp : cands) {
+    FgPlan& q = cp.second;
+    // Finalize grid: enough blocks to cover (m + n) B elements, at most 4 waves of the SMs.
+    q.fin_grid = (int)std::max<int64_t>(1, std::min<int64_t>((N + 255) / 256, 4LL * c->nsm));
+  }
+  // Cached choice for this shape, or measure the best few candidates of the model.
+  const PlanKey key{c->device, c->m, c->n, c->ldx, K, B, same, masked};
+  int pick = 0;
+  int cached_wc = 0, cached_ncs = 0;
+  const bool measure = !(force_wc || force_ncs) && autotune_enabled() && cands.size() > 1;
+  if (measure && plan_cache_get(key, &cached_wc, &cached_ncs)) {
+    for (size_t i = 0; i < cands.size(); ++i)
+      if (cands[i].second.WC == cached_wc && cands[i].second.ncs == cached_ncs) pick = (int)i;
+  } else if (measure) {
+    const int ntry = (int)std::min<size_t>(6, cands.size());
+    double best_ms = 1e300;
+    for (int i = 0; i < ntry; ++i) {
+      FgPlan& q = cands[i].second;
+      rpca_status s = finish_plan(c, &q);
+      if (s != RPCA_OK) return s;
+      double ms = 0;
+      s = time_plan(c, q, &ms);
+      if (s != RPCA_OK) return s;
+      if (ms < best_ms) {
+        best_ms = ms;
+        pick = i;
+      }
+    }
+    plan_cache_put(key, cands[pick].second.WC, cands[pick].second.ncs);
+  }
+  FgPlan bp = cands[pick].second;
+  rpca_status s = finish_plan(c, &bp);
+  if (s != RPCA_OK) return s;
+  *P = bp;
+  return RPCA_OK;
+}
+
+template <typename T>
+static rpca_status ensure(rpca_ctx* c, T** p, size_t* have, size_t need) {
+  if (*have >= need) return RPCA_OK;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  *have = 0;
+  RPCA_CUDA(c, cudaMalloc(p, std::max<size_t>(need, 1) * sizeof(T)));
+  *have = need;
+  return RPCA_OK;
+}
+
+static rpca_status size_workspace(rpca_ctx* c, const FgPlan& P) {
+  rpca_status s;
+  if ((s = ensure(c, &c->ws.PU, &c->ws.PU_n, (size_t)P.ncs * P.B * c->mpad)) != RPCA_OK) return s;
+  if ((s = ensure(c, &c->ws.PV, &c->ws.PV_n, (size_t)P.nrb * P.B * c->n)) != RPCA_OK) return s;
+  if ((s = ensure(c, &c->ws.Ppsi, &c->ws.Ppsi_n, (size_t)P.nrb * P.ncs)) != RPCA_OK) return s;
+  if ((s = ensure(c, &c->ws.blk, &c->ws.blk_n, (size_t)3 * P.fin_grid)) != RPCA_OK) return s;
+  return RPCA_OK;
+}
+
+const FgPlan* apply_plan(rpca_ctx* c, int K) {
+  int slot = K == 0 ? 0 : (K <= 8 ? 1 : 2);
+  FgPlan* P = &c->ap_plan[slot];
+  if (!P->valid) {
+    const int KK = slot == 0 ? 0 : (slot == 1 ? 8 : 16);
+    const int BB = slot == 0 ? 16 : 8;
+    if (make_plan(c, P, KK, BB, false) != RPCA_OK) return nullptr;
+    if (size_workspace(c, *P) != RPCA_OK) return nullptr;
+  }
+  return P;
+}
+
+rpca_status launch_fg(rpca_ctx* c, const FgPlan& P, const FgLaunch& L, cudaStream_t stream) {
+  FgArgs a;
+  a.m = c->m;
+  a.n = c->n;
+  a.mpad = c->mpad;
+  a.U = L.U;
+  a.V = L.V;
+  a.dU = L.dU;
+  a.dV = L.dV;
+  a.alpha = L.alpha;
+  a.alpha_dev = L.alpha_dev;
+  a.gate = L.gate;
+  a.BU = L.BU;
+  a.BV = L.BV;
+  const double lam = L.lam >= 0.0 ? L.lam : c->lam_S;
+  a.lam_S = std::isinf(lam) ? INFINITY : (float)lam;
+  a.nrb = P.nrb;
+  a.ncs = P.ncs;
+  a.BN = P.BN;
+  a.PU = c->ws.PU;
+  a.PV = c->ws.PV;
+  a.Ppsi = c->ws.Ppsi;
+  a.err = c->ws.err;
+  void* args[] = {(void*)&P.tmX, (void*)&P.tmM, (void*)&a};
+  // Event pairs bracket the two launches while profiling (never inside a graph capture).
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (c->prof) cudaStreamIsCapturing(stream, &cap);
+  const bool timed = c->prof && cap == cudaStreamCaptureStatusNone;
+  if (timed) {
+    while (c->ev_pool.size() < c->ev_used + 4) {
+      cudaEvent_t e;
+      RPCA_CUDA(c, cudaEventCreate(&e));
+      c->ev_pool.push_back(e);
+    }
+    for (int i = 0; i < 4; ++i) ev[i] = c->ev_pool[c->ev_used + i];
+    c->ev_used += 4;
+    RPCA_CUDA(c, cudaEventRecord(ev[0], stream));
+  }
+  RPCA_CUDA(c, cudaLaunchKernel(P.var->fn, dim3(P.nrb * P.ncs), dim3(P.threads), args, P.smem, stream));
+  if (timed) RPCA_CUDA(c, cudaEventRecord(ev[1], stream));
+  count_launches(c, 2);
+  FinArgs f;
+  f.m = c->m;
+  f.n = c->n;
+  f.B = P.B;
+  f.mpad = c->mpad;
+  f.nrb = P.nrb;
+  f.ncs = P.ncs;
+  f.nctas = P.nrb * P.ncs;
+  f.PU = c->ws.PU;
+  f.PV = c->ws.PV;
+  f.Ppsi = c->ws.Ppsi;
+  f.mode = L.fin_mode;
+  f.U = L.U;
+  f.V = L.V;
+  f.dU = L.dU;
+  f.dV = L.dV;
+  f.alpha = L.alpha;
+  f.alpha_dev = L.alpha_dev;
+  f.gate = L.gate;
+  f.lam_L = c->lam_L;
+  f.GU = L.GU;
+  f.GV = L.GV;
+  f.Ut = L.Ut;
+  f.Vt = L.Vt;
+  f.DU = L.DU;
+  f.DV = L.DV;
+  f.blk = c->ws.blk;
+  f.counter = c->ws.counter;
+  f.out = L.out ? L.out : c->ws.out;
+  if (timed) RPCA_CUDA(c, cudaEventRecord(ev[2], stream));
+  finalize_kernel<<<P.fin_grid, 256, 0, stream>>>(f);
+  RPCA_CUDA(c, cudaGetLastError());
+  if (timed) {
+    RPCA_CUDA(c, cudaEventRecord(ev[3], stream));
+    if (c->ev_used >= 4096) {  // fold the recorded pairs into the running sums
+      RPCA_CUDA(c, cudaStreamSynchronize(stream));
+      for (size_t i = 0; i + 3 < c->ev_used; i += 4) {
+        float a0 = 0, a1 = 0;
+        cudaEventElapsedTime(&a0, c->ev_pool[i], c->ev_pool[i + 1]);
+        cudaEventElapsedTime(&a1, c->ev_pool[i + 2], c->ev_pool[i + 3]);
+        c->prof_ms[0] += a0;
+        c->prof_ms[1] += a1;
+        c->prof_n[0] += 1;
+        c->prof_n[1] += 1;
+      }
+      c->ev_used = 0;
+    }
+  }
+  return RPCA_OK;
+}
+
+void free_solver(rpca_ctx* c);  // solver.cu
+void free_cert(rpca_ctx* c);    // cert.cu
+
+}  // namespace rpca
+
+using namespace rpca;
+
+extern "C" {
+
+void rpca_default_options(rpca_options* o) {
+  if (!o) return;
+  memset(o, 0, sizeof *o);
+  o->lbfgs_mem = 10;
+  o->max_iter = 1000;
+  o->cert_tol = 1e-4;
+  o->cert_every = 25;
+  o->init = RPCA_INIT_SKETCH;
+  o->seed = 0;
+  o->x_dtype = RPCA_F32;
+  o->refine_fp32 = 1;
+  o->timeout_s = 0.0;
+  o->gtol = 0.0;
+  o->sketch_oversample = 10;
+  o->sketch_power = 2;
+}
+
+const char* rpca_version(void) { return "rpca-gb300 0.1 (sm_103a)"; }
+
+rpca_status rpca_profile(rpca_ctx* c, int enable) {
+  if (!c) return RPCA_EINVAL;
+  if (enable && !c->prof) {
+    c->ev_used = 0;
+    c->prof_ms[0] = c->prof_ms[1] = 0;
+    c->prof_n[0] = c->prof_n[1] = 0;
+    c->launches = 0;
+    c->graph_launches = 0;
+  }
+  c->prof = enable != 0;
+  return RPCA_OK;
+}
+
+rpca_status rpca_profile_read(rpca_ctx* c, double* out) {
+  if (!c || !out) return RPCA_EINVAL;
+  RPCA_CUDA(c, cudaStreamSynchronize(c->stream));
+  for (size_t i = 0; i + 3 < c->ev_used; i += 4) {
+    float a0 = 0, a1 = 0;
+    cudaEventElapsedTime(&a0, c->ev_pool[i], c->ev_pool[i + 1]);
+    cudaEventElapsedTime(&a1, c->ev_pool[i + 2], c->ev_pool[i + 3]);
+    c->prof_ms[0] += a0;
+    c->prof_ms[1] += a1;
+    c->prof_n[0] += 1;
+    c->prof_n[1] += 1;
+  }
+  c->ev_used = 0;
+  out[0] = (double)c->prof_n[0];
+  out[1] = c->prof_ms[0];
+  out[2] = (double)c->prof_n[1];
+  out[3] = c->prof_ms[1];
+  out[4] = (double)c->launches;
+  out[5] = (double)c->graph_launches;
+  return RPCA_OK;
+}
+
+rpca_status rpca_plan_info(const rpca_ctx* c, int which, int64_t* out) {
+  if (!c || !out || which < 0 || which > 2) return RPCA_EINVAL;
+  const FgPlan& P = which == 0 ? c->fg_plan : c->ap_plan[which == 1 ? (c->k <= 8 ? 1 : 2) : 0];
+  if (!P.valid) return RPCA_EINVAL;
+  const int64_t v[8] = {P.R, P.WC, P.nrb, P.ncs, P.BN, P.threads, (int64_t)P.smem, P.cps};
+  for (int i = 0; i < 8; ++i) out[i] = v[i];
+  return RPCA_OK;
+}
+
+const char* rpca_last_error(const rpca_ctx* c) { return c ? c->err.c_str() : g_create_err.c_str(); }
+
+rpca_status rpca_create(rpca_ctx** out, int64_t m, int64_t n, const float* X, int64_t ldx, const uint8_t* mask,
+                        int64_t ldmask, int k, double lambda_L, double lambda_S, const rpca_options* opt,
+                        void* cuda_stream) {
+  if (!out) return set_err(nullptr, RPCA_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (m < 1 || n < 1 || m > (1LL << 30) || n > (1LL << 30))
+    return set_err(nullptr, RPCA_EINVAL, "m and n must be in [1, 2^30]");
+  if ((m * n) > (1LL << 40)) return set_err(nullptr, RPCA_EINVAL, "m * n too large");
+  if (!X) return set_err(nullptr, RPCA_EINVAL, "X is NULL");
+  if (ldx < m) return set_err(nullptr, RPCA_EINVAL, "ldx < m");
+  if ((ldx * 4) % 16 != 0 || (reinterpret_cast<uintptr_t>(X) & 15) != 0)
+    return set_err(nullptr, RPCA_EINVAL, "X must be 16-byte aligned with ldx a multiple of 4");
+  if (mask && ldmask < m) return set_err(nullptr, RPCA_EINVAL, "ldmask < m");
+  if (k < 1 || k > std::min<int64_t>(m, n)) return set_err(nullptr, RPCA_EINVAL, "k must be in [1, min(m, n)]");
+  if (k > 16) return set_err(nullptr, RPCA_EUNSUPPORTED, "k > 16 is not compiled in this build");
+  if (!(lambda_L > 0) || !std::isfinite(lambda_L)) return set_err(nullptr, RPCA_EINVAL, "lambda_L must be finite and > 0");
+  if (!(lambda_S > 0)) return set_err(nullptr, RPCA_EINVAL, "lambda_S must be > 0 (+inf allowed)");
+  rpca_options o;
+  rpca_default_options(&o);
+  if (opt) o = *opt;
+  if (o.lbfgs_mem < 1 || o.lbfgs_mem > 32) return set_err(nullptr, RPCA_EINVAL, "lbfgs_mem must be in [1, 32]");
+  if (o.x_dtype != RPCA_F32) return set_err(nullptr, RPCA_EUNSUPPORTED, "only RPCA_F32 storage is built");
+
+  rpca_ctx* c = new (std::nothrow) rpca_ctx();
+  if (!c) return set_err(nullptr, RPCA_ENOMEM, "host allocation failed");
+  c->m = (int)m;
+  c->n = (int)n;
+  c->k = k;
+  c->X = X;
+  c->ldx = ldx;
+  c->mask = mask;
+  c->ldmask = ldmask;
+  c->lam_L = lambda_L;
+  c->lam_S = lambda_S;
+  c->opt = o;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  c->mpad = (int)((m + 3) / 4 * 4);
+  auto fail = [&](rpca_status s) {
+    g_create_err = c->err;
+    rpca_destroy(c);
+    return s;
+  };
+  cudaError_t e;
+  if ((e = cudaGetDevice(&c->device)) != cudaSuccess) return fail(cuda_err(c, e, "cudaGetDevice"));
+  int v = 0;
+  cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, c->device);
+  c->nsm = v;
+  cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
+  c->max_smem = (size_t)v;
+  int cc_major = 0, cc_minor = 0;
+  cudaDeviceGetAttribute(&cc_major, cudaDevAttrComputeCapabilityMajor, c->device);
+  cudaDeviceGetAttribute(&cc_minor, cudaDevAttrComputeCapabilityMinor, c->device);
+  if (cc_major != 10 || cc_minor != 3)
+    return fail(set_err(c, RPCA_EUNSUPPORTED, "this library is built for sm_103a (GB300) only"));
+
+  if ((e = cudaMalloc(&c->ws.counter, 64)) != cudaSuccess) return fail(cuda_err(c, e, "cudaMalloc"));
+  if ((e = cudaMalloc(&c->ws.out, 8 * sizeof(double))) != cudaSuccess) return fail(cuda_err(c, e, "cudaMalloc"));
+  if ((e = cudaMalloc(&c->ws.err, 64)) != cudaSuccess) return fail(cuda_err(c, e, "cudaMalloc"));
+  cudaMemsetAsync(c->ws.counter, 0, 64, c->stream);
+  cudaMemsetAsync(c->ws.err, 0, 64, c->stream);
+
+  // Validate X on the observed set.
+  unsigned long long* cnt = nullptr;
+  if ((e = cudaMalloc(&cnt, 2 * sizeof(unsigned long long))) != cudaSuccess) return fail(cuda_err(c, e, "cudaMalloc"));
+  cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), c->stream);
+  check_x_kernel<<<4 * c->nsm, 256, 0, c->stream>>>(X, ldx, mask, ldmask, c->m, c->n, cnt, cnt + 1);
+  unsigned long long hc[2] = {0, 0};
+  cudaMemcpyAsync(hc, cnt, sizeof hc, cudaMemcpyDeviceToHost, c->stream);
+  e = cudaStreamSynchronize(c->stream);
+  cudaFree(cnt);
+  if (e != cudaSuccess) return fail(cuda_err(c, e, "validating X"));
+  if (hc[0] != 0) return fail(set_err(c, RPCA_EINVAL, "X has non-finite observed entries"));
+  c->p_hat = (double)hc[1] / ((double)m * (double)n);
+
+  if (mask) {
+    c->wpad = (int)(((m + 31) / 32 + 3) / 4 * 4);
+    if ((e = cudaMalloc(&c->bits, (size_t)c->wpad * n * 4)) != cudaSuccess) return fail(cuda_err(c, e, "cudaMalloc"));
+    const int64_t warps = (int64_t)c->wpad * n;
+    pack_mask_kernel<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, c->stream>>>(mask, ldmask, c->m, c->n, c->wpad,
+                                                                                c->bits);
+    if ((e = cudaGetLastError()) != cudaSuccess) return fail(cuda_err(c, e, "pack_mask_kernel"));
+  }
+  rpca_status s = make_plan(c, &c->fg_plan, k, k, true);
+  if (s != RPCA_OK) return fail(s);
+  if ((s = size_workspace(c, c->fg_plan)) != RPCA_OK) return fail(s);
+  // Plans (and workspace sizes) of the apply kernels the certificate and the sketch use are
+  // fixed here, so that buffers captured in CUDA graphs never move afterwards.
+  if (!apply_plan(c, k) || !apply_plan(c, 0)) return fail(c->err.empty() ? RPCA_EUNSUPPORTED : RPCA_ECUDA);
+  if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return fail(cuda_err(c, e, "rpca_create"));
+  c->F_best = INFINITY;
+  c->F0 = NAN;
+  *out = c;
+  return RPCA_OK;
+}
+
+rpca_status rpca_fg(rpca_ctx* c, const float* U, const float* V, double* f, float* gU, float* gV) {
+  if (!c) return RPCA_EINVAL;
+  if (!U || !V || !gU || !gV) return set_err(c, RPCA_EINVAL, "U, V, gU and gV are required");
+  FgLaunch L;
+  L.U = U;
+  L.V = V;
+  L.GU = gU;
+  L.GV = gV;
+  L.out = c->ws.out;
+  rpca_status s = launch_fg(c, c->fg_plan, L, c->stream);
+  if (s != RPCA_OK) return s;
+  if (f) {
+    RPCA_CUDA(c, cudaMemcpyAsync(f, c->ws.out, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if ((s = check_dev_err(c)) != RPCA_OK) return s;
+    if (*f < c->F_best) c->F_best = *f;
+  }
+  return RPCA_OK;
+}
+
+rpca_status rpca_apply(rpca_ctx* c, const float* U, const float* V, int b, const float* Bv, const float* Bu,
+                       float* DBv, float* DtBu) {
+  if (!c) return RPCA_EINVAL;
+  if (!U || !V || !Bv || !Bu || !DBv || !DtBu) return set_err(c, RPCA_EINVAL, "null argument");
+  if (b < 1 || b > 8) return set_err(c, RPCA_EINVAL, "b must be in [1, 8]");
+  const FgPlan* P = apply_plan(c, c->k);
+  if (!P) return RPCA_EUNSUPPORTED;
+  // The kernel reads P->K columns of U, V and 8 of Bu, Bv: pass zero-padded copies.
+  const int Kp = P->K;
+  float *Up = nullptr, *Vp = nullptr, *Bup = nullptr, *Bvp = nullptr, *Y1 = nullptr, *Y2 = nullptr;
+  const size_t m = c->m, n = c->n;
+  cudaError_t e = cudaMalloc(&Up, sizeof(float) * (m * Kp + n * Kp + m * 8 + n * 8 + m * 8 + n * 8));
+  if (e != cudaSuccess) return cuda_err(c, e, "cudaMalloc");
+  Vp = Up + m * Kp;
+  Bup = Vp + n * Kp;
+  Bvp = Bup + m * 8;
+  Y1 = Bvp + n * 8;
+  Y2 = Y1 + m * 8;
+  cudaMemsetAsync(Up, 0, sizeof(float) * (m * Kp + n * Kp + m * 8 + n * 8), c->stream);
+  cudaMemcpyAsync(Up, U, sizeof(float) * m * c->k, cudaMemcpyDeviceToDevice, c->stream);
+  cudaMemcpyAsync(Vp, V, sizeof(float) * n * c->k, cudaMemcpyDeviceToDevice, c->stream);
+  cudaMemcpyAsync(Bup, Bu, sizeof(float) * m * b, cudaMemcpyDeviceToDevice, c->stream);
+  cudaMemcpyAsync(Bvp, Bv, sizeof(float) * n * b, cudaMemcpyDeviceToDevice, c->stream);
+  FgLaunch L;
+  L.U = Up;
+  L.V = Vp;
+  L.BU = Bup;
+  L.BV = Bvp;
+  L.fin_mode = FIN_APPLY;
+  L.GU = Y1;
+  L.GV = Y2;
+  rpca_status s = launch_fg(c, *P, L, c->stream);
+  if (s == RPCA_OK) {
+    cudaMemcpyAsync(DBv, Y1, sizeof(float) * m * b, cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(DtBu, Y2, sizeof(float) * n * b, cudaMemcpyDeviceToDevice, c->stream);
+    s = check_dev_err(c);
+  }
+  cudaStreamSynchronize(c->stream);
+  cudaFree(Up);
+  return s;
+}
+
+void rpca_destroy(rpca_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  free_solver(c);
+  free_cert(c);
+  cudaFree(c->bits);
+  cudaFree(c->ws.PU);
+  cudaFree(c->ws.PV);
+  cudaFree(c->ws.Ppsi);
+  cudaFree(c->ws.blk);
+  cudaFree(c->ws.counter);
+  cudaFree(c->ws.out);
+  cudaFree(c->ws.err);
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  delete c;
+}
+
+}  // extern "C"

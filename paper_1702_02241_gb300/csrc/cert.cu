@@ -1,0 +1,626 @@
+// Computable convergence certificate of Sec. 3.4 on the device.
+//
+// At L = U V^T the certificate is ||E||_F for an element E = lam_L Z + D of the
+// subdifferential of lam_L ||L||_* + phi(L), D = P_Omega(clip(U V^T - X)) (Sec. 3.2):
+//   ||E||_F^2 = t1 + t2 + t3 + t4,
+//   t1 = ||lam_L I + U1^T D V1||^2,  t2 = ||U1^T D V2||^2,  t3 = ||U2^T D V1||^2,
+//   t4 = sum_i (sigma_i(P_U1perp D P_V1perp) - lam_L)_+^2     (projection onto the ball)
+// with U1, V1 the singular vectors of L for its r nonzero singular values.
+//
+// Steps (all on the device, float64 unless noted):
+//  1. one pass over X: F(U, V) and the raw products DV = D V (m x k), DtU = D^T U (n x k);
+//  2. Gram matrices U^T U, V^T V, U^T (D V);
+//  3. one CTA: eigen-decompositions of the two Grams give orthonormal bases of range(U),
+//     range(V) (the thin-QR route of the footnote in Sec. 3.4, with rank-deficient factors
+//     allowed), the SVD of the small core M gives sigma(L), U1 = U T_U, V1 = V T_V, r, and
+//     B = U1^T D V1 = T_U^T (U^T D V) T_V, t1 = ||lam_L I + B||^2;
+//  4. t3 = ||D V1 - U1 B||^2 and t2 = ||D^T U1 - V1 B^T||^2 row by row (the same numbers as
+//     the paper's ||U1^T D||^2 - ||U1^T D V1||^2, without its cancellation near optimum);
+//  5. t4: block Golub-Kahan-Lanczos (block 8, full re-orthogonalisation) on
+//     P_U1perp D P_V1perp, whose products D Q and D^T P each take one pass over X through
+//     the fused kernel in apply mode; Ritz values from a float32 one-sided Jacobi SVD of the
+//     projected matrix T = P^T A Q; stops when the leading Ritz value and t4 settle.
+// Also F_bound = min(F(0), best F seen) and the gap bound cert * (||L||_F + F_bound/lam_L)
+// (Sec. 3.4, "Bounding the distance to the feasible set").
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "common.cuh"
+#include "ctx.h"
+#include "smallla.cuh"
+#include "tsla_ctx.h"
+
+namespace rpca {
+
+constexpr int CERT_KMAX = 16;
+constexpr int LZ_B = 8;       // Lanczos block size
+constexpr int LZ_SMAX = 32;   // maximum block steps (Krylov dimension 256)
+constexpr int LZ_TMAX = LZ_B * LZ_SMAX;
+constexpr double RANK_TAU = 1e-8;  // numerical rank of L: sigma_i > RANK_TAU * sigma_1
+constexpr double DROP_TAU = 1e-3;  // tiny-and-inactive directions go to the complement
+
+struct CertState {
+  double AUU[CERT_KMAX * CERT_KMAX], AVV[CERT_KMAX * CERT_KMAX], MUDV[CERT_KMAX * CERT_KMAX];
+  double TU[CERT_KMAX * CERT_KMAX], TV[CERT_KMAX * CERT_KMAX];  // k x r, ld KMAX
+  double P2[CERT_KMAX * CERT_KMAX], P3[CERT_KMAX * CERT_KMAX];  // T_U B, T_V B^T
+  double sig[CERT_KMAX];
+  int r;
+  double t1, t2, t3, t4, normL, sigma1;
+  double G[LZ_TMAX * LZ_B];    // Gram scratch (p x q)
+  double G2[LZ_TMAX * LZ_B];
+  double R[LZ_B * LZ_B], Rinv[LZ_B * LZ_B];
+  int bad_mask;  // columns whose Cholesky pivot collapsed in the last block QR
+  double t4_prev, s1_prev;
+  int converged;
+  double resid[2];
+};
+
+struct CertBuffers {
+  int Kp = 0;
+  float* DV = nullptr;   // m x k
+  float* DtU = nullptr;  // n x k
+  float* U1 = nullptr;   // m x KMAX
+  float* V1 = nullptr;   // n x KMAX
+  float* P = nullptr;    // m x TMAX
+  float* Q = nullptr;    // n x (TMAX + B)
+  float* W = nullptr;    // m x B
+  float* Z = nullptr;    // n x B
+  float* Up = nullptr;   // m x Kp (zero-padded U)
+  float* Vp = nullptr;   // n x Kp
+  float* zm = nullptr;   // m x max(B, k) zeros
+  float* zn = nullptr;   // n x max(B, k) zeros
+  double* T = nullptr;   // TMAX x TMAX
+  float* Tw = nullptr;   // TMAX x TMAX float32 working copy for the Ritz SVD
+  float* Tv = nullptr;   // TMAX x TMAX right vectors
+  float* Wraw = nullptr; // m x B, A Q_j before orthogonalisation
+  CertState* st = nullptr;
+  CertState* host = nullptr;
+  double* blk = nullptr;
+  unsigned int* counter = nullptr;
+  TsScratch ts;
+  bool have_F0 = false;
+};
+
+// ---------------------------------------------------------------------------------------------
+// Step 3: one CTA of 256 threads.
+__global__ void __launch_bounds__(256) cert_small_kernel(CertState* st, int k, double lam_L) {
+  __shared__ double Au[CERT_KMAX * CERT_KMAX], Wu[CERT_KMAX * CERT_KMAX], su[CERT_KMAX];
+  __shared__ double Av[CERT_KMAX * CERT_KMAX], Wv[CERT_KMAX * CERT_KMAX], sv[CERT_KMAX];
+  __shared__ double M[CERT_KMAX * CERT_KMAX], Vm[CERT_KMAX * CERT_KMAX], sm[CERT_KMAX];
+  __shared__ double Ru[CERT_KMAX * CERT_KMAX], Rv[CERT_KMAX * CERT_KMAX];
+  __shared__ int ordu[CERT_KMAX], ordv[CERT_KMAX], ordm[CERT_KMAX];
+  __shared__ int flag, ku, kv;
+  const int t = threadIdx.x;
+  for (int i = t; i < k * k; i += blockDim.x) {
+    const int a = i % k, b = i / k;
+    Au[i] = st->AUU[a + b * CERT_KMAX];
+    Av[i] = st->AVV[a + b * CERT_KMAX];
+  }
+  __syncthreads();
+  // Symmetric PSD Grams: the one-sided Jacobi SVD is their eigen-decomposition.
+  cta_jacobi_svd<double>(Au, k, k, k, Wu, k, su, &flag, 60, 1e-15);
+  cta_jacobi_svd<double>(Av, k, k, k, Wv, k, sv, &flag, 60, 1e-15);
+  cta_sort_desc<double>(su, k, ordu);
+  cta_sort_desc<double>(sv, k, ordv);
+  if (t == 0) {
+    // Eigen-directions kept for the range bases (float64 floor on the Gram eigenvalues).
+    ku = 0;
+    kv = 0;
+    for (int i = 0; i < k; ++i) ku += su[ordu[i]] > 1e-14 * su[ordu[0]] && su[ordu[i]] > 0.0;
+    for (int i = 0; i < k; ++i) kv += sv[ordv[i]] > 1e-14 * sv[ordv[0]] && sv[ordv[i]] > 0.0;
+  }
+  __syncthreads();
+  // R_U = Lambda_U^{1/2} W_U^T (ku x k) and R_V likewise; M = R_U R_V^T (ku x kv).
+  for (int i = t; i < ku * k; i += blockDim.x) {
+    const int a = i % ku, b = i / ku;
+    Ru[a + b * CERT_KMAX] = sqrt(su[ordu[a]]) * Wu[b + ordu[a] * k];
+  }
+  for (int i = t; i < kv * k; i += blockDim.x) {
+    const int a = i % kv, b = i / kv;
+    Rv[a + b * CERT_KMAX] = sqrt(sv[ordv[a]]) * Wv[b + ordv[a] * k];
+  }
+  __syncthreads();
+  for (int i = t; i < ku * kv; i += blockDim.x) {
+    const int a = i % ku, b = i / ku;
+    double s = 0.0;
+    for (int l = 0; l < k; ++l) s += Ru[a + l * CERT_KMAX] * Rv[b + l * CERT_KMAX];
+    M[a + b * ku] = s;
+  }
+  __syncthreads();
+  int r = 0;
+  if (ku > 0 && kv > 0) {
+    cta_jacobi_svd<double>(M, ku, kv, ku, Vm, kv, sm, &flag, 60, 1e-15);
+    cta_sort_desc<double>(sm, kv, ordm);
+    const double s1 = sm[ordm[0]];
+    for (int i = 0; i < std::min(ku, kv); ++i) r += (sm[ordm[i]] > RANK_TAU * s1 && s1 > 0.0);
+  }
+  __syncthreads();
+  // T_U = W_U Lambda_U^{-1/2} U_M[:, :r], U_M[:, c] = M_c / sigma_c; T_V = W_V Lambda_V^{-1/2} V_M[:, :r].
+  for (int i = t; i < k * r; i += blockDim.x) {
+    const int l = i % k, c = i / k;
+    const int jc = ordm[c];
+    double su_ = 0.0, sv_ = 0.0;
+    for (int a = 0; a < ku; ++a) su_ += Wu[l + ordu[a] * k] / sqrt(su[ordu[a]]) * (M[a + jc * ku] / sm[jc]);
+    for (int b = 0; b < kv; ++b) sv_ += Wv[l + ordv[b] * k] / sqrt(sv[ordv[b]]) * Vm[b + jc * kv];
+    st->TU[l + c * CERT_KMAX] = su_;
+    st->TV[l + c * CERT_KMAX] = sv_;
+  }
+  __syncthreads();
+  // B = T_U^T (U^T D V) T_V (r x r), t1, P2 = T_U B, P3 = T_V B^T.
+  __shared__ double Bs[CERT_KMAX * CERT_KMAX], Tmp[CERT_KMAX * CERT_KMAX];
+  for (int i = t; i < k * r; i += blockDim.x) {  // Tmp = (U^T D V) T_V   (k x r)
+    const int a = i % k, c = i / k;
+    double s = 0.0;
+    for (int l = 0; l < k; ++l) s += st->MUDV[a + l * CERT_KMAX] * st->TV[l + c * CERT_KMAX];
+    Tmp[a + c * CERT_KMAX] = s;
+  }
+  __syncthreads();
+  for (int i = t; i < r * r; i += blockDim.x) {
+    const int a = i % r, c = i / r;
+    double s = 0.0;
+    for (int l = 0; l < k; ++l) s += st->TU[l + a * CERT_KMAX] * Tmp[l + c * CERT_KMAX];
+    Bs[a + c * CERT_KMAX] = s;
+  }
+  __syncthreads();
+  // A direction that is both tiny (sigma_i <= DROP_TAU sigma_1) and inactive
+  // (|lam_L + u_i^T D v_i| > lam_L / 2) is moved to the complement block: it is rounding
+  // residue of a factor column that the nuclear penalty drives to zero, and the certificate
+  // is then that of L with it truncated.
+  __shared__ int keep[CERT_KMAX], rk;
+  if (t == 0) {
+    rk = 0;
+    for (int c = 0; c < r; ++c) {
+      const bool tiny = sm[ordm[c]] <= DROP_TAU * sm[ordm[0]];
+      const bool inactive = fabs(lam_L + Bs[c + c * CERT_KMAX]) > 0.5 * lam_L;
+      if (!(tiny && inactive)) keep[rk++] = c;
+    }
+    if (rk < r) {
+      for (int q = 0; q < rk; ++q) {
+        for (int l = 0; l < k; ++l) {
+          st->TU[l + q * CERT_KMAX] = st->TU[l + keep[q] * CERT_KMAX];
+          st->TV[l + q * CERT_KMAX] = st->TV[l + keep[q] * CERT_KMAX];
+        }
+      }
+      for (int q = 0; q < rk; ++q)
+        for (int q2 = 0; q2 < rk; ++q2) Tmp[q + q2 * CERT_KMAX] = Bs[keep[q] + keep[q2] * CERT_KMAX];
+      for (int q = 0; q < rk; ++q)
+        for (int q2 = 0; q2 < rk; ++q2) Bs[q + q2 * CERT_KMAX] = Tmp[q + q2 * CERT_KMAX];
+    }
+  }
+  __syncthreads();
+  r = rk;
+  for (int i = t; i < k * r; i += blockDim.x) {
+    const int l = i % k, c = i / k;
+    double s2 = 0.0, s3 = 0.0;
+    for (int a = 0; a < r; ++a) {
+      s2 += st->TU[l + a * CERT_KMAX] * Bs[a + c * CERT_KMAX];
+      s3 += st->TV[l + a * CERT_KMAX] * Bs[c + a * CERT_KMAX];
+    }
+    st->P2[l + c * CERT_KMAX] = s2;
+    st->P3[l + c * CERT_KMAX] = s3;
+  }
+  if (t == 0) {
+    double t1 = 0.0;
+    for (int a = 0; a < r; ++a)
+      for (int c = 0; c < r; ++c) {
+        const double e = Bs[a + c * CERT_KMAX] + (a == c ? lam_L : 0.0);
+        t1 += e * e;
+      }
+    double nl = 0.0;
+    for (int i = 0; i < std::min(ku, kv); ++i) nl += sm[ordm[i]] * sm[ordm[i]];
+    st->t1 = t1;
+    st->r = r;
+    st->normL = sqrt(nl);
+    for (int i = 0; i < CERT_KMAX; ++i) st->sig[i] = i < std::min(ku, kv) ? sm[ordm[i]] : 0.0;
+  }
+}
+
+// Step 4: sum over rows of ||A_i T - C_i P||^2 (A, C rows x k; T, P k x r), float64.
+__global__ void __launch_bounds__(256) cert_resid_kernel(const float* A, const float* Cm, int64_t rows, int k,
+                                                         const CertState* st, int which, double* blk,
+                                                         unsigned int* counter, CertState* out) {
+  __shared__ double Ts[CERT_KMAX * CERT_KMAX], Ps[CERT_KMAX * CERT_KMAX];
+  __shared__ double scr[32];
+  __shared__ bool is_last;
+  const int r = st->r;
+  const double* T = which == 0 ? st->TV : st->TU;
+  const double* P = which == 0 ? st->P2 : st->P3;
+  for (int i = threadIdx.x; i < CERT_KMAX * CERT_KMAX; i += blockDim.x) {
+    Ts[i] = T[i];
+    Ps[i] = P[i];
+  }
+  __syncthreads();
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < rows; i += (int64_t)gridDim.x * blockDim.x) {
+    double a[CERT_KMAX], cc[CERT_KMAX];
+    for (int l = 0; l < k; ++l) {
+      a[l] = A[i + (int64_t)l * rows];
+      cc[l] = Cm[i + (int64_t)l * rows];
+    }
+    for (int c = 0; c < r; ++c) {
+      double e = 0.0;
+      for (int l = 0; l < k; ++l) e += a[l] * Ts[l + c * CERT_KMAX] - cc[l] * Ps[l + c * CERT_KMAX];
+      acc += e * e;
+    }
+  }
+  acc = block_sum_d(acc, scr);
+  if (threadIdx.x == 0) {
+    blk[blockIdx.x] = acc;
+    __threadfence();
+    is_last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  double s = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) s += __ldcg(&blk[b]);
+  s = block_sum_d(s, scr);
+  if (threadIdx.x == 0) {
+    out->resid[which] = s;
+    *counter = 0u;
+  }
+}
+
+// Cholesky of the 8 x 8 Gram in st->G; records the columns whose pivot collapsed (that
+// column is numerically in the span of the earlier ones).
+__global__ void cert_chol_kernel(CertState* st) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double dmax = 0.0;
+  for (int i = 0; i < LZ_B; ++i) dmax = fmax(dmax, st->G[i + i * LZ_B]);
+  chol_upper_inv(st->G, LZ_B, st->R, st->Rinv);
+  int mask = 0;
+  for (int i = 0; i < LZ_B; ++i)
+    if (!(st->R[i + i * LZ_B] * st->R[i + i * LZ_B] > 1e-12 * fmax(dmax, 1e-300))) mask |= 1 << i;
+  st->bad_mask = mask;
+}
+
+// Collapsed columns of Y (rows x 8) are replaced by fresh Gaussian columns.
+__global__ void cert_refill_kernel(float* Y, int64_t rows, const CertState* st, uint64_t seed) {
+  const int mask = st->bad_mask;
+  if (mask == 0) return;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < rows * LZ_B; i += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(i / rows);
+    if ((mask >> c) & 1) {
+      uint64_t z = seed * 0x9E3779B97F4A7C15ull + (uint64_t)i;
+      z += 0x9e3779b97f4a7c15ull;
+      z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+      z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+      z ^= z >> 31;
+      Y[i] = (float)((double)(z >> 11) * (1.0 / 9007199254740992.0) - 0.5);
+    }
+  }
+}
+
+// T[0:p, col:col+8] = st->G (p x 8): the block P^T (A Q_j) of the projected matrix.
+__global__ void cert_store_T_kernel(const CertState* st, double* T, int p, int col) {
+  for (int i = threadIdx.x; i < p * LZ_B; i += blockDim.x) {
+    const int a = i % p, b = i / p;
+    T[a + (int64_t)(col + b) * LZ_TMAX] = st->G[i];
+  }
+}
+
+__global__ void cert_zero_T_kernel(double* T) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < LZ_TMAX * LZ_TMAX; i += gridDim.x * blockDim.x) T[i] = 0.0;
+}
+
+__global__ void cert_reset_kernel(CertState* st) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  st->bad_mask = 0;
+  st->t4_prev = -1.0;
+  st->s1_prev = -1.0;
+  st->converged = 0;
+  st->t4 = 0.0;
+  st->sigma1 = 0.0;
+}
+
+// Ritz values of T[0:d, 0:d] (float32 one-sided Jacobi in global memory) -> t4 estimate,
+// sigma_1, and whether both have settled since the previous check.
+__global__ void __launch_bounds__(1024) cert_ritz_kernel(CertState* st, const double* T, float* A, float* V, int d,
+                                                          double lam_L, int final_step) {
+  __shared__ float s[LZ_TMAX];
+  __shared__ int ord[LZ_TMAX];
+  __shared__ int flag;
+  for (int i = threadIdx.x; i < d * d; i += blockDim.x) {
+    const int a = i % d, b = i / d;
+    A[i] = (float)T[a + (int64_t)b * LZ_TMAX];
+  }
+  __syncthreads();
+  cta_jacobi_svd<float>(A, d, d, d, V, d, s, &flag, 40, 1e-7f);
+  cta_sort_desc<float>(s, d, ord);
+  if (threadIdx.x == 0) {
+    double t4 = 0.0;
+    for (int i = 0; i < d; ++i) {
+      const double e = (double)s[i] - lam_L;
+      if (e > 0.0) t4 += e * e;
+    }
+    const double s1 = s[ord[0]];
+    const bool settled = st->s1_prev >= 0.0 && fabs(s1 - st->s1_prev) <= 1e-5 * s1 &&
+                         fabs(t4 - st->t4_prev) <= 1e-4 * t4 + 1e-12 * lam_L * lam_L;
+    st->converged = settled || final_step;
+    st->t4_prev = t4;
+    st->s1_prev = s1;
+    st->t4 = t4;
+    st->sigma1 = s1;
+  }
+}
+
+__global__ void pad_copy_kernel(const float* src, int64_t rows, int k, float* dst, int kp) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < rows * kp; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = i / rows;
+    dst[i] = c < k ? src[i] : 0.f;
+  }
+}
+
+void fill_normal(float* out, int64_t count, uint64_t seed, float scale, cudaStream_t s);
+
+// ---------------------------------------------------------------------------------------------
+void free_cert(rpca_ctx* c) {
+  CertBuffers* b = c->cert;
+  if (!b) return;
+  cudaFree(b->DV);
+  cudaFree(b->T);
+  cudaFree(b->st);
+  cudaFree(b->blk);
+  cudaFree(b->counter);
+  cudaFree(b->ts.part);
+  cudaFree(b->ts.counter);
+  cudaFreeHost(b->host);
+  delete b;
+  c->cert = nullptr;
+}
+
+#define CERT_CUDA(call)                                   \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) return cuda_err(c, e_, #call); \
+  } while (0)
+
+static rpca_status ensure_cert(rpca_ctx* c) {
+  if (c->cert) return RPCA_OK;
+  CertBuffers* b = new CertBuffers();
+  c->cert = b;
+  const int64_t m = c->m, n = c->n, k = c->k;
+  b->Kp = k <= 8 ? 8 : 16;
+  const int zc = std::max<int>(LZ_B, (int)k);
+  const int64_t nf = m * k + n * k + m * CERT_KMAX + n * CERT_KMAX + m * LZ_TMAX + n * (LZ_TMAX + LZ_B) + m * LZ_B +
+                     n * LZ_B + m * b->Kp + n * b->Kp + m * zc + n * zc + m * LZ_B + 2 * LZ_TMAX * LZ_TMAX;
+  CERT_CUDA(cudaMalloc(&b->DV, sizeof(float) * nf));
+  float* p = b->DV;
+  p += m * k;
+  b->DtU = p;
+  p += n * k;
+  b->U1 = p;
+  p += m * CERT_KMAX;
+  b->V1 = p;
+  p += n * CERT_KMAX;
+  b->P = p;
+  p += m * LZ_TMAX;
+  b->Q = p;
+  p += n * (LZ_TMAX + LZ_B);
+  b->W = p;
+  p += m * LZ_B;
+  b->Z = p;
+  p += n * LZ_B;
+  b->Up = p;
+  p += m * b->Kp;
+  b->Vp = p;
+  p += n * b->Kp;
+  b->zm = p;
+  p += m * zc;
+  b->zn = p;
+  p += n * zc;
+  b->Wraw = p;
+  p += m * LZ_B;
+  b->Tw = p;
+  p += LZ_TMAX * LZ_TMAX;
+  b->Tv = p;
+  CERT_CUDA(cudaMemsetAsync(b->zm, 0, sizeof(float) * (m + n) * zc, c->stream));
+  CERT_CUDA(cudaMalloc(&b->T, sizeof(double) * LZ_TMAX * LZ_TMAX));
+  CERT_CUDA(cudaMalloc(&b->st, sizeof(CertState)));
+  CERT_CUDA(cudaMemsetAsync(b->st, 0, sizeof(CertState), c->stream));
+  CERT_CUDA(cudaMallocHost(&b->host, sizeof(CertState)));
+  CERT_CUDA(cudaMalloc(&b->blk, sizeof(double) * 4 * c->nsm));
+  CERT_CUDA(cudaMalloc(&b->counter, 64));
+  CERT_CUDA(cudaMemsetAsync(b->counter, 0, 64, c->stream));
+  b->ts.grid = 2 * c->nsm;
+  b->ts.part_n = (size_t)b->ts.grid * 2048;
+  CERT_CUDA(cudaMalloc(&b->ts.part, sizeof(double) * b->ts.part_n));
+  CERT_CUDA(cudaMalloc(&b->ts.counter, 64));
+  CERT_CUDA(cudaMemsetAsync(b->ts.counter, 0, 64, c->stream));
+  return RPCA_OK;
+}
+
+// Y (rows x 8) <- Y - B (B^T Y) for a basis B (rows x p, orthonormal columns).
+static rpca_status project_out(rpca_ctx* c, const float* Bm, int p, float* Y, int64_t rows) {
+  CertBuffers* b = c->cert;
+  if (p == 0) return RPCA_OK;
+  CERT_CUDA(ts_gram_c(c, Bm, rows, p, Y, rows, LZ_B, rows, b->st->G2, b->ts, c->stream));
+  CERT_CUDA(ts_mul_c(c, Bm, rows, p, b->st->G2, p, LZ_B, Y, rows, rows, -1.f, 1.f, c->stream));
+  return RPCA_OK;
+}
+
+static rpca_status chol_pass(rpca_ctx* c, float* Y, int64_t rows) {
+  CertBuffers* b = c->cert;
+  CERT_CUDA(ts_gram_c(c, Y, rows, LZ_B, Y, rows, LZ_B, rows, b->st->G, b->ts, c->stream));
+  cert_chol_kernel<<<1, 1, 0, c->stream>>>(b->st);
+  count_launches(c, 1);
+  CERT_CUDA(ts_mul_c(c, Y, rows, LZ_B, b->st->Rinv, LZ_B, LZ_B, Y, rows, rows, 1.f, 0.f, c->stream));
+  return RPCA_OK;
+}
+
+// Orthonormalises the block Y (rows x 8) against the fixed basis F (rows x f) and the
+// Krylov basis B (rows x p): two rounds of classical Gram-Schmidt and CholeskyQR; columns
+// that collapse in the first round are replaced by random ones, which the second round
+// orthonormalises.  All on the stream, no host synchronisation.
+static rpca_status orth_block(rpca_ctx* c, float* Y, int64_t rows, const float* F, int f, const float* Bm, int p,
+                              uint64_t seed) {
+  rpca_status s;
+  for (int round = 0; round < 2; ++round) {
+    if ((s = project_out(c, F, f, Y, rows)) != RPCA_OK) return s;
+    if ((s = project_out(c, Bm, p, Y, rows)) != RPCA_OK) return s;
+    if ((s = project_out(c, F, f, Y, rows)) != RPCA_OK) return s;
+    if ((s = project_out(c, Bm, p, Y, rows)) != RPCA_OK) return s;
+    if ((s = chol_pass(c, Y, rows)) != RPCA_OK) return s;
+    if (round == 0) {
+      cert_refill_kernel<<<256, 256, 0, c->stream>>>(Y, rows, c->cert->st, seed);
+      count_launches(c, 1);
+    }
+  }
+  return RPCA_OK;
+}
+
+static rpca_status apply_D(rpca_ctx* c, const float* BV, const float* BU, float* Y1, float* Y2) {
+  CertBuffers* b = c->cert;
+  const FgPlan* P = apply_plan(c, c->k);
+  if (!P) return RPCA_EUNSUPPORTED;
+  FgLaunch L;
+  L.U = b->Up;
+  L.V = b->Vp;
+  L.BU = BU;
+  L.BV = BV;
+  L.fin_mode = FIN_APPLY;
+  L.GU = Y1;
+  L.GV = Y2;
+  return launch_fg(c, *P, L, c->stream);
+}
+
+rpca_status cert_compute(rpca_ctx* c, const float* U, const float* V, rpca_cert* out, bool full) {
+  rpca_status s = ensure_cert(c);
+  if (s != RPCA_OK) return s;
+  CertBuffers* b = c->cert;
+  const int64_t m = c->m, n = c->n;
+  const int k = c->k;
+  CertState* st = b->st;
+  cert_reset_kernel<<<1, 1, 0, c->stream>>>(st);
+  count_launches(c, 1);
+  // F(0) = phi(0) once per context (distance bound).
+  if (!b->have_F0) {
+    FgLaunch L0;
+    L0.U = b->zm;
+    L0.V = b->zn;
+    L0.GU = b->DV;
+    L0.GV = b->DtU;
+    L0.fin_mode = FIN_FG_RAW;
+    L0.out = c->ws.out + 4;
+    if ((s = launch_fg(c, c->fg_plan, L0, c->stream)) != RPCA_OK) return s;
+    double f0 = 0;
+    CERT_CUDA(cudaMemcpyAsync(&f0, c->ws.out + 4, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CERT_CUDA(cudaStreamSynchronize(c->stream));
+    c->F0 = f0;
+    b->have_F0 = true;
+  }
+  // 1. F and the raw products.
+  FgLaunch L;
+  L.U = U;
+  L.V = V;
+  L.GU = b->DV;
+  L.GV = b->DtU;
+  L.fin_mode = FIN_FG_RAW;
+  L.out = c->ws.out;
+  if ((s = launch_fg(c, c->fg_plan, L, c->stream)) != RPCA_OK) return s;
+  // 2. Grams.
+  CERT_CUDA(ts_gram_c(c, U, m, k, U, m, k, m, st->G, b->ts, c->stream));
+  CERT_CUDA(cudaMemcpy2DAsync(st->AUU, CERT_KMAX * 8, st->G, k * 8, k * 8, k, cudaMemcpyDeviceToDevice, c->stream));
+  CERT_CUDA(ts_gram_c(c, V, n, k, V, n, k, n, st->G, b->ts, c->stream));
+  CERT_CUDA(cudaMemcpy2DAsync(st->AVV, CERT_KMAX * 8, st->G, k * 8, k * 8, k, cudaMemcpyDeviceToDevice, c->stream));
+  CERT_CUDA(ts_gram_c(c, U, m, k, b->DV, m, k, m, st->G, b->ts, c->stream));
+  CERT_CUDA(cudaMemcpy2DAsync(st->MUDV, CERT_KMAX * 8, st->G, k * 8, k * 8, k, cudaMemcpyDeviceToDevice, c->stream));
+  // 3. Small factorisations, t1.
+  cert_small_kernel<<<1, 256, 0, c->stream>>>(st, k, c->lam_L);
+  count_launches(c, 1);
+  CERT_CUDA(cudaGetLastError());
+  // 4. t3 = ||DV T_V - U P2||^2, t2 = ||DtU T_U - V P3||^2.
+  const int rg = (int)std::min<int64_t>(2 * c->nsm, (std::max(m, n) + 255) / 256);
+  cert_resid_kernel<<<std::max(1, (int)std::min<int64_t>(rg, (m + 255) / 256)), 256, 0, c->stream>>>(
+      b->DV, U, m, k, st, 0, b->blk, b->counter, st);
+  count_launches(c, 1);
+  cert_resid_kernel<<<std::max(1, (int)std::min<int64_t>(rg, (n + 255) / 256)), 256, 0, c->stream>>>(
+      b->DtU, V, n, k, st, 1, b->blk, b->counter, st);
+  count_launches(c, 1);
+  CERT_CUDA(cudaGetLastError());
+  CERT_CUDA(cudaMemcpyAsync(b->host, st, sizeof(CertState), cudaMemcpyDeviceToHost, c->stream));
+  double F = 0;
+  CERT_CUDA(cudaMemcpyAsync(&F, c->ws.out, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CERT_CUDA(cudaStreamSynchronize(c->stream));
+  const int r = b->host->r;
+  int steps = 0;
+  if (full) {
+    // 5. t4 by block Golub-Kahan-Lanczos on A = P_U1perp D P_V1perp.
+    CERT_CUDA(ts_mul_c(c, U, m, k, st->TU, CERT_KMAX, std::max(r, 1), b->U1, m, m, 1.f, 0.f, c->stream));
+    CERT_CUDA(ts_mul_c(c, V, n, k, st->TV, CERT_KMAX, std::max(r, 1), b->V1, n, n, 1.f, 0.f, c->stream));
+    pad_copy_kernel<<<256, 256, 0, c->stream>>>(U, m, k, b->Up, b->Kp);
+    count_launches(c, 1);
+    pad_copy_kernel<<<256, 256, 0, c->stream>>>(V, n, k, b->Vp, b->Kp);
+    count_launches(c, 1);
+    cert_zero_T_kernel<<<64, 256, 0, c->stream>>>(b->T);
+    count_launches(c, 1);
+    fill_normal(b->Q, n * LZ_B, 0x5eedULL + (uint64_t)c->opt.seed, 1.f, c->stream);
+    count_launches(c, 1);
+    if ((s = orth_block(c, b->Q, n, b->V1, r, nullptr, 0, 11)) != RPCA_OK) return s;
+    // Krylov dimension cap: 256, or the dimension of the complement of range(V1).
+    const int64_t room = std::max<int64_t>(1, std::min(m, n) - r);
+    const int smax = (int)std::min<int64_t>(LZ_SMAX, (room + LZ_B - 1) / LZ_B);
+    for (int j = 0; j < smax; ++j) {
+      float* Qj = b->Q + (int64_t)j * LZ_B * n;
+      float* Pj = b->P + (int64_t)j * LZ_B * m;
+      // A Q_j = P_U1perp D Q_j  (Q_j is orthogonal to V1 by construction).
+      if ((s = apply_D(c, Qj, b->zm, b->Wraw, b->Z)) != RPCA_OK) return s;
+      if ((s = project_out(c, b->U1, r, b->Wraw, m)) != RPCA_OK) return s;
+      if ((s = project_out(c, b->U1, r, b->Wraw, m)) != RPCA_OK) return s;
+      CERT_CUDA(cudaMemcpyAsync(Pj, b->Wraw, sizeof(float) * m * LZ_B, cudaMemcpyDeviceToDevice, c->stream));
+      if ((s = orth_block(c, Pj, m, b->U1, r, b->P, j * LZ_B, 1000 + 2 * j)) != RPCA_OK) return s;
+      // Column block j of T = P^T A Q.
+      CERT_CUDA(ts_gram_c(c, b->P, m, (j + 1) * LZ_B, b->Wraw, m, LZ_B, m, st->G, b->ts, c->stream));
+      cert_store_T_kernel<<<1, 256, 0, c->stream>>>(st, b->T, (j + 1) * LZ_B, j * LZ_B);
+      count_launches(c, 1);
+      steps = j + 1;
+      const bool last = (j == smax - 1);
+      if (steps == 2 || (steps % 4) == 0 || last) {
+        cert_ritz_kernel<<<1, 1024, 0, c->stream>>>(st, b->T, b->Tw, b->Tv, steps * LZ_B, c->lam_L, last ? 1 : 0);
+        count_launches(c, 1);
+        CERT_CUDA(cudaGetLastError());
+        int conv = 0;
+        CERT_CUDA(cudaMemcpyAsync(&conv, &st->converged, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        CERT_CUDA(cudaStreamSynchronize(c->stream));
+        if (conv) break;
+      }
+      // Q_{j+1} from A^T P_j = P_V1perp D^T P_j, orthogonal to V1 and Q_0..Q_j.
+      float* Qn = b->Q + (int64_t)(j + 1) * LZ_B * n;
+      if ((s = apply_D(c, b->zn, Pj, b->W, Qn)) != RPCA_OK) return s;
+      if ((s = orth_block(c, Qn, n, b->V1, r, b->Q, (j + 1) * LZ_B, 1001 + 2 * j)) != RPCA_OK) return s;
+    }
+  }
+  CERT_CUDA(cudaMemcpyAsync(b->host, st, sizeof(CertState), cudaMemcpyDeviceToHost, c->stream));
+  CERT_CUDA(cudaStreamSynchronize(c->stream));
+  if ((s = check_dev_err(c)) != RPCA_OK) return s;
+  const CertState& h = *b->host;
+  rpca_cert o;
+  memset(&o, 0, sizeof o);
+  o.t1 = h.t1;
+  o.t2 = h.resid[1];
+  o.t3 = h.resid[0];
+  o.t4 = full ? h.t4 : 0.0;
+  o.cert = std::sqrt(std::max(0.0, o.t1 + o.t2 + o.t3 + o.t4));
+  o.cert_rel = o.cert / c->lam_L;
+  o.normL_F = h.normL;
+  o.F = F;
+  if (F < c->F_best) c->F_best = F;
+  o.F_bound = std::min(c->F0, c->F_best);
+  o.gap_bound = o.cert * (o.normL_F + o.F_bound / c->lam_L);
+  o.rank_r = h.r;
+  o.krylov_steps = steps;
+  o.sigma1_perp = full ? h.sigma1 : 0.0;
+  *out = o;
+  return RPCA_OK;
+}
+
+}  // namespace rpca
+
+using namespace rpca;
+
+extern "C" rpca_status rpca_certificate(rpca_ctx* c, const float* U, const float* V, rpca_cert* out) {
+  if (!c) return RPCA_EINVAL;
+  if (!U || !V || !out) return set_err(c, RPCA_EINVAL, "U, V and out are required");
+  return cert_compute(c, U, V, out, true);
+}

@@ -1,0 +1,141 @@
+// Shared device helpers: packed fp32 math, mbarrier / TMA inline PTX, bounded waits,
+// deterministic block reductions.  sm_103a only.
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define RPCA_DEV __device__ __forceinline__
+
+namespace rpca {
+
+// Error bits written to the device status word by kernels whose bounded waits give up.
+enum : int { DEV_ERR_TIMEOUT_FULL = 1, DEV_ERR_TIMEOUT_EMPTY = 2, DEV_ERR_TIMEOUT_DRAIN = 4 };
+
+// Wait limit for every spin on an mbarrier: 2 s of %globaltimer.
+constexpr uint64_t kWaitLimitNs = 2000000000ull;
+
+RPCA_DEV uint64_t globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+RPCA_DEV float2 f2(float a, float b) { return make_float2(a, b); }
+RPCA_DEV float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+RPCA_DEV float2 fadd2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+
+RPCA_DEV uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// ---- mbarrier ------------------------------------------------------------------------
+RPCA_DEV void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+RPCA_DEV void fence_barrier_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+RPCA_DEV void mbar_arrive(uint64_t* bar) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(bar))
+               : "memory");
+}
+RPCA_DEV void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(
+                   smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+RPCA_DEV bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait on phase `parity`; returns false (and the caller must bail out) after the limit.
+RPCA_DEV bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer();
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (globaltimer() - t0 > kWaitLimitNs) return false;
+  }
+}
+
+// ---- TMA (tiled tensor copies, no multicast) --------------------------------------------
+RPCA_DEV void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+      "[%4];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+RPCA_DEV void prefetch_tmap(const CUtensorMap* map) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+
+// Named barrier over `nthreads` threads (ids 1..15; 0 is __syncthreads).
+RPCA_DEV void named_bar(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// ---- warp reduce-scatter of C floats over 32 lanes -----------------------------------
+// After the call every lane holds rs_count(C) fully reduced values v[0..), standing for the
+// original indices base + t.  Lanes that differ only in the bits of rs_dup_mask(C) hold the
+// same values; exactly the lanes with (lane & rs_dup_mask(C)) == 0 should publish them.
+__host__ __device__ constexpr int rs_count(int c, int o = 16) {
+  return o == 0 ? c : (c % 2 == 0 ? rs_count(c / 2, o / 2) : rs_count(c, o / 2));
+}
+__host__ __device__ constexpr int rs_dup_mask(int c, int o = 16) {
+  return o == 0 ? 0 : (c % 2 == 0 ? rs_dup_mask(c / 2, o / 2) : (o | rs_dup_mask(c, o / 2)));
+}
+template <int C, int O>
+struct ReduceScatter {
+  static RPCA_DEV void run(float* v, int lane, int& base) {
+    if constexpr (O == 0) {
+      return;
+    } else if constexpr (C % 2 == 0) {
+      constexpr int H = C / 2;
+      const bool up = (lane & O) != 0;
+#pragma unroll
+      for (int t = 0; t < H; ++t) {
+        const float send = up ? v[t] : v[t + H];
+        const float keep = up ? v[t + H] : v[t];
+        v[t] = keep + __shfl_xor_sync(0xffffffffu, send, O);
+      }
+      if (up) base += H;
+      ReduceScatter<H, O / 2>::run(v, lane, base);
+    } else {
+#pragma unroll
+      for (int t = 0; t < C; ++t) v[t] += __shfl_xor_sync(0xffffffffu, v[t], O);
+      ReduceScatter<C, O / 2>::run(v, lane, base);
+    }
+  }
+};
+
+RPCA_DEV double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Deterministic block sum of one double per thread (blockDim.x <= 1024); result valid in
+// thread 0.  `scratch` holds >= 32 doubles.
+RPCA_DEV double block_sum_d(double v, double* scratch) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  v = warp_sum_d(v);
+  __syncthreads();
+  if (lane == 0) scratch[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    for (int i = 0; i < nw; ++i) s += scratch[i];
+  }
+  return s;
+}
+
+}  // namespace rpca

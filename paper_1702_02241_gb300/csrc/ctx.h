@@ -1,0 +1,115 @@
+// Private host-side state of an rpca_ctx.
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/rpca.h"
+#include "fg_variants.h"
+#include "kernels.h"
+
+namespace rpca {
+
+// One launch configuration of the fused kernel for a (K, B, mode, mask) combination.
+struct FgPlan {
+  bool valid = false;
+  const FgVariant* var = nullptr;
+  int K = 0, B = 0;
+  bool same = true, masked = false;
+  int R = 0, WC = 0, nrb = 0, ncs = 0, BN = 0;
+  int threads = 0;
+  size_t smem = 0;
+  int fin_grid = 0;
+  int cps = 0;  // CTAs per SM at this configuration
+  CUtensorMap tmX;  // box {32 R rows, 8 columns}
+  CUtensorMap tmM;  // bitmap box {WC * R words, 8 columns}
+};
+
+struct Workspace {
+  float* PU = nullptr;
+  size_t PU_n = 0;
+  float* PV = nullptr;
+  size_t PV_n = 0;
+  double* Ppsi = nullptr;
+  size_t Ppsi_n = 0;
+  double* blk = nullptr;
+  size_t blk_n = 0;
+  unsigned int* counter = nullptr;
+  double* out = nullptr;  // [8]
+  int* err = nullptr;     // device status word
+};
+
+struct SolverBuffers;  // solver.cu
+struct CertBuffers;    // cert.cu
+
+}  // namespace rpca
+
+struct rpca_ctx {
+  int m = 0, n = 0, k = 0;
+  const float* X = nullptr;
+  int64_t ldx = 0;
+  const uint8_t* mask = nullptr;
+  int64_t ldmask = 0;
+  double lam_L = 0, lam_S = 0;
+  rpca_options opt;
+  cudaStream_t stream = nullptr;
+  int device = 0, nsm = 0;
+  size_t max_smem = 0;
+  int mpad = 0;
+  uint32_t* bits = nullptr;  // observation bitmap [n][wpad], owned
+  int wpad = 0;
+  double p_hat = 1.0;        // observed fraction
+  double F0 = 0.0;           // F(0) = phi(0), for the distance bound
+  double F_best = 0.0;       // best objective seen on this context
+  rpca::FgPlan fg_plan;      // K = k, fg mode
+  rpca::FgPlan ap_plan[3];   // apply modes: (0,16), (8,8), (16,8)
+  rpca::Workspace ws;
+  rpca::SolverBuffers* sol = nullptr;
+  rpca::CertBuffers* cert = nullptr;
+  std::string err;
+  // Instrumentation (rpca_profile).
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_pool;  // pairs: fused kernel start/stop, finalize start/stop
+  size_t ev_used = 0;
+  double prof_ms[2] = {0, 0};
+  int64_t prof_n[2] = {0, 0};
+  int64_t launches = 0;
+  int64_t graph_launches = 0;
+};
+
+namespace rpca {
+
+rpca_status set_err(rpca_ctx* c, rpca_status s, const std::string& msg);
+rpca_status cuda_err(rpca_ctx* c, cudaError_t e, const char* what);
+rpca_status check_dev_err(rpca_ctx* c);
+
+// Launches fused kernel + finalize for plan P.  fin_mode FIN_FG: (GU, GV) <- gradient at
+// the trial point, out[0..3] <- f, g.d, ||g||^2, ||x||^2.  FIN_APPLY: GU <- D Bv, GV <- D^T Bu.
+struct FgLaunch {
+  const float* U = nullptr;
+  const float* V = nullptr;
+  const float* dU = nullptr;
+  const float* dV = nullptr;
+  float alpha = 0.f;
+  const double* alpha_dev = nullptr;
+  const int* gate = nullptr;
+  const float* BU = nullptr;
+  const float* BV = nullptr;
+  int fin_mode = FIN_FG;
+  float* GU = nullptr;
+  float* GV = nullptr;
+  float* Ut = nullptr;
+  float* Vt = nullptr;
+  const float* DU = nullptr;
+  const float* DV = nullptr;
+  double* out = nullptr;
+  double lam = -1.0;  // clip threshold override (< 0: the context's lam_S; +inf allowed)
+};
+rpca_status launch_fg(rpca_ctx* c, const FgPlan& P, const FgLaunch& L, cudaStream_t stream);
+const FgPlan* apply_plan(rpca_ctx* c, int K);  // plan for forming rank >= K (0, 8 or 16)
+inline void count_launches(rpca_ctx* c, int64_t n) { c->launches += n; }
+
+}  // namespace rpca

@@ -1,0 +1,384 @@
+// Fused evaluation of the Split-SPCP objective and gradient (paper Eq. Thm5 / Eq. 7,
+// gradient from Sec. 3.2, masked form Sec. 6.2) in one pass over X.
+//
+// For a tile of X (rows [row0, row0+BM) x columns [col0, col0+BN)) a CTA forms
+//   r_ij = (u_i . v_j) - x_ij,  d_ij = clip(r_ij, +-lam_S) (0 off the mask),
+//   psi_ij = d_ij (r_ij - d_ij / 2)                       (Huber value, Sec. 1)
+// and accumulates  PU = -(D Bv) over its columns,  PV = D^T Bu over its rows,  sum psi.
+// In "fg" mode Bu = u and Bv = v (so PU, PV give the gradient terms D V and D^T U); in
+// "apply" mode Bu, Bv are other matrices (the certificate's spectral step and the sketch).
+// R = U V^T - X is never written to memory.
+//
+// Layout: X, U, V, Bu, Bv column-major.  One producer warp streams X (and the observation
+// bitmap) into a ring of shared-memory stages with 2-D TMA tensor copies; WC consumer warps
+// each own 32*R rows of the tile (R rows per lane, as float2 pairs for the packed fp32x2
+// FMA pipe) and walk the tile's columns.  Per lane the factor rows live in registers for
+// the whole tile; the gradient rows (D Bv) accumulate in registers over all columns; the
+// column sums (D^T Bu) are reduced across lanes with a shuffle reduce-scatter and across
+// warps through shared memory, in a fixed order (bitwise deterministic).
+#pragma once
+#include "common.cuh"
+
+namespace rpca {
+
+struct FgArgs {
+  int m, n;
+  int mpad;  // leading dimension of PU (multiple of 4, >= m)
+  const float* U;   // m x K (ld m): forming factor, trial point U + alpha dU
+  const float* V;   // n x K (ld n)
+  const float* dU;  // may be null
+  const float* dV;  // may be null
+  float alpha;
+  const double* alpha_dev;  // when non-null, the step is read from here (CUDA-graph replay)
+  const int* gate;          // when non-null and *gate == 0 the launch does nothing
+  const float* BU;  // apply mode: m x B (ld m)
+  const float* BV;  // apply mode: n x B (ld n)
+  float lam_S;
+  int nrb, ncs, BN;  // row blocks, column splits, columns per split (multiple of 8)
+  float* PU;         // [ncs][B][mpad]  -(D Bv) partial sums over a CTA's columns
+  float* PV;         // [nrb][B][n]      D^T Bu partial sums over a CTA's rows
+  double* Ppsi;      // [nrb*ncs]        sum of psi over a CTA's tile
+  int* err;          // device status word (error bits)
+};
+
+constexpr int FG_BJ = 8;      // columns per pipeline stage
+constexpr int FG_NSTAGE = 3;  // pipeline depth
+
+struct FgSmem {
+  size_t x_off, m_off, v_off, red_off, bar_off, scr_off, total;
+};
+
+// Observation bitmap of one stage: one TMA box per CTA, {WC * R words, BJ columns}, so the
+// box's x coordinate row0 / 32 is a multiple of WC * R >= 4 words (16 bytes).
+__host__ __device__ inline size_t fg_mask_stage_bytes(int WC, int R) {
+  return ((size_t)FG_BJ * WC * R * 4 + 127) & ~(size_t)127;
+}
+
+// Shared-memory carve-up (byte offsets from a 1024-byte aligned base).
+__host__ __device__ inline FgSmem fg_smem_layout(int WC, int R, bool masked, int BN, int KV, int JB) {
+  FgSmem L;
+  size_t o = 0;
+  L.x_off = o;
+  o += (size_t)FG_NSTAGE * WC * FG_BJ * 32 * R * 4;
+  L.m_off = o;
+  if (masked) o += (size_t)FG_NSTAGE * fg_mask_stage_bytes(WC, R);
+  o = (o + 15) & ~(size_t)15;
+  L.v_off = o;
+  o += (size_t)BN * KV * 8;
+  L.red_off = o;
+  o += (size_t)2 * WC * JB * 4;
+  o = (o + 7) & ~(size_t)7;
+  L.bar_off = o;
+  o += 2 * FG_NSTAGE * 8;
+  L.scr_off = o;
+  o += 32 * 8;
+  L.total = o + 1024;  // slack for aligning the base
+  return L;
+}
+
+template <int K, int B, bool SAME, int R, int J>
+struct FgTraits {
+  static constexpr int NP = R / 2;       // float2 pairs of rows per lane
+  static constexpr int ROWS_W = 32 * R;  // rows per warp
+  static constexpr int KV = SAME ? K : K + B;
+  static constexpr int JB = J * B;
+  static_assert(R == 2 || R == 4 || R == 8, "rows per lane");
+  static_assert(FG_BJ % J == 0, "group size");
+  static_assert(!SAME || K == B, "fg mode multiplies D by the forming factors");
+};
+
+// Row of pair p, element e (0/1) for this lane, relative to the warp's first row.
+template <int R>
+RPCA_DEV int lane_row(int p, int e, int lane) {
+  if constexpr (R == 2) return 2 * lane + e;
+  else return (p >> 1) * 128 + 4 * lane + (p & 1) * 2 + e;
+}
+// Offset of the lane's x values for pair-group `grp` inside one column of the warp's box.
+template <int R>
+RPCA_DEV int lane_xoff(int grp, int lane) {
+  if constexpr (R == 2) return 2 * lane;
+  else return grp * 128 + 4 * lane;
+}
+// Bitmap word (within the warp's R words of one column) and bit for pair p, element e.
+template <int R>
+RPCA_DEV void lane_bit(int p, int e, int lane, int& word, int& bit) {
+  if constexpr (R == 2) {
+    word = lane >> 4;
+    bit = 2 * (lane & 15) + e;
+  } else {
+    word = (p >> 1) * 4 + (lane >> 3);
+    bit = 4 * (lane & 7) + (p & 1) * 2 + e;
+  }
+}
+
+template <int K, int B, bool SAME, bool MASKED, int R, int J>
+__global__ void __launch_bounds__(288) fg_kernel(const __grid_constant__ CUtensorMap tmX,
+                                                 const __grid_constant__ CUtensorMap tmM, FgArgs a) {
+  using T = FgTraits<K, B, SAME, R, J>;
+  constexpr int NP = T::NP, ROWS_W = T::ROWS_W, KV = T::KV, JB = T::JB;
+  if (a.gate != nullptr && *a.gate == 0) return;  // uniform over the grid
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                                       ~static_cast<uintptr_t>(1023));
+  const int WC = (int)(blockDim.x >> 5) - 1;  // consumer warps; the last warp produces
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rb = blockIdx.x % a.nrb, cs = blockIdx.x / a.nrb;
+  const int row0 = rb * WC * ROWS_W;
+  const int col0 = cs * a.BN;
+  const int ncols = min(a.BN, a.n - col0);
+  const int nchunks = (ncols + FG_BJ - 1) / FG_BJ;
+  const FgSmem L = fg_smem_layout(WC, R, MASKED, a.BN, KV, JB);
+  float* xs_all = reinterpret_cast<float*>(sm + L.x_off);
+  uint32_t* ms_all = reinterpret_cast<uint32_t*>(sm + L.m_off);
+  float2* vsl = reinterpret_cast<float2*>(sm + L.v_off);
+  float* red = reinterpret_cast<float*>(sm + L.red_off);
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + L.bar_off);
+  uint64_t* empty = full + FG_NSTAGE;
+  double* scr = reinterpret_cast<double*>(sm + L.scr_off);
+  const size_t xbox = (size_t)FG_BJ * ROWS_W;                // floats per warp box of X
+  const size_t mstage = fg_mask_stage_bytes(WC, R) / 4;      // words per bitmap stage
+  const int mrow = WC * R;                                   // bitmap words per column of a stage
+  const uint32_t stage_bytes = (uint32_t)(WC * xbox * 4 + (MASKED ? (size_t)FG_BJ * mrow * 4 : 0));
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < FG_NSTAGE; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], WC);
+    }
+    fence_barrier_init();
+  }
+  __syncthreads();
+
+  if (warp == WC) {  // ---------------- producer ----------------
+    if (lane == 0) {
+      prefetch_tmap(&tmX);
+      if (MASKED) prefetch_tmap(&tmM);
+      int issued = 0;
+      bool ok = true;
+      for (int c = 0; c < nchunks; ++c) {
+        const int s = c % FG_NSTAGE;
+        const uint32_t ph = (uint32_t)(c / FG_NSTAGE) & 1u;
+        if (c >= FG_NSTAGE && !mbar_wait_bounded(&empty[s], ph ^ 1u)) {
+          atomicOr(a.err, DEV_ERR_TIMEOUT_EMPTY);
+          ok = false;
+          break;
+        }
+        mbar_arrive_expect_tx(&full[s], stage_bytes);
+        for (int w = 0; w < WC; ++w)
+          tma_load_2d(xs_all + ((size_t)s * WC + w) * xbox, &tmX, row0 + w * ROWS_W, col0 + c * FG_BJ, &full[s]);
+        if constexpr (MASKED) tma_load_2d(ms_all + (size_t)s * mstage, &tmM, row0 / 32, col0 + c * FG_BJ, &full[s]);
+        issued = c + 1;
+      }
+      // Wait (bounded) until every copy this thread issued has landed before leaving.
+      for (int c = max(0, issued - FG_NSTAGE); c < issued; ++c) {
+        if (!mbar_wait_bounded(&full[c % FG_NSTAGE], (uint32_t)(c / FG_NSTAGE) & 1u)) {
+          atomicOr(a.err, DEV_ERR_TIMEOUT_DRAIN);
+          break;
+        }
+      }
+      (void)ok;
+    }
+    return;
+  }
+
+  // ---------------- consumers ----------------
+  const int nct = WC * 32;
+  const int tid = threadIdx.x;
+  const int wrow0 = row0 + warp * ROWS_W;
+  const float alpha = a.alpha_dev ? (float)*a.alpha_dev : a.alpha;
+
+  // Factor slice for this CTA's columns, as duplicated pairs (v, v) for the fp32x2 FMA.
+  for (int idx = tid; idx < a.BN * KV; idx += nct) {
+    const int jj = idx / KV, q = idx - jj * KV;
+    const int j = col0 + jj;
+    float v = 0.f;
+    if (jj < ncols) {
+      if (q < K) {
+        const size_t o = (size_t)q * a.n + j;
+        v = a.V[o];
+        if (a.dV) v = fmaf(alpha, a.dV[o], v);
+      } else {
+        v = a.BV[(size_t)(q - K) * a.n + j];
+      }
+    }
+    vsl[idx] = f2(v, v);
+  }
+
+  // This lane's rows of the forming factor (negated, so that r' = x - u.v = -r) and,
+  // in apply mode, of Bu (negated too, which makes D^T Bu come out with its own sign).
+  float2 un[NP][K > 0 ? K : 1];
+  float2 bun[NP][SAME ? 1 : B];
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+    const int i0 = wrow0 + lane_row<R>(p, 0, lane), i1 = i0 + 1;
+#pragma unroll
+    for (int l = 0; l < K; ++l) {
+      float u0 = 0.f, u1 = 0.f;
+      const size_t o = (size_t)l * a.m;
+      if (i0 < a.m) {
+        u0 = a.U[o + i0];
+        if (a.dU) u0 = fmaf(alpha, a.dU[o + i0], u0);
+      }
+      if (i1 < a.m) {
+        u1 = a.U[o + i1];
+        if (a.dU) u1 = fmaf(alpha, a.dU[o + i1], u1);
+      }
+      un[p][l] = f2(-u0, -u1);
+    }
+    if constexpr (!SAME) {
+#pragma unroll
+      for (int b = 0; b < B; ++b) {
+        const size_t o = (size_t)b * a.m;
+        const float b0 = i0 < a.m ? a.BU[o + i0] : 0.f;
+        const float b1 = i1 < a.m ? a.BU[o + i1] : 0.f;
+        bun[p][b] = f2(-b0, -b1);
+      }
+    }
+  }
+  named_bar(1, nct);
+
+  float2 gu[NP][B];
+#pragma unroll
+  for (int p = 0; p < NP; ++p)
+#pragma unroll
+    for (int b = 0; b < B; ++b) gu[p][b] = f2(0.f, 0.f);
+  double psi_d = 0.0;
+  const float lam = a.lam_S;
+  const float2 mhalf = f2(-0.5f, -0.5f);
+  bool failed = false;
+  int gcount = 0;
+
+  for (int c = 0; c < nchunks; ++c) {
+    const int s = c % FG_NSTAGE;
+    if (!failed && !mbar_wait_bounded(&full[s], (uint32_t)(c / FG_NSTAGE) & 1u)) {
+      failed = true;
+      if (lane == 0) atomicOr(a.err, DEV_ERR_TIMEOUT_FULL);
+    }
+    const float* xs = xs_all + ((size_t)s * WC + warp) * xbox;
+    const uint32_t* ms = ms_all + (size_t)s * mstage + warp * R;  // this warp's words of column 0
+    float2 psi2 = f2(0.f, 0.f);
+#pragma unroll 1
+    for (int g = 0; g < FG_BJ / J; ++g) {
+      float2 gv[J][B];
+#pragma unroll
+      for (int jj = 0; jj < J; ++jj)
+#pragma unroll
+        for (int b = 0; b < B; ++b) gv[jj][b] = f2(0.f, 0.f);
+#pragma unroll
+      for (int jj = 0; jj < J; ++jj) {
+        const int cc = g * J + jj;           // column within the stage
+        const int jl = c * FG_BJ + cc;       // column within the CTA slice
+        const float2* vrow = vsl + (size_t)jl * KV;
+        float2 vv[K > 0 ? K : 1];
+#pragma unroll
+        for (int l = 0; l < K; ++l) vv[l] = vrow[l];
+        float2 bvv[SAME ? 1 : B];
+        if constexpr (!SAME) {
+#pragma unroll
+          for (int b = 0; b < B; ++b) bvv[b] = vrow[K + b];
+        }
+        float xv[R];
+        if constexpr (R == 2) {
+          const float2 t = *reinterpret_cast<const float2*>(xs + (size_t)cc * ROWS_W + lane_xoff<R>(0, lane));
+          xv[0] = t.x;
+          xv[1] = t.y;
+        } else {
+#pragma unroll
+          for (int grp = 0; grp < R / 4; ++grp) {
+            const float4 t = *reinterpret_cast<const float4*>(xs + (size_t)cc * ROWS_W + lane_xoff<R>(grp, lane));
+            xv[grp * 4 + 0] = t.x;
+            xv[grp * 4 + 1] = t.y;
+            xv[grp * 4 + 2] = t.z;
+            xv[grp * 4 + 3] = t.w;
+          }
+        }
+        uint32_t mw[R == 2 ? 1 : R / 4];
+        if constexpr (MASKED) {
+          if constexpr (R == 2) {
+            mw[0] = ms[(size_t)cc * mrow + (lane >> 4)];
+          } else {
+#pragma unroll
+            for (int grp = 0; grp < R / 4; ++grp) mw[grp] = ms[(size_t)cc * mrow + grp * 4 + (lane >> 3)];
+          }
+        }
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+          float2 r = f2(xv[2 * p], xv[2 * p + 1]);
+#pragma unroll
+          for (int l = 0; l < K; ++l) r = ffma2(un[p][l], vv[l], r);
+          if constexpr (MASKED) {
+            int w0, b0, w1, b1;
+            lane_bit<R>(p, 0, lane, w0, b0);
+            lane_bit<R>(p, 1, lane, w1, b1);
+            const uint32_t word = mw[R == 2 ? 0 : (p >> 1)];
+            r.x = ((word >> b0) & 1u) ? r.x : 0.f;
+            r.y = ((word >> b1) & 1u) ? r.y : 0.f;
+            (void)w0;
+            (void)w1;
+          }
+          const float2 d = f2(fminf(fmaxf(r.x, -lam), lam), fminf(fmaxf(r.y, -lam), lam));
+          psi2 = ffma2(d, ffma2(d, mhalf, r), psi2);
+          if constexpr (SAME) {
+#pragma unroll
+            for (int b = 0; b < B; ++b) gu[p][b] = ffma2(d, vv[b], gu[p][b]);
+#pragma unroll
+            for (int b = 0; b < B; ++b) gv[jj][b] = ffma2(d, un[p][b], gv[jj][b]);
+          } else {
+#pragma unroll
+            for (int b = 0; b < B; ++b) gu[p][b] = ffma2(d, bvv[b], gu[p][b]);
+#pragma unroll
+            for (int b = 0; b < B; ++b) gv[jj][b] = ffma2(d, bun[p][b], gv[jj][b]);
+          }
+        }
+      }
+      // Column sums of this group: lanes, then warps (fixed order).
+      float vals[JB];
+#pragma unroll
+      for (int jj = 0; jj < J; ++jj)
+#pragma unroll
+        for (int b = 0; b < B; ++b) vals[jj * B + b] = gv[jj][b].x + gv[jj][b].y;
+      int base = 0;
+      ReduceScatter<JB, 16>::run(vals, lane, base);
+      constexpr int CF = rs_count(JB), DUP = rs_dup_mask(JB);
+      float* rbuf = red + (size_t)(gcount & 1) * WC * JB;
+      if ((lane & DUP) == 0) {
+#pragma unroll
+        for (int t = 0; t < CF; ++t) rbuf[warp * JB + base + t] = vals[t];
+      }
+      named_bar(1, nct);
+      if (tid < JB) {
+        float sum = 0.f;
+        for (int w = 0; w < WC; ++w) sum += rbuf[w * JB + tid];
+        const int jj = tid / B, b = tid - (tid / B) * B;
+        const int j = col0 + c * FG_BJ + g * J + jj;
+        if (j < col0 + ncols) a.PV[((size_t)rb * B + b) * a.n + j] = sum;
+      }
+      ++gcount;
+    }
+    psi_d += (double)psi2.x + (double)psi2.y;
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[s]);
+  }
+
+  // Row sums -(D Bv) over this CTA's columns.
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+    const int i0 = wrow0 + lane_row<R>(p, 0, lane);
+    if (i0 < a.mpad) {
+#pragma unroll
+      for (int b = 0; b < B; ++b)
+        *reinterpret_cast<float2*>(a.PU + ((size_t)cs * B + b) * a.mpad + i0) = gu[p][b];
+    }
+  }
+  // Sum of psi over the tile.
+  psi_d = warp_sum_d(psi_d);
+  if (lane == 0) scr[warp] = psi_d;
+  named_bar(1, nct);
+  if (tid == 0) {
+    double s = 0.0;
+    for (int w = 0; w < WC; ++w) s += scr[w];
+    a.Ppsi[blockIdx.x] = s;
+  }
+}
+
+}  // namespace rpca

@@ -1,0 +1,24 @@
+// Registry of compiled instantiations of the fused f/grad kernel.
+#pragma once
+#include <cuda.h>
+
+namespace rpca {
+
+struct FgArgs;
+typedef void (*FgKernelFn)(const CUtensorMap, const CUtensorMap, FgArgs);
+
+struct FgVariant {
+  const void* fn;  // __global__ function pointer (nullptr: not compiled)
+  int R;           // rows per lane
+  int J;           // columns per reduction group
+};
+
+// Forming rank K (0..16), product width B, fg mode (B == K, operands = forming factors) or
+// apply mode, masked or not.  Returns nullptr when that combination is not compiled.
+const FgVariant* fg_variant(int K, int B, bool same, bool masked);
+
+void fg_register_same_small(FgVariant (*tab)[2]);   // K = 1..8
+void fg_register_same_large(FgVariant (*tab)[2]);   // K = 9..16
+void fg_register_apply(FgVariant (*tab)[2]);        // (K, B) = (0, 16), (8, 8), (16, 8)
+
+}  // namespace rpca

@@ -1,0 +1,43 @@
+// Declarations shared by the kernel translation units and the host API.
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rpca {
+
+// FIN_FG: gradient + penalty at the trial point; FIN_FG_RAW: same objective, but GU/GV get
+// the raw products D V and D^T U; FIN_APPLY: plain products D Bv, D^T Bu, no objective.
+enum { FIN_FG = 0, FIN_APPLY = 1, FIN_FG_RAW = 2 };
+
+struct FinArgs {
+  int m, n, B, mpad, nrb, ncs, nctas;
+  const float* PU;
+  const float* PV;
+  const double* Ppsi;
+  int mode;  // FIN_*
+  const float* U;
+  const float* V;
+  const float* dU;
+  const float* dV;
+  float alpha;
+  const double* alpha_dev;  // when non-null, the step is read from here
+  const int* gate;          // when non-null and *gate == 0 the launch does nothing
+  double lam_L;
+  float* GU;  // m x B (ld m): G_U (fg) or D Bv (apply)
+  float* GV;  // n x B (ld n): G_V (fg) or D^T Bu (apply)
+  float* Ut;  // optional copy of the trial point
+  float* Vt;
+  const float* DU;  // optional direction for g.d
+  const float* DV;
+  double* blk;              // [3 * gridDim.x] block partials
+  unsigned int* counter;    // zero between launches (reset by the last block)
+  double* out;              // [4]: f, g.d, ||g||^2, ||x_t||^2
+};
+
+__global__ void finalize_kernel(FinArgs a);
+__global__ void pack_mask_kernel(const uint8_t* mask, int64_t ldmask, int m, int n, int wpad, uint32_t* bits);
+__global__ void check_x_kernel(const float* X, int64_t ldx, const uint8_t* mask, int64_t ldmask, int m, int n,
+                               unsigned long long* bad, unsigned long long* observed);
+
+}  // namespace rpca

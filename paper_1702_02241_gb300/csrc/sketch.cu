@@ -1,0 +1,179 @@
+// Randomized-SVD initialisation (Sec. 4.2): U0 = U_k Sigma^1/2, V0 = V_k Sigma^1/2 from the
+// SVD of A*(X) (observed entries, rescaled by 1/p_hat when a mask is present), computed with
+// a rank-(k + p) sketch and q power iterations (Halko, Martinsson & Tropp; p = 10, q = 2 by
+// default).  Products with A*(X) and its transpose are passes of the fused kernel in apply
+// mode with no forming factors and no clipping (then D = -A*(X)); orthonormalisation is
+// CholeskyQR2 with float64 Grams; the small SVD is a float64 one-sided Jacobi on the Gram of
+// B^T = A*(X)^T Q.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "common.cuh"
+#include "ctx.h"
+#include "smallla.cuh"
+#include "tsla_ctx.h"
+
+namespace rpca {
+
+constexpr int SK_LMAX = 32;
+
+struct SketchState {
+  double G[SK_LMAX * SK_LMAX];
+  double R[SK_LMAX * SK_LMAX], Rinv[SK_LMAX * SK_LMAX];
+  double C1[SK_LMAX * SK_LMAX], C2[SK_LMAX * SK_LMAX];
+  int bad;
+};
+
+void fill_normal(float* out, int64_t count, uint64_t seed, float scale, cudaStream_t s);
+
+__global__ void sk_chol_kernel(SketchState* st, int l) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  st->bad = chol_upper_inv(st->G, l, st->R, st->Rinv);
+}
+
+// Eigen-decomposition of the l x l Gram of B^T (one CTA); C1 = U_B[:, :k] Sigma^{1/2} and
+// C2 = U_B[:, :k] Sigma^{-1/2} (scaled by `scale`), both l x k (ld l).
+__global__ void __launch_bounds__(256) sk_small_svd_kernel(SketchState* st, int l, int k) {
+  __shared__ double A[SK_LMAX * SK_LMAX], W[SK_LMAX * SK_LMAX], ev[SK_LMAX];
+  __shared__ int ord[SK_LMAX];
+  __shared__ int flag;
+  for (int i = threadIdx.x; i < l * l; i += blockDim.x) A[i] = st->G[i];
+  __syncthreads();
+  cta_jacobi_svd<double>(A, l, l, l, W, l, ev, &flag, 60, 1e-15);
+  cta_sort_desc<double>(ev, l, ord);
+  for (int i = threadIdx.x; i < l * k; i += blockDim.x) {
+    const int a = i % l, c = i / l;
+    const double lam = ev[ord[c]];                 // sigma_c^2
+    const double sg = lam > 0.0 ? sqrt(lam) : 0.0;  // sigma_c
+    const double u = W[a + ord[c] * l];
+    st->C1[a + c * l] = u * sqrt(sg);
+    st->C2[a + c * l] = sg > 0.0 ? u / sqrt(sg) : 0.0;
+  }
+}
+
+struct SketchBuffers {
+  float* buf = nullptr;
+  float *Om, *Y, *Z, *BVc, *BUc, *Y1c, *Y2c;
+  SketchState* st = nullptr;
+  TsScratch ts;
+};
+
+static void free_sketch_buffers(SketchBuffers& b) {
+  cudaFree(b.buf);
+  cudaFree(b.st);
+  cudaFree(b.ts.part);
+  cudaFree(b.ts.counter);
+}
+
+#define SK_CUDA(call)                                     \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) return cuda_err(c, e_, #call); \
+  } while (0)
+
+// Y1 (m x l) = -A*(X) BV (BV n x l),  or  Y2 (n x l) = -A*(X)^T BU (BU m x l); chunks of 16.
+static rpca_status sk_apply(rpca_ctx* c, SketchBuffers& b, int l, const float* BV, const float* BU, float* Y1,
+                            float* Y2) {
+  const FgPlan* P = apply_plan(c, 0);
+  if (!P) return RPCA_EUNSUPPORTED;
+  const int64_t m = c->m, n = c->n;
+  for (int c0 = 0; c0 < l; c0 += 16) {
+    const int w = std::min(16, l - c0);
+    SK_CUDA(cudaMemsetAsync(b.BVc, 0, sizeof(float) * n * 16, c->stream));
+    SK_CUDA(cudaMemsetAsync(b.BUc, 0, sizeof(float) * m * 16, c->stream));
+    if (BV) SK_CUDA(cudaMemcpyAsync(b.BVc, BV + n * c0, sizeof(float) * n * w, cudaMemcpyDeviceToDevice, c->stream));
+    if (BU) SK_CUDA(cudaMemcpyAsync(b.BUc, BU + m * c0, sizeof(float) * m * w, cudaMemcpyDeviceToDevice, c->stream));
+    FgLaunch L;
+    L.U = b.BUc;  // unused with no forming factors
+    L.V = b.BVc;
+    L.BU = b.BUc;
+    L.BV = b.BVc;
+    L.fin_mode = FIN_APPLY;
+    L.GU = b.Y1c;
+    L.GV = b.Y2c;
+    L.lam = INFINITY;
+    rpca_status s = launch_fg(c, *P, L, c->stream);
+    if (s != RPCA_OK) return s;
+    if (Y1) SK_CUDA(cudaMemcpyAsync(Y1 + m * c0, b.Y1c, sizeof(float) * m * w, cudaMemcpyDeviceToDevice, c->stream));
+    if (Y2) SK_CUDA(cudaMemcpyAsync(Y2 + n * c0, b.Y2c, sizeof(float) * n * w, cudaMemcpyDeviceToDevice, c->stream));
+  }
+  return RPCA_OK;
+}
+
+static rpca_status sk_orth(rpca_ctx* c, SketchBuffers& b, float* Y, int64_t rows, int l) {
+  for (int pass = 0; pass < 2; ++pass) {
+    SK_CUDA(ts_gram_c(c, Y, rows, l, Y, rows, l, rows, b.st->G, b.ts, c->stream));
+    sk_chol_kernel<<<1, 1, 0, c->stream>>>(b.st, l);
+    count_launches(c, 1);
+    SK_CUDA(ts_mul_c(c, Y, rows, l, b.st->Rinv, l, l, Y, rows, rows, 1.f, 0.f, c->stream));
+  }
+  return RPCA_OK;
+}
+
+rpca_status sketch_init(rpca_ctx* c, const float* Omega, float* U, float* V) {
+  const int k = c->k;
+  const int l = std::min(std::min(k + std::max(0, c->opt.sketch_oversample), SK_LMAX), std::min(c->m, c->n));
+  const int q = std::max(0, c->opt.sketch_power);
+  const int64_t m = c->m, n = c->n;
+  SketchBuffers b;
+  auto done = [&](rpca_status s) {
+    cudaStreamSynchronize(c->stream);
+    free_sketch_buffers(b);
+    return s;
+  };
+  const int64_t nf = n * l + m * l + n * l + n * 16 + m * 16 + m * 16 + n * 16;
+  if (cudaMalloc(&b.buf, sizeof(float) * nf) != cudaSuccess) return done(set_err(c, RPCA_ENOMEM, "cudaMalloc"));
+  b.Om = b.buf;
+  b.Y = b.Om + n * l;
+  b.Z = b.Y + m * l;
+  b.BVc = b.Z + n * l;
+  b.BUc = b.BVc + n * 16;
+  b.Y1c = b.BUc + m * 16;
+  b.Y2c = b.Y1c + m * 16;
+  if (cudaMalloc(&b.st, sizeof(SketchState)) != cudaSuccess) return done(set_err(c, RPCA_ENOMEM, "cudaMalloc"));
+  b.ts.grid = 2 * c->nsm;
+  b.ts.part_n = (size_t)b.ts.grid * 2048;
+  if (cudaMalloc(&b.ts.part, sizeof(double) * b.ts.part_n) != cudaSuccess ||
+      cudaMalloc(&b.ts.counter, 64) != cudaSuccess)
+    return done(set_err(c, RPCA_ENOMEM, "cudaMalloc"));
+  cudaMemsetAsync(b.ts.counter, 0, 64, c->stream);
+  if (Omega) cudaMemcpyAsync(b.Om, Omega, sizeof(float) * n * l, cudaMemcpyDeviceToDevice, c->stream);
+  else {
+    fill_normal(b.Om, n * l, 0xC0FFEEULL ^ (c->opt.seed * 0x9E3779B97F4A7C15ULL), 1.f, c->stream);
+    count_launches(c, 1);
+  }
+  rpca_status s;
+  if ((s = sk_apply(c, b, l, b.Om, nullptr, b.Y, nullptr)) != RPCA_OK) return done(s);
+  if ((s = sk_orth(c, b, b.Y, m, l)) != RPCA_OK) return done(s);
+  for (int it = 0; it < q; ++it) {
+    if ((s = sk_apply(c, b, l, nullptr, b.Y, nullptr, b.Z)) != RPCA_OK) return done(s);
+    if ((s = sk_orth(c, b, b.Z, n, l)) != RPCA_OK) return done(s);
+    if ((s = sk_apply(c, b, l, b.Z, nullptr, b.Y, nullptr)) != RPCA_OK) return done(s);
+    if ((s = sk_orth(c, b, b.Y, m, l)) != RPCA_OK) return done(s);
+  }
+  // B^T = A*(X)^T Q = -(D^T Q) / p_hat.
+  if ((s = sk_apply(c, b, l, nullptr, b.Y, nullptr, b.Z)) != RPCA_OK) return done(s);
+  if (ts_gram_c(c, b.Z, n, l, b.Z, n, l, n, b.st->G, b.ts, c->stream) != cudaSuccess)
+    return done(set_err(c, RPCA_ECUDA, "ts_gram"));
+  sk_small_svd_kernel<<<1, 256, 0, c->stream>>>(b.st, l, k);
+  count_launches(c, 1);
+  const float inv_p = (float)(1.0 / std::max(c->p_hat, 1e-30));
+  // The Gram was formed from D^T Q = -p_hat B^T: its eigenvalues are p_hat^2 sigma^2, so
+  // sqrt(sigma) picks up sqrt(p_hat) -- rescale both factors accordingly.
+  const float su = std::sqrt(inv_p);
+  if (ts_mul_c(c, b.Y, m, l, b.st->C1, l, k, U, m, m, su, 0.f, c->stream) != cudaSuccess ||
+      ts_mul_c(c, b.Z, n, l, b.st->C2, l, k, V, n, n, -su, 0.f, c->stream) != cudaSuccess)
+    return done(set_err(c, RPCA_ECUDA, "ts_mul"));
+  return done(check_dev_err(c));
+}
+
+}  // namespace rpca
+
+using namespace rpca;
+
+extern "C" rpca_status rpca_init_sketch(rpca_ctx* c, const float* Omega, float* U, float* V) {
+  if (!c) return RPCA_EINVAL;
+  if (!U || !V) return set_err(c, RPCA_EINVAL, "U and V are required");
+  return sketch_init(c, Omega, U, V);
+}

@@ -1,0 +1,133 @@
+// rpca_solve: drives the device L-BFGS graph, checks the certificate every cert_every
+// iterations, returns the solution and its certificate.  Random initialisation kernel.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+#include "common.cuh"
+#include "ctx.h"
+#include "solver.h"
+
+namespace rpca {
+
+rpca_status solver_prepare(rpca_ctx* c, const float* U, const float* V);
+rpca_status solver_iterations(rpca_ctx* c, int count);
+rpca_status solver_read_state(rpca_ctx* c, SolverState* out);
+const float* solver_point(rpca_ctx* c);
+rpca_status cert_compute(rpca_ctx* c, const float* U, const float* V, rpca_cert* out, bool full);
+rpca_status sketch_init(rpca_ctx* c, const float* Omega, float* U, float* V);
+
+// Counter-based normal variates: splitmix64 of (seed, index) -> two uniforms -> Box-Muller.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t z) {
+  z += 0x9e3779b97f4a7c15ull;
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return z ^ (z >> 31);
+}
+__device__ __forceinline__ float normal_at(uint64_t seed, uint64_t i) {
+  const uint64_t r = splitmix64(seed * 0x632be59bd9b4e019ull + i);
+  const double u1 = ((double)(r >> 11) + 1.0) * (1.0 / 9007199254740993.0);  // (0, 1]
+  const double u2 = (double)(splitmix64(r) >> 11) * (1.0 / 9007199254740992.0);
+  return (float)(sqrt(-2.0 * log(u1)) * cospi(2.0 * u2));
+}
+
+__global__ void fill_normal_kernel(float* out, int64_t count, uint64_t seed, float scale) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = scale * normal_at(seed, (uint64_t)i);
+}
+
+void fill_normal(float* out, int64_t count, uint64_t seed, float scale, cudaStream_t s) {
+  const int grid = (int)std::min<int64_t>(1024, (count + 255) / 256);
+  fill_normal_kernel<<<std::max(grid, 1), 256, 0, s>>>(out, count, seed, scale);
+}
+
+}  // namespace rpca
+
+using namespace rpca;
+
+extern "C" rpca_status rpca_solve(rpca_ctx* c, float* U, float* V, rpca_result* res) {
+  if (!c) return RPCA_EINVAL;
+  if (!U || !V) return set_err(c, RPCA_EINVAL, "U and V are required");
+  const auto t0 = std::chrono::steady_clock::now();
+  rpca_result r;
+  memset(&r, 0, sizeof r);
+  rpca_status s = RPCA_OK;
+  const int64_t mk = (int64_t)c->m * c->k, nk = (int64_t)c->n * c->k;
+  switch (c->opt.init) {
+    case RPCA_INIT_USER:
+      break;
+    case RPCA_INIT_RANDOM:
+      fill_normal(U, mk, c->opt.seed * 2 + 1, 1e-1f, c->stream);
+      fill_normal(V, nk, c->opt.seed * 2 + 2, 1e-1f, c->stream);
+      count_launches(c, 2);
+      break;
+    case RPCA_INIT_SKETCH:
+      if ((s = sketch_init(c, nullptr, U, V)) != RPCA_OK) return s;
+      break;
+    default:
+      return set_err(c, RPCA_EUNSUPPORTED, "this initialisation is not built");
+  }
+  const int64_t graph_launches0 = c->graph_launches;
+  if ((s = solver_prepare(c, U, V)) != RPCA_OK) return s;
+  SolverState st;
+  const int every = c->opt.cert_every > 0 ? c->opt.cert_every : 0;
+  bool certified = false;
+  int last_cert_iter = -1;
+  rpca_cert cert;
+  memset(&cert, 0, sizeof cert);
+  int cert_evals = 0;
+  while (true) {
+    if ((s = solver_read_state(c, &st)) != RPCA_OK) return s;
+    if (!st.active) break;
+    if (st.iter >= c->opt.max_iter) break;
+    if (every > 0 && st.iter > 0 && st.iter % every == 0 && st.iter != last_cert_iter) {
+      last_cert_iter = st.iter;
+      // Cheap terms first; the spectral term only when they already meet the tolerance.
+      if ((s = cert_compute(c, solver_point(c), solver_point(c) + mk, &cert, false)) != RPCA_OK) return s;
+      ++cert_evals;
+      if (cert.cert_rel <= c->opt.cert_tol) {
+        if ((s = cert_compute(c, solver_point(c), solver_point(c) + mk, &cert, true)) != RPCA_OK) return s;
+        if (cert.cert_rel <= c->opt.cert_tol) {
+          certified = true;
+          break;
+        }
+      }
+    }
+    if (c->opt.timeout_s > 0) {
+      const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      if (el > c->opt.timeout_s) break;
+    }
+    int batch = every > 0 ? every - (st.iter % every) : 25;
+    batch = std::max(1, std::min(batch, c->opt.max_iter - st.iter));
+    if ((s = solver_iterations(c, batch)) != RPCA_OK) return s;
+  }
+  if ((s = check_dev_err(c)) != RPCA_OK) return s;
+  cudaMemcpyAsync(U, solver_point(c), sizeof(float) * mk, cudaMemcpyDeviceToDevice, c->stream);
+  cudaMemcpyAsync(V, solver_point(c) + mk, sizeof(float) * nk, cudaMemcpyDeviceToDevice, c->stream);
+  if (!certified) {
+    if ((s = cert_compute(c, U, V, &cert, true)) != RPCA_OK) return s;
+  }
+  ++cert_evals;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_err(c, cudaGetLastError(), "rpca_solve");
+  // Fused kernel + finalize + line-search step per while-body pass: one per trial, and one
+  // (early-exit) pass in every graph launch that ran no trial.
+  const int64_t gl = c->graph_launches - graph_launches0;
+  count_launches(c, 3LL * std::max<int64_t>(gl, (int64_t)st.evals - 1));
+  r.F = st.f;
+  r.iters = st.iter;
+  r.evals = st.evals;
+  r.cert_evals = cert_evals;
+  r.cert = cert;
+  r.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  r.status = cert.cert_rel <= c->opt.cert_tol ? RPCA_OK : RPCA_ENOTCONV;
+  if (st.f < c->F_best) c->F_best = st.f;
+  if (res) *res = r;
+  if (r.status != RPCA_OK) {
+    char buf[200];
+    snprintf(buf, sizeof buf, "stopped after %d iterations (reason %d) with cert_rel %.3e > %.1e", st.iter, st.stop,
+             cert.cert_rel, c->opt.cert_tol);
+    set_err(c, RPCA_ENOTCONV, buf);
+  }
+  return r.status;
+}

@@ -1,0 +1,655 @@
+// L-BFGS with memory M (Sec. 5.1: memory 10) and a strong-Wolfe line search, run entirely
+// on the device.
+//
+// One iteration is one CUDA-graph launch:
+//   WHILE (line search running):  fg_kernel + finalize_kernel at x + a d,  ls_step_kernel
+//   lbfgs_accept_kernel:  accept the step (s = x_t - x, y = g_t - g into the history ring,
+//                         x <- x_t, g <- g_t).
+//   lbfgs_dots_kernel:    all inner products the two-loop recursion needs (one block row
+//                         per history slot); its last block runs the two-loop recursion on
+//                         those scalars (float64) and the stopping tests.
+//   lbfgs_direction_kernel:  d = c_g g + sum_j (c_s[j] s_j + c_y[j] y_j), and g.d.
+// The two-loop recursion (Nocedal & Wright Alg. 7.4) is evaluated on inner products only:
+// with q = g - sum a_j y_j and r = gamma q + sum c_j s_j, every dot it needs is a
+// combination of s_i.g, y_i.g, s_i.y_j and y_i.y_j, which are kept in a Gram table and
+// updated with one new row and column per accepted pair.  The line search is the
+// bracketing + zoom procedure of Nocedal & Wright Alg. 3.5 / 3.6 with safeguarded cubic
+// interpolation (the paper is silent on the line search; its solvers came from minFunc).
+//
+// Products are formed in float32 and summed over a few elements per thread in float32;
+// all further sums, the Gram table, the two-loop scalars and the line-search arithmetic
+// are float64.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+#include "common.cuh"
+#include "ctx.h"
+#include "solver.h"
+
+namespace rpca {
+
+constexpr double LS_C1 = 1e-4, LS_C2 = 0.9, LS_AMAX = 1e10, CURV_EPS = 1e-10;
+constexpr int LS_MAX_TRIALS = 25;
+
+struct SolverArgs {
+  SolverState* st;
+  int64_t N;
+  float* x;
+  float* g;
+  float* xt;
+  float* gt;
+  float* d;
+  float* S;  // [(MCAP + 1) * N]
+  float* Y;
+  double* blk;
+  unsigned int* counter;
+};
+
+// ---------------------------------------------------------------------------------------------
+__device__ double cubic_step(double a, double fa, double ga, double b, double fb, double gb, bool* ok) {
+  // Minimiser of the cubic through (a, fa, ga), (b, fb, gb) (Nocedal & Wright Eq. 3.59).
+  *ok = false;
+  if (a == b) return 0.5 * (a + b);
+  const double d1 = ga + gb - 3.0 * (fa - fb) / (a - b);
+  const double disc = d1 * d1 - ga * gb;
+  if (!isfinite(disc) || disc < 0.0) return 0.5 * (a + b);
+  const double d2 = (b > a ? 1.0 : -1.0) * sqrt(disc);
+  const double den = gb - ga + 2.0 * d2;
+  if (den == 0.0 || !isfinite(den)) return 0.5 * (a + b);
+  *ok = true;
+  return b - (b - a) * (gb + d2 - d1) / den;
+}
+
+__device__ double zoom_trial(const LineSearch& L) {
+  const double left = fmin(L.lo, L.hi), right = fmax(L.lo, L.hi), w = right - left;
+  if (!isfinite(L.fhi)) return 0.5 * (L.lo + L.hi);
+  bool ok;
+  double t = cubic_step(L.lo, L.flo, L.glo, L.hi, L.fhi, L.ghi, &ok);
+  if (!ok || !isfinite(t)) return 0.5 * (L.lo + L.hi);
+  return fmin(fmax(t, left + 0.1 * w), right - 0.1 * w);
+}
+
+// One step of the line-search state machine after the trial at L.a has been evaluated
+// (st->out[0] = phi(a), st->out[1] = phi'(a)).
+__global__ void ls_step_kernel(SolverState* st, cudaGraphConditionalHandle h) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  LineSearch& L = st->ls;
+  if (!st->active || L.state != LS_RUNNING) {
+    st->gate = 0;
+    cudaGraphSetConditional(h, 0);
+    return;
+  }
+  const double a = L.a, fa = st->out[0], ga = st->out[1];
+  L.evals += 1;
+  st->evals += 1;
+  bool accept = false;
+  const bool armijo_fail = !isfinite(fa) || fa > L.f0 + LS_C1 * a * L.g0;
+  if (L.phase == 0) {  // bracketing (Alg. 3.5)
+    if (armijo_fail || (!L.first && fa >= L.f_prev)) {
+      L.lo = L.a_prev; L.flo = L.f_prev; L.glo = L.g_prev;
+      L.hi = a; L.fhi = fa; L.ghi = ga;
+      L.phase = 1;
+    } else if (fabs(ga) <= -LS_C2 * L.g0) {
+      accept = true;
+    } else if (ga >= 0.0) {
+      L.lo = a; L.flo = fa; L.glo = ga;
+      L.hi = L.a_prev; L.fhi = L.f_prev; L.ghi = L.g_prev;
+      L.phase = 1;
+    } else {
+      L.a_prev = a; L.f_prev = fa; L.g_prev = ga;
+      L.a = fmin(4.0 * a, LS_AMAX);
+      L.first = 0;
+    }
+  } else {  // zoom (Alg. 3.6)
+    if (armijo_fail || fa >= L.flo) {
+      L.hi = a; L.fhi = fa; L.ghi = ga;
+    } else {
+      if (fabs(ga) <= -LS_C2 * L.g0) {
+        accept = true;
+      } else {
+        if (ga * (L.hi - L.lo) >= 0.0) {
+          L.hi = L.lo; L.fhi = L.flo; L.ghi = L.glo;
+        }
+        L.lo = a; L.flo = fa; L.glo = ga;
+      }
+    }
+  }
+  if (accept) {
+    L.state = LS_ACCEPTED;
+    L.f_acc = fa;
+  } else if (L.evals >= LS_MAX_TRIALS) {
+    L.state = LS_FAILED;
+  } else if (L.phase == 1) {
+    L.a = zoom_trial(L);
+  }
+  const int running = L.state == LS_RUNNING;
+  st->gate = running;
+  cudaGraphSetConditional(h, running ? 1u : 0u);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Two-loop recursion on the Gram table (thread 0 of the last block of lbfgs_update_kernel).
+__device__ void two_loop_coefs(SolverState* st) {
+  const int n = st->count;
+  for (int j = 0; j < SOLVER_MAX_SLOTS; ++j) {
+    st->coef_s[j] = 0.0;
+    st->coef_y[j] = 0.0;
+  }
+  if (n == 0) {
+    st->coef_g = -1.0;
+    return;
+  }
+  double a[SOLVER_MAX_SLOTS], c[SOLVER_MAX_SLOTS];
+  const int* id = st->ids;  // newest first
+  for (int i = 0; i < n; ++i) {  // newest -> oldest
+    double t = st->sg[id[i]];
+    for (int j = 0; j < i; ++j) t -= a[j] * st->SY[id[i]][id[j]];
+    a[i] = t / st->SY[id[i]][id[i]];
+  }
+  const double gamma = st->SY[id[0]][id[0]] / st->YY[id[0]][id[0]];
+  for (int i = n - 1; i >= 0; --i) {  // oldest -> newest
+    double t = st->yg[id[i]];
+    for (int j = 0; j < n; ++j) t -= a[j] * st->YY[id[i]][id[j]];
+    t *= gamma;
+    for (int j = i + 1; j < n; ++j) t += c[j] * st->SY[id[j]][id[i]];
+    const double b = t / st->SY[id[i]][id[i]];
+    c[i] = a[i] - b;
+  }
+  st->coef_g = -gamma;
+  for (int i = 0; i < n; ++i) {
+    st->coef_y[id[i]] = gamma * a[i];
+    st->coef_s[id[i]] = -c[i];
+  }
+}
+
+// Scalar part of an iteration: ring update, stopping tests, next direction's coefficients
+// and the line-search start.  `v` holds the reduced inner products (layout: see below).
+template <int NS>
+__device__ void iteration_scalars(SolverState* st, const double* v) {
+  const int state = st->ls.state;
+  int added = -1;  // slot of the pair added by this step, if any
+  if (state == LS_ACCEPTED) {
+    st->f = st->ls.f_acc;
+    st->iter += 1;
+    st->fails = 0;
+    const double sy = v[5 * NS + 2], yy = v[5 * NS + 3], ss = v[5 * NS + 4];
+    const int sp = st->spare;
+    if (sy > CURV_EPS * sqrt(ss * yy) && yy > 0.0) {
+      for (int q = 0; q < st->count; ++q) {
+        const int j = st->ids[q];
+        st->SY[sp][j] = v[5 * j + 3];  // s_new . y_j
+        st->SY[j][sp] = v[5 * j + 2];  // s_j . y_new
+        st->YY[sp][j] = v[5 * j + 4];
+        st->YY[j][sp] = v[5 * j + 4];
+      }
+      st->SY[sp][sp] = sy;
+      st->YY[sp][sp] = yy;
+      int dropped = -1;
+      if (st->count == st->mem) dropped = st->ids[st->count - 1];
+      const int keep = st->count == st->mem ? st->count - 1 : st->count;
+      for (int q = keep; q > 0; --q) st->ids[q] = st->ids[q - 1];
+      st->ids[0] = sp;
+      st->count = keep + 1;
+      added = sp;
+      if (dropped >= 0) {
+        st->spare = dropped;
+      } else {
+        for (int cand = 0; cand < NS; ++cand) {
+          bool used = false;
+          for (int q = 0; q < st->count; ++q) used |= st->ids[q] == cand;
+          if (!used) {
+            st->spare = cand;
+            break;
+          }
+        }
+      }
+    }
+  } else if (state == LS_FAILED) {
+    st->count = 0;  // reset the memory; the next direction is steepest descent
+    st->fails += 1;
+    if (st->fails >= 2) {
+      st->stop = STOP_LSFAIL;
+      st->active = 0;
+    }
+  }
+  for (int q = 0; q < st->count; ++q) {
+    const int j = st->ids[q];
+    st->sg[j] = j == added ? v[5 * NS + 0] : v[5 * j + 0];
+    st->yg[j] = j == added ? v[5 * NS + 1] : v[5 * j + 1];
+  }
+  st->gg = v[5 * NS + 5];
+  st->g1 = v[5 * NS + 6];
+  if (!isfinite(st->f) || !isfinite(st->gg)) {
+    st->stop = STOP_NONFINITE;
+    st->active = 0;
+  } else if (st->gtol > 0.0 && sqrt(st->gg) <= st->gtol * fmax(1.0, fabs(st->f))) {
+    st->stop = STOP_GTOL;
+    st->active = 0;
+  } else if (st->iter >= st->max_iter) {
+    st->stop = STOP_MAXITER;
+    st->active = 0;
+  }
+  if (st->f < st->best_f) st->best_f = st->f;
+  two_loop_coefs(st);
+  // Descent check on the Gram table; fall back to steepest descent otherwise.
+  double gd = st->coef_g * st->gg;
+  for (int q = 0; q < st->count; ++q) {
+    const int j = st->ids[q];
+    gd += st->coef_s[j] * st->sg[j] + st->coef_y[j] * st->yg[j];
+  }
+  if (!(gd < 0.0)) {
+    st->count = 0;
+    two_loop_coefs(st);
+  }
+  LineSearch& L = st->ls;
+  L.a = st->count == 0 ? fmin(1.0, 1.0 / st->g1) : 1.0;
+  L.f0 = st->f;
+  L.a_prev = 0.0;
+  L.f_prev = st->f;
+  L.phase = 0;
+  L.first = 1;
+  L.evals = 0;
+  L.state = LS_RUNNING;
+}
+
+// Accepting a step: s = x_t - x and y = g_t - g go to the spare history slot, x <- x_t,
+// g <- g_t.  Nothing happens unless the line search accepted.
+__global__ void __launch_bounds__(256) lbfgs_accept_kernel(SolverArgs a) {
+  SolverState* st = a.st;
+  if (!st->active || st->ls.state != LS_ACCEPTED) return;
+  const int64_t N = a.N, sp = st->spare;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x) {
+    const float xo = a.x[e], xn = a.xt[e], go = a.g[e], gn = a.gt[e];
+    a.S[sp * N + e] = xn - xo;
+    a.Y[sp * N + e] = gn - go;
+    a.x[e] = xn;
+    a.g[e] = gn;
+  }
+}
+
+// Inner products.  Block row blockIdx.y = j < NS handles history slot j:
+//   v[5 j + 0..4] = s_j.g, y_j.g, s_j.y_new, s_new.y_j, y_new.y_j
+// and row NS the new pair and the gradient:
+//   v[5 NS + 0..6] = s_new.g, y_new.g, s_new.y_new, y_new.y_new, s_new.s_new, g.g, |g|_1
+// Products in float32, summed in float32 over each thread's elements, float64 beyond.
+// The last block to finish runs the scalar part of the iteration.
+template <int MCAP>
+__global__ void __launch_bounds__(256) lbfgs_dots_kernel(SolverArgs a) {
+  constexpr int NS = MCAP + 1;
+  constexpr int NV = 5 * NS + 7;
+  __shared__ double red[8][7];
+  __shared__ double fin[NV];
+  __shared__ bool is_last;
+  SolverState* st = a.st;
+  if (!st->active) return;
+  const int j = blockIdx.y;
+  const bool accepted = st->ls.state == LS_ACCEPTED;
+  bool live = false;
+  for (int q = 0; q < st->count; ++q) live |= st->ids[q] == j;
+  const int64_t N = a.N, sp = st->spare;
+  float acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  if (j < NS ? live : true) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x) {
+      const float gc = a.g[e];
+      const float s = accepted ? a.S[sp * N + e] : 0.f;
+      const float y = accepted ? a.Y[sp * N + e] : 0.f;
+      if (j < NS) {
+        const float sj = a.S[(int64_t)j * N + e], yj = a.Y[(int64_t)j * N + e];
+        acc[0] = fmaf(sj, gc, acc[0]);
+        acc[1] = fmaf(yj, gc, acc[1]);
+        acc[2] = fmaf(sj, y, acc[2]);
+        acc[3] = fmaf(s, yj, acc[3]);
+        acc[4] = fmaf(y, yj, acc[4]);
+      } else {
+        acc[0] = fmaf(s, gc, acc[0]);
+        acc[1] = fmaf(y, gc, acc[1]);
+        acc[2] = fmaf(s, y, acc[2]);
+        acc[3] = fmaf(y, y, acc[3]);
+        acc[4] = fmaf(s, s, acc[4]);
+        acc[5] = fmaf(gc, gc, acc[5]);
+        acc[6] += fabsf(gc);
+      }
+    }
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int nv = j < NS ? 5 : 7;
+#pragma unroll
+  for (int v = 0; v < 7; ++v) {
+    const double t = warp_sum_d((double)acc[v]);
+    if (lane == 0) red[w][v] = t;
+  }
+  __syncthreads();
+  const int64_t bid = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
+  if (threadIdx.x < nv) {
+    double t = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q][threadIdx.x];
+    a.blk[bid * 7 + threadIdx.x] = t;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) is_last = atomicAdd(a.counter, 1u) == gridDim.x * gridDim.y - 1;
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  // Fixed-order reduction over the x-blocks: warp w owns values w, w + 8, ...
+  for (int v = w; v < NV; v += (int)(blockDim.x >> 5)) {
+    const int row = v < 5 * NS ? v / 5 : NS;
+    const int col = v < 5 * NS ? v - 5 * (v / 5) : v - 5 * NS;
+    double t = 0.0;
+    for (int b = lane; b < (int)gridDim.x; b += 32) t += __ldcg(&a.blk[((int64_t)row * gridDim.x + b) * 7 + col]);
+    t = warp_sum_d(t);
+    if (lane == 0) fin[v] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    *a.counter = 0u;
+    iteration_scalars<NS>(st, fin);
+    st->gate = st->active;
+  }
+}
+
+// d = c_g g + sum over ring slots (c_s[j] s_j + c_y[j] y_j); then g.d in float64 starts the
+// line search (phi'(0)).
+template <int MCAP>
+__global__ void __launch_bounds__(256) lbfgs_direction_kernel(SolverArgs a) {
+  constexpr int NS = MCAP + 1;
+  __shared__ double scr[32];
+  __shared__ bool is_last;
+  __shared__ float cs[NS], cy[NS];
+  __shared__ float cg;
+  SolverState* st = a.st;
+  if (!st->active) return;
+  uint64_t live = 0;
+  for (int q = 0; q < st->count; ++q) live |= 1ull << st->ids[q];
+  if (threadIdx.x < NS) {
+    cs[threadIdx.x] = (float)st->coef_s[threadIdx.x];
+    cy[threadIdx.x] = (float)st->coef_y[threadIdx.x];
+  }
+  if (threadIdx.x == 0) cg = (float)st->coef_g;
+  __syncthreads();
+  double gd = 0.0;
+  const int64_t N = a.N;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x) {
+    const float ge = a.g[e];
+    float dv = cg * ge;
+#pragma unroll
+    for (int j = 0; j < NS; ++j) {
+      if ((live >> j) & 1ull) {
+        dv = fmaf(cs[j], a.S[(int64_t)j * N + e], dv);
+        dv = fmaf(cy[j], a.Y[(int64_t)j * N + e], dv);
+      }
+    }
+    a.d[e] = dv;
+    gd += (double)(ge * dv);
+  }
+  gd = block_sum_d(gd, scr);
+  if (threadIdx.x == 0) {
+    a.blk[blockIdx.x] = gd;
+    __threadfence();
+    is_last = atomicAdd(a.counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  double t = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) t += __ldcg(&a.blk[b]);
+  t = block_sum_d(t, scr);
+  if (threadIdx.x == 0) {
+    *a.counter = 0u;
+    LineSearch& L = st->ls;
+    L.g0 = t;
+    L.g_prev = t;
+    if (!(t < 0.0) || !isfinite(t)) L.state = LS_FAILED;  // not a descent direction
+    st->gate = (st->active && L.state == LS_RUNNING) ? 1 : 0;
+  }
+}
+
+__global__ void solver_init_kernel(SolverState* st, int mem, int max_iter, double gtol) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  st->f = st->out[0];
+  st->best_f = st->out[0];
+  st->mem = mem;
+  st->count = 0;
+  st->spare = 0;
+  st->iter = 0;
+  st->evals = 1;
+  st->fails = 0;
+  st->stop = STOP_NONE;
+  st->active = 1;
+  st->gate = 1;
+  st->max_iter = max_iter;
+  st->gtol = gtol;
+  st->ls.state = LS_NONE;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Host side.
+
+struct SolverBuffers {
+  int mcap = 0;
+  int64_t N = 0;
+  float* x = nullptr;  // [U | V], the current point
+  float* g = nullptr;
+  float* xt = nullptr;
+  float* gt = nullptr;
+  float* d = nullptr;
+  float* S = nullptr;
+  float* Y = nullptr;
+  SolverState* st = nullptr;
+  SolverState* host = nullptr;  // pinned copy
+  double* blk = nullptr;
+  unsigned int* counter = nullptr;
+  int grid = 0;
+  cudaStream_t cap = nullptr, cap2 = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+static int mem_cap(int mem) { return mem <= 4 ? 4 : (mem <= 10 ? 10 : (mem <= 16 ? 16 : 32)); }
+
+template <int MCAP>
+static cudaError_t launch_update(const SolverArgs& a, int grid, cudaStream_t s) {
+  lbfgs_accept_kernel<<<grid, 256, 0, s>>>(a);
+  const int gx = std::max(1, grid / (MCAP + 2));
+  lbfgs_dots_kernel<MCAP><<<dim3(gx, MCAP + 2), 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+template <int MCAP>
+static cudaError_t launch_direction(const SolverArgs& a, int grid, cudaStream_t s) {
+  lbfgs_direction_kernel<MCAP><<<grid, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+static cudaError_t update_and_direction(int mcap, const SolverArgs& a, int grid, cudaStream_t s) {
+  cudaError_t e;
+  switch (mcap) {
+    case 4: if ((e = launch_update<4>(a, grid, s)) != cudaSuccess) return e; return launch_direction<4>(a, grid, s);
+    case 10: if ((e = launch_update<10>(a, grid, s)) != cudaSuccess) return e; return launch_direction<10>(a, grid, s);
+    case 16: if ((e = launch_update<16>(a, grid, s)) != cudaSuccess) return e; return launch_direction<16>(a, grid, s);
+    default: if ((e = launch_update<32>(a, grid, s)) != cudaSuccess) return e; return launch_direction<32>(a, grid, s);
+  }
+}
+
+void free_solver(rpca_ctx* c) {
+  SolverBuffers* b = c->sol;
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  if (b->cap2) cudaStreamDestroy(b->cap2);
+  cudaFree(b->x);
+  cudaFree(b->S);
+  cudaFree(b->st);
+  cudaFree(b->blk);
+  cudaFree(b->counter);
+  cudaFreeHost(b->host);
+  delete b;
+  c->sol = nullptr;
+}
+
+#define SOL_CUDA(call)                                    \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) return cuda_err(c, e_, #call); \
+  } while (0)
+
+static SolverArgs solver_args(rpca_ctx* c) {
+  SolverBuffers* b = c->sol;
+  SolverArgs a;
+  a.st = b->st;
+  a.N = b->N;
+  a.x = b->x;
+  a.g = b->g;
+  a.xt = b->xt;
+  a.gt = b->gt;
+  a.d = b->d;
+  a.S = b->S;
+  a.Y = b->Y;
+  a.blk = b->blk;
+  a.counter = b->counter;
+  return a;
+}
+
+static FgLaunch trial_launch(rpca_ctx* c) {
+  SolverBuffers* b = c->sol;
+  const int64_t mk = (int64_t)c->m * c->k;
+  FgLaunch L;
+  L.U = b->x;
+  L.V = b->x + mk;
+  L.dU = b->d;
+  L.dV = b->d + mk;
+  L.alpha_dev = &b->st->ls.a;
+  L.gate = &b->st->gate;
+  L.GU = b->gt;
+  L.GV = b->gt + mk;
+  L.Ut = b->xt;
+  L.Vt = b->xt + mk;
+  L.DU = b->d;
+  L.DV = b->d + mk;
+  L.out = b->st->out;
+  return L;
+}
+
+static rpca_status ensure_solver(rpca_ctx* c) {
+  const int mcap = mem_cap(c->opt.lbfgs_mem);
+  if (c->sol && c->sol->mcap == mcap) return RPCA_OK;
+  free_solver(c);
+  SolverBuffers* b = new SolverBuffers();
+  c->sol = b;
+  b->mcap = mcap;
+  b->N = (int64_t)(c->m + c->n) * c->k;
+  const int64_t N = b->N;
+  SOL_CUDA(cudaMalloc(&b->x, sizeof(float) * 5 * N));
+  b->g = b->x + N;
+  b->xt = b->g + N;
+  b->gt = b->xt + N;
+  b->d = b->gt + N;
+  SOL_CUDA(cudaMalloc(&b->S, sizeof(float) * 2 * (mcap + 1) * N));
+  b->Y = b->S + (int64_t)(mcap + 1) * N;
+  SOL_CUDA(cudaMalloc(&b->st, sizeof(SolverState)));
+  SOL_CUDA(cudaMemset(b->st, 0, sizeof(SolverState)));
+  SOL_CUDA(cudaMallocHost(&b->host, sizeof(SolverState)));
+  b->grid = (int)std::max<int64_t>(1, std::min<int64_t>(2LL * c->nsm, (N + 255) / 256));
+  SOL_CUDA(cudaMalloc(&b->blk, sizeof(double) * 7 * ((size_t)b->grid + 64) * (mcap + 2)));
+  SOL_CUDA(cudaMalloc(&b->counter, 64));
+  SOL_CUDA(cudaMemset(b->counter, 0, 64));
+  SOL_CUDA(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
+  SOL_CUDA(cudaStreamCreateWithFlags(&b->cap2, cudaStreamNonBlocking));
+
+  // Capture one iteration: WHILE(line search) { fg, finalize, ls_step }, update, direction.
+  SolverArgs a = solver_args(c);
+  SOL_CUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+  cudaStreamCaptureStatus cst;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(b->cap, &cst, nullptr, &g, &deps, nullptr, &ndeps);
+  cudaGraphConditionalHandle h;
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+  cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t wnode;
+  if (e == cudaSuccess) e = cudaGraphAddNode(&wnode, g, deps, nullptr, ndeps, &cp);
+  if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(b->cap, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies);
+  if (e == cudaSuccess) {
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(b->cap2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      rpca_status s = launch_fg(c, c->fg_plan, trial_launch(c), b->cap2);
+      if (s == RPCA_OK) {
+        ls_step_kernel<<<1, 32, 0, b->cap2>>>(b->st, h);
+        e = cudaGetLastError();
+      } else {
+        e = cudaErrorUnknown;
+      }
+      cudaGraph_t body_out = nullptr;
+      cudaError_t e2 = cudaStreamEndCapture(b->cap2, &body_out);
+      if (e == cudaSuccess) e = e2;
+    }
+  }
+  if (e == cudaSuccess) e = update_and_direction(mcap, a, b->grid, b->cap);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e3 = cudaStreamEndCapture(b->cap, &graph);
+  if (e == cudaSuccess) e = e3;
+  if (e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return cuda_err(c, e, "capturing the L-BFGS iteration graph");
+  }
+  b->graph = graph;
+  SOL_CUDA(cudaGraphInstantiate(&b->exec, graph, 0));
+  return RPCA_OK;
+}
+
+// Prepares the solver state at the point stored in sol->x: gradient, objective, first
+// direction.  Stream-ordered on c->stream.
+static rpca_status solver_start(rpca_ctx* c) {
+  SolverBuffers* b = c->sol;
+  const int64_t mk = (int64_t)c->m * c->k;
+  FgLaunch L;
+  L.U = b->x;
+  L.V = b->x + mk;
+  L.GU = b->g;
+  L.GV = b->g + mk;
+  L.out = b->st->out;
+  rpca_status s = launch_fg(c, c->fg_plan, L, c->stream);
+  if (s != RPCA_OK) return s;
+  solver_init_kernel<<<1, 1, 0, c->stream>>>(b->st, c->opt.lbfgs_mem, c->opt.max_iter, c->opt.gtol);
+  SOL_CUDA(cudaGetLastError());
+  SOL_CUDA(update_and_direction(b->mcap, solver_args(c), b->grid, c->stream));
+  count_launches(c, 4);
+  return RPCA_OK;
+}
+
+rpca_status solver_read_state(rpca_ctx* c, SolverState* out) {
+  SolverBuffers* b = c->sol;
+  SOL_CUDA(cudaMemcpyAsync(b->host, b->st, sizeof(SolverState), cudaMemcpyDeviceToHost, c->stream));
+  SOL_CUDA(cudaStreamSynchronize(c->stream));
+  memcpy(out, b->host, sizeof(SolverState));
+  return RPCA_OK;
+}
+
+rpca_status solver_prepare(rpca_ctx* c, const float* U, const float* V) {
+  rpca_status s = ensure_solver(c);
+  if (s != RPCA_OK) return s;
+  const int64_t mk = (int64_t)c->m * c->k, nk = (int64_t)c->n * c->k;
+  SOL_CUDA(cudaMemcpyAsync(c->sol->x, U, sizeof(float) * mk, cudaMemcpyDeviceToDevice, c->stream));
+  SOL_CUDA(cudaMemcpyAsync(c->sol->x + mk, V, sizeof(float) * nk, cudaMemcpyDeviceToDevice, c->stream));
+  return solver_start(c);
+}
+
+rpca_status solver_iterations(rpca_ctx* c, int count) {
+  for (int i = 0; i < count; ++i) SOL_CUDA(cudaGraphLaunch(c->sol->exec, c->stream));
+  c->graph_launches += count;
+  // Kernels inside: accept + dots + direction per launch; the while body (fused kernel,
+  // finalize, line-search step) is added from the trial count when the solve finishes.
+  count_launches(c, 3LL * count);
+  return RPCA_OK;
+}
+
+const float* solver_point(rpca_ctx* c) { return c->sol ? c->sol->x : nullptr; }
+
+}  // namespace rpca

@@ -1,0 +1,40 @@
+// Device-resident state of the L-BFGS solver (read by the host between graph launches).
+#pragma once
+#include <stdint.h>
+
+namespace rpca {
+
+constexpr int SOLVER_MAX_SLOTS = 33;  // history slots: memory cap (<= 32) + 1 spare
+
+enum { LS_RUNNING = 0, LS_ACCEPTED = 1, LS_FAILED = 2, LS_NONE = 3 };
+enum { STOP_NONE = 0, STOP_GTOL = 1, STOP_MAXITER = 2, STOP_LSFAIL = 3, STOP_CERT = 4, STOP_TIMEOUT = 5,
+       STOP_NONFINITE = 6 };
+
+struct LineSearch {
+  double f0, g0;                  // phi(0), phi'(0)
+  double a;                       // current trial step
+  double a_prev, f_prev, g_prev;  // previous trial of the bracketing phase
+  double lo, flo, glo;            // zoom bracket end with the lower objective
+  double hi, fhi, ghi;            // other bracket end
+  double f_acc;                   // objective at the accepted step
+  int phase;                      // 0 bracketing, 1 zoom
+  int first;                      // first trial of the bracketing phase
+  int evals;                      // trials in this line search
+  int state;                      // LS_*
+};
+
+struct SolverState {
+  double f, gg, g1, best_f;
+  double out[4];  // finalize output of the last trial: f, g.d, ||g||^2, ||x||^2
+  LineSearch ls;
+  int mem, count, spare;
+  int ids[SOLVER_MAX_SLOTS];  // history slots in the ring, newest first
+  double SY[SOLVER_MAX_SLOTS][SOLVER_MAX_SLOTS];  // s_i . y_j by slot
+  double YY[SOLVER_MAX_SLOTS][SOLVER_MAX_SLOTS];  // y_i . y_j by slot
+  double sg[SOLVER_MAX_SLOTS], yg[SOLVER_MAX_SLOTS];
+  double coef_g, coef_s[SOLVER_MAX_SLOTS], coef_y[SOLVER_MAX_SLOTS];
+  int iter, evals, active, gate, stop, fails, max_iter;
+  double gtol;
+};
+
+}  // namespace rpca

@@ -1,0 +1,191 @@
+"""Thin ctypes binding of librpca.so (include/rpca.h), same names as the C ABI.
+
+Argument marshalling only: every step of the computation runs in the library's CUDA
+kernels.  Device buffers may be passed as integers (raw device pointers) or as torch CUDA
+tensors (their ``data_ptr()`` is used; the caller keeps them alive).  Matrices are
+column-major: a torch tensor of shape (n, m), contiguous, holds an m x n column-major matrix.
+
+If the shared library is missing this module raises at load time; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librpca.so")
+
+RPCA_OK, RPCA_EINVAL, RPCA_ENOMEM, RPCA_ECUDA = 0, -1, -2, -3
+RPCA_ENOTCONV, RPCA_ETIMEOUT, RPCA_EUNSUPPORTED = -4, -5, -6
+STATUS_NAMES = {0: "RPCA_OK", -1: "RPCA_EINVAL", -2: "RPCA_ENOMEM", -3: "RPCA_ECUDA", -4: "RPCA_ENOTCONV",
+                -5: "RPCA_ETIMEOUT", -6: "RPCA_EUNSUPPORTED"}
+RPCA_F32, RPCA_BF16, RPCA_FP8E4M3 = 0, 1, 2
+RPCA_INIT_SKETCH, RPCA_INIT_RANDOM, RPCA_INIT_LEARNED, RPCA_INIT_USER = 0, 1, 2, 3
+
+
+class rpca_options(C.Structure):
+    _fields_ = [("lbfgs_mem", C.c_int), ("max_iter", C.c_int), ("cert_tol", C.c_double),
+                ("cert_every", C.c_int), ("init", C.c_int), ("seed", C.c_uint64), ("x_dtype", C.c_int),
+                ("refine_fp32", C.c_int), ("timeout_s", C.c_double), ("gtol", C.c_double),
+                ("sketch_oversample", C.c_int), ("sketch_power", C.c_int)]
+
+
+class rpca_cert(C.Structure):
+    _fields_ = [("cert", C.c_double), ("cert_rel", C.c_double), ("t1", C.c_double), ("t2", C.c_double),
+                ("t3", C.c_double), ("t4", C.c_double), ("normL_F", C.c_double), ("F", C.c_double),
+                ("F_bound", C.c_double), ("gap_bound", C.c_double), ("rank_r", C.c_int),
+                ("krylov_steps", C.c_int), ("sigma1_perp", C.c_double)]
+
+    def asdict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class rpca_result(C.Structure):
+    _fields_ = [("F", C.c_double), ("iters", C.c_int), ("evals", C.c_int), ("cert_evals", C.c_int),
+                ("seconds", C.c_double), ("cert", rpca_cert), ("status", C.c_int)]
+
+
+_lib = None
+
+
+def lib():
+    """Load librpca.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_1702_02241_gb300.build` "
+                           "(there is no CPU fallback)")
+    L = C.CDLL(LIB_PATH)
+    P, I64, I, D = C.c_void_p, C.c_int64, C.c_int, C.c_double
+    L.rpca_default_options.argtypes = [C.POINTER(rpca_options)]
+    L.rpca_default_options.restype = None
+    L.rpca_create.argtypes = [C.POINTER(P), I64, I64, P, I64, P, I64, I, D, D, C.POINTER(rpca_options), P]
+    L.rpca_create.restype = I
+    L.rpca_fg.argtypes = [P, P, P, C.POINTER(C.c_double), P, P]
+    L.rpca_fg.restype = I
+    L.rpca_apply.argtypes = [P, P, P, I, P, P, P, P]
+    L.rpca_apply.restype = I
+    L.rpca_init_sketch.argtypes = [P, P, P, P]
+    L.rpca_init_sketch.restype = I
+    L.rpca_solve.argtypes = [P, P, P, C.POINTER(rpca_result)]
+    L.rpca_solve.restype = I
+    L.rpca_certificate.argtypes = [P, P, P, C.POINTER(rpca_cert)]
+    L.rpca_certificate.restype = I
+    L.rpca_destroy.argtypes = [P]
+    L.rpca_destroy.restype = None
+    L.rpca_last_error.argtypes = [P]
+    L.rpca_last_error.restype = C.c_char_p
+    L.rpca_plan_info.argtypes = [P, I, C.POINTER(C.c_int64)]
+    L.rpca_plan_info.restype = I
+    L.rpca_profile.argtypes = [P, I]
+    L.rpca_profile.restype = I
+    L.rpca_profile_read.argtypes = [P, C.POINTER(C.c_double)]
+    L.rpca_profile_read.restype = I
+    L.rpca_version.argtypes = []
+    L.rpca_version.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+EXPORTED = ["rpca_default_options", "rpca_create", "rpca_fg", "rpca_apply", "rpca_init_sketch", "rpca_solve",
+            "rpca_certificate", "rpca_destroy", "rpca_last_error", "rpca_version", "rpca_plan_info",
+            "rpca_profile", "rpca_profile_read"]
+
+
+class RpcaError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _check(st, ctx):
+    if st != RPCA_OK:
+        raise RpcaError(st, rpca_last_error(ctx))
+    return st
+
+
+def rpca_default_options() -> rpca_options:
+    o = rpca_options()
+    lib().rpca_default_options(C.byref(o))
+    return o
+
+
+def rpca_last_error(ctx=None) -> str:
+    r = lib().rpca_last_error(ctx)
+    return r.decode() if r else ""
+
+
+def rpca_version() -> str:
+    return lib().rpca_version().decode()
+
+
+def rpca_create(m, n, X, ldx, mask, ldmask, k, lam_L, lam_S, opt=None, stream=None):
+    """Returns an opaque context handle (int).  X / mask: device pointers or torch tensors."""
+    h = C.c_void_p()
+    st = lib().rpca_create(C.byref(h), m, n, _ptr(X), ldx, _ptr(mask), ldmask, k, float(lam_L),
+                           float(lam_S) if not math.isinf(lam_S) else float("inf"),
+                           C.byref(opt) if opt is not None else None, stream)
+    _check(st, None)
+    return h.value
+
+
+def rpca_fg(ctx, U, V, gU, gV, want_f=True):
+    f = C.c_double(float("nan"))
+    st = lib().rpca_fg(ctx, _ptr(U), _ptr(V), C.byref(f) if want_f else None, _ptr(gU), _ptr(gV))
+    _check(st, ctx)
+    return f.value
+
+
+def rpca_apply(ctx, U, V, b, Bv, Bu, DBv, DtBu):
+    _check(lib().rpca_apply(ctx, _ptr(U), _ptr(V), b, _ptr(Bv), _ptr(Bu), _ptr(DBv), _ptr(DtBu)), ctx)
+
+
+def rpca_init_sketch(ctx, Omega, U, V):
+    _check(lib().rpca_init_sketch(ctx, _ptr(Omega), _ptr(U), _ptr(V)), ctx)
+
+
+def rpca_solve(ctx, U, V, check=True) -> rpca_result:
+    res = rpca_result()
+    st = lib().rpca_solve(ctx, _ptr(U), _ptr(V), C.byref(res))
+    if check and st not in (RPCA_OK, RPCA_ENOTCONV):
+        _check(st, ctx)
+    res.status = st
+    return res
+
+
+def rpca_certificate(ctx, U, V) -> rpca_cert:
+    out = rpca_cert()
+    _check(lib().rpca_certificate(ctx, _ptr(U), _ptr(V), C.byref(out)), ctx)
+    return out
+
+
+def rpca_plan_info(ctx, which=0) -> dict:
+    out = (C.c_int64 * 8)()
+    _check(lib().rpca_plan_info(ctx, which, out), ctx)
+    keys = ["R", "warps", "row_blocks", "col_splits", "cols_per_cta", "threads", "smem", "ctas_per_sm"]
+    return dict(zip(keys, list(out)))
+
+
+def rpca_profile(ctx, enable=True):
+    _check(lib().rpca_profile(ctx, 1 if enable else 0), ctx)
+
+
+def rpca_profile_read(ctx) -> dict:
+    out = (C.c_double * 6)()
+    _check(lib().rpca_profile_read(ctx, out), ctx)
+    keys = ["fg_launches", "fg_ms", "finalize_launches", "finalize_ms", "kernel_launches", "graph_launches"]
+    return dict(zip(keys, list(out)))
+
+
+def rpca_destroy(ctx):
+    lib().rpca_destroy(ctx)

@@ -1,0 +1,100 @@
+"""GPU certificate (Sec. 3.4) against the FP64 oracle's explicit computation.
+
+t1..t3 are float64 reductions of float32 products: compared at 1e-6 relative (plus an
+absolute floor of 1e-6 * lam_L^2 for terms that vanish).  t4 comes from block Lanczos with
+float32 Ritz values: 1e-3 relative (the tolerance stated for the spectral step).
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import certificate as ocert  # noqa: E402
+from oracle import lbfgs, sketch  # noqa: E402
+from paper_1702_02241_gb300 import gen  # noqa: E402
+
+from gpu_util import dev, make_problem  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1702_02241_gb300 import build
+    build.build()
+
+
+def compare(c, o, lam_L, t4_rel=1e-3):
+    floor = 1e-6 * lam_L ** 2
+    for name in ("t1", "t2", "t3"):
+        a, b = getattr(c, name), getattr(o, name)
+        assert abs(a - b) <= 1e-6 * abs(b) + floor, (name, a, b)
+    assert abs(c.t4 - o.t4) <= t4_rel * o.t4 + floor, (c.t4, o.t4)
+    assert c.rank_r == o.rank_r
+    assert c.normL_F == pytest.approx(o.normL_F, rel=1e-6)
+    assert c.F == pytest.approx(o.F, rel=1e-6)
+    assert c.F_bound <= o.F_bound * (1 + 1e-6)
+    assert c.cert == pytest.approx(o.cert, rel=1e-3, abs=1e-3 * lam_L)
+
+
+@pytest.mark.parametrize("m,n,k,masked", [(300, 200, 5, False), (257, 190, 3, True), (400, 130, 12, False)])
+def test_certificate_random_point(m, n, k, masked):
+    g = np.random.default_rng(m + k)
+    X = np.asfortranarray(g.normal(size=(m, n)).astype(np.float32))
+    mask = np.asfortranarray((g.random((m, n)) < 0.6).astype(np.uint8)) if masked else None
+    U, V = gen.factors(m, n, k, seed=k, scale=0.3)
+    lam_L, lam_S = 2.0, 0.5
+    P = make_problem(X, mask, k, lam_L, lam_S)
+    c = P.certificate(dev(U), dev(V))
+    o = ocert.certificate(X, mask, U, V, lam_L, lam_S)
+    compare(c, o, lam_L)
+    P.close()
+
+
+def test_certificate_rank_deficient_factors():
+    g = np.random.default_rng(3)
+    m, n, k = 200, 150, 6
+    X = np.asfortranarray(g.normal(size=(m, n)).astype(np.float32))
+    U, V = gen.factors(m, n, k, seed=1, scale=0.5)
+    U[:, 4:] = 0.0
+    V[:, 4:] = 0.0
+    P = make_problem(X, None, k, 1.0, 0.4)
+    c = P.certificate(dev(U), dev(V))
+    o = ocert.certificate(X, None, U, V, 1.0, 0.4)
+    assert c.rank_r == o.rank_r == 4
+    compare(c, o, 1.0)
+    P.close()
+
+
+def test_certificate_at_optimum_is_small():
+    inst = gen.planted_500x400(0)
+    Om = gen.gaussian(inst.n, inst.k + 10, seed=11)
+    U0, V0 = sketch.rsvd_init(inst.X, None, inst.k, Om)
+    ref = lbfgs.solve(inst.X, None, U0, V0, inst.lam_L, inst.lam_S, gtol=1e-11, max_iter=3000)
+    U, V = ref.U.astype(np.float32), ref.V.astype(np.float32)
+    P = make_problem(inst.X, None, inst.k, inst.lam_L, inst.lam_S)
+    c = P.certificate(dev(U), dev(V))
+    o = ocert.certificate(inst.X, None, U, V, inst.lam_L, inst.lam_S)
+    assert o.cert_rel < 1e-4 and c.cert_rel < 1e-4
+    assert c.t4 == 0.0 and o.t4 == 0.0
+    assert c.rank_r == o.rank_r == 5
+    assert c.sigma1_perp == pytest.approx(o.sigma_perp[0], rel=1e-3)
+    P.close()
+
+
+def test_certificate_plateau_when_k_too_small():
+    g = np.random.default_rng(5)
+    m, n = 120, 90
+    X = np.asfortranarray((g.normal(size=(m, 4)) @ g.normal(size=(4, n)) * 2.0).astype(np.float32))
+    U0, V0 = gen.factors(m, n, 2, seed=2, scale=0.5)
+    ref = lbfgs.solve(X, None, U0, V0, 1.0, math.inf, gtol=1e-12, max_iter=5000)
+    U, V = ref.U.astype(np.float32), ref.V.astype(np.float32)
+    P = make_problem(X, None, 2, 1.0, math.inf)
+    c = P.certificate(dev(U), dev(V))
+    o = ocert.certificate(X, None, U, V, 1.0, math.inf)
+    assert o.t4 > 1.0
+    compare(c, o, 1.0)
+    P.close()
