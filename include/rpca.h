@@ -73,6 +73,8 @@ typedef struct {
   double gtol;           /* also stop when ||grad F||_F <= gtol * max(1, |F|) (0 = off) */
   int sketch_oversample; /* rSVD oversampling p (10) */
   int sketch_power;      /* rSVD power iterations q (2) */
+  double ls_noise;       /* relative noise level of F below which the line search also accepts
+                            the approximate Wolfe conditions (Hager & Zhang 2005); 1e-8 */
 } rpca_options;
 
 typedef struct {
@@ -167,8 +169,9 @@ RPCA_API const char *rpca_last_error(const rpca_ctx *c);
 /*
  * Launch configuration the planner picked for the fused kernel of this context
  * (which = 0: objective/gradient; 1, 2: the certificate's and the sketch's products).
- * out[0..7] = {rows per lane R, consumer warps per CTA, row blocks, column splits,
- * columns per CTA, threads per CTA, dynamic shared memory bytes, CTAs per SM}.
+ * out[0..8] = {rows per lane R, consumer warps per CTA, row blocks, column splits,
+ * columns per CTA, threads per CTA, dynamic shared memory bytes, CTAs per SM, pipeline
+ * stages}.
  * The planner can be overridden with the environment variable RPCA_PLAN="warps,splits".
  */
 RPCA_API rpca_status rpca_plan_info(const rpca_ctx *c, int which, int64_t *out);
@@ -185,6 +188,14 @@ RPCA_API rpca_status rpca_plan_info(const rpca_ctx *c, int which, int64_t *out);
  */
 RPCA_API rpca_status rpca_profile(rpca_ctx *c, int enable);
 RPCA_API rpca_status rpca_profile_read(rpca_ctx *c, double *out);
+
+/*
+ * Per-iteration log of the last rpca_solve on c (device log ring, copied out here): fills
+ * up to max_rows rows of 7 doubles, oldest first: {iteration, F, ||grad F||_F, accepted
+ * step, line-search trials, outcome (1 accepted, 2 failed), L-BFGS pairs in use}.
+ * *rows receives the number of rows written (the ring keeps the last 256 iterations).
+ */
+RPCA_API rpca_status rpca_solve_log(rpca_ctx *c, double *out, int max_rows, int *rows);
 
 /* Library version string. */
 RPCA_API const char *rpca_version(void);

@@ -203,6 +203,7 @@ static rpca_status time_plan(rpca_ctx* c, const FgPlan& q, double* ms) {
   a.nrb = q.nrb;
   a.ncs = q.ncs;
   a.BN = q.BN;
+  a.nstage = q.nstage;
   a.PU = c->ws.PU;
   a.PV = c->ws.PV;
   a.Ppsi = c->ws.Ppsi;
@@ -233,21 +234,20 @@ static rpca_status time_plan(rpca_ctx* c, const FgPlan& q, double* ms) {
 // Chooses consumer warps per CTA (WC) and the column split (ncs, BN).  A time model ranks
 // the configurations that fit (whole waves of tiles at full bandwidth, a partly filled last
 // wave costing at least half a wave, plus the write and re-read of the partial sums); the
-// six best are then timed on the device and the fastest is kept (cached per shape in this
-// process).  RPCA_PLAN="warps,splits" forces one configuration; RPCA_AUTOTUNE=0 keeps the
+// twelve best are then timed on the device and the fastest is kept (cached per shape in
+// this process).  RPCA_PLAN="warps,splits" forces one configuration; RPCA_AUTOTUNE=0 keeps the
 // model's choice without timing.
 static rpca_status make_plan(rpca_ctx* c, FgPlan* P, int K, int B, bool same) {
   const bool masked = c->bits != nullptr;
   const FgVariant* v = fg_variant(K, B, same, masked);
   if (!v) return set_err(c, RPCA_EUNSUPPORTED, "no compiled kernel for this factor rank");
   const int KV = same ? K : K + B;
-  const int JB = v->J * B;
   double best = 1e300;
   std::vector<std::pair<double, FgPlan>> cands;
   int force_wc = 0, force_ncs = 0, n_smem = 0, n_attr = 0, n_occ = 0, n_try = 0;
   cudaError_t last_occ = cudaSuccess;
   if (const char* env = getenv("RPCA_PLAN")) sscanf(env, "%d,%d", &force_wc, &force_ncs);
-  for (int WC : {8, 4, 2}) {
+  for (int WC : {8, 4, 2}) for (int nst : {3, 2}) {
     if (force_wc && WC != force_wc) continue;
     const int BM = WC * 32 * v->R;
     const int nrb = (c->m + BM - 1) / BM;
@@ -261,7 +261,7 @@ static rpca_status make_plan(rpca_ctx* c, FgPlan* P, int K, int B, bool same) {
       if (ncs == last_ncs) continue;
       if (force_ncs && ncs != force_ncs) continue;
       last_ncs = ncs;
-      const FgSmem L = fg_smem_layout(WC, v->R, masked, BN, KV, JB);
+      const FgSmem L = fg_smem_layout(WC, v->R, masked, BN, KV, B, nst);
       ++n_try;
       if (L.total > c->max_smem) {
         ++n_smem;
@@ -303,6 +303,7 @@ static rpca_status make_plan(rpca_ctx* c, FgPlan* P, int K, int B, bool same) {
       cand.threads = threads;
       cand.smem = L.total;
       cand.cps = cps;
+      cand.nstage = nst;
       cands.push_back({t, cand});
       if (t < best) best = t;
     }
@@ -317,11 +318,13 @@ static rpca_status make_plan(rpca_ctx* c, FgPlan* P, int K, int B, bool same) {
   }
   std::sort(cands.begin(), cands.end(),
             [](const std::pair<double, FgPlan>& a, const std::pair<double, FgPlan>& b) { return a.first < b.first; });
-  const int64_t N = (int64_t)(c->m + c->n) * B;
   for (auto& cp : cands) {
     FgPlan& q = cp.second;
-    // Finalize grid: enough blocks to cover (m + n) B elements, at most 4 waves of the SMs.
-    q.fin_grid = (int)std::max<int64_t>(1, std::min<int64_t>((N + 255) / 256, 4LL * c->nsm));
+    // Finalize grid: one m x B element per thread and one n x B element per warp (so every
+    // load is in flight at once), capped at a few dozen waves.
+    q.fin_gu = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)c->m * B + 255) / 256, 64LL * c->nsm));
+    q.fin_gv = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)c->n * B + 7) / 8, 16LL * c->nsm));
+    q.fin_grid = q.fin_gu + q.fin_gv;
   }
   // Cached choice for this shape, or measure the best few candidates of the model.
   const PlanKey key{c->device, c->m, c->n, c->ldx, K, B, same, masked};
@@ -330,9 +333,10 @@ static rpca_status make_plan(rpca_ctx* c, FgPlan* P, int K, int B, bool same) {
   const bool measure = !(force_wc || force_ncs) && autotune_enabled() && cands.size() > 1;
   if (measure && plan_cache_get(key, &cached_wc, &cached_ncs)) {
     for (size_t i = 0; i < cands.size(); ++i)
-      if (cands[i].second.WC == cached_wc && cands[i].second.ncs == cached_ncs) pick = (int)i;
+      if (cands[i].second.WC * 16 + cands[i].second.nstage == cached_wc && cands[i].second.ncs == cached_ncs)
+        pick = (int)i;
   } else if (measure) {
-    const int ntry = (int)std::min<size_t>(6, cands.size());
+    const int ntry = (int)std::min<size_t>(12, cands.size());
     double best_ms = 1e300;
     for (int i = 0; i < ntry; ++i) {
       FgPlan& q = cands[i].second;
@@ -346,7 +350,7 @@ static rpca_status make_plan(rpca_ctx* c, FgPlan* P, int K, int B, bool same) {
         pick = i;
       }
     }
-    plan_cache_put(key, cands[pick].second.WC, cands[pick].second.ncs);
+    plan_cache_put(key, cands[pick].second.WC * 16 + cands[pick].second.nstage, cands[pick].second.ncs);
   }
   FgPlan bp = cands[pick].second;
   rpca_status s = finish_plan(c, &bp);
@@ -406,6 +410,7 @@ rpca_status launch_fg(rpca_ctx* c, const FgPlan& P, const FgLaunch& L, cudaStrea
   a.nrb = P.nrb;
   a.ncs = P.ncs;
   a.BN = P.BN;
+  a.nstage = P.nstage;
   a.PU = c->ws.PU;
   a.PV = c->ws.PV;
   a.Ppsi = c->ws.Ppsi;
@@ -437,6 +442,7 @@ rpca_status launch_fg(rpca_ctx* c, const FgPlan& P, const FgLaunch& L, cudaStrea
   f.nrb = P.nrb;
   f.ncs = P.ncs;
   f.nctas = P.nrb * P.ncs;
+  f.gu = P.fin_gu;
   f.PU = c->ws.PU;
   f.PV = c->ws.PV;
   f.Ppsi = c->ws.Ppsi;
@@ -504,6 +510,7 @@ void rpca_default_options(rpca_options* o) {
   o->gtol = 0.0;
   o->sketch_oversample = 10;
   o->sketch_power = 2;
+  o->ls_noise = 1e-8;
 }
 
 const char* rpca_version(void) { return "rpca-gb300 0.1 (sm_103a)"; }
@@ -547,8 +554,8 @@ rpca_status rpca_plan_info(const rpca_ctx* c, int which, int64_t* out) {
   if (!c || !out || which < 0 || which > 2) return RPCA_EINVAL;
   const FgPlan& P = which == 0 ? c->fg_plan : c->ap_plan[which == 1 ? (c->k <= 8 ? 1 : 2) : 0];
   if (!P.valid) return RPCA_EINVAL;
-  const int64_t v[8] = {P.R, P.WC, P.nrb, P.ncs, P.BN, P.threads, (int64_t)P.smem, P.cps};
-  for (int i = 0; i < 8; ++i) out[i] = v[i];
+  const int64_t v[9] = {P.R, P.WC, P.nrb, P.ncs, P.BN, P.threads, (int64_t)P.smem, P.cps, P.nstage};
+  for (int i = 0; i < 9; ++i) out[i] = v[i];
   return RPCA_OK;
 }
 

@@ -51,6 +51,7 @@ struct CertState {
   double G2[LZ_TMAX * LZ_B];
   double R[LZ_B * LZ_B], Rinv[LZ_B * LZ_B];
   int bad_mask;  // columns whose Cholesky pivot collapsed in the last block QR
+  double n0[LZ_B];  // squared column norms before the last projection
   double t4_prev, s1_prev;
   int converged;
   double resid[2];
@@ -263,16 +264,25 @@ __global__ void __launch_bounds__(256) cert_resid_kernel(const float* A, const f
 }
 
 // Cholesky of the 8 x 8 Gram in st->G; records the columns whose pivot collapsed (that
-// column is numerically in the span of the earlier ones).
-__global__ void cert_chol_kernel(CertState* st) {
+// column is numerically in the span of the earlier ones and of the bases projected out).
+__global__ void cert_chol_kernel(CertState* st, double rel, int per_column) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double dmax = 0.0;
-  for (int i = 0; i < LZ_B; ++i) dmax = fmax(dmax, st->G[i + i * LZ_B]);
-  chol_upper_inv(st->G, LZ_B, st->R, st->Rinv);
   int mask = 0;
-  for (int i = 0; i < LZ_B; ++i)
-    if (!(st->R[i + i * LZ_B] * st->R[i + i * LZ_B] > 1e-12 * fmax(dmax, 1e-300))) mask |= 1 << i;
+  chol_upper_inv_masked(st->G, LZ_B, rel, st->R, st->Rinv, &mask, per_column ? st->n0 : nullptr);
   st->bad_mask = mask;
+}
+
+// Records the squared column norms (diagonal of the Gram in st->G).
+__global__ void cert_norms_kernel(CertState* st) {
+  if (threadIdx.x < LZ_B && blockIdx.x == 0) st->n0[threadIdx.x] = st->G[threadIdx.x * (LZ_B + 1)];
+}
+
+// Columns flagged in st->bad_mask are set to zero (the Krylov space is exhausted there).
+__global__ void cert_zero_cols_kernel(float* Y, int64_t rows, const CertState* st) {
+  const int mask = st->bad_mask;
+  if (mask == 0) return;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < rows * LZ_B; i += (int64_t)gridDim.x * blockDim.x)
+    if ((mask >> (int)(i / rows)) & 1) Y[i] = 0.f;
 }
 
 // Collapsed columns of Y (rows x 8) are replaced by fresh Gaussian columns.
@@ -335,8 +345,12 @@ __global__ void __launch_bounds__(1024) cert_ritz_kernel(CertState* st, const do
       if (e > 0.0) t4 += e * e;
     }
     const double s1 = s[ord[0]];
+    int above = 0;
+    for (int i = 0; i < d; ++i) above += (double)s[i] > lam_L;
+    // Settled: sigma_1 and t4 stopped moving, and the Ritz values above lam_L leave at least
+    // two blocks of the Krylov space to spare (otherwise more of them may be missing).
     const bool settled = st->s1_prev >= 0.0 && fabs(s1 - st->s1_prev) <= 1e-5 * s1 &&
-                         fabs(t4 - st->t4_prev) <= 1e-4 * t4 + 1e-12 * lam_L * lam_L;
+                         fabs(t4 - st->t4_prev) <= 1e-4 * t4 + 1e-12 * lam_L * lam_L && above + 2 * LZ_B <= d;
     st->converged = settled || final_step;
     st->t4_prev = t4;
     st->s1_prev = s1;
@@ -440,34 +454,66 @@ static rpca_status project_out(rpca_ctx* c, const float* Bm, int p, float* Y, in
   return RPCA_OK;
 }
 
-static rpca_status chol_pass(rpca_ctx* c, float* Y, int64_t rows) {
+// Gram of Y and its masked Cholesky.  per_column: a pivot below rel * (squared norm of
+// that column recorded by record_norms) marks it collapsed; otherwise the floor is
+// rel * (largest squared column norm).
+static rpca_status gram_chol(rpca_ctx* c, float* Y, int64_t rows, double rel, int per_column) {
   CertBuffers* b = c->cert;
   CERT_CUDA(ts_gram_c(c, Y, rows, LZ_B, Y, rows, LZ_B, rows, b->st->G, b->ts, c->stream));
-  cert_chol_kernel<<<1, 1, 0, c->stream>>>(b->st);
+  cert_chol_kernel<<<1, 1, 0, c->stream>>>(b->st, rel, per_column);
   count_launches(c, 1);
-  CERT_CUDA(ts_mul_c(c, Y, rows, LZ_B, b->st->Rinv, LZ_B, LZ_B, Y, rows, rows, 1.f, 0.f, c->stream));
+  return RPCA_OK;
+}
+
+static rpca_status record_norms(rpca_ctx* c, float* Y, int64_t rows) {
+  CertBuffers* b = c->cert;
+  CERT_CUDA(ts_gram_c(c, Y, rows, LZ_B, Y, rows, LZ_B, rows, b->st->G, b->ts, c->stream));
+  cert_norms_kernel<<<1, 32, 0, c->stream>>>(b->st);
+  count_launches(c, 1);
+  return RPCA_OK;
+}
+
+static rpca_status project_all(rpca_ctx* c, float* Y, int64_t rows, const float* F, int f, const float* Bm, int p) {
+  rpca_status s;
+  for (int pass = 0; pass < 2; ++pass) {
+    if ((s = project_out(c, F, f, Y, rows)) != RPCA_OK) return s;
+    if ((s = project_out(c, Bm, p, Y, rows)) != RPCA_OK) return s;
+  }
+  return RPCA_OK;
+}
+
+static rpca_status normalise(rpca_ctx* c, float* Y, int64_t rows) {
+  rpca_status s = gram_chol(c, Y, rows, 1e-12, 0);
+  if (s != RPCA_OK) return s;
+  CERT_CUDA(ts_mul_c(c, Y, rows, LZ_B, c->cert->st->Rinv, LZ_B, LZ_B, Y, rows, rows, 1.f, 0.f, c->stream));
   return RPCA_OK;
 }
 
 // Orthonormalises the block Y (rows x 8) against the fixed basis F (rows x f) and the
-// Krylov basis B (rows x p): two rounds of classical Gram-Schmidt and CholeskyQR; columns
-// that collapse in the first round are replaced by random ones, which the second round
-// orthonormalises.  All on the stream, no host synchronisation.
+// Krylov basis B (rows x p), on the stream with no host synchronisation.  A column that
+// loses all but 1e-3 of its norm to the projections and to the earlier columns of its block
+// is treated as collapsed (in float32 its remainder is mostly rounding along F and B, which
+// normalising would amplify): it is replaced by a random column, projected again, and
+// zeroed if it collapses again (the complement of F and B is exhausted).  After the first
+// normalisation the block is projected once more, then normalised again.
 static rpca_status orth_block(rpca_ctx* c, float* Y, int64_t rows, const float* F, int f, const float* Bm, int p,
                               uint64_t seed) {
   rpca_status s;
-  for (int round = 0; round < 2; ++round) {
-    if ((s = project_out(c, F, f, Y, rows)) != RPCA_OK) return s;
-    if ((s = project_out(c, Bm, p, Y, rows)) != RPCA_OK) return s;
-    if ((s = project_out(c, F, f, Y, rows)) != RPCA_OK) return s;
-    if ((s = project_out(c, Bm, p, Y, rows)) != RPCA_OK) return s;
-    if ((s = chol_pass(c, Y, rows)) != RPCA_OK) return s;
-    if (round == 0) {
-      cert_refill_kernel<<<256, 256, 0, c->stream>>>(Y, rows, c->cert->st, seed);
-      count_launches(c, 1);
-    }
-  }
-  return RPCA_OK;
+  CertBuffers* b = c->cert;
+  const double collapse = 1e-6;  // squared-norm ratio
+  if ((s = record_norms(c, Y, rows)) != RPCA_OK) return s;
+  if ((s = project_all(c, Y, rows, F, f, Bm, p)) != RPCA_OK) return s;
+  if ((s = gram_chol(c, Y, rows, collapse, 1)) != RPCA_OK) return s;
+  cert_refill_kernel<<<256, 256, 0, c->stream>>>(Y, rows, b->st, seed);
+  count_launches(c, 1);
+  if ((s = record_norms(c, Y, rows)) != RPCA_OK) return s;
+  if ((s = project_all(c, Y, rows, F, f, Bm, p)) != RPCA_OK) return s;
+  if ((s = gram_chol(c, Y, rows, collapse, 1)) != RPCA_OK) return s;
+  cert_zero_cols_kernel<<<256, 256, 0, c->stream>>>(Y, rows, b->st);
+  count_launches(c, 1);
+  if ((s = normalise(c, Y, rows)) != RPCA_OK) return s;
+  if ((s = project_all(c, Y, rows, F, f, Bm, p)) != RPCA_OK) return s;
+  return normalise(c, Y, rows);
 }
 
 static rpca_status apply_D(rpca_ctx* c, const float* BV, const float* BU, float* Y1, float* Y2) {

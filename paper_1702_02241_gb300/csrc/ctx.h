@@ -22,8 +22,9 @@ struct FgPlan {
   int R = 0, WC = 0, nrb = 0, ncs = 0, BN = 0;
   int threads = 0;
   size_t smem = 0;
-  int fin_grid = 0;
+  int fin_grid = 0, fin_gu = 0, fin_gv = 0;
   int cps = 0;  // CTAs per SM at this configuration
+  int nstage = 3;
   CUtensorMap tmX;  // box {32 R rows, 8 columns}
   CUtensorMap tmM;  // bitmap box {WC * R words, 8 columns}
 };

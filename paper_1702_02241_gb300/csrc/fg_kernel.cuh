@@ -14,8 +14,9 @@
 // each own 32*R rows of the tile (R rows per lane, as float2 pairs for the packed fp32x2
 // FMA pipe) and walk the tile's columns.  Per lane the factor rows live in registers for
 // the whole tile; the gradient rows (D Bv) accumulate in registers over all columns; the
-// column sums (D^T Bu) are reduced across lanes with a shuffle reduce-scatter and across
-// warps through shared memory, in a fixed order (bitwise deterministic).
+// column sums (D^T Bu) are reduced across lanes with a shuffle reduce-scatter into a
+// per-warp shared-memory slab, and across warps once at the end of the tile, in a fixed
+// order (bitwise deterministic).
 #pragma once
 #include "common.cuh"
 
@@ -35,6 +36,7 @@ struct FgArgs {
   const float* BV;  // apply mode: n x B (ld n)
   float lam_S;
   int nrb, ncs, BN;  // row blocks, column splits, columns per split (multiple of 8)
+  int nstage;        // pipeline depth (2 or FG_NSTAGE)
   float* PU;         // [ncs][B][mpad]  -(D Bv) partial sums over a CTA's columns
   float* PV;         // [nrb][B][n]      D^T Bu partial sums over a CTA's rows
   double* Ppsi;      // [nrb*ncs]        sum of psi over a CTA's tile
@@ -42,10 +44,10 @@ struct FgArgs {
 };
 
 constexpr int FG_BJ = 8;      // columns per pipeline stage
-constexpr int FG_NSTAGE = 3;  // pipeline depth
+constexpr int FG_NSTAGE = 3;  // maximum pipeline depth
 
 struct FgSmem {
-  size_t x_off, m_off, v_off, red_off, bar_off, scr_off, total;
+  size_t x_off, m_off, v_off, cs_off, bar_off, scr_off, total;
 };
 
 // Observation bitmap of one stage: one TMA box per CTA, {WC * R words, BJ columns}, so the
@@ -54,19 +56,20 @@ __host__ __device__ inline size_t fg_mask_stage_bytes(int WC, int R) {
   return ((size_t)FG_BJ * WC * R * 4 + 127) & ~(size_t)127;
 }
 
-// Shared-memory carve-up (byte offsets from a 1024-byte aligned base).
-__host__ __device__ inline FgSmem fg_smem_layout(int WC, int R, bool masked, int BN, int KV, int JB) {
+// Shared-memory carve-up (byte offsets from a 1024-byte aligned base): X stages, bitmap
+// stages, the CTA's factor slice, one slab of column sums per consumer warp, mbarriers.
+__host__ __device__ inline FgSmem fg_smem_layout(int WC, int R, bool masked, int BN, int KV, int B, int nstage) {
   FgSmem L;
   size_t o = 0;
   L.x_off = o;
-  o += (size_t)FG_NSTAGE * WC * FG_BJ * 32 * R * 4;
+  o += (size_t)nstage * WC * FG_BJ * 32 * R * 4;
   L.m_off = o;
-  if (masked) o += (size_t)FG_NSTAGE * fg_mask_stage_bytes(WC, R);
+  if (masked) o += (size_t)nstage * fg_mask_stage_bytes(WC, R);
   o = (o + 15) & ~(size_t)15;
   L.v_off = o;
   o += (size_t)BN * KV * 8;
-  L.red_off = o;
-  o += (size_t)2 * WC * JB * 4;
+  L.cs_off = o;
+  o += (size_t)WC * BN * B * 4;
   o = (o + 7) & ~(size_t)7;
   L.bar_off = o;
   o += 2 * FG_NSTAGE * 8;
@@ -127,11 +130,12 @@ __global__ void __launch_bounds__(288) fg_kernel(const __grid_constant__ CUtenso
   const int col0 = cs * a.BN;
   const int ncols = min(a.BN, a.n - col0);
   const int nchunks = (ncols + FG_BJ - 1) / FG_BJ;
-  const FgSmem L = fg_smem_layout(WC, R, MASKED, a.BN, KV, JB);
+  const int nst = a.nstage;
+  const FgSmem L = fg_smem_layout(WC, R, MASKED, a.BN, KV, B, nst);
   float* xs_all = reinterpret_cast<float*>(sm + L.x_off);
   uint32_t* ms_all = reinterpret_cast<uint32_t*>(sm + L.m_off);
   float2* vsl = reinterpret_cast<float2*>(sm + L.v_off);
-  float* red = reinterpret_cast<float*>(sm + L.red_off);
+  float* csum = reinterpret_cast<float*>(sm + L.cs_off);  // [WC][BN][B]
   uint64_t* full = reinterpret_cast<uint64_t*>(sm + L.bar_off);
   uint64_t* empty = full + FG_NSTAGE;
   double* scr = reinterpret_cast<double*>(sm + L.scr_off);
@@ -141,7 +145,7 @@ __global__ void __launch_bounds__(288) fg_kernel(const __grid_constant__ CUtenso
   const uint32_t stage_bytes = (uint32_t)(WC * xbox * 4 + (MASKED ? (size_t)FG_BJ * mrow * 4 : 0));
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < FG_NSTAGE; ++s) {
+    for (int s = 0; s < nst; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], WC);
     }
@@ -156,9 +160,9 @@ __global__ void __launch_bounds__(288) fg_kernel(const __grid_constant__ CUtenso
       int issued = 0;
       bool ok = true;
       for (int c = 0; c < nchunks; ++c) {
-        const int s = c % FG_NSTAGE;
-        const uint32_t ph = (uint32_t)(c / FG_NSTAGE) & 1u;
-        if (c >= FG_NSTAGE && !mbar_wait_bounded(&empty[s], ph ^ 1u)) {
+        const int s = c % nst;
+        const uint32_t ph = (uint32_t)(c / nst) & 1u;
+        if (c >= nst && !mbar_wait_bounded(&empty[s], ph ^ 1u)) {
           atomicOr(a.err, DEV_ERR_TIMEOUT_EMPTY);
           ok = false;
           break;
@@ -170,8 +174,8 @@ __global__ void __launch_bounds__(288) fg_kernel(const __grid_constant__ CUtenso
         issued = c + 1;
       }
       // Wait (bounded) until every copy this thread issued has landed before leaving.
-      for (int c = max(0, issued - FG_NSTAGE); c < issued; ++c) {
-        if (!mbar_wait_bounded(&full[c % FG_NSTAGE], (uint32_t)(c / FG_NSTAGE) & 1u)) {
+      for (int c = max(0, issued - nst); c < issued; ++c) {
+        if (!mbar_wait_bounded(&full[c % nst], (uint32_t)(c / nst) & 1u)) {
           atomicOr(a.err, DEV_ERR_TIMEOUT_DRAIN);
           break;
         }
@@ -246,11 +250,10 @@ __global__ void __launch_bounds__(288) fg_kernel(const __grid_constant__ CUtenso
   const float lam = a.lam_S;
   const float2 mhalf = f2(-0.5f, -0.5f);
   bool failed = false;
-  int gcount = 0;
 
   for (int c = 0; c < nchunks; ++c) {
-    const int s = c % FG_NSTAGE;
-    if (!failed && !mbar_wait_bounded(&full[s], (uint32_t)(c / FG_NSTAGE) & 1u)) {
+    const int s = c % nst;
+    if (!failed && !mbar_wait_bounded(&full[s], (uint32_t)(c / nst) & 1u)) {
       failed = true;
       if (lane == 0) atomicOr(a.err, DEV_ERR_TIMEOUT_FULL);
     }
@@ -340,20 +343,12 @@ __global__ void __launch_bounds__(288) fg_kernel(const __grid_constant__ CUtenso
       int base = 0;
       ReduceScatter<JB, 16>::run(vals, lane, base);
       constexpr int CF = rs_count(JB), DUP = rs_dup_mask(JB);
-      float* rbuf = red + (size_t)(gcount & 1) * WC * JB;
+      // This warp's sums for the group's J columns go to its own slab (no barrier here).
+      float* slab = csum + ((size_t)warp * a.BN + (size_t)c * FG_BJ + g * J) * B;
       if ((lane & DUP) == 0) {
 #pragma unroll
-        for (int t = 0; t < CF; ++t) rbuf[warp * JB + base + t] = vals[t];
+        for (int t = 0; t < CF; ++t) slab[base + t] = vals[t];
       }
-      named_bar(1, nct);
-      if (tid < JB) {
-        float sum = 0.f;
-        for (int w = 0; w < WC; ++w) sum += rbuf[w * JB + tid];
-        const int jj = tid / B, b = tid - (tid / B) * B;
-        const int j = col0 + c * FG_BJ + g * J + jj;
-        if (j < col0 + ncols) a.PV[((size_t)rb * B + b) * a.n + j] = sum;
-      }
-      ++gcount;
     }
     psi_d += (double)psi2.x + (double)psi2.y;
     __syncwarp();
@@ -370,7 +365,7 @@ __global__ void __launch_bounds__(288) fg_kernel(const __grid_constant__ CUtenso
         *reinterpret_cast<float2*>(a.PU + ((size_t)cs * B + b) * a.mpad + i0) = gu[p][b];
     }
   }
-  // Sum of psi over the tile.
+  // Sum of psi over the tile; column sums over the consumer warps in fixed order.
   psi_d = warp_sum_d(psi_d);
   if (lane == 0) scr[warp] = psi_d;
   named_bar(1, nct);
@@ -378,6 +373,12 @@ __global__ void __launch_bounds__(288) fg_kernel(const __grid_constant__ CUtenso
     double s = 0.0;
     for (int w = 0; w < WC; ++w) s += scr[w];
     a.Ppsi[blockIdx.x] = s;
+  }
+  for (int idx = tid; idx < ncols * B; idx += nct) {
+    const int b = idx / ncols, jl = idx - b * ncols;
+    float sum = 0.f;
+    for (int w = 0; w < WC; ++w) sum += csum[((size_t)w * a.BN + jl) * B + b];
+    a.PV[((size_t)rb * B + b) * a.n + col0 + jl] = sum;
   }
 }
 

@@ -12,6 +12,7 @@ enum { FIN_FG = 0, FIN_APPLY = 1, FIN_FG_RAW = 2 };
 
 struct FinArgs {
   int m, n, B, mpad, nrb, ncs, nctas;
+  int gu;  // blocks [0, gu) handle the m x B side; the rest the n x B side
   const float* PU;
   const float* PV;
   const double* Ppsi;

@@ -3,7 +3,7 @@
 // finalize_kernel sums the per-CTA partials of fg_kernel in a fixed order and adds the
 // factor penalty of Eq. (Thm5):
 //   G_U = D V + lam_L U,  G_V = D^T U + lam_L V,
-//   f   = sum psi + lam_L/2 (||U||_F^2 + ||V||_F^2)       (all sums over CTAs in float64)
+//   f   = sum psi + lam_L/2 (||U||_F^2 + ||V||_F^2)       (sums over CTAs in float64)
 // at the trial point (U + alpha dU, V + alpha dV).  It also returns, in float64, the
 // directional derivative g.d along an optional direction and ||g||^2.  The last block to
 // finish (atomic ticket) combines the per-block partials in index order, so the result is
@@ -13,59 +13,99 @@
 
 namespace rpca {
 
+// Deterministic block sum of three doubles per thread; results valid in thread 0.
+RPCA_DEV void block_sum3(double& x, double& y, double& z, double (*scr)[3]) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    x += __shfl_xor_sync(0xffffffffu, x, o);
+    y += __shfl_xor_sync(0xffffffffu, y, o);
+    z += __shfl_xor_sync(0xffffffffu, z, o);
+  }
+  __syncthreads();
+  if (lane == 0) {
+    scr[w][0] = x;
+    scr[w][1] = y;
+    scr[w][2] = z;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    x = y = z = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+      x += scr[i][0];
+      y += scr[i][1];
+      z += scr[i][2];
+    }
+  }
+}
+
+// Blocks [0, a.gu) handle the m x B side one element per thread (a few column-split
+// partials each); blocks [a.gu, gridDim.x) handle the n x B side one element per warp, the
+// lanes splitting the row-block partials (fixed-order shuffle sum).
 __global__ void __launch_bounds__(256) finalize_kernel(FinArgs a) {
-  __shared__ double scr[32];
+  __shared__ double scr[32][3];
   __shared__ bool is_last;
   if (a.gate != nullptr && *a.gate == 0) return;
-  const int64_t mB = (int64_t)a.m * a.B, N = mB + (int64_t)a.n * a.B;
   const float alpha = a.alpha_dev ? (float)*a.alpha_dev : a.alpha;
-  double nrm = 0.0, gd = 0.0, gg = 0.0;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x) {
-    float g, xt, dir = 0.f;
-    if (e < mB) {
+  const float lam = (float)a.lam_L;
+  const int64_t mB = (int64_t)a.m * a.B, nB = (int64_t)a.n * a.B;
+  // Element-wise work in float32 (GB300's float64 pipe is ~1/64 of float32; the partial
+  // sums are float32 already); each thread's dot products go to float64 once at the end.
+  float nrm_f = 0.f, gd_f = 0.f, gg_f = 0.f;
+  if ((int)blockIdx.x < a.gu) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < mB; e += (int64_t)a.gu * blockDim.x) {
       const int l = (int)(e / a.m), i = (int)(e - (int64_t)l * a.m);
-      double s = 0.0;
-      for (int c = 0; c < a.ncs; ++c) s += (double)a.PU[((int64_t)c * a.B + l) * a.mpad + i];
+      float s = 0.f;
+      for (int c = 0; c < a.ncs; ++c) s += a.PU[((int64_t)c * a.B + l) * a.mpad + i];
+      float g, xt = 0.f, dir = 0.f;
       if (a.mode != FIN_APPLY) {
         xt = a.U[e];
         if (a.dU) xt = fmaf(alpha, a.dU[e], xt);
-        g = a.mode == FIN_FG ? (float)(-s + a.lam_L * (double)xt) : (float)(-s);
+        g = a.mode == FIN_FG ? fmaf(lam, xt, -s) : -s;
         if (a.Ut) a.Ut[e] = xt;
         if (a.DU) dir = a.DU[e];
       } else {
-        xt = 0.f;
-        g = (float)(-s);
+        g = -s;
       }
       a.GU[e] = g;
-    } else {
-      const int64_t e2 = e - mB;
-      const int l = (int)(e2 / a.n), j = (int)(e2 - (int64_t)l * a.n);
-      double s = 0.0;
-      for (int r = 0; r < a.nrb; ++r) s += (double)a.PV[((int64_t)r * a.B + l) * a.n + j];
-      if (a.mode != FIN_APPLY) {
-        xt = a.V[e2];
-        if (a.dV) xt = fmaf(alpha, a.dV[e2], xt);
-        g = a.mode == FIN_FG ? (float)(s + a.lam_L * (double)xt) : (float)s;
-        if (a.Vt) a.Vt[e2] = xt;
-        if (a.DV) dir = a.DV[e2];
-      } else {
-        xt = 0.f;
-        g = (float)s;
-      }
-      a.GV[e2] = g;
+      nrm_f = fmaf(xt, xt, nrm_f);
+      gd_f = fmaf(g, dir, gd_f);
+      gg_f = fmaf(g, g, gg_f);
     }
-    nrm += (double)xt * (double)xt;
-    gd += (double)g * (double)dir;
-    gg += (double)g * (double)g;
+  } else {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)(gridDim.x - a.gu) * (blockDim.x >> 5);
+    for (int64_t e2 = (int64_t)(blockIdx.x - a.gu) * (blockDim.x >> 5) + (threadIdx.x >> 5); e2 < nB; e2 += warps) {
+      const int l = (int)(e2 / a.n), j = (int)(e2 - (int64_t)l * a.n);
+      float s = 0.f;
+      for (int r = lane; r < a.nrb; r += 32) s += a.PV[((int64_t)r * a.B + l) * a.n + j];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) {
+        float g, xt = 0.f, dir = 0.f;
+        if (a.mode != FIN_APPLY) {
+          xt = a.V[e2];
+          if (a.dV) xt = fmaf(alpha, a.dV[e2], xt);
+          g = a.mode == FIN_FG ? fmaf(lam, xt, s) : s;
+          if (a.Vt) a.Vt[e2] = xt;
+          if (a.DV) dir = a.DV[e2];
+        } else {
+          g = s;
+        }
+        a.GV[e2] = g;
+        nrm_f = fmaf(xt, xt, nrm_f);
+        gd_f = fmaf(g, dir, gd_f);
+        gg_f = fmaf(g, g, gg_f);
+      }
+    }
   }
+  double nrm = nrm_f, gd = gd_f, gg = gg_f;
   if (a.mode == FIN_APPLY) return;
-  const double s0 = block_sum_d(nrm, scr);
-  const double s1 = block_sum_d(gd, scr);
-  const double s2 = block_sum_d(gg, scr);
+  block_sum3(nrm, gd, gg, scr);
   if (threadIdx.x == 0) {
-    a.blk[3 * blockIdx.x + 0] = s0;
-    a.blk[3 * blockIdx.x + 1] = s1;
-    a.blk[3 * blockIdx.x + 2] = s2;
+    a.blk[3 * blockIdx.x + 0] = nrm;
+    a.blk[3 * blockIdx.x + 1] = gd;
+    a.blk[3 * blockIdx.x + 2] = gg;
     __threadfence();
     const unsigned t = atomicAdd(a.counter, 1u);
     is_last = (t == gridDim.x - 1);
@@ -79,11 +119,11 @@ __global__ void __launch_bounds__(256) finalize_kernel(FinArgs a) {
     p1 += __ldcg(&a.blk[3 * b + 1]);
     p2 += __ldcg(&a.blk[3 * b + 2]);
   }
+  block_sum3(p0, p1, p2, scr);
+  __syncthreads();
   for (int b = threadIdx.x; b < a.nctas; b += blockDim.x) ps += __ldcg(&a.Ppsi[b]);
-  p0 = block_sum_d(p0, scr);
-  p1 = block_sum_d(p1, scr);
-  p2 = block_sum_d(p2, scr);
-  ps = block_sum_d(ps, scr);
+  double d1 = 0.0, d2 = 0.0;
+  block_sum3(ps, d1, d2, scr);
   if (threadIdx.x == 0) {
     a.out[0] = ps + 0.5 * a.lam_L * p0;
     a.out[1] = p1;

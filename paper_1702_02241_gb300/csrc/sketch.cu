@@ -27,9 +27,19 @@ struct SketchState {
 
 void fill_normal(float* out, int64_t count, uint64_t seed, float scale, cudaStream_t s);
 
+// Cholesky of the l x l Gram; collapsed columns (the sketch of a matrix of rank < l) are
+// flagged and left uncoupled.
 __global__ void sk_chol_kernel(SketchState* st, int l) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  st->bad = chol_upper_inv(st->G, l, st->R, st->Rinv);
+  chol_upper_inv_masked(st->G, l, 1e-10, st->R, st->Rinv, &st->bad);
+}
+
+// Zero the flagged columns of Y (rows x l).
+__global__ void sk_zero_cols_kernel(float* Y, int64_t rows, int l, const SketchState* st) {
+  const int mask = st->bad;
+  if (mask == 0) return;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < rows * l; i += (int64_t)gridDim.x * blockDim.x)
+    if ((mask >> (int)(i / rows)) & 1) Y[i] = 0.f;
 }
 
 // Eigen-decomposition of the l x l Gram of B^T (one CTA); C1 = U_B[:, :k] Sigma^{1/2} and
@@ -101,11 +111,17 @@ static rpca_status sk_apply(rpca_ctx* c, SketchBuffers& b, int l, const float* B
   return RPCA_OK;
 }
 
+// CholeskyQR2; columns that collapse in the first pass are zeroed (rank of the sketch < l).
 static rpca_status sk_orth(rpca_ctx* c, SketchBuffers& b, float* Y, int64_t rows, int l) {
-  for (int pass = 0; pass < 2; ++pass) {
+  for (int pass = 0; pass < 3; ++pass) {
     SK_CUDA(ts_gram_c(c, Y, rows, l, Y, rows, l, rows, b.st->G, b.ts, c->stream));
     sk_chol_kernel<<<1, 1, 0, c->stream>>>(b.st, l);
     count_launches(c, 1);
+    if (pass == 0) {
+      sk_zero_cols_kernel<<<256, 256, 0, c->stream>>>(Y, rows, l, b.st);
+      count_launches(c, 1);
+      continue;
+    }
     SK_CUDA(ts_mul_c(c, Y, rows, l, b.st->Rinv, l, l, Y, rows, rows, 1.f, 0.f, c->stream));
   }
   return RPCA_OK;

@@ -134,4 +134,46 @@ __device__ inline int chol_upper_inv(const double* G, int n, double* R, double* 
   return bad;
 }
 
+// Upper Cholesky of the n x n Gram G (column-major) that tolerates collapsed columns: a
+// pivot below `rel` * max diagonal marks column j in *mask and gets R_jj = 1 with no
+// coupling (R_jk = 0), so that an all-zero column j stays zero and leaves the others alone.
+// When ref is non-null the floor of column j is rel * ref[j] (e.g. its squared norm before
+// a projection) instead of rel * max diagonal.
+__device__ inline void chol_upper_inv_masked(const double* G, int n, double rel, double* R, double* Rinv, int* mask,
+                                             const double* ref = nullptr) {
+  double dmax = 0.0;
+  for (int i = 0; i < n; ++i) dmax = fmax(dmax, G[i + i * n]);
+  const double floor_all = fmax(dmax, 1e-300) * rel;
+  int bad = 0;
+  for (int i = 0; i < n * n; ++i) R[i] = 0.0;
+  for (int j = 0; j < n; ++j) {
+    for (int i = 0; i < j; ++i) {
+      if ((bad >> i) & 1) continue;
+      double s = G[i + j * n];
+      for (int p = 0; p < i; ++p) s -= R[p + i * n] * R[p + j * n];
+      R[i + j * n] = s / R[i + i * n];
+    }
+    double s = G[j + j * n];
+    for (int p = 0; p < j; ++p) s -= R[p + j * n] * R[p + j * n];
+    const double floor_ = ref ? fmax(rel * ref[j], 1e-300) : floor_all;
+    if (!(s > floor_)) {
+      bad |= 1 << j;
+      for (int p = 0; p < j; ++p) R[p + j * n] = 0.0;
+      R[j + j * n] = 1.0;
+    } else {
+      R[j + j * n] = sqrt(s);
+    }
+  }
+  for (int i = 0; i < n * n; ++i) Rinv[i] = 0.0;
+  for (int j = 0; j < n; ++j) {
+    Rinv[j + j * n] = 1.0 / R[j + j * n];
+    for (int i = j - 1; i >= 0; --i) {
+      double t = 0.0;
+      for (int p = i + 1; p <= j; ++p) t += R[i + p * n] * Rinv[p + j * n];
+      Rinv[i + j * n] = -t / R[i + i * n];
+    }
+  }
+  *mask = bad;
+}
+
 }  // namespace rpca

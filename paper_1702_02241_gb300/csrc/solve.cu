@@ -46,6 +46,22 @@ void fill_normal(float* out, int64_t count, uint64_t seed, float scale, cudaStre
 
 using namespace rpca;
 
+extern "C" rpca_status rpca_solve_log(rpca_ctx* c, double* out, int max_rows, int* rows) {
+  if (!c || !out || !rows || max_rows < 0) return RPCA_EINVAL;
+  *rows = 0;
+  if (!c->sol) return RPCA_OK;
+  SolverState st;
+  rpca_status s = solver_read_state(c, &st);
+  if (s != RPCA_OK) return s;
+  const int n = std::min(std::min(st.log_n, SOLVER_LOG), max_rows);
+  for (int i = 0; i < n; ++i) {
+    const int idx = (st.log_n - n + i) % SOLVER_LOG;
+    for (int q = 0; q < 7; ++q) out[7 * i + q] = st.log[idx][q];
+  }
+  *rows = n;
+  return RPCA_OK;
+}
+
 extern "C" rpca_status rpca_solve(rpca_ctx* c, float* U, float* V, rpca_result* res) {
   if (!c) return RPCA_EINVAL;
   if (!U || !V) return set_err(c, RPCA_EINVAL, "U and V are required");

@@ -14,7 +14,9 @@
 // combination of s_i.g, y_i.g, s_i.y_j and y_i.y_j, which are kept in a Gram table and
 // updated with one new row and column per accepted pair.  The line search is the
 // bracketing + zoom procedure of Nocedal & Wright Alg. 3.5 / 3.6 with safeguarded cubic
-// interpolation (the paper is silent on the line search; its solvers came from minFunc).
+// interpolation (the paper is silent on the line search; its solvers came from minFunc),
+// with the approximate Wolfe conditions of Hager & Zhang (2005) for steps whose objective
+// change is below the float32 noise level of f.
 //
 // Products are formed in float32 and summed over a few elements per thread in float32;
 // all further sums, the Gram table, the two-loop scalars and the line-search arithmetic
@@ -85,9 +87,27 @@ __global__ void ls_step_kernel(SolverState* st, cudaGraphConditionalHandle h) {
   L.evals += 1;
   st->evals += 1;
   bool accept = false;
-  const bool armijo_fail = !isfinite(fa) || fa > L.f0 + LS_C1 * a * L.g0;
+  // Sufficient decrease: the Armijo test, or -- once the objective differences are at the
+  // noise level of f (|f(a) - f(0)| <= ls_noise |f(0)|) -- the approximate Wolfe test of
+  // Hager & Zhang, phi'(a) <= (2 c1 - 1) phi'(0), which uses the (float64-accumulated)
+  // directional derivative instead of the noisy function difference.
+  const double epsf = st->ls_noise * fabs(L.f0);
+  const bool approx_ok = isfinite(fa) && fa <= L.f0 + epsf && ga <= (2.0 * LS_C1 - 1.0) * L.g0;
+  const double gga = st->out[2];
+  if (L.force) {  // the fallback trial (see below) is taken as it is
+    L.state = LS_ACCEPTED;
+    L.f_acc = fa;
+    st->gate = 0;
+    cudaGraphSetConditional(h, 0u);
+    return;
+  }
+  if (isfinite(fa) && fa <= L.f0 + epsf && isfinite(gga) && gga < L.best_gg) {
+    L.best_gg = gga;
+    L.best_a = a;
+  }
+  const bool armijo_fail = !isfinite(fa) || (fa > L.f0 + LS_C1 * a * L.g0 && !approx_ok);
   if (L.phase == 0) {  // bracketing (Alg. 3.5)
-    if (armijo_fail || (!L.first && fa >= L.f_prev)) {
+    if (armijo_fail || (!L.first && fa > L.f_prev + epsf)) {
       L.lo = L.a_prev; L.flo = L.f_prev; L.glo = L.g_prev;
       L.hi = a; L.fhi = fa; L.ghi = ga;
       L.phase = 1;
@@ -103,7 +123,8 @@ __global__ void ls_step_kernel(SolverState* st, cudaGraphConditionalHandle h) {
       L.first = 0;
     }
   } else {  // zoom (Alg. 3.6)
-    if (armijo_fail || fa >= L.flo) {
+    // phi(a) >= phi(lo) counts only beyond the noise level unless the approximate test fails.
+    if (armijo_fail || fa > L.flo + epsf || (fa >= L.flo && !approx_ok)) {
       L.hi = a; L.fhi = fa; L.ghi = ga;
     } else {
       if (fabs(ga) <= -LS_C2 * L.g0) {
@@ -119,8 +140,16 @@ __global__ void ls_step_kernel(SolverState* st, cudaGraphConditionalHandle h) {
   if (accept) {
     L.state = LS_ACCEPTED;
     L.f_acc = fa;
-  } else if (L.evals >= LS_MAX_TRIALS) {
-    L.state = LS_FAILED;
+  } else if (L.evals >= LS_MAX_TRIALS - 1) {
+    // Out of trials (at the float32 noise floor the curvature test can stay out of reach):
+    // re-evaluate the trial with the smallest gradient among those that did not increase f
+    // beyond the noise level, if it improves on the current point, and accept it.
+    if (L.best_a > 0.0 && L.best_gg < st->gg) {
+      L.a = L.best_a;
+      L.force = 1;
+    } else {
+      L.state = LS_FAILED;
+    }
   } else if (L.phase == 1) {
     L.a = zoom_trial(L);
   }
@@ -170,6 +199,7 @@ template <int NS>
 __device__ void iteration_scalars(SolverState* st, const double* v) {
   const int state = st->ls.state;
   int added = -1;  // slot of the pair added by this step, if any
+  const double step = st->ls.a, trials = st->ls.evals;
   if (state == LS_ACCEPTED) {
     st->f = st->ls.f_acc;
     st->iter += 1;
@@ -221,6 +251,17 @@ __device__ void iteration_scalars(SolverState* st, const double* v) {
   }
   st->gg = v[5 * NS + 5];
   st->g1 = v[5 * NS + 6];
+  if (state != LS_NONE) {
+    double* rec = st->log[st->log_n % SOLVER_LOG];
+    rec[0] = st->iter;
+    rec[1] = st->f;
+    rec[2] = sqrt(st->gg);
+    rec[3] = step;
+    rec[4] = trials;
+    rec[5] = state;
+    rec[6] = st->count;
+    st->log_n += 1;
+  }
   if (!isfinite(st->f) || !isfinite(st->gg)) {
     st->stop = STOP_NONFINITE;
     st->active = 0;
@@ -251,6 +292,9 @@ __device__ void iteration_scalars(SolverState* st, const double* v) {
   L.phase = 0;
   L.first = 1;
   L.evals = 0;
+  L.best_a = 0.0;
+  L.best_gg = INFINITY;
+  L.force = 0;
   L.state = LS_RUNNING;
 }
 
@@ -406,7 +450,7 @@ __global__ void __launch_bounds__(256) lbfgs_direction_kernel(SolverArgs a) {
   }
 }
 
-__global__ void solver_init_kernel(SolverState* st, int mem, int max_iter, double gtol) {
+__global__ void solver_init_kernel(SolverState* st, int mem, int max_iter, double gtol, double ls_noise) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   st->f = st->out[0];
   st->best_f = st->out[0];
@@ -421,7 +465,9 @@ __global__ void solver_init_kernel(SolverState* st, int mem, int max_iter, doubl
   st->gate = 1;
   st->max_iter = max_iter;
   st->gtol = gtol;
+  st->ls_noise = ls_noise;
   st->ls.state = LS_NONE;
+  st->log_n = 0;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -617,7 +663,8 @@ static rpca_status solver_start(rpca_ctx* c) {
   L.out = b->st->out;
   rpca_status s = launch_fg(c, c->fg_plan, L, c->stream);
   if (s != RPCA_OK) return s;
-  solver_init_kernel<<<1, 1, 0, c->stream>>>(b->st, c->opt.lbfgs_mem, c->opt.max_iter, c->opt.gtol);
+  solver_init_kernel<<<1, 1, 0, c->stream>>>(b->st, c->opt.lbfgs_mem, c->opt.max_iter, c->opt.gtol,
+                                              c->opt.ls_noise);
   SOL_CUDA(cudaGetLastError());
   SOL_CUDA(update_and_direction(b->mcap, solver_args(c), b->grid, c->stream));
   count_launches(c, 4);

@@ -5,6 +5,7 @@
 namespace rpca {
 
 constexpr int SOLVER_MAX_SLOTS = 33;  // history slots: memory cap (<= 32) + 1 spare
+constexpr int SOLVER_LOG = 256;       // per-iteration log ring
 
 enum { LS_RUNNING = 0, LS_ACCEPTED = 1, LS_FAILED = 2, LS_NONE = 3 };
 enum { STOP_NONE = 0, STOP_GTOL = 1, STOP_MAXITER = 2, STOP_LSFAIL = 3, STOP_CERT = 4, STOP_TIMEOUT = 5,
@@ -17,6 +18,8 @@ struct LineSearch {
   double lo, flo, glo;            // zoom bracket end with the lower objective
   double hi, fhi, ghi;            // other bracket end
   double f_acc;                   // objective at the accepted step
+  double best_a, best_gg;         // trial with the smallest ||g||^2 among those with f <= f(0) + noise
+  int force;                      // the current trial is the fallback: accept it
   int phase;                      // 0 bracketing, 1 zoom
   int first;                      // first trial of the bracketing phase
   int evals;                      // trials in this line search
@@ -35,6 +38,11 @@ struct SolverState {
   double coef_g, coef_s[SOLVER_MAX_SLOTS], coef_y[SOLVER_MAX_SLOTS];
   int iter, evals, active, gate, stop, fails, max_iter;
   double gtol;
+  double ls_noise;  // relative noise level of f for the approximate Wolfe test
+  // Per-iteration log ring: {iteration, f, ||g||, accepted step, line-search trials,
+  // outcome (LS_*), history pairs in use}, newest at (log_n - 1) % SOLVER_LOG.
+  int log_n;
+  double log[SOLVER_LOG][7];
 };
 
 }  // namespace rpca

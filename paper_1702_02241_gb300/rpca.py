@@ -28,7 +28,7 @@ class rpca_options(C.Structure):
     _fields_ = [("lbfgs_mem", C.c_int), ("max_iter", C.c_int), ("cert_tol", C.c_double),
                 ("cert_every", C.c_int), ("init", C.c_int), ("seed", C.c_uint64), ("x_dtype", C.c_int),
                 ("refine_fp32", C.c_int), ("timeout_s", C.c_double), ("gtol", C.c_double),
-                ("sketch_oversample", C.c_int), ("sketch_power", C.c_int)]
+                ("sketch_oversample", C.c_int), ("sketch_power", C.c_int), ("ls_noise", C.c_double)]
 
 
 class rpca_cert(C.Structure):
@@ -83,6 +83,8 @@ def lib():
     L.rpca_profile.restype = I
     L.rpca_profile_read.argtypes = [P, C.POINTER(C.c_double)]
     L.rpca_profile_read.restype = I
+    L.rpca_solve_log.argtypes = [P, C.POINTER(C.c_double), I, C.POINTER(C.c_int)]
+    L.rpca_solve_log.restype = I
     L.rpca_version.argtypes = []
     L.rpca_version.restype = C.c_char_p
     _lib = L
@@ -91,7 +93,7 @@ def lib():
 
 EXPORTED = ["rpca_default_options", "rpca_create", "rpca_fg", "rpca_apply", "rpca_init_sketch", "rpca_solve",
             "rpca_certificate", "rpca_destroy", "rpca_last_error", "rpca_version", "rpca_plan_info",
-            "rpca_profile", "rpca_profile_read"]
+            "rpca_profile", "rpca_profile_read", "rpca_solve_log"]
 
 
 class RpcaError(RuntimeError):
@@ -170,9 +172,9 @@ def rpca_certificate(ctx, U, V) -> rpca_cert:
 
 
 def rpca_plan_info(ctx, which=0) -> dict:
-    out = (C.c_int64 * 8)()
+    out = (C.c_int64 * 9)()
     _check(lib().rpca_plan_info(ctx, which, out), ctx)
-    keys = ["R", "warps", "row_blocks", "col_splits", "cols_per_cta", "threads", "smem", "ctas_per_sm"]
+    keys = ["R", "warps", "row_blocks", "col_splits", "cols_per_cta", "threads", "smem", "ctas_per_sm", "stages"]
     return dict(zip(keys, list(out)))
 
 
@@ -185,6 +187,14 @@ def rpca_profile_read(ctx) -> dict:
     _check(lib().rpca_profile_read(ctx, out), ctx)
     keys = ["fg_launches", "fg_ms", "finalize_launches", "finalize_ms", "kernel_launches", "graph_launches"]
     return dict(zip(keys, list(out)))
+
+
+def rpca_solve_log(ctx, max_rows=256):
+    """Rows {iteration, F, ||grad||, step, trials, outcome, pairs} of the last solve."""
+    out = (C.c_double * (7 * max_rows))()
+    rows = C.c_int(0)
+    _check(lib().rpca_solve_log(ctx, out, max_rows, C.byref(rows)), ctx)
+    return [list(out[7 * i:7 * i + 7]) for i in range(rows.value)]
 
 
 def rpca_destroy(ctx):
