@@ -197,6 +197,27 @@ RPCA_API rpca_status rpca_profile_read(rpca_ctx *c, double *out);
  */
 RPCA_API rpca_status rpca_solve_log(rpca_ctx *c, double *out, int max_rows, int *rows);
 
+/*
+ * One objective/gradient evaluation, as rpca_fg (same formulas, same kernels), that
+ * allocates nothing: for callers that cannot allocate device memory where they evaluate
+ * (an application that owns all device memory through its own arena, code running while a
+ * CUDA graph is captured, a plugin host).  The paper has no counterpart; this is an
+ * interface of this library.  No context: X (m x n, ldx, 16-byte aligned, ldx a multiple
+ * of 4, fully observed -- no mask), k in [1, 16], lambda_L, lambda_S as in rpca_create; U,
+ * V in; f (HOST pointer, may be NULL), gU, gV out.  The scratch comes from one file-scope
+ * device array of 32 MiB that every GPU loading the library holds until exit; shapes whose
+ * partial sums need more ((ncs m + nrb n) k floats plus a little) are rejected with
+ * RPCA_EINVAL and a message (use rpca_fg).  X is not checked for non-finite values.  The
+ * first call on a device looks up the array's device address (do that first call before
+ * any stream capture).  The call synchronises the stream.  All calls share the array:
+ * calls that overlap on the GPU (other streams, other host threads) race and must be
+ * serialised by the caller.  Errors: rpca_last_error(NULL).  No launch-configuration
+ * timing is done, so it can be slower than rpca_fg.
+ */
+RPCA_API rpca_status rpca_fg_noalloc(int64_t m, int64_t n, const float *X, int64_t ldx, int k, double lambda_L,
+                                     double lambda_S, const float *U, const float *V, double *f, float *gU,
+                                     float *gV, void *cuda_stream);
+
 /* Library version string. */
 RPCA_API const char *rpca_version(void);
 

@@ -18,11 +18,18 @@
 
 namespace rpca {
 
-static thread_local std::string g_create_err;
+// Message of the last failure of a call without a context (a fixed buffer: recording it
+// never allocates).
+static thread_local char g_create_err[512];
 
 rpca_status set_err(rpca_ctx* c, rpca_status s, const std::string& msg) {
   if (c) c->err = msg;
-  else g_create_err = msg;
+  else snprintf(g_create_err, sizeof g_create_err, "%s", msg.c_str());
+  return s;
+}
+
+rpca_status set_err_noctx(rpca_status s, const char* msg) {
+  snprintf(g_create_err, sizeof g_create_err, "%s", msg);
   return s;
 }
 
@@ -95,10 +102,13 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-static rpca_status make_tmap(rpca_ctx* c, CUtensorMap* map, CUtensorMapDataType dt, const void* base, int64_t d0,
-                             int64_t d1, int64_t stride_bytes, int b0, int b1) {
+rpca_status make_tmap(rpca_ctx* c, CUtensorMap* map, CUtensorMapDataType dt, const void* base, int64_t d0,
+                      int64_t d1, int64_t stride_bytes, int b0, int b1) {
   auto fn = encode_fn();
-  if (!fn) return set_err(c, RPCA_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  if (!fn) {
+    const char* msg = "cuTensorMapEncodeTiled is not available from the driver";
+    return c ? set_err(c, RPCA_ECUDA, msg) : set_err_noctx(RPCA_ECUDA, msg);
+  }
   cuuint64_t dims[2] = {(cuuint64_t)d0, (cuuint64_t)d1};
   cuuint64_t strides[1] = {(cuuint64_t)stride_bytes};
   cuuint32_t box[2] = {(cuuint32_t)b0, (cuuint32_t)b1};
@@ -109,14 +119,14 @@ static rpca_status make_tmap(rpca_ctx* c, CUtensorMap* map, CUtensorMapDataType 
     char buf[160];
     snprintf(buf, sizeof buf, "cuTensorMapEncodeTiled failed (%d) for dims %lld x %lld, box %d x %d", (int)r,
              (long long)d0, (long long)d1, b0, b1);
-    return set_err(c, RPCA_ECUDA, buf);
+    return c ? set_err(c, RPCA_ECUDA, buf) : set_err_noctx(RPCA_ECUDA, buf);
   }
   return RPCA_OK;
 }
 
 // Raises a kernel's dynamic shared-memory limit to at least `bytes` (never lowers it, so
 // plans made earlier stay launchable).  False when the device cannot provide that much.
-static bool allow_smem(const void* fn, size_t bytes) {
+bool allow_smem(const void* fn, size_t bytes) {
   static std::mutex mu;
   static const void* fns[64];
   static size_t lim[64];
@@ -559,7 +569,7 @@ rpca_status rpca_plan_info(const rpca_ctx* c, int which, int64_t* out) {
   return RPCA_OK;
 }
 
-const char* rpca_last_error(const rpca_ctx* c) { return c ? c->err.c_str() : g_create_err.c_str(); }
+const char* rpca_last_error(const rpca_ctx* c) { return c ? c->err.c_str() : g_create_err; }
 
 rpca_status rpca_create(rpca_ctx** out, int64_t m, int64_t n, const float* X, int64_t ldx, const uint8_t* mask,
                         int64_t ldmask, int k, double lambda_L, double lambda_S, const rpca_options* opt,
@@ -599,7 +609,7 @@ rpca_status rpca_create(rpca_ctx** out, int64_t m, int64_t n, const float* X, in
   c->stream = static_cast<cudaStream_t>(cuda_stream);
   c->mpad = (int)((m + 3) / 4 * 4);
   auto fail = [&](rpca_status s) {
-    g_create_err = c->err;
+    snprintf(g_create_err, sizeof g_create_err, "%s", c->err.c_str());
     rpca_destroy(c);
     return s;
   };

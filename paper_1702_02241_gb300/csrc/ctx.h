@@ -84,6 +84,10 @@ struct rpca_ctx {
 namespace rpca {
 
 rpca_status set_err(rpca_ctx* c, rpca_status s, const std::string& msg);
+rpca_status set_err_noctx(rpca_status s, const char* msg);  // no allocation
+bool allow_smem(const void* fn, size_t bytes);
+rpca_status make_tmap(rpca_ctx* c, CUtensorMap* map, CUtensorMapDataType dt, const void* base, int64_t d0,
+                      int64_t d1, int64_t stride_bytes, int b0, int b1);
 rpca_status cuda_err(rpca_ctx* c, cudaError_t e, const char* what);
 rpca_status check_dev_err(rpca_ctx* c);
 

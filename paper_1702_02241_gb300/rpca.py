@@ -85,6 +85,8 @@ def lib():
     L.rpca_profile_read.restype = I
     L.rpca_solve_log.argtypes = [P, C.POINTER(C.c_double), I, C.POINTER(C.c_int)]
     L.rpca_solve_log.restype = I
+    L.rpca_fg_noalloc.argtypes = [I64, I64, P, I64, I, D, D, P, P, C.POINTER(C.c_double), P, P, P]
+    L.rpca_fg_noalloc.restype = I
     L.rpca_version.argtypes = []
     L.rpca_version.restype = C.c_char_p
     _lib = L
@@ -93,7 +95,7 @@ def lib():
 
 EXPORTED = ["rpca_default_options", "rpca_create", "rpca_fg", "rpca_apply", "rpca_init_sketch", "rpca_solve",
             "rpca_certificate", "rpca_destroy", "rpca_last_error", "rpca_version", "rpca_plan_info",
-            "rpca_profile", "rpca_profile_read", "rpca_solve_log"]
+            "rpca_profile", "rpca_profile_read", "rpca_solve_log", "rpca_fg_noalloc"]
 
 
 class RpcaError(RuntimeError):
@@ -145,6 +147,15 @@ def rpca_fg(ctx, U, V, gU, gV, want_f=True):
     f = C.c_double(float("nan"))
     st = lib().rpca_fg(ctx, _ptr(U), _ptr(V), C.byref(f) if want_f else None, _ptr(gU), _ptr(gV))
     _check(st, ctx)
+    return f.value
+
+
+def rpca_fg_noalloc(m, n, X, ldx, k, lam_L, lam_S, U, V, gU, gV, stream=None):
+    """Evaluation without a context and without allocation; returns f."""
+    f = C.c_double(float("nan"))
+    st = lib().rpca_fg_noalloc(m, n, _ptr(X), ldx, k, float(lam_L), float(lam_S), _ptr(U), _ptr(V), C.byref(f),
+                               _ptr(gU), _ptr(gV), stream)
+    _check(st, None)
     return f.value
 
 
