@@ -98,6 +98,9 @@ typedef struct {
   double seconds;  /* wall time of rpca_solve */
   rpca_cert cert;  /* certificate at the returned point */
   rpca_status status;
+  double ms_init;  /* device time of the initialisation (sketch or random), CUDA events */
+  double ms_iter;  /* device time of the L-BFGS iterations (graph launches) */
+  double ms_cert;  /* device time of the certificate evaluations */
 } rpca_result;
 
 /* Fills *opt with the defaults named in the comments above. */
@@ -168,13 +171,14 @@ RPCA_API const char *rpca_last_error(const rpca_ctx *c);
 
 /*
  * Launch configuration the planner picked for the fused kernel of this context
- * (which = 0: objective/gradient; 1, 2: the certificate's and the sketch's products).
+ * (which = 0: objective/gradient; 1, 2: the certificate's and the sketch's D Bv products;
+ * those two are planned, and tuned, on first use).
  * out[0..8] = {rows per lane R, consumer warps per CTA, row blocks, column splits,
  * columns per CTA, threads per CTA, dynamic shared memory bytes, CTAs per SM, pipeline
  * stages}.
  * The planner can be overridden with the environment variable RPCA_PLAN="warps,splits".
  */
-RPCA_API rpca_status rpca_plan_info(const rpca_ctx *c, int which, int64_t *out);
+RPCA_API rpca_status rpca_plan_info(rpca_ctx *c, int which, int64_t *out);
 
 /*
  * Instrumentation (tracing).  rpca_profile(c, 1) starts recording: CUDA events bracket every

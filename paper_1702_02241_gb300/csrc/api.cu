@@ -60,7 +60,7 @@ rpca_status check_dev_err(rpca_ctx* c) {
 
 // ---- kernel variant table ----------------------------------------------------------------
 static FgVariant g_same[17][2];
-static FgVariant g_apply[3][2];
+static FgVariant g_apply[3][3][2];
 static std::once_flag g_once;
 
 static void init_tables() {
@@ -73,18 +73,17 @@ static void init_tables() {
   });
 }
 
-const FgVariant* fg_variant(int K, int B, bool same, bool masked) {
+const FgVariant* fg_variant(int K, int B, bool same, bool masked, int side) {
   init_tables();
   if (same) {
-    if (K < 1 || K > 16 || B != K) return nullptr;
+    if (K < 1 || K > 16 || B != K || side != 0) return nullptr;
     return g_same[K][masked ? 1 : 0].fn ? &g_same[K][masked ? 1 : 0] : nullptr;
   }
-  int slot = -1;
-  if (K == 0 && B == 16) slot = 0;
-  if (K == 8 && B == 8) slot = 1;
-  if (K == 16 && B == 8) slot = 2;
+  if (B != 8 || side < 0 || side > 2) return nullptr;
+  const int slot = K == 0 ? 0 : (K == 8 ? 1 : (K == 16 ? 2 : -1));
   if (slot < 0) return nullptr;
-  return &g_apply[slot][masked ? 1 : 0];
+  const FgVariant* v = &g_apply[slot][side][masked ? 1 : 0];
+  return v->fn ? v : nullptr;
 }
 
 // ---- TMA descriptors -----------------------------------------------------------------------
@@ -175,6 +174,7 @@ static bool autotune_enabled() {
 }
 
 static rpca_status size_workspace(rpca_ctx* c, const FgPlan& P);
+static Workspace& plan_ws(rpca_ctx* c, const FgPlan& P);
 
 // Tensor maps for a chosen configuration.
 static rpca_status finish_plan(rpca_ctx* c, FgPlan* q) {
@@ -214,9 +214,10 @@ static rpca_status time_plan(rpca_ctx* c, const FgPlan& q, double* ms) {
   a.ncs = q.ncs;
   a.BN = q.BN;
   a.nstage = q.nstage;
-  a.PU = c->ws.PU;
-  a.PV = c->ws.PV;
-  a.Ppsi = c->ws.Ppsi;
+  Workspace& wsp = plan_ws(c, q);
+  a.PU = wsp.PU;
+  a.PV = wsp.PV;
+  a.Ppsi = wsp.Ppsi;
   a.err = c->ws.err;
   void* args[] = {(void*)&q.tmX, (void*)&q.tmM, (void*)&a};
   cudaEvent_t e0, e1;
@@ -247,11 +248,12 @@ static rpca_status time_plan(rpca_ctx* c, const FgPlan& q, double* ms) {
 // twelve best are then timed on the device and the fastest is kept (cached per shape in
 // this process).  RPCA_PLAN="warps,splits" forces one configuration; RPCA_AUTOTUNE=0 keeps the
 // model's choice without timing.
-static rpca_status make_plan(rpca_ctx* c, FgPlan* P, int K, int B, bool same) {
+static rpca_status make_plan(rpca_ctx* c, FgPlan* P, int K, int B, bool same, int side) {
   const bool masked = c->bits != nullptr;
-  const FgVariant* v = fg_variant(K, B, same, masked);
+  const FgVariant* v = fg_variant(K, B, same, masked, side);
   if (!v) return set_err(c, RPCA_EUNSUPPORTED, "no compiled kernel for this factor rank");
-  const int KV = same ? K : K + B;
+  const int KV = (same || side == 2) ? K : K + B;
+  const int CSB = side == 1 ? 0 : B;
   double best = 1e300;
   std::vector<std::pair<double, FgPlan>> cands;
   int force_wc = 0, force_ncs = 0, n_smem = 0, n_attr = 0, n_occ = 0, n_try = 0;
@@ -271,7 +273,7 @@ static rpca_status make_plan(rpca_ctx* c, FgPlan* P, int K, int B, bool same) {
       if (ncs == last_ncs) continue;
       if (force_ncs && ncs != force_ncs) continue;
       last_ncs = ncs;
-      const FgSmem L = fg_smem_layout(WC, v->R, masked, BN, KV, B, nst);
+      const FgSmem L = fg_smem_layout(WC, v->R, masked, BN, KV, CSB, nst);
       ++n_try;
       if (L.total > c->max_smem) {
         ++n_smem;
@@ -304,6 +306,7 @@ static rpca_status make_plan(rpca_ctx* c, FgPlan* P, int K, int B, bool same) {
       cand.K = K;
       cand.B = B;
       cand.same = same;
+      cand.side = side;
       cand.masked = masked;
       cand.R = v->R;
       cand.WC = WC;
@@ -330,14 +333,14 @@ static rpca_status make_plan(rpca_ctx* c, FgPlan* P, int K, int B, bool same) {
             [](const std::pair<double, FgPlan>& a, const std::pair<double, FgPlan>& b) { return a.first < b.first; });
   for (auto& cp : cands) {
     FgPlan& q = cp.second;
-    // Finalize grid: one m x B element per thread and one n x B element per warp (so every
-    // load is in flight at once), capped at a few dozen waves.
-    q.fin_gu = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)c->m * B + 255) / 256, 64LL * c->nsm));
-    q.fin_gv = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)c->n * B + 7) / 8, 16LL * c->nsm));
+    // Finalize grid: about two waves of blocks for the m x B side (four elements in flight
+    // per thread per pass), one wave of warps (one element each) for the n x B side.
+    q.fin_gu = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)c->m * B + 1023) / 1024, 2LL * c->nsm));
+    q.fin_gv = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)c->n * B + 7) / 8, (int64_t)c->nsm));
     q.fin_grid = q.fin_gu + q.fin_gv;
   }
   // Cached choice for this shape, or measure the best few candidates of the model.
-  const PlanKey key{c->device, c->m, c->n, c->ldx, K, B, same, masked};
+  const PlanKey key{c->device, c->m, c->n, c->ldx, K, B * 4 + side, same, masked};
   int pick = 0;
   int cached_wc = 0, cached_ncs = 0;
   const bool measure = !(force_wc || force_ncs) && autotune_enabled() && cands.size() > 1;
@@ -346,7 +349,7 @@ static rpca_status make_plan(rpca_ctx* c, FgPlan* P, int K, int B, bool same) {
       if (cands[i].second.WC * 16 + cands[i].second.nstage == cached_wc && cands[i].second.ncs == cached_ncs)
         pick = (int)i;
   } else if (measure) {
-    const int ntry = (int)std::min<size_t>(12, cands.size());
+    const int ntry = (int)std::min<size_t>(same ? 12 : 6, cands.size());
     double best_ms = 1e300;
     for (int i = 0; i < ntry; ++i) {
       FgPlan& q = cands[i].second;
@@ -380,22 +383,27 @@ static rpca_status ensure(rpca_ctx* c, T** p, size_t* have, size_t need) {
   return RPCA_OK;
 }
 
+// Partial-sum buffers: the objective/gradient plan (whose buffers CUDA graphs capture) and
+// the apply plans (created on first use) have separate ones, so that a new apply plan never
+// moves a captured buffer.
+static Workspace& plan_ws(rpca_ctx* c, const FgPlan& P) { return P.same ? c->ws : c->ws_ap; }
+
 static rpca_status size_workspace(rpca_ctx* c, const FgPlan& P) {
   rpca_status s;
-  if ((s = ensure(c, &c->ws.PU, &c->ws.PU_n, (size_t)P.ncs * P.B * c->mpad)) != RPCA_OK) return s;
-  if ((s = ensure(c, &c->ws.PV, &c->ws.PV_n, (size_t)P.nrb * P.B * c->n)) != RPCA_OK) return s;
-  if ((s = ensure(c, &c->ws.Ppsi, &c->ws.Ppsi_n, (size_t)P.nrb * P.ncs)) != RPCA_OK) return s;
-  if ((s = ensure(c, &c->ws.blk, &c->ws.blk_n, (size_t)3 * P.fin_grid)) != RPCA_OK) return s;
+  Workspace& w = plan_ws(c, P);
+  if ((s = ensure(c, &w.PU, &w.PU_n, (size_t)P.ncs * P.B * c->mpad)) != RPCA_OK) return s;
+  if ((s = ensure(c, &w.PV, &w.PV_n, (size_t)P.nrb * P.B * c->n)) != RPCA_OK) return s;
+  if ((s = ensure(c, &w.Ppsi, &w.Ppsi_n, (size_t)P.nrb * P.ncs)) != RPCA_OK) return s;
+  if ((s = ensure(c, &w.blk, &w.blk_n, (size_t)3 * P.fin_grid)) != RPCA_OK) return s;
   return RPCA_OK;
 }
 
-const FgPlan* apply_plan(rpca_ctx* c, int K) {
-  int slot = K == 0 ? 0 : (K <= 8 ? 1 : 2);
-  FgPlan* P = &c->ap_plan[slot];
+const FgPlan* apply_plan(rpca_ctx* c, int K, int side) {
+  const int slot = K == 0 ? 0 : (K <= 8 ? 1 : 2);
+  FgPlan* P = &c->ap_plan[slot][side];
   if (!P->valid) {
     const int KK = slot == 0 ? 0 : (slot == 1 ? 8 : 16);
-    const int BB = slot == 0 ? 16 : 8;
-    if (make_plan(c, P, KK, BB, false) != RPCA_OK) return nullptr;
+    if (make_plan(c, P, KK, 8, false, side) != RPCA_OK) return nullptr;
     if (size_workspace(c, *P) != RPCA_OK) return nullptr;
   }
   return P;
@@ -421,9 +429,10 @@ rpca_status launch_fg(rpca_ctx* c, const FgPlan& P, const FgLaunch& L, cudaStrea
   a.ncs = P.ncs;
   a.BN = P.BN;
   a.nstage = P.nstage;
-  a.PU = c->ws.PU;
-  a.PV = c->ws.PV;
-  a.Ppsi = c->ws.Ppsi;
+  Workspace& w = plan_ws(c, P);
+  a.PU = w.PU;
+  a.PV = w.PV;
+  a.Ppsi = w.Ppsi;
   a.err = c->ws.err;
   void* args[] = {(void*)&P.tmX, (void*)&P.tmM, (void*)&a};
   // Event pairs bracket the two launches while profiling (never inside a graph capture).
@@ -443,7 +452,7 @@ rpca_status launch_fg(rpca_ctx* c, const FgPlan& P, const FgLaunch& L, cudaStrea
   }
   RPCA_CUDA(c, cudaLaunchKernel(P.var->fn, dim3(P.nrb * P.ncs), dim3(P.threads), args, P.smem, stream));
   if (timed) RPCA_CUDA(c, cudaEventRecord(ev[1], stream));
-  count_launches(c, 2);
+  count_launches(c, L.fin_mode != FIN_APPLY ? 3 : 2);
   FinArgs f;
   f.m = c->m;
   f.n = c->n;
@@ -453,10 +462,11 @@ rpca_status launch_fg(rpca_ctx* c, const FgPlan& P, const FgLaunch& L, cudaStrea
   f.ncs = P.ncs;
   f.nctas = P.nrb * P.ncs;
   f.gu = P.fin_gu;
-  f.PU = c->ws.PU;
-  f.PV = c->ws.PV;
-  f.Ppsi = c->ws.Ppsi;
+  f.PU = w.PU;
+  f.PV = w.PV;
+  f.Ppsi = w.Ppsi;
   f.mode = L.fin_mode;
+  f.side = P.side;
   f.U = L.U;
   f.V = L.V;
   f.dU = L.dU;
@@ -471,11 +481,12 @@ rpca_status launch_fg(rpca_ctx* c, const FgPlan& P, const FgLaunch& L, cudaStrea
   f.Vt = L.Vt;
   f.DU = L.DU;
   f.DV = L.DV;
-  f.blk = c->ws.blk;
+  f.blk = w.blk;
   f.counter = c->ws.counter;
   f.out = L.out ? L.out : c->ws.out;
   if (timed) RPCA_CUDA(c, cudaEventRecord(ev[2], stream));
   finalize_kernel<<<P.fin_grid, 256, 0, stream>>>(f);
+  if (L.fin_mode != FIN_APPLY) finalize_reduce_kernel<<<1, 256, 0, stream>>>(f, P.fin_grid);
   RPCA_CUDA(c, cudaGetLastError());
   if (timed) {
     RPCA_CUDA(c, cudaEventRecord(ev[3], stream));
@@ -560,10 +571,11 @@ rpca_status rpca_profile_read(rpca_ctx* c, double* out) {
   return RPCA_OK;
 }
 
-rpca_status rpca_plan_info(const rpca_ctx* c, int which, int64_t* out) {
+rpca_status rpca_plan_info(rpca_ctx* c, int which, int64_t* out) {
   if (!c || !out || which < 0 || which > 2) return RPCA_EINVAL;
-  const FgPlan& P = which == 0 ? c->fg_plan : c->ap_plan[which == 1 ? (c->k <= 8 ? 1 : 2) : 0];
-  if (!P.valid) return RPCA_EINVAL;
+  const FgPlan* Pp = which == 0 ? &c->fg_plan : apply_plan(c, which == 1 ? c->k : 0, 1);
+  if (!Pp || !Pp->valid) return RPCA_EINVAL;
+  const FgPlan& P = *Pp;
   const int64_t v[9] = {P.R, P.WC, P.nrb, P.ncs, P.BN, P.threads, (int64_t)P.smem, P.cps, P.nstage};
   for (int i = 0; i < 9; ++i) out[i] = v[i];
   return RPCA_OK;
@@ -653,12 +665,9 @@ rpca_status rpca_create(rpca_ctx** out, int64_t m, int64_t n, const float* X, in
                                                                                 c->bits);
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(cuda_err(c, e, "pack_mask_kernel"));
   }
-  rpca_status s = make_plan(c, &c->fg_plan, k, k, true);
+  rpca_status s = make_plan(c, &c->fg_plan, k, k, true, 0);
   if (s != RPCA_OK) return fail(s);
   if ((s = size_workspace(c, c->fg_plan)) != RPCA_OK) return fail(s);
-  // Plans (and workspace sizes) of the apply kernels the certificate and the sketch use are
-  // fixed here, so that buffers captured in CUDA graphs never move afterwards.
-  if (!apply_plan(c, k) || !apply_plan(c, 0)) return fail(c->err.empty() ? RPCA_EUNSUPPORTED : RPCA_ECUDA);
   if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return fail(cuda_err(c, e, "rpca_create"));
   c->F_best = INFINITY;
   c->F0 = NAN;
@@ -690,7 +699,7 @@ rpca_status rpca_apply(rpca_ctx* c, const float* U, const float* V, int b, const
   if (!c) return RPCA_EINVAL;
   if (!U || !V || !Bv || !Bu || !DBv || !DtBu) return set_err(c, RPCA_EINVAL, "null argument");
   if (b < 1 || b > 8) return set_err(c, RPCA_EINVAL, "b must be in [1, 8]");
-  const FgPlan* P = apply_plan(c, c->k);
+  const FgPlan* P = apply_plan(c, c->k, 0);
   if (!P) return RPCA_EUNSUPPORTED;
   // The kernel reads P->K columns of U, V and 8 of Bu, Bv: pass zero-padded copies.
   const int Kp = P->K;
@@ -737,6 +746,10 @@ void rpca_destroy(rpca_ctx* c) {
   cudaFree(c->ws.PV);
   cudaFree(c->ws.Ppsi);
   cudaFree(c->ws.blk);
+  cudaFree(c->ws_ap.PU);
+  cudaFree(c->ws_ap.PV);
+  cudaFree(c->ws_ap.Ppsi);
+  cudaFree(c->ws_ap.blk);
   cudaFree(c->ws.counter);
   cudaFree(c->ws.out);
   cudaFree(c->ws.err);

@@ -47,8 +47,8 @@ struct CertState {
   double sig[CERT_KMAX];
   int r;
   double t1, t2, t3, t4, normL, sigma1;
-  double G[LZ_TMAX * LZ_B];    // Gram scratch (p x q)
-  double G2[LZ_TMAX * LZ_B];
+  double G[(CERT_KMAX + LZ_TMAX) * LZ_B];    // Gram scratch (p x q)
+  double G2[(CERT_KMAX + LZ_TMAX) * LZ_B];
   double R[LZ_B * LZ_B], Rinv[LZ_B * LZ_B];
   int bad_mask;  // columns whose Cholesky pivot collapsed in the last block QR
   double n0[LZ_B];  // squared column norms before the last projection
@@ -351,7 +351,10 @@ __global__ void __launch_bounds__(1024) cert_ritz_kernel(CertState* st, const do
     // two blocks of the Krylov space to spare (otherwise more of them may be missing).
     const bool settled = st->s1_prev >= 0.0 && fabs(s1 - st->s1_prev) <= 1e-5 * s1 &&
                          fabs(t4 - st->t4_prev) <= 1e-4 * t4 + 1e-12 * lam_L * lam_L && above + 2 * LZ_B <= d;
-    st->converged = settled || final_step;
+    // When the leading Ritz value has settled (to 1e-3) at half of lam_L or less, no singular
+    // value of the projected residual reaches lam_L: t4 = 0.
+    const bool clear = st->s1_prev >= 0.0 && fabs(s1 - st->s1_prev) <= 1e-3 * s1 && s1 <= 0.5 * lam_L;
+    st->converged = settled || clear || final_step;
     st->t4_prev = t4;
     st->s1_prev = s1;
     st->t4 = t4;
@@ -397,21 +400,19 @@ static rpca_status ensure_cert(rpca_ctx* c) {
   const int64_t m = c->m, n = c->n, k = c->k;
   b->Kp = k <= 8 ? 8 : 16;
   const int zc = std::max<int>(LZ_B, (int)k);
-  const int64_t nf = m * k + n * k + m * CERT_KMAX + n * CERT_KMAX + m * LZ_TMAX + n * (LZ_TMAX + LZ_B) + m * LZ_B +
+  const int64_t nf = m * k + n * k + m * (CERT_KMAX + LZ_TMAX) + n * (CERT_KMAX + LZ_TMAX + LZ_B) + m * LZ_B +
                      n * LZ_B + m * b->Kp + n * b->Kp + m * zc + n * zc + m * LZ_B + 2 * LZ_TMAX * LZ_TMAX;
   CERT_CUDA(cudaMalloc(&b->DV, sizeof(float) * nf));
   float* p = b->DV;
   p += m * k;
   b->DtU = p;
   p += n * k;
-  b->U1 = p;
-  p += m * CERT_KMAX;
-  b->V1 = p;
-  p += n * CERT_KMAX;
-  b->P = p;
-  p += m * LZ_TMAX;
-  b->Q = p;
-  p += n * (LZ_TMAX + LZ_B);
+  // [U1 | P_0 | P_1 | ...] and [V1 | Q_0 | Q_1 | ...] are contiguous: U1 (r columns) sits
+  // right before P_0, so one projection covers both bases.
+  b->P = p + m * CERT_KMAX;
+  p += m * (CERT_KMAX + LZ_TMAX);
+  b->Q = p + n * CERT_KMAX;
+  p += n * (CERT_KMAX + LZ_TMAX + LZ_B);
   b->W = p;
   p += m * LZ_B;
   b->Z = p;
@@ -438,7 +439,7 @@ static rpca_status ensure_cert(rpca_ctx* c) {
   CERT_CUDA(cudaMalloc(&b->counter, 64));
   CERT_CUDA(cudaMemsetAsync(b->counter, 0, 64, c->stream));
   b->ts.grid = 2 * c->nsm;
-  b->ts.part_n = (size_t)b->ts.grid * 2048;
+  b->ts.part_n = (size_t)b->ts.grid * 2304;
   CERT_CUDA(cudaMalloc(&b->ts.part, sizeof(double) * b->ts.part_n));
   CERT_CUDA(cudaMalloc(&b->ts.counter, 64));
   CERT_CUDA(cudaMemsetAsync(b->ts.counter, 0, 64, c->stream));
@@ -473,12 +474,11 @@ static rpca_status record_norms(rpca_ctx* c, float* Y, int64_t rows) {
   return RPCA_OK;
 }
 
-static rpca_status project_all(rpca_ctx* c, float* Y, int64_t rows, const float* F, int f, const float* Bm, int p) {
+// Two passes of classical Gram-Schmidt against the basis B (rows x p, orthonormal columns).
+static rpca_status project_twice(rpca_ctx* c, float* Y, int64_t rows, const float* Bm, int p) {
   rpca_status s;
-  for (int pass = 0; pass < 2; ++pass) {
-    if ((s = project_out(c, F, f, Y, rows)) != RPCA_OK) return s;
+  for (int pass = 0; pass < 2; ++pass)
     if ((s = project_out(c, Bm, p, Y, rows)) != RPCA_OK) return s;
-  }
   return RPCA_OK;
 }
 
@@ -489,36 +489,36 @@ static rpca_status normalise(rpca_ctx* c, float* Y, int64_t rows) {
   return RPCA_OK;
 }
 
-// Orthonormalises the block Y (rows x 8) against the fixed basis F (rows x f) and the
-// Krylov basis B (rows x p), on the stream with no host synchronisation.  A column that
-// loses all but 1e-3 of its norm to the projections and to the earlier columns of its block
-// is treated as collapsed (in float32 its remainder is mostly rounding along F and B, which
-// normalising would amplify): it is replaced by a random column, projected again, and
-// zeroed if it collapses again (the complement of F and B is exhausted).  After the first
-// normalisation the block is projected once more, then normalised again.
-static rpca_status orth_block(rpca_ctx* c, float* Y, int64_t rows, const float* F, int f, const float* Bm, int p,
-                              uint64_t seed) {
+// Orthonormalises the block Y (rows x 8) against the basis B (rows x p; the fixed range
+// basis followed by the Krylov blocks, contiguous), on the stream with no host
+// synchronisation.  A column that loses all but 1e-3 of its norm to the projection and to
+// the earlier columns of its block is treated as collapsed (in float32 its remainder is
+// mostly rounding along B, which normalising would amplify) and replaced by a random
+// column, projected again, and zeroed if it collapses once more (the complement of B is
+// exhausted).  Then: normalise, project again, normalise again; zero columns stay zero.
+static rpca_status orth_block(rpca_ctx* c, float* Y, int64_t rows, const float* Bm, int p, uint64_t seed) {
   rpca_status s;
   CertBuffers* b = c->cert;
   const double collapse = 1e-6;  // squared-norm ratio
   if ((s = record_norms(c, Y, rows)) != RPCA_OK) return s;
-  if ((s = project_all(c, Y, rows, F, f, Bm, p)) != RPCA_OK) return s;
+  if ((s = project_twice(c, Y, rows, Bm, p)) != RPCA_OK) return s;
   if ((s = gram_chol(c, Y, rows, collapse, 1)) != RPCA_OK) return s;
   cert_refill_kernel<<<256, 256, 0, c->stream>>>(Y, rows, b->st, seed);
   count_launches(c, 1);
   if ((s = record_norms(c, Y, rows)) != RPCA_OK) return s;
-  if ((s = project_all(c, Y, rows, F, f, Bm, p)) != RPCA_OK) return s;
+  if ((s = project_twice(c, Y, rows, Bm, p)) != RPCA_OK) return s;
   if ((s = gram_chol(c, Y, rows, collapse, 1)) != RPCA_OK) return s;
   cert_zero_cols_kernel<<<256, 256, 0, c->stream>>>(Y, rows, b->st);
   count_launches(c, 1);
   if ((s = normalise(c, Y, rows)) != RPCA_OK) return s;
-  if ((s = project_all(c, Y, rows, F, f, Bm, p)) != RPCA_OK) return s;
+  if ((s = project_twice(c, Y, rows, Bm, p)) != RPCA_OK) return s;
   return normalise(c, Y, rows);
 }
 
-static rpca_status apply_D(rpca_ctx* c, const float* BV, const float* BU, float* Y1, float* Y2) {
+// side 1: Y1 = D BV;  side 2: Y2 = D^T BU  (one pass over X each).
+static rpca_status apply_D(rpca_ctx* c, int side, const float* BV, const float* BU, float* Y1, float* Y2) {
   CertBuffers* b = c->cert;
-  const FgPlan* P = apply_plan(c, c->k);
+  const FgPlan* P = apply_plan(c, c->k, side);
   if (!P) return RPCA_EUNSUPPORTED;
   FgLaunch L;
   L.U = b->Up;
@@ -593,8 +593,12 @@ rpca_status cert_compute(rpca_ctx* c, const float* U, const float* V, rpca_cert*
   int steps = 0;
   if (full) {
     // 5. t4 by block Golub-Kahan-Lanczos on A = P_U1perp D P_V1perp.
-    CERT_CUDA(ts_mul_c(c, U, m, k, st->TU, CERT_KMAX, std::max(r, 1), b->U1, m, m, 1.f, 0.f, c->stream));
-    CERT_CUDA(ts_mul_c(c, V, n, k, st->TV, CERT_KMAX, std::max(r, 1), b->V1, n, n, 1.f, 0.f, c->stream));
+    b->U1 = b->P - m * r;
+    b->V1 = b->Q - n * r;
+    if (r > 0) {
+      CERT_CUDA(ts_mul_c(c, U, m, k, st->TU, CERT_KMAX, r, b->U1, m, m, 1.f, 0.f, c->stream));
+      CERT_CUDA(ts_mul_c(c, V, n, k, st->TV, CERT_KMAX, r, b->V1, n, n, 1.f, 0.f, c->stream));
+    }
     pad_copy_kernel<<<256, 256, 0, c->stream>>>(U, m, k, b->Up, b->Kp);
     count_launches(c, 1);
     pad_copy_kernel<<<256, 256, 0, c->stream>>>(V, n, k, b->Vp, b->Kp);
@@ -603,7 +607,7 @@ rpca_status cert_compute(rpca_ctx* c, const float* U, const float* V, rpca_cert*
     count_launches(c, 1);
     fill_normal(b->Q, n * LZ_B, 0x5eedULL + (uint64_t)c->opt.seed, 1.f, c->stream);
     count_launches(c, 1);
-    if ((s = orth_block(c, b->Q, n, b->V1, r, nullptr, 0, 11)) != RPCA_OK) return s;
+    if ((s = orth_block(c, b->Q, n, b->V1, r, 11)) != RPCA_OK) return s;
     // Krylov dimension cap: 256, or the dimension of the complement of range(V1).
     const int64_t room = std::max<int64_t>(1, std::min(m, n) - r);
     const int smax = (int)std::min<int64_t>(LZ_SMAX, (room + LZ_B - 1) / LZ_B);
@@ -611,18 +615,17 @@ rpca_status cert_compute(rpca_ctx* c, const float* U, const float* V, rpca_cert*
       float* Qj = b->Q + (int64_t)j * LZ_B * n;
       float* Pj = b->P + (int64_t)j * LZ_B * m;
       // A Q_j = P_U1perp D Q_j  (Q_j is orthogonal to V1 by construction).
-      if ((s = apply_D(c, Qj, b->zm, b->Wraw, b->Z)) != RPCA_OK) return s;
-      if ((s = project_out(c, b->U1, r, b->Wraw, m)) != RPCA_OK) return s;
-      if ((s = project_out(c, b->U1, r, b->Wraw, m)) != RPCA_OK) return s;
+      if ((s = apply_D(c, 1, Qj, b->zm, b->Wraw, b->Z)) != RPCA_OK) return s;
+      if ((s = project_twice(c, b->Wraw, m, b->U1, r)) != RPCA_OK) return s;
       CERT_CUDA(cudaMemcpyAsync(Pj, b->Wraw, sizeof(float) * m * LZ_B, cudaMemcpyDeviceToDevice, c->stream));
-      if ((s = orth_block(c, Pj, m, b->U1, r, b->P, j * LZ_B, 1000 + 2 * j)) != RPCA_OK) return s;
+      if ((s = orth_block(c, Pj, m, b->U1, r + j * LZ_B, 1000 + 2 * j)) != RPCA_OK) return s;
       // Column block j of T = P^T A Q.
       CERT_CUDA(ts_gram_c(c, b->P, m, (j + 1) * LZ_B, b->Wraw, m, LZ_B, m, st->G, b->ts, c->stream));
       cert_store_T_kernel<<<1, 256, 0, c->stream>>>(st, b->T, (j + 1) * LZ_B, j * LZ_B);
       count_launches(c, 1);
       steps = j + 1;
       const bool last = (j == smax - 1);
-      if (steps == 2 || (steps % 4) == 0 || last) {
+      if (steps == 2 || steps == 3 || steps == 4 || steps == 6 || (steps % 4) == 0 || last) {
         cert_ritz_kernel<<<1, 1024, 0, c->stream>>>(st, b->T, b->Tw, b->Tv, steps * LZ_B, c->lam_L, last ? 1 : 0);
         count_launches(c, 1);
         CERT_CUDA(cudaGetLastError());
@@ -633,8 +636,8 @@ rpca_status cert_compute(rpca_ctx* c, const float* U, const float* V, rpca_cert*
       }
       // Q_{j+1} from A^T P_j = P_V1perp D^T P_j, orthogonal to V1 and Q_0..Q_j.
       float* Qn = b->Q + (int64_t)(j + 1) * LZ_B * n;
-      if ((s = apply_D(c, b->zn, Pj, b->W, Qn)) != RPCA_OK) return s;
-      if ((s = orth_block(c, Qn, n, b->V1, r, b->Q, (j + 1) * LZ_B, 1001 + 2 * j)) != RPCA_OK) return s;
+      if ((s = apply_D(c, 2, b->zn, Pj, b->W, Qn)) != RPCA_OK) return s;
+      if ((s = orth_block(c, Qn, n, b->V1, r + (j + 1) * LZ_B, 1001 + 2 * j)) != RPCA_OK) return s;
     }
   }
   CERT_CUDA(cudaMemcpyAsync(b->host, st, sizeof(CertState), cudaMemcpyDeviceToHost, c->stream));

@@ -19,6 +19,7 @@ struct FgPlan {
   const FgVariant* var = nullptr;
   int K = 0, B = 0;
   bool same = true, masked = false;
+  int side = 0;  // apply mode: 0 both products, 1 D Bv only, 2 D^T Bu only
   int R = 0, WC = 0, nrb = 0, ncs = 0, BN = 0;
   int threads = 0;
   size_t smem = 0;
@@ -66,8 +67,9 @@ struct rpca_ctx {
   double F0 = 0.0;           // F(0) = phi(0), for the distance bound
   double F_best = 0.0;       // best objective seen on this context
   rpca::FgPlan fg_plan;      // K = k, fg mode
-  rpca::FgPlan ap_plan[3];   // apply modes: (0,16), (8,8), (16,8)
-  rpca::Workspace ws;
+  rpca::FgPlan ap_plan[3][3];  // apply modes: forming rank 0 / 8 / 16 x side
+  rpca::Workspace ws;          // partial sums of the objective/gradient plan (graph-captured)
+  rpca::Workspace ws_ap;       // partial sums of the apply plans
   rpca::SolverBuffers* sol = nullptr;
   rpca::CertBuffers* cert = nullptr;
   std::string err;
@@ -114,7 +116,7 @@ struct FgLaunch {
   double lam = -1.0;  // clip threshold override (< 0: the context's lam_S; +inf allowed)
 };
 rpca_status launch_fg(rpca_ctx* c, const FgPlan& P, const FgLaunch& L, cudaStream_t stream);
-const FgPlan* apply_plan(rpca_ctx* c, int K);  // plan for forming rank >= K (0, 8 or 16)
+const FgPlan* apply_plan(rpca_ctx* c, int K, int side);  // forming rank >= K (0, 8 or 16), side
 inline void count_launches(rpca_ctx* c, int64_t n) { c->launches += n; }
 
 }  // namespace rpca

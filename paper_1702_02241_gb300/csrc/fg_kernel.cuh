@@ -79,15 +79,18 @@ __host__ __device__ inline FgSmem fg_smem_layout(int WC, int R, bool masked, int
   return L;
 }
 
-template <int K, int B, bool SAME, int R, int J>
+// SIDE (apply mode): 0 both products, 1 only D Bv (row side), 2 only D^T Bu (column side).
+template <int K, int B, bool SAME, int R, int J, int SIDE = 0>
 struct FgTraits {
   static constexpr int NP = R / 2;       // float2 pairs of rows per lane
   static constexpr int ROWS_W = 32 * R;  // rows per warp
-  static constexpr int KV = SAME ? K : K + B;
+  static constexpr int KV = (SAME || SIDE == 2) ? K : K + B;
+  static constexpr int CSB = SIDE == 1 ? 0 : B;  // column sums per column kept in the slabs
   static constexpr int JB = J * B;
   static_assert(R == 2 || R == 4 || R == 8, "rows per lane");
   static_assert(FG_BJ % J == 0, "group size");
   static_assert(!SAME || K == B, "fg mode multiplies D by the forming factors");
+  static_assert(!SAME || SIDE == 0, "fg mode needs both products");
 };
 
 // Row of pair p, element e (0/1) for this lane, relative to the warp's first row.
@@ -114,11 +117,12 @@ RPCA_DEV void lane_bit(int p, int e, int lane, int& word, int& bit) {
   }
 }
 
-template <int K, int B, bool SAME, bool MASKED, int R, int J>
+template <int K, int B, bool SAME, bool MASKED, int R, int J, int SIDE = 0>
 __global__ void __launch_bounds__(288) fg_kernel(const __grid_constant__ CUtensorMap tmX,
                                                  const __grid_constant__ CUtensorMap tmM, FgArgs a) {
-  using T = FgTraits<K, B, SAME, R, J>;
+  using T = FgTraits<K, B, SAME, R, J, SIDE>;
   constexpr int NP = T::NP, ROWS_W = T::ROWS_W, KV = T::KV, JB = T::JB;
+  constexpr bool ROWSIDE = SIDE != 2, COLSIDE = SIDE != 1;  // which products are formed
   if (a.gate != nullptr && *a.gate == 0) return;  // uniform over the grid
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -131,7 +135,7 @@ __global__ void __launch_bounds__(288) fg_kernel(const __grid_constant__ CUtenso
   const int ncols = min(a.BN, a.n - col0);
   const int nchunks = (ncols + FG_BJ - 1) / FG_BJ;
   const int nst = a.nstage;
-  const FgSmem L = fg_smem_layout(WC, R, MASKED, a.BN, KV, B, nst);
+  const FgSmem L = fg_smem_layout(WC, R, MASKED, a.BN, KV, T::CSB, nst);
   float* xs_all = reinterpret_cast<float*>(sm + L.x_off);
   uint32_t* ms_all = reinterpret_cast<uint32_t*>(sm + L.m_off);
   float2* vsl = reinterpret_cast<float2*>(sm + L.v_off);
@@ -211,7 +215,7 @@ __global__ void __launch_bounds__(288) fg_kernel(const __grid_constant__ CUtenso
   // This lane's rows of the forming factor (negated, so that r' = x - u.v = -r) and,
   // in apply mode, of Bu (negated too, which makes D^T Bu come out with its own sign).
   float2 un[NP][K > 0 ? K : 1];
-  float2 bun[NP][SAME ? 1 : B];
+  float2 bun[NP][(SAME || !COLSIDE) ? 1 : B];
 #pragma unroll
   for (int p = 0; p < NP; ++p) {
     const int i0 = wrow0 + lane_row<R>(p, 0, lane), i1 = i0 + 1;
@@ -229,7 +233,7 @@ __global__ void __launch_bounds__(288) fg_kernel(const __grid_constant__ CUtenso
       }
       un[p][l] = f2(-u0, -u1);
     }
-    if constexpr (!SAME) {
+    if constexpr (!SAME && COLSIDE) {
 #pragma unroll
       for (int b = 0; b < B; ++b) {
         const size_t o = (size_t)b * a.m;
@@ -241,11 +245,11 @@ __global__ void __launch_bounds__(288) fg_kernel(const __grid_constant__ CUtenso
   }
   named_bar(1, nct);
 
-  float2 gu[NP][B];
+  float2 gu[NP][ROWSIDE ? B : 1];
 #pragma unroll
   for (int p = 0; p < NP; ++p)
 #pragma unroll
-    for (int b = 0; b < B; ++b) gu[p][b] = f2(0.f, 0.f);
+    for (int b = 0; b < (ROWSIDE ? B : 1); ++b) gu[p][b] = f2(0.f, 0.f);
   double psi_d = 0.0;
   const float lam = a.lam_S;
   const float2 mhalf = f2(-0.5f, -0.5f);
@@ -262,11 +266,11 @@ __global__ void __launch_bounds__(288) fg_kernel(const __grid_constant__ CUtenso
     float2 psi2 = f2(0.f, 0.f);
 #pragma unroll 1
     for (int g = 0; g < FG_BJ / J; ++g) {
-      float2 gv[J][B];
+      float2 gv[J][COLSIDE ? B : 1];
 #pragma unroll
       for (int jj = 0; jj < J; ++jj)
 #pragma unroll
-        for (int b = 0; b < B; ++b) gv[jj][b] = f2(0.f, 0.f);
+        for (int b = 0; b < (COLSIDE ? B : 1); ++b) gv[jj][b] = f2(0.f, 0.f);
 #pragma unroll
       for (int jj = 0; jj < J; ++jj) {
         const int cc = g * J + jj;           // column within the stage
@@ -275,8 +279,8 @@ __global__ void __launch_bounds__(288) fg_kernel(const __grid_constant__ CUtenso
         float2 vv[K > 0 ? K : 1];
 #pragma unroll
         for (int l = 0; l < K; ++l) vv[l] = vrow[l];
-        float2 bvv[SAME ? 1 : B];
-        if constexpr (!SAME) {
+        float2 bvv[(SAME || !ROWSIDE) ? 1 : B];
+        if constexpr (!SAME && ROWSIDE) {
 #pragma unroll
           for (int b = 0; b < B; ++b) bvv[b] = vrow[K + b];
         }
@@ -320,21 +324,26 @@ __global__ void __launch_bounds__(288) fg_kernel(const __grid_constant__ CUtenso
             (void)w1;
           }
           const float2 d = f2(fminf(fmaxf(r.x, -lam), lam), fminf(fmaxf(r.y, -lam), lam));
-          psi2 = ffma2(d, ffma2(d, mhalf, r), psi2);
           if constexpr (SAME) {
+            psi2 = ffma2(d, ffma2(d, mhalf, r), psi2);
 #pragma unroll
             for (int b = 0; b < B; ++b) gu[p][b] = ffma2(d, vv[b], gu[p][b]);
 #pragma unroll
             for (int b = 0; b < B; ++b) gv[jj][b] = ffma2(d, un[p][b], gv[jj][b]);
           } else {
+            if constexpr (ROWSIDE) {
 #pragma unroll
-            for (int b = 0; b < B; ++b) gu[p][b] = ffma2(d, bvv[b], gu[p][b]);
+              for (int b = 0; b < B; ++b) gu[p][b] = ffma2(d, bvv[b], gu[p][b]);
+            }
+            if constexpr (COLSIDE) {
 #pragma unroll
-            for (int b = 0; b < B; ++b) gv[jj][b] = ffma2(d, bun[p][b], gv[jj][b]);
+              for (int b = 0; b < B; ++b) gv[jj][b] = ffma2(d, bun[p][b], gv[jj][b]);
+            }
           }
         }
       }
       // Column sums of this group: lanes, then warps (fixed order).
+      if constexpr (COLSIDE) {
       float vals[JB];
 #pragma unroll
       for (int jj = 0; jj < J; ++jj)
@@ -349,6 +358,7 @@ __global__ void __launch_bounds__(288) fg_kernel(const __grid_constant__ CUtenso
 #pragma unroll
         for (int t = 0; t < CF; ++t) slab[base + t] = vals[t];
       }
+      }
     }
     psi_d += (double)psi2.x + (double)psi2.y;
     __syncwarp();
@@ -357,12 +367,12 @@ __global__ void __launch_bounds__(288) fg_kernel(const __grid_constant__ CUtenso
 
   // Row sums -(D Bv) over this CTA's columns.
 #pragma unroll
-  for (int p = 0; p < NP; ++p) {
+  for (int p = 0; p < (ROWSIDE ? NP : 0); ++p) {
     const int i0 = wrow0 + lane_row<R>(p, 0, lane);
     if (i0 < a.mpad) {
 #pragma unroll
       for (int b = 0; b < B; ++b)
-        *reinterpret_cast<float2*>(a.PU + ((size_t)cs * B + b) * a.mpad + i0) = gu[p][b];
+        *reinterpret_cast<float2*>(a.PU + ((size_t)cs * B + b) * a.mpad + i0) = gu[p][ROWSIDE ? b : 0];
     }
   }
   // Sum of psi over the tile; column sums over the consumer warps in fixed order.
@@ -374,7 +384,7 @@ __global__ void __launch_bounds__(288) fg_kernel(const __grid_constant__ CUtenso
     for (int w = 0; w < WC; ++w) s += scr[w];
     a.Ppsi[blockIdx.x] = s;
   }
-  for (int idx = tid; idx < ncols * B; idx += nct) {
+  for (int idx = tid; idx < (COLSIDE ? ncols * B : 0); idx += nct) {
     const int b = idx / ncols, jl = idx - b * ncols;
     float sum = 0.f;
     for (int w = 0; w < WC; ++w) sum += csum[((size_t)w * a.BN + jl) * B + b];

@@ -17,6 +17,7 @@ struct FinArgs {
   const float* PV;
   const double* Ppsi;
   int mode;  // FIN_*
+  int side;  // 0 both sides, 1 only the m x B side (GU), 2 only the n x B side (GV)
   const float* U;
   const float* V;
   const float* dU;
@@ -37,6 +38,7 @@ struct FinArgs {
 };
 
 __global__ void finalize_kernel(FinArgs a);
+__global__ void finalize_reduce_kernel(FinArgs a, int nblocks);
 __global__ void pack_mask_kernel(const uint8_t* mask, int64_t ldmask, int m, int n, int wpad, uint32_t* bits);
 __global__ void check_x_kernel(const float* X, int64_t ldx, const uint8_t* mask, int64_t ldmask, int m, int n,
                                unsigned long long* bad, unsigned long long* observed);

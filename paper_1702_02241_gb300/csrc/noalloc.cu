@@ -93,8 +93,8 @@ extern "C" rpca_status rpca_fg_noalloc(int64_t m, int64_t n, const float* X, int
     if (smem <= (size_t)smem_optin || BN <= FG_BJ) break;
   }
   if (smem > (size_t)smem_optin) return set_err_noctx(RPCA_EUNSUPPORTED, "no launch configuration fits");
-  const int fin_gu = (int)std::max<int64_t>(1, std::min<int64_t>((m * k + 255) / 256, 64LL * nsm));
-  const int fin_gv = (int)std::max<int64_t>(1, std::min<int64_t>((n * k + 7) / 8, 16LL * nsm));
+  const int fin_gu = (int)std::max<int64_t>(1, std::min<int64_t>((m * k + 1023) / 1024, 2LL * nsm));
+  const int fin_gv = (int)std::max<int64_t>(1, std::min<int64_t>((n * k + 7) / 8, (int64_t)nsm));
   const int fin_grid = fin_gu + fin_gv;
 
   // Scratch carve-up: partial sums, per-CTA psi sums, finalize block partials, counter,
@@ -175,6 +175,7 @@ extern "C" rpca_status rpca_fg_noalloc(int64_t m, int64_t n, const float* X, int
   fa.counter = reinterpret_cast<unsigned int*>(base + off_ctr);
   fa.out = reinterpret_cast<double*>(base + off_out);
   finalize_kernel<<<fin_grid, 256, 0, stream>>>(fa);
+  finalize_reduce_kernel<<<1, 256, 0, stream>>>(fa, fin_grid);
   if ((e = cudaGetLastError()) != cudaSuccess) return set_err_noctx(RPCA_ECUDA, cudaGetErrorString(e));
   // Synchronise and read f and the status word into host variables (no allocation).
   double fh = 0.0;

@@ -39,12 +39,12 @@ RPCA_DEV void block_sum3(double& x, double& y, double& z, double (*scr)[3]) {
   }
 }
 
-// Blocks [0, a.gu) handle the m x B side one element per thread (a few column-split
-// partials each); blocks [a.gu, gridDim.x) handle the n x B side one element per warp, the
-// lanes splitting the row-block partials (fixed-order shuffle sum).
+// Blocks [0, a.gu) handle the m x B side (threads stride over elements, four independent
+// loads in flight); blocks [a.gu, gridDim.x) handle the n x B side, one element per warp,
+// the lanes splitting the row-block partials (fixed-order shuffle sum).  Each block writes
+// its partial dot products; finalize_reduce_kernel combines them (no atomics, no fences).
 __global__ void __launch_bounds__(256) finalize_kernel(FinArgs a) {
   __shared__ double scr[32][3];
-  __shared__ bool is_last;
   if (a.gate != nullptr && *a.gate == 0) return;
   const float alpha = a.alpha_dev ? (float)*a.alpha_dev : a.alpha;
   const float lam = (float)a.lam_L;
@@ -53,29 +53,44 @@ __global__ void __launch_bounds__(256) finalize_kernel(FinArgs a) {
   // sums are float32 already); each thread's dot products go to float64 once at the end.
   float nrm_f = 0.f, gd_f = 0.f, gg_f = 0.f;
   if ((int)blockIdx.x < a.gu) {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < mB; e += (int64_t)a.gu * blockDim.x) {
-      const int l = (int)(e / a.m), i = (int)(e - (int64_t)l * a.m);
-      float s = 0.f;
-      for (int c = 0; c < a.ncs; ++c) s += a.PU[((int64_t)c * a.B + l) * a.mpad + i];
-      float g, xt = 0.f, dir = 0.f;
-      if (a.mode != FIN_APPLY) {
-        xt = a.U[e];
-        if (a.dU) xt = fmaf(alpha, a.dU[e], xt);
-        g = a.mode == FIN_FG ? fmaf(lam, xt, -s) : -s;
-        if (a.Ut) a.Ut[e] = xt;
-        if (a.DU) dir = a.DU[e];
-      } else {
-        g = -s;
+    const int64_t stride = (int64_t)a.gu * blockDim.x;
+    for (int64_t e0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a.side != 2 && e0 < mB; e0 += 4 * stride) {
+      float sv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t e = e0 + u * stride;
+        sv[u] = 0.f;
+        if (e < mB) {
+          const int l = (int)(e / a.m), i = (int)(e - (int64_t)l * a.m);
+          for (int c = 0; c < a.ncs; ++c) sv[u] += a.PU[((int64_t)c * a.B + l) * a.mpad + i];
+        }
       }
-      a.GU[e] = g;
-      nrm_f = fmaf(xt, xt, nrm_f);
-      gd_f = fmaf(g, dir, gd_f);
-      gg_f = fmaf(g, g, gg_f);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t e = e0 + u * stride;
+        if (e >= mB) break;
+        const float s = sv[u];
+        float g, xt = 0.f, dir = 0.f;
+        if (a.mode != FIN_APPLY) {
+          xt = a.U[e];
+          if (a.dU) xt = fmaf(alpha, a.dU[e], xt);
+          g = a.mode == FIN_FG ? fmaf(lam, xt, -s) : -s;
+          if (a.Ut) a.Ut[e] = xt;
+          if (a.DU) dir = a.DU[e];
+        } else {
+          g = -s;
+        }
+        a.GU[e] = g;
+        nrm_f = fmaf(xt, xt, nrm_f);
+        gd_f = fmaf(g, dir, gd_f);
+        gg_f = fmaf(g, g, gg_f);
+      }
     }
   } else {
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)(gridDim.x - a.gu) * (blockDim.x >> 5);
-    for (int64_t e2 = (int64_t)(blockIdx.x - a.gu) * (blockDim.x >> 5) + (threadIdx.x >> 5); e2 < nB; e2 += warps) {
+    for (int64_t e2 = (int64_t)(blockIdx.x - a.gu) * (blockDim.x >> 5) + (threadIdx.x >> 5); a.side != 1 && e2 < nB;
+         e2 += warps) {
       const int l = (int)(e2 / a.n), j = (int)(e2 - (int64_t)l * a.n);
       float s = 0.f;
       for (int r = lane; r < a.nrb; r += 32) s += a.PV[((int64_t)r * a.B + l) * a.n + j];
@@ -99,29 +114,30 @@ __global__ void __launch_bounds__(256) finalize_kernel(FinArgs a) {
       }
     }
   }
-  double nrm = nrm_f, gd = gd_f, gg = gg_f;
   if (a.mode == FIN_APPLY) return;
+  double nrm = nrm_f, gd = gd_f, gg = gg_f;
   block_sum3(nrm, gd, gg, scr);
   if (threadIdx.x == 0) {
     a.blk[3 * blockIdx.x + 0] = nrm;
     a.blk[3 * blockIdx.x + 1] = gd;
     a.blk[3 * blockIdx.x + 2] = gg;
-    __threadfence();
-    const unsigned t = atomicAdd(a.counter, 1u);
-    is_last = (t == gridDim.x - 1);
   }
-  __syncthreads();
-  if (!is_last) return;
-  __threadfence();
+}
+
+// One block: fixed-order sums of the finalize partials and of the per-CTA psi sums.
+// out = {f, g.d, ||g||^2, ||x||^2}.
+__global__ void __launch_bounds__(256) finalize_reduce_kernel(FinArgs a, int nblocks) {
+  __shared__ double scr[32][3];
+  if (a.gate != nullptr && *a.gate == 0) return;
   double p0 = 0.0, p1 = 0.0, p2 = 0.0, ps = 0.0;
-  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
-    p0 += __ldcg(&a.blk[3 * b + 0]);
-    p1 += __ldcg(&a.blk[3 * b + 1]);
-    p2 += __ldcg(&a.blk[3 * b + 2]);
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+    p0 += a.blk[3 * b + 0];
+    p1 += a.blk[3 * b + 1];
+    p2 += a.blk[3 * b + 2];
   }
   block_sum3(p0, p1, p2, scr);
   __syncthreads();
-  for (int b = threadIdx.x; b < a.nctas; b += blockDim.x) ps += __ldcg(&a.Ppsi[b]);
+  for (int b = threadIdx.x; b < a.nctas; b += blockDim.x) ps += a.Ppsi[b];
   double d1 = 0.0, d2 = 0.0;
   block_sum3(ps, d1, d2, scr);
   if (threadIdx.x == 0) {
@@ -129,7 +145,6 @@ __global__ void __launch_bounds__(256) finalize_kernel(FinArgs a) {
     a.out[1] = p1;
     a.out[2] = p2;
     a.out[3] = p0;
-    *a.counter = 0u;
   }
 }
 

@@ -82,23 +82,34 @@ static void free_sketch_buffers(SketchBuffers& b) {
     if (e_ != cudaSuccess) return cuda_err(c, e_, #call); \
   } while (0)
 
-// Y1 (m x l) = -A*(X) BV (BV n x l),  or  Y2 (n x l) = -A*(X)^T BU (BU m x l); chunks of 16.
+// Y1 (m x l) = -A*(X) BV (BV n x l),  or  Y2 (n x l) = -A*(X)^T BU (BU m x l), in chunks of
+// 8 columns, each one pass of the one-sided apply kernel with no forming factors.
 static rpca_status sk_apply(rpca_ctx* c, SketchBuffers& b, int l, const float* BV, const float* BU, float* Y1,
                             float* Y2) {
-  const FgPlan* P = apply_plan(c, 0);
+  const int side = BV ? 1 : 2;
+  const FgPlan* P = apply_plan(c, 0, side);
   if (!P) return RPCA_EUNSUPPORTED;
   const int64_t m = c->m, n = c->n;
-  for (int c0 = 0; c0 < l; c0 += 16) {
-    const int w = std::min(16, l - c0);
-    SK_CUDA(cudaMemsetAsync(b.BVc, 0, sizeof(float) * n * 16, c->stream));
-    SK_CUDA(cudaMemsetAsync(b.BUc, 0, sizeof(float) * m * 16, c->stream));
-    if (BV) SK_CUDA(cudaMemcpyAsync(b.BVc, BV + n * c0, sizeof(float) * n * w, cudaMemcpyDeviceToDevice, c->stream));
-    if (BU) SK_CUDA(cudaMemcpyAsync(b.BUc, BU + m * c0, sizeof(float) * m * w, cudaMemcpyDeviceToDevice, c->stream));
+  for (int c0 = 0; c0 < l; c0 += 8) {
+    const int w = std::min(8, l - c0);
+    const float* bv = BV ? BV + n * c0 : b.BVc;
+    const float* bu = BU ? BU + m * c0 : b.BUc;
+    if (w < 8) {  // ragged last chunk: zero-padded copy
+      if (BV) {
+        SK_CUDA(cudaMemsetAsync(b.BVc, 0, sizeof(float) * n * 8, c->stream));
+        SK_CUDA(cudaMemcpyAsync(b.BVc, bv, sizeof(float) * n * w, cudaMemcpyDeviceToDevice, c->stream));
+        bv = b.BVc;
+      } else {
+        SK_CUDA(cudaMemsetAsync(b.BUc, 0, sizeof(float) * m * 8, c->stream));
+        SK_CUDA(cudaMemcpyAsync(b.BUc, bu, sizeof(float) * m * w, cudaMemcpyDeviceToDevice, c->stream));
+        bu = b.BUc;
+      }
+    }
     FgLaunch L;
-    L.U = b.BUc;  // unused with no forming factors
+    L.U = b.BUc;  // not read: no forming factors
     L.V = b.BVc;
-    L.BU = b.BUc;
-    L.BV = b.BVc;
+    L.BU = bu;
+    L.BV = bv;
     L.fin_mode = FIN_APPLY;
     L.GU = b.Y1c;
     L.GV = b.Y2c;
@@ -138,18 +149,18 @@ rpca_status sketch_init(rpca_ctx* c, const float* Omega, float* U, float* V) {
     free_sketch_buffers(b);
     return s;
   };
-  const int64_t nf = n * l + m * l + n * l + n * 16 + m * 16 + m * 16 + n * 16;
+  const int64_t nf = n * l + m * l + n * l + n * 8 + m * 8 + m * 8 + n * 8;
   if (cudaMalloc(&b.buf, sizeof(float) * nf) != cudaSuccess) return done(set_err(c, RPCA_ENOMEM, "cudaMalloc"));
   b.Om = b.buf;
   b.Y = b.Om + n * l;
   b.Z = b.Y + m * l;
   b.BVc = b.Z + n * l;
-  b.BUc = b.BVc + n * 16;
-  b.Y1c = b.BUc + m * 16;
-  b.Y2c = b.Y1c + m * 16;
+  b.BUc = b.BVc + n * 8;
+  b.Y1c = b.BUc + m * 8;
+  b.Y2c = b.Y1c + m * 8;
   if (cudaMalloc(&b.st, sizeof(SketchState)) != cudaSuccess) return done(set_err(c, RPCA_ENOMEM, "cudaMalloc"));
   b.ts.grid = 2 * c->nsm;
-  b.ts.part_n = (size_t)b.ts.grid * 2048;
+  b.ts.part_n = (size_t)b.ts.grid * 2304;
   if (cudaMalloc(&b.ts.part, sizeof(double) * b.ts.part_n) != cudaSuccess ||
       cudaMalloc(&b.ts.counter, 64) != cudaSuccess)
     return done(set_err(c, RPCA_ENOMEM, "cudaMalloc"));

@@ -8,7 +8,7 @@ namespace rpca {
 
 constexpr int TS_TR = 32;      // rows per shared-memory tile
 constexpr int TS_PAD = 33;     // padded column stride of the tile (bank-conflict free)
-constexpr int TS_MAXOUT = 8;   // outputs per thread (p * q <= 8 * 256)
+constexpr int TS_MAXOUT = 9;   // outputs per thread (p * q <= 9 * 256)
 
 // Products in float32 over a 32-row tile, float64 across tiles and blocks.
 __global__ void __launch_bounds__(256) ts_gram_kernel(const float* A, int64_t lda, int p, const float* B,

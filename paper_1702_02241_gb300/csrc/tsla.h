@@ -13,7 +13,7 @@ struct TsScratch {
 };
 
 // C (p x q, column-major, ld p, device float64) = A^T B, A rows x p (lda), B rows x q (ldb).
-// p * q <= 2048.  Deterministic (fixed-order reduction).
+// p * q <= 2304.  Deterministic (fixed-order reduction).
 cudaError_t ts_gram(const float* A, int64_t lda, int p, const float* B, int64_t ldb, int q, int64_t rows, double* C,
                     const TsScratch& s, cudaStream_t st);
 

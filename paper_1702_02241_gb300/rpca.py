@@ -43,7 +43,8 @@ class rpca_cert(C.Structure):
 
 class rpca_result(C.Structure):
     _fields_ = [("F", C.c_double), ("iters", C.c_int), ("evals", C.c_int), ("cert_evals", C.c_int),
-                ("seconds", C.c_double), ("cert", rpca_cert), ("status", C.c_int)]
+                ("seconds", C.c_double), ("cert", rpca_cert), ("status", C.c_int), ("ms_init", C.c_double),
+                ("ms_iter", C.c_double), ("ms_cert", C.c_double)]
 
 
 _lib = None
