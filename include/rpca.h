@@ -202,6 +202,16 @@ RPCA_API rpca_status rpca_profile_read(rpca_ctx *c, double *out);
 RPCA_API rpca_status rpca_solve_log(rpca_ctx *c, double *out, int max_rows, int *rows);
 
 /*
+ * Per-trial log of the line searches of the last rpca_solve on c (device ring of the last
+ * 256 trials, copied out here): up to max_rows rows of 7 doubles, oldest first:
+ * {iteration, trial step a, F(x + a d) - F(x), phi'(a) / |phi'(0)| (directional derivative
+ * along d, relative), ||grad F(x + a d)||_F^2, phase (0 bracketing, 1 zoom), trial number}.
+ * The line search is the strong-Wolfe search of Nocedal & Wright Alg. 3.5/3.6 that the
+ * L-BFGS iteration of Sec. 3.3 uses.  *rows receives the number of rows written.
+ */
+RPCA_API rpca_status rpca_solve_trials(rpca_ctx *c, double *out, int max_rows, int *rows);
+
+/*
  * One objective/gradient evaluation, as rpca_fg (same formulas, same kernels), that
  * allocates nothing: for callers that cannot allocate device memory where they evaluate
  * (an application that owns all device memory through its own arena, code running while a

@@ -48,7 +48,7 @@ struct CertState {
   int r;
   double t1, t2, t3, t4, normL, sigma1;
   double G[(CERT_KMAX + LZ_TMAX) * LZ_B];    // Gram scratch (p x q)
-  double G2[(CERT_KMAX + LZ_TMAX) * LZ_B];
+  double G2[(CERT_KMAX + LZ_TMAX + LZ_B) * LZ_B];  // projection Gram [B | Y]^T Y
   double R[LZ_B * LZ_B], Rinv[LZ_B * LZ_B];
   int bad_mask;  // columns whose Cholesky pivot collapsed in the last block QR
   double n0[LZ_B];  // squared column norms before the last projection
@@ -100,8 +100,8 @@ __global__ void __launch_bounds__(256) cert_small_kernel(CertState* st, int k, d
   }
   __syncthreads();
   // Symmetric PSD Grams: the one-sided Jacobi SVD is their eigen-decomposition.
-  cta_jacobi_svd<double>(Au, k, k, k, Wu, k, su, &flag, 60, 1e-15);
-  cta_jacobi_svd<double>(Av, k, k, k, Wv, k, sv, &flag, 60, 1e-15);
+  cta_jacobi_svd<double>(Au, k, k, k, Wu, k, su, &flag, 60, 1e-13, 4.0 * k * 1.1e-16);
+  cta_jacobi_svd<double>(Av, k, k, k, Wv, k, sv, &flag, 60, 1e-13, 4.0 * k * 1.1e-16);
   cta_sort_desc<double>(su, k, ordu);
   cta_sort_desc<double>(sv, k, ordv);
   if (t == 0) {
@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(256) cert_small_kernel(CertState* st, int k, d
   __syncthreads();
   int r = 0;
   if (ku > 0 && kv > 0) {
-    cta_jacobi_svd<double>(M, ku, kv, ku, Vm, kv, sm, &flag, 60, 1e-15);
+    cta_jacobi_svd<double>(M, ku, kv, ku, Vm, kv, sm, &flag, 60, 1e-13, 4.0 * ku * 1.1e-16);
     cta_sort_desc<double>(sm, kv, ordm);
     const double s1 = sm[ordm[0]];
     for (int i = 0; i < std::min(ku, kv); ++i) r += (sm[ordm[i]] > RANK_TAU * s1 && s1 > 0.0);
@@ -263,18 +263,34 @@ __global__ void __launch_bounds__(256) cert_resid_kernel(const float* A, const f
   }
 }
 
-// Cholesky of the 8 x 8 Gram in st->G; records the columns whose pivot collapsed (that
-// column is numerically in the span of the earlier ones and of the bases projected out).
-__global__ void cert_chol_kernel(CertState* st, double rel, int per_column) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  int mask = 0;
-  chol_upper_inv_masked(st->G, LZ_B, rel, st->R, st->Rinv, &mask, per_column ? st->n0 : nullptr);
-  st->bad_mask = mask;
+// Sums the Gram partials of an 8-column block into st->G and factors it (masked Cholesky);
+// records the columns whose pivot collapsed (that column is numerically in the span of the
+// earlier ones and of the bases projected out).
+constexpr int CHOL_THREADS = 512;
+__global__ void __launch_bounds__(CHOL_THREADS) cert_gram_chol_kernel(const double* part, int nblk, CertState* st,
+                                                                      double rel, int per_column) {
+  __shared__ double scratch[CHOL_THREADS];
+  __shared__ double G[LZ_B * LZ_B], W[LZ_B * LZ_B], R[LZ_B * LZ_B], Ri[LZ_B * LZ_B], rd[LZ_B];
+  __shared__ int bad;
+  ts_reduce_partials_cta(part, nblk, LZ_B * LZ_B, G, scratch);
+  __syncthreads();
+  const int mask = cta_chol_masked(G, LZ_B, rel, per_column ? st->n0 : nullptr, W, R, Ri, rd, &bad);
+  if (threadIdx.x < LZ_B * LZ_B) {
+    st->G[threadIdx.x] = G[threadIdx.x];
+    st->R[threadIdx.x] = R[threadIdx.x];
+    st->Rinv[threadIdx.x] = Ri[threadIdx.x];
+  }
+  if (threadIdx.x == 0) st->bad_mask = mask;
 }
 
-// Records the squared column norms (diagonal of the Gram in st->G).
-__global__ void cert_norms_kernel(CertState* st) {
-  if (threadIdx.x < LZ_B && blockIdx.x == 0) st->n0[threadIdx.x] = st->G[threadIdx.x * (LZ_B + 1)];
+// Sums the Gram partials into st->G and records the squared column norms (its diagonal).
+__global__ void __launch_bounds__(CHOL_THREADS) cert_gram_norms_kernel(const double* part, int nblk, CertState* st) {
+  __shared__ double scratch[CHOL_THREADS];
+  __shared__ double G[LZ_B * LZ_B];
+  ts_reduce_partials_cta(part, nblk, LZ_B * LZ_B, G, scratch);
+  __syncthreads();
+  if (threadIdx.x < LZ_B * LZ_B) st->G[threadIdx.x] = G[threadIdx.x];
+  if (threadIdx.x < LZ_B) st->n0[threadIdx.x] = G[threadIdx.x * (LZ_B + 1)];
 }
 
 // Columns flagged in st->bad_mask are set to zero (the Krylov space is exhausted there).
@@ -326,17 +342,24 @@ __global__ void cert_reset_kernel(CertState* st) {
 
 // Ritz values of T[0:d, 0:d] (float32 one-sided Jacobi in global memory) -> t4 estimate,
 // sigma_1, and whether both have settled since the previous check.
-__global__ void __launch_bounds__(1024) cert_ritz_kernel(CertState* st, const double* T, float* A, float* V, int d,
+__global__ void __launch_bounds__(1024) cert_ritz_kernel(CertState* st, const double* T, float* Ag, float* Vg, int d,
                                                           double lam_L, int final_step) {
   __shared__ float s[LZ_TMAX];
   __shared__ int ord[LZ_TMAX];
   __shared__ int flag;
+  extern __shared__ float dyn[];
+  // Small projected matrices (d <= 96) are worked on in shared memory, larger ones in global.
+  const bool in_smem = d <= 96;
+  float* A = in_smem ? dyn : Ag;
+  float* V = in_smem ? dyn + d * d : Vg;
   for (int i = threadIdx.x; i < d * d; i += blockDim.x) {
     const int a = i % d, b = i / d;
     A[i] = (float)T[a + (int64_t)b * LZ_TMAX];
   }
   __syncthreads();
-  cta_jacobi_svd<float>(A, d, d, d, V, d, s, &flag, 40, 1e-7f);
+  // Rotation threshold above the float32 rounding of the column inner products (about
+  // d * eps relative); below it every sweep would rotate every pair until the sweep limit.
+  cta_jacobi_svd<float>(A, d, d, d, V, d, s, &flag, 40, fmaxf(1e-6f, 4.0f * d * 1.2e-7f), 2.0f * d * 6e-8f);
   cta_sort_desc<float>(s, d, ord);
   if (threadIdx.x == 0) {
     double t4 = 0.0;
@@ -381,7 +404,6 @@ void free_cert(rpca_ctx* c) {
   cudaFree(b->blk);
   cudaFree(b->counter);
   cudaFree(b->ts.part);
-  cudaFree(b->ts.counter);
   cudaFreeHost(b->host);
   delete b;
   c->cert = nullptr;
@@ -441,9 +463,24 @@ static rpca_status ensure_cert(rpca_ctx* c) {
   b->ts.grid = 2 * c->nsm;
   b->ts.part_n = (size_t)b->ts.grid * 2304;
   CERT_CUDA(cudaMalloc(&b->ts.part, sizeof(double) * b->ts.part_n));
-  CERT_CUDA(cudaMalloc(&b->ts.counter, 64));
-  CERT_CUDA(cudaMemsetAsync(b->ts.counter, 0, 64, c->stream));
   return RPCA_OK;
+}
+
+// Sums the partials of [B | Y]^T Y ((p + 8) x 8, one warp per output) into st->G2 and records
+// the squared column norms of Y (the diagonal of its trailing 8 x 8 block) in st->n0.
+__global__ void __launch_bounds__(256) cert_proj_reduce_kernel(const double* part, int nblk, int p, CertState* st) {
+  const int ld = p + LZ_B, nout = ld * LZ_B;
+  const int o = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (o >= nout) return;
+  double t = 0.0;
+  for (int b = lane; b < nblk; b += 32) t += part[(int64_t)b * nout + o];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+  if (lane == 0) {
+    st->G2[o] = t;
+    const int i = o % ld, j = o / ld;
+    if (i - p == j) st->n0[j] = t;
+  }
 }
 
 // Y (rows x 8) <- Y - B (B^T Y) for a basis B (rows x p, orthonormal columns).
@@ -460,17 +497,21 @@ static rpca_status project_out(rpca_ctx* c, const float* Bm, int p, float* Y, in
 // rel * (largest squared column norm).
 static rpca_status gram_chol(rpca_ctx* c, float* Y, int64_t rows, double rel, int per_column) {
   CertBuffers* b = c->cert;
-  CERT_CUDA(ts_gram_c(c, Y, rows, LZ_B, Y, rows, LZ_B, rows, b->st->G, b->ts, c->stream));
-  cert_chol_kernel<<<1, 1, 0, c->stream>>>(b->st, rel, per_column);
+  const int nblk = ts_gram_partial_c(c, Y, rows, LZ_B, Y, rows, LZ_B, rows, b->ts, c->stream);
+  if (nblk < 0) return set_err(c, RPCA_ECUDA, "ts_gram_partial");
+  cert_gram_chol_kernel<<<1, CHOL_THREADS, 0, c->stream>>>(b->ts.part, nblk, b->st, rel, per_column);
   count_launches(c, 1);
+  CERT_CUDA(cudaGetLastError());
   return RPCA_OK;
 }
 
 static rpca_status record_norms(rpca_ctx* c, float* Y, int64_t rows) {
   CertBuffers* b = c->cert;
-  CERT_CUDA(ts_gram_c(c, Y, rows, LZ_B, Y, rows, LZ_B, rows, b->st->G, b->ts, c->stream));
-  cert_norms_kernel<<<1, 32, 0, c->stream>>>(b->st);
+  const int nblk = ts_gram_partial_c(c, Y, rows, LZ_B, Y, rows, LZ_B, rows, b->ts, c->stream);
+  if (nblk < 0) return set_err(c, RPCA_ECUDA, "ts_gram_partial");
+  cert_gram_norms_kernel<<<1, CHOL_THREADS, 0, c->stream>>>(b->ts.part, nblk, b->st);
   count_launches(c, 1);
+  CERT_CUDA(cudaGetLastError());
   return RPCA_OK;
 }
 
@@ -490,28 +531,46 @@ static rpca_status normalise(rpca_ctx* c, float* Y, int64_t rows) {
 }
 
 // Orthonormalises the block Y (rows x 8) against the basis B (rows x p; the fixed range
-// basis followed by the Krylov blocks, contiguous), on the stream with no host
-// synchronisation.  A column that loses all but 1e-3 of its norm to the projection and to
-// the earlier columns of its block is treated as collapsed (in float32 its remainder is
-// mostly rounding along B, which normalising would amplify) and replaced by a random
-// column, projected again, and zeroed if it collapses once more (the complement of B is
-// exhausted).  Then: normalise, project again, normalise again; zero columns stay zero.
+// basis followed by the Krylov blocks, contiguous), by two passes of classical Gram-Schmidt
+// and CholeskyQR.  A column that loses all but 1e-3 of its norm to the projection and to the
+// earlier columns of its block is treated as collapsed (in float32 its remainder is mostly
+// rounding along B, which normalising would amplify): it is replaced by a random column,
+// projected again, and zeroed if it collapses once more (the complement of B is exhausted).
+// Then: normalise, project again, normalise again; zero columns stay zero.  The host reads
+// the collapse mask once per block; when nothing collapsed, the factor of the collapse test
+// is the first CholeskyQR pass.
 static rpca_status orth_block(rpca_ctx* c, float* Y, int64_t rows, const float* Bm, int p, uint64_t seed) {
   rpca_status s;
   CertBuffers* b = c->cert;
   const double collapse = 1e-6;  // squared-norm ratio
-  if ((s = record_norms(c, Y, rows)) != RPCA_OK) return s;
-  if ((s = project_twice(c, Y, rows, Bm, p)) != RPCA_OK) return s;
+  if (p > 0 && Bm + (int64_t)p * rows == Y) {
+    // First projection with the column norms of Y from the same pass: [B | Y]^T Y.
+    const int nblk = ts_gram_partial_c(c, Bm, rows, p + LZ_B, Y, rows, LZ_B, rows, b->ts, c->stream);
+    if (nblk < 0) return set_err(c, RPCA_ECUDA, "ts_gram_partial");
+    cert_proj_reduce_kernel<<<((p + LZ_B) * LZ_B + 7) / 8, 256, 0, c->stream>>>(b->ts.part, nblk, p, b->st);
+    count_launches(c, 1);
+    CERT_CUDA(ts_mul_c(c, Bm, rows, p, b->st->G2, p + LZ_B, LZ_B, Y, rows, rows, -1.f, 1.f, c->stream));
+    if ((s = project_out(c, Bm, p, Y, rows)) != RPCA_OK) return s;
+  } else {
+    if ((s = record_norms(c, Y, rows)) != RPCA_OK) return s;
+    if ((s = project_twice(c, Y, rows, Bm, p)) != RPCA_OK) return s;
+  }
   if ((s = gram_chol(c, Y, rows, collapse, 1)) != RPCA_OK) return s;
-  cert_refill_kernel<<<256, 256, 0, c->stream>>>(Y, rows, b->st, seed);
-  count_launches(c, 1);
-  if ((s = record_norms(c, Y, rows)) != RPCA_OK) return s;
-  if ((s = project_twice(c, Y, rows, Bm, p)) != RPCA_OK) return s;
-  if ((s = gram_chol(c, Y, rows, collapse, 1)) != RPCA_OK) return s;
-  cert_zero_cols_kernel<<<256, 256, 0, c->stream>>>(Y, rows, b->st);
-  count_launches(c, 1);
-  if ((s = normalise(c, Y, rows)) != RPCA_OK) return s;
-  if ((s = project_twice(c, Y, rows, Bm, p)) != RPCA_OK) return s;
+  CERT_CUDA(cudaMemcpyAsync(&b->host->bad_mask, &b->st->bad_mask, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CERT_CUDA(cudaStreamSynchronize(c->stream));
+  if (b->host->bad_mask != 0) {
+    cert_refill_kernel<<<256, 256, 0, c->stream>>>(Y, rows, b->st, seed);
+    count_launches(c, 1);
+    if ((s = record_norms(c, Y, rows)) != RPCA_OK) return s;
+    if ((s = project_twice(c, Y, rows, Bm, p)) != RPCA_OK) return s;
+    if ((s = gram_chol(c, Y, rows, collapse, 1)) != RPCA_OK) return s;
+    cert_zero_cols_kernel<<<256, 256, 0, c->stream>>>(Y, rows, b->st);
+    count_launches(c, 1);
+    if ((s = normalise(c, Y, rows)) != RPCA_OK) return s;
+  } else {
+    CERT_CUDA(ts_mul_c(c, Y, rows, LZ_B, b->st->Rinv, LZ_B, LZ_B, Y, rows, rows, 1.f, 0.f, c->stream));
+  }
+  if ((s = project_out(c, Bm, p, Y, rows)) != RPCA_OK) return s;
   return normalise(c, Y, rows);
 }
 
@@ -614,9 +673,10 @@ rpca_status cert_compute(rpca_ctx* c, const float* U, const float* V, rpca_cert*
     for (int j = 0; j < smax; ++j) {
       float* Qj = b->Q + (int64_t)j * LZ_B * n;
       float* Pj = b->P + (int64_t)j * LZ_B * m;
-      // A Q_j = P_U1perp D Q_j  (Q_j is orthogonal to V1 by construction).
+      // D Q_j (Q_j is orthogonal to V1 by construction).  A Q_j = P_U1perp D Q_j; its
+      // projection on U1 is removed by orth_block, and T = P^T A Q_j = P^T D Q_j because the
+      // columns of P are orthogonal to U1.
       if ((s = apply_D(c, 1, Qj, b->zm, b->Wraw, b->Z)) != RPCA_OK) return s;
-      if ((s = project_twice(c, b->Wraw, m, b->U1, r)) != RPCA_OK) return s;
       CERT_CUDA(cudaMemcpyAsync(Pj, b->Wraw, sizeof(float) * m * LZ_B, cudaMemcpyDeviceToDevice, c->stream));
       if ((s = orth_block(c, Pj, m, b->U1, r + j * LZ_B, 1000 + 2 * j)) != RPCA_OK) return s;
       // Column block j of T = P^T A Q.
@@ -625,8 +685,12 @@ rpca_status cert_compute(rpca_ctx* c, const float* U, const float* V, rpca_cert*
       count_launches(c, 1);
       steps = j + 1;
       const bool last = (j == smax - 1);
-      if (steps == 2 || steps == 3 || steps == 4 || steps == 6 || (steps % 4) == 0 || last) {
-        cert_ritz_kernel<<<1, 1024, 0, c->stream>>>(st, b->T, b->Tw, b->Tv, steps * LZ_B, c->lam_L, last ? 1 : 0);
+      if (steps == 2 || steps == 4 || steps == 6 || (steps % 4) == 0 || last) {
+        const int d = steps * LZ_B;
+        const size_t rsm = d <= 96 ? (size_t)2 * d * d * sizeof(float) : 0;
+        CERT_CUDA(cudaFuncSetAttribute(cert_ritz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       2 * 96 * 96 * (int)sizeof(float)));
+        cert_ritz_kernel<<<1, 1024, rsm, c->stream>>>(st, b->T, b->Tw, b->Tv, d, c->lam_L, last ? 1 : 0);
         count_launches(c, 1);
         CERT_CUDA(cudaGetLastError());
         int conv = 0;

@@ -27,11 +27,24 @@ struct SketchState {
 
 void fill_normal(float* out, int64_t count, uint64_t seed, float scale, cudaStream_t s);
 
-// Cholesky of the l x l Gram; collapsed columns (the sketch of a matrix of rank < l) are
-// flagged and left uncoupled.
-__global__ void sk_chol_kernel(SketchState* st, int l) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  chol_upper_inv_masked(st->G, l, 1e-10, st->R, st->Rinv, &st->bad);
+// Sums the Gram partials of the l x l Gram and factors it; collapsed columns (the sketch of a
+// matrix of rank < l) are flagged and left uncoupled.
+constexpr int SK_CHOL_THREADS = 1024;
+__global__ void __launch_bounds__(SK_CHOL_THREADS) sk_gram_chol_kernel(const double* part, int nblk, SketchState* st,
+                                                                       int l) {
+  __shared__ double scratch[SK_CHOL_THREADS];
+  __shared__ double G[SK_LMAX * SK_LMAX], W[SK_LMAX * SK_LMAX], R[SK_LMAX * SK_LMAX], Ri[SK_LMAX * SK_LMAX];
+  __shared__ double rd[SK_LMAX];
+  __shared__ int bad;
+  ts_reduce_partials_cta(part, nblk, l * l, G, scratch);
+  __syncthreads();
+  const int mask = cta_chol_masked(G, l, 1e-10, nullptr, W, R, Ri, rd, &bad);
+  for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
+    st->G[e] = G[e];
+    st->R[e] = R[e];
+    st->Rinv[e] = Ri[e];
+  }
+  if (threadIdx.x == 0) st->bad = mask;
 }
 
 // Zero the flagged columns of Y (rows x l).
@@ -50,7 +63,7 @@ __global__ void __launch_bounds__(256) sk_small_svd_kernel(SketchState* st, int 
   __shared__ int flag;
   for (int i = threadIdx.x; i < l * l; i += blockDim.x) A[i] = st->G[i];
   __syncthreads();
-  cta_jacobi_svd<double>(A, l, l, l, W, l, ev, &flag, 60, 1e-15);
+  cta_jacobi_svd<double>(A, l, l, l, W, l, ev, &flag, 60, 1e-13, 4.0 * l * 1.1e-16);
   cta_sort_desc<double>(ev, l, ord);
   for (int i = threadIdx.x; i < l * k; i += blockDim.x) {
     const int a = i % l, c = i / l;
@@ -73,7 +86,6 @@ static void free_sketch_buffers(SketchBuffers& b) {
   cudaFree(b.buf);
   cudaFree(b.st);
   cudaFree(b.ts.part);
-  cudaFree(b.ts.counter);
 }
 
 #define SK_CUDA(call)                                     \
@@ -125,9 +137,11 @@ static rpca_status sk_apply(rpca_ctx* c, SketchBuffers& b, int l, const float* B
 // CholeskyQR2; columns that collapse in the first pass are zeroed (rank of the sketch < l).
 static rpca_status sk_orth(rpca_ctx* c, SketchBuffers& b, float* Y, int64_t rows, int l) {
   for (int pass = 0; pass < 3; ++pass) {
-    SK_CUDA(ts_gram_c(c, Y, rows, l, Y, rows, l, rows, b.st->G, b.ts, c->stream));
-    sk_chol_kernel<<<1, 1, 0, c->stream>>>(b.st, l);
+    const int nblk = ts_gram_partial_c(c, Y, rows, l, Y, rows, l, rows, b.ts, c->stream);
+    if (nblk < 0) return set_err(c, RPCA_ECUDA, "ts_gram_partial");
+    sk_gram_chol_kernel<<<1, SK_CHOL_THREADS, 0, c->stream>>>(b.ts.part, nblk, b.st, l);
     count_launches(c, 1);
+    SK_CUDA(cudaGetLastError());
     if (pass == 0) {
       sk_zero_cols_kernel<<<256, 256, 0, c->stream>>>(Y, rows, l, b.st);
       count_launches(c, 1);
@@ -161,10 +175,8 @@ rpca_status sketch_init(rpca_ctx* c, const float* Omega, float* U, float* V) {
   if (cudaMalloc(&b.st, sizeof(SketchState)) != cudaSuccess) return done(set_err(c, RPCA_ENOMEM, "cudaMalloc"));
   b.ts.grid = 2 * c->nsm;
   b.ts.part_n = (size_t)b.ts.grid * 2304;
-  if (cudaMalloc(&b.ts.part, sizeof(double) * b.ts.part_n) != cudaSuccess ||
-      cudaMalloc(&b.ts.counter, 64) != cudaSuccess)
+  if (cudaMalloc(&b.ts.part, sizeof(double) * b.ts.part_n) != cudaSuccess)
     return done(set_err(c, RPCA_ENOMEM, "cudaMalloc"));
-  cudaMemsetAsync(b.ts.counter, 0, 64, c->stream);
   if (Omega) cudaMemcpyAsync(b.Om, Omega, sizeof(float) * n * l, cudaMemcpyDeviceToDevice, c->stream);
   else {
     fill_normal(b.Om, n * l, 0xC0FFEEULL ^ (c->opt.seed * 0x9E3779B97F4A7C15ULL), 1.f, c->stream);

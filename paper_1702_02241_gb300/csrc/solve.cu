@@ -101,6 +101,22 @@ extern "C" rpca_status rpca_solve_log(rpca_ctx* c, double* out, int max_rows, in
   return RPCA_OK;
 }
 
+extern "C" rpca_status rpca_solve_trials(rpca_ctx* c, double* out, int max_rows, int* rows) {
+  if (!c || !out || !rows || max_rows < 0) return RPCA_EINVAL;
+  *rows = 0;
+  if (!c->sol) return RPCA_OK;
+  SolverState st;
+  rpca_status s = solver_read_state(c, &st);
+  if (s != RPCA_OK) return s;
+  const int n = std::min(std::min(st.tlog_n, SOLVER_TLOG), max_rows);
+  for (int i = 0; i < n; ++i) {
+    const int idx = (st.tlog_n - n + i) % SOLVER_TLOG;
+    for (int q = 0; q < 7; ++q) out[7 * i + q] = st.tlog[idx][q];
+  }
+  *rows = n;
+  return RPCA_OK;
+}
+
 extern "C" rpca_status rpca_solve(rpca_ctx* c, float* U, float* V, rpca_result* res) {
   if (!c) return RPCA_EINVAL;
   if (!U || !V) return set_err(c, RPCA_EINVAL, "U and V are required");

@@ -22,6 +22,7 @@
 // all further sums, the Gram table, the two-loop scalars and the line-search arithmetic
 // are float64.
 #include <algorithm>
+#include <cstddef>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -64,13 +65,27 @@ __device__ double cubic_step(double a, double fa, double ga, double b, double fb
   return b - (b - a) * (gb + d2 - d1) / den;
 }
 
-__device__ double zoom_trial(const LineSearch& L) {
-  const double left = fmin(L.lo, L.hi), right = fmax(L.lo, L.hi), w = right - left;
-  if (!isfinite(L.fhi)) return 0.5 * (L.lo + L.hi);
-  bool ok;
-  double t = cubic_step(L.lo, L.flo, L.glo, L.hi, L.fhi, L.ghi, &ok);
-  if (!ok || !isfinite(t)) return 0.5 * (L.lo + L.hi);
-  return fmin(fmax(t, left + 0.1 * w), right - 0.1 * w);
+// Next trial inside the bracket (lo, hi).  Where the objective values differ by more than
+// their noise level, the minimiser of the cubic through both ends (f and phi'); where they
+// do not, the secant root of phi' (the objective differences are rounding there, the
+// directional derivatives are not).  A bracket that did not shrink to 2/3 of its previous
+// width is bisected (Hager & Zhang's safeguard).
+__device__ double zoom_trial(const LineSearch& L, double epsf) {
+  const double w = L.hi - L.lo;
+  const double mid = 0.5 * (L.lo + L.hi);
+  if (!isfinite(L.fhi) || !isfinite(L.ghi)) return mid;
+  if (L.width_prev > 0.0 && w > 0.66 * L.width_prev) return mid;
+  double t;
+  if (fabs(L.fhi - L.flo) > 100.0 * epsf) {
+    bool ok;
+    t = cubic_step(L.lo, L.flo, L.glo, L.hi, L.fhi, L.ghi, &ok);
+    if (!ok) return mid;
+  } else {
+    if (!(L.ghi > L.glo)) return mid;
+    t = L.lo - L.glo * w / (L.ghi - L.glo);
+  }
+  if (!isfinite(t)) return mid;
+  return fmin(fmax(t, L.lo + 0.01 * w), L.hi - 0.01 * w);
 }
 
 // One step of the line-search state machine after the trial at L.a has been evaluated
@@ -94,6 +109,17 @@ __global__ void ls_step_kernel(SolverState* st, cudaGraphConditionalHandle h) {
   const double epsf = st->ls_noise * fabs(L.f0);
   const bool approx_ok = isfinite(fa) && fa <= L.f0 + epsf && ga <= (2.0 * LS_C1 - 1.0) * L.g0;
   const double gga = st->out[2];
+  {
+    double* rec = st->tlog[st->tlog_n % SOLVER_TLOG];
+    rec[0] = st->iter;
+    rec[1] = a;
+    rec[2] = fa - L.f0;
+    rec[3] = ga / fabs(L.g0);
+    rec[4] = gga;
+    rec[5] = L.phase;
+    rec[6] = L.evals;
+    st->tlog_n += 1;
+  }
   if (L.force) {  // the fallback trial (see below) is taken as it is
     L.state = LS_ACCEPTED;
     L.f_acc = fa;
@@ -107,35 +133,32 @@ __global__ void ls_step_kernel(SolverState* st, cudaGraphConditionalHandle h) {
   }
   const bool armijo_fail = !isfinite(fa) || (fa > L.f0 + LS_C1 * a * L.g0 && !approx_ok);
   if (L.phase == 0) {  // bracketing (Alg. 3.5)
-    if (armijo_fail || (!L.first && fa > L.f_prev + epsf)) {
+    if (armijo_fail || (!L.first && fa > L.f_prev + epsf) || (fabs(ga) > -LS_C2 * L.g0 && ga >= 0.0)) {
+      // [a_prev, a] holds a point of the strong Wolfe conditions: phi'(a_prev) < 0 and phi
+      // there is within the sufficient-decrease band, while at a either phi rose or phi' >= 0.
       L.lo = L.a_prev; L.flo = L.f_prev; L.glo = L.g_prev;
       L.hi = a; L.fhi = fa; L.ghi = ga;
+      L.width_prev = 0.0;
       L.phase = 1;
     } else if (fabs(ga) <= -LS_C2 * L.g0) {
       accept = true;
-    } else if (ga >= 0.0) {
-      L.lo = a; L.flo = fa; L.glo = ga;
-      L.hi = L.a_prev; L.fhi = L.f_prev; L.ghi = L.g_prev;
-      L.phase = 1;
     } else {
       L.a_prev = a; L.f_prev = fa; L.g_prev = ga;
       L.a = fmin(4.0 * a, LS_AMAX);
       L.first = 0;
     }
-  } else {  // zoom (Alg. 3.6)
-    // phi(a) >= phi(lo) counts only beyond the noise level unless the approximate test fails.
-    if (armijo_fail || fa > L.flo + epsf || (fa >= L.flo && !approx_ok)) {
+  } else {  // zoom (Alg. 3.6), with the bracket kept by the sign of phi' (Hager & Zhang)
+    const double w = L.hi - L.lo;
+    if (armijo_fail || fa > L.flo + epsf) {
+      L.hi = a; L.fhi = fa; L.ghi = ga;
+    } else if (fabs(ga) <= -LS_C2 * L.g0) {
+      accept = true;
+    } else if (ga >= 0.0) {
       L.hi = a; L.fhi = fa; L.ghi = ga;
     } else {
-      if (fabs(ga) <= -LS_C2 * L.g0) {
-        accept = true;
-      } else {
-        if (ga * (L.hi - L.lo) >= 0.0) {
-          L.hi = L.lo; L.fhi = L.flo; L.ghi = L.glo;
-        }
-        L.lo = a; L.flo = fa; L.glo = ga;
-      }
+      L.lo = a; L.flo = fa; L.glo = ga;
     }
+    L.width_prev = w;
   }
   if (accept) {
     L.state = LS_ACCEPTED;
@@ -151,7 +174,7 @@ __global__ void ls_step_kernel(SolverState* st, cudaGraphConditionalHandle h) {
       L.state = LS_FAILED;
     }
   } else if (L.phase == 1) {
-    L.a = zoom_trial(L);
+    L.a = zoom_trial(L, epsf);
   }
   const int running = L.state == LS_RUNNING;
   st->gate = running;
@@ -170,12 +193,13 @@ __device__ void two_loop_coefs(SolverState* st) {
     st->coef_g = -1.0;
     return;
   }
-  double a[SOLVER_MAX_SLOTS], c[SOLVER_MAX_SLOTS];
+  double a[SOLVER_MAX_SLOTS], c[SOLVER_MAX_SLOTS], rho[SOLVER_MAX_SLOTS];
   const int* id = st->ids;  // newest first
+  for (int i = 0; i < n; ++i) rho[i] = 1.0 / st->SY[id[i]][id[i]];  // independent divisions
   for (int i = 0; i < n; ++i) {  // newest -> oldest
     double t = st->sg[id[i]];
     for (int j = 0; j < i; ++j) t -= a[j] * st->SY[id[i]][id[j]];
-    a[i] = t / st->SY[id[i]][id[i]];
+    a[i] = t * rho[i];
   }
   const double gamma = st->SY[id[0]][id[0]] / st->YY[id[0]][id[0]];
   for (int i = n - 1; i >= 0; --i) {  // oldest -> newest
@@ -183,7 +207,7 @@ __device__ void two_loop_coefs(SolverState* st) {
     for (int j = 0; j < n; ++j) t -= a[j] * st->YY[id[i]][id[j]];
     t *= gamma;
     for (int j = i + 1; j < n; ++j) t += c[j] * st->SY[id[j]][id[i]];
-    const double b = t / st->SY[id[i]][id[i]];
+    const double b = t * rho[i];
     c[i] = a[i] - b;
   }
   st->coef_g = -gamma;
@@ -196,7 +220,7 @@ __device__ void two_loop_coefs(SolverState* st) {
 // Scalar part of an iteration: ring update, stopping tests, next direction's coefficients
 // and the line-search start.  `v` holds the reduced inner products (layout: see below).
 template <int NS>
-__device__ void iteration_scalars(SolverState* st, const double* v) {
+__device__ void iteration_scalars(SolverState* st, SolverState* logst, const double* v) {
   const int state = st->ls.state;
   int added = -1;  // slot of the pair added by this step, if any
   const double step = st->ls.a, trials = st->ls.evals;
@@ -252,7 +276,7 @@ __device__ void iteration_scalars(SolverState* st, const double* v) {
   st->gg = v[5 * NS + 5];
   st->g1 = v[5 * NS + 6];
   if (state != LS_NONE) {
-    double* rec = st->log[st->log_n % SOLVER_LOG];
+    double* rec = logst->log[logst->log_n % SOLVER_LOG];
     rec[0] = st->iter;
     rec[1] = st->f;
     rec[2] = sqrt(st->gg);
@@ -260,7 +284,7 @@ __device__ void iteration_scalars(SolverState* st, const double* v) {
     rec[4] = trials;
     rec[5] = state;
     rec[6] = st->count;
-    st->log_n += 1;
+    logst->log_n += 1;
   }
   if (!isfinite(st->f) || !isfinite(st->gg)) {
     st->stop = STOP_NONFINITE;
@@ -292,6 +316,7 @@ __device__ void iteration_scalars(SolverState* st, const double* v) {
   L.phase = 0;
   L.first = 1;
   L.evals = 0;
+  L.width_prev = 0.0;
   L.best_a = 0.0;
   L.best_gg = INFINITY;
   L.force = 0;
@@ -319,6 +344,28 @@ __global__ void __launch_bounds__(256) lbfgs_accept_kernel(SolverArgs a) {
 //   v[5 NS + 0..6] = s_new.g, y_new.g, s_new.y_new, y_new.y_new, s_new.s_new, g.g, |g|_1
 // Products in float32, summed in float32 over each thread's elements, float64 beyond.
 // The last block to finish runs the scalar part of the iteration.
+// The scalar part of an iteration, run by the last block of the dots reduction: the solver
+// state up to the log rings is copied to shared memory by the whole block, updated there by
+// one thread (a chain of dependent float64 operations, which must not wait on global
+// memory), and copied back.
+constexpr int SOLVER_CORE_WORDS = (int)(offsetof(SolverState, log_n) / sizeof(double));
+static_assert(offsetof(SolverState, log_n) % sizeof(double) == 0, "solver core must be whole words");
+template <int NS>
+__device__ void scalar_tail(SolverState* gst, const double* fin) {
+  __shared__ double core[SOLVER_CORE_WORDS];
+  const double* src = reinterpret_cast<const double*>(gst);
+  for (int i = threadIdx.x; i < SOLVER_CORE_WORDS; i += blockDim.x) core[i] = __ldcg(src + i);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    SolverState* s = reinterpret_cast<SolverState*>(core);
+    iteration_scalars<NS>(s, gst, fin);
+    s->gate = s->active;
+  }
+  __syncthreads();
+  double* dst = reinterpret_cast<double*>(gst);
+  for (int i = threadIdx.x; i < SOLVER_CORE_WORDS; i += blockDim.x) dst[i] = core[i];
+}
+
 template <int MCAP>
 __global__ void __launch_bounds__(256) lbfgs_dots_kernel(SolverArgs a) {
   constexpr int NS = MCAP + 1;
@@ -387,11 +434,8 @@ __global__ void __launch_bounds__(256) lbfgs_dots_kernel(SolverArgs a) {
     if (lane == 0) fin[v] = t;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    *a.counter = 0u;
-    iteration_scalars<NS>(st, fin);
-    st->gate = st->active;
-  }
+  if (threadIdx.x == 0) *a.counter = 0u;
+  scalar_tail<NS>(st, fin);
 }
 
 // d = c_g g + sum over ring slots (c_s[j] s_j + c_y[j] y_j); then g.d in float64 starts the
@@ -418,11 +462,17 @@ __global__ void __launch_bounds__(256) lbfgs_direction_kernel(SolverArgs a) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x) {
     const float ge = a.g[e];
     float dv = cg * ge;
+    float sv[NS], yv[NS];  // loads first, all in flight together (see the dots kernel)
+#pragma unroll
+    for (int j = 0; j < NS; ++j) {
+      sv[j] = a.S[(int64_t)j * N + e];
+      yv[j] = a.Y[(int64_t)j * N + e];
+    }
 #pragma unroll
     for (int j = 0; j < NS; ++j) {
       if ((live >> j) & 1ull) {
-        dv = fmaf(cs[j], a.S[(int64_t)j * N + e], dv);
-        dv = fmaf(cy[j], a.Y[(int64_t)j * N + e], dv);
+        dv = fmaf(cs[j], sv[j], dv);
+        dv = fmaf(cy[j], yv[j], dv);
       }
     }
     a.d[e] = dv;
@@ -468,6 +518,7 @@ __global__ void solver_init_kernel(SolverState* st, int mem, int max_iter, doubl
   st->ls_noise = ls_noise;
   st->ls.state = LS_NONE;
   st->log_n = 0;
+  st->tlog_n = 0;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -495,11 +546,127 @@ struct SolverBuffers {
 
 static int mem_cap(int mem) { return mem <= 4 ? 4 : (mem <= 10 ? 10 : (mem <= 16 ? 16 : 32)); }
 
+constexpr int DOTS_GRP = 16;      // blocks per group of the two-level reduction
+constexpr int DOTS_MAX_GRP = 60;  // groups the counter buffer has room for
+
+// Accept and dots in one pass (memory caps whose 5 (MCAP + 1) + 7 sums fit in 64 registers):
+// each element of x, g, x_t, g_t and of every live history pair is read once; the thread
+// keeps all the sums of its elements, a warp reduce-scatter leaves two per lane, the warps are
+// added in a fixed order, and the last block (ticket) adds the blocks in a fixed order and
+// runs the scalar part of the iteration.
+template <int MCAP>
+__global__ void __launch_bounds__(256) lbfgs_accept_dots_kernel(SolverArgs a) {
+  constexpr int NS = MCAP + 1;
+  constexpr int NV = 5 * NS + 7;
+  static_assert(NV <= 64, "too many sums for the one-pass kernel");
+  __shared__ double red[8][64];
+  __shared__ double fin[64];
+  __shared__ bool is_last;
+  SolverState* st = a.st;
+  if (!st->active) return;
+  const bool accepted = st->ls.state == LS_ACCEPTED;
+  unsigned int live = 0;
+  for (int q = 0; q < st->count; ++q) live |= 1u << st->ids[q];
+  const int64_t N = a.N, sp = st->spare;
+  float acc[64];
+#pragma unroll
+  for (int v = 0; v < 64; ++v) acc[v] = 0.f;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x) {
+    float gc, s = 0.f, y = 0.f;
+    if (accepted) {
+      const float xo = a.x[e], xn = a.xt[e], go = a.g[e], gn = a.gt[e];
+      s = xn - xo;
+      y = gn - go;
+      a.S[sp * N + e] = s;
+      a.Y[sp * N + e] = y;
+      a.x[e] = xn;
+      a.g[e] = gn;
+      gc = gn;
+    } else {
+      gc = a.g[e];
+    }
+    // All slots are loaded first (every slot lies inside the history buffers), so that the
+    // loads are in flight together; only the sums of the live slots are updated.
+    float sv[NS], yv[NS];
+#pragma unroll
+    for (int j = 0; j < NS; ++j) {
+      sv[j] = a.S[(int64_t)j * N + e];
+      yv[j] = a.Y[(int64_t)j * N + e];
+    }
+#pragma unroll
+    for (int j = 0; j < NS; ++j) {
+      if ((live >> j) & 1u) {
+        acc[5 * j + 0] = fmaf(sv[j], gc, acc[5 * j + 0]);
+        acc[5 * j + 1] = fmaf(yv[j], gc, acc[5 * j + 1]);
+        acc[5 * j + 2] = fmaf(sv[j], y, acc[5 * j + 2]);
+        acc[5 * j + 3] = fmaf(s, yv[j], acc[5 * j + 3]);
+        acc[5 * j + 4] = fmaf(y, yv[j], acc[5 * j + 4]);
+      }
+    }
+    acc[5 * NS + 0] = fmaf(s, gc, acc[5 * NS + 0]);
+    acc[5 * NS + 1] = fmaf(y, gc, acc[5 * NS + 1]);
+    acc[5 * NS + 2] = fmaf(s, y, acc[5 * NS + 2]);
+    acc[5 * NS + 3] = fmaf(y, y, acc[5 * NS + 3]);
+    acc[5 * NS + 4] = fmaf(s, s, acc[5 * NS + 4]);
+    acc[5 * NS + 5] = fmaf(gc, gc, acc[5 * NS + 5]);
+    acc[5 * NS + 6] += fabsf(gc);
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int base = 0;
+  ReduceScatter<64, 16>::run(acc, lane, base);
+  red[w][base] = (double)acc[0];
+  red[w][base + 1] = (double)acc[1];
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    double t = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q][threadIdx.x];
+    a.blk[(int64_t)blockIdx.x * 64 + threadIdx.x] = t;
+  }
+  // Two-level ticket tree (one L2 round trip per level instead of one per block): the last
+  // block of each group of DOTS_GRP blocks sums the group, the last group sums the groups.
+  const int nb = (int)gridDim.x, grp = blockIdx.x / DOTS_GRP, ngrp = (nb + DOTS_GRP - 1) / DOTS_GRP;
+  const int gsize = min(DOTS_GRP, nb - grp * DOTS_GRP);
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) is_last = atomicAdd(a.counter + 1 + grp, 1u) == (unsigned)gsize - 1;
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  double* gblk = a.blk + (int64_t)nb * 64;
+  if (threadIdx.x < 64) {
+    double t = 0.0;
+#pragma unroll
+    for (int u = 0; u < DOTS_GRP; ++u)
+      if (u < gsize) t += __ldcg(&a.blk[(int64_t)(grp * DOTS_GRP + u) * 64 + threadIdx.x]);
+    gblk[grp * 64 + threadIdx.x] = t;
+  }
+  if (threadIdx.x == 0) a.counter[1 + grp] = 0u;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) is_last = atomicAdd(a.counter, 1u) == (unsigned)ngrp - 1;
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  if (threadIdx.x < 64) {
+    double t = 0.0;
+#pragma unroll 8
+    for (int q = 0; q < ngrp; ++q) t += __ldcg(&gblk[q * 64 + threadIdx.x]);
+    fin[threadIdx.x] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *a.counter = 0u;
+  scalar_tail<NS>(st, fin);
+}
+
 template <int MCAP>
 static cudaError_t launch_update(const SolverArgs& a, int grid, cudaStream_t s) {
-  lbfgs_accept_kernel<<<grid, 256, 0, s>>>(a);
-  const int gx = std::max(1, grid / (MCAP + 2));
-  lbfgs_dots_kernel<MCAP><<<dim3(gx, MCAP + 2), 256, 0, s>>>(a);
+  if constexpr (5 * (MCAP + 1) + 7 <= 64) {
+    lbfgs_accept_dots_kernel<MCAP><<<grid, 256, 0, s>>>(a);
+  } else {
+    lbfgs_accept_kernel<<<grid, 256, 0, s>>>(a);
+    const int gx = std::max(1, grid / (MCAP + 2));
+    lbfgs_dots_kernel<MCAP><<<dim3(gx, MCAP + 2), 256, 0, s>>>(a);
+  }
   return cudaGetLastError();
 }
 template <int MCAP>
@@ -507,6 +674,9 @@ static cudaError_t launch_direction(const SolverArgs& a, int grid, cudaStream_t 
   lbfgs_direction_kernel<MCAP><<<grid, 256, 0, s>>>(a);
   return cudaGetLastError();
 }
+
+// Kernels launched by update_and_direction.
+static int update_launches(int mcap) { return 5 * (mcap + 1) + 7 <= 64 ? 2 : 3; }
 
 static cudaError_t update_and_direction(int mcap, const SolverArgs& a, int grid, cudaStream_t s) {
   cudaError_t e;
@@ -594,13 +764,16 @@ static rpca_status ensure_solver(rpca_ctx* c) {
   b->d = b->gt + N;
   SOL_CUDA(cudaMalloc(&b->S, sizeof(float) * 2 * (mcap + 1) * N));
   b->Y = b->S + (int64_t)(mcap + 1) * N;
+  SOL_CUDA(cudaMemset(b->S, 0, sizeof(float) * 2 * (mcap + 1) * N));
   SOL_CUDA(cudaMalloc(&b->st, sizeof(SolverState)));
   SOL_CUDA(cudaMemset(b->st, 0, sizeof(SolverState)));
   SOL_CUDA(cudaMallocHost(&b->host, sizeof(SolverState)));
-  b->grid = (int)std::max<int64_t>(1, std::min<int64_t>(2LL * c->nsm, (N + 255) / 256));
-  SOL_CUDA(cudaMalloc(&b->blk, sizeof(double) * 7 * ((size_t)b->grid + 64) * (mcap + 2)));
-  SOL_CUDA(cudaMalloc(&b->counter, 64));
-  SOL_CUDA(cudaMemset(b->counter, 0, 64));
+  const int64_t grid_cap = std::min<int64_t>(2LL * c->nsm, (int64_t)DOTS_GRP * DOTS_MAX_GRP);
+  b->grid = (int)std::max<int64_t>(1, std::min<int64_t>(grid_cap, (N + 255) / 256));
+  SOL_CUDA(cudaMalloc(&b->blk, sizeof(double) * std::max<size_t>(7 * ((size_t)b->grid + 64) * (mcap + 2),
+                                                                  64 * ((size_t)b->grid + DOTS_MAX_GRP))));
+  SOL_CUDA(cudaMalloc(&b->counter, sizeof(unsigned int) * (1 + DOTS_MAX_GRP + 3)));
+  SOL_CUDA(cudaMemset(b->counter, 0, sizeof(unsigned int) * (1 + DOTS_MAX_GRP + 3)));
   SOL_CUDA(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
   SOL_CUDA(cudaStreamCreateWithFlags(&b->cap2, cudaStreamNonBlocking));
 
@@ -667,7 +840,7 @@ static rpca_status solver_start(rpca_ctx* c) {
                                               c->opt.ls_noise);
   SOL_CUDA(cudaGetLastError());
   SOL_CUDA(update_and_direction(b->mcap, solver_args(c), b->grid, c->stream));
-  count_launches(c, 4);
+  count_launches(c, 1 + update_launches(b->mcap));
   return RPCA_OK;
 }
 
@@ -691,9 +864,10 @@ rpca_status solver_prepare(rpca_ctx* c, const float* U, const float* V) {
 rpca_status solver_iterations(rpca_ctx* c, int count) {
   for (int i = 0; i < count; ++i) SOL_CUDA(cudaGraphLaunch(c->sol->exec, c->stream));
   c->graph_launches += count;
-  // Kernels inside: accept + dots + direction per launch; the while body (fused kernel,
-  // finalize, line-search step) is added from the trial count when the solve finishes.
-  count_launches(c, 3LL * count);
+  // Kernels inside: accept + dots (one kernel for small memory caps) + direction per launch;
+  // the while body (fused kernel, finalize, line-search step) is added from the trial count
+  // when the solve finishes.
+  count_launches(c, (int64_t)update_launches(c->sol->mcap) * count);
   return RPCA_OK;
 }
 

@@ -6,6 +6,7 @@ namespace rpca {
 
 constexpr int SOLVER_MAX_SLOTS = 33;  // history slots: memory cap (<= 32) + 1 spare
 constexpr int SOLVER_LOG = 256;       // per-iteration log ring
+constexpr int SOLVER_TLOG = 256;      // per-trial log ring
 
 enum { LS_RUNNING = 0, LS_ACCEPTED = 1, LS_FAILED = 2, LS_NONE = 3 };
 enum { STOP_NONE = 0, STOP_GTOL = 1, STOP_MAXITER = 2, STOP_LSFAIL = 3, STOP_CERT = 4, STOP_TIMEOUT = 5,
@@ -15,8 +16,9 @@ struct LineSearch {
   double f0, g0;                  // phi(0), phi'(0)
   double a;                       // current trial step
   double a_prev, f_prev, g_prev;  // previous trial of the bracketing phase
-  double lo, flo, glo;            // zoom bracket end with the lower objective
-  double hi, fhi, ghi;            // other bracket end
+  double lo, flo, glo;            // zoom bracket, left end: phi'(lo) < 0, phi(lo) <= phi(0) + noise
+  double hi, fhi, ghi;            // right end: phi'(hi) >= 0 or phi(hi) too large
+  double width_prev;              // bracket width before the last zoom trial
   double f_acc;                   // objective at the accepted step
   double best_a, best_gg;         // trial with the smallest ||g||^2 among those with f <= f(0) + noise
   int force;                      // the current trial is the fallback: accept it
@@ -43,6 +45,10 @@ struct SolverState {
   // outcome (LS_*), history pairs in use}, newest at (log_n - 1) % SOLVER_LOG.
   int log_n;
   double log[SOLVER_LOG][7];
+  // Per-trial log ring: {iteration, trial step a, f(a) - f(0), phi'(a) / |phi'(0)|, ||g(a)||^2,
+  // phase (0 bracketing, 1 zoom), trial number}, newest at (tlog_n - 1) % SOLVER_TLOG.
+  int tlog_n;
+  double tlog[SOLVER_TLOG][7];
 };
 
 }  // namespace rpca

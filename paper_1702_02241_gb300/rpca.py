@@ -86,6 +86,8 @@ def lib():
     L.rpca_profile_read.restype = I
     L.rpca_solve_log.argtypes = [P, C.POINTER(C.c_double), I, C.POINTER(C.c_int)]
     L.rpca_solve_log.restype = I
+    L.rpca_solve_trials.argtypes = [P, C.POINTER(C.c_double), I, C.POINTER(C.c_int)]
+    L.rpca_solve_trials.restype = I
     L.rpca_fg_noalloc.argtypes = [I64, I64, P, I64, I, D, D, P, P, C.POINTER(C.c_double), P, P, P]
     L.rpca_fg_noalloc.restype = I
     L.rpca_version.argtypes = []
@@ -96,7 +98,7 @@ def lib():
 
 EXPORTED = ["rpca_default_options", "rpca_create", "rpca_fg", "rpca_apply", "rpca_init_sketch", "rpca_solve",
             "rpca_certificate", "rpca_destroy", "rpca_last_error", "rpca_version", "rpca_plan_info",
-            "rpca_profile", "rpca_profile_read", "rpca_solve_log", "rpca_fg_noalloc"]
+            "rpca_profile", "rpca_profile_read", "rpca_solve_log", "rpca_solve_trials", "rpca_fg_noalloc"]
 
 
 class RpcaError(RuntimeError):
@@ -206,6 +208,14 @@ def rpca_solve_log(ctx, max_rows=256):
     out = (C.c_double * (7 * max_rows))()
     rows = C.c_int(0)
     _check(lib().rpca_solve_log(ctx, out, max_rows, C.byref(rows)), ctx)
+    return [list(out[7 * i:7 * i + 7]) for i in range(rows.value)]
+
+
+def rpca_solve_trials(ctx, max_rows=256):
+    """Rows {iteration, a, f(a) - f(0), phi'(a)/|phi'(0)|, ||g(a)||^2, phase, trial} of the last solve."""
+    out = (C.c_double * (7 * max_rows))()
+    rows = C.c_int(0)
+    _check(lib().rpca_solve_trials(ctx, out, max_rows, C.byref(rows)), ctx)
     return [list(out[7 * i:7 * i + 7]) for i in range(rows.value)]
 
 
