@@ -107,7 +107,8 @@ typedef struct {
 RPCA_API void rpca_default_options(rpca_options *opt);
 
 /*
- * Creates a solver context for X (m x n, device, column-major, ldx >= m; ldx * 4 must be a
+ * Creates a solver context for X (m x n with 1 <= m, n <= 2^27, device, column-major,
+ * ldx >= m; ldx * 4 must be a
  * multiple of 16 bytes and X 16-byte aligned, as the tiled TMA copies require), an optional
  * observation mask (device uint8, m x n column-major with ldmask >= m, nonzero = observed,
  * NULL = all observed; Sec. 6.2), factor rank k (1..16), lambda_L > 0 and lambda_S > 0

@@ -243,11 +243,15 @@ static rpca_status time_plan(rpca_ctx* c, const FgPlan& q, double* ms) {
 
 // ---- launch planning -----------------------------------------------------------------------
 // Chooses consumer warps per CTA (WC) and the column split (ncs, BN).  A time model ranks
-// the configurations that fit (whole waves of tiles at full bandwidth, a partly filled last
-// wave costing at least half a wave, plus the write and re-read of the partial sums); the
-// twelve best are then timed on the device and the fastest is kept (cached per shape in
-// this process).  RPCA_PLAN="warps,splits" forces one configuration; RPCA_AUTOTUNE=0 keeps the
-// model's choice without timing.
+// the configurations that fit: an SM streams its tiles at a bounded rate (the kernel is
+// limited per SM by issue as much as by HBM), so the time is the larger of the busiest SM's
+// bytes (waves of cps tiles) at that rate and all bytes at the HBM rate, plus the write and
+// re-read of the partial sums.  The twelve best are then timed on the device and the fastest
+// is kept (cached per shape in this process).  RPCA_PLAN="warps,splits" forces one
+// configuration; RPCA_AUTOTUNE=0 keeps the model's choice without timing.
+// Cache code of a plan's kernel configuration (warps, stages).
+static int plan_code(const FgPlan& q) { return q.WC * 16 + q.nstage; }
+
 static rpca_status make_plan(rpca_ctx* c, FgPlan* P, int K, int B, bool same, int side) {
   const bool masked = c->bits != nullptr;
   const FgVariant* v = fg_variant(K, B, same, masked, side);
@@ -292,14 +296,19 @@ static rpca_status make_plan(rpca_ctx* c, FgPlan* P, int K, int B, bool same, in
         ++n_occ;
         continue;
       }
-      const double slots = (double)c->nsm * cps;
       const double tiles = (double)nrb * ncs;
       const double tile_bytes = (double)BM * BN * 4.0 * (masked ? 33.0 / 32.0 : 1.0);
-      const double full_waves = std::floor(tiles / slots);
-      const double rem = tiles - full_waves * slots;
-      double t = full_waves * slots * tile_bytes;
-      if (rem > 0) t += std::max(rem, 0.5 * slots) * tile_bytes;
-      t += 2.0 * 4.0 * ((double)ncs * c->mpad * B + (double)nrb * c->n * B);
+      // The busiest SM holds kt tiles, cw of them at a time; its rate grows with the consumer
+      // warps resident on it up to about eight.
+      constexpr double SM_GBS = 30.0, HBM_GBS = 6700.0;  // per-SM streaming rate, whole-GPU rate
+      const double kt = std::ceil(tiles / c->nsm);
+      const double cw = std::min<double>(cps, kt);
+      const double waves = std::ceil(kt / cw);
+      const double rate = SM_GBS * std::min(1.0, cw * WC / 8.0);
+      const double t_sm = waves * cw * tile_bytes / rate;
+      const double t_hbm = tiles * tile_bytes / HBM_GBS;
+      double t = std::max(t_sm, t_hbm);
+      t += 2.0 * 4.0 * ((double)ncs * c->mpad * B + (double)nrb * c->n * B) / HBM_GBS;
       FgPlan cand;
       cand.valid = true;
       cand.var = v;
@@ -333,10 +342,8 @@ static rpca_status make_plan(rpca_ctx* c, FgPlan* P, int K, int B, bool same, in
             [](const std::pair<double, FgPlan>& a, const std::pair<double, FgPlan>& b) { return a.first < b.first; });
   for (auto& cp : cands) {
     FgPlan& q = cp.second;
-    // Finalize grid: about two waves of blocks for the m x B side (four elements in flight
-    // per thread per pass), one wave of warps (one element each) for the n x B side.
-    q.fin_gu = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)c->m * B + 1023) / 1024, 2LL * c->nsm));
-    q.fin_gv = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)c->n * B + 7) / 8, (int64_t)c->nsm));
+    q.fin_gu = fin_grid_u(c->m, B);
+    q.fin_gv = fin_grid_v(c->n, B);
     q.fin_grid = q.fin_gu + q.fin_gv;
   }
   // Cached choice for this shape, or measure the best few candidates of the model.
@@ -346,8 +353,7 @@ static rpca_status make_plan(rpca_ctx* c, FgPlan* P, int K, int B, bool same, in
   const bool measure = !(force_wc || force_ncs) && autotune_enabled() && cands.size() > 1;
   if (measure && plan_cache_get(key, &cached_wc, &cached_ncs)) {
     for (size_t i = 0; i < cands.size(); ++i)
-      if (cands[i].second.WC * 16 + cands[i].second.nstage == cached_wc && cands[i].second.ncs == cached_ncs)
-        pick = (int)i;
+      if (plan_code(cands[i].second) == cached_wc && cands[i].second.ncs == cached_ncs) pick = (int)i;
   } else if (measure) {
     const int ntry = (int)std::min<size_t>(same ? 12 : 6, cands.size());
     double best_ms = 1e300;
@@ -363,7 +369,7 @@ static rpca_status make_plan(rpca_ctx* c, FgPlan* P, int K, int B, bool same, in
         pick = i;
       }
     }
-    plan_cache_put(key, cands[pick].second.WC * 16 + cands[pick].second.nstage, cands[pick].second.ncs);
+    plan_cache_put(key, plan_code(cands[pick].second), cands[pick].second.ncs);
   }
   FgPlan bp = cands[pick].second;
   rpca_status s = finish_plan(c, &bp);
@@ -475,6 +481,7 @@ rpca_status launch_fg(rpca_ctx* c, const FgPlan& P, const FgLaunch& L, cudaStrea
   f.alpha_dev = L.alpha_dev;
   f.gate = L.gate;
   f.lam_L = c->lam_L;
+  f.lam_f = (float)c->lam_L;
   f.GU = L.GU;
   f.GV = L.GV;
   f.Ut = L.Ut;
@@ -588,8 +595,9 @@ rpca_status rpca_create(rpca_ctx** out, int64_t m, int64_t n, const float* X, in
                         void* cuda_stream) {
   if (!out) return set_err(nullptr, RPCA_EINVAL, "out is NULL");
   *out = nullptr;
-  if (m < 1 || n < 1 || m > (1LL << 30) || n > (1LL << 30))
-    return set_err(nullptr, RPCA_EINVAL, "m and n must be in [1, 2^30]");
+  // m and n up to 2^27: every (row or column) x (block of <= 16 columns) index fits 31 bits.
+  if (m < 1 || n < 1 || m > (1LL << 27) || n > (1LL << 27))
+    return set_err(nullptr, RPCA_EINVAL, "m and n must be in [1, 2^27]");
   if ((m * n) > (1LL << 40)) return set_err(nullptr, RPCA_EINVAL, "m * n too large");
   if (!X) return set_err(nullptr, RPCA_EINVAL, "X is NULL");
   if (ldx < m) return set_err(nullptr, RPCA_EINVAL, "ldx < m");

@@ -161,6 +161,7 @@ __global__ void __launch_bounds__(288) fg_kernel(const __grid_constant__ CUtenso
     if (lane == 0) {
       prefetch_tmap(&tmX);
       if (MASKED) prefetch_tmap(&tmM);
+      const uint64_t pol = l2_evict_first_policy();  // X and its bitmap are streamed once per pass
       int issued = 0;
       bool ok = true;
       for (int c = 0; c < nchunks; ++c) {
@@ -173,8 +174,10 @@ __global__ void __launch_bounds__(288) fg_kernel(const __grid_constant__ CUtenso
         }
         mbar_arrive_expect_tx(&full[s], stage_bytes);
         for (int w = 0; w < WC; ++w)
-          tma_load_2d(xs_all + ((size_t)s * WC + w) * xbox, &tmX, row0 + w * ROWS_W, col0 + c * FG_BJ, &full[s]);
-        if constexpr (MASKED) tma_load_2d(ms_all + (size_t)s * mstage, &tmM, row0 / 32, col0 + c * FG_BJ, &full[s]);
+          tma_load_2d_hint(xs_all + ((size_t)s * WC + w) * xbox, &tmX, row0 + w * ROWS_W, col0 + c * FG_BJ, &full[s],
+                           pol);
+        if constexpr (MASKED)
+          tma_load_2d_hint(ms_all + (size_t)s * mstage, &tmM, row0 / 32, col0 + c * FG_BJ, &full[s], pol);
         issued = c + 1;
       }
       // Wait (bounded) until every copy this thread issued has landed before leaving.
@@ -250,7 +253,9 @@ __global__ void __launch_bounds__(288) fg_kernel(const __grid_constant__ CUtenso
   for (int p = 0; p < NP; ++p)
 #pragma unroll
     for (int b = 0; b < (ROWSIDE ? B : 1); ++b) gu[p][b] = f2(0.f, 0.f);
-  double psi_d = 0.0;
+  // Sum of psi over the lane's elements: float32 with Kahan compensation (a float64 add per
+  // chunk would occupy this GPU's narrow float64 pipe); float64 once per tile.
+  float psi_s = 0.f, psi_c = 0.f;
   const float lam = a.lam_S;
   const float2 mhalf = f2(-0.5f, -0.5f);
   bool failed = false;
@@ -360,7 +365,12 @@ __global__ void __launch_bounds__(288) fg_kernel(const __grid_constant__ CUtenso
       }
       }
     }
-    psi_d += (double)psi2.x + (double)psi2.y;
+    {
+      const float y = (psi2.x + psi2.y) - psi_c;
+      const float t = psi_s + y;
+      psi_c = (t - psi_s) - y;
+      psi_s = t;
+    }
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[s]);
   }
@@ -376,7 +386,7 @@ __global__ void __launch_bounds__(288) fg_kernel(const __grid_constant__ CUtenso
     }
   }
   // Sum of psi over the tile; column sums over the consumer warps in fixed order.
-  psi_d = warp_sum_d(psi_d);
+  double psi_d = warp_sum_d((double)psi_s - (double)psi_c);
   if (lane == 0) scr[warp] = psi_d;
   named_bar(1, nct);
   if (tid == 0) {

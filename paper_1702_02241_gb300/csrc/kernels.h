@@ -1,5 +1,6 @@
 // Declarations shared by the kernel translation units and the host API.
 #pragma once
+#include <algorithm>
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -26,6 +27,7 @@ struct FinArgs {
   const double* alpha_dev;  // when non-null, the step is read from here
   const int* gate;          // when non-null and *gate == 0 the launch does nothing
   double lam_L;
+  float lam_f;  // lam_L as float32 (converted on the host)
   float* GU;  // m x B (ld m): G_U (fg) or D Bv (apply)
   float* GV;  // n x B (ld n): G_V (fg) or D^T Bu (apply)
   float* Ut;  // optional copy of the trial point
@@ -36,6 +38,11 @@ struct FinArgs {
   unsigned int* counter;    // zero between launches (reset by the last block)
   double* out;              // [4]: f, g.d, ||g||^2, ||x_t||^2
 };
+
+// Finalize grid: one thread per element of the m x B side, 64 elements (four groups of 64
+// threads splitting the row-block partials) per block on the n x B side.
+inline int fin_grid_u(int64_t m, int B) { return (int)std::max<int64_t>(1, (m * B + 255) / 256); }
+inline int fin_grid_v(int64_t n, int B) { return (int)std::max<int64_t>(1, (n * B + 63) / 64); }
 
 __global__ void finalize_kernel(FinArgs a);
 __global__ void finalize_reduce_kernel(FinArgs a, int nblocks);

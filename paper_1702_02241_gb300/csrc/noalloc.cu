@@ -52,7 +52,7 @@ using namespace rpca;
 extern "C" rpca_status rpca_fg_noalloc(int64_t m, int64_t n, const float* X, int64_t ldx, int k, double lambda_L,
                                        double lambda_S, const float* U, const float* V, double* f, float* gU,
                                        float* gV, void* cuda_stream) {
-  if (m < 1 || n < 1 || m > (1LL << 30) || n > (1LL << 30)) return set_err_noctx(RPCA_EINVAL, "m and n out of range");
+  if (m < 1 || n < 1 || m > (1LL << 27) || n > (1LL << 27)) return set_err_noctx(RPCA_EINVAL, "m and n out of range");
   if (!X || !U || !V || !gU || !gV) return set_err_noctx(RPCA_EINVAL, "X, U, V, gU and gV are required");
   if (ldx < m || (ldx * 4) % 16 != 0 || (reinterpret_cast<uintptr_t>(X) & 15) != 0)
     return set_err_noctx(RPCA_EINVAL, "X must be 16-byte aligned with ldx >= m a multiple of 4");
@@ -93,8 +93,8 @@ extern "C" rpca_status rpca_fg_noalloc(int64_t m, int64_t n, const float* X, int
     if (smem <= (size_t)smem_optin || BN <= FG_BJ) break;
   }
   if (smem > (size_t)smem_optin) return set_err_noctx(RPCA_EUNSUPPORTED, "no launch configuration fits");
-  const int fin_gu = (int)std::max<int64_t>(1, std::min<int64_t>((m * k + 1023) / 1024, 2LL * nsm));
-  const int fin_gv = (int)std::max<int64_t>(1, std::min<int64_t>((n * k + 7) / 8, (int64_t)nsm));
+  const int fin_gu = fin_grid_u(m, k);
+  const int fin_gv = fin_grid_v(n, k);
   const int fin_grid = fin_gu + fin_gv;
 
   // Scratch carve-up: partial sums, per-CTA psi sums, finalize block partials, counter,
@@ -169,6 +169,7 @@ extern "C" rpca_status rpca_fg_noalloc(int64_t m, int64_t n, const float* X, int
   fa.U = U;
   fa.V = V;
   fa.lam_L = lambda_L;
+  fa.lam_f = (float)lambda_L;
   fa.GU = gU;
   fa.GV = gV;
   fa.blk = reinterpret_cast<double*>(base + off_blk);

@@ -39,85 +39,109 @@ RPCA_DEV void block_sum3(double& x, double& y, double& z, double (*scr)[3]) {
   }
 }
 
-// Blocks [0, a.gu) handle the m x B side (threads stride over elements, four independent
-// loads in flight); blocks [a.gu, gridDim.x) handle the n x B side, one element per warp,
-// the lanes splitting the row-block partials (fixed-order shuffle sum).  Each block writes
-// its partial dot products; finalize_reduce_kernel combines them (no atomics, no fences).
+// Gradient assembly.  Blocks [0, a.gu) handle the m x B side, one thread per element: the
+// column-split partials of PU are summed (coalesced, loads unrolled) and G_U = lam_L U_t - PU
+// (fg) or D Bv = -PU (apply) is written.  The other blocks handle the n x B side, 64 elements
+// per block: four groups of 64 threads each sum every fourth row-block partial of PV
+// (coalesced across consecutive columns) and the groups are added in a fixed order.
+// Elementwise work is float32 (the partial sums are float32 already); each block's dot
+// products (||x_t||^2, g.d, ||g||^2) go to float64 for the fixed-order block sums.
 __global__ void __launch_bounds__(256) finalize_kernel(FinArgs a) {
   __shared__ double scr[32][3];
+  __shared__ float vs[4][64];
+  __shared__ float alpha_s;
   if (a.gate != nullptr && *a.gate == 0) return;
-  const float alpha = a.alpha_dev ? (float)*a.alpha_dev : a.alpha;
-  const float lam = (float)a.lam_L;
-  const int64_t mB = (int64_t)a.m * a.B, nB = (int64_t)a.n * a.B;
-  // Element-wise work in float32 (GB300's float64 pipe is ~1/64 of float32; the partial
-  // sums are float32 already); each thread's dot products go to float64 once at the end.
+  // Conversions from float64 and 64-bit divisions run on the float64 pipe, which is narrow on
+  // this GPU: the step is converted once per block, indices use 32-bit unsigned division
+  // (m B and n B are below 2^31, checked when the context is created).
+  if (threadIdx.x == 0) alpha_s = a.alpha_dev ? (float)*a.alpha_dev : a.alpha;
+  __syncthreads();
+  const float alpha = alpha_s;
+  const float lam = a.lam_f;
+  const unsigned mB = (unsigned)a.m * (unsigned)a.B, nB = (unsigned)a.n * (unsigned)a.B;
   float nrm_f = 0.f, gd_f = 0.f, gg_f = 0.f;
   if ((int)blockIdx.x < a.gu) {
-    const int64_t stride = (int64_t)a.gu * blockDim.x;
-    for (int64_t e0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a.side != 2 && e0 < mB; e0 += 4 * stride) {
-      float sv[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int64_t e = e0 + u * stride;
-        sv[u] = 0.f;
-        if (e < mB) {
-          const int l = (int)(e / a.m), i = (int)(e - (int64_t)l * a.m);
-          for (int c = 0; c < a.ncs; ++c) sv[u] += a.PU[((int64_t)c * a.B + l) * a.mpad + i];
-        }
+    const unsigned e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a.side != 2 && e < mB) {
+      const unsigned l = e / (unsigned)a.m, i = e - l * (unsigned)a.m;
+      const float* pu = a.PU + (int64_t)l * a.mpad + i;
+      const int64_t cstride = (int64_t)a.B * a.mpad;
+      float s = 0.f;
+#pragma unroll 8
+      for (int c = 0; c < a.ncs; ++c) s += pu[c * cstride];
+      float g, xt = 0.f, dir = 0.f;
+      if (a.mode != FIN_APPLY) {
+        xt = a.U[e];
+        if (a.dU) xt = fmaf(alpha, a.dU[e], xt);
+        g = a.mode == FIN_FG ? fmaf(lam, xt, -s) : -s;
+        if (a.Ut) a.Ut[e] = xt;
+        if (a.DU) dir = a.DU[e];
+      } else {
+        g = -s;
       }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int64_t e = e0 + u * stride;
-        if (e >= mB) break;
-        const float s = sv[u];
-        float g, xt = 0.f, dir = 0.f;
-        if (a.mode != FIN_APPLY) {
-          xt = a.U[e];
-          if (a.dU) xt = fmaf(alpha, a.dU[e], xt);
-          g = a.mode == FIN_FG ? fmaf(lam, xt, -s) : -s;
-          if (a.Ut) a.Ut[e] = xt;
-          if (a.DU) dir = a.DU[e];
-        } else {
-          g = -s;
-        }
-        a.GU[e] = g;
-        nrm_f = fmaf(xt, xt, nrm_f);
-        gd_f = fmaf(g, dir, gd_f);
-        gg_f = fmaf(g, g, gg_f);
-      }
+      a.GU[e] = g;
+      nrm_f = xt * xt;
+      gd_f = g * dir;
+      gg_f = g * g;
     }
   } else {
-    const int lane = threadIdx.x & 31;
-    const int64_t warps = (int64_t)(gridDim.x - a.gu) * (blockDim.x >> 5);
-    for (int64_t e2 = (int64_t)(blockIdx.x - a.gu) * (blockDim.x >> 5) + (threadIdx.x >> 5); a.side != 1 && e2 < nB;
-         e2 += warps) {
-      const int l = (int)(e2 / a.n), j = (int)(e2 - (int64_t)l * a.n);
-      float s = 0.f;
-      for (int r = lane; r < a.nrb; r += 32) s += a.PV[((int64_t)r * a.B + l) * a.n + j];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) {
-        float g, xt = 0.f, dir = 0.f;
-        if (a.mode != FIN_APPLY) {
-          xt = a.V[e2];
-          if (a.dV) xt = fmaf(alpha, a.dV[e2], xt);
-          g = a.mode == FIN_FG ? fmaf(lam, xt, s) : s;
-          if (a.Vt) a.Vt[e2] = xt;
-          if (a.DV) dir = a.DV[e2];
-        } else {
-          g = s;
-        }
-        a.GV[e2] = g;
-        nrm_f = fmaf(xt, xt, nrm_f);
-        gd_f = fmaf(g, dir, gd_f);
-        gg_f = fmaf(g, g, gg_f);
+    const int q = threadIdx.x >> 6, t = threadIdx.x & 63;
+    const unsigned e2 = (blockIdx.x - a.gu) * 64 + t;
+    const bool live = a.side != 1 && e2 < nB;
+    unsigned l = 0, j = 0;
+    float s = 0.f;
+    if (live) {
+      l = e2 / (unsigned)a.n;
+      j = e2 - l * (unsigned)a.n;
+      const float* pv = a.PV + (int64_t)l * a.n + j;
+      const int64_t rstride = (int64_t)a.B * a.n;
+#pragma unroll 4
+      for (int r = q; r < a.nrb; r += 4) s += pv[r * rstride];
+    }
+    vs[q][t] = s;
+    __syncthreads();
+    if (q == 0 && live) {
+      s = (vs[0][t] + vs[1][t]) + (vs[2][t] + vs[3][t]);
+      float g, xt = 0.f, dir = 0.f;
+      if (a.mode != FIN_APPLY) {
+        xt = a.V[e2];
+        if (a.dV) xt = fmaf(alpha, a.dV[e2], xt);
+        g = a.mode == FIN_FG ? fmaf(lam, xt, s) : s;
+        if (a.Vt) a.Vt[e2] = xt;
+        if (a.DV) dir = a.DV[e2];
+      } else {
+        g = s;
       }
+      a.GV[e2] = g;
+      nrm_f = xt * xt;
+      gd_f = g * dir;
+      gg_f = g * g;
     }
   }
   if (a.mode == FIN_APPLY) return;
-  double nrm = nrm_f, gd = gd_f, gg = gg_f;
-  block_sum3(nrm, gd, gg, scr);
+  // Warp sums in float32 (float64 is slow on this GPU: a float64 tree over every thread of
+  // the grid costs more than the whole assembly), then float64 across the warps.
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    nrm_f += __shfl_xor_sync(0xffffffffu, nrm_f, o);
+    gd_f += __shfl_xor_sync(0xffffffffu, gd_f, o);
+    gg_f += __shfl_xor_sync(0xffffffffu, gg_f, o);
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) {
+    scr[w][0] = nrm_f;
+    scr[w][1] = gd_f;
+    scr[w][2] = gg_f;
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
+    double nrm = 0.0, gd = 0.0, gg = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+      nrm += scr[i][0];
+      gd += scr[i][1];
+      gg += scr[i][2];
+    }
     a.blk[3 * blockIdx.x + 0] = nrm;
     a.blk[3 * blockIdx.x + 1] = gd;
     a.blk[3 * blockIdx.x + 2] = gg;
@@ -130,6 +154,7 @@ __global__ void __launch_bounds__(256) finalize_reduce_kernel(FinArgs a, int nbl
   __shared__ double scr[32][3];
   if (a.gate != nullptr && *a.gate == 0) return;
   double p0 = 0.0, p1 = 0.0, p2 = 0.0, ps = 0.0;
+#pragma unroll 4
   for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
     p0 += a.blk[3 * b + 0];
     p1 += a.blk[3 * b + 1];
@@ -137,6 +162,7 @@ __global__ void __launch_bounds__(256) finalize_reduce_kernel(FinArgs a, int nbl
   }
   block_sum3(p0, p1, p2, scr);
   __syncthreads();
+#pragma unroll 4
   for (int b = threadIdx.x; b < a.nctas; b += blockDim.x) ps += a.Ppsi[b];
   double d1 = 0.0, d2 = 0.0;
   block_sum3(ps, d1, d2, scr);

@@ -36,6 +36,9 @@ namespace rpca {
 constexpr double LS_C1 = 1e-4, LS_C2 = 0.9, LS_AMAX = 1e10, CURV_EPS = 1e-10;
 constexpr int LS_MAX_TRIALS = 25;
 
+constexpr int DOTS_GRP = 16;      // blocks per group of the two-level reduction
+constexpr int DOTS_MAX_GRP = 60;  // groups the counter buffer has room for
+
 struct SolverArgs {
   SolverState* st;
   int64_t N;
@@ -219,8 +222,11 @@ __device__ void two_loop_coefs(SolverState* st) {
 
 // Scalar part of an iteration: ring update, stopping tests, next direction's coefficients
 // and the line-search start.  `v` holds the reduced inner products (layout: see below).
+// The scalar part of an iteration before the two-loop coefficients: the new pair enters
+// the Gram table (or the memory is reset after a failed search), the history dot products
+// are refreshed, the log record is written, and the stopping tests run.
 template <int NS>
-__device__ void iteration_scalars(SolverState* st, SolverState* logst, const double* v) {
+__device__ void iteration_update(SolverState* st, SolverState* logst, const double* v) {
   const int state = st->ls.state;
   int added = -1;  // slot of the pair added by this step, if any
   const double step = st->ls.a, trials = st->ls.evals;
@@ -297,7 +303,11 @@ __device__ void iteration_scalars(SolverState* st, SolverState* logst, const dou
     st->active = 0;
   }
   if (st->f < st->best_f) st->best_f = st->f;
-  two_loop_coefs(st);
+}
+
+// The rest of the scalar part after the two-loop coefficients: the descent check and the
+// first trial of the next line search.
+__device__ void iteration_finish(SolverState* st) {
   // Descent check on the Gram table; fall back to steepest descent otherwise.
   double gd = st->coef_g * st->gg;
   for (int q = 0; q < st->count; ++q) {
@@ -344,6 +354,62 @@ __global__ void __launch_bounds__(256) lbfgs_accept_kernel(SolverArgs a) {
 //   v[5 NS + 0..6] = s_new.g, y_new.g, s_new.y_new, y_new.y_new, s_new.s_new, g.g, |g|_1
 // Products in float32, summed in float32 over each thread's elements, float64 beyond.
 // The last block to finish runs the scalar part of the iteration.
+// two_loop_coefs run by one warp (count <= 32): lane i holds history pair i (newest first).
+// Both loops of the two-loop recursion are triangular solves; at step j the lane that owns
+// pair j finishes its coefficient, broadcasts it, and every lane that still needs it adds
+// its product -- one broadcast and one FMA per step instead of a dependent dot product.
+// The same terms as two_loop_coefs, each sum taken in the same index order (rounding differs
+// only in that the sum is formed before it is subtracted).
+__device__ void two_loop_coefs_warp(SolverState* st) {
+  const int lane = threadIdx.x & 31;
+  const int n = st->count;
+  for (int j = lane; j < SOLVER_MAX_SLOTS; j += 32) {
+    st->coef_s[j] = 0.0;
+    st->coef_y[j] = 0.0;
+  }
+  __syncwarp();
+  if (n == 0) {
+    if (lane == 0) st->coef_g = -1.0;
+    return;
+  }
+  const bool mine = lane < n;
+  const int id = mine ? st->ids[lane] : 0;
+  const double rho = mine ? 1.0 / st->SY[id][id] : 0.0;
+  const double sg = mine ? st->sg[id] : 0.0, yg = mine ? st->yg[id] : 0.0;
+  // Loop 1 (newest -> oldest): a_i = rho_i (sg_i - sum_{j < i} a_j s_i . y_j).
+  double acc = 0.0, a_mine = 0.0;
+  for (int j = 0; j < n; ++j) {
+    if (lane == j) a_mine = (sg - acc) * rho;
+    const double aj = __shfl_sync(0xffffffffu, a_mine, j);
+    const int idj = st->ids[j];
+    if (mine && lane > j) acc += aj * st->SY[id][idj];
+  }
+  const double gamma = st->SY[st->ids[0]][st->ids[0]] / st->YY[st->ids[0]][st->ids[0]];
+  // y_i . (sum_j a_j y_j), independent per lane.
+  double ay = 0.0;
+  for (int j = 0; j < n; ++j) {
+    const double aj = __shfl_sync(0xffffffffu, a_mine, j);
+    if (mine) ay += aj * st->YY[id][st->ids[j]];
+  }
+  // Loop 2 (oldest -> newest): c_i = a_i - rho_i (gamma (yg_i - ay_i) + sum_{j > i} c_j s_j . y_i).
+  double acc2 = 0.0, c_mine = 0.0;
+  for (int j = n - 1; j >= 0; --j) {
+    if (lane == j) {
+      const double t = (yg - ay) * gamma + acc2;
+      c_mine = a_mine - t * rho;
+    }
+    const double cj = __shfl_sync(0xffffffffu, c_mine, j);
+    const int idj = st->ids[j];
+    if (mine && lane < j) acc2 += cj * st->SY[idj][id];
+  }
+  __syncwarp();
+  if (mine) {
+    st->coef_y[id] = gamma * a_mine;
+    st->coef_s[id] = -c_mine;
+  }
+  if (lane == 0) st->coef_g = -gamma;
+}
+
 // The scalar part of an iteration, run by the last block of the dots reduction: the solver
 // state up to the log rings is copied to shared memory by the whole block, updated there by
 // one thread (a chain of dependent float64 operations, which must not wait on global
@@ -356,9 +422,13 @@ __device__ void scalar_tail(SolverState* gst, const double* fin) {
   const double* src = reinterpret_cast<const double*>(gst);
   for (int i = threadIdx.x; i < SOLVER_CORE_WORDS; i += blockDim.x) core[i] = __ldcg(src + i);
   __syncthreads();
+  SolverState* s = reinterpret_cast<SolverState*>(core);
+  if (threadIdx.x == 0) iteration_update<NS>(s, gst, fin);
+  __syncthreads();
+  if (threadIdx.x < 32) two_loop_coefs_warp(s);
+  __syncthreads();
   if (threadIdx.x == 0) {
-    SolverState* s = reinterpret_cast<SolverState*>(core);
-    iteration_scalars<NS>(s, gst, fin);
+    iteration_finish(s);
     s->gate = s->active;
   }
   __syncthreads();
@@ -440,10 +510,13 @@ __global__ void __launch_bounds__(256) lbfgs_dots_kernel(SolverArgs a) {
 
 // d = c_g g + sum over ring slots (c_s[j] s_j + c_y[j] y_j); then g.d in float64 starts the
 // line search (phi'(0)).
+// d = coef_g g + sum over live pairs (coef_s s_j + coef_y y_j) and phi'(0) = g . d.  Two
+// elements per thread (one for memory caps above 10) with every load in flight; g . d summed in float32 within a warp,
+// float64 across warps, blocks (two-level ticket tree as in the dots kernel).
 template <int MCAP>
 __global__ void __launch_bounds__(256) lbfgs_direction_kernel(SolverArgs a) {
   constexpr int NS = MCAP + 1;
-  __shared__ double scr[32];
+  __shared__ double scr[8];
   __shared__ bool is_last;
   __shared__ float cs[NS], cy[NS];
   __shared__ float cg;
@@ -457,40 +530,78 @@ __global__ void __launch_bounds__(256) lbfgs_direction_kernel(SolverArgs a) {
   }
   if (threadIdx.x == 0) cg = (float)st->coef_g;
   __syncthreads();
-  double gd = 0.0;
+  constexpr int EPT = NS <= 11 ? 2 : 1;  // elements per thread per pass (register budget)
+  float gd_f = 0.f;
   const int64_t N = a.N;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x) {
-    const float ge = a.g[e];
-    float dv = cg * ge;
-    float sv[NS], yv[NS];  // loads first, all in flight together (see the dots kernel)
+  for (int64_t e0 = (int64_t)blockIdx.x * blockDim.x * EPT + threadIdx.x; e0 < N;
+       e0 += (int64_t)gridDim.x * blockDim.x * EPT) {
+    float ge[EPT], sv[EPT][NS], yv[EPT][NS];
 #pragma unroll
-    for (int j = 0; j < NS; ++j) {
-      sv[j] = a.S[(int64_t)j * N + e];
-      yv[j] = a.Y[(int64_t)j * N + e];
-    }
+    for (int u = 0; u < EPT; ++u) {
+      const int64_t e = e0 + u * blockDim.x;
+      const bool in = e < N;
+      ge[u] = in ? a.g[e] : 0.f;
 #pragma unroll
-    for (int j = 0; j < NS; ++j) {
-      if ((live >> j) & 1ull) {
-        dv = fmaf(cs[j], sv[j], dv);
-        dv = fmaf(cy[j], yv[j], dv);
+      for (int j = 0; j < NS; ++j) {
+        sv[u][j] = in ? a.S[(int64_t)j * N + e] : 0.f;
+        yv[u][j] = in ? a.Y[(int64_t)j * N + e] : 0.f;
       }
     }
-    a.d[e] = dv;
-    gd += (double)(ge * dv);
+#pragma unroll
+    for (int u = 0; u < EPT; ++u) {
+      const int64_t e = e0 + u * blockDim.x;
+      float dv = cg * ge[u];
+#pragma unroll
+      for (int j = 0; j < NS; ++j) {
+        if ((live >> j) & 1ull) {
+          dv = fmaf(cs[j], sv[u][j], dv);
+          dv = fmaf(cy[j], yv[u][j], dv);
+        }
+      }
+      if (e < N) {
+        a.d[e] = dv;
+        gd_f = fmaf(ge[u], dv, gd_f);
+      }
+    }
   }
-  gd = block_sum_d(gd, scr);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) gd_f += __shfl_xor_sync(0xffffffffu, gd_f, o);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) scr[w] = gd_f;
+  __syncthreads();
   if (threadIdx.x == 0) {
-    a.blk[blockIdx.x] = gd;
-    __threadfence();
-    is_last = atomicAdd(a.counter, 1u) == gridDim.x - 1;
+    double t = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += scr[q];
+    a.blk[blockIdx.x] = t;
   }
+  const int nb = (int)gridDim.x, grp = blockIdx.x / DOTS_GRP, ngrp = (nb + DOTS_GRP - 1) / DOTS_GRP;
+  const int gsize = min(DOTS_GRP, nb - grp * DOTS_GRP);
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) is_last = atomicAdd(a.counter + 1 + grp, 1u) == (unsigned)gsize - 1;
   __syncthreads();
   if (!is_last) return;
   __threadfence();
-  double t = 0.0;
-  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) t += __ldcg(&a.blk[b]);
-  t = block_sum_d(t, scr);
-  if (threadIdx.x == 0) {
+  // Both levels are summed by warp 0: one load per lane (two at the top), a fixed shuffle tree.
+  double* gblk = a.blk + nb;
+  if (threadIdx.x < 32) {
+    double t = lane < gsize ? __ldcg(&a.blk[grp * DOTS_GRP + lane]) : 0.0;
+    t = warp_sum_d(t);
+    if (lane == 0) {
+      gblk[grp] = t;
+      a.counter[1 + grp] = 0u;
+      __threadfence();
+      is_last = atomicAdd(a.counter, 1u) == (unsigned)ngrp - 1;
+    }
+  }
+  __syncthreads();
+  if (!is_last) return;
+  if (threadIdx.x < 32) {
+    __threadfence();
+    double t = 0.0;
+    for (int q = lane; q < ngrp; q += 32) t += __ldcg(&gblk[q]);
+    t = warp_sum_d(t);
+    if (lane != 0) return;
     *a.counter = 0u;
     LineSearch& L = st->ls;
     L.g0 = t;
@@ -545,9 +656,6 @@ struct SolverBuffers {
 };
 
 static int mem_cap(int mem) { return mem <= 4 ? 4 : (mem <= 10 ? 10 : (mem <= 16 ? 16 : 32)); }
-
-constexpr int DOTS_GRP = 16;      // blocks per group of the two-level reduction
-constexpr int DOTS_MAX_GRP = 60;  // groups the counter buffer has room for
 
 // Accept and dots in one pass (memory caps whose 5 (MCAP + 1) + 7 sums fit in 64 registers):
 // each element of x, g, x_t, g_t and of every live history pair is read once; the thread
@@ -671,7 +779,9 @@ static cudaError_t launch_update(const SolverArgs& a, int grid, cudaStream_t s) 
 }
 template <int MCAP>
 static cudaError_t launch_direction(const SolverArgs& a, int grid, cudaStream_t s) {
-  lbfgs_direction_kernel<MCAP><<<grid, 256, 0, s>>>(a);
+  // As many blocks as fit at once (the update grid: two per SM), striding over the elements.
+  const int64_t g = std::min<int64_t>(std::min<int64_t>((a.N + 511) / 512, grid), (int64_t)DOTS_GRP * DOTS_MAX_GRP);
+  lbfgs_direction_kernel<MCAP><<<(int)std::max<int64_t>(1, g), 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 
