@@ -93,12 +93,13 @@ __device__ double zoom_trial(const LineSearch& L, double epsf) {
 
 // One step of the line-search state machine after the trial at L.a has been evaluated
 // (st->out[0] = phi(a), st->out[1] = phi'(a)).
-__global__ void ls_step_kernel(SolverState* st, cudaGraphConditionalHandle h) {
+// in_graph = 0: launched from the host-driven loop (no conditional node to set).
+__global__ void ls_step_kernel(SolverState* st, cudaGraphConditionalHandle h, int in_graph) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   LineSearch& L = st->ls;
   if (!st->active || L.state != LS_RUNNING) {
     st->gate = 0;
-    cudaGraphSetConditional(h, 0);
+    if (in_graph) cudaGraphSetConditional(h, 0);
     return;
   }
   const double a = L.a, fa = st->out[0], ga = st->out[1];
@@ -127,7 +128,7 @@ __global__ void ls_step_kernel(SolverState* st, cudaGraphConditionalHandle h) {
     L.state = LS_ACCEPTED;
     L.f_acc = fa;
     st->gate = 0;
-    cudaGraphSetConditional(h, 0u);
+    if (in_graph) cudaGraphSetConditional(h, 0u);
     return;
   }
   if (isfinite(fa) && fa <= L.f0 + epsf && isfinite(gga) && gga < L.best_gg) {
@@ -181,7 +182,7 @@ __global__ void ls_step_kernel(SolverState* st, cudaGraphConditionalHandle h) {
   }
   const int running = L.state == LS_RUNNING;
   st->gate = running;
-  cudaGraphSetConditional(h, running ? 1u : 0u);
+  if (in_graph) cudaGraphSetConditional(h, running ? 1u : 0u);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -887,6 +888,11 @@ static rpca_status ensure_solver(rpca_ctx* c) {
   SOL_CUDA(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
   SOL_CUDA(cudaStreamCreateWithFlags(&b->cap2, cudaStreamNonBlocking));
 
+  // RPCA_SOLVER_GRAPH=0 runs the same kernels from a host loop (one synchronisation per
+  // line-search trial), for per-kernel profilers that do not see inside conditional graphs.
+  if (const char* e = getenv("RPCA_SOLVER_GRAPH"))
+    if (e[0] == '0') return RPCA_OK;
+
   // Capture one iteration: WHILE(line search) { fg, finalize, ls_step }, update, direction.
   SolverArgs a = solver_args(c);
   SOL_CUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
@@ -910,7 +916,7 @@ static rpca_status ensure_solver(rpca_ctx* c) {
     if (e == cudaSuccess) {
       rpca_status s = launch_fg(c, c->fg_plan, trial_launch(c), b->cap2);
       if (s == RPCA_OK) {
-        ls_step_kernel<<<1, 32, 0, b->cap2>>>(b->st, h);
+        ls_step_kernel<<<1, 32, 0, b->cap2>>>(b->st, h, 1);
         e = cudaGetLastError();
       } else {
         e = cudaErrorUnknown;
@@ -971,8 +977,33 @@ rpca_status solver_prepare(rpca_ctx* c, const float* U, const float* V) {
   return solver_start(c);
 }
 
+// The host-driven form of one graph launch: trials until the line search ends, then the
+// update and the next direction.
+static rpca_status host_iteration(rpca_ctx* c) {
+  SolverBuffers* b = c->sol;
+  for (int trial = 0; trial <= LS_MAX_TRIALS + 1; ++trial) {
+    SOL_CUDA(cudaMemcpyAsync(&b->host->active, &b->st->active, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    SOL_CUDA(cudaMemcpyAsync(&b->host->ls.state, &b->st->ls.state, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    SOL_CUDA(cudaStreamSynchronize(c->stream));
+    if (!b->host->active || b->host->ls.state != LS_RUNNING) break;
+    rpca_status s = launch_fg(c, c->fg_plan, trial_launch(c), c->stream);
+    if (s != RPCA_OK) return s;
+    ls_step_kernel<<<1, 32, 0, c->stream>>>(b->st, 0, 0);
+    SOL_CUDA(cudaGetLastError());
+  }
+  SOL_CUDA(update_and_direction(b->mcap, solver_args(c), b->grid, c->stream));
+  return RPCA_OK;
+}
+
 rpca_status solver_iterations(rpca_ctx* c, int count) {
-  for (int i = 0; i < count; ++i) SOL_CUDA(cudaGraphLaunch(c->sol->exec, c->stream));
+  if (!c->sol->exec) {
+    for (int i = 0; i < count; ++i) {
+      rpca_status s = host_iteration(c);
+      if (s != RPCA_OK) return s;
+    }
+  } else {
+    for (int i = 0; i < count; ++i) SOL_CUDA(cudaGraphLaunch(c->sol->exec, c->stream));
+  }
   c->graph_launches += count;
   // Kernels inside: accept + dots (one kernel for small memory caps) + direction per launch;
   // the while body (fused kernel, finalize, line-search step) is added from the trial count

@@ -118,3 +118,25 @@ def test_solve_reports_not_converged_when_capped():
     res = P.solve(Ud, Vd)
     assert res.status == rpca.RPCA_ENOTCONV and res.iters == 3
     P.close()
+
+
+def test_host_driven_solver_matches_graph(monkeypatch):
+    """RPCA_SOLVER_GRAPH=0 runs the same kernels from a host loop: identical iterates."""
+    inst = gen.planted_500x400(1)
+    out = []
+    for flag in (None, "0"):
+        if flag is None:
+            monkeypatch.delenv("RPCA_SOLVER_GRAPH", raising=False)
+        else:
+            monkeypatch.setenv("RPCA_SOLVER_GRAPH", flag)
+        P = make_problem(inst.X, None, inst.k, inst.lam_L, inst.lam_S, init=rpca.RPCA_INIT_SKETCH,
+                         max_iter=3000, cert_every=10)
+        Ud, Vd = empty_factors(inst.m, inst.n, inst.k)
+        res = P.solve(Ud, Vd)
+        out.append((res.status, res.iters, res.evals, res.F, host(Ud, inst.m)))
+        P.close()
+    (s0, i0, e0, f0, U0), (s1, i1, e1, f1, U1) = out
+    assert s0 == s1 == rpca.RPCA_OK
+    assert (i0, e0) == (i1, e1)
+    assert f0 == f1
+    assert np.array_equal(U0, U1)
