@@ -263,7 +263,7 @@ static rpca_status make_plan(rpca_ctx* c, FgPlan* P, int K, int B, bool same, in
   int force_wc = 0, force_ncs = 0, n_smem = 0, n_attr = 0, n_occ = 0, n_try = 0;
   cudaError_t last_occ = cudaSuccess;
   if (const char* env = getenv("RPCA_PLAN")) sscanf(env, "%d,%d", &force_wc, &force_ncs);
-  for (int WC : {8, 4, 2}) for (int nst : {3, 2}) {
+  for (int WC : {8, 4, 2}) for (int nst : {6, 4, 2}) {
     if (force_wc && WC != force_wc) continue;
     const int BM = WC * 32 * v->R;
     const int nrb = (c->m + BM - 1) / BM;
@@ -277,7 +277,7 @@ static rpca_status make_plan(rpca_ctx* c, FgPlan* P, int K, int B, bool same, in
       if (ncs == last_ncs) continue;
       if (force_ncs && ncs != force_ncs) continue;
       last_ncs = ncs;
-      const FgSmem L = fg_smem_layout(WC, v->R, masked, BN, KV, CSB, nst);
+      const FgSmem L = fg_smem_layout(WC, v->R, masked, BN, KV, CSB, nst, side == 1 ? 0 : v->J * B);
       ++n_try;
       if (L.total > c->max_smem) {
         ++n_smem;

@@ -342,24 +342,9 @@ __global__ void cert_reset_kernel(CertState* st) {
 
 // Ritz values of T[0:d, 0:d] (float32 one-sided Jacobi in global memory) -> t4 estimate,
 // sigma_1, and whether both have settled since the previous check.
-__global__ void __launch_bounds__(1024) cert_ritz_kernel(CertState* st, const double* T, float* Ag, float* Vg, int d,
-                                                          double lam_L, int final_step) {
-  __shared__ float s[LZ_TMAX];
-  __shared__ int ord[LZ_TMAX];
-  __shared__ int flag;
-  extern __shared__ float dyn[];
-  // Small projected matrices (d <= 96) are worked on in shared memory, larger ones in global.
-  const bool in_smem = d <= 96;
-  float* A = in_smem ? dyn : Ag;
-  float* V = in_smem ? dyn + d * d : Vg;
-  for (int i = threadIdx.x; i < d * d; i += blockDim.x) {
-    const int a = i % d, b = i / d;
-    A[i] = (float)T[a + (int64_t)b * LZ_TMAX];
-  }
-  __syncthreads();
-  // Rotation threshold above the float32 rounding of the column inner products (about
-  // d * eps relative); below it every sweep would rotate every pair until the sweep limit.
-  cta_jacobi_svd<float>(A, d, d, d, V, d, s, &flag, 40, fmaxf(1e-6f, 4.0f * d * 1.2e-7f), 2.0f * d * 6e-8f);
+// Ritz values of the projected matrix, sorted: t4 and the stopping tests of the Lanczos loop.
+// Called by the whole CTA (the sort is CTA-wide); thread 0 updates the state.
+__device__ void ritz_finish(CertState* st, const float* s, int* ord, int d, double lam_L, int final_step) {
   cta_sort_desc<float>(s, d, ord);
   if (threadIdx.x == 0) {
     double t4 = 0.0;
@@ -383,6 +368,45 @@ __global__ void __launch_bounds__(1024) cert_ritz_kernel(CertState* st, const do
     st->t4 = t4;
     st->sigma1 = s1;
   }
+}
+
+// Rotation threshold of the Ritz SVDs: above the float32 rounding of the column inner
+// products (about d * eps relative); below it every sweep would rotate every pair until the
+// sweep limit.
+__device__ inline float ritz_tol(int d) { return fmaxf(1e-6f, 4.0f * d * 1.2e-7f); }
+__device__ inline float ritz_noise(int d) { return 2.0f * d * 6e-8f; }
+
+// d <= 32: one warp, the matrix in registers (warp_jacobi_svd).
+__global__ void __launch_bounds__(32) cert_ritz_warp_kernel(CertState* st, const double* T, int d, double lam_L,
+                                                            int final_step) {
+  __shared__ float A[32 * 32], V[32 * 32], s[32];
+  __shared__ int ord[32];
+  for (int i = threadIdx.x; i < d * d; i += blockDim.x) {
+    const int a = i % d, b = i / d;
+    A[i] = (float)T[a + (int64_t)b * LZ_TMAX];
+  }
+  __syncwarp();
+  warp_jacobi_svd<float, 32, 32>(A, d, d, d, V, d, s, 40, ritz_tol(d), ritz_noise(d));
+  ritz_finish(st, s, ord, d, lam_L, final_step);
+}
+
+// Larger d: the CTA form, in shared memory up to d = 96, else in global memory.
+__global__ void __launch_bounds__(1024) cert_ritz_kernel(CertState* st, const double* T, float* Ag, float* Vg, int d,
+                                                          double lam_L, int final_step) {
+  __shared__ float s[LZ_TMAX];
+  __shared__ int ord[LZ_TMAX];
+  __shared__ int flag;
+  extern __shared__ float dyn[];
+  const bool in_smem = d <= 96;
+  float* A = in_smem ? dyn : Ag;
+  float* V = in_smem ? dyn + d * d : Vg;
+  for (int i = threadIdx.x; i < d * d; i += blockDim.x) {
+    const int a = i % d, b = i / d;
+    A[i] = (float)T[a + (int64_t)b * LZ_TMAX];
+  }
+  __syncthreads();
+  cta_jacobi_svd<float>(A, d, d, d, V, d, s, &flag, 40, ritz_tol(d), ritz_noise(d));
+  ritz_finish(st, s, ord, d, lam_L, final_step);
 }
 
 __global__ void pad_copy_kernel(const float* src, int64_t rows, int k, float* dst, int kp) {
@@ -687,10 +711,14 @@ rpca_status cert_compute(rpca_ctx* c, const float* U, const float* V, rpca_cert*
       const bool last = (j == smax - 1);
       if (steps == 2 || steps == 4 || steps == 6 || (steps % 4) == 0 || last) {
         const int d = steps * LZ_B;
-        const size_t rsm = d <= 96 ? (size_t)2 * d * d * sizeof(float) : 0;
-        CERT_CUDA(cudaFuncSetAttribute(cert_ritz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       2 * 96 * 96 * (int)sizeof(float)));
-        cert_ritz_kernel<<<1, 1024, rsm, c->stream>>>(st, b->T, b->Tw, b->Tv, d, c->lam_L, last ? 1 : 0);
+        if (d <= 32) {
+          cert_ritz_warp_kernel<<<1, 32, 0, c->stream>>>(st, b->T, d, c->lam_L, last ? 1 : 0);
+        } else {
+          const size_t rsm = d <= 96 ? (size_t)2 * d * d * sizeof(float) : 0;
+          CERT_CUDA(cudaFuncSetAttribute(cert_ritz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         2 * 96 * 96 * (int)sizeof(float)));
+          cert_ritz_kernel<<<1, 1024, rsm, c->stream>>>(st, b->T, b->Tw, b->Tv, d, c->lam_L, last ? 1 : 0);
+        }
         count_launches(c, 1);
         CERT_CUDA(cudaGetLastError());
         int conv = 0;

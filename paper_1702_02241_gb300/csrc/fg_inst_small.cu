@@ -16,7 +16,7 @@ void fg_register_same_small(FgVariant (*tab)[2]) {
   reg<3, 8, 4>(tab);
   reg<4, 8, 4>(tab);
   reg<5, 8, 4>(tab);
-  reg<6, 8, 4>(tab);
+  reg<6, 8, 2>(tab);
   reg<7, 4, 2>(tab);
   reg<8, 4, 2>(tab);
 }

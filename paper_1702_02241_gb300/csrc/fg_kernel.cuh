@@ -36,19 +36,21 @@ struct FgArgs {
   const float* BV;  // apply mode: n x B (ld n)
   float lam_S;
   int nrb, ncs, BN;  // row blocks, column splits, columns per split (multiple of 8)
-  int nstage;        // pipeline depth (2 or FG_NSTAGE)
+  int nstage;        // pipeline depth (2 .. FG_NSTAGE)
   float* PU;         // [ncs][B][mpad]  -(D Bv) partial sums over a CTA's columns
   float* PV;         // [nrb][B][n]      D^T Bu partial sums over a CTA's rows
   double* Ppsi;      // [nrb*ncs]        sum of psi over a CTA's tile
   int* err;          // device status word (error bits)
 };
 
-constexpr int FG_BJ = 8;      // columns per pipeline stage
-constexpr int FG_NSTAGE = 3;  // maximum pipeline depth
+constexpr int FG_BJ = 4;      // columns per pipeline stage
+constexpr int FG_NSTAGE = 6;  // maximum pipeline depth
 
 struct FgSmem {
-  size_t x_off, m_off, v_off, cs_off, bar_off, scr_off, total;
+  size_t x_off, m_off, v_off, cs_off, tr_off, bar_off, scr_off, total;
 };
+
+constexpr int FG_TR_LD = 36;  // row stride (floats) of the column-sum transposition buffer
 
 // Observation bitmap of one stage: one TMA box per CTA, {WC * R words, BJ columns}, so the
 // box's x coordinate row0 / 32 is a multiple of WC * R >= 4 words (16 bytes).
@@ -57,8 +59,10 @@ __host__ __device__ inline size_t fg_mask_stage_bytes(int WC, int R) {
 }
 
 // Shared-memory carve-up (byte offsets from a 1024-byte aligned base): X stages, bitmap
-// stages, the CTA's factor slice, one slab of column sums per consumer warp, mbarriers.
-__host__ __device__ inline FgSmem fg_smem_layout(int WC, int R, bool masked, int BN, int KV, int B, int nstage) {
+// stages, the CTA's factor slice, one slab of column sums per consumer warp, one
+// transposition buffer per consumer warp (JB rows of FG_TR_LD floats), mbarriers.
+__host__ __device__ inline FgSmem fg_smem_layout(int WC, int R, bool masked, int BN, int KV, int B, int nstage,
+                                                 int JB) {
   FgSmem L;
   size_t o = 0;
   L.x_off = o;
@@ -70,6 +74,9 @@ __host__ __device__ inline FgSmem fg_smem_layout(int WC, int R, bool masked, int
   o += (size_t)BN * KV * 8;
   L.cs_off = o;
   o += (size_t)WC * BN * B * 4;
+  o = (o + 15) & ~(size_t)15;
+  L.tr_off = o;
+  o += (size_t)WC * JB * FG_TR_LD * 4;
   o = (o + 7) & ~(size_t)7;
   L.bar_off = o;
   o += 2 * FG_NSTAGE * 8;
@@ -118,7 +125,7 @@ RPCA_DEV void lane_bit(int p, int e, int lane, int& word, int& bit) {
 }
 
 template <int K, int B, bool SAME, bool MASKED, int R, int J, int SIDE = 0>
-__global__ void __launch_bounds__(288) fg_kernel(const __grid_constant__ CUtensorMap tmX,
+__global__ void __launch_bounds__(288, 1) fg_kernel(const __grid_constant__ CUtensorMap tmX,
                                                  const __grid_constant__ CUtensorMap tmM, FgArgs a) {
   using T = FgTraits<K, B, SAME, R, J, SIDE>;
   constexpr int NP = T::NP, ROWS_W = T::ROWS_W, KV = T::KV, JB = T::JB;
@@ -135,11 +142,12 @@ __global__ void __launch_bounds__(288) fg_kernel(const __grid_constant__ CUtenso
   const int ncols = min(a.BN, a.n - col0);
   const int nchunks = (ncols + FG_BJ - 1) / FG_BJ;
   const int nst = a.nstage;
-  const FgSmem L = fg_smem_layout(WC, R, MASKED, a.BN, KV, T::CSB, nst);
+  const FgSmem L = fg_smem_layout(WC, R, MASKED, a.BN, KV, T::CSB, nst, COLSIDE ? JB : 0);
   float* xs_all = reinterpret_cast<float*>(sm + L.x_off);
   uint32_t* ms_all = reinterpret_cast<uint32_t*>(sm + L.m_off);
   float2* vsl = reinterpret_cast<float2*>(sm + L.v_off);
   float* csum = reinterpret_cast<float*>(sm + L.cs_off);  // [WC][BN][B]
+  float* trbuf = reinterpret_cast<float*>(sm + L.tr_off);  // [WC][JB][FG_TR_LD]
   uint64_t* full = reinterpret_cast<uint64_t*>(sm + L.bar_off);
   uint64_t* empty = full + FG_NSTAGE;
   double* scr = reinterpret_cast<double*>(sm + L.scr_off);
@@ -347,22 +355,33 @@ __global__ void __launch_bounds__(288) fg_kernel(const __grid_constant__ CUtenso
           }
         }
       }
-      // Column sums of this group: lanes, then warps (fixed order).
+      // Column sums of this group over the warp's rows: each lane writes its JB partials
+      // (value-major, so the 32 lanes fill one row of the buffer), then lane t < JB sums
+      // row t with 16-byte loads in four independent chains (fixed order).  The warp's sums
+      // for the group's J columns go to its own slab (no barrier across warps here).
       if constexpr (COLSIDE) {
-      float vals[JB];
+        static_assert(JB <= 32, "one lane per column sum");
+        float* tr = trbuf + (size_t)warp * JB * FG_TR_LD;
 #pragma unroll
-      for (int jj = 0; jj < J; ++jj)
+        for (int jj = 0; jj < J; ++jj)
 #pragma unroll
-        for (int b = 0; b < B; ++b) vals[jj * B + b] = gv[jj][b].x + gv[jj][b].y;
-      int base = 0;
-      ReduceScatter<JB, 16>::run(vals, lane, base);
-      constexpr int CF = rs_count(JB), DUP = rs_dup_mask(JB);
-      // This warp's sums for the group's J columns go to its own slab (no barrier here).
-      float* slab = csum + ((size_t)warp * a.BN + (size_t)c * FG_BJ + g * J) * B;
-      if ((lane & DUP) == 0) {
+          for (int b = 0; b < B; ++b) tr[(jj * B + b) * FG_TR_LD + lane] = gv[jj][b].x + gv[jj][b].y;
+        __syncwarp();
+        if (lane < JB) {
+          const float4* row = reinterpret_cast<const float4*>(tr + lane * FG_TR_LD);
+          float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
 #pragma unroll
-        for (int t = 0; t < CF; ++t) slab[base + t] = vals[t];
-      }
+          for (int q = 0; q < 8; ++q) {
+            const float4 t4 = row[q];
+            s0 += t4.x;
+            s1 += t4.y;
+            s2 += t4.z;
+            s3 += t4.w;
+          }
+          float* slab = csum + ((size_t)warp * a.BN + (size_t)c * FG_BJ + g * J) * B;
+          slab[lane] = (s0 + s1) + (s2 + s3);
+        }
+        __syncwarp();
       }
     }
     {

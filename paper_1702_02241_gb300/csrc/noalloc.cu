@@ -79,7 +79,7 @@ extern "C" rpca_status rpca_fg_noalloc(int64_t m, int64_t n, const float* X, int
       break;
     }
   }
-  const int BM = WC * 32 * v->R, nst = 2;
+  const int BM = WC * 32 * v->R, nst = 4;
   const int nrb = (int)((m + BM - 1) / BM);
   const int mpad = (int)((m + 3) / 4 * 4);
   int ncs_req = std::max(1, (nsm + nrb - 1) / nrb);
@@ -89,7 +89,7 @@ extern "C" rpca_status rpca_fg_noalloc(int64_t m, int64_t n, const float* X, int
     BN = (int)((n + ncs_req - 1) / ncs_req);
     BN = (BN + FG_BJ - 1) / FG_BJ * FG_BJ;
     ncs = (int)((n + BN - 1) / BN);
-    smem = fg_smem_layout(WC, v->R, false, BN, k, k, nst).total;
+    smem = fg_smem_layout(WC, v->R, false, BN, k, k, nst, v->J * k).total;
     if (smem <= (size_t)smem_optin || BN <= FG_BJ) break;
   }
   if (smem > (size_t)smem_optin) return set_err_noctx(RPCA_EUNSUPPORTED, "no launch configuration fits");

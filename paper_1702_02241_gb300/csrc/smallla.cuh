@@ -29,6 +29,12 @@ template <typename T>
 __device__ int cta_jacobi_svd(T* A, int rows, int cols, int lda, T* V, int ldv, T* sig, int* flag, int max_sweeps,
                               T tol, T noise = T(0)) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  // Butterfly width: the lanes that hold data (rows of A) or apply the rotation (rows of A,
+  // rows of V = cols) must all get the sums, so the tree spans max(rows, cols) lanes.
+  const int nact = rows > cols ? rows : cols;
+  int top = 16;
+  while (top > 1 && top >= nact) top >>= 1;
+  if (nact > 32) top = 16;
   for (int idx = threadIdx.x; idx < cols * cols; idx += blockDim.x) {
     const int i = idx % cols, j = idx / cols;
     V[i + (size_t)j * ldv] = (i == j) ? T(1) : T(0);
@@ -53,16 +59,24 @@ __device__ int cta_jacobi_svd(T* A, int rows, int cols, int lda, T* V, int ldv, 
           be += y * y;
           ga += x * y;
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
+        // Lanes at or beyond `rows` hold zeros: the tree spans the first 2 * top lanes.
+        for (int o = top; o > 0; o >>= 1) {
           al += __shfl_xor_sync(0xffffffffu, al, o);
           be += __shfl_xor_sync(0xffffffffu, be, o);
           ga += __shfl_xor_sync(0xffffffffu, ga, o);
         }
-        if (ga != T(0) && fabs(ga) > tol * sqrt(al * be) && fabs(ga) > noise * (al + be)) {
-          const T zeta = (be - al) / (T(2) * ga);
-          const T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
-          const T cs = T(1) / sqrt(T(1) + t * t), sn = cs * t;
+        if (ga != T(0) && ga * ga > tol * tol * (al * be) && fabs(ga) > noise * (al + be)) {
+          // Rotation angle in float32 with fast operations (its accuracy only affects how
+          // far this step reduces a_p . a_q), then (cs, sn) renormalised in T by one Newton
+          // step on 1/sqrt(cs^2 + sn^2), so that the rotation is orthogonal to T's rounding
+          // (float64 square roots and divides cost hundreds of cycles each on this GPU).
+          const float zeta = __fdividef((float)(be - al), 2.f * (float)ga);
+          const float tf = copysignf(1.f, zeta) * __frcp_rn(fabsf(zeta) + __fsqrt_rn(fmaf(zeta, zeta, 1.f)));
+          const float csf = __frsqrt_rn(fmaf(tf, tf, 1.f));
+          T cs = (T)csf, sn = (T)(csf * tf);
+          const T corr = T(1.5) - T(0.5) * (cs * cs + sn * sn);
+          cs *= corr;
+          sn *= corr;
           for (int i = lane; i < rows; i += 32) {
             const T x = ap[i], y = aq[i];
             ap[i] = cs * x - sn * y;
@@ -90,6 +104,95 @@ __device__ int cta_jacobi_svd(T* A, int rows, int cols, int lda, T* V, int ldv, 
     sig[j] = sqrt(s);
   }
   __syncthreads();
+  return sweep;
+}
+
+// One-sided Jacobi (Hestenes) SVD of a small matrix by one warp: cols <= CMAX <= 32,
+// rows <= RMAX.  Meant for float32 (the Ritz values): its inner products are per-lane
+// chains over RMAX rows, which in float64 (64-cycle dependent adds here) lose to the CTA form.
+// Lane j holds column j of A and of V in registers; round r of the round-robin ("circle")
+// schedule pairs lane j with (2r - j) mod (ne - 1) (ne - 1 with r), the pair exchanges columns
+// with shuffles, both lanes form the same rotation from the same three inner products, and
+// each updates its own column.  No barriers: a sweep is ne - 1 rounds of shuffles and FMAs.
+// Rotation test and angle as in cta_jacobi_svd.  A (rows x cols, lda) is overwritten by
+// U diag(sig) in shared or global memory, V (cols x cols, ldv) receives the right singular
+// vectors, sig[j] = ||A_j||.  Call from all 32 lanes of one warp; returns the sweep count.
+template <typename T, int RMAX, int CMAX>
+__device__ int warp_jacobi_svd(T* A, int rows, int cols, int lda, T* V, int ldv, T* sig, int max_sweeps, T tol,
+                               T noise) {
+  static_assert(CMAX <= 32, "one lane per column");
+  const int lane = threadIdx.x & 31;
+  const bool mine = lane < cols;
+  T a[RMAX], v[CMAX];
+#pragma unroll
+  for (int i = 0; i < RMAX; ++i) a[i] = (mine && i < rows) ? A[i + (size_t)lane * lda] : T(0);
+#pragma unroll
+  for (int i = 0; i < CMAX; ++i) v[i] = (i == lane) ? T(1) : T(0);
+  const int ne = cols + (cols & 1);
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    bool rotated = false;
+    for (int r = 0; r < ne - 1; ++r) {
+      int partner;
+      if (lane == ne - 1) partner = r;
+      else if (lane == r) partner = ne - 1;
+      else partner = (2 * r - lane + 2 * (ne - 1)) % (ne - 1);
+      const bool act = mine && partner < cols && lane < ne;
+      const int src = act ? partner : lane;
+      T b[RMAX];
+#pragma unroll
+      for (int i = 0; i < RMAX; ++i) b[i] = __shfl_sync(0xffffffffu, a[i], src);
+      const bool low = lane < partner;  // the lower index plays p, the higher q
+      // Inner products in four interleaved partial sums (shorter dependent chains).
+      T al4[4] = {0, 0, 0, 0}, be4[4] = {0, 0, 0, 0}, ga4[4] = {0, 0, 0, 0};
+#pragma unroll
+      for (int i = 0; i < RMAX; ++i) {
+        const T ap = low ? a[i] : b[i], aq = low ? b[i] : a[i];
+        al4[i & 3] += ap * ap;
+        be4[i & 3] += aq * aq;
+        ga4[i & 3] += ap * aq;
+      }
+      const T al = (al4[0] + al4[1]) + (al4[2] + al4[3]);
+      const T be = (be4[0] + be4[1]) + (be4[2] + be4[3]);
+      const T ga = (ga4[0] + ga4[1]) + (ga4[2] + ga4[3]);
+      T cs = T(1), sn = T(0);
+      const bool rot = act && ga != T(0) && ga * ga > tol * tol * (al * be) && fabs(ga) > noise * (al + be);
+      if (rot) {
+        const float zeta = __fdividef((float)(be - al), 2.f * (float)ga);
+        const float tf = copysignf(1.f, zeta) * __frcp_rn(fabsf(zeta) + __fsqrt_rn(fmaf(zeta, zeta, 1.f)));
+        const float csf = __frsqrt_rn(fmaf(tf, tf, 1.f));
+        cs = (T)csf;
+        sn = (T)(csf * tf);
+        const T corr = T(1.5) - T(0.5) * (cs * cs + sn * sn);
+        cs *= corr;
+        sn *= corr;
+        rotated = true;
+      }
+      // p' = cs p - sn q,  q' = sn p + cs q.
+      const T ca = cs, cb = low ? -sn : sn;
+#pragma unroll
+      for (int i = 0; i < RMAX; ++i) a[i] = ca * a[i] + cb * b[i];
+#pragma unroll
+      for (int i = 0; i < CMAX; ++i) {
+        const T w = __shfl_sync(0xffffffffu, v[i], src);
+        v[i] = ca * v[i] + cb * w;
+      }
+    }
+    if (!__any_sync(0xffffffffu, rotated)) break;
+  }
+  if (mine) {
+    T s2 = 0;
+#pragma unroll
+    for (int i = 0; i < RMAX; ++i) {
+      s2 += a[i] * a[i];
+      if (i < rows) A[i + (size_t)lane * lda] = a[i];
+    }
+    sig[lane] = sqrt(s2);
+#pragma unroll
+    for (int i = 0; i < CMAX; ++i)
+      if (i < cols) V[i + (size_t)lane * ldv] = v[i];
+  }
+  __syncwarp();
   return sweep;
 }
 
