@@ -20,6 +20,8 @@ Modules and the passages they follow:
                      (Sec. 1 notes proximal methods apply but need an SVD): reference solutions
                      on tiny instances.
 * ``sketch``      -- randomized-SVD initialisation U0 = U_k S^1/2, V0 = V_k S^1/2 (Sec. 4.2).
+* ``quant``       -- the values X takes when stored as bfloat16 or FP8 E4M3 (per-column scale),
+                     from the formats' definitions, for the precision form of the objective pass.
 
 Every function is pinned by ``tests/test_oracle_*.py`` against something other than itself:
 brute-force minimisation, finite differences, closed-form SVT solutions, the explicit
