@@ -67,8 +67,10 @@ typedef struct {
   int cert_every;        /* evaluate the certificate every cert_every iterations (0 = only at the end) */
   int init;              /* rpca_init_kind */
   uint64_t seed;         /* seed of the device generator (sketch, random init) */
-  rpca_dtype x_dtype;    /* storage of X inside the engine (RPCA_F32 only in this build) */
-  int refine_fp32;       /* reserved for the reduced-precision form */
+  rpca_dtype x_dtype;    /* storage of X the objective pass reads: RPCA_F32 (the caller's X),
+                            RPCA_BF16 or RPCA_FP8E4M3 (a copy the library makes at create;
+                            k <= 8); see rpca_create and rpca_solve */
+  int refine_fp32;       /* with narrow storage: 1 (default) = finish rpca_solve on float32 X */
   double timeout_s;      /* wall-clock limit of rpca_solve (0 = none) */
   double gtol;           /* also stop when ||grad F||_F <= gtol * max(1, |F|) (0 = off) */
   int sketch_oversample; /* rSVD oversampling p (10) */
@@ -117,6 +119,11 @@ RPCA_API void rpca_default_options(rpca_options *opt);
  * Checks that every observed X entry is finite (RPCA_EINVAL otherwise).  Allocates the
  * context's device workspaces (partial-sum buffers, L-BFGS history of 2 * mem (m + n) k
  * floats, certificate buffers) and packs the mask into a bitmap it owns.
+ * Precision form (opt.x_dtype = RPCA_BF16 or RPCA_FP8E4M3, k <= 8): the library also keeps
+ * its own copy of X in that type (m x n, column-major; unobserved entries 0), rounded to
+ * nearest even; FP8 E4M3 stores x / s_j, s_j = max_i |x_ij| / 448 over the observed entries
+ * of column j (1 for an all-zero column), saturating at +-448.  X must still outlive the
+ * context (the float32 refinement and the certificate read it).
  */
 RPCA_API rpca_status rpca_create(rpca_ctx **out, int64_t m, int64_t n, const float *X, int64_t ldx,
                         const uint8_t *mask, int64_t ldmask, int k, double lambda_L, double lambda_S,
@@ -127,6 +134,8 @@ RPCA_API rpca_status rpca_create(rpca_ctx **out, int64_t m, int64_t n, const flo
  * through L = U V^T):  gU = D V + lam_L U,  gV = D^T U + lam_L V,  D = P_Omega(clip(U V^T - X)).
  * One pass over X.  f is a HOST pointer (may be NULL; the call then does not synchronise);
  * gU (m x k) and gV (n x k) are required device buffers.  The objective is summed in float64.
+ * With narrow storage (opt.x_dtype) the pass reads the library's copy: F and the gradient
+ * are those of the stored values (float32 arithmetic throughout).
  */
 RPCA_API rpca_status rpca_fg(rpca_ctx *c, const float *U, const float *V, double *f, float *gU, float *gV);
 
@@ -154,8 +163,21 @@ RPCA_API rpca_status rpca_init_sketch(rpca_ctx *c, const float *Omega, float *U,
  * point when opt.init == RPCA_INIT_USER, out = the solution.  Stops at cert_rel <= cert_tol
  * (certificate every cert_every iterations), max_iter, gtol, or timeout.  res may be NULL.
  * Returns RPCA_OK when the certificate tolerance was met, RPCA_ENOTCONV otherwise.
+ * With narrow storage the iterations first read the library's copy of X; when the
+ * (float32) certificate stops halving between checks, or that phase's iteration stops, the
+ * solve continues from the point reached on float32 X with fresh L-BFGS memory (unless
+ * opt.refine_fp32 == 0).  The certificate and res->F are always those of float32 X.
  */
 RPCA_API rpca_status rpca_solve(rpca_ctx *c, float *U, float *V, rpca_result *res);
+
+/*
+ * The library's narrow copy of X (precision form): *dtype receives the storage type
+ * (RPCA_F32 when the context keeps none, and nothing else is written).  host_out (may be
+ * NULL) receives the stored elements, m x n column-major with leading dimension ld_out >= m,
+ * 2 bytes each (bfloat16 bits) or 1 byte each (E4M3 codes); scales_out (may be NULL) the n
+ * per-column FP8 scales.  Synchronous.
+ */
+RPCA_API rpca_status rpca_x_storage(rpca_ctx *c, int *dtype, void *host_out, int64_t ld_out, float *scales_out);
 
 /*
  * The convergence certificate of Sec. 3.4 at L = U V^T: one pass over X for F and the
@@ -172,7 +194,8 @@ RPCA_API const char *rpca_last_error(const rpca_ctx *c);
 
 /*
  * Launch configuration the planner picked for the fused kernel of this context
- * (which = 0: objective/gradient; 1, 2: the certificate's and the sketch's D Bv products;
+ * (which = 0: objective/gradient -- the narrow-storage plan when the context keeps a narrow
+ * copy of X, the one rpca_fg uses; 1, 2: the certificate's and the sketch's D Bv products;
  * those two are planned, and tuned, on first use).
  * out[0..8] = {rows per lane R, consumer warps per CTA, row blocks, column splits,
  * columns per CTA, threads per CTA, dynamic shared memory bytes, CTAs per SM, pipeline

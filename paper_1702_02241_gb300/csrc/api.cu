@@ -60,21 +60,30 @@ rpca_status check_dev_err(rpca_ctx* c) {
 
 // ---- kernel variant table ----------------------------------------------------------------
 static FgVariant g_same[17][2];
+static FgVariant g_same_x[2][17][2];  // narrow storage of X: bfloat16, FP8 E4M3
 static FgVariant g_apply[3][3][2];
 static std::once_flag g_once;
 
 static void init_tables() {
   std::call_once(g_once, [] {
     memset(g_same, 0, sizeof g_same);
+    memset(g_same_x, 0, sizeof g_same_x);
     memset(g_apply, 0, sizeof g_apply);
     fg_register_same_small(g_same);
+    fg_register_same_bf16(g_same_x[0]);
+    fg_register_same_e4m3(g_same_x[1]);
     fg_register_same_large(g_same);
     fg_register_apply(g_apply);
   });
 }
 
-const FgVariant* fg_variant(int K, int B, bool same, bool masked, int side) {
+const FgVariant* fg_variant(int K, int B, bool same, bool masked, int side, int xt) {
   init_tables();
+  if (xt != 0) {
+    if (!same || xt < 1 || xt > 2 || K < 1 || K > 16 || B != K || side != 0) return nullptr;
+    const FgVariant* v = &g_same_x[xt - 1][K][masked ? 1 : 0];
+    return v->fn ? v : nullptr;
+  }
   if (same) {
     if (K < 1 || K > 16 || B != K || side != 0) return nullptr;
     return g_same[K][masked ? 1 : 0].fn ? &g_same[K][masked ? 1 : 0] : nullptr;
@@ -149,8 +158,10 @@ struct PlanKey {
   int64_t ldx;
   int K, B;
   bool same, masked;
+  int xt;
   bool operator<(const PlanKey& o) const {
-    return std::tie(dev, m, n, ldx, K, B, same, masked) < std::tie(o.dev, o.m, o.n, o.ldx, o.K, o.B, o.same, o.masked);
+    return std::tie(dev, m, n, ldx, K, B, same, masked, xt) <
+           std::tie(o.dev, o.m, o.n, o.ldx, o.K, o.B, o.same, o.masked, o.xt);
   }
 };
 static std::mutex g_cache_mu;
@@ -178,8 +189,13 @@ static Workspace& plan_ws(rpca_ctx* c, const FgPlan& P);
 
 // Tensor maps for a chosen configuration.
 static rpca_status finish_plan(rpca_ctx* c, FgPlan* q) {
-  rpca_status s = make_tmap(c, &q->tmX, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, c->X, c->m, c->n, c->ldx * 4, 32 * q->R,
-                            FG_BJ);
+  rpca_status s;
+  if (q->xt == FG_X_F32) {
+    s = make_tmap(c, &q->tmX, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, c->X, c->m, c->n, c->ldx * 4, 32 * q->R, FG_BJ);
+  } else {
+    const CUtensorMapDataType dt = q->xt == FG_X_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8;
+    s = make_tmap(c, &q->tmX, dt, c->Xq, c->m, c->n, c->ldq * fg_x_bytes(q->xt), 32 * q->R, FG_BJ);
+  }
   if (s != RPCA_OK) return s;
   if (q->masked) {
     s = make_tmap(c, &q->tmM, CU_TENSOR_MAP_DATA_TYPE_UINT32, c->bits, c->wpad, c->n, (int64_t)c->wpad * 4,
@@ -219,6 +235,7 @@ static rpca_status time_plan(rpca_ctx* c, const FgPlan& q, double* ms) {
   a.PV = wsp.PV;
   a.Ppsi = wsp.Ppsi;
   a.err = c->ws.err;
+  a.xscale = c->xscale;
   void* args[] = {(void*)&q.tmX, (void*)&q.tmM, (void*)&a};
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
@@ -252,10 +269,10 @@ static rpca_status time_plan(rpca_ctx* c, const FgPlan& q, double* ms) {
 // Cache code of a plan's kernel configuration (warps, stages).
 static int plan_code(const FgPlan& q) { return q.WC * 16 + q.nstage; }
 
-static rpca_status make_plan(rpca_ctx* c, FgPlan* P, int K, int B, bool same, int side) {
+static rpca_status make_plan(rpca_ctx* c, FgPlan* P, int K, int B, bool same, int side, int xt = FG_X_F32) {
   const bool masked = c->bits != nullptr;
-  const FgVariant* v = fg_variant(K, B, same, masked, side);
-  if (!v) return set_err(c, RPCA_EUNSUPPORTED, "no compiled kernel for this factor rank");
+  const FgVariant* v = fg_variant(K, B, same, masked, side, xt);
+  if (!v) return set_err(c, RPCA_EUNSUPPORTED, "no compiled kernel for this factor rank and storage type");
   const int KV = (same || side == 2) ? K : K + B;
   const int CSB = side == 1 ? 0 : B;
   double best = 1e300;
@@ -277,7 +294,7 @@ static rpca_status make_plan(rpca_ctx* c, FgPlan* P, int K, int B, bool same, in
       if (ncs == last_ncs) continue;
       if (force_ncs && ncs != force_ncs) continue;
       last_ncs = ncs;
-      const FgSmem L = fg_smem_layout(WC, v->R, masked, BN, KV, CSB, nst, side == 1 ? 0 : v->J * B);
+      const FgSmem L = fg_smem_layout(WC, v->R, masked, BN, KV, CSB, nst, side == 1 ? 0 : v->J * B, fg_x_bytes(xt));
       ++n_try;
       if (L.total > c->max_smem) {
         ++n_smem;
@@ -297,7 +314,7 @@ static rpca_status make_plan(rpca_ctx* c, FgPlan* P, int K, int B, bool same, in
         continue;
       }
       const double tiles = (double)nrb * ncs;
-      const double tile_bytes = (double)BM * BN * 4.0 * (masked ? 33.0 / 32.0 : 1.0);
+      const double tile_bytes = (double)BM * BN * fg_x_bytes(xt) + (masked ? (double)BM * BN / 8.0 : 0.0);
       // The busiest SM holds kt tiles, cw of them at a time; its rate grows with the consumer
       // warps resident on it up to about eight.
       constexpr double SM_GBS = 30.0, HBM_GBS = 6700.0;  // per-SM streaming rate, whole-GPU rate
@@ -326,6 +343,7 @@ static rpca_status make_plan(rpca_ctx* c, FgPlan* P, int K, int B, bool same, in
       cand.smem = L.total;
       cand.cps = cps;
       cand.nstage = nst;
+      cand.xt = xt;
       cands.push_back({t, cand});
       if (t < best) best = t;
     }
@@ -347,7 +365,7 @@ static rpca_status make_plan(rpca_ctx* c, FgPlan* P, int K, int B, bool same, in
     q.fin_grid = q.fin_gu + q.fin_gv;
   }
   // Cached choice for this shape, or measure the best few candidates of the model.
-  const PlanKey key{c->device, c->m, c->n, c->ldx, K, B * 4 + side, same, masked};
+  const PlanKey key{c->device, c->m, c->n, c->ldx, K, B * 4 + side, same, masked, xt};
   int pick = 0;
   int cached_wc = 0, cached_ncs = 0;
   const bool measure = !(force_wc || force_ncs) && autotune_enabled() && cands.size() > 1;
@@ -440,6 +458,7 @@ rpca_status launch_fg(rpca_ctx* c, const FgPlan& P, const FgLaunch& L, cudaStrea
   a.PV = w.PV;
   a.Ppsi = w.Ppsi;
   a.err = c->ws.err;
+  a.xscale = c->xscale;
   void* args[] = {(void*)&P.tmX, (void*)&P.tmM, (void*)&a};
   // Event pairs bracket the two launches while profiling (never inside a graph capture).
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -580,7 +599,7 @@ rpca_status rpca_profile_read(rpca_ctx* c, double* out) {
 
 rpca_status rpca_plan_info(rpca_ctx* c, int which, int64_t* out) {
   if (!c || !out || which < 0 || which > 2) return RPCA_EINVAL;
-  const FgPlan* Pp = which == 0 ? &c->fg_plan : apply_plan(c, which == 1 ? c->k : 0, 1);
+  const FgPlan* Pp = which == 0 ? &eval_plan(c) : apply_plan(c, which == 1 ? c->k : 0, 1);
   if (!Pp || !Pp->valid) return RPCA_EINVAL;
   const FgPlan& P = *Pp;
   const int64_t v[9] = {P.R, P.WC, P.nrb, P.ncs, P.BN, P.threads, (int64_t)P.smem, P.cps, P.nstage};
@@ -612,7 +631,10 @@ rpca_status rpca_create(rpca_ctx** out, int64_t m, int64_t n, const float* X, in
   rpca_default_options(&o);
   if (opt) o = *opt;
   if (o.lbfgs_mem < 1 || o.lbfgs_mem > 32) return set_err(nullptr, RPCA_EINVAL, "lbfgs_mem must be in [1, 32]");
-  if (o.x_dtype != RPCA_F32) return set_err(nullptr, RPCA_EUNSUPPORTED, "only RPCA_F32 storage is built");
+  if (o.x_dtype != RPCA_F32 && o.x_dtype != RPCA_BF16 && o.x_dtype != RPCA_FP8E4M3)
+    return set_err(nullptr, RPCA_EINVAL, "x_dtype must be RPCA_F32, RPCA_BF16 or RPCA_FP8E4M3");
+  if (o.x_dtype != RPCA_F32 && k > 8)
+    return set_err(nullptr, RPCA_EUNSUPPORTED, "narrow storage of X is compiled for k <= 8");
 
   rpca_ctx* c = new (std::nothrow) rpca_ctx();
   if (!c) return set_err(nullptr, RPCA_ENOMEM, "host allocation failed");
@@ -676,10 +698,34 @@ rpca_status rpca_create(rpca_ctx** out, int64_t m, int64_t n, const float* X, in
   rpca_status s = make_plan(c, &c->fg_plan, k, k, true, 0);
   if (s != RPCA_OK) return fail(s);
   if ((s = size_workspace(c, c->fg_plan)) != RPCA_OK) return fail(s);
+  if (o.x_dtype != RPCA_F32) {
+    // Both objective/gradient plans share one workspace (captured by the solver's graph):
+    // size it for both before any capture.
+    if ((s = make_xq(c, (int)o.x_dtype)) != RPCA_OK) return fail(s);
+    if ((s = make_plan(c, &c->fg_plan_q, k, k, true, 0, (int)o.x_dtype)) != RPCA_OK) return fail(s);
+    if ((s = size_workspace(c, c->fg_plan_q)) != RPCA_OK) return fail(s);
+  }
+  c->solve_plan = &c->fg_plan;
   if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return fail(cuda_err(c, e, "rpca_create"));
   c->F_best = INFINITY;
   c->F0 = NAN;
   *out = c;
+  return RPCA_OK;
+}
+
+rpca_status rpca_x_storage(rpca_ctx* c, int* dtype, void* host_out, int64_t ld_out, float* scales_out) {
+  if (!c || !dtype) return RPCA_EINVAL;
+  *dtype = c->xq_dt;
+  if (c->xq_dt == 0) return RPCA_OK;
+  const size_t eb = (size_t)fg_x_bytes(c->xq_dt);
+  if (host_out) {
+    if (ld_out < c->m) return set_err(c, RPCA_EINVAL, "ld_out < m");
+    RPCA_CUDA(c, cudaMemcpy2DAsync(host_out, (size_t)ld_out * eb, c->Xq, (size_t)c->ldq * eb, (size_t)c->m * eb, c->n,
+                                   cudaMemcpyDeviceToHost, c->stream));
+  }
+  if (scales_out && c->xscale)
+    RPCA_CUDA(c, cudaMemcpyAsync(scales_out, c->xscale, sizeof(float) * c->n, cudaMemcpyDeviceToHost, c->stream));
+  RPCA_CUDA(c, cudaStreamSynchronize(c->stream));
   return RPCA_OK;
 }
 
@@ -692,7 +738,7 @@ rpca_status rpca_fg(rpca_ctx* c, const float* U, const float* V, double* f, floa
   L.GU = gU;
   L.GV = gV;
   L.out = c->ws.out;
-  rpca_status s = launch_fg(c, c->fg_plan, L, c->stream);
+  rpca_status s = launch_fg(c, eval_plan(c), L, c->stream);
   if (s != RPCA_OK) return s;
   if (f) {
     RPCA_CUDA(c, cudaMemcpyAsync(f, c->ws.out, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -750,6 +796,8 @@ void rpca_destroy(rpca_ctx* c) {
   free_solver(c);
   free_cert(c);
   cudaFree(c->bits);
+  cudaFree(c->Xq);
+  cudaFree(c->xscale);
   cudaFree(c->ws.PU);
   cudaFree(c->ws.PV);
   cudaFree(c->ws.Ppsi);

@@ -26,8 +26,9 @@ struct FgPlan {
   int fin_grid = 0, fin_gu = 0, fin_gv = 0;
   int cps = 0;  // CTAs per SM at this configuration
   int nstage = 3;
-  CUtensorMap tmX;  // box {32 R rows, 8 columns}
-  CUtensorMap tmM;  // bitmap box {WC * R words, 8 columns}
+  int xt = 0;       // storage type of X read by this plan (FG_X_*)
+  CUtensorMap tmX;  // box {32 R rows, FG_BJ columns}
+  CUtensorMap tmM;  // bitmap box {WC * R words, FG_BJ columns}
 };
 
 struct Workspace {
@@ -66,7 +67,14 @@ struct rpca_ctx {
   double p_hat = 1.0;        // observed fraction
   double F0 = 0.0;           // F(0) = phi(0), for the distance bound
   double F_best = 0.0;       // best objective seen on this context
-  rpca::FgPlan fg_plan;      // K = k, fg mode
+  rpca::FgPlan fg_plan;      // K = k, fg mode, float32 X
+  // Precision form: X stored by the library as bfloat16 or FP8 E4M3 (column-major, ld ldq).
+  void* Xq = nullptr;        // owned
+  int64_t ldq = 0;
+  int xq_dt = 0;             // FG_X_* (0: no narrow copy)
+  float* xscale = nullptr;   // FP8: per-column scales, owned
+  rpca::FgPlan fg_plan_q;    // K = k, fg mode, narrow X
+  const rpca::FgPlan* solve_plan = nullptr;  // the plan the solver's iteration uses
   rpca::FgPlan ap_plan[3][3];  // apply modes: forming rank 0 / 8 / 16 x side
   rpca::Workspace ws;          // partial sums of the objective/gradient plan (graph-captured)
   rpca::Workspace ws_ap;       // partial sums of the apply plans
@@ -117,6 +125,9 @@ struct FgLaunch {
 };
 rpca_status launch_fg(rpca_ctx* c, const FgPlan& P, const FgLaunch& L, cudaStream_t stream);
 const FgPlan* apply_plan(rpca_ctx* c, int K, int side);  // forming rank >= K (0, 8 or 16), side
+rpca_status make_xq(rpca_ctx* c, int xt);                // narrow copy of X (xq.cu)
+// The objective/gradient plan rpca_fg uses: the narrow copy's when there is one.
+inline const FgPlan& eval_plan(const rpca_ctx* c) { return c->xq_dt ? c->fg_plan_q : c->fg_plan; }
 inline void count_launches(rpca_ctx* c, int64_t n) { c->launches += n; }
 
 }  // namespace rpca

@@ -18,6 +18,9 @@
 // per-warp shared-memory slab, and across warps once at the end of the tile, in a fixed
 // order (bitwise deterministic).
 #pragma once
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+
 #include "common.cuh"
 
 namespace rpca {
@@ -41,13 +44,19 @@ struct FgArgs {
   float* PV;         // [nrb][B][n]      D^T Bu partial sums over a CTA's rows
   double* Ppsi;      // [nrb*ncs]        sum of psi over a CTA's tile
   int* err;          // device status word (error bits)
+  const float* xscale;  // FP8 storage: per-column scales (x = stored value * scale)
 };
+
+// Storage type of X read by an instantiation: float32, bfloat16, or FP8 E4M3 with a
+// per-column scale.
+enum { FG_X_F32 = 0, FG_X_BF16 = 1, FG_X_E4M3 = 2 };
+__host__ __device__ constexpr int fg_x_bytes(int xt) { return xt == FG_X_F32 ? 4 : (xt == FG_X_BF16 ? 2 : 1); }
 
 constexpr int FG_BJ = 4;      // columns per pipeline stage
 constexpr int FG_NSTAGE = 6;  // maximum pipeline depth
 
 struct FgSmem {
-  size_t x_off, m_off, v_off, cs_off, tr_off, bar_off, scr_off, total;
+  size_t x_off, m_off, v_off, cs_off, tr_off, sc_off, bar_off, scr_off, total;
 };
 
 constexpr int FG_TR_LD = 36;  // row stride (floats) of the column-sum transposition buffer
@@ -58,15 +67,16 @@ __host__ __device__ inline size_t fg_mask_stage_bytes(int WC, int R) {
   return ((size_t)FG_BJ * WC * R * 4 + 127) & ~(size_t)127;
 }
 
-// Shared-memory carve-up (byte offsets from a 1024-byte aligned base): X stages, bitmap
-// stages, the CTA's factor slice, one slab of column sums per consumer warp, one
-// transposition buffer per consumer warp (JB rows of FG_TR_LD floats), mbarriers.
+// Shared-memory carve-up (byte offsets from a 1024-byte aligned base): X stages (xbytes per
+// element), bitmap stages, the CTA's factor slice, one slab of column sums per consumer warp,
+// one transposition buffer per consumer warp (JB rows of FG_TR_LD floats), the column scales
+// of FP8 storage, mbarriers.
 __host__ __device__ inline FgSmem fg_smem_layout(int WC, int R, bool masked, int BN, int KV, int B, int nstage,
-                                                 int JB) {
+                                                 int JB, int xbytes = 4) {
   FgSmem L;
   size_t o = 0;
   L.x_off = o;
-  o += (size_t)nstage * WC * FG_BJ * 32 * R * 4;
+  o += (size_t)nstage * WC * FG_BJ * 32 * R * xbytes;
   L.m_off = o;
   if (masked) o += (size_t)nstage * fg_mask_stage_bytes(WC, R);
   o = (o + 15) & ~(size_t)15;
@@ -77,6 +87,8 @@ __host__ __device__ inline FgSmem fg_smem_layout(int WC, int R, bool masked, int
   o = (o + 15) & ~(size_t)15;
   L.tr_off = o;
   o += (size_t)WC * JB * FG_TR_LD * 4;
+  L.sc_off = o;
+  if (xbytes == 1) o += (size_t)BN * 4;
   o = (o + 7) & ~(size_t)7;
   L.bar_off = o;
   o += 2 * FG_NSTAGE * 8;
@@ -124,12 +136,14 @@ RPCA_DEV void lane_bit(int p, int e, int lane, int& word, int& bit) {
   }
 }
 
-template <int K, int B, bool SAME, bool MASKED, int R, int J, int SIDE = 0>
+template <int K, int B, bool SAME, bool MASKED, int R, int J, int SIDE = 0, int XT = FG_X_F32>
 __global__ void __launch_bounds__(288, 1) fg_kernel(const __grid_constant__ CUtensorMap tmX,
                                                  const __grid_constant__ CUtensorMap tmM, FgArgs a) {
   using T = FgTraits<K, B, SAME, R, J, SIDE>;
   constexpr int NP = T::NP, ROWS_W = T::ROWS_W, KV = T::KV, JB = T::JB;
   constexpr bool ROWSIDE = SIDE != 2, COLSIDE = SIDE != 1;  // which products are formed
+  constexpr int XB = fg_x_bytes(XT);
+  static_assert(XT == FG_X_F32 || R >= 4, "narrow storage is read four rows per lane at a time");
   if (a.gate != nullptr && *a.gate == 0) return;  // uniform over the grid
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -142,8 +156,9 @@ __global__ void __launch_bounds__(288, 1) fg_kernel(const __grid_constant__ CUte
   const int ncols = min(a.BN, a.n - col0);
   const int nchunks = (ncols + FG_BJ - 1) / FG_BJ;
   const int nst = a.nstage;
-  const FgSmem L = fg_smem_layout(WC, R, MASKED, a.BN, KV, T::CSB, nst, COLSIDE ? JB : 0);
-  float* xs_all = reinterpret_cast<float*>(sm + L.x_off);
+  const FgSmem L = fg_smem_layout(WC, R, MASKED, a.BN, KV, T::CSB, nst, COLSIDE ? JB : 0, XB);
+  unsigned char* xs_all = sm + L.x_off;
+  float* xsc = reinterpret_cast<float*>(sm + L.sc_off);  // FP8 storage: column scales of the slice
   uint32_t* ms_all = reinterpret_cast<uint32_t*>(sm + L.m_off);
   float2* vsl = reinterpret_cast<float2*>(sm + L.v_off);
   float* csum = reinterpret_cast<float*>(sm + L.cs_off);  // [WC][BN][B]
@@ -151,10 +166,10 @@ __global__ void __launch_bounds__(288, 1) fg_kernel(const __grid_constant__ CUte
   uint64_t* full = reinterpret_cast<uint64_t*>(sm + L.bar_off);
   uint64_t* empty = full + FG_NSTAGE;
   double* scr = reinterpret_cast<double*>(sm + L.scr_off);
-  const size_t xbox = (size_t)FG_BJ * ROWS_W;                // floats per warp box of X
+  const size_t xbox = (size_t)FG_BJ * ROWS_W;                // elements per warp box of X
   const size_t mstage = fg_mask_stage_bytes(WC, R) / 4;      // words per bitmap stage
   const int mrow = WC * R;                                   // bitmap words per column of a stage
-  const uint32_t stage_bytes = (uint32_t)(WC * xbox * 4 + (MASKED ? (size_t)FG_BJ * mrow * 4 : 0));
+  const uint32_t stage_bytes = (uint32_t)(WC * xbox * XB + (MASKED ? (size_t)FG_BJ * mrow * 4 : 0));
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < nst; ++s) {
@@ -182,8 +197,8 @@ __global__ void __launch_bounds__(288, 1) fg_kernel(const __grid_constant__ CUte
         }
         mbar_arrive_expect_tx(&full[s], stage_bytes);
         for (int w = 0; w < WC; ++w)
-          tma_load_2d_hint(xs_all + ((size_t)s * WC + w) * xbox, &tmX, row0 + w * ROWS_W, col0 + c * FG_BJ, &full[s],
-                           pol);
+          tma_load_2d_hint(xs_all + ((size_t)s * WC + w) * xbox * XB, &tmX, row0 + w * ROWS_W, col0 + c * FG_BJ,
+                           &full[s], pol);
         if constexpr (MASKED)
           tma_load_2d_hint(ms_all + (size_t)s * mstage, &tmM, row0 / 32, col0 + c * FG_BJ, &full[s], pol);
         issued = c + 1;
@@ -221,6 +236,9 @@ __global__ void __launch_bounds__(288, 1) fg_kernel(const __grid_constant__ CUte
       }
     }
     vsl[idx] = f2(v, v);
+  }
+  if constexpr (XT == FG_X_E4M3) {
+    for (int jj = tid; jj < a.BN; jj += nct) xsc[jj] = jj < ncols ? a.xscale[col0 + jj] : 0.f;
   }
 
   // This lane's rows of the forming factor (negated, so that r' = x - u.v = -r) and,
@@ -274,7 +292,7 @@ __global__ void __launch_bounds__(288, 1) fg_kernel(const __grid_constant__ CUte
       failed = true;
       if (lane == 0) atomicOr(a.err, DEV_ERR_TIMEOUT_FULL);
     }
-    const float* xs = xs_all + ((size_t)s * WC + warp) * xbox;
+    const unsigned char* xsw = xs_all + ((size_t)s * WC + warp) * xbox * XB;  // this warp's box
     const uint32_t* ms = ms_all + (size_t)s * mstage + warp * R;  // this warp's words of column 0
     float2 psi2 = f2(0.f, 0.f);
 #pragma unroll 1
@@ -298,18 +316,46 @@ __global__ void __launch_bounds__(288, 1) fg_kernel(const __grid_constant__ CUte
           for (int b = 0; b < B; ++b) bvv[b] = vrow[K + b];
         }
         float xv[R];
-        if constexpr (R == 2) {
-          const float2 t = *reinterpret_cast<const float2*>(xs + (size_t)cc * ROWS_W + lane_xoff<R>(0, lane));
-          xv[0] = t.x;
-          xv[1] = t.y;
-        } else {
+        if constexpr (XT == FG_X_F32) {
+          const float* xs = reinterpret_cast<const float*>(xsw);
+          if constexpr (R == 2) {
+            const float2 t = *reinterpret_cast<const float2*>(xs + (size_t)cc * ROWS_W + lane_xoff<R>(0, lane));
+            xv[0] = t.x;
+            xv[1] = t.y;
+          } else {
+#pragma unroll
+            for (int grp = 0; grp < R / 4; ++grp) {
+              const float4 t = *reinterpret_cast<const float4*>(xs + (size_t)cc * ROWS_W + lane_xoff<R>(grp, lane));
+              xv[grp * 4 + 0] = t.x;
+              xv[grp * 4 + 1] = t.y;
+              xv[grp * 4 + 2] = t.z;
+              xv[grp * 4 + 3] = t.w;
+            }
+          }
+        } else if constexpr (XT == FG_X_BF16) {
+          // bfloat16 -> float32 is exact: the 16 stored bits are the top half of the float.
+          const uint16_t* xs = reinterpret_cast<const uint16_t*>(xsw);
 #pragma unroll
           for (int grp = 0; grp < R / 4; ++grp) {
-            const float4 t = *reinterpret_cast<const float4*>(xs + (size_t)cc * ROWS_W + lane_xoff<R>(grp, lane));
-            xv[grp * 4 + 0] = t.x;
-            xv[grp * 4 + 1] = t.y;
-            xv[grp * 4 + 2] = t.z;
-            xv[grp * 4 + 3] = t.w;
+            const uint2 t = *reinterpret_cast<const uint2*>(xs + (size_t)cc * ROWS_W + lane_xoff<R>(grp, lane));
+            xv[grp * 4 + 0] = __uint_as_float(t.x << 16);
+            xv[grp * 4 + 1] = __uint_as_float(t.x & 0xffff0000u);
+            xv[grp * 4 + 2] = __uint_as_float(t.y << 16);
+            xv[grp * 4 + 3] = __uint_as_float(t.y & 0xffff0000u);
+          }
+        } else {
+          // E4M3 pairs -> half2 (exact) -> float2 (exact), times the column's scale.
+          const uint8_t* xs = reinterpret_cast<const uint8_t*>(xsw);
+          const float sc = xsc[jl];
+#pragma unroll
+          for (int grp = 0; grp < R / 4; ++grp) {
+            const uint32_t t = *reinterpret_cast<const uint32_t*>(xs + (size_t)cc * ROWS_W + lane_xoff<R>(grp, lane));
+            const float2 lo = __half22float2(__half2(__nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(t & 0xffffu), __NV_E4M3)));
+            const float2 hi = __half22float2(__half2(__nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(t >> 16), __NV_E4M3)));
+            xv[grp * 4 + 0] = lo.x * sc;
+            xv[grp * 4 + 1] = lo.y * sc;
+            xv[grp * 4 + 2] = hi.x * sc;
+            xv[grp * 4 + 3] = hi.y * sc;
           }
         }
         uint32_t mw[R == 2 ? 1 : R / 4];

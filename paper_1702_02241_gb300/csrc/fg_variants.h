@@ -16,10 +16,14 @@ struct FgVariant {
 // Forming rank K (0..16), product width B, fg mode (B == K, operands = forming factors) or
 // apply mode with side 0 (both products), 1 (D Bv only) or 2 (D^T Bu only), masked or not.
 // Returns nullptr when that combination is not compiled.
-const FgVariant* fg_variant(int K, int B, bool same, bool masked, int side = 0);
+// xt: storage type of X (0 float32, 1 bfloat16, 2 FP8 E4M3); narrow storage is compiled for
+// fg mode with K <= 8 only.
+const FgVariant* fg_variant(int K, int B, bool same, bool masked, int side = 0, int xt = 0);
 
 void fg_register_same_small(FgVariant (*tab)[2]);   // K = 1..8
 void fg_register_same_large(FgVariant (*tab)[2]);   // K = 9..16
+void fg_register_same_bf16(FgVariant (*tab)[2]);    // K = 1..8, X stored as bfloat16
+void fg_register_same_e4m3(FgVariant (*tab)[2]);    // K = 1..8, X stored as FP8 E4M3
 void fg_register_apply(FgVariant (*tab)[3][2]);     // K = 0, 8, 16; B = 8; three sides
 
 }  // namespace rpca

@@ -145,19 +145,45 @@ extern "C" rpca_status rpca_solve(rpca_ctx* c, float* U, float* V, rpca_result* 
   const int64_t graph_launches0 = c->graph_launches;
   timer.end();
   timer.begin(1);
+  // Precision form: iterate on the narrow copy of X first (its objective differs from the
+  // float32 one by the storage rounding), then refine on float32 X.  The certificate is
+  // always that of the float32 problem.
+  bool narrow = c->xq_dt != 0;
+  c->solve_plan = narrow ? &c->fg_plan_q : &c->fg_plan;
   if ((s = solver_prepare(c, U, V)) != RPCA_OK) return s;
   timer.end();
   SolverState st;
   const int every = c->opt.cert_every > 0 ? c->opt.cert_every : 0;
   bool certified = false;
   int last_cert_iter = -1;
+  int iter_base = 0, evals_base = 0;  // iterations and trials of the narrow phase
+  double narrow_best = INFINITY;      // best cheap certificate seen in the narrow phase
   rpca_cert cert;
   memset(&cert, 0, sizeof cert);
   int cert_evals = 0;
+  // Leaves the narrow phase: the point so far becomes the start of a float32 solve (fresh
+  // L-BFGS memory; the float32 objective differs from the narrow one).
+  auto refine = [&]() -> rpca_status {
+    cudaMemcpyAsync(U, solver_point(c), sizeof(float) * mk, cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(V, solver_point(c) + mk, sizeof(float) * nk, cudaMemcpyDeviceToDevice, c->stream);
+    iter_base += st.iter;
+    evals_base += st.evals;
+    narrow = false;
+    c->solve_plan = &c->fg_plan;
+    last_cert_iter = -1;
+    return solver_prepare(c, U, V);
+  };
   while (true) {
     if ((s = solver_read_state(c, &st)) != RPCA_OK) return s;
-    if (!st.active) break;
-    if (st.iter >= c->opt.max_iter) break;
+    if (!st.active || st.iter >= c->opt.max_iter - iter_base) {
+      if (narrow && c->opt.refine_fp32 && st.iter < c->opt.max_iter - iter_base) {
+        timer.begin(1);
+        if ((s = refine()) != RPCA_OK) return s;
+        timer.end();
+        continue;
+      }
+      break;
+    }
     if (every > 0 && st.iter > 0 && st.iter % every == 0 && st.iter != last_cert_iter) {
       last_cert_iter = st.iter;
       // Cheap terms first; the spectral term only when they already meet the tolerance.
@@ -170,13 +196,25 @@ extern "C" rpca_status rpca_solve(rpca_ctx* c, float* U, float* V, rpca_result* 
       }
       timer.end();
       if (certified) break;
+      // The narrow phase has done its part once the float32 certificate stops halving
+      // between checks: what is left is the storage rounding of X.
+      if (narrow && c->opt.refine_fp32) {
+        const bool plateau = cert.cert_rel > 0.5 * narrow_best;
+        narrow_best = std::min(narrow_best, cert.cert_rel);
+        if (plateau) {
+          timer.begin(1);
+          if ((s = refine()) != RPCA_OK) return s;
+          timer.end();
+          continue;
+        }
+      }
     }
     if (c->opt.timeout_s > 0) {
       const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
       if (el > c->opt.timeout_s) break;
     }
     int batch = every > 0 ? every - (st.iter % every) : 25;
-    batch = std::max(1, std::min(batch, c->opt.max_iter - st.iter));
+    batch = std::max(1, std::min(batch, c->opt.max_iter - iter_base - st.iter));
     timer.begin(1);
     if ((s = solver_iterations(c, batch)) != RPCA_OK) return s;
     timer.end();
@@ -194,16 +232,16 @@ extern "C" rpca_status rpca_solve(rpca_ctx* c, float* U, float* V, rpca_result* 
   // Fused kernel + finalize + line-search step per while-body pass: one per trial, and one
   // (early-exit) pass in every graph launch that ran no trial.
   const int64_t gl = c->graph_launches - graph_launches0;
-  count_launches(c, 3LL * std::max<int64_t>(gl, (int64_t)st.evals - 1));
+  count_launches(c, 3LL * std::max<int64_t>(gl, (int64_t)(evals_base + st.evals) - 1));
   timer.collect(&r.ms_init, &r.ms_iter, &r.ms_cert);
-  r.F = st.f;
-  r.iters = st.iter;
-  r.evals = st.evals;
+  r.F = narrow ? cert.F : st.f;  // the float32 objective (the narrow phase's st.f is not)
+  r.iters = iter_base + st.iter;
+  r.evals = evals_base + st.evals;
   r.cert_evals = cert_evals;
   r.cert = cert;
   r.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   r.status = cert.cert_rel <= c->opt.cert_tol ? RPCA_OK : RPCA_ENOTCONV;
-  if (st.f < c->F_best) c->F_best = st.f;
+  if (r.F < c->F_best) c->F_best = r.F;
   if (res) *res = r;
   if (r.status != RPCA_OK) {
     char buf[200];

@@ -654,6 +654,7 @@ struct SolverBuffers {
   cudaStream_t cap = nullptr, cap2 = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  const FgPlan* plan = nullptr;  // objective/gradient plan the iteration was built for
 };
 
 static int mem_cap(int mem) { return mem <= 4 ? 4 : (mem <= 10 ? 10 : (mem <= 16 ? 16 : 32)); }
@@ -861,11 +862,13 @@ static FgLaunch trial_launch(rpca_ctx* c) {
 
 static rpca_status ensure_solver(rpca_ctx* c) {
   const int mcap = mem_cap(c->opt.lbfgs_mem);
-  if (c->sol && c->sol->mcap == mcap) return RPCA_OK;
+  const FgPlan* plan = c->solve_plan ? c->solve_plan : &c->fg_plan;
+  if (c->sol && c->sol->mcap == mcap && c->sol->plan == plan) return RPCA_OK;
   free_solver(c);
   SolverBuffers* b = new SolverBuffers();
   c->sol = b;
   b->mcap = mcap;
+  b->plan = plan;
   b->N = (int64_t)(c->m + c->n) * c->k;
   const int64_t N = b->N;
   SOL_CUDA(cudaMalloc(&b->x, sizeof(float) * 5 * N));
@@ -914,7 +917,7 @@ static rpca_status ensure_solver(rpca_ctx* c) {
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     e = cudaStreamBeginCaptureToGraph(b->cap2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-      rpca_status s = launch_fg(c, c->fg_plan, trial_launch(c), b->cap2);
+      rpca_status s = launch_fg(c, *b->plan, trial_launch(c), b->cap2);
       if (s == RPCA_OK) {
         ls_step_kernel<<<1, 32, 0, b->cap2>>>(b->st, h, 1);
         e = cudaGetLastError();
@@ -950,7 +953,7 @@ static rpca_status solver_start(rpca_ctx* c) {
   L.GU = b->g;
   L.GV = b->g + mk;
   L.out = b->st->out;
-  rpca_status s = launch_fg(c, c->fg_plan, L, c->stream);
+  rpca_status s = launch_fg(c, *b->plan, L, c->stream);
   if (s != RPCA_OK) return s;
   solver_init_kernel<<<1, 1, 0, c->stream>>>(b->st, c->opt.lbfgs_mem, c->opt.max_iter, c->opt.gtol,
                                               c->opt.ls_noise);
@@ -986,7 +989,7 @@ static rpca_status host_iteration(rpca_ctx* c) {
     SOL_CUDA(cudaMemcpyAsync(&b->host->ls.state, &b->st->ls.state, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     SOL_CUDA(cudaStreamSynchronize(c->stream));
     if (!b->host->active || b->host->ls.state != LS_RUNNING) break;
-    rpca_status s = launch_fg(c, c->fg_plan, trial_launch(c), c->stream);
+    rpca_status s = launch_fg(c, *b->plan, trial_launch(c), c->stream);
     if (s != RPCA_OK) return s;
     ls_step_kernel<<<1, 32, 0, c->stream>>>(b->st, 0, 0);
     SOL_CUDA(cudaGetLastError());

@@ -88,6 +88,8 @@ def lib():
     L.rpca_solve_log.restype = I
     L.rpca_solve_trials.argtypes = [P, C.POINTER(C.c_double), I, C.POINTER(C.c_int)]
     L.rpca_solve_trials.restype = I
+    L.rpca_x_storage.argtypes = [P, C.POINTER(C.c_int), C.c_void_p, C.c_int64, C.c_void_p]
+    L.rpca_x_storage.restype = I
     L.rpca_fg_noalloc.argtypes = [I64, I64, P, I64, I, D, D, P, P, C.POINTER(C.c_double), P, P, P]
     L.rpca_fg_noalloc.restype = I
     L.rpca_version.argtypes = []
@@ -98,7 +100,7 @@ def lib():
 
 EXPORTED = ["rpca_default_options", "rpca_create", "rpca_fg", "rpca_apply", "rpca_init_sketch", "rpca_solve",
             "rpca_certificate", "rpca_destroy", "rpca_last_error", "rpca_version", "rpca_plan_info",
-            "rpca_profile", "rpca_profile_read", "rpca_solve_log", "rpca_solve_trials", "rpca_fg_noalloc"]
+            "rpca_profile", "rpca_profile_read", "rpca_solve_log", "rpca_solve_trials", "rpca_x_storage", "rpca_fg_noalloc"]
 
 
 class RpcaError(RuntimeError):
@@ -217,6 +219,20 @@ def rpca_solve_trials(ctx, max_rows=256):
     rows = C.c_int(0)
     _check(lib().rpca_solve_trials(ctx, out, max_rows, C.byref(rows)), ctx)
     return [list(out[7 * i:7 * i + 7]) for i in range(rows.value)]
+
+
+def rpca_x_storage(ctx, m, n):
+    """(dtype, stored elements as a numpy (m, n) array of uint16/uint8 or None, scales or None)."""
+    import numpy as np
+    dt = C.c_int(0)
+    _check(lib().rpca_x_storage(ctx, C.byref(dt), None, 0, None), ctx)
+    if dt.value == RPCA_F32:
+        return dt.value, None, None
+    buf = np.zeros((n, m), np.uint16 if dt.value == RPCA_BF16 else np.uint8)
+    sc = np.zeros(n, np.float32)
+    _check(lib().rpca_x_storage(ctx, C.byref(dt), buf.ctypes.data_as(C.c_void_p), m,
+                                sc.ctypes.data_as(C.c_void_p) if dt.value == RPCA_FP8E4M3 else None), ctx)
+    return dt.value, buf.T, (sc if dt.value == RPCA_FP8E4M3 else None)
 
 
 def rpca_destroy(ctx):
