@@ -27,6 +27,11 @@ Readings of the paper taken here (each is pinned by a test):
   residue of a factor column that the nuclear penalty drives to zero, and the certificate is
   then the one of L with that direction truncated (a valid subgradient of the truncated
   point, as the W' block of Eq. subdiff allows).
+* A direction whose whole nuclear-norm term is negligible against the objective,
+  lam_L sigma_i <= 1e-12 F(L), is numerically zero and goes to the complement block as
+  well, active or not (the relative test above cannot see it when every singular value of
+  L is at that level, e.g. factors at the rounding floor of float32 when the solution is
+  L = 0).  Truncating it changes F by at most (lam_L + ||D||_2) sigma_i.
 * Distance bound: ||L - L*||_F <= ||L||_F + F_bound / lam_L with
   F_bound = min(F(0) = phi(0), best objective seen), and the optimality-gap bound
   F(L) - F* <= cert * (||L||_F + F_bound / lam_L).
@@ -41,6 +46,7 @@ from . import core
 
 TAU = 1e-8
 DROP_TAU = 1e-3
+NEG_TAU = 1e-12
 
 
 @dataclasses.dataclass
@@ -113,10 +119,12 @@ def certificate(X, mask, U, V, lam_L, lam_S, F_best=None, tau=TAU, t4_method="au
     V = np.asarray(V, np.float64)
     R = core.residual(X, U, V)
     D = core.D_of_R(R, mask, lam_S)
+    F = 0.5 * lam_L * (np.sum(U * U) + np.sum(V * V)) + core.phi_of_R(R, mask, lam_S)
     U1, V1, s1 = range_bases(U, V, tau)
     if s1.size:
         b_diag = np.einsum("ij,ij->j", U1, D @ V1)
         keep = ~((s1 <= DROP_TAU * s1[0]) & (np.abs(lam_L + b_diag) > 0.5 * lam_L))
+        keep &= ~(lam_L * s1 <= NEG_TAU * F)
         U1, V1, s1_kept = U1[:, keep], V1[:, keep], s1[keep]
     else:
         s1_kept = s1
@@ -134,7 +142,6 @@ def certificate(X, mask, U, V, lam_L, lam_S, F_best=None, tau=TAU, t4_method="au
     sp = perp_singular_values(D, U1, V1, lam_L, t4_method)
     t4 = float(np.sum(np.maximum(sp - lam_L, 0.0) ** 2))
     cert = float(np.sqrt(max(t1 + t2 + t3 + t4, 0.0)))
-    F = 0.5 * lam_L * (np.sum(U * U) + np.sum(V * V)) + core.phi_of_R(R, mask, lam_S)
     F0 = core.phi_of_R(-np.asarray(X, np.float64), mask, lam_S)
     F_bound = min(F0, F if F_best is None else min(F, F_best))
     normL = float(np.sqrt(np.sum(s1 ** 2)))

@@ -348,3 +348,38 @@ def test_certificate_moves_tiny_inactive_direction_to_complement():
     # Without the rule the extra direction would sit in U1 with u^T D v ~ 0: t1 >= lam_L^2 / 4.
     U1, V1, s = ocert.range_bases(U, V)
     assert s.size == 4 and s[3] / s[0] < 1e-3
+
+
+def test_certificate_of_rounding_floor_factors_is_that_of_zero():
+    """Factors at the float32 rounding floor (|L| ~ 1e-44) when the solution is L = 0: every
+    direction is negligible, r = 0, and the certificate equals the closed form at L = 0:
+    t1 = t2 = t3 = 0, t4 = sum_i (sigma_i(D0) - lam_L)_+^2 with D0 = clip(-X) (Sec. 3.4),
+    computed here from a dense SVD of D0 directly."""
+    g = np.random.default_rng(8)
+    m, n, k = 60, 40, 4
+    X = g.normal(size=(m, n))
+    lam_S = 0.3
+    D0 = np.clip(-X, -lam_S, lam_S)
+    sv = np.linalg.svd(D0, compute_uv=False)
+    for lam_L in (0.8 * sv[0], 1.1 * sv[0]):   # zero is not optimal / optimal
+        U = 1e-22 * g.normal(size=(m, k))
+        V = 1e-22 * g.normal(size=(n, k))
+        c = ocert.certificate(X, None, U, V, lam_L, lam_S)
+        assert c.rank_r == 0
+        assert c.t1 == 0.0 and c.t2 == 0.0 and c.t3 == 0.0
+        assert c.t4 == pytest.approx(np.sum(np.maximum(sv - lam_L, 0.0) ** 2), rel=1e-9, abs=1e-12)
+    # Without the rule the same point keeps a direction in U1 with u^T D v far from -lam_L.
+    U1, V1, s = ocert.range_bases(U, V)
+    assert s.size == k
+
+
+def test_certificate_keeps_small_but_significant_direction():
+    """A direction far below sigma_1 but not negligible against F stays in U1 when active
+    (the negligibility floor is absolute in F, not relative to sigma_1)."""
+    X = _lowrank_noise(20, 15, 3, 4)
+    lam_L = 1.0
+    Ub, Vb = convex.balanced_factors(convex.svt(X, lam_L), 3)
+    c = ocert.certificate(X, np.ones(X.shape, np.uint8), Ub, Vb, lam_L, np.inf)
+    U1, V1, s = ocert.range_bases(Ub, Vb)
+    assert s.size == 3 and lam_L * s[-1] > 1e-12 * c.F
+    assert c.rank_r == 3 and c.cert_rel < 1e-6
