@@ -39,6 +39,7 @@ constexpr int LZ_SMAX = 32;   // maximum block steps (Krylov dimension 256)
 constexpr int LZ_TMAX = LZ_B * LZ_SMAX;
 constexpr double RANK_TAU = 1e-8;  // numerical rank of L: sigma_i > RANK_TAU * sigma_1
 constexpr double DROP_TAU = 1e-3;  // tiny-and-inactive directions go to the complement
+constexpr double NEG_TAU = 1e-12;  // lam_L sigma_i <= NEG_TAU F: numerically zero direction
 
 struct CertState {
   double AUU[CERT_KMAX * CERT_KMAX], AVV[CERT_KMAX * CERT_KMAX], MUDV[CERT_KMAX * CERT_KMAX];
@@ -85,7 +86,7 @@ struct CertBuffers {
 
 // ---------------------------------------------------------------------------------------------
 // Step 3: one CTA of 256 threads.
-__global__ void __launch_bounds__(256) cert_small_kernel(CertState* st, int k, double lam_L) {
+__global__ void __launch_bounds__(256) cert_small_kernel(CertState* st, int k, double lam_L, const double* Fp) {
   __shared__ double Au[CERT_KMAX * CERT_KMAX], Wu[CERT_KMAX * CERT_KMAX], su[CERT_KMAX];
   __shared__ double Av[CERT_KMAX * CERT_KMAX], Wv[CERT_KMAX * CERT_KMAX], sv[CERT_KMAX];
   __shared__ double M[CERT_KMAX * CERT_KMAX], Vm[CERT_KMAX * CERT_KMAX], sm[CERT_KMAX];
@@ -167,14 +168,18 @@ __global__ void __launch_bounds__(256) cert_small_kernel(CertState* st, int k, d
   // A direction that is both tiny (sigma_i <= DROP_TAU sigma_1) and inactive
   // (|lam_L + u_i^T D v_i| > lam_L / 2) is moved to the complement block: it is rounding
   // residue of a factor column that the nuclear penalty drives to zero, and the certificate
-  // is then that of L with it truncated.
+  // is then that of L with it truncated.  So is a direction whose nuclear-norm term is
+  // negligible against the objective (lam_L sigma_i <= NEG_TAU F), which the relative test
+  // cannot see when all of L is at the float32 rounding floor (a solution L = 0).
   __shared__ int keep[CERT_KMAX], rk;
   if (t == 0) {
     rk = 0;
+    const double Fv = *Fp;
     for (int c = 0; c < r; ++c) {
       const bool tiny = sm[ordm[c]] <= DROP_TAU * sm[ordm[0]];
       const bool inactive = fabs(lam_L + Bs[c + c * CERT_KMAX]) > 0.5 * lam_L;
-      if (!(tiny && inactive)) keep[rk++] = c;
+      const bool negligible = lam_L * sm[ordm[c]] <= NEG_TAU * Fv;
+      if (!(tiny && inactive) && !negligible) keep[rk++] = c;
     }
     if (rk < r) {
       for (int q = 0; q < rk; ++q) {
@@ -656,7 +661,7 @@ rpca_status cert_compute(rpca_ctx* c, const float* U, const float* V, rpca_cert*
   CERT_CUDA(ts_gram_c(c, U, m, k, b->DV, m, k, m, st->G, b->ts, c->stream));
   CERT_CUDA(cudaMemcpy2DAsync(st->MUDV, CERT_KMAX * 8, st->G, k * 8, k * 8, k, cudaMemcpyDeviceToDevice, c->stream));
   // 3. Small factorisations, t1.
-  cert_small_kernel<<<1, 256, 0, c->stream>>>(st, k, c->lam_L);
+  cert_small_kernel<<<1, 256, 0, c->stream>>>(st, k, c->lam_L, c->ws.out);
   count_launches(c, 1);
   CERT_CUDA(cudaGetLastError());
   // 4. t3 = ||DV T_V - U P2||^2, t2 = ||DtU T_U - V P3||^2.

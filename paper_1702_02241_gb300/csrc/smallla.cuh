@@ -16,6 +16,43 @@ RPCA_DEV void rr_pair(int r, int k, int ne, int& p, int& q) {
   }
 }
 
+// 2^-e for x in [2^e, 2^(e+1)) when x is positive, normal and finite (from the exponent
+// field; exact), else 0.
+RPCA_DEV double pow2_inv_scale(double x) {
+  const int e = (int)((__double_as_longlong(x) >> 52) & 0x7ff);
+  if (!(x > 0.0) || e == 0 || e >= 0x7fe) return 0.0;
+  return __longlong_as_double((long long)(2046 - e) << 52);
+}
+RPCA_DEV float pow2_inv_scale(float x) {
+  const int e = (int)((__float_as_uint(x) >> 23) & 0xff);
+  if (!(x > 0.f) || e == 0 || e >= 0xfe) return 0.f;
+  return __uint_as_float((unsigned)(254 - e) << 23);
+}
+
+// Rotation (cs, sn) of one Jacobi step on columns with squared norms al, be and inner
+// product ga.  The angle is formed in float32 with fast operations (its accuracy only affects
+// how far the step reduces a_p . a_q) from (be - al) and ga scaled by the same power of two,
+// so that tiny or huge columns neither underflow nor overflow float32 (a flushed ga would
+// make the angle 0/0); then (cs, sn) is renormalised in T by one Newton step on
+// 1/sqrt(cs^2 + sn^2), so that the rotation is orthogonal to T's rounding (float64 square
+// roots and divides cost hundreds of cycles each on this GPU).  Returns false, and leaves
+// the pair alone, when the scaled inner product is below float32 resolution or not finite.
+template <typename T>
+RPCA_DEV bool jacobi_rotation(T al, T be, T ga, T& cs, T& sn) {
+  const T sc = pow2_inv_scale(al + be);
+  const float g = (float)(ga * sc);
+  if (!(fabsf(g) >= 1e-30f && fabsf(g) <= 2.f)) return false;
+  const float zeta = __fdividef((float)((be - al) * sc), 2.f * g);
+  const float tf = copysignf(1.f, zeta) * __frcp_rn(fabsf(zeta) + __fsqrt_rn(fmaf(zeta, zeta, 1.f)));
+  const float csf = __frsqrt_rn(fmaf(tf, tf, 1.f));
+  cs = (T)csf;
+  sn = (T)(csf * tf);
+  const T corr = T(1.5) - T(0.5) * (cs * cs + sn * sn);
+  cs *= corr;
+  sn *= corr;
+  return true;
+}
+
 // One-sided Jacobi (Hestenes) SVD, executed by the whole CTA (blockDim multiple of 32).
 // A: rows x cols column-major (lda), overwritten by U * diag(sig) (columns in input order).
 // V: cols x cols (ldv), right singular vectors.  sig[j] = ||A_j||.  Returns the sweep count.
@@ -65,18 +102,9 @@ __device__ int cta_jacobi_svd(T* A, int rows, int cols, int lda, T* V, int ldv, 
           be += __shfl_xor_sync(0xffffffffu, be, o);
           ga += __shfl_xor_sync(0xffffffffu, ga, o);
         }
-        if (ga != T(0) && ga * ga > tol * tol * (al * be) && fabs(ga) > noise * (al + be)) {
-          // Rotation angle in float32 with fast operations (its accuracy only affects how
-          // far this step reduces a_p . a_q), then (cs, sn) renormalised in T by one Newton
-          // step on 1/sqrt(cs^2 + sn^2), so that the rotation is orthogonal to T's rounding
-          // (float64 square roots and divides cost hundreds of cycles each on this GPU).
-          const float zeta = __fdividef((float)(be - al), 2.f * (float)ga);
-          const float tf = copysignf(1.f, zeta) * __frcp_rn(fabsf(zeta) + __fsqrt_rn(fmaf(zeta, zeta, 1.f)));
-          const float csf = __frsqrt_rn(fmaf(tf, tf, 1.f));
-          T cs = (T)csf, sn = (T)(csf * tf);
-          const T corr = T(1.5) - T(0.5) * (cs * cs + sn * sn);
-          cs *= corr;
-          sn *= corr;
+        T cs, sn;
+        if (ga != T(0) && ga * ga > tol * tol * (al * be) && fabs(ga) > noise * (al + be) &&
+            jacobi_rotation(al, be, ga, cs, sn)) {
           for (int i = lane; i < rows; i += 32) {
             const T x = ap[i], y = aq[i];
             ap[i] = cs * x - sn * y;
@@ -156,18 +184,13 @@ __device__ int warp_jacobi_svd(T* A, int rows, int cols, int lda, T* V, int ldv,
       const T be = (be4[0] + be4[1]) + (be4[2] + be4[3]);
       const T ga = (ga4[0] + ga4[1]) + (ga4[2] + ga4[3]);
       T cs = T(1), sn = T(0);
-      const bool rot = act && ga != T(0) && ga * ga > tol * tol * (al * be) && fabs(ga) > noise * (al + be);
-      if (rot) {
-        const float zeta = __fdividef((float)(be - al), 2.f * (float)ga);
-        const float tf = copysignf(1.f, zeta) * __frcp_rn(fabsf(zeta) + __fsqrt_rn(fmaf(zeta, zeta, 1.f)));
-        const float csf = __frsqrt_rn(fmaf(tf, tf, 1.f));
-        cs = (T)csf;
-        sn = (T)(csf * tf);
-        const T corr = T(1.5) - T(0.5) * (cs * cs + sn * sn);
-        cs *= corr;
-        sn *= corr;
-        rotated = true;
+      const bool rot = act && ga != T(0) && ga * ga > tol * tol * (al * be) && fabs(ga) > noise * (al + be) &&
+                       jacobi_rotation(al, be, ga, cs, sn);
+      if (!rot) {
+        cs = T(1);
+        sn = T(0);
       }
+      rotated |= rot;
       // p' = cs p - sn q,  q' = sn p + cs q.
       const T ca = cs, cb = low ? -sn : sn;
 #pragma unroll
@@ -196,12 +219,19 @@ __device__ int warp_jacobi_svd(T* A, int rows, int cols, int lda, T* V, int ldv,
   return sweep;
 }
 
-// order[t] = index of the t-th largest of v[0..n) (ties by index); run by the CTA.
+// order[t] = index of the t-th largest of v[0..n) (ties by index, NaNs last by index); run by
+// the CTA.  The ranks come from a strict total order on (value, index), so `order` is a
+// permutation of 0..n-1 whatever the values are: callers index memory with it.
 template <typename T>
 __device__ void cta_sort_desc(const T* v, int n, int* order) {
   for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const T vj = v[j];
+    const bool nj = isnan(vj);
     int rank = 0;
-    for (int i = 0; i < n; ++i) rank += (v[i] > v[j]) || (v[i] == v[j] && i < j);
+    for (int i = 0; i < n; ++i) {
+      const T vi = v[i];
+      rank += isnan(vi) ? (nj && i < j) : (nj || vi > vj || (vi == vj && i < j));
+    }
     order[rank] = j;
   }
   __syncthreads();

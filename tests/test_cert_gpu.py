@@ -98,3 +98,46 @@ def test_certificate_plateau_when_k_too_small():
     assert o.t4 > 1.0
     compare(c, o, 1.0)
     P.close()
+
+
+def test_certificate_with_vanishing_surplus_columns():
+    """k above the rank of L: the nuclear penalty drives the surplus factor columns to zero,
+    through the float32 subnormal range.  Their Gram entries are then tiny float64 values;
+    the Jacobi rotations of the small eigen-problems must stay finite there, and the
+    certificate must be that of the rank-5 part."""
+    g = np.random.default_rng(17)
+    m, n, k = 1092, 181, 11
+    X = np.asfortranarray(g.normal(size=(m, n)).astype(np.float32))
+    U, V = gen.factors(m, n, k, seed=4, scale=0.5)
+    for j in range(5, k):
+        s = np.float32(10.0 ** (-19 - (j - 5)))
+        U[:, j] *= s
+        V[:, j] *= s
+    P = make_problem(X, None, k, 2.0, 0.5)
+    c = P.certificate(dev(U), dev(V))
+    o = ocert.certificate(X, None, U, V, 2.0, 0.5)
+    assert math.isfinite(c.cert) and c.rank_r == o.rank_r == 5
+    compare(c, o, 2.0)
+    P.close()
+
+
+@pytest.mark.parametrize("zero_optimal", [True, False])
+def test_certificate_of_rounding_floor_factors(zero_optimal):
+    """Factors at the float32 rounding floor (|U|, |V| ~ 1e-22): L is numerically zero, r = 0,
+    and the certificate is the one of L = 0 (t4 from sigma_i(clip(-X)) against lam_L)."""
+    g = np.random.default_rng(21)
+    m, n, k = 1092, 181, 11
+    X = np.asfortranarray(g.normal(size=(m, n)).astype(np.float32))
+    lam_S = 0.3
+    s0 = np.linalg.svd(np.clip(-X.astype(np.float64), -lam_S, lam_S), compute_uv=False)[0]
+    lam_L = 1.1 * s0 if zero_optimal else 0.8 * s0
+    U = np.asfortranarray((1e-22 * g.normal(size=(m, k))).astype(np.float32))
+    V = np.asfortranarray((1e-22 * g.normal(size=(n, k))).astype(np.float32))
+    P = make_problem(X, None, k, lam_L, lam_S)
+    c = P.certificate(dev(U), dev(V))
+    o = ocert.certificate(X, None, U, V, lam_L, lam_S)
+    assert c.rank_r == o.rank_r == 0
+    compare(c, o, lam_L)
+    if zero_optimal:
+        assert c.cert_rel == 0.0
+    P.close()

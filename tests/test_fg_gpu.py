@@ -58,7 +58,8 @@ def random_case(m, n, k, seed, mask_p=None, lam_S=0.3, scale=0.5):
 
 @pytest.mark.parametrize("m,n,k", [(500, 400, 10), (37, 29, 3), (1001, 77, 1), (3000, 260, 5),
                                    (5000, 300, 16), (2100, 130, 8), (64, 8, 2), (9, 5, 4), (4099, 1027, 6),
-                                   (777, 333, 12), (1500, 99, 13), (200, 17, 7)])
+                                   (777, 333, 12), (1500, 99, 13), (200, 17, 7), (1092, 181, 11),
+                                   (640, 90, 9), (333, 120, 15), (2035, 193, 14)])
 def test_fg_unmasked(m, n, k):
     X, mask, U, V, lam_L, lam_S = random_case(m, n, k, seed=m + n + k)
     check(*run_case(X, mask, U, V, lam_L, lam_S))
