@@ -77,6 +77,8 @@ typedef struct {
   int sketch_power;      /* rSVD power iterations q (2) */
   double ls_noise;       /* relative noise level of F below which the line search also accepts
                             the approximate Wolfe conditions (Hager & Zhang 2005); 1e-8 */
+  int autotune;          /* 1 (default): time the best launch configurations of the planner's
+                            model on the device; 0: take the model's choice */
 } rpca_options;
 
 typedef struct {
@@ -169,6 +171,34 @@ RPCA_API rpca_status rpca_init_sketch(rpca_ctx *c, const float *Omega, float *U,
  * opt.refine_fp32 == 0).  The certificate and res->F are always those of float32 X.
  */
 RPCA_API rpca_status rpca_solve(rpca_ctx *c, float *U, float *V, rpca_result *res);
+
+/*
+ * Batched form: count independent problems (m[i] x n[i] float32 X[i] on the device,
+ * column-major, leading dimension ldx[i] (NULL: m[i]), rank k[i], lambda_L[i], lambda_S[i],
+ * fully observed), each a context of its own (rpca_create's checks and ownership rules,
+ * options opt for all, launch configurations from the planner's model without device
+ * timing), each with a CUDA stream the batch owns.  The paper has no counterpart: it
+ * solves one problem at a time; this is an interface of this library for many small ones.
+ * Errors: rpca_batch_last_error(NULL).
+ */
+typedef struct rpca_batch rpca_batch;
+RPCA_API rpca_status rpca_create_batch(rpca_batch **out, int count, const int64_t *m, const int64_t *n,
+                                       const float *const *X, const int64_t *ldx, const int *k,
+                                       const double *lambda_L, const double *lambda_S, const rpca_options *opt,
+                                       void *cuda_stream);
+/*
+ * Solves every problem of the batch as rpca_solve does (U[i], V[i]: device m[i] x k[i] and
+ * n[i] x k[i] buffers, in and out), concurrently: host workers drive the instances' solves
+ * on their own streams, so that their kernels overlap on the GPU.  res (may be NULL) receives
+ * count results.  Work on cuda_stream before the call is ordered before the solves, and the
+ * stream is ordered after them.  Returns RPCA_OK when every instance met its certificate
+ * tolerance, RPCA_ENOTCONV when some did not (see res[i].status), another status on an error.
+ */
+RPCA_API rpca_status rpca_solve_batch(rpca_batch *b, float *const *U, float *const *V, rpca_result *res);
+RPCA_API rpca_ctx *rpca_batch_context(rpca_batch *b, int i); /* instance i's context (owned by b) */
+RPCA_API int rpca_batch_size(const rpca_batch *b);
+RPCA_API const char *rpca_batch_last_error(const rpca_batch *b);
+RPCA_API void rpca_destroy_batch(rpca_batch *b);
 
 /*
  * The library's narrow copy of X (precision form): *dtype receives the storage type

@@ -368,7 +368,7 @@ static rpca_status make_plan(rpca_ctx* c, FgPlan* P, int K, int B, bool same, in
   const PlanKey key{c->device, c->m, c->n, c->ldx, K, B * 4 + side, same, masked, xt};
   int pick = 0;
   int cached_wc = 0, cached_ncs = 0;
-  const bool measure = !(force_wc || force_ncs) && autotune_enabled() && cands.size() > 1;
+  const bool measure = !(force_wc || force_ncs) && autotune_enabled() && c->opt.autotune && cands.size() > 1;
   if (measure && plan_cache_get(key, &cached_wc, &cached_ncs)) {
     for (size_t i = 0; i < cands.size(); ++i)
       if (plan_code(cands[i].second) == cached_wc && cands[i].second.ncs == cached_ncs) pick = (int)i;
@@ -396,10 +396,16 @@ static rpca_status make_plan(rpca_ctx* c, FgPlan* P, int K, int B, bool same, in
   return RPCA_OK;
 }
 
+// Grows a workspace buffer.  Work already queued on the context's stream may still use the
+// old buffer (the stream may be non-blocking, which cudaFree's implicit synchronisation does
+// not cover), so the stream is drained first.
 template <typename T>
 static rpca_status ensure(rpca_ctx* c, T** p, size_t* have, size_t need) {
   if (*have >= need) return RPCA_OK;
-  if (*p) cudaFree(*p);
+  if (*p) {
+    RPCA_CUDA(c, cudaStreamSynchronize(c->stream));
+    cudaFree(*p);
+  }
   *p = nullptr;
   *have = 0;
   RPCA_CUDA(c, cudaMalloc(p, std::max<size_t>(need, 1) * sizeof(T)));
@@ -553,6 +559,7 @@ void rpca_default_options(rpca_options* o) {
   o->seed = 0;
   o->x_dtype = RPCA_F32;
   o->refine_fp32 = 1;
+  o->autotune = 1;
   o->timeout_s = 0.0;
   o->gtol = 0.0;
   o->sketch_oversample = 10;

@@ -1,0 +1,131 @@
+// Batched form: many independent problems (the C4 workload of varied m, n, k) solved
+// concurrently.  Each instance is a full context with its own CUDA stream, planned by the
+// time model alone (no per-shape timing: hundreds of shapes), and its own graph-captured
+// L-BFGS iteration.  One host thread starts every solve and then steps them round-robin;
+// each step waits for its own stream only, so the instances' iterations overlap on the GPU
+// (a small instance fills a few SMs only) without any two host threads in the CUDA API.
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ctx.h"
+
+namespace rpca {
+rpca_status solve_jobs(rpca_ctx* const* ctx, float* const* U, float* const* V, rpca_result* res, int count,
+                       rpca_status* status);  // solve.cu
+}
+
+struct rpca_batch {
+  std::vector<rpca_ctx*> ctx;
+  std::vector<cudaStream_t> streams;  // owned
+  cudaStream_t user = nullptr;
+  std::string err;
+};
+
+namespace {
+thread_local char g_batch_err[512];
+}  // namespace
+
+extern "C" {
+
+rpca_status rpca_create_batch(rpca_batch** out, int count, const int64_t* m, const int64_t* n, const float* const* X,
+                              const int64_t* ldx, const int* k, const double* lambda_L, const double* lambda_S,
+                              const rpca_options* opt, void* cuda_stream) {
+  if (!out) return RPCA_EINVAL;
+  *out = nullptr;
+  if (count < 1 || !m || !n || !X || !k || !lambda_L || !lambda_S) {
+    snprintf(g_batch_err, sizeof g_batch_err, "count >= 1 and the m, n, X, k, lambda arrays are required");
+    return RPCA_EINVAL;
+  }
+  rpca_batch* b = new (std::nothrow) rpca_batch();
+  if (!b) return RPCA_ENOMEM;
+  b->user = static_cast<cudaStream_t>(cuda_stream);
+  b->ctx.assign(count, nullptr);
+  b->streams.assign(count, nullptr);
+  rpca_options o;
+  rpca_default_options(&o);
+  if (opt) o = *opt;
+  o.autotune = 0;  // the time model only: timing every shape would dominate
+  for (int i = 0; i < count; ++i) {
+    if (cudaStreamCreateWithFlags(&b->streams[i], cudaStreamNonBlocking) != cudaSuccess) {
+      rpca_destroy_batch(b);
+      snprintf(g_batch_err, sizeof g_batch_err, "cudaStreamCreate failed");
+      return RPCA_ECUDA;
+    }
+  }
+  for (int i = 0; i < count; ++i) {
+    const int64_t ld = ldx ? ldx[i] : m[i];
+    const rpca_status r = rpca_create(&b->ctx[i], m[i], n[i], X[i], ld, nullptr, 0, k[i], lambda_L[i], lambda_S[i],
+                                      &o, b->streams[i]);
+    if (r != RPCA_OK) {
+      snprintf(g_batch_err, sizeof g_batch_err, "instance %d: %s", i, rpca_last_error(nullptr));
+      rpca_destroy_batch(b);
+      return r;
+    }
+  }
+  *out = b;
+  return RPCA_OK;
+}
+
+rpca_status rpca_solve_batch(rpca_batch* b, float* const* U, float* const* V, rpca_result* res) {
+  if (!b || !U || !V) return RPCA_EINVAL;
+  const int count = (int)b->ctx.size();
+  // Inputs written on the caller's stream come first.
+  cudaEvent_t ready = nullptr;
+  if (cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) != cudaSuccess) return RPCA_ECUDA;
+  cudaEventRecord(ready, b->user);
+  for (int i = 0; i < count; ++i) cudaStreamWaitEvent(b->streams[i], ready, 0);
+  cudaEventDestroy(ready);
+  std::vector<rpca_result> local(count);
+  std::vector<rpca_status> st(count, RPCA_OK);
+  rpca::solve_jobs(b->ctx.data(), U, V, local.data(), count, st.data());
+  int notconv = 0;
+  rpca_status s = RPCA_OK;
+  for (int i = 0; i < count; ++i) {
+    if (st[i] == RPCA_ENOTCONV) ++notconv;
+    else if (st[i] != RPCA_OK && s == RPCA_OK) s = st[i];
+  }
+  if (res) memcpy(res, local.data(), sizeof(rpca_result) * count);
+  // Every solve has synchronised its own stream; order the caller's stream after them too.
+  for (int i = 0; i < count; ++i) {
+    cudaEvent_t done = nullptr;
+    if (cudaEventCreateWithFlags(&done, cudaEventDisableTiming) == cudaSuccess) {
+      cudaEventRecord(done, b->streams[i]);
+      cudaStreamWaitEvent(b->user, done, 0);
+      cudaEventDestroy(done);
+    }
+  }
+  if (s != RPCA_OK) {
+    for (int i = 0; i < count; ++i)
+      if (st[i] != RPCA_OK && st[i] != RPCA_ENOTCONV) {
+        b->err = "instance " + std::to_string(i) + ": " + rpca_last_error(b->ctx[i]);
+        break;
+      }
+    return s;
+  }
+  if (notconv > 0) {
+    b->err = std::to_string(notconv) + " instance(s) stopped before the certificate tolerance";
+    return RPCA_ENOTCONV;
+  }
+  return RPCA_OK;
+}
+
+rpca_ctx* rpca_batch_context(rpca_batch* b, int i) {
+  if (!b || i < 0 || i >= (int)b->ctx.size()) return nullptr;
+  return b->ctx[i];
+}
+
+int rpca_batch_size(const rpca_batch* b) { return b ? (int)b->ctx.size() : 0; }
+
+const char* rpca_batch_last_error(const rpca_batch* b) { return b ? b->err.c_str() : g_batch_err; }
+
+void rpca_destroy_batch(rpca_batch* b) {
+  if (!b) return;
+  for (rpca_ctx* c : b->ctx) rpca_destroy(c);
+  for (cudaStream_t s : b->streams)
+    if (s) cudaStreamDestroy(s);
+  delete b;
+}
+
+}  // extern "C"

@@ -117,23 +117,46 @@ extern "C" rpca_status rpca_solve_trials(rpca_ctx* c, double* out, int max_rows,
   return RPCA_OK;
 }
 
-extern "C" rpca_status rpca_solve(rpca_ctx* c, float* U, float* V, rpca_result* res) {
-  if (!c) return RPCA_EINVAL;
-  if (!U || !V) return set_err(c, RPCA_EINVAL, "U and V are required");
-  const auto t0 = std::chrono::steady_clock::now();
-  rpca_result r;
-  memset(&r, 0, sizeof r);
-  rpca_status s = RPCA_OK;
-  const int64_t mk = (int64_t)c->m * c->k, nk = (int64_t)c->n * c->k;
+namespace rpca {
+
+// One solve in progress, resumable: start() runs the initialisation and prepares the
+// iteration, step() waits for the iterations launched last (this context's stream only),
+// evaluates the certificate when due and launches the next batch of iterations, finish()
+// writes the result.  rpca_solve runs them back to back; rpca_solve_batch interleaves the
+// steps of many jobs from one host thread so that their iterations overlap on the GPU.
+struct SolveJob {
+  rpca_ctx* c = nullptr;
+  float* U = nullptr;
+  float* V = nullptr;
+  std::chrono::steady_clock::time_point t0;
+  PhaseTimer* timer = nullptr;
+  int64_t mk = 0, nk = 0, graph_launches0 = 0;
+  SolverState st;
+  int every = 0, last_cert_iter = -1, iter_base = 0, evals_base = 0, cert_evals = 0;
+  bool narrow = false, certified = false, done = false;
+  double narrow_best = INFINITY;
+  rpca_cert cert;
+  ~SolveJob() { delete timer; }
+};
+
+static rpca_status job_start(SolveJob& j, rpca_ctx* c, float* U, float* V) {
+  j.c = c;
+  j.U = U;
+  j.V = V;
+  j.t0 = std::chrono::steady_clock::now();
+  j.mk = (int64_t)c->m * c->k;
+  j.nk = (int64_t)c->n * c->k;
+  memset(&j.cert, 0, sizeof j.cert);
+  rpca_status s;
   // Phase timing: event pairs around each phase on the stream, summed at the end.
-  PhaseTimer timer(c->stream);
-  timer.begin(0);
+  j.timer = new PhaseTimer(c->stream);
+  j.timer->begin(0);
   switch (c->opt.init) {
     case RPCA_INIT_USER:
       break;
     case RPCA_INIT_RANDOM:
-      fill_normal(U, mk, c->opt.seed * 2 + 1, 1e-1f, c->stream);
-      fill_normal(V, nk, c->opt.seed * 2 + 2, 1e-1f, c->stream);
+      fill_normal(U, j.mk, c->opt.seed * 2 + 1, 1e-1f, c->stream);
+      fill_normal(V, j.nk, c->opt.seed * 2 + 2, 1e-1f, c->stream);
       count_launches(c, 2);
       break;
     case RPCA_INIT_SKETCH:
@@ -142,112 +165,175 @@ extern "C" rpca_status rpca_solve(rpca_ctx* c, float* U, float* V, rpca_result* 
     default:
       return set_err(c, RPCA_EUNSUPPORTED, "this initialisation is not built");
   }
-  const int64_t graph_launches0 = c->graph_launches;
-  timer.end();
-  timer.begin(1);
+  j.graph_launches0 = c->graph_launches;
+  j.timer->end();
+  j.timer->begin(1);
   // Precision form: iterate on the narrow copy of X first (its objective differs from the
   // float32 one by the storage rounding), then refine on float32 X.  The certificate is
   // always that of the float32 problem.
-  bool narrow = c->xq_dt != 0;
-  c->solve_plan = narrow ? &c->fg_plan_q : &c->fg_plan;
+  j.narrow = c->xq_dt != 0;
+  c->solve_plan = j.narrow ? &c->fg_plan_q : &c->fg_plan;
   if ((s = solver_prepare(c, U, V)) != RPCA_OK) return s;
-  timer.end();
-  SolverState st;
-  const int every = c->opt.cert_every > 0 ? c->opt.cert_every : 0;
-  bool certified = false;
-  int last_cert_iter = -1;
-  int iter_base = 0, evals_base = 0;  // iterations and trials of the narrow phase
-  double narrow_best = INFINITY;      // best cheap certificate seen in the narrow phase
-  rpca_cert cert;
-  memset(&cert, 0, sizeof cert);
-  int cert_evals = 0;
-  // Leaves the narrow phase: the point so far becomes the start of a float32 solve (fresh
-  // L-BFGS memory; the float32 objective differs from the narrow one).
-  auto refine = [&]() -> rpca_status {
-    cudaMemcpyAsync(U, solver_point(c), sizeof(float) * mk, cudaMemcpyDeviceToDevice, c->stream);
-    cudaMemcpyAsync(V, solver_point(c) + mk, sizeof(float) * nk, cudaMemcpyDeviceToDevice, c->stream);
-    iter_base += st.iter;
-    evals_base += st.evals;
-    narrow = false;
-    c->solve_plan = &c->fg_plan;
-    last_cert_iter = -1;
-    return solver_prepare(c, U, V);
-  };
+  j.timer->end();
+  j.every = c->opt.cert_every > 0 ? c->opt.cert_every : 0;
+  return RPCA_OK;
+}
+
+// Leaves the narrow phase: the point so far becomes the start of a float32 solve (fresh
+// L-BFGS memory; the float32 objective differs from the narrow one).
+static rpca_status job_refine(SolveJob& j) {
+  rpca_ctx* c = j.c;
+  cudaMemcpyAsync(j.U, solver_point(c), sizeof(float) * j.mk, cudaMemcpyDeviceToDevice, c->stream);
+  cudaMemcpyAsync(j.V, solver_point(c) + j.mk, sizeof(float) * j.nk, cudaMemcpyDeviceToDevice, c->stream);
+  j.iter_base += j.st.iter;
+  j.evals_base += j.st.evals;
+  j.narrow = false;
+  c->solve_plan = &c->fg_plan;
+  j.last_cert_iter = -1;
+  j.timer->begin(1);
+  const rpca_status s = solver_prepare(c, j.U, j.V);
+  j.timer->end();
+  return s;
+}
+
+// Advances the job until it has iterations in flight (returns with them launched) or is
+// done (j.done).
+static rpca_status job_step(SolveJob& j) {
+  rpca_ctx* c = j.c;
+  rpca_status s;
   while (true) {
-    if ((s = solver_read_state(c, &st)) != RPCA_OK) return s;
-    if (!st.active || st.iter >= c->opt.max_iter - iter_base) {
-      if (narrow && c->opt.refine_fp32 && st.iter < c->opt.max_iter - iter_base) {
-        timer.begin(1);
-        if ((s = refine()) != RPCA_OK) return s;
-        timer.end();
+    if ((s = solver_read_state(c, &j.st)) != RPCA_OK) return s;
+    const SolverState& st = j.st;
+    if (!st.active || st.iter >= c->opt.max_iter - j.iter_base) {
+      if (j.narrow && c->opt.refine_fp32 && st.iter < c->opt.max_iter - j.iter_base) {
+        if ((s = job_refine(j)) != RPCA_OK) return s;
         continue;
       }
-      break;
+      j.done = true;
+      return RPCA_OK;
     }
-    if (every > 0 && st.iter > 0 && st.iter % every == 0 && st.iter != last_cert_iter) {
-      last_cert_iter = st.iter;
+    if (j.every > 0 && st.iter > 0 && st.iter % j.every == 0 && st.iter != j.last_cert_iter) {
+      j.last_cert_iter = st.iter;
       // Cheap terms first; the spectral term only when they already meet the tolerance.
-      timer.begin(2);
-      if ((s = cert_compute(c, solver_point(c), solver_point(c) + mk, &cert, false)) != RPCA_OK) return s;
-      ++cert_evals;
-      if (cert.cert_rel <= c->opt.cert_tol) {
-        if ((s = cert_compute(c, solver_point(c), solver_point(c) + mk, &cert, true)) != RPCA_OK) return s;
-        if (cert.cert_rel <= c->opt.cert_tol) certified = true;
+      j.timer->begin(2);
+      if ((s = cert_compute(c, solver_point(c), solver_point(c) + j.mk, &j.cert, false)) != RPCA_OK) return s;
+      ++j.cert_evals;
+      if (j.cert.cert_rel <= c->opt.cert_tol) {
+        if ((s = cert_compute(c, solver_point(c), solver_point(c) + j.mk, &j.cert, true)) != RPCA_OK) return s;
+        if (j.cert.cert_rel <= c->opt.cert_tol) j.certified = true;
       }
-      timer.end();
-      if (certified) break;
+      j.timer->end();
+      if (j.certified) {
+        j.done = true;
+        return RPCA_OK;
+      }
       // The narrow phase has done its part once the float32 certificate stops halving
       // between checks: what is left is the storage rounding of X.
-      if (narrow && c->opt.refine_fp32) {
-        const bool plateau = cert.cert_rel > 0.5 * narrow_best;
-        narrow_best = std::min(narrow_best, cert.cert_rel);
+      if (j.narrow && c->opt.refine_fp32) {
+        const bool plateau = j.cert.cert_rel > 0.5 * j.narrow_best;
+        j.narrow_best = std::min(j.narrow_best, j.cert.cert_rel);
         if (plateau) {
-          timer.begin(1);
-          if ((s = refine()) != RPCA_OK) return s;
-          timer.end();
+          if ((s = job_refine(j)) != RPCA_OK) return s;
           continue;
         }
       }
     }
     if (c->opt.timeout_s > 0) {
-      const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-      if (el > c->opt.timeout_s) break;
+      const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - j.t0).count();
+      if (el > c->opt.timeout_s) {
+        j.done = true;
+        return RPCA_OK;
+      }
     }
-    int batch = every > 0 ? every - (st.iter % every) : 25;
-    batch = std::max(1, std::min(batch, c->opt.max_iter - iter_base - st.iter));
-    timer.begin(1);
+    int batch = j.every > 0 ? j.every - (st.iter % j.every) : 25;
+    batch = std::max(1, std::min(batch, c->opt.max_iter - j.iter_base - st.iter));
+    j.timer->begin(1);
     if ((s = solver_iterations(c, batch)) != RPCA_OK) return s;
-    timer.end();
+    j.timer->end();
+    return RPCA_OK;
   }
+}
+
+static rpca_status job_finish(SolveJob& j, rpca_result* res) {
+  rpca_ctx* c = j.c;
+  rpca_status s;
   if ((s = check_dev_err(c)) != RPCA_OK) return s;
-  cudaMemcpyAsync(U, solver_point(c), sizeof(float) * mk, cudaMemcpyDeviceToDevice, c->stream);
-  cudaMemcpyAsync(V, solver_point(c) + mk, sizeof(float) * nk, cudaMemcpyDeviceToDevice, c->stream);
-  if (!certified) {
-    timer.begin(2);
-    if ((s = cert_compute(c, U, V, &cert, true)) != RPCA_OK) return s;
-    timer.end();
+  cudaMemcpyAsync(j.U, solver_point(c), sizeof(float) * j.mk, cudaMemcpyDeviceToDevice, c->stream);
+  cudaMemcpyAsync(j.V, solver_point(c) + j.mk, sizeof(float) * j.nk, cudaMemcpyDeviceToDevice, c->stream);
+  if (!j.certified) {
+    j.timer->begin(2);
+    if ((s = cert_compute(c, j.U, j.V, &j.cert, true)) != RPCA_OK) return s;
+    j.timer->end();
   }
-  ++cert_evals;
+  ++j.cert_evals;
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_err(c, cudaGetLastError(), "rpca_solve");
   // Fused kernel + finalize + line-search step per while-body pass: one per trial, and one
   // (early-exit) pass in every graph launch that ran no trial.
-  const int64_t gl = c->graph_launches - graph_launches0;
-  count_launches(c, 3LL * std::max<int64_t>(gl, (int64_t)(evals_base + st.evals) - 1));
-  timer.collect(&r.ms_init, &r.ms_iter, &r.ms_cert);
-  r.F = narrow ? cert.F : st.f;  // the float32 objective (the narrow phase's st.f is not)
-  r.iters = iter_base + st.iter;
-  r.evals = evals_base + st.evals;
-  r.cert_evals = cert_evals;
-  r.cert = cert;
-  r.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-  r.status = cert.cert_rel <= c->opt.cert_tol ? RPCA_OK : RPCA_ENOTCONV;
+  const int64_t gl = c->graph_launches - j.graph_launches0;
+  count_launches(c, 3LL * std::max<int64_t>(gl, (int64_t)(j.evals_base + j.st.evals) - 1));
+  rpca_result r;
+  memset(&r, 0, sizeof r);
+  j.timer->collect(&r.ms_init, &r.ms_iter, &r.ms_cert);
+  r.F = j.narrow ? j.cert.F : j.st.f;  // the float32 objective (the narrow phase's st.f is not)
+  r.iters = j.iter_base + j.st.iter;
+  r.evals = j.evals_base + j.st.evals;
+  r.cert_evals = j.cert_evals;
+  r.cert = j.cert;
+  r.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - j.t0).count();
+  r.status = j.cert.cert_rel <= c->opt.cert_tol ? RPCA_OK : RPCA_ENOTCONV;
   if (r.F < c->F_best) c->F_best = r.F;
   if (res) *res = r;
   if (r.status != RPCA_OK) {
     char buf[200];
-    snprintf(buf, sizeof buf, "stopped after %d iterations (reason %d) with cert_rel %.3e > %.1e", st.iter, st.stop,
-             cert.cert_rel, c->opt.cert_tol);
+    snprintf(buf, sizeof buf, "stopped after %d iterations (reason %d) with cert_rel %.3e > %.1e", r.iters,
+             j.st.stop, j.cert.cert_rel, c->opt.cert_tol);
     set_err(c, RPCA_ENOTCONV, buf);
   }
   return r.status;
 }
+
+}  // namespace rpca
+
+using namespace rpca;
+
+extern "C" rpca_status rpca_solve(rpca_ctx* c, float* U, float* V, rpca_result* res) {
+  if (!c) return RPCA_EINVAL;
+  if (!U || !V) return set_err(c, RPCA_EINVAL, "U and V are required");
+  SolveJob j;
+  rpca_status s = job_start(j, c, U, V);
+  while (s == RPCA_OK && !j.done) s = job_step(j);
+  if (s != RPCA_OK) return s;
+  return job_finish(j, res);
+}
+
+namespace rpca {
+
+// Many solves from one host thread: every job is started (initialisation, iteration graph),
+// then the jobs are stepped round-robin; a step waits for its own context's stream only, so
+// the other jobs' iterations keep the GPU busy meanwhile.
+rpca_status solve_jobs(rpca_ctx* const* ctx, float* const* U, float* const* V, rpca_result* res, int count,
+                       rpca_status* status) {
+  std::vector<SolveJob> jobs(count);
+  std::vector<bool> live(count, true);
+  for (int i = 0; i < count; ++i) {
+    status[i] = job_start(jobs[i], ctx[i], U[i], V[i]);
+    if (status[i] != RPCA_OK) live[i] = false;
+  }
+  int remaining = 0;
+  for (int i = 0; i < count; ++i) remaining += live[i];
+  while (remaining > 0) {
+    for (int i = 0; i < count; ++i) {
+      if (!live[i]) continue;
+      status[i] = job_step(jobs[i]);
+      if (status[i] != RPCA_OK || jobs[i].done) {
+        live[i] = false;
+        --remaining;
+      }
+    }
+  }
+  for (int i = 0; i < count; ++i)
+    if (status[i] == RPCA_OK) status[i] = job_finish(jobs[i], res ? &res[i] : nullptr);
+  return RPCA_OK;
+}
+
+}  // namespace rpca

@@ -803,6 +803,7 @@ static cudaError_t update_and_direction(int mcap, const SolverArgs& a, int grid,
 void free_solver(rpca_ctx* c) {
   SolverBuffers* b = c->sol;
   if (!b) return;
+  cudaStreamSynchronize(c->stream);  // no graph launch or kernel of this solver still queued
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   if (b->cap) cudaStreamDestroy(b->cap);
@@ -878,16 +879,16 @@ static rpca_status ensure_solver(rpca_ctx* c) {
   b->d = b->gt + N;
   SOL_CUDA(cudaMalloc(&b->S, sizeof(float) * 2 * (mcap + 1) * N));
   b->Y = b->S + (int64_t)(mcap + 1) * N;
-  SOL_CUDA(cudaMemset(b->S, 0, sizeof(float) * 2 * (mcap + 1) * N));
+  SOL_CUDA(cudaMemsetAsync(b->S, 0, sizeof(float) * 2 * (mcap + 1) * N, c->stream));
   SOL_CUDA(cudaMalloc(&b->st, sizeof(SolverState)));
-  SOL_CUDA(cudaMemset(b->st, 0, sizeof(SolverState)));
+  SOL_CUDA(cudaMemsetAsync(b->st, 0, sizeof(SolverState), c->stream));
   SOL_CUDA(cudaMallocHost(&b->host, sizeof(SolverState)));
   const int64_t grid_cap = std::min<int64_t>(2LL * c->nsm, (int64_t)DOTS_GRP * DOTS_MAX_GRP);
   b->grid = (int)std::max<int64_t>(1, std::min<int64_t>(grid_cap, (N + 255) / 256));
   SOL_CUDA(cudaMalloc(&b->blk, sizeof(double) * std::max<size_t>(7 * ((size_t)b->grid + 64) * (mcap + 2),
                                                                   64 * ((size_t)b->grid + DOTS_MAX_GRP))));
   SOL_CUDA(cudaMalloc(&b->counter, sizeof(unsigned int) * (1 + DOTS_MAX_GRP + 3)));
-  SOL_CUDA(cudaMemset(b->counter, 0, sizeof(unsigned int) * (1 + DOTS_MAX_GRP + 3)));
+  SOL_CUDA(cudaMemsetAsync(b->counter, 0, sizeof(unsigned int) * (1 + DOTS_MAX_GRP + 3), c->stream));
   SOL_CUDA(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
   SOL_CUDA(cudaStreamCreateWithFlags(&b->cap2, cudaStreamNonBlocking));
 

@@ -190,3 +190,27 @@ def video_76800x1000(seed: int = 0, **kw) -> Instance:
 def video_110592x2000(seed: int = 0, **kw) -> Instance:
     """384 x 288 frames, 2000 frames, background rank 5, k = 5, 50% Bernoulli mask."""
     return video(h=288, w=384, n=2000, rank=5, k=5, mask_p=0.5, seed=seed, **kw)
+
+
+def batch_c4(count: int = 256, seed: int = 0, m_range=(1024, 20000), n_range=(50, 600),
+             k_range=(2, 16)) -> list:
+    """Independent planted instances of varied shape (the batched workload): m ~ U[1024, 20000],
+    n ~ U[50, 600], k ~ U{2..16}, planted rank max(1, k // 2), outliers Bernoulli(U[0.02, 0.10])
+    with +-U[1, 5], noise 1e-3, fully observed.  lam_S = 1 / sqrt(max(m, n)) and
+    lam_L = 4 lam_S (sqrt(m) + sqrt(n)), as for the video workloads.  Instance i is drawn
+    from its own seed (seed * 100003 + i), so any prefix of the batch is reproducible alone."""
+    g = rng(seed)
+    ms = g.integers(m_range[0], m_range[1] + 1, size=count)
+    ns = g.integers(n_range[0], n_range[1] + 1, size=count)
+    ks = g.integers(k_range[0], k_range[1] + 1, size=count)
+    ps = g.uniform(0.02, 0.10, size=count)
+    out = []
+    for i in range(count):
+        m, n, k = int(ms[i]), int(ns[i]), int(ks[i])
+        lam_S = 1.0 / math.sqrt(max(m, n))
+        inst = planted(m, n, rank=max(1, k // 2), k=k, p_outlier=float(ps[i]), noise=1e-3,
+                       lam_L=4.0 * lam_S * (math.sqrt(m) + math.sqrt(n)), lam_S=lam_S,
+                       seed=seed * 100003 + i)
+        inst.name = f"c4_{i}_{m}x{n}k{k}"
+        out.append(inst)
+    return out

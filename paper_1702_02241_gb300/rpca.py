@@ -28,7 +28,8 @@ class rpca_options(C.Structure):
     _fields_ = [("lbfgs_mem", C.c_int), ("max_iter", C.c_int), ("cert_tol", C.c_double),
                 ("cert_every", C.c_int), ("init", C.c_int), ("seed", C.c_uint64), ("x_dtype", C.c_int),
                 ("refine_fp32", C.c_int), ("timeout_s", C.c_double), ("gtol", C.c_double),
-                ("sketch_oversample", C.c_int), ("sketch_power", C.c_int), ("ls_noise", C.c_double)]
+                ("sketch_oversample", C.c_int), ("sketch_power", C.c_int), ("ls_noise", C.c_double),
+                ("autotune", C.c_int)]
 
 
 class rpca_cert(C.Structure):
@@ -90,6 +91,20 @@ def lib():
     L.rpca_solve_trials.restype = I
     L.rpca_x_storage.argtypes = [P, C.POINTER(C.c_int), C.c_void_p, C.c_int64, C.c_void_p]
     L.rpca_x_storage.restype = I
+    L.rpca_create_batch.argtypes = [C.POINTER(P), I, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_void_p),
+                                    C.POINTER(C.c_int64), C.POINTER(C.c_int), C.POINTER(C.c_double),
+                                    C.POINTER(C.c_double), C.POINTER(rpca_options), P]
+    L.rpca_create_batch.restype = I
+    L.rpca_solve_batch.argtypes = [P, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.POINTER(rpca_result)]
+    L.rpca_solve_batch.restype = I
+    L.rpca_batch_context.argtypes = [P, I]
+    L.rpca_batch_context.restype = P
+    L.rpca_batch_size.argtypes = [P]
+    L.rpca_batch_size.restype = I
+    L.rpca_batch_last_error.argtypes = [P]
+    L.rpca_batch_last_error.restype = C.c_char_p
+    L.rpca_destroy_batch.argtypes = [P]
+    L.rpca_destroy_batch.restype = None
     L.rpca_fg_noalloc.argtypes = [I64, I64, P, I64, I, D, D, P, P, C.POINTER(C.c_double), P, P, P]
     L.rpca_fg_noalloc.restype = I
     L.rpca_version.argtypes = []
@@ -100,7 +115,9 @@ def lib():
 
 EXPORTED = ["rpca_default_options", "rpca_create", "rpca_fg", "rpca_apply", "rpca_init_sketch", "rpca_solve",
             "rpca_certificate", "rpca_destroy", "rpca_last_error", "rpca_version", "rpca_plan_info",
-            "rpca_profile", "rpca_profile_read", "rpca_solve_log", "rpca_solve_trials", "rpca_x_storage", "rpca_fg_noalloc"]
+            "rpca_profile", "rpca_profile_read", "rpca_solve_log", "rpca_solve_trials", "rpca_x_storage", "rpca_fg_noalloc", "rpca_create_batch",
+            "rpca_solve_batch", "rpca_batch_context", "rpca_batch_size", "rpca_batch_last_error",
+            "rpca_destroy_batch"]
 
 
 class RpcaError(RuntimeError):
@@ -233,6 +250,53 @@ def rpca_x_storage(ctx, m, n):
     _check(lib().rpca_x_storage(ctx, C.byref(dt), buf.ctypes.data_as(C.c_void_p), m,
                                 sc.ctypes.data_as(C.c_void_p) if dt.value == RPCA_FP8E4M3 else None), ctx)
     return dt.value, buf.T, (sc if dt.value == RPCA_FP8E4M3 else None)
+
+
+def rpca_create_batch(Xs, lds, ks, lam_Ls, lam_Ss, opt=None, stream=None):
+    """Xs: device tensors (n_i, ld_i) holding column-major m_i x n_i X_i; returns the batch handle."""
+    cnt = len(Xs)
+    ms = (C.c_int64 * cnt)(*[int(m) for m, _ in lds])
+    ns = (C.c_int64 * cnt)(*[int(X.shape[0]) for X in Xs])
+    ldx = (C.c_int64 * cnt)(*[int(ld) for _, ld in lds])
+    ptr = (C.c_void_p * cnt)(*[X.data_ptr() for X in Xs])
+    kk = (C.c_int * cnt)(*[int(k) for k in ks])
+    lL = (C.c_double * cnt)(*[float(v) for v in lam_Ls])
+    lS = (C.c_double * cnt)(*[float(v) for v in lam_Ss])
+    out = C.c_void_p()
+    st = lib().rpca_create_batch(C.byref(out), cnt, ms, ns, ptr, ldx, kk, lL, lS,
+                                 C.byref(opt) if opt is not None else None, stream)
+    if st != RPCA_OK:
+        raise RpcaError(st, lib().rpca_batch_last_error(None).decode())
+    return out
+
+
+def rpca_solve_batch(b, Us, Vs):
+    """Solves the batch; Us, Vs: device (k_i, m_i) / (k_i, n_i) tensors.  Returns (status, results)."""
+    cnt = len(Us)
+    pu = (C.c_void_p * cnt)(*[U.data_ptr() for U in Us])
+    pv = (C.c_void_p * cnt)(*[V.data_ptr() for V in Vs])
+    res = (rpca_result * cnt)()
+    st = lib().rpca_solve_batch(b, pu, pv, res)
+    if st not in (RPCA_OK, RPCA_ENOTCONV):
+        raise RpcaError(st, lib().rpca_batch_last_error(b).decode())
+    return st, list(res)
+
+
+def rpca_batch_context(b, i):
+    """Instance i's context (owned by the batch)."""
+    return lib().rpca_batch_context(b, i)
+
+
+def rpca_batch_size(b):
+    return lib().rpca_batch_size(b)
+
+
+def rpca_batch_last_error(b=None):
+    return lib().rpca_batch_last_error(b).decode()
+
+
+def rpca_destroy_batch(b):
+    lib().rpca_destroy_batch(b)
 
 
 def rpca_destroy(ctx):
