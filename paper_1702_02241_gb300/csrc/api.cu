@@ -2,6 +2,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -348,6 +349,16 @@ static rpca_status make_plan(rpca_ctx* c, FgPlan* P, int K, int B, bool same, in
       if (t < best) best = t;
     }
   }
+  // A context that shares the GPU (grid_cap > 0) keeps the configurations within its CTA
+  // budget, or the smallest grids when none is.
+  if (c->grid_cap > 0 && !cands.empty()) {
+    int gmin = INT_MAX;
+    for (auto& cp : cands) gmin = std::min(gmin, cp.second.nrb * cp.second.ncs);
+    const int cap = std::max(c->grid_cap, gmin);
+    cands.erase(std::remove_if(cands.begin(), cands.end(),
+                               [&](const std::pair<double, FgPlan>& cp) { return cp.second.nrb * cp.second.ncs > cap; }),
+                cands.end());
+  }
   if (cands.empty()) {
     char buf[256];
     snprintf(buf, sizeof buf,
@@ -619,6 +630,18 @@ const char* rpca_last_error(const rpca_ctx* c) { return c ? c->err.c_str() : g_c
 rpca_status rpca_create(rpca_ctx** out, int64_t m, int64_t n, const float* X, int64_t ldx, const uint8_t* mask,
                         int64_t ldmask, int k, double lambda_L, double lambda_S, const rpca_options* opt,
                         void* cuda_stream) {
+  return rpca::create_ctx(out, m, n, X, ldx, mask, ldmask, k, lambda_L, lambda_S, opt, cuda_stream, 0);
+}
+
+}  // extern "C"
+
+namespace rpca {
+
+// rpca_create with a cap on the CTAs of the objective/gradient launch (0: none), for
+// contexts that share the GPU with many others (the batched form).
+rpca_status create_ctx(rpca_ctx** out, int64_t m, int64_t n, const float* X, int64_t ldx, const uint8_t* mask,
+                       int64_t ldmask, int k, double lambda_L, double lambda_S, const rpca_options* opt,
+                       void* cuda_stream, int grid_cap) {
   if (!out) return set_err(nullptr, RPCA_EINVAL, "out is NULL");
   *out = nullptr;
   // m and n up to 2^27: every (row or column) x (block of <= 16 columns) index fits 31 bits.
@@ -656,6 +679,7 @@ rpca_status rpca_create(rpca_ctx** out, int64_t m, int64_t n, const float* X, in
   c->lam_S = lambda_S;
   c->opt = o;
   c->stream = static_cast<cudaStream_t>(cuda_stream);
+  c->grid_cap = std::max(0, grid_cap);
   c->mpad = (int)((m + 3) / 4 * 4);
   auto fail = [&](rpca_status s) {
     snprintf(g_create_err, sizeof g_create_err, "%s", c->err.c_str());
@@ -719,6 +743,10 @@ rpca_status rpca_create(rpca_ctx** out, int64_t m, int64_t n, const float* X, in
   *out = c;
   return RPCA_OK;
 }
+
+}  // namespace rpca
+
+extern "C" {
 
 rpca_status rpca_x_storage(rpca_ctx* c, int* dtype, void* host_out, int64_t ld_out, float* scales_out) {
   if (!c || !dtype) return RPCA_EINVAL;

@@ -1,19 +1,22 @@
 // Batched form: many independent problems (the C4 workload of varied m, n, k) solved
 // concurrently.  Each instance is a full context with its own CUDA stream, planned by the
 // time model alone (no per-shape timing: hundreds of shapes), and its own graph-captured
-// L-BFGS iteration.  One host thread starts every solve and then steps them round-robin;
-// each step waits for its own stream only, so the instances' iterations overlap on the GPU
-// (a small instance fills a few SMs only) without any two host threads in the CUDA API.
+// L-BFGS iteration.  A few host threads (RPCA_BATCH_THREADS, default the hardware threads up
+// to 16) share the instances; each starts its solves and steps them round-robin, and a step
+// waits for its own stream only, so the instances' iterations overlap on the GPU (a small
+// instance fills a few SMs only).
 #include <algorithm>
 #include <cstring>
+#include <cstdlib>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "ctx.h"
 
 namespace rpca {
 rpca_status solve_jobs(rpca_ctx* const* ctx, float* const* U, float* const* V, rpca_result* res, int count,
-                       rpca_status* status);  // solve.cu
+                       rpca_status* status, int threads);  // solve.cu
 }
 
 struct rpca_batch {
@@ -54,10 +57,12 @@ rpca_status rpca_create_batch(rpca_batch** out, int count, const int64_t* m, con
       return RPCA_ECUDA;
     }
   }
+  int grid_cap = 0;
+  if (const char* e = getenv("RPCA_BATCH_GRID")) grid_cap = std::max(0, atoi(e));
   for (int i = 0; i < count; ++i) {
     const int64_t ld = ldx ? ldx[i] : m[i];
-    const rpca_status r = rpca_create(&b->ctx[i], m[i], n[i], X[i], ld, nullptr, 0, k[i], lambda_L[i], lambda_S[i],
-                                      &o, b->streams[i]);
+    const rpca_status r = rpca::create_ctx(&b->ctx[i], m[i], n[i], X[i], ld, nullptr, 0, k[i], lambda_L[i],
+                                           lambda_S[i], &o, b->streams[i], grid_cap);
     if (r != RPCA_OK) {
       snprintf(g_batch_err, sizeof g_batch_err, "instance %d: %s", i, rpca_last_error(nullptr));
       rpca_destroy_batch(b);
@@ -79,7 +84,9 @@ rpca_status rpca_solve_batch(rpca_batch* b, float* const* U, float* const* V, rp
   cudaEventDestroy(ready);
   std::vector<rpca_result> local(count);
   std::vector<rpca_status> st(count, RPCA_OK);
-  rpca::solve_jobs(b->ctx.data(), U, V, local.data(), count, st.data());
+  int threads = (int)std::min(16u, std::max(1u, std::thread::hardware_concurrency()));
+  if (const char* e = getenv("RPCA_BATCH_THREADS")) threads = std::max(1, atoi(e));
+  rpca::solve_jobs(b->ctx.data(), U, V, local.data(), count, st.data(), threads);
   int notconv = 0;
   rpca_status s = RPCA_OK;
   for (int i = 0; i < count; ++i) {

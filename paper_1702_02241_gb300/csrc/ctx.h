@@ -59,6 +59,7 @@ struct rpca_ctx {
   double lam_L = 0, lam_S = 0;
   rpca_options opt;
   cudaStream_t stream = nullptr;
+  int grid_cap = 0;  // CTA budget of the objective/gradient launch (0: the whole GPU)
   int device = 0, nsm = 0;
   size_t max_smem = 0;
   int mpad = 0;
@@ -126,6 +127,9 @@ struct FgLaunch {
 rpca_status launch_fg(rpca_ctx* c, const FgPlan& P, const FgLaunch& L, cudaStream_t stream);
 const FgPlan* apply_plan(rpca_ctx* c, int K, int side);  // forming rank >= K (0, 8 or 16), side
 rpca_status make_xq(rpca_ctx* c, int xt);                // narrow copy of X (xq.cu)
+rpca_status create_ctx(rpca_ctx** out, int64_t m, int64_t n, const float* X, int64_t ldx, const uint8_t* mask,
+                       int64_t ldmask, int k, double lambda_L, double lambda_S, const rpca_options* opt,
+                       void* cuda_stream, int grid_cap);  // api.cu
 // The objective/gradient plan rpca_fg uses: the narrow copy's when there is one.
 inline const FgPlan& eval_plan(const rpca_ctx* c) { return c->xq_dt ? c->fg_plan_q : c->fg_plan; }
 inline void count_launches(rpca_ctx* c, int64_t n) { c->launches += n; }

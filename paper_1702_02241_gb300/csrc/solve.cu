@@ -4,6 +4,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <thread>
 #include <utility>
 #include <vector>
 
@@ -308,31 +309,62 @@ extern "C" rpca_status rpca_solve(rpca_ctx* c, float* U, float* V, rpca_result* 
 
 namespace rpca {
 
-// Many solves from one host thread: every job is started (initialisation, iteration graph),
-// then the jobs are stepped round-robin; a step waits for its own context's stream only, so
-// the other jobs' iterations keep the GPU busy meanwhile.
+// Many solves: the jobs are split over up to `threads` host threads (largest instances first,
+// each to the least loaded thread); a thread starts its jobs (initialisation, iteration graph)
+// and then steps them round-robin.  A step waits for its own context's stream only, so the
+// other jobs' iterations keep the GPU busy meanwhile, and a thread blocked in one job's
+// certificate holds up only the jobs of its own share.
 rpca_status solve_jobs(rpca_ctx* const* ctx, float* const* U, float* const* V, rpca_result* res, int count,
-                       rpca_status* status) {
+                       rpca_status* status, int threads) {
   std::vector<SolveJob> jobs(count);
-  std::vector<bool> live(count, true);
-  for (int i = 0; i < count; ++i) {
-    status[i] = job_start(jobs[i], ctx[i], U[i], V[i]);
-    if (status[i] != RPCA_OK) live[i] = false;
-  }
-  int remaining = 0;
-  for (int i = 0; i < count; ++i) remaining += live[i];
-  while (remaining > 0) {
-    for (int i = 0; i < count; ++i) {
-      if (!live[i]) continue;
-      status[i] = job_step(jobs[i]);
-      if (status[i] != RPCA_OK || jobs[i].done) {
-        live[i] = false;
-        --remaining;
-      }
+  threads = std::max(1, std::min(threads, count));
+  std::vector<std::vector<int>> share(threads);
+  {
+    std::vector<int> order(count);
+    for (int i = 0; i < count; ++i) order[i] = i;
+    auto work = [&](int i) { return (double)ctx[i]->m * (double)ctx[i]->n * (double)ctx[i]->k; };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work(a) > work(b); });
+    std::vector<double> load(threads, 0.0);
+    for (int i : order) {
+      const int t = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+      share[t].push_back(i);
+      load[t] += work(i);
     }
   }
-  for (int i = 0; i < count; ++i)
-    if (status[i] == RPCA_OK) status[i] = job_finish(jobs[i], res ? &res[i] : nullptr);
+  auto run = [&](int t) {
+    const std::vector<int>& mine = share[t];
+    if (mine.empty()) return;
+    cudaSetDevice(ctx[mine[0]]->device);
+    std::vector<bool> live(mine.size(), true);
+    int remaining = 0;
+    for (size_t q = 0; q < mine.size(); ++q) {
+      const int i = mine[q];
+      status[i] = job_start(jobs[i], ctx[i], U[i], V[i]);
+      live[q] = status[i] == RPCA_OK;
+      remaining += live[q];
+    }
+    while (remaining > 0) {
+      for (size_t q = 0; q < mine.size(); ++q) {
+        if (!live[q]) continue;
+        const int i = mine[q];
+        status[i] = job_step(jobs[i]);
+        if (status[i] != RPCA_OK || jobs[i].done) {
+          live[q] = false;
+          --remaining;
+        }
+      }
+    }
+    for (int i : mine)
+      if (status[i] == RPCA_OK) status[i] = job_finish(jobs[i], res ? &res[i] : nullptr);
+  };
+  if (threads == 1) {
+    run(0);
+  } else {
+    std::vector<std::thread> pool;
+    pool.reserve(threads);
+    for (int t = 0; t < threads; ++t) pool.emplace_back(run, t);
+    for (auto& th : pool) th.join();
+  }
   return RPCA_OK;
 }
 
