@@ -197,8 +197,11 @@ def batch_c4(count: int = 256, seed: int = 0, m_range=(1024, 20000), n_range=(50
     """Independent planted instances of varied shape (the batched workload): m ~ U[1024, 20000],
     n ~ U[50, 600], k ~ U{2..16}, planted rank max(1, k // 2), outliers Bernoulli(U[0.02, 0.10])
     with +-U[1, 5], noise 1e-3, fully observed.  lam_S = 1 / sqrt(max(m, n)) and
-    lam_L = 4 lam_S (sqrt(m) + sqrt(n)), as for the video workloads.  Instance i is drawn
-    from its own seed (seed * 100003 + i), so any prefix of the batch is reproducible alone."""
+    lam_L = lam_S (sqrt(m) + sqrt(n)): the first value of the rule "lam_S (sqrt(m) + sqrt(n)),
+    doubled until the solution has the planted rank", which these unit-variance planted
+    instances already meet (a larger lam_L shrinks L far below the planted part).  Instance i
+    is drawn from its own seed (seed * 100003 + i), so any prefix of the batch is reproducible
+    alone."""
     g = rng(seed)
     ms = g.integers(m_range[0], m_range[1] + 1, size=count)
     ns = g.integers(n_range[0], n_range[1] + 1, size=count)
@@ -209,7 +212,7 @@ def batch_c4(count: int = 256, seed: int = 0, m_range=(1024, 20000), n_range=(50
         m, n, k = int(ms[i]), int(ns[i]), int(ks[i])
         lam_S = 1.0 / math.sqrt(max(m, n))
         inst = planted(m, n, rank=max(1, k // 2), k=k, p_outlier=float(ps[i]), noise=1e-3,
-                       lam_L=4.0 * lam_S * (math.sqrt(m) + math.sqrt(n)), lam_S=lam_S,
+                       lam_L=lam_S * (math.sqrt(m) + math.sqrt(n)), lam_S=lam_S,
                        seed=seed * 100003 + i)
         inst.name = f"c4_{i}_{m}x{n}k{k}"
         out.append(inst)
