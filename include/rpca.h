@@ -40,6 +40,7 @@ extern "C" {
 #endif
 
 typedef struct rpca_ctx rpca_ctx; /* opaque, owned by the library */
+typedef struct rpca_ws rpca_ws;   /* learned warm-start model, opaque (see the end of this file) */
 
 typedef enum {
   RPCA_OK = 0,
@@ -56,7 +57,8 @@ typedef enum { RPCA_F32 = 0, RPCA_BF16 = 1, RPCA_FP8E4M3 = 2 } rpca_dtype;
 typedef enum {
   RPCA_INIT_SKETCH = 0, /* randomized SVD of A*(X): U0 = U_k S^1/2, V0 = V_k S^1/2 (Sec. 4.2) */
   RPCA_INIT_RANDOM = 1, /* iid N(0, 1e-2) factors from the seeded device generator */
-  RPCA_INIT_LEARNED = 2,
+  RPCA_INIT_LEARNED = 2, /* the sketch start with each component scaled by a trained network's
+                            share w_j (rpca_set_warm_start); kept only when F is lower there */
   RPCA_INIT_USER = 3    /* start from the U, V passed to rpca_solve */
 } rpca_init_kind;
 
@@ -105,6 +107,8 @@ typedef struct {
   double ms_init;  /* device time of the initialisation (sketch or random), CUDA events */
   double ms_iter;  /* device time of the L-BFGS iterations (graph launches) */
   double ms_cert;  /* device time of the certificate evaluations */
+  int init_used;   /* rpca_init_kind of the start actually used (RPCA_INIT_LEARNED falls back
+                      to RPCA_INIT_SKETCH when the learned start's objective is not lower) */
 } rpca_result;
 
 /* Fills *opt with the defaults named in the comments above. */
@@ -289,6 +293,72 @@ RPCA_API rpca_status rpca_fg_noalloc(int64_t m, int64_t n, const float *X, int64
 
 /* Library version string. */
 RPCA_API const char *rpca_version(void);
+
+/* ---- Learned warm start ---------------------------------------------------------------
+ * An extension of this library (the paper compares SVD, randomized-SVD and random starts,
+ * Sec. 4.2, and finds that the start matters).  A three-layer network (40 inputs, two hidden
+ * layers of 256 with ReLU, 16 sigmoid outputs; weight matrices used in bfloat16, float32
+ * arithmetic) maps features of the randomized sketch's spectrum to the share w_j in [0, 1]
+ * of each sketch component that the solution keeps; the learned start is the sketch start
+ * with column j of U0 and V0 scaled by sqrt(w_j).
+ *
+ * Features x (40 floats) of a context whose last initialisation ran the sketch, with
+ * s_1 >= ... >= s_l its singular values of A*(X) (l = k + sketch_oversample, <= 32):
+ *   x_j = log(s_j / s_l) (j < l; 0 for l <= j < 32), x_32 = log(lam_L / s_l),
+ *   x_33 = log(lam_S sqrt(m n) / s_l) (0 when lam_S is infinite), x_34 = k / 16,
+ *   x_35 = l / 32, x_36 = log(m / n) / 4, x_37 = log(m n) / 20, x_38 = x_39 = 0.
+ * Target of component j: w*_j = clip(u_j^T L* v_j / s_j, 0, 1), u_j and v_j the sketch's unit
+ * singular vectors, L* = U V^T a solution.  Loss (1 / B) sum_b sum_{j < k_b} (w_j - w*_j)^2,
+ * Adam (beta1 0.9, beta2 0.999, eps 1e-8) on float32 master parameters, the gradient taken
+ * at the bfloat16-rounded weights.
+ *
+ * Parameters (rpca_ws_nparam() floats, packed): W1 (256 x 40, row-major) | b1 (256) |
+ * W2T (256 x 256, W2T[i][u] = W2[u][i]) | b2 (256) | W3 (16 x 256, row-major) | b3 (16).
+ * Errors of the model calls: rpca_ws_last_error(model) (NULL before a model exists).
+ */
+RPCA_API int rpca_ws_nparam(void);
+/* A model with parameters theta (host, rpca_ws_nparam() floats); calls run on cuda_stream. */
+RPCA_API rpca_status rpca_ws_create(rpca_ws **out, const float *theta, void *cuda_stream);
+/* Replaces the parameters (host) and resets the optimiser state.  Synchronous. */
+RPCA_API rpca_status rpca_ws_set_params(rpca_ws *w, const float *theta);
+/* Copies the parameters and (grad may be NULL) the last training step's gradient to host. */
+RPCA_API rpca_status rpca_ws_get_params(rpca_ws *w, float *theta, float *grad);
+/* W (device, B x 16) = the network's outputs for the features X (device, B x 40, row-major). */
+RPCA_API rpca_status rpca_ws_predict(rpca_ws *w, const float *X, int B, float *W);
+/* One Adam step on the batch (device X: B x 40, T: B x 16 targets, K: B factor ranks; outputs
+ * j >= K[b] are ignored) with step size lr; *loss (host, may be NULL; synchronises) = the
+ * batch loss at the parameters before the step. */
+RPCA_API rpca_status rpca_ws_train_step(rpca_ws *w, const float *X, const float *T, const int *K, int B, float lr,
+                                        float *loss);
+RPCA_API const char *rpca_ws_last_error(const rpca_ws *w);
+RPCA_API void rpca_ws_destroy(rpca_ws *w);
+/* The model opt.init == RPCA_INIT_LEARNED uses on this context (not owned; NULL clears). */
+RPCA_API rpca_status rpca_set_warm_start(rpca_ctx *c, const rpca_ws *w);
+/* The l singular values (host, <= 32 floats) of the context's last sketch; *l = 0 if none. */
+RPCA_API rpca_status rpca_sketch_spectrum(rpca_ctx *c, float *s, int *l);
+/* A training sample: x (device, 40) = the features of the context's last sketch; if wstar
+ * (device, 16) is not NULL, the targets of the sketch start (Us, Vs: device m x k and n x k,
+ * as rpca_init_sketch wrote them) against the solution (U, V); entries j >= k are 0. */
+RPCA_API rpca_status rpca_ws_sample(rpca_ctx *c, const float *Us, const float *Vs, const float *U, const float *V,
+                                    float *x, float *wstar);
+
+/* ---- Counter-based generator of planted instances (training data) ------------------------
+ * Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC 2011), key = seed (low word first).
+ * rpca_gen_planted writes X (device, m x n column-major, ld ldx >= m) = A B^T + S + N and,
+ * if L0 is not NULL (device, m x n, ld m), A B^T:
+ *   A[i][c]: counter (i, c, 0, instance); B[j][c]: (j, c, 1, instance); entry (i, j): (i, j, 2,
+ *   instance).  uniform24(w) = (w >> 8) 2^-24; normal(wa, wb) = sqrt(-2 ln(((wa >> 8) + 1) 2^-24))
+ *   cos(2 pi uniform24(wb)).  A, B = rank^(-1/4) normal(w0, w1) (L entries of unit variance);
+ *   outlier where uniform24(w0) < p_outlier, value +-(1 + 4 (w1 & 0xffffff) 2^-24), negative
+ *   when the top bit of w1 is set; N = noise_std normal(w2, w3).  m, n < 2^32, rank <= 64.
+ * rpca_philox4x32_10 writes count x 4 words (device out) for the counters (ctr[0] + t, ctr[1],
+ * ctr[2], ctr[3]) (host ctr), t < count.  Both are asynchronous on cuda_stream; errors:
+ * rpca_last_error(NULL).
+ */
+RPCA_API rpca_status rpca_gen_planted(int64_t m, int64_t n, int rank, double p_outlier, double noise_std, uint64_t seed,
+                                      uint32_t instance, float *X, int64_t ldx, float *L0, void *cuda_stream);
+RPCA_API rpca_status rpca_philox4x32_10(uint32_t *out, int64_t count, const uint32_t *ctr, uint64_t key,
+                                        void *cuda_stream);
 
 #ifdef __cplusplus
 }

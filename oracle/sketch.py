@@ -24,8 +24,9 @@ def sampled(X, mask):
     return np.where(M, X, 0.0) / max(p, 1e-300)
 
 
-def rsvd_init(X, mask, k, Omega, q=2):
-    """Return (U0, V0) float64 from the randomized SVD of A*(X) with test matrix Omega."""
+def rsvd_parts(X, mask, Omega, q=2):
+    """Q U_B, the singular values s (descending, one per column of Omega) and V_B of the
+    randomized SVD of A*(X) with test matrix Omega."""
     Xs = sampled(X, mask)
     Om = np.asarray(Omega, np.float64)
     Q, _ = np.linalg.qr(Xs @ Om)
@@ -34,5 +35,11 @@ def rsvd_init(X, mask, k, Omega, q=2):
         Q, _ = np.linalg.qr(Xs @ Z)
     B = Q.T @ Xs
     Ub, s, Vbt = np.linalg.svd(B, full_matrices=False)
+    return Q @ Ub, s, Vbt.T
+
+
+def rsvd_init(X, mask, k, Omega, q=2):
+    """Return (U0, V0) float64 from the randomized SVD of A*(X) with test matrix Omega."""
+    Uq, s, Vq = rsvd_parts(X, mask, Omega, q)
     sq = np.sqrt(s[:k])
-    return (Q @ Ub[:, :k]) * sq, Vbt[:k].T * sq
+    return Uq[:, :k] * sq, Vq[:, :k] * sq

@@ -39,11 +39,7 @@ rpca_status cuda_err(rpca_ctx* c, cudaError_t e, const char* what) {
   return set_err(c, e == cudaErrorMemoryAllocation ? RPCA_ENOMEM : RPCA_ECUDA, msg);
 }
 
-#define RPCA_CUDA(c, call)                              \
-  do {                                                  \
-    cudaError_t e_ = (call);                            \
-    if (e_ != cudaSuccess) return cuda_err((c), e_, #call); \
-  } while (0)
+
 
 // Reads (and clears) the device status word; call after a synchronise.
 rpca_status check_dev_err(rpca_ctx* c) {
@@ -833,6 +829,7 @@ void rpca_destroy(rpca_ctx* c) {
   cudaFree(c->bits);
   cudaFree(c->Xq);
   cudaFree(c->xscale);
+  cudaFree(c->sk_sigma);
   cudaFree(c->ws.PU);
   cudaFree(c->ws.PV);
   cudaFree(c->ws.Ppsi);

@@ -81,6 +81,10 @@ struct rpca_ctx {
   rpca::Workspace ws_ap;       // partial sums of the apply plans
   rpca::SolverBuffers* sol = nullptr;
   rpca::CertBuffers* cert = nullptr;
+  // Learned warm start: the model (not owned) and the last sketch's singular values.
+  const rpca_ws* ws_model = nullptr;
+  float* sk_sigma = nullptr;  // 32 floats on the device, owned
+  int sk_l = 0;
   std::string err;
   // Instrumentation (rpca_profile).
   bool prof = false;
@@ -101,6 +105,13 @@ rpca_status make_tmap(rpca_ctx* c, CUtensorMap* map, CUtensorMapDataType dt, con
                       int64_t d1, int64_t stride_bytes, int b0, int b1);
 rpca_status cuda_err(rpca_ctx* c, cudaError_t e, const char* what);
 rpca_status check_dev_err(rpca_ctx* c);
+
+// Returns from the calling function with RPCA_ECUDA (and the context's error text) on failure.
+#define RPCA_CUDA(c, call)                              \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return cuda_err((c), e_, #call); \
+  } while (0)
 
 // Launches fused kernel + finalize for plan P.  fin_mode FIN_FG: (GU, GV) <- gradient at
 // the trial point, out[0..3] <- f, g.d, ||g||^2, ||x||^2.  FIN_APPLY: GU <- D Bv, GV <- D^T Bu.
@@ -127,6 +138,7 @@ struct FgLaunch {
 rpca_status launch_fg(rpca_ctx* c, const FgPlan& P, const FgLaunch& L, cudaStream_t stream);
 const FgPlan* apply_plan(rpca_ctx* c, int K, int side);  // forming rank >= K (0, 8 or 16), side
 rpca_status make_xq(rpca_ctx* c, int xt);                // narrow copy of X (xq.cu)
+rpca_status ws_learned_init(rpca_ctx* c, float* U, float* V, int* used);  // ws.cu
 rpca_status create_ctx(rpca_ctx** out, int64_t m, int64_t n, const float* X, int64_t ldx, const uint8_t* mask,
                        int64_t ldmask, int k, double lambda_L, double lambda_S, const rpca_options* opt,
                        void* cuda_stream, int grid_cap);  // api.cu

@@ -57,7 +57,8 @@ __global__ void sk_zero_cols_kernel(float* Y, int64_t rows, int l, const SketchS
 
 // Eigen-decomposition of the l x l Gram of B^T (one CTA); C1 = U_B[:, :k] Sigma^{1/2} and
 // C2 = U_B[:, :k] Sigma^{-1/2} (scaled by `scale`), both l x k (ld l).
-__global__ void __launch_bounds__(256) sk_small_svd_kernel(SketchState* st, int l, int k) {
+__global__ void __launch_bounds__(256) sk_small_svd_kernel(SketchState* st, int l, int k, float* sig_out,
+                                                            float inv_p) {
   __shared__ double A[SK_LMAX * SK_LMAX], W[SK_LMAX * SK_LMAX], ev[SK_LMAX];
   __shared__ int ord[SK_LMAX];
   __shared__ int flag;
@@ -72,6 +73,11 @@ __global__ void __launch_bounds__(256) sk_small_svd_kernel(SketchState* st, int 
     const double u = W[a + ord[c] * l];
     st->C1[a + c * l] = u * sqrt(sg);
     st->C2[a + c * l] = sg > 0.0 ? u / sqrt(sg) : 0.0;
+  }
+  // The sketch's singular values of A*(X), descending (the Gram's eigenvalues carry p_hat^2).
+  for (int c = threadIdx.x; c < l; c += blockDim.x) {
+    const double lam = ev[ord[c]];
+    sig_out[c] = (float)((lam > 0.0 ? sqrt(lam) : 0.0) * inv_p);
   }
 }
 
@@ -195,9 +201,12 @@ rpca_status sketch_init(rpca_ctx* c, const float* Omega, float* U, float* V) {
   if ((s = sk_apply(c, b, l, nullptr, b.Y, nullptr, b.Z)) != RPCA_OK) return done(s);
   if (ts_gram_c(c, b.Z, n, l, b.Z, n, l, n, b.st->G, b.ts, c->stream) != cudaSuccess)
     return done(set_err(c, RPCA_ECUDA, "ts_gram"));
-  sk_small_svd_kernel<<<1, 256, 0, c->stream>>>(b.st, l, k);
-  count_launches(c, 1);
+  if (!c->sk_sigma && cudaMalloc(&c->sk_sigma, sizeof(float) * SK_LMAX) != cudaSuccess)
+    return done(set_err(c, RPCA_ENOMEM, "cudaMalloc"));
   const float inv_p = (float)(1.0 / std::max(c->p_hat, 1e-30));
+  sk_small_svd_kernel<<<1, 256, 0, c->stream>>>(b.st, l, k, c->sk_sigma, inv_p);
+  count_launches(c, 1);
+  c->sk_l = l;
   // The Gram was formed from D^T Q = -p_hat B^T: its eigenvalues are p_hat^2 sigma^2, so
   // sqrt(sigma) picks up sqrt(p_hat) -- rescale both factors accordingly.
   const float su = std::sqrt(inv_p);

@@ -134,6 +134,7 @@ struct SolveJob {
   int64_t mk = 0, nk = 0, graph_launches0 = 0;
   SolverState st;
   int every = 0, last_cert_iter = -1, iter_base = 0, evals_base = 0, cert_evals = 0;
+  int init_used = 0;
   bool narrow = false, certified = false, done = false;
   double narrow_best = INFINITY;
   rpca_cert cert;
@@ -148,6 +149,7 @@ static rpca_status job_start(SolveJob& j, rpca_ctx* c, float* U, float* V) {
   j.mk = (int64_t)c->m * c->k;
   j.nk = (int64_t)c->n * c->k;
   memset(&j.cert, 0, sizeof j.cert);
+  j.init_used = c->opt.init;
   rpca_status s;
   // Phase timing: event pairs around each phase on the stream, summed at the end.
   j.timer = new PhaseTimer(c->stream);
@@ -163,6 +165,13 @@ static rpca_status job_start(SolveJob& j, rpca_ctx* c, float* U, float* V) {
     case RPCA_INIT_SKETCH:
       if ((s = sketch_init(c, nullptr, U, V)) != RPCA_OK) return s;
       break;
+    case RPCA_INIT_LEARNED: {
+      if ((s = sketch_init(c, nullptr, U, V)) != RPCA_OK) return s;
+      int used = 0;
+      if ((s = ws_learned_init(c, U, V, &used)) != RPCA_OK) return s;
+      j.init_used = used ? RPCA_INIT_LEARNED : RPCA_INIT_SKETCH;
+      break;
+    }
     default:
       return set_err(c, RPCA_EUNSUPPORTED, "this initialisation is not built");
   }
@@ -280,6 +289,7 @@ static rpca_status job_finish(SolveJob& j, rpca_result* res) {
   r.evals = j.evals_base + j.st.evals;
   r.cert_evals = j.cert_evals;
   r.cert = j.cert;
+  r.init_used = j.init_used;
   r.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - j.t0).count();
   r.status = j.cert.cert_rel <= c->opt.cert_tol ? RPCA_OK : RPCA_ENOTCONV;
   if (r.F < c->F_best) c->F_best = r.F;

@@ -217,3 +217,60 @@ def batch_c4(count: int = 256, seed: int = 0, m_range=(1024, 20000), n_range=(50
         inst.name = f"c4_{i}_{m}x{n}k{k}"
         out.append(inst)
     return out
+
+
+# ---- Counter-based generator (Philox4x32-10, Salmon et al., SC 2011) -------------------------
+# The same stream the library's device generator draws (rpca_gen_planted); used by tests to
+# check that generator and by anything that needs an instance's values on the host.
+
+_PH_M0, _PH_M1, _PH_W0, _PH_W1 = 0xD2511F53, 0xCD9E8D57, 0x9E3779B9, 0xBB67AE85
+
+
+def philox4x32_10(ctr, key):
+    """Philox4x32 with 10 rounds.  ctr: (..., 4) uint32 counters; key: (k0, k1).  Returns the
+    (..., 4) uint32 output words.  Rounds: (x, y, z, w) -> (hi(M1 z) ^ y ^ k0, lo(M1 z),
+    hi(M0 x) ^ w ^ k1, lo(M0 x)), the key advanced by (W0, W1) before each round but the first."""
+    c = np.array(ctr, dtype=np.uint64) & 0xFFFFFFFF
+    x, y, z, w = c[..., 0], c[..., 1], c[..., 2], c[..., 3]
+    k0, k1 = np.uint64(key[0] & 0xFFFFFFFF), np.uint64(key[1] & 0xFFFFFFFF)
+    mask = np.uint64(0xFFFFFFFF)
+    for r in range(10):
+        if r > 0:
+            k0 = (k0 + np.uint64(_PH_W0)) & mask
+            k1 = (k1 + np.uint64(_PH_W1)) & mask
+        p0 = np.uint64(_PH_M0) * x
+        p1 = np.uint64(_PH_M1) * z
+        x, y, z, w = ((p1 >> np.uint64(32)) ^ y ^ k0, p1 & mask, (p0 >> np.uint64(32)) ^ w ^ k1, p0 & mask)
+    return np.stack([x, y, z, w], axis=-1).astype(np.uint32)
+
+
+def _uniform24(wd):
+    return (wd >> np.uint32(8)).astype(np.float64) * 2.0 ** -24
+
+
+def _normal(wa, wb):
+    u1 = ((wa >> np.uint32(8)).astype(np.float64) + 1.0) * 2.0 ** -24
+    return np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * math.pi * _uniform24(wb))
+
+
+def planted_philox(m, n, rank, p_outlier, noise, seed, instance):
+    """The planted instance rpca_gen_planted writes (float64 values of the same draws): returns
+    X, L0, the outlier mask.  Counter layout and transforms as documented in include/rpca.h."""
+    k = (seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF)
+    sc = rank ** -0.25
+    def factor(rows, which):
+        r, c = np.meshgrid(np.arange(rows), np.arange(rank), indexing="ij")
+        ctr = np.stack([r, c, np.full_like(r, which), np.full_like(r, instance)], axis=-1)
+        wd = philox4x32_10(ctr, k)
+        return sc * _normal(wd[..., 0], wd[..., 1])
+    A = factor(m, 0)
+    B = factor(n, 1)
+    L0 = A @ B.T
+    ii, jj = np.meshgrid(np.arange(m), np.arange(n), indexing="ij")
+    ctr = np.stack([ii, jj, np.full_like(ii, 2), np.full_like(ii, instance)], axis=-1)
+    wd = philox4x32_10(ctr, k)
+    out = _uniform24(wd[..., 0]) < p_outlier
+    mag = 1.0 + 4.0 * (wd[..., 1] & np.uint32(0xFFFFFF)).astype(np.float64) * 2.0 ** -24
+    S = np.where(out, np.where(wd[..., 1] >> np.uint32(31), -mag, mag), 0.0)
+    N = noise * _normal(wd[..., 2], wd[..., 3])
+    return L0 + S + N, L0, out

@@ -45,7 +45,7 @@ class rpca_cert(C.Structure):
 class rpca_result(C.Structure):
     _fields_ = [("F", C.c_double), ("iters", C.c_int), ("evals", C.c_int), ("cert_evals", C.c_int),
                 ("seconds", C.c_double), ("cert", rpca_cert), ("status", C.c_int), ("ms_init", C.c_double),
-                ("ms_iter", C.c_double), ("ms_cert", C.c_double)]
+                ("ms_iter", C.c_double), ("ms_cert", C.c_double), ("init_used", C.c_int)]
 
 
 _lib = None
@@ -109,6 +109,33 @@ def lib():
     L.rpca_fg_noalloc.restype = I
     L.rpca_version.argtypes = []
     L.rpca_version.restype = C.c_char_p
+    FP = C.POINTER(C.c_float)
+    L.rpca_ws_nparam.argtypes = []
+    L.rpca_ws_nparam.restype = I
+    L.rpca_ws_create.argtypes = [C.POINTER(P), FP, P]
+    L.rpca_ws_create.restype = I
+    L.rpca_ws_set_params.argtypes = [P, FP]
+    L.rpca_ws_set_params.restype = I
+    L.rpca_ws_get_params.argtypes = [P, FP, FP]
+    L.rpca_ws_get_params.restype = I
+    L.rpca_ws_predict.argtypes = [P, P, I, P]
+    L.rpca_ws_predict.restype = I
+    L.rpca_ws_train_step.argtypes = [P, P, P, P, I, C.c_float, FP]
+    L.rpca_ws_train_step.restype = I
+    L.rpca_ws_last_error.argtypes = [P]
+    L.rpca_ws_last_error.restype = C.c_char_p
+    L.rpca_ws_destroy.argtypes = [P]
+    L.rpca_ws_destroy.restype = None
+    L.rpca_set_warm_start.argtypes = [P, P]
+    L.rpca_set_warm_start.restype = I
+    L.rpca_sketch_spectrum.argtypes = [P, FP, C.POINTER(C.c_int)]
+    L.rpca_sketch_spectrum.restype = I
+    L.rpca_ws_sample.argtypes = [P, P, P, P, P, P, P]
+    L.rpca_ws_sample.restype = I
+    L.rpca_gen_planted.argtypes = [I64, I64, I, D, D, C.c_uint64, C.c_uint32, P, I64, P, P]
+    L.rpca_gen_planted.restype = I
+    L.rpca_philox4x32_10.argtypes = [P, I64, C.POINTER(C.c_uint32), C.c_uint64, P]
+    L.rpca_philox4x32_10.restype = I
     _lib = L
     return L
 
@@ -117,7 +144,10 @@ EXPORTED = ["rpca_default_options", "rpca_create", "rpca_fg", "rpca_apply", "rpc
             "rpca_certificate", "rpca_destroy", "rpca_last_error", "rpca_version", "rpca_plan_info",
             "rpca_profile", "rpca_profile_read", "rpca_solve_log", "rpca_solve_trials", "rpca_x_storage", "rpca_fg_noalloc", "rpca_create_batch",
             "rpca_solve_batch", "rpca_batch_context", "rpca_batch_size", "rpca_batch_last_error",
-            "rpca_destroy_batch"]
+            "rpca_destroy_batch", "rpca_ws_nparam", "rpca_ws_create", "rpca_ws_set_params", "rpca_ws_get_params",
+            "rpca_ws_predict", "rpca_ws_train_step", "rpca_ws_last_error", "rpca_ws_destroy",
+            "rpca_set_warm_start", "rpca_sketch_spectrum", "rpca_ws_sample", "rpca_gen_planted",
+            "rpca_philox4x32_10"]
 
 
 class RpcaError(RuntimeError):
@@ -301,3 +331,97 @@ def rpca_destroy_batch(b):
 
 def rpca_destroy(ctx):
     lib().rpca_destroy(ctx)
+
+
+# ---- Learned warm start -------------------------------------------------------------------
+
+
+class WsError(RuntimeError):
+    pass
+
+
+def _ws_check(st, w):
+    if st != RPCA_OK:
+        raise RpcaError(st, rpca_ws_last_error(w))
+    return st
+
+
+def _floats(a, n):
+    import numpy as np
+    a = np.ascontiguousarray(a, dtype=np.float32).ravel()
+    if a.size != n:
+        raise ValueError(f"expected {n} floats, got {a.size}")
+    return a, a.ctypes.data_as(C.POINTER(C.c_float))
+
+
+def rpca_ws_nparam():
+    return lib().rpca_ws_nparam()
+
+
+def rpca_ws_create(theta, stream=None):
+    """A model from the packed float32 parameters theta (host array)."""
+    keep, ptr = _floats(theta, rpca_ws_nparam())
+    w = C.c_void_p()
+    _ws_check(lib().rpca_ws_create(C.byref(w), ptr, stream), None)
+    return w.value
+
+
+def rpca_ws_set_params(w, theta):
+    keep, ptr = _floats(theta, rpca_ws_nparam())
+    _ws_check(lib().rpca_ws_set_params(w, ptr), w)
+
+
+def rpca_ws_get_params(w):
+    """(theta, grad of the last training step) as host float32 arrays."""
+    import numpy as np
+    n = rpca_ws_nparam()
+    th = np.zeros(n, np.float32)
+    gr = np.zeros(n, np.float32)
+    _ws_check(lib().rpca_ws_get_params(w, th.ctypes.data_as(C.POINTER(C.c_float)),
+                                       gr.ctypes.data_as(C.POINTER(C.c_float))), w)
+    return th, gr
+
+
+def rpca_ws_predict(w, X, B, W):
+    _ws_check(lib().rpca_ws_predict(w, _ptr(X), B, _ptr(W)), w)
+
+
+def rpca_ws_train_step(w, X, T, K, B, lr):
+    """One Adam step; returns the batch loss before the step."""
+    loss = C.c_float(0.0)
+    _ws_check(lib().rpca_ws_train_step(w, _ptr(X), _ptr(T), _ptr(K), B, lr, C.byref(loss)), w)
+    return loss.value
+
+
+def rpca_ws_last_error(w):
+    return lib().rpca_ws_last_error(w).decode()
+
+
+def rpca_ws_destroy(w):
+    lib().rpca_ws_destroy(w)
+
+
+def rpca_set_warm_start(ctx, w):
+    _check(lib().rpca_set_warm_start(ctx, w), ctx)
+
+
+def rpca_sketch_spectrum(ctx):
+    import numpy as np
+    s = np.zeros(32, np.float32)
+    l = C.c_int(0)
+    _check(lib().rpca_sketch_spectrum(ctx, s.ctypes.data_as(C.POINTER(C.c_float)), C.byref(l)), ctx)
+    return s[:l.value].copy()
+
+
+def rpca_ws_sample(ctx, Us, Vs, U, V, x, wstar):
+    _check(lib().rpca_ws_sample(ctx, _ptr(Us), _ptr(Vs), _ptr(U), _ptr(V), _ptr(x), _ptr(wstar)), ctx)
+
+
+def rpca_gen_planted(m, n, rank, p_outlier, noise_std, seed, instance, X, ldx, L0=None, stream=None):
+    _check(lib().rpca_gen_planted(m, n, rank, p_outlier, noise_std, seed, instance, _ptr(X), ldx, _ptr(L0),
+                                  stream), None)
+
+
+def rpca_philox4x32_10(out, count, ctr, key, stream=None):
+    c = (C.c_uint32 * 4)(*[int(v) & 0xFFFFFFFF for v in ctr])
+    _check(lib().rpca_philox4x32_10(_ptr(out), count, c, key, stream), None)
