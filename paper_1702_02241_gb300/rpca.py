@@ -386,11 +386,18 @@ def rpca_ws_predict(w, X, B, W):
     _ws_check(lib().rpca_ws_predict(w, _ptr(X), B, _ptr(W)), w)
 
 
-def rpca_ws_train_step(w, X, T, K, B, lr):
-    """One Adam step; returns the batch loss before the step."""
+def rpca_ws_train_step(w, X, T, K, B, lr, want_loss=True):
+    """One Adam step; returns the batch loss before the step (None unless want_loss: reading
+    it synchronises)."""
     loss = C.c_float(0.0)
-    _ws_check(lib().rpca_ws_train_step(w, _ptr(X), _ptr(T), _ptr(K), B, lr, C.byref(loss)), w)
-    return loss.value
+    _ws_check(lib().rpca_ws_train_step(w, _ptr(X), _ptr(T), _ptr(K), B, lr,
+                                       C.byref(loss) if want_loss else None), w)
+    return loss.value if want_loss else None
+
+
+def offset(T, elements):
+    """Device address of element `elements` of a contiguous torch tensor (no copy)."""
+    return T.data_ptr() + elements * T.element_size()
 
 
 def rpca_ws_last_error(w):

@@ -183,3 +183,21 @@ def test_learned_start_kept_when_better_and_dropped_when_worse():
     P.close()
     rpca.rpca_ws_destroy(good)
     rpca.rpca_ws_destroy(bad)
+
+
+def test_trained_start_needs_fewer_iterations_on_heldout():
+    """End to end on a small protocol: instances generated on the device, solved from the
+    sketch, the network trained on (features, targets), then held-out instances solved from
+    the learned start need fewer iterations than from the sketch start, to the same objective."""
+    from paper_1702_02241_gb300 import warm_start as W
+    specs = W.instance_params(240, 7, m=1024, n=128)
+    x, t, K, _ = W.make_samples(specs, 7)
+    w, losses = W.train(x, t, K, epochs=150, batch=64, seed=3)
+    assert losses[-1][1] < 0.5 * losses[0][1]
+    held = W.instance_params(16, 8, m=1024, n=128)
+    res = W.evaluate(w, held, 8, starts=("sketch", "learned"))
+    assert res["sketch"]["ok"] == res["learned"]["ok"] == len(held)
+    assert np.mean(res["learned"]["iters"]) < np.mean(res["sketch"]["iters"])
+    for a, b in zip(res["learned"]["F"], res["sketch"]["F"]):
+        assert a == pytest.approx(b, rel=1e-5)
+    rpca.rpca_ws_destroy(w)
