@@ -149,3 +149,39 @@ def certificate(X, mask, U, V, lam_L, lam_S, F_best=None, tau=TAU, t4_method="au
     return Cert(cert=cert, cert_rel=cert / lam_L, t1=t1, t2=t2, t3=t3, t4=t4, rank_r=r,
                 normL_F=normL, F=float(F), F_bound=float(F_bound), gap_bound=float(gap),
                 sigma_perp=sp)
+
+
+def perp_top_pair(X, mask, U, V, lam_L, lam_S, tau=TAU):
+    """Largest singular value sigma_1 of P_U1perp D P_V1perp at L = U V^T and its unit singular
+    vectors (u_1, v_1) with u_1^T D v_1 = sigma_1 (dense SVD of the explicit projected matrix;
+    U1, V1 as the certificate takes them, negligible and tiny-inactive directions included in
+    the complement)."""
+    U = np.asarray(U, np.float64)
+    V = np.asarray(V, np.float64)
+    R = core.residual(X, U, V)
+    D = core.D_of_R(R, mask, lam_S)
+    F = 0.5 * lam_L * (np.sum(U * U) + np.sum(V * V)) + core.phi_of_R(R, mask, lam_S)
+    U1, V1, s1 = range_bases(U, V, tau)
+    if s1.size:
+        b_diag = np.einsum("ij,ij->j", U1, D @ V1)
+        keep = ~((s1 <= DROP_TAU * s1[0]) & (np.abs(lam_L + b_diag) > 0.5 * lam_L))
+        keep &= ~(lam_L * s1 <= NEG_TAU * F)
+        U1, V1 = U1[:, keep], V1[:, keep]
+    M = D - U1 @ (U1.T @ D)
+    M = M - (M @ V1) @ V1.T
+    Uu, ss, Vt = np.linalg.svd(M, full_matrices=False)
+    return float(ss[0]), Uu[:, 0], Vt[0]
+
+
+def grow_column(X, mask, U, V, lam_L, lam_S):
+    """Dynamic rank increase (Sec. 4.1): one more column for (U, V).  Reading of the paper,
+    which leaves u, v open: the top singular pair of P_U1perp D P_V1perp, scaled so that the
+    new rank-one term is -t u_1 v_1^T with t = sigma_1 - lam_L (the minimiser of the quadratic
+    upper bound F(L) - t (sigma_1 - lam_L) + t^2 / 2 that psi'' <= 1 gives); no column (t = 0)
+    when sigma_1 <= lam_L.  Returns (U', V', sigma_1)."""
+    s1, u1, v1 = perp_top_pair(X, mask, U, V, lam_L, lam_S)
+    t = max(s1 - lam_L, 0.0)
+    r = np.sqrt(t)
+    U2 = np.concatenate([np.asarray(U, np.float64), (r * u1)[:, None]], axis=1)
+    V2 = np.concatenate([np.asarray(V, np.float64), (-r * v1)[:, None]], axis=1)
+    return U2, V2, s1

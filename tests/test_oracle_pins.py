@@ -383,3 +383,36 @@ def test_certificate_keeps_small_but_significant_direction():
     U1, V1, s = ocert.range_bases(Ub, Vb)
     assert s.size == 3 and lam_L * s[-1] > 1e-12 * c.F
     assert c.rank_r == 3 and c.cert_rel < 1e-6
+
+
+@pytest.mark.parametrize("lam_S", [0.3, math.inf])
+def test_grow_column_decreases_by_the_quadratic_bound(lam_S):
+    """Rank increase (Sec. 4.1): with k below the rank of the solution the certificate's
+    spectral term is positive (sigma_1 > lam_L), and the added column lowers F by at least
+    (sigma_1 - lam_L)^2 / 2 -- the bound that psi'' <= 1 gives along a unit rank-one
+    direction -- computed here from F itself, not from the column's construction."""
+    g = np.random.default_rng(12)
+    m, n = 60, 45
+    X = g.normal(size=(m, 5)) @ g.normal(size=(5, n)) * 1.5 + 0.05 * g.normal(size=(m, n))
+    lam_L = 1.0
+    U0, V0 = gen.factors(m, n, 2, seed=3, scale=0.5)
+    r = lbfgs.solve(X, None, U0, V0, lam_L, lam_S, gtol=1e-11, max_iter=4000)
+    U, V = r.U, r.V
+    F0 = core.objective(X, None, U, V, lam_L, lam_S)
+    U2, V2, s1 = ocert.grow_column(X, None, U, V, lam_L, lam_S)
+    assert s1 > lam_L
+    F1 = core.objective(X, None, U2, V2, lam_L, lam_S)
+    assert F1 <= F0 - 0.5 * (s1 - lam_L) ** 2 + 1e-9 * abs(F0)
+    # The pair is the top singular pair of the projected residual gradient: its value is the
+    # certificate's largest perpendicular singular value.
+    c = ocert.certificate(X, None, U, V, lam_L, lam_S)
+    assert s1 == pytest.approx(c.sigma_perp[0], rel=1e-10)
+
+
+def test_grow_column_adds_nothing_at_a_solution():
+    """At a solution (sigma_1 <= lam_L) the new column is zero and F is unchanged."""
+    X = _lowrank_noise(20, 15, 3, 4)
+    Ub, Vb = convex.balanced_factors(convex.svt(X, 1.0), 3)
+    U2, V2, s1 = ocert.grow_column(X, np.ones(X.shape, np.uint8), Ub, Vb, 1.0, np.inf)
+    assert s1 <= 1.0 + 1e-9
+    assert np.all(U2[:, 3] == 0) and np.all(V2[:, 3] == 0)
