@@ -294,6 +294,35 @@ RPCA_API rpca_status rpca_fg_noalloc(int64_t m, int64_t n, const float *X, int64
 /* Library version string. */
 RPCA_API const char *rpca_version(void);
 
+/*
+ * Unit singular vectors (u: device m floats, v: device n floats) of the largest singular value
+ * of P_U1perp D P_V1perp at the point of this context's last full certificate (the spectral
+ * term of Sec. 3.4), from its block-Lanczos bases; *sigma1 (may be NULL) = that singular value,
+ * u^T D v = sigma1.  Needs a certificate with a spectral step (rpca_certificate, or the end of
+ * rpca_solve) on this context.  Synchronous.
+ */
+RPCA_API rpca_status rpca_perp_direction(rpca_ctx *c, float *u, float *v, double *sigma1);
+/* The q <= min(qmax, 16) leading pairs of the same: U (device, m x q, ld ldu >= m), V (device,
+ * n x q, ld ldv >= n), sig (host, q values, descending), *q_out = q (at most the Ritz values
+ * the last spectral step computed).  Synchronous. */
+RPCA_API rpca_status rpca_perp_directions(rpca_ctx *c, int qmax, float *U, int64_t ldu, float *V, int64_t ldv,
+                                          double *sig, int *q_out);
+
+/*
+ * Dynamic rank increase (Sec. 4.1).  U, V: device m x kmax and n x kmax buffers (column-major,
+ * leading dimensions m and n); the first k columns (k of the context) follow rpca_solve's
+ * rules.  Solves; a solve at a rank that cannot certify stops once t1..t3 meet the tolerance
+ * while t4 > 0.  While the certificate's spectral term shows directions the factors cannot
+ * represent (singular values sigma_i of P_U1perp D P_V1perp above lam_L) and the rank is below
+ * kmax (<= 16), one column (sqrt(t_i) u_i, -sqrt(t_i) v_i), t_i = sigma_i - lam_L, is added per
+ * such direction (the minimiser of the quadratic upper bound of F along it; the paper leaves
+ * the column open and allows growing k aggressively), kept when F drops, and the solve
+ * continues from the grown point at the new rank (contexts for larger ranks are made on demand
+ * and owned by c).  *k_out = the final rank; res (may be NULL) = the last solve's result with the
+ * iteration, evaluation and time counts of all of them.
+ */
+RPCA_API rpca_status rpca_solve_grow(rpca_ctx *c, float *U, float *V, int kmax, rpca_result *res, int *k_out);
+
 /* ---- Learned warm start ---------------------------------------------------------------
  * An extension of this library (the paper compares SVD, randomized-SVD and random starts,
  * Sec. 4.2, and finds that the start matters).  A three-layer network (40 inputs, two hidden

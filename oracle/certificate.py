@@ -151,11 +151,9 @@ def certificate(X, mask, U, V, lam_L, lam_S, F_best=None, tau=TAU, t4_method="au
                 sigma_perp=sp)
 
 
-def perp_top_pair(X, mask, U, V, lam_L, lam_S, tau=TAU):
-    """Largest singular value sigma_1 of P_U1perp D P_V1perp at L = U V^T and its unit singular
-    vectors (u_1, v_1) with u_1^T D v_1 = sigma_1 (dense SVD of the explicit projected matrix;
-    U1, V1 as the certificate takes them, negligible and tiny-inactive directions included in
-    the complement)."""
+def perp_matrix(X, mask, U, V, lam_L, lam_S, tau=TAU):
+    """The explicit projected matrix P_U1perp D P_V1perp at L = U V^T (U1, V1 as the
+    certificate takes them: negligible and tiny-inactive directions in the complement)."""
     U = np.asarray(U, np.float64)
     V = np.asarray(V, np.float64)
     R = core.residual(X, U, V)
@@ -168,9 +166,22 @@ def perp_top_pair(X, mask, U, V, lam_L, lam_S, tau=TAU):
         keep &= ~(lam_L * s1 <= NEG_TAU * F)
         U1, V1 = U1[:, keep], V1[:, keep]
     M = D - U1 @ (U1.T @ D)
-    M = M - (M @ V1) @ V1.T
+    return M - (M @ V1) @ V1.T
+
+
+def perp_top_pairs(X, mask, U, V, lam_L, lam_S, q, tau=TAU):
+    """The q largest singular values of P_U1perp D P_V1perp (descending) and their unit
+    singular vectors (columns of Uq, Vq, u_i^T D v_i = sigma_i)."""
+    M = perp_matrix(X, mask, U, V, lam_L, lam_S, tau)
     Uu, ss, Vt = np.linalg.svd(M, full_matrices=False)
-    return float(ss[0]), Uu[:, 0], Vt[0]
+    return ss[:q], Uu[:, :q], Vt[:q].T
+
+
+def perp_top_pair(X, mask, U, V, lam_L, lam_S, tau=TAU):
+    """Largest singular value sigma_1 of P_U1perp D P_V1perp at L = U V^T and its unit singular
+    vectors (u_1, v_1) with u_1^T D v_1 = sigma_1 (dense SVD of the explicit projected matrix)."""
+    ss, Uq, Vq = perp_top_pairs(X, mask, U, V, lam_L, lam_S, 1, tau)
+    return float(ss[0]), Uq[:, 0], Vq[:, 0]
 
 
 def grow_column(X, mask, U, V, lam_L, lam_S):
@@ -185,3 +196,17 @@ def grow_column(X, mask, U, V, lam_L, lam_S):
     U2 = np.concatenate([np.asarray(U, np.float64), (r * u1)[:, None]], axis=1)
     V2 = np.concatenate([np.asarray(V, np.float64), (-r * v1)[:, None]], axis=1)
     return U2, V2, s1
+
+
+def grow_columns(X, mask, U, V, lam_L, lam_S, qmax):
+    """Dynamic rank increase by several columns at once (Sec. 4.1 allows growing k
+    "aggressively"): every singular pair of P_U1perp D P_V1perp with sigma_i > lam_L, at most
+    qmax of them, each scaled like grow_column's (t_i = sigma_i - lam_L).  The pairs are
+    orthonormal, so the nuclear norms and the quadratic terms add: F drops by at least
+    sum_i (sigma_i - lam_L)^2 / 2.  Returns (U', V', sigmas added)."""
+    ss, Uq, Vq = perp_top_pairs(X, mask, U, V, lam_L, lam_S, qmax)
+    keep = ss > lam_L
+    t = np.sqrt(ss[keep] - lam_L)
+    U2 = np.concatenate([np.asarray(U, np.float64), Uq[:, keep] * t], axis=1)
+    V2 = np.concatenate([np.asarray(V, np.float64), -Vq[:, keep] * t], axis=1)
+    return U2, V2, ss[keep]

@@ -823,6 +823,9 @@ rpca_status rpca_apply(rpca_ctx* c, const float* U, const float* V, int b, const
 
 void rpca_destroy(rpca_ctx* c) {
   if (!c) return;
+  for (rpca_ctx* g : c->grown)
+    if (g) rpca_destroy(g);
+  c->grown.clear();
   cudaStreamSynchronize(c->stream);
   free_solver(c);
   free_cert(c);

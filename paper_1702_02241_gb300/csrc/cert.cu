@@ -37,6 +37,7 @@ constexpr int CERT_KMAX = 16;
 constexpr int LZ_B = 8;       // Lanczos block size
 constexpr int LZ_SMAX = 32;   // maximum block steps (Krylov dimension 256)
 constexpr int LZ_TMAX = LZ_B * LZ_SMAX;
+constexpr int RITZ_TOPQ = 16;  // leading Ritz pairs kept for the rank increase
 constexpr double RANK_TAU = 1e-8;  // numerical rank of L: sigma_i > RANK_TAU * sigma_1
 constexpr double DROP_TAU = 1e-3;  // tiny-and-inactive directions go to the complement
 constexpr double NEG_TAU = 1e-12;  // lam_L sigma_i <= NEG_TAU F: numerically zero direction
@@ -56,6 +57,10 @@ struct CertState {
   double t4_prev, s1_prev;
   int converged;
   double resid[2];
+  // Leading Ritz pairs of the last spectral evaluation (their coefficients in the Lanczos
+  // bases P[:, 0:d], Q[:, 0:d] are in CertBuffers::ritz): values, count, d.
+  double ritz_s[RITZ_TOPQ];
+  int ritz_q, ritz_d;
 };
 
 struct CertBuffers {
@@ -73,6 +78,7 @@ struct CertBuffers {
   float* zm = nullptr;   // m x max(B, k) zeros
   float* zn = nullptr;   // n x max(B, k) zeros
   double* T = nullptr;   // TMAX x TMAX
+  double* ritz = nullptr;  // leading Ritz pairs' coefficients: [2][RITZ_TOPQ][LZ_TMAX] (P side, Q side)
   float* Tw = nullptr;   // TMAX x TMAX float32 working copy for the Ritz SVD
   float* Tv = nullptr;   // TMAX x TMAX right vectors
   float* Wraw = nullptr; // m x B, A Q_j before orthogonalisation
@@ -343,14 +349,32 @@ __global__ void cert_reset_kernel(CertState* st) {
   st->converged = 0;
   st->t4 = 0.0;
   st->sigma1 = 0.0;
+  st->ritz_d = 0;
+  st->ritz_q = 0;
 }
 
 // Ritz values of T[0:d, 0:d] (float32 one-sided Jacobi in global memory) -> t4 estimate,
 // sigma_1, and whether both have settled since the previous check.
 // Ritz values of the projected matrix, sorted: t4 and the stopping tests of the Lanczos loop.
 // Called by the whole CTA (the sort is CTA-wide); thread 0 updates the state.
-__device__ void ritz_finish(CertState* st, const float* s, int* ord, int d, double lam_L, int final_step) {
+__device__ void ritz_finish(CertState* st, const float* s, int* ord, int d, double lam_L, int final_step,
+                            const float* A, const float* V, double* ritz) {
   cta_sort_desc<float>(s, d, ord);
+  {  // the leading pairs: left vector A[:, j] / s_j (A holds U diag(s)), right vector V[:, j]
+    const int q = d < RITZ_TOPQ ? d : RITZ_TOPQ;
+    for (int e = threadIdx.x; e < q * d; e += blockDim.x) {
+      const int t = e / d, c = e - t * d;
+      const int j = ord[t];
+      const float sj = s[j];
+      ritz[t * LZ_TMAX + c] = sj > 0.f ? (double)A[c + (size_t)j * d] / (double)sj : 0.0;
+      ritz[(RITZ_TOPQ + t) * LZ_TMAX + c] = (double)V[c + (size_t)j * d];
+    }
+    for (int t = threadIdx.x; t < q; t += blockDim.x) st->ritz_s[t] = s[ord[t]];
+    if (threadIdx.x == 0) {
+      st->ritz_d = d;
+      st->ritz_q = q;
+    }
+  }
   if (threadIdx.x == 0) {
     double t4 = 0.0;
     for (int i = 0; i < d; ++i) {
@@ -383,7 +407,7 @@ __device__ inline float ritz_noise(int d) { return 2.0f * d * 6e-8f; }
 
 // d <= 32: one warp, the matrix in registers (warp_jacobi_svd).
 __global__ void __launch_bounds__(32) cert_ritz_warp_kernel(CertState* st, const double* T, int d, double lam_L,
-                                                            int final_step) {
+                                                            int final_step, double* ritz) {
   __shared__ float A[32 * 32], V[32 * 32], s[32];
   __shared__ int ord[32];
   for (int i = threadIdx.x; i < d * d; i += blockDim.x) {
@@ -392,12 +416,12 @@ __global__ void __launch_bounds__(32) cert_ritz_warp_kernel(CertState* st, const
   }
   __syncwarp();
   warp_jacobi_svd<float, 32, 32>(A, d, d, d, V, d, s, 40, ritz_tol(d), ritz_noise(d));
-  ritz_finish(st, s, ord, d, lam_L, final_step);
+  ritz_finish(st, s, ord, d, lam_L, final_step, A, V, ritz);
 }
 
 // Larger d: the CTA form, in shared memory up to d = 96, else in global memory.
 __global__ void __launch_bounds__(1024) cert_ritz_kernel(CertState* st, const double* T, float* Ag, float* Vg, int d,
-                                                          double lam_L, int final_step) {
+                                                          double lam_L, int final_step, double* ritz) {
   __shared__ float s[LZ_TMAX];
   __shared__ int ord[LZ_TMAX];
   __shared__ int flag;
@@ -411,7 +435,7 @@ __global__ void __launch_bounds__(1024) cert_ritz_kernel(CertState* st, const do
   }
   __syncthreads();
   cta_jacobi_svd<float>(A, d, d, d, V, d, s, &flag, 40, ritz_tol(d), ritz_noise(d));
-  ritz_finish(st, s, ord, d, lam_L, final_step);
+  ritz_finish(st, s, ord, d, lam_L, final_step, A, V, ritz);
 }
 
 __global__ void pad_copy_kernel(const float* src, int64_t rows, int k, float* dst, int kp) {
@@ -429,6 +453,7 @@ void free_cert(rpca_ctx* c) {
   if (!b) return;
   cudaFree(b->DV);
   cudaFree(b->T);
+  cudaFree(b->ritz);
   cudaFree(b->st);
   cudaFree(b->blk);
   cudaFree(b->counter);
@@ -483,6 +508,7 @@ static rpca_status ensure_cert(rpca_ctx* c) {
   b->Tv = p;
   CERT_CUDA(cudaMemsetAsync(b->zm, 0, sizeof(float) * (m + n) * zc, c->stream));
   CERT_CUDA(cudaMalloc(&b->T, sizeof(double) * LZ_TMAX * LZ_TMAX));
+  CERT_CUDA(cudaMalloc(&b->ritz, sizeof(double) * 2 * RITZ_TOPQ * LZ_TMAX));
   CERT_CUDA(cudaMalloc(&b->st, sizeof(CertState)));
   CERT_CUDA(cudaMemsetAsync(b->st, 0, sizeof(CertState), c->stream));
   CERT_CUDA(cudaMallocHost(&b->host, sizeof(CertState)));
@@ -717,12 +743,12 @@ rpca_status cert_compute(rpca_ctx* c, const float* U, const float* V, rpca_cert*
       if (steps == 2 || steps == 4 || steps == 6 || (steps % 4) == 0 || last) {
         const int d = steps * LZ_B;
         if (d <= 32) {
-          cert_ritz_warp_kernel<<<1, 32, 0, c->stream>>>(st, b->T, d, c->lam_L, last ? 1 : 0);
+          cert_ritz_warp_kernel<<<1, 32, 0, c->stream>>>(st, b->T, d, c->lam_L, last ? 1 : 0, b->ritz);
         } else {
           const size_t rsm = d <= 96 ? (size_t)2 * d * d * sizeof(float) : 0;
           CERT_CUDA(cudaFuncSetAttribute(cert_ritz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          2 * 96 * 96 * (int)sizeof(float)));
-          cert_ritz_kernel<<<1, 1024, rsm, c->stream>>>(st, b->T, b->Tw, b->Tv, d, c->lam_L, last ? 1 : 0);
+          cert_ritz_kernel<<<1, 1024, rsm, c->stream>>>(st, b->T, b->Tw, b->Tv, d, c->lam_L, last ? 1 : 0, b->ritz);
         }
         count_launches(c, 1);
         CERT_CUDA(cudaGetLastError());
@@ -769,4 +795,37 @@ extern "C" rpca_status rpca_certificate(rpca_ctx* c, const float* U, const float
   if (!c) return RPCA_EINVAL;
   if (!U || !V || !out) return set_err(c, RPCA_EINVAL, "U, V and out are required");
   return cert_compute(c, U, V, out, true);
+}
+
+extern "C" rpca_status rpca_perp_directions(rpca_ctx* c, int qmax, float* U, int64_t ldu, float* V, int64_t ldv,
+                                            double* sig, int* q_out) {
+  if (!c) return RPCA_EINVAL;
+  if (!U || !V || !q_out || qmax < 1 || ldu < c->m || ldv < c->n)
+    return set_err(c, RPCA_EINVAL, "U, V, q_out are required, qmax >= 1, ldu >= m, ldv >= n");
+  *q_out = 0;
+  CertBuffers* b = c->cert;
+  if (!b) return set_err(c, RPCA_EINVAL, "no certificate has been computed on this context");
+  int dq[2] = {0, 0};
+  double s[RITZ_TOPQ];
+  CERT_CUDA(cudaMemcpyAsync(dq, &b->st->ritz_q, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CERT_CUDA(cudaMemcpyAsync(s, b->st->ritz_s, sizeof s, cudaMemcpyDeviceToHost, c->stream));
+  CERT_CUDA(cudaStreamSynchronize(c->stream));
+  const int q = std::min(std::min(qmax, dq[0]), RITZ_TOPQ), d = dq[1];
+  if (d < 1 || q < 1) return set_err(c, RPCA_EINVAL, "the last certificate had no spectral step (rpca_certificate first)");
+  const int64_t m = c->m, n = c->n;
+  CERT_CUDA(ts_mul_c(c, b->P, m, d, b->ritz, LZ_TMAX, q, U, ldu, m, 1.f, 0.f, c->stream));
+  CERT_CUDA(ts_mul_c(c, b->Q, n, d, b->ritz + RITZ_TOPQ * LZ_TMAX, LZ_TMAX, q, V, ldv, n, 1.f, 0.f, c->stream));
+  CERT_CUDA(cudaStreamSynchronize(c->stream));
+  if (sig)
+    for (int t = 0; t < q; ++t) sig[t] = s[t];
+  *q_out = q;
+  return RPCA_OK;
+}
+
+extern "C" rpca_status rpca_perp_direction(rpca_ctx* c, float* u, float* v, double* sigma1) {
+  int q = 0;
+  double s1 = 0.0;
+  rpca_status st = rpca_perp_directions(c, 1, u, c ? c->m : 0, v, c ? c->n : 0, &s1, &q);
+  if (st == RPCA_OK && sigma1) *sigma1 = s1;
+  return st;
 }

@@ -85,6 +85,9 @@ struct rpca_ctx {
   const rpca_ws* ws_model = nullptr;
   float* sk_sigma = nullptr;  // 32 floats on the device, owned
   int sk_l = 0;
+  // Rank increase: contexts for k + 1, k + 2, ... on the same X (owned), made on demand.
+  std::vector<rpca_ctx*> grown;
+  bool grow_stop = false;  // a solve returns once t1..t3 meet the tolerance but t4 > 0
   std::string err;
   // Instrumentation (rpca_profile).
   bool prof = false;

@@ -77,6 +77,16 @@ struct PhaseTimer {
   }
 };
 
+__global__ void scale_kernel(float* x, int64_t count, float t) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] *= t;
+}
+
+void fill_scale(float* x, int64_t count, float t, cudaStream_t s) {
+  const int grid = (int)std::min<int64_t>(1024, (count + 255) / 256);
+  scale_kernel<<<std::max(grid, 1), 256, 0, s>>>(x, count, t);
+}
+
 void fill_normal(float* out, int64_t count, uint64_t seed, float scale, cudaStream_t s) {
   const int grid = (int)std::min<int64_t>(1024, (count + 255) / 256);
   fill_normal_kernel<<<std::max(grid, 1), 256, 0, s>>>(out, count, seed, scale);
@@ -228,12 +238,17 @@ static rpca_status job_step(SolveJob& j) {
       j.timer->begin(2);
       if ((s = cert_compute(c, solver_point(c), solver_point(c) + j.mk, &j.cert, false)) != RPCA_OK) return s;
       ++j.cert_evals;
+      bool rank_deficit = false;
       if (j.cert.cert_rel <= c->opt.cert_tol) {
         if ((s = cert_compute(c, solver_point(c), solver_point(c) + j.mk, &j.cert, true)) != RPCA_OK) return s;
         if (j.cert.cert_rel <= c->opt.cert_tol) j.certified = true;
+        else rank_deficit = j.cert.t4 > 0.0;
       }
       j.timer->end();
-      if (j.certified) {
+      // Stationary in the factors' range (t1..t3 meet the tolerance) with a direction outside
+      // it that would lower F (t4 > 0): more iterations at this rank cannot certify; the
+      // rank-increasing solve takes over from here (Sec. 4.1).
+      if (j.certified || (rank_deficit && c->grow_stop)) {
         j.done = true;
         return RPCA_OK;
       }
@@ -379,3 +394,100 @@ rpca_status solve_jobs(rpca_ctx* const* ctx, float* const* U, float* const* V, r
 }
 
 }  // namespace rpca
+
+extern "C" rpca_status rpca_perp_directions(rpca_ctx* c, int qmax, float* U, int64_t ldu, float* V, int64_t ldv,
+                                            double* sig, int* q_out);  // cert.cu
+
+// Dynamic rank increase (Sec. 4.1): solve; while the certificate's spectral term shows
+// directions the factors cannot represent (singular values of P_U1perp D P_V1perp above lam_L)
+// and k < kmax, add one column (sqrt(t_i) u_i, -sqrt(t_i) v_i), t_i = sigma_i - lam_L, per such
+// direction (the paper allows growing k aggressively), keep them if F drops, and continue on
+// a context with the new rank from the grown point.
+extern "C" rpca_status rpca_solve_grow(rpca_ctx* c, float* U, float* V, int kmax, rpca_result* res, int* k_out) {
+  if (!c) return RPCA_EINVAL;
+  if (!U || !V || !k_out) return set_err(c, RPCA_EINVAL, "U, V and k_out are required");
+  if (kmax < c->k || kmax > 16 || kmax > std::min(c->m, c->n))
+    return set_err(c, RPCA_EINVAL, "kmax must be in [k, min(16, m, n)]");
+  *k_out = c->k;
+  rpca_result r, tot;
+  memset(&tot, 0, sizeof tot);
+  rpca_ctx* cur = c;
+  int k = c->k;
+  struct GrowFlag {  // set for the duration of the call
+    rpca_ctx* c;
+    explicit GrowFlag(rpca_ctx* x) : c(x) { c->grow_stop = true; }
+    ~GrowFlag() { c->grow_stop = false; }
+  } flag(c);
+  rpca_status s = rpca_solve(cur, U, V, &r);
+  auto add = [&](const rpca_result& x) {
+    tot.iters += x.iters;
+    tot.evals += x.evals;
+    tot.cert_evals += x.cert_evals;
+    tot.seconds += x.seconds;
+    tot.ms_init += x.ms_init;
+    tot.ms_iter += x.ms_iter;
+    tot.ms_cert += x.ms_cert;
+  };
+  add(r);
+  if (c->grown.size() < 17) c->grown.resize(17, nullptr);
+  while (s == RPCA_ENOTCONV && k < kmax && r.cert.t4 > 0.0 && r.cert.sigma1_perp > c->lam_L) {
+    const int64_t m = c->m, n = c->n;
+    double sig[16];
+    int q = 0;
+    // The certificate at the returned point left its Lanczos bases on `cur`.
+    rpca_status st = rpca_perp_directions(cur, kmax - k, U + m * k, m, V + n * k, n, sig, &q);
+    if (st != RPCA_OK) return st;
+    int add_cols = 0;
+    while (add_cols < q && sig[add_cols] > c->lam_L) ++add_cols;
+    if (add_cols == 0) break;
+    for (int t = 0; t < add_cols; ++t) {
+      const float sc = (float)std::sqrt(sig[t] - c->lam_L);
+      fill_scale(U + m * (k + t), m, sc, cur->stream);
+      fill_scale(V + n * (k + t), n, -sc, cur->stream);
+    }
+    const int k2 = k + add_cols;
+    if (!c->grown[k2]) {
+      rpca_options o = c->opt;
+      o.init = RPCA_INIT_USER;
+      rpca_ctx* nx = nullptr;
+      st = create_ctx(&nx, m, n, c->X, c->ldx, c->mask, c->ldmask, k2, c->lam_L, c->lam_S, &o, c->stream,
+                      c->grid_cap);
+      if (st != RPCA_OK) return set_err(c, st, std::string("rank increase: ") + rpca_last_error(nullptr));
+      nx->grow_stop = true;  // internal: only ever solved by this function
+      c->grown[k2] = nx;
+    }
+    rpca_ctx* nxt = c->grown[k2];
+    // Keep the columns only if the objective drops.
+    double f_new = 0.0;
+    float* g = nullptr;
+    if (cudaMalloc(&g, sizeof(float) * (m + n) * k2) != cudaSuccess) return set_err(c, RPCA_ENOMEM, "cudaMalloc");
+    st = rpca_fg(nxt, U, V, &f_new, g, g + m * k2);
+    cudaStreamSynchronize(nxt->stream);
+    cudaFree(g);
+    if (st != RPCA_OK) return st;
+    if (!(f_new < r.F)) {
+      cudaMemsetAsync(U + m * k, 0, sizeof(float) * m * add_cols, cur->stream);
+      cudaMemsetAsync(V + n * k, 0, sizeof(float) * n * add_cols, cur->stream);
+      break;
+    }
+    k = k2;
+    cur = nxt;
+    s = rpca_solve(cur, U, V, &r);
+    add(r);
+  }
+  *k_out = k;
+  if (res) {
+    rpca_result o = r;
+    o.iters = tot.iters;
+    o.evals = tot.evals;
+    o.cert_evals = tot.cert_evals;
+    o.seconds = tot.seconds;
+    o.ms_init = tot.ms_init;
+    o.ms_iter = tot.ms_iter;
+    o.ms_cert = tot.ms_cert;
+    o.init_used = c->opt.init;
+    *res = o;
+  }
+  if (s != RPCA_OK && cur != c) set_err(c, s, rpca_last_error(cur));
+  return s;
+}

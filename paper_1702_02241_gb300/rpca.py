@@ -109,6 +109,12 @@ def lib():
     L.rpca_fg_noalloc.restype = I
     L.rpca_version.argtypes = []
     L.rpca_version.restype = C.c_char_p
+    L.rpca_perp_direction.argtypes = [P, P, P, C.POINTER(C.c_double)]
+    L.rpca_perp_direction.restype = I
+    L.rpca_perp_directions.argtypes = [P, I, P, I64, P, I64, C.POINTER(C.c_double), C.POINTER(C.c_int)]
+    L.rpca_perp_directions.restype = I
+    L.rpca_solve_grow.argtypes = [P, P, P, I, C.POINTER(rpca_result), C.POINTER(C.c_int)]
+    L.rpca_solve_grow.restype = I
     FP = C.POINTER(C.c_float)
     L.rpca_ws_nparam.argtypes = []
     L.rpca_ws_nparam.restype = I
@@ -147,7 +153,8 @@ EXPORTED = ["rpca_default_options", "rpca_create", "rpca_fg", "rpca_apply", "rpc
             "rpca_destroy_batch", "rpca_ws_nparam", "rpca_ws_create", "rpca_ws_set_params", "rpca_ws_get_params",
             "rpca_ws_predict", "rpca_ws_train_step", "rpca_ws_last_error", "rpca_ws_destroy",
             "rpca_set_warm_start", "rpca_sketch_spectrum", "rpca_ws_sample", "rpca_gen_planted",
-            "rpca_philox4x32_10"]
+            "rpca_philox4x32_10", "rpca_perp_direction", "rpca_perp_directions",
+            "rpca_solve_grow"]
 
 
 class RpcaError(RuntimeError):
@@ -432,3 +439,30 @@ def rpca_gen_planted(m, n, rank, p_outlier, noise_std, seed, instance, X, ldx, L
 def rpca_philox4x32_10(out, count, ctr, key, stream=None):
     c = (C.c_uint32 * 4)(*[int(v) & 0xFFFFFFFF for v in ctr])
     _check(lib().rpca_philox4x32_10(_ptr(out), count, c, key, stream), None)
+
+
+def rpca_perp_direction(ctx, u, v):
+    """Writes the unit top singular pair of P_U1perp D P_V1perp (last full certificate) into the
+    device buffers u (m) and v (n); returns sigma_1."""
+    s1 = C.c_double(0.0)
+    _check(lib().rpca_perp_direction(ctx, _ptr(u), _ptr(v), C.byref(s1)), ctx)
+    return s1.value
+
+
+def rpca_solve_grow(ctx, U, V, kmax):
+    """Solve with dynamic rank increase; U, V: device (kmax, m) / (kmax, n) tensors.  Returns
+    (result, final rank)."""
+    r = rpca_result()
+    k = C.c_int(0)
+    st = lib().rpca_solve_grow(ctx, _ptr(U), _ptr(V), kmax, C.byref(r), C.byref(k))
+    if st not in (RPCA_OK, RPCA_ENOTCONV):
+        raise RpcaError(st, rpca_last_error(ctx))
+    return r, k.value
+
+
+def rpca_perp_directions(ctx, qmax, U, ldu, V, ldv):
+    """The leading pairs of P_U1perp D P_V1perp into device buffers; returns the singular values."""
+    sig = (C.c_double * 16)()
+    q = C.c_int(0)
+    _check(lib().rpca_perp_directions(ctx, qmax, _ptr(U), ldu, _ptr(V), ldv, sig, C.byref(q)), ctx)
+    return list(sig)[:q.value]
