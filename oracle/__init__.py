@@ -22,6 +22,8 @@ Modules and the passages they follow:
 * ``sketch``      -- randomized-SVD initialisation U0 = U_k S^1/2, V0 = V_k S^1/2 (Sec. 4.2).
 * ``quant``       -- the values X takes when stored as bfloat16 or FP8 E4M3 (per-column scale),
                      from the formats' definitions, for the precision form of the objective pass.
+* ``frank_wolfe`` -- the Frank-Wolfe method with marginalization (Sec. 6.2, Algorithm 1): the
+                     linear subproblem's top singular pair, the closed-form step, the gap.
 * ``warm_start``  -- the learned warm start (an extension: the paper compares SVD, rSVD and
                      random starts, Sec. 4.2): spectrum features of the sketch, the three-layer
                      network with bfloat16 weights, its gradient, Adam, the targets w*.
