@@ -323,6 +323,30 @@ RPCA_API rpca_status rpca_perp_directions(rpca_ctx *c, int qmax, float *U, int64
  */
 RPCA_API rpca_status rpca_solve_grow(rpca_ctx *c, float *U, float *V, int kmax, rpca_result *res, int *k_out);
 
+/*
+ * Frank-Wolfe method with marginalization (Sec. 6.2, Algorithm 1), the paper's alternative
+ * solver of the convex program min over ||L||_* <= t of lam_L t + phi(L), on a dense L.
+ * L: device m x n float32 (column-major, ld ldl >= m a multiple of 4, 16-byte aligned), the
+ * start on entry (the zero matrix: t_0 = 0) and the iterate on return.  Each iteration: the
+ * gradient G = P_Omega(clip(L - X)), the top singular pair of G by power_iters power
+ * iterations (warm-started), the vertex V = -B u v^T (or 0 when sigma_1 <= lam_L), the exact
+ * line search of the printed quadratic with S fixed (its lam_L term read as lam_L ((1 - eta) t
+ * + eta Vt)), L <- (1 - eta) L + eta V, t likewise, the radius bound B as printed.  Stops when
+ * the Frank-Wolfe gap <G, L - V> + lam_L (t - Vt) <= gap_tol max(1, |F|) or after max_iter
+ * iterations.  log (host, may be NULL): 4 doubles per iteration {F(L, t) before the step,
+ * gap, sigma_1, eta}.  float32 X only (no narrow storage).  Synchronous.
+ */
+typedef struct {
+  double F;        /* phi(L) + lam_L t at the returned iterate */
+  double t;        /* the nuclear-norm bound (>= ||L||_*) */
+  double gap;      /* Frank-Wolfe gap of the last iteration */
+  double sigma1;   /* top singular value of the last gradient */
+  int iters;       /* iterations taken */
+  double seconds;  /* wall time */
+} rpca_fw_result;
+RPCA_API rpca_status rpca_fw_solve(rpca_ctx *c, float *L, int64_t ldl, int max_iter, double gap_tol, int power_iters,
+                                   double *log, rpca_fw_result *res);
+
 /* ---- Learned warm start ---------------------------------------------------------------
  * An extension of this library (the paper compares SVD, randomized-SVD and random starts,
  * Sec. 4.2, and finds that the start matters).  A three-layer network (40 inputs, two hidden

@@ -42,6 +42,11 @@ class rpca_cert(C.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class rpca_fw_result(C.Structure):
+    _fields_ = [("F", C.c_double), ("t", C.c_double), ("gap", C.c_double), ("sigma1", C.c_double),
+                ("iters", C.c_int), ("seconds", C.c_double)]
+
+
 class rpca_result(C.Structure):
     _fields_ = [("F", C.c_double), ("iters", C.c_int), ("evals", C.c_int), ("cert_evals", C.c_int),
                 ("seconds", C.c_double), ("cert", rpca_cert), ("status", C.c_int), ("ms_init", C.c_double),
@@ -113,6 +118,8 @@ def lib():
     L.rpca_perp_direction.restype = I
     L.rpca_perp_directions.argtypes = [P, I, P, I64, P, I64, C.POINTER(C.c_double), C.POINTER(C.c_int)]
     L.rpca_perp_directions.restype = I
+    L.rpca_fw_solve.argtypes = [P, P, I64, I, D, I, C.POINTER(C.c_double), C.POINTER(rpca_fw_result)]
+    L.rpca_fw_solve.restype = I
     L.rpca_solve_grow.argtypes = [P, P, P, I, C.POINTER(rpca_result), C.POINTER(C.c_int)]
     L.rpca_solve_grow.restype = I
     FP = C.POINTER(C.c_float)
@@ -154,7 +161,7 @@ EXPORTED = ["rpca_default_options", "rpca_create", "rpca_fg", "rpca_apply", "rpc
             "rpca_ws_predict", "rpca_ws_train_step", "rpca_ws_last_error", "rpca_ws_destroy",
             "rpca_set_warm_start", "rpca_sketch_spectrum", "rpca_ws_sample", "rpca_gen_planted",
             "rpca_philox4x32_10", "rpca_perp_direction", "rpca_perp_directions",
-            "rpca_solve_grow"]
+            "rpca_solve_grow", "rpca_fw_solve"]
 
 
 class RpcaError(RuntimeError):
@@ -466,3 +473,13 @@ def rpca_perp_directions(ctx, qmax, U, ldu, V, ldv):
     q = C.c_int(0)
     _check(lib().rpca_perp_directions(ctx, qmax, _ptr(U), ldu, _ptr(V), ldv, sig, C.byref(q)), ctx)
     return list(sig)[:q.value]
+
+
+def rpca_fw_solve(ctx, L, ldl, max_iter, gap_tol=0.0, power_iters=2, want_log=True):
+    """Frank-Wolfe with marginalization on the dense device iterate L (torch (n, ldl)).
+    Returns (rpca_fw_result, log rows [F, gap, sigma_1, eta] or None)."""
+    r = rpca_fw_result()
+    log = (C.c_double * (4 * max(1, max_iter)))() if want_log else None
+    _check(lib().rpca_fw_solve(ctx, _ptr(L), ldl, max_iter, gap_tol, power_iters, log, C.byref(r)), ctx)
+    rows = [list(log[4 * i:4 * i + 4]) for i in range(r.iters)] if want_log else None
+    return r, rows
