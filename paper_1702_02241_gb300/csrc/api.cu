@@ -447,6 +447,7 @@ const FgPlan* apply_plan(rpca_ctx* c, int K, int side) {
 }
 
 rpca_status launch_fg(rpca_ctx* c, const FgPlan& P, const FgLaunch& L, cudaStream_t stream) {
+  if (P.large) return launch_fg_large(c, P, L, stream);
   FgArgs a;
   a.m = c->m;
   a.n = c->n;
@@ -650,7 +651,7 @@ rpca_status create_ctx(rpca_ctx** out, int64_t m, int64_t n, const float* X, int
     return set_err(nullptr, RPCA_EINVAL, "X must be 16-byte aligned with ldx a multiple of 4");
   if (mask && ldmask < m) return set_err(nullptr, RPCA_EINVAL, "ldmask < m");
   if (k < 1 || k > std::min<int64_t>(m, n)) return set_err(nullptr, RPCA_EINVAL, "k must be in [1, min(m, n)]");
-  if (k > 16) return set_err(nullptr, RPCA_EUNSUPPORTED, "k > 16 is not compiled in this build");
+  if (k > 256) return set_err(nullptr, RPCA_EUNSUPPORTED, "k must be at most 256");
   if (!(lambda_L > 0) || !std::isfinite(lambda_L)) return set_err(nullptr, RPCA_EINVAL, "lambda_L must be finite and > 0");
   if (!(lambda_S > 0)) return set_err(nullptr, RPCA_EINVAL, "lambda_S must be > 0 (+inf allowed)");
   rpca_options o;
@@ -722,9 +723,14 @@ rpca_status create_ctx(rpca_ctx** out, int64_t m, int64_t n, const float* X, int
                                                                                 c->bits);
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(cuda_err(c, e, "pack_mask_kernel"));
   }
-  rpca_status s = make_plan(c, &c->fg_plan, k, k, true, 0);
-  if (s != RPCA_OK) return fail(s);
-  if ((s = size_workspace(c, c->fg_plan)) != RPCA_OK) return fail(s);
+  rpca_status s;
+  if (k > 16) {
+    // Above the fused kernel's ranks: GEMMs and an elementwise pass (largek.cu).
+    if ((s = lk_setup(c)) != RPCA_OK) return fail(s);
+  } else {
+    if ((s = make_plan(c, &c->fg_plan, k, k, true, 0)) != RPCA_OK) return fail(s);
+    if ((s = size_workspace(c, c->fg_plan)) != RPCA_OK) return fail(s);
+  }
   if (o.x_dtype != RPCA_F32) {
     // Both objective/gradient plans share one workspace (captured by the solver's graph):
     // size it for both before any capture.
@@ -826,6 +832,7 @@ void rpca_destroy(rpca_ctx* c) {
   for (rpca_ctx* g : c->grown)
     if (g) rpca_destroy(g);
   c->grown.clear();
+  lk_free(c);
   cudaStreamSynchronize(c->stream);
   free_solver(c);
   free_cert(c);

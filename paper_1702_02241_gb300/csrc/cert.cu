@@ -793,6 +793,7 @@ using namespace rpca;
 
 extern "C" rpca_status rpca_certificate(rpca_ctx* c, const float* U, const float* V, rpca_cert* out) {
   if (!c) return RPCA_EINVAL;
+  if (c->lk) return set_err(c, RPCA_EUNSUPPORTED, "the certificate is built for k <= 16");
   if (!U || !V || !out) return set_err(c, RPCA_EINVAL, "U, V and out are required");
   return cert_compute(c, U, V, out, true);
 }

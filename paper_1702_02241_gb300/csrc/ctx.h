@@ -27,6 +27,7 @@ struct FgPlan {
   int cps = 0;  // CTAs per SM at this configuration
   int nstage = 3;
   int xt = 0;       // storage type of X read by this plan (FG_X_*)
+  bool large = false;  // k > 16: GEMMs + elementwise pass (largek.cu) instead of the fused kernel
   CUtensorMap tmX;  // box {32 R rows, FG_BJ columns}
   CUtensorMap tmM;  // bitmap box {WC * R words, FG_BJ columns}
 };
@@ -47,6 +48,7 @@ struct Workspace {
 
 struct SolverBuffers;  // solver.cu
 struct CertBuffers;    // cert.cu
+struct LargeK;         // largek.cu
 
 }  // namespace rpca
 
@@ -81,6 +83,7 @@ struct rpca_ctx {
   rpca::Workspace ws_ap;       // partial sums of the apply plans
   rpca::SolverBuffers* sol = nullptr;
   rpca::CertBuffers* cert = nullptr;
+  rpca::LargeK* lk = nullptr;  // k > 16 (largek.cu)
   // Learned warm start: the model (not owned) and the last sketch's singular values.
   const rpca_ws* ws_model = nullptr;
   float* sk_sigma = nullptr;  // 32 floats on the device, owned
@@ -142,6 +145,9 @@ rpca_status launch_fg(rpca_ctx* c, const FgPlan& P, const FgLaunch& L, cudaStrea
 const FgPlan* apply_plan(rpca_ctx* c, int K, int side);  // forming rank >= K (0, 8 or 16), side
 rpca_status make_xq(rpca_ctx* c, int xt);                // narrow copy of X (xq.cu)
 rpca_status ws_learned_init(rpca_ctx* c, float* U, float* V, int* used);  // ws.cu
+rpca_status lk_setup(rpca_ctx* c);                                           // largek.cu
+void lk_free(rpca_ctx* c);
+rpca_status launch_fg_large(rpca_ctx* c, const FgPlan& P, const FgLaunch& L, cudaStream_t stream);
 rpca_status create_ctx(rpca_ctx** out, int64_t m, int64_t n, const float* X, int64_t ldx, const uint8_t* mask,
                        int64_t ldmask, int k, double lambda_L, double lambda_S, const rpca_options* opt,
                        void* cuda_stream, int grid_cap);  // api.cu

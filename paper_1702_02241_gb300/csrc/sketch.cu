@@ -158,7 +158,10 @@ static rpca_status sk_orth(rpca_ctx* c, SketchBuffers& b, float* Y, int64_t rows
   return RPCA_OK;
 }
 
+rpca_status sketch_init_large(rpca_ctx* c, const float* Omega, float* U, float* V);  // largek.cu
+
 rpca_status sketch_init(rpca_ctx* c, const float* Omega, float* U, float* V) {
+  if (c->lk) return sketch_init_large(c, Omega, U, V);  // k > 16: sketches wider than 32
   const int k = c->k;
   const int l = std::min(std::min(k + std::max(0, c->opt.sketch_oversample), SK_LMAX), std::min(c->m, c->n));
   const int q = std::max(0, c->opt.sketch_power);

@@ -896,6 +896,8 @@ static rpca_status ensure_solver(rpca_ctx* c) {
   // line-search trial), for per-kernel profilers that do not see inside conditional graphs.
   if (const char* e = getenv("RPCA_SOLVER_GRAPH"))
     if (e[0] == '0') return RPCA_OK;
+  // Ranks above the fused kernel's call cuBLAS in their objective pass: host loop as well.
+  if (c->lk) return RPCA_OK;
 
   // Capture one iteration: WHILE(line search) { fg, finalize, ls_step }, update, direction.
   SolverArgs a = solver_args(c);

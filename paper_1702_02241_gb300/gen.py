@@ -219,6 +219,25 @@ def batch_c4(count: int = 256, seed: int = 0, m_range=(1024, 20000), n_range=(50
     return out
 
 
+def synthetic_sec53(seed: int = 0, m: int = 1000, n: int = 1000, rank: int = 150, p_sparse: float = 0.5,
+                    rel_noise: float = 8.12e-5, k: int = 200) -> Instance:
+    """The synthetic problem of Sec. 5.3: L = A B^T with A (m x rank), B (n x rank) iid N(0, 1);
+    S with N(0, 1) entries on a Bernoulli(p_sparse) set (50 %), zero elsewhere; X = L + S + N with
+    white Gaussian N scaled so that ||L + S - X||_F / ||X||_F = rel_noise (8.12e-5); k = 200,
+    lam_L = 2.95, lam_S = 0.1."""
+    g = rng(seed)
+    A = g.normal(size=(m, rank))
+    B = g.normal(size=(n, rank))
+    L0 = A @ B.T
+    S0 = np.where(g.random((m, n)) < p_sparse, g.normal(size=(m, n)), 0.0)
+    N = g.normal(size=(m, n))
+    Y = L0 + S0
+    # ||N_s|| / ||Y + N_s|| = rel  ->  ||N_s|| ~= rel ||Y|| / sqrt(1 - rel^2) (N nearly orthogonal to Y)
+    N *= rel_noise * np.linalg.norm(Y) / math.sqrt(1.0 - rel_noise ** 2) / np.linalg.norm(N)
+    X = np.asfortranarray((Y + N).astype(np.float32))
+    return Instance(X=X, mask=None, k=k, lam_L=2.95, lam_S=0.1, L0=L0, S0=S0, name=f"sec53_{m}x{n}r{rank}")
+
+
 # ---- Counter-based generator (Philox4x32-10, Salmon et al., SC 2011) -------------------------
 # The same stream the library's device generator draws (rpca_gen_planted); used by tests to
 # check that generator and by anything that needs an instance's values on the host.

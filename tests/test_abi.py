@@ -64,8 +64,8 @@ def test_create_rejects_bad_arguments_without_a_gpu(lib):
             rpca.rpca_create(cs["m"], cs["n"], cs["X"], cs["ldx"], None, 0, cs["k"], cs["lam_L"], cs["lam_S"])
         assert ei.value.status == rpca.RPCA_EINVAL, cs
         assert rpca.rpca_last_error(None)
-    with pytest.raises(rpca.RpcaError) as ei:
-        rpca.rpca_create(64, 64, 16, 64, None, 0, 17, 1.0, 1.0)
+    with pytest.raises(rpca.RpcaError) as ei:  # factor ranks above 256 are not built
+        rpca.rpca_create(512, 512, 16, 512, None, 0, 257, 1.0, 1.0)
     assert ei.value.status == rpca.RPCA_EUNSUPPORTED
 
 
