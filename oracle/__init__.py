@@ -24,6 +24,7 @@ Modules and the passages they follow:
                      from the formats' definitions, for the precision form of the objective pass.
 * ``frank_wolfe`` -- the Frank-Wolfe method with marginalization (Sec. 6.2, Algorithm 1): the
                      linear subproblem's top singular pair, the closed-form step, the gap.
+* ``aicc``        -- the corrected Akaike information criterion of a solution (Sec. 5.2).
 * ``warm_start``  -- the learned warm start (an extension: the paper compares SVD, rSVD and
                      random starts, Sec. 4.2): spectrum features of the sketch, the three-layer
                      network with bfloat16 weights, its gradient, Adam, the targets w*.
