@@ -347,6 +347,28 @@ typedef struct {
 RPCA_API rpca_status rpca_fw_solve(rpca_ctx *c, float *L, int64_t ldl, int max_iter, double gap_tol, int power_iters,
                                    double *log, rpca_fw_result *res);
 
+/*
+ * Corrected Akaike information criterion of the solution L = U V^T (Sec. 5.2), the paper's
+ * model-quality measure: S = shrink(X - L, lam_S) on the observed set, Z = L + S - X,
+ * sigma^2 = ||X||^2 / N, b = ||S||_1 / N, b_* = ||L||_* / rank(L) (N = observed entries),
+ * ell = -(N/2) log(2 pi sigma^2) - ||Z||^2/(2 sigma^2) - N log(2b) - ||S||_1/(2b)
+ *       - rank(L) log(2 b_*) - ||L||_* / (2 b_*),
+ * p = r (m + n - r) + nnz(S) + (||Z||^2 / ||X||^2) N, AIC_c = 2 (p - ell) + 2 p (p + 1) / (N - p - 1);
+ * rank(L) counts singular values above 1e-6 of the largest.  U, V: device factors (k columns).
+ * float32 X only.  Synchronous.
+ */
+typedef struct {
+  double aicc, loglik, dof;
+  int rank;         /* rank of L */
+  double nuclear;   /* ||L||_* */
+  double s_l1;      /* ||S||_1 */
+  int64_t nnz_s;    /* nonzeros of S */
+  double resid2;    /* ||Z||_F^2 */
+  double x2;        /* ||X||_F^2 over the observed entries */
+  int64_t count;    /* observed entries */
+} rpca_aicc_result;
+RPCA_API rpca_status rpca_aicc(rpca_ctx *c, const float *U, const float *V, rpca_aicc_result *out);
+
 /* ---- Learned warm start ---------------------------------------------------------------
  * An extension of this library (the paper compares SVD, randomized-SVD and random starts,
  * Sec. 4.2, and finds that the start matters).  A three-layer network (40 inputs, two hidden

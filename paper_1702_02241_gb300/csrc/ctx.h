@@ -148,6 +148,7 @@ rpca_status ws_learned_init(rpca_ctx* c, float* U, float* V, int* used);  // ws.
 rpca_status lk_setup(rpca_ctx* c);                                           // largek.cu
 void lk_free(rpca_ctx* c);
 rpca_status launch_fg_large(rpca_ctx* c, const FgPlan& P, const FgLaunch& L, cudaStream_t stream);
+rpca_status lk_product(rpca_ctx* c, const float* U, const float* V, const float** Lp, int64_t* ldl);
 rpca_status create_ctx(rpca_ctx** out, int64_t m, int64_t n, const float* X, int64_t ldx, const uint8_t* mask,
                        int64_t ldmask, int k, double lambda_L, double lambda_S, const rpca_options* opt,
                        void* cuda_stream, int grid_cap);  // api.cu

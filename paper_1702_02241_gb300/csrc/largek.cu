@@ -135,6 +135,21 @@ void lk_free(rpca_ctx* c) {
   c->lk = nullptr;
 }
 
+// L = U V^T into the context's m x n buffer (ld mpad); *Lp, *ldl receive it.
+rpca_status lk_product(rpca_ctx* c, const float* U, const float* V, const float** Lp, int64_t* ldl) {
+  LargeK* lk = c->lk;
+  if (!lk) return set_err(c, RPCA_EINVAL, "no large-rank state on this context");
+  rpca_status s;
+  if ((s = lk_cublas(c, cublasSetStream(lk->h, c->stream), "cublasSetStream")) != RPCA_OK) return s;
+  if ((s = lk_cublas(c, lk_gemm(lk, CUBLAS_OP_N, CUBLAS_OP_T, c->m, c->n, c->k, 1.f, U, c->m, V, c->n, 0.f, lk->R,
+                                c->mpad),
+                     "GEMM U V^T")) != RPCA_OK)
+    return s;
+  *Lp = lk->R;
+  *ldl = c->mpad;
+  return RPCA_OK;
+}
+
 rpca_status launch_fg_large(rpca_ctx* c, const FgPlan& P, const FgLaunch& L, cudaStream_t stream) {
   LargeK* lk = c->lk;
   if (!lk) return set_err(c, RPCA_EINVAL, "no large-rank state on this context");

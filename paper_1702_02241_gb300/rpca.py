@@ -47,6 +47,15 @@ class rpca_fw_result(C.Structure):
                 ("iters", C.c_int), ("seconds", C.c_double)]
 
 
+class rpca_aicc_result(C.Structure):
+    _fields_ = [("aicc", C.c_double), ("loglik", C.c_double), ("dof", C.c_double), ("rank", C.c_int),
+                ("nuclear", C.c_double), ("s_l1", C.c_double), ("nnz_s", C.c_int64), ("resid2", C.c_double),
+                ("x2", C.c_double), ("count", C.c_int64)]
+
+    def asdict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class rpca_result(C.Structure):
     _fields_ = [("F", C.c_double), ("iters", C.c_int), ("evals", C.c_int), ("cert_evals", C.c_int),
                 ("seconds", C.c_double), ("cert", rpca_cert), ("status", C.c_int), ("ms_init", C.c_double),
@@ -118,6 +127,8 @@ def lib():
     L.rpca_perp_direction.restype = I
     L.rpca_perp_directions.argtypes = [P, I, P, I64, P, I64, C.POINTER(C.c_double), C.POINTER(C.c_int)]
     L.rpca_perp_directions.restype = I
+    L.rpca_aicc.argtypes = [P, P, P, C.POINTER(rpca_aicc_result)]
+    L.rpca_aicc.restype = I
     L.rpca_fw_solve.argtypes = [P, P, I64, I, D, I, C.POINTER(C.c_double), C.POINTER(rpca_fw_result)]
     L.rpca_fw_solve.restype = I
     L.rpca_solve_grow.argtypes = [P, P, P, I, C.POINTER(rpca_result), C.POINTER(C.c_int)]
@@ -161,7 +172,7 @@ EXPORTED = ["rpca_default_options", "rpca_create", "rpca_fg", "rpca_apply", "rpc
             "rpca_ws_predict", "rpca_ws_train_step", "rpca_ws_last_error", "rpca_ws_destroy",
             "rpca_set_warm_start", "rpca_sketch_spectrum", "rpca_ws_sample", "rpca_gen_planted",
             "rpca_philox4x32_10", "rpca_perp_direction", "rpca_perp_directions",
-            "rpca_solve_grow", "rpca_fw_solve"]
+            "rpca_solve_grow", "rpca_fw_solve", "rpca_aicc"]
 
 
 class RpcaError(RuntimeError):
@@ -483,3 +494,10 @@ def rpca_fw_solve(ctx, L, ldl, max_iter, gap_tol=0.0, power_iters=2, want_log=Tr
     _check(lib().rpca_fw_solve(ctx, _ptr(L), ldl, max_iter, gap_tol, power_iters, log, C.byref(r)), ctx)
     rows = [list(log[4 * i:4 * i + 4]) for i in range(r.iters)] if want_log else None
     return r, rows
+
+
+def rpca_aicc(ctx, U, V):
+    """AIC_c of the solution (U, V) (device factors); returns an rpca_aicc_result."""
+    r = rpca_aicc_result()
+    _check(lib().rpca_aicc(ctx, _ptr(U), _ptr(V), C.byref(r)), ctx)
+    return r
