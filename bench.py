@@ -491,7 +491,8 @@ def run_batch(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": BATCH_WORKLOAD.format(count=len(specs)), "count": len(specs),
                    "l2": "inputs larger than L2 (3.5 GB of X)", "parallelism": "replicas" if world > 1 else "1 GPU",
-                   "cert_every": 25, "host_threads": os.environ.get("RPCA_BATCH_THREADS", "auto")},
+                   "cert_every": 25, "host_threads": os.environ.get("RPCA_BATCH_THREADS", "auto"),
+                   "cuda_device_max_connections": os.environ.get("CUDA_DEVICE_MAX_CONNECTIONS")},
         "valid": bool(ok),
         "metrics": {"instances_certified": sum(r.status == rpca.RPCA_OK for r in res),
                     "evals": sum(r.evals for r in res), "iters": sum(r.iters for r in res),
@@ -517,6 +518,10 @@ def run_batch(args):
 
 def main():
     args = parse_args()
+    if args.workload == "batch":
+        # Many instances on their own streams: more hardware work queues than the default 8
+        # (read when CUDA initialises, so before torch touches the GPU).
+        os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch":

@@ -173,6 +173,35 @@ def evaluate(w, specs, seed, starts=("sketch", "learned", "random")):
     return res
 
 
+def evaluate_batch(w, specs, seed, reps=2):
+    """The held-out instances solved as one batch (rpca_solve_batch), from the sketch starts and
+    from the learned starts: wall time per batch (best of reps), iterations, certified count."""
+    Xs, lds = zip(*[generate(s, seed, i) for i, s in enumerate(specs)])
+    lams = [lambdas(s["m"], s["n"]) for s in specs]
+    out = {}
+    for name, kind in (("sketch", rpca.RPCA_INIT_SKETCH), ("learned", rpca.RPCA_INIT_LEARNED)):
+        b = rpca.rpca_create_batch(list(Xs), [(s["m"], ld) for s, ld in zip(specs, lds)], [s["k"] for s in specs],
+                                   [l[0] for l in lams], [l[1] for l in lams], _opts(kind))
+        if kind == rpca.RPCA_INIT_LEARNED:
+            for i in range(len(specs)):
+                rpca.rpca_set_warm_start(rpca.rpca_batch_context(b, i), w)
+        best = None
+        for _ in range(reps):
+            Us, Vs = zip(*[_factors(s["m"], s["n"], s["k"]) for s in specs])
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st, res = rpca.rpca_solve_batch(b, list(Us), list(Vs))
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            if best is None or dt < best[0]:
+                best = (dt, sum(r.iters for r in res), sum(r.status == rpca.RPCA_OK for r in res),
+                        sum(r.init_used == rpca.RPCA_INIT_LEARNED for r in res))
+        out[name] = {"batch_seconds": best[0], "iters": best[1], "certified": best[2], "learned_start_kept": best[3],
+                     "count": len(specs)}
+        rpca.rpca_destroy_batch(b)
+    return out
+
+
 def summary(res):
     out = {}
     for st, d in res.items():
@@ -192,22 +221,34 @@ def main(argv=None):
     ap.add_argument("--seed", type=int, default=20170207)
     ap.add_argument("--out", default=PARAMS_PATH)
     ap.add_argument("--json", default=None)
+    ap.add_argument("--load", action="store_true", help="evaluate the saved parameters instead of training")
+    ap.add_argument("--batch-eval", type=int, default=0,
+                    help="also solve this many held-out instances as one batch, sketch vs learned starts")
     a = ap.parse_args(argv)
     log = lambda s: print(s, flush=True)  # noqa: E731
-    t0 = time.time()
-    specs = instance_params(a.train, a.seed)
-    x, t, K, it_train = make_samples(specs, a.seed)
-    log(f"training set: {a.train} instances in {time.time() - t0:.1f} s, mean sketch iterations {np.mean(it_train):.1f}")
-    t1 = time.time()
-    w, losses = train(x, t, K, epochs=a.epochs, seed=a.seed, log=log)
-    log(f"training: {time.time() - t1:.1f} s")
-    th, _ = rpca.rpca_ws_get_params(w)
-    np.save(a.out, th)
+    losses = []
+    if a.load:
+        w = rpca.rpca_ws_create(np.load(a.out))
+    else:
+        t0 = time.time()
+        specs = instance_params(a.train, a.seed)
+        x, t, K, it_train = make_samples(specs, a.seed)
+        log(f"training set: {a.train} instances in {time.time() - t0:.1f} s, "
+            f"mean sketch iterations {np.mean(it_train):.1f}")
+        t1 = time.time()
+        w, losses = train(x, t, K, epochs=a.epochs, seed=a.seed, log=log)
+        log(f"training: {time.time() - t1:.1f} s")
+        th, _ = rpca.rpca_ws_get_params(w)
+        np.save(a.out, th)
     held = instance_params(a.heldout, a.seed + 1)
     res = summary(evaluate(w, held, a.seed + 1))
     log("held-out 4096x256: " + json.dumps(res))
     out = {"train": a.train, "epochs": a.epochs, "final_loss": losses[-1][1] if losses else None,
            "heldout_4096x256": res}
+    if a.batch_eval:
+        rb = evaluate_batch(w, instance_params(a.batch_eval, a.seed + 2), a.seed + 2)
+        log(f"held-out batch of {a.batch_eval}: " + json.dumps(rb))
+        out["heldout_batch"] = rb
     if a.video:
         vids = []
         for i in range(a.video):
