@@ -416,3 +416,19 @@ def test_grow_column_adds_nothing_at_a_solution():
     U2, V2, s1 = ocert.grow_column(X, np.ones(X.shape, np.uint8), Ub, Vb, 1.0, np.inf)
     assert s1 <= 1.0 + 1e-9
     assert np.all(U2[:, 3] == 0) and np.all(V2[:, 3] == 0)
+
+
+def test_grow_columns_decrease_by_the_summed_bound():
+    """Several columns at once: F drops by at least sum_i (sigma_i - lam_L)^2 / 2 (orthonormal
+    pairs), and every added sigma_i exceeds lam_L."""
+    g = np.random.default_rng(13)
+    m, n = 70, 50
+    X = g.normal(size=(m, 6)) @ g.normal(size=(6, n)) * 1.5 + 0.05 * g.normal(size=(m, n))
+    lam_L, lam_S = 1.0, 0.4
+    U0, V0 = gen.factors(m, n, 2, seed=4, scale=0.5)
+    r = lbfgs.solve(X, None, U0, V0, lam_L, lam_S, gtol=1e-11, max_iter=4000)
+    F0 = core.objective(X, None, r.U, r.V, lam_L, lam_S)
+    U2, V2, ss = ocert.grow_columns(X, None, r.U, r.V, lam_L, lam_S, 10)
+    assert ss.size >= 2 and np.all(ss > lam_L)
+    F1 = core.objective(X, None, U2, V2, lam_L, lam_S)
+    assert F1 <= F0 - 0.5 * np.sum((ss - lam_L) ** 2) + 1e-9 * abs(F0)
