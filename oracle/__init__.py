@@ -18,7 +18,10 @@ Modules and the passages they follow:
                      QR + small-SVD route of its footnote, the distance bound F_bound).
 * ``convex``      -- proximal gradient / FISTA with singular-value thresholding on Eq. (4)
                      (Sec. 1 notes proximal methods apply but need an SVD): reference solutions
-                     on tiny instances.
+                     on tiny instances; and the convex baseline of Sec. 6.1, the same iteration
+                     with the thresholding done through a TSQR-based randomized SVD.
+* ``tsqr``        -- TSQR, the QR of a tall-skinny matrix by a reduction tree of small QRs
+                     (Sec. 6.1), normalised to a non-negative diagonal of R.
 * ``sketch``      -- randomized-SVD initialisation U0 = U_k S^1/2, V0 = V_k S^1/2 (Sec. 4.2).
 * ``quant``       -- the values X takes when stored as bfloat16 or FP8 E4M3 (per-column scale),
                      from the formats' definitions, for the precision form of the objective pass.
