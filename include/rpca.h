@@ -348,6 +348,52 @@ RPCA_API rpca_status rpca_fw_solve(rpca_ctx *c, float *L, int64_t ldl, int max_i
                                    double *log, rpca_fw_result *res);
 
 /*
+ * TSQR (Sec. 6.1, after Demmel, Grigori, Hoemmen and Langou 2012): A = Q R for a tall-skinny
+ * device matrix A (rows x l, float32, column-major, ld lda >= rows; 1 <= l <= 32, rows >= l),
+ * by a reduction tree of float32 Householder QRs (row blocks first, then groups of stacked R's).
+ * Q: device rows x l (column-major, ld ldq >= rows) with orthonormal columns; R: device l x l
+ * (column-major, may be NULL), upper triangular with a non-negative diagonal (the unique QR of a
+ * full-rank A).  A rank-deficient A still gives an orthonormal Q with Q R = A.  Scratch is
+ * allocated and freed on c's stream.  Synchronous.  RPCA_EINVAL on bad sizes.
+ */
+RPCA_API rpca_status rpca_tsqr(rpca_ctx *c, const float *A, int64_t lda, int64_t rows, int l, float *Q, int64_t ldq,
+                               float *R);
+
+/*
+ * The convex baseline of Sec. 6.1: FISTA (unit step) on the Lagrangian program
+ * min_L lam_L ||L||_* + phi(L) (S marginalised), whose singular-value thresholding is taken on a
+ * rank-l randomized SVD of the gradient point Z = Y - P_Omega clip(Y - X) with power_iters power
+ * iterations and every QR a TSQR (rpca_tsqr's algorithm); the test matrix of each iteration is
+ * the right singular basis found by the previous one (Omega0 for the first).  Iteration k:
+ * Y = L_k + beta_k (L_k - L_{k-1}) (beta_0 = 0, beta_k = (t_{k-1} - 1) / t_k, t_0 = 1,
+ * t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2), L_{k+1} = left diag(max(s - lam_L, 0)) right^T.
+ * L: device m x n float32 (column-major, ld ldl >= m a multiple of 4, 16-byte aligned); the
+ * solve starts from L = 0 and returns the last iterate L_k in it.  l: the sketch width, 1 <= l
+ * <= min(32, m, n); the prox is exact while fewer than l singular values of Z exceed lam_L
+ * (res->truncated reports the last one that was not).  Omega0: device n x l float32
+ * (column-major, ld n), e.g. standard normal.  Stops at the first k >= 1 with
+ * ||L_k - L_{k-1}||_F <= tol max(1, ||L_k||_F), or at k = max_iter.  profile != 0 times the
+ * phases with CUDA events.  log (host, may be NULL): 4 doubles per iterate k = 0 .. iters
+ * {F(L_k) = lam_L ||L_k||_* + phi(L_k), the relative change, rank L_k, the l-th sketch singular
+ * value that formed L_k}.  float32 X only.  Synchronous.
+ */
+typedef struct {
+  double F;           /* lam_L ||L||_* + phi(L) at the returned iterate */
+  double phi;         /* phi(L) */
+  double nuclear;     /* ||L||_* (the thresholded singular values that formed L) */
+  double rel_change;  /* ||L_k - L_{k-1}||_F / max(1, ||L_k||_F) */
+  int iters;          /* prox steps taken (the returned iterate is L_iters) */
+  int rank;           /* rank of the returned L */
+  int truncated;      /* 1 if the last prox kept all l sketch directions (l may be too small) */
+  double seconds;     /* wall time */
+  double ms_pass, ms_rsvd, ms_tsqr, ms_recon; /* device time of the phases (profile), else 0;
+                                                 ms_tsqr is part of ms_rsvd */
+} rpca_convex_result;
+RPCA_API rpca_status rpca_convex_solve(rpca_ctx *c, float *L, int64_t ldl, int l, int power_iters,
+                                       const float *Omega0, int max_iter, double tol, int profile, double *log,
+                                       rpca_convex_result *res);
+
+/*
  * Corrected Akaike information criterion of the solution L = U V^T (Sec. 5.2), the paper's
  * model-quality measure: S = shrink(X - L, lam_S) on the observed set, Z = L + S - X,
  * sigma^2 = ||X||^2 / N, b = ||S||_1 / N, b_* = ||L||_* / rank(L) (N = observed entries),

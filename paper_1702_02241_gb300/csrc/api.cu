@@ -834,6 +834,7 @@ void rpca_destroy(rpca_ctx* c) {
   c->grown.clear();
   lk_free(c);
   cudaStreamSynchronize(c->stream);
+  cvx_free(c);
   free_solver(c);
   free_cert(c);
   cudaFree(c->bits);

@@ -49,6 +49,7 @@ struct Workspace {
 struct SolverBuffers;  // solver.cu
 struct CertBuffers;    // cert.cu
 struct LargeK;         // largek.cu
+struct ConvexBuffers;  // convex.cu
 
 }  // namespace rpca
 
@@ -84,6 +85,7 @@ struct rpca_ctx {
   rpca::SolverBuffers* sol = nullptr;
   rpca::CertBuffers* cert = nullptr;
   rpca::LargeK* lk = nullptr;  // k > 16 (largek.cu)
+  rpca::ConvexBuffers* cvx = nullptr;  // the convex baseline's scratch (convex.cu), made on first use
   // Learned warm start: the model (not owned) and the last sketch's singular values.
   const rpca_ws* ws_model = nullptr;
   float* sk_sigma = nullptr;  // 32 floats on the device, owned
@@ -147,6 +149,7 @@ rpca_status make_xq(rpca_ctx* c, int xt);                // narrow copy of X (xq
 rpca_status ws_learned_init(rpca_ctx* c, float* U, float* V, int* used);  // ws.cu
 rpca_status lk_setup(rpca_ctx* c);                                           // largek.cu
 void lk_free(rpca_ctx* c);
+void cvx_free(rpca_ctx* c);  // convex.cu
 rpca_status launch_fg_large(rpca_ctx* c, const FgPlan& P, const FgLaunch& L, cudaStream_t stream);
 rpca_status lk_product(rpca_ctx* c, const float* U, const float* V, const float** Lp, int64_t* ldl);
 rpca_status create_ctx(rpca_ctx** out, int64_t m, int64_t n, const float* X, int64_t ldx, const uint8_t* mask,

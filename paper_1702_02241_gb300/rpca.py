@@ -47,6 +47,16 @@ class rpca_fw_result(C.Structure):
                 ("iters", C.c_int), ("seconds", C.c_double)]
 
 
+class rpca_convex_result(C.Structure):
+    _fields_ = [("F", C.c_double), ("phi", C.c_double), ("nuclear", C.c_double), ("rel_change", C.c_double),
+                ("iters", C.c_int), ("rank", C.c_int), ("truncated", C.c_int), ("seconds", C.c_double),
+                ("ms_pass", C.c_double), ("ms_rsvd", C.c_double), ("ms_tsqr", C.c_double),
+                ("ms_recon", C.c_double)]
+
+    def asdict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class rpca_aicc_result(C.Structure):
     _fields_ = [("aicc", C.c_double), ("loglik", C.c_double), ("dof", C.c_double), ("rank", C.c_int),
                 ("nuclear", C.c_double), ("s_l1", C.c_double), ("nnz_s", C.c_int64), ("resid2", C.c_double),
@@ -131,6 +141,11 @@ def lib():
     L.rpca_aicc.restype = I
     L.rpca_fw_solve.argtypes = [P, P, I64, I, D, I, C.POINTER(C.c_double), C.POINTER(rpca_fw_result)]
     L.rpca_fw_solve.restype = I
+    L.rpca_tsqr.argtypes = [P, P, I64, I64, I, P, I64, P]
+    L.rpca_tsqr.restype = I
+    L.rpca_convex_solve.argtypes = [P, P, I64, I, I, P, I, D, I, C.POINTER(C.c_double),
+                                    C.POINTER(rpca_convex_result)]
+    L.rpca_convex_solve.restype = I
     L.rpca_solve_grow.argtypes = [P, P, P, I, C.POINTER(rpca_result), C.POINTER(C.c_int)]
     L.rpca_solve_grow.restype = I
     FP = C.POINTER(C.c_float)
@@ -172,7 +187,7 @@ EXPORTED = ["rpca_default_options", "rpca_create", "rpca_fg", "rpca_apply", "rpc
             "rpca_ws_predict", "rpca_ws_train_step", "rpca_ws_last_error", "rpca_ws_destroy",
             "rpca_set_warm_start", "rpca_sketch_spectrum", "rpca_ws_sample", "rpca_gen_planted",
             "rpca_philox4x32_10", "rpca_perp_direction", "rpca_perp_directions",
-            "rpca_solve_grow", "rpca_fw_solve", "rpca_aicc"]
+            "rpca_solve_grow", "rpca_fw_solve", "rpca_aicc", "rpca_tsqr", "rpca_convex_solve"]
 
 
 class RpcaError(RuntimeError):
@@ -493,6 +508,22 @@ def rpca_fw_solve(ctx, L, ldl, max_iter, gap_tol=0.0, power_iters=2, want_log=Tr
     log = (C.c_double * (4 * max(1, max_iter)))() if want_log else None
     _check(lib().rpca_fw_solve(ctx, _ptr(L), ldl, max_iter, gap_tol, power_iters, log, C.byref(r)), ctx)
     rows = [list(log[4 * i:4 * i + 4]) for i in range(r.iters)] if want_log else None
+    return r, rows
+
+
+def rpca_tsqr(ctx, A, lda, rows, l, Q, ldq, R=None):
+    """TSQR of the device matrix A (rows x l) into Q (rows x l) and R (l x l, or None)."""
+    _check(lib().rpca_tsqr(ctx, _ptr(A), lda, rows, l, _ptr(Q), ldq, _ptr(R) if R is not None else None), ctx)
+
+
+def rpca_convex_solve(ctx, L, ldl, l, Omega0, max_iter, tol=0.0, power_iters=1, profile=False, want_log=True):
+    """The Sec. 6.1 convex baseline (FISTA with a TSQR-based rSVD prox) into the device iterate L.
+    Returns (rpca_convex_result, log rows [F, rel_change, rank, s_l] for k = 0..iters, or None)."""
+    r = rpca_convex_result()
+    log = (C.c_double * (4 * (max_iter + 1)))() if want_log else None
+    _check(lib().rpca_convex_solve(ctx, _ptr(L), ldl, l, power_iters, _ptr(Omega0), max_iter, tol,
+                                   1 if profile else 0, log, C.byref(r)), ctx)
+    rows = [list(log[4 * i:4 * i + 4]) for i in range(r.iters + 1)] if want_log else None
     return r, rows
 
 
