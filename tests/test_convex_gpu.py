@@ -130,9 +130,9 @@ def test_converges_to_the_certified_factored_optimum(mask_p):
     # Stop at a relative change of 1e-6: float32 iterates settle at a few 1e-7.
     r, log, Ld = _run(X, mask, lam_L, lam_S, 8, _omega(n, 8, 1), 2000, q=1, tol=1e-6)
     assert r.rel_change <= 1e-6 and r.truncated == 0
-    P = make_problem(X, mask, 6, lam_L, lam_S, init=rpca.RPCA_INIT_SKETCH, max_iter=5000, cert_tol=1e-5)
-    U = torch.zeros((6, m), dtype=torch.float32, device="cuda")
-    V = torch.zeros((6, n), dtype=torch.float32, device="cuda")
+    P = make_problem(X, mask, 4, lam_L, lam_S, init=rpca.RPCA_INIT_SKETCH, max_iter=5000, cert_tol=1e-4)
+    U = torch.zeros((4, m), dtype=torch.float32, device="cuda")
+    V = torch.zeros((4, n), dtype=torch.float32, device="cuda")
     res = P.solve(U, V)
     assert res.status == rpca.RPCA_OK
     F_star = res.F
