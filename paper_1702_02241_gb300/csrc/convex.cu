@@ -5,7 +5,7 @@
 //   pass   Z = Y - P_Omega clip(Y - X),  Y = L + beta (L - L_prev),  A = Z Omega      (fused;
 //          also phi(L), ||L - L_prev||^2, ||L||^2 for the objective and the stopping test)
 //   rSVD   Q = tsqr(A); q times {Q_w = tsqr(Z^T Q), Q = tsqr(Z Q_w)}; W = Z^T Q = Q_w R_w;
-//          R_w = U_r diag(s) V_r^T (one-CTA Jacobi)
+//          R_w = U_r diag(s) V_r^T (one-warp Jacobi)
 //   prox   L_new = (Q V_r diag(max(s - lam_L, 0))) (Q_w U_r)^T   (rank-l product pass)
 // and Omega for the next iteration = Q_w U_r (the right singular basis found).  Every pass over
 // an m x n array is a stream through HBM (4 rows per thread, 16-byte accesses); the sketch
@@ -211,12 +211,26 @@ __global__ void __launch_bounds__(CV_T) cv_left_kernel(const float* Z, int64_t l
   }
 }
 
-// W (n x l, column-major, ld n) = sum over nb blocks of Wpart (fixed order).
-__global__ void cv_wsum_kernel(const float* Wpart, int nb, int64_t nl, float* W) {
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nl; e += (int64_t)gridDim.x * blockDim.x) {
+// W (n x l, column-major, ld n) = sum over nb blocks of Wpart, in a fixed order: each block
+// takes 32 consecutive outputs, 8 threads per output sum every 8th partial, then the 8 sums
+// are added in order.
+__global__ void __launch_bounds__(256) cv_wsum_kernel(const float* Wpart, int nb, int64_t nl, float* W) {
+  __shared__ float part[8][32];
+  const int o = threadIdx.x & 31, g = threadIdx.x >> 5;
+  for (int64_t e0 = (int64_t)blockIdx.x * 32; e0 < nl; e0 += (int64_t)gridDim.x * 32) {
+    const int64_t e = e0 + o;
     float s = 0.f;
-    for (int b = 0; b < nb; ++b) s += Wpart[(size_t)b * nl + e];
-    W[e] = s;
+    if (e < nl)
+      for (int b = g; b < nb; b += 8) s += Wpart[(size_t)b * nl + e];
+    part[g][o] = s;
+    __syncthreads();
+    if (g == 0 && e < nl) {
+      float t = 0.f;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) t += part[q][o];
+      W[e] = t;
+    }
+    __syncthreads();
   }
 }
 
@@ -282,27 +296,26 @@ __global__ void __launch_bounds__(CV_T) cv_recon_kernel(const float* P, int64_t 
   }
 }
 
-// SVD of R_w (l x l) by one-sided Jacobi in T (float64 for l <= 16, float32 above), sorted
-// descending: Cl = V_r diag(s_thr) and Cr = U_r (both l x l, column-major), s_thr =
-// max(s - lam_L, 0); info = {sum s_thr, rank (s_thr > 0), s_1, s_l}.  One CTA.
-template <typename T>
-__global__ void __launch_bounds__(256) cv_small_svd_kernel(const float* Rw, int l, double lamL, float* Cl, float* Cr,
-                                                           double* sv, double* info) {
-  __shared__ T A[TQ_LMAX * TQ_LMAX], V[TQ_LMAX * TQ_LMAX], sig[TQ_LMAX];
-  __shared__ int ord[TQ_LMAX];
-  __shared__ int flag;
-  for (int e = threadIdx.x; e < l * l; e += blockDim.x) A[e] = (T)Rw[e];
-  __syncthreads();
-  const T eps = sizeof(T) == 8 ? T(1.1e-16) : T(6e-8);
-  cta_jacobi_svd<T>(A, l, l, l, V, l, sig, &flag, 60, T(8) * l * eps, T(4) * l * eps);
-  cta_sort_desc<T>(sig, l, ord);
-  for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
+// SVD of R_w (l x l) by one-sided Jacobi in float32 on one warp (lane j holds column j; no
+// barriers), sorted descending: Cl = V_r diag(s_thr) and Cr = U_r (both l x l, column-major),
+// s_thr = max(s - lam_L, 0); info = {sum s_thr, rank (s_thr > 0), s_1, s_l}.  One warp.
+template <int LP>
+__global__ void __launch_bounds__(32) cv_small_svd_kernel(const float* Rw, int l, double lamL, float* Cl, float* Cr,
+                                                          double* sv, double* info) {
+  __shared__ float A[LP * LP], V[LP * LP], sig[LP];
+  __shared__ int ord[LP];
+  for (int e = threadIdx.x; e < l * l; e += 32) A[e] = Rw[e];
+  __syncwarp();
+  const float eps = 6e-8f;
+  warp_jacobi_svd<float, LP, LP>(A, l, l, l, V, l, sig, 40, 8.f * l * eps, 4.f * l * eps);
+  cta_sort_desc<float>(sig, l, ord);
+  for (int e = threadIdx.x; e < l * l; e += 32) {
     const int a = e % l, o = e / l;
     const int c = ord[o];
-    const T s = sig[c];
-    const T st = s > (T)lamL ? s - (T)lamL : T(0);
-    Cl[e] = (float)(V[a + c * l] * st);
-    Cr[e] = s > T(0) ? (float)(A[a + c * l] / s) : 0.f;
+    const float s = sig[c];
+    const float st = (double)s > lamL ? (float)((double)s - lamL) : 0.f;
+    Cl[e] = V[a + c * l] * st;
+    Cr[e] = s > 0.f ? A[a + c * l] / s : 0.f;
   }
   if (threadIdx.x == 0) {
     double tot = 0.0;
@@ -345,7 +358,7 @@ void cv_launch_sketch(bool grad, dim3 g, cudaStream_t st, const float* L, const 
 
 // Scratch of the solver, kept on the context between solves of the same shape.
 struct ConvexBuffers {
-  int l = 0, LP = 0, gx = 0, gy = 0;
+  int l = 0, LP = 0, gx = 0, gy = 0, gyl = 0;  // gyl: column chunks of the Z^T Q pass
   int64_t ldl = 0, mp = 0;
   TsqrPlan pm, pn;
   float* buf = nullptr;
@@ -377,6 +390,7 @@ static rpca_status cvx_setup(rpca_ctx* c, int l, int64_t ldl) {
   b->mp = (m + 3) & ~(int64_t)3;
   b->gx = (int)((m + CV_ROWS - 1) / CV_ROWS);
   b->gy = (int)std::max<int64_t>(1, std::min<int64_t>({n, 16, (int64_t)(4 * c->nsm + b->gx - 1) / b->gx}));
+  b->gyl = b->gy;
   b->pm = tsqr_plan(m, l, c->nsm);
   b->pn = tsqr_plan(n, l, c->nsm);
   // Two more iterate buffers and Z (ldl x n each), A partials (gy x l x mp), Q and P (mp x l),
@@ -478,7 +492,7 @@ extern "C" rpca_status rpca_convex_solve(rpca_ctx* c, float* L, int64_t ldl, int
   const dim3 g2(gx, gy);
   const int mul_grid_m = (int)std::min<int64_t>(4 * c->nsm, (m + 255) / 256);
   const int mul_grid_n = (int)std::min<int64_t>(4 * c->nsm, (n + 255) / 256);
-  const int ws_grid = (int)std::min<int64_t>(4 * c->nsm, ((int64_t)n * l + 255) / 256);
+  const int ws_grid = (int)std::min<int64_t>(8 * c->nsm, ((int64_t)n * l + 31) / 32);
   auto sketch = [&](bool grad, const float* Lc, const float* Lpv, float beta, const float* Omx) {
     if (LP == 8)
       cv_launch_sketch<8>(grad, g2, st, Lc, Lpv, c->X, c->ldx, c->mask, c->ldmask, m, n, beta, lam, B.Z, ldl, Omx,
@@ -491,13 +505,14 @@ extern "C" rpca_status rpca_convex_solve(rpca_ctx* c, float* L, int64_t ldl, int
                            l, B.Ap, mp, part);
     count_launches(c, 1);
   };
+  const dim3 gl2(gx, B.gyl);
   auto left = [&](const float* Qm) {  // W = Z^T Q
     if (LP == 8)
-      cv_left_kernel<8><<<g2, CV_T, 0, st>>>(B.Z, ldl, m, n, Qm, mp, l, B.Wp);
+      cv_left_kernel<8><<<gl2, CV_T, 0, st>>>(B.Z, ldl, m, n, Qm, mp, l, B.Wp);
     else if (LP == 16)
-      cv_left_kernel<16><<<g2, CV_T, 0, st>>>(B.Z, ldl, m, n, Qm, mp, l, B.Wp);
+      cv_left_kernel<16><<<gl2, CV_T, 0, st>>>(B.Z, ldl, m, n, Qm, mp, l, B.Wp);
     else
-      cv_left_kernel<32><<<g2, CV_T, 0, st>>>(B.Z, ldl, m, n, Qm, mp, l, B.Wp);
+      cv_left_kernel<32><<<gl2, CV_T, 0, st>>>(B.Z, ldl, m, n, Qm, mp, l, B.Wp);
     cv_wsum_kernel<<<ws_grid, 256, 0, st>>>(B.Wp, gx, (int64_t)n * l, B.W);
     count_launches(c, 2);
   };
@@ -574,10 +589,12 @@ extern "C" rpca_status rpca_convex_solve(rpca_ctx* c, float* L, int64_t ldl, int
         e = tsqr(B.pn, B.W, n, 1, 0, B.Qw, n, false, B.Rw, B.Tn);
       }
       if (e == cudaSuccess) {
-        if (l <= 16)
-          cv_small_svd_kernel<double><<<1, 256, 0, st>>>(B.Rw, l, lamL, B.Cl, B.Cr, sv, info);
+        if (LP == 8)
+          cv_small_svd_kernel<8><<<1, 32, 0, st>>>(B.Rw, l, lamL, B.Cl, B.Cr, sv, info);
+        else if (LP == 16)
+          cv_small_svd_kernel<16><<<1, 32, 0, st>>>(B.Rw, l, lamL, B.Cl, B.Cr, sv, info);
         else
-          cv_small_svd_kernel<float><<<1, 256, 0, st>>>(B.Rw, l, lamL, B.Cl, B.Cr, sv, info);
+          cv_small_svd_kernel<32><<<1, 32, 0, st>>>(B.Rw, l, lamL, B.Cl, B.Cr, sv, info);
         count_launches(c, 1);
         // Prox: P = Q Cl, Omega <- Q_w Cr (the right basis: the next sketch's test matrix),
         // L_{k+1} = P Omega^T.

@@ -62,10 +62,19 @@ __device__ void tq_house_qr(float* A, int rows, int cols, int ld, float* tau, fl
       float* b = A + (size_t)cc * ld;
       const float bj = b[j];
       float d = 0.f;
-      for (int i = j + 1 + lane; i < rows; i += 32) d = fmaf(a[i], b[i], d);
+      float d1 = 0.f;
+      int i = j + 1 + lane;
+#pragma unroll 2
+      for (; i + 32 < rows; i += 64) {
+        d = fmaf(a[i], b[i], d);
+        d1 = fmaf(a[i + 32], b[i + 32], d1);
+      }
+      if (i < rows) d = fmaf(a[i], b[i], d);
+      d += d1;
       for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
       d = t * (d + bj);
-      for (int i = j + 1 + lane; i < rows; i += 32) b[i] = fmaf(-d, a[i], b[i]);
+#pragma unroll 4
+      for (int i2 = j + 1 + lane; i2 < rows; i2 += 32) b[i2] = fmaf(-d, a[i2], b[i2]);
       if (lane == 0) b[j] = bj - d;
     }
     if (threadIdx.x == 0) {
@@ -88,10 +97,19 @@ __device__ void tq_house_q(float* A, int rows, int cols, int ld, const float* ta
       float* b = A + (size_t)cc * ld;
       const float bj = b[j];
       float d = 0.f;
-      for (int i = j + 1 + lane; i < rows; i += 32) d = fmaf(a[i], b[i], d);
+      float d1 = 0.f;
+      int i = j + 1 + lane;
+#pragma unroll 2
+      for (; i + 32 < rows; i += 64) {
+        d = fmaf(a[i], b[i], d);
+        d1 = fmaf(a[i + 32], b[i + 32], d1);
+      }
+      if (i < rows) d = fmaf(a[i], b[i], d);
+      d += d1;
       for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
       d = t * (d + bj);
-      for (int i = j + 1 + lane; i < rows; i += 32) b[i] = fmaf(-d, a[i], b[i]);
+#pragma unroll 4
+      for (int i2 = j + 1 + lane; i2 < rows; i2 += 32) b[i2] = fmaf(-d, a[i2], b[i2]);
       if (lane == 0) b[j] = bj - d;
     }
     __syncthreads();
@@ -117,10 +135,14 @@ __global__ void __launch_bounds__(TQ_T) tq_leaf_kernel(const float* A, int64_t l
   const int64_t r0 = (int64_t)p * b;
   const int nb = (int)(p == P - 1 ? rows - r0 : b);
   float* S = tq_smem;
+  // Unrolled so that the loads of several elements and partials are in flight together (the
+  // partials are added in order).
+#pragma unroll 4
   for (int e = threadIdx.x; e < nb * l; e += blockDim.x) {
     const int i = e % nb, c = e / nb;
     const float* src = A + (r0 + i) + (int64_t)c * lda;
     float v = 0.f;
+#pragma unroll 4
     for (int t = 0; t < npart; ++t) v += src[(int64_t)t * pstride];
     S[e] = v;
   }
@@ -229,7 +251,6 @@ TsqrPlan tsqr_plan(int64_t rows, int l, int nsm) {
   const int64_t bmax = std::max<int64_t>(l, (TQ_SMEM_FLOATS / l + 1) / 2);
   int64_t b = std::max<int64_t>(32, (rows + 2 * (int64_t)nsm - 1) / (2 * (int64_t)nsm));
   b = std::max<int64_t>(l, std::min(b, bmax));
-  if (rows * l <= TQ_SMEM_FLOATS) b = rows;  // fits one CTA: a single leaf, no tree
   p.b = (int)b;
   p.P = (int)std::max<int64_t>(1, rows / b);
   p.G = std::max(2, std::min(32, TQ_SMEM_FLOATS / (l * l)));
