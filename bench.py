@@ -346,7 +346,7 @@ def run_ours(args):
         "config": {"workload": WORKLOAD, "m": m, "n": n, "k": k, "lam_L": inst.lam_L, "lam_S": inst.lam_S,
                    "init": "rsvd (p=10, q=2)", "lbfgs_mem": 10, "cert_every": 25,
                    "l2": "inputs larger than L2 (X is 307 MB)", "parallelism": "replicas" if world > 1 else "1 GPU",
-                   "plan": rpca.rpca_plan_info(P.ctx, 0)},
+                   "plan": {**rpca.rpca_plan_info(P.ctx, 0), **rpca.rpca_plan_kernel(P.ctx, 0)}},
         "valid": bool(ok),
         "metrics": {"time_to_certificate_s": t_solve, "fg_evals_per_s": evals_per_s,
                     "fg_kernel_ms": fg_kernel_ms, "finalize_ms": fin_ms, "fg_hbm_gbs": achieved,

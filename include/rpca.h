@@ -240,6 +240,20 @@ RPCA_API const char *rpca_last_error(const rpca_ctx *c);
 RPCA_API rpca_status rpca_plan_info(rpca_ctx *c, int which, int64_t *out);
 
 /*
+ * Which form of the fused objective/gradient pass a plan of c uses (which as for
+ * rpca_plan_info).  out[0] = 0: the CUDA-core kernel (every product on the fp32x2 FMA pipe);
+ * 1: the tensor-core kernel (R^T = X - V U^T and D^T U as warp-level tf32 MMAs with a
+ * three-term hi / lo split of every operand, D V on the FMA pipe; float32 X, fg mode,
+ * k <= 8, no mask); 2: factor ranks above 16 (GEMMs around an elementwise pass).  out[1] =
+ * row passes per CTA of the tensor-core kernel (its CTA covers out[1] x 32 x warps rows;
+ * 1 otherwise).  The CUDA-core form is the default (it is faster on the workloads measured);
+ * the environment variable RPCA_FG_KERNEL=mma, set before rpca_create, plans the
+ * tensor-core form where it applies.  RPCA_EINVAL for a NULL argument, which out of range,
+ * or a plan that cannot be made.
+ */
+RPCA_API rpca_status rpca_plan_kernel(rpca_ctx *c, int which, int64_t *out);
+
+/*
  * Instrumentation (tracing).  rpca_profile(c, 1) starts recording: CUDA events bracket every
  * launch of the fused objective/gradient kernel and of its finalize kernel issued outside a
  * CUDA graph, on the context's stream, and every kernel the library issues is counted

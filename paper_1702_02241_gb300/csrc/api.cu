@@ -59,6 +59,7 @@ rpca_status check_dev_err(rpca_ctx* c) {
 static FgVariant g_same[17][2];
 static FgVariant g_same_x[2][17][2];  // narrow storage of X: bfloat16, FP8 E4M3
 static FgVariant g_apply[3][3][2];
+static FgVariant g_mma[17];  // tensor-core form, unmasked, K = 1..8
 static std::once_flag g_once;
 
 static void init_tables() {
@@ -66,6 +67,8 @@ static void init_tables() {
     memset(g_same, 0, sizeof g_same);
     memset(g_same_x, 0, sizeof g_same_x);
     memset(g_apply, 0, sizeof g_apply);
+    memset(g_mma, 0, sizeof g_mma);
+    fg_register_mma(g_mma);
     fg_register_same_small(g_same);
     fg_register_same_bf16(g_same_x[0]);
     fg_register_same_e4m3(g_same_x[1]);
@@ -92,6 +95,12 @@ const FgVariant* fg_variant(int K, int B, bool same, bool masked, int side, int 
   return v->fn ? v : nullptr;
 }
 
+const FgVariant* fg_mma_variant(int K, bool masked) {
+  init_tables();
+  if (masked || K < 1 || K > 8) return nullptr;
+  return g_mma[K].fn ? &g_mma[K] : nullptr;
+}
+
 // ---- TMA descriptors -----------------------------------------------------------------------
 static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -107,8 +116,20 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
+static rpca_status make_tmap_swz(rpca_ctx* c, CUtensorMap* map, CUtensorMapDataType dt, const void* base,
+                                 int64_t d0, int64_t d1, int64_t stride_bytes, int b0, int b1,
+                                 CUtensorMapSwizzle swz);
+
 rpca_status make_tmap(rpca_ctx* c, CUtensorMap* map, CUtensorMapDataType dt, const void* base, int64_t d0,
                       int64_t d1, int64_t stride_bytes, int b0, int b1) {
+  return make_tmap_swz(c, map, dt, base, d0, d1, stride_bytes, b0, b1, CU_TENSOR_MAP_SWIZZLE_NONE);
+}
+
+// swz = CU_TENSOR_MAP_SWIZZLE_128B needs b0 * element size <= 128 bytes and a 1024-byte
+// aligned shared-memory destination.
+static rpca_status make_tmap_swz(rpca_ctx* c, CUtensorMap* map, CUtensorMapDataType dt, const void* base,
+                                 int64_t d0, int64_t d1, int64_t stride_bytes, int b0, int b1,
+                                 CUtensorMapSwizzle swz) {
   auto fn = encode_fn();
   if (!fn) {
     const char* msg = "cuTensorMapEncodeTiled is not available from the driver";
@@ -119,7 +140,7 @@ rpca_status make_tmap(rpca_ctx* c, CUtensorMap* map, CUtensorMapDataType dt, con
   cuuint32_t box[2] = {(cuuint32_t)b0, (cuuint32_t)b1};
   cuuint32_t es[2] = {1, 1};
   CUresult r = fn(map, dt, 2, const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                  swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     char buf[160];
     snprintf(buf, sizeof buf, "cuTensorMapEncodeTiled failed (%d) for dims %lld x %lld, box %d x %d", (int)r,
@@ -187,6 +208,13 @@ static Workspace& plan_ws(rpca_ctx* c, const FgPlan& P);
 // Tensor maps for a chosen configuration.
 static rpca_status finish_plan(rpca_ctx* c, FgPlan* q) {
   rpca_status s;
+  if (q->mma) {
+    s = make_tmap_swz(c, &q->tmX, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, c->X, c->m, c->n, c->ldx * 4, 32, 16,
+                      CU_TENSOR_MAP_SWIZZLE_128B);
+    if (s != RPCA_OK) return s;
+    q->tmM = q->tmX;
+    return RPCA_OK;
+  }
   if (q->xt == FG_X_F32) {
     s = make_tmap(c, &q->tmX, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, c->X, c->m, c->n, c->ldx * 4, 32 * q->R, FG_BJ);
   } else {
@@ -227,6 +255,7 @@ static rpca_status time_plan(rpca_ctx* c, const FgPlan& q, double* ms) {
   a.ncs = q.ncs;
   a.BN = q.BN;
   a.nstage = q.nstage;
+  a.npass = q.npass;
   Workspace& wsp = plan_ws(c, q);
   a.PU = wsp.PU;
   a.PV = wsp.PV;
@@ -264,7 +293,7 @@ static rpca_status time_plan(rpca_ctx* c, const FgPlan& q, double* ms) {
 // is kept (cached per shape in this process).  RPCA_PLAN="warps,splits" forces one
 // configuration; RPCA_AUTOTUNE=0 keeps the model's choice without timing.
 // Cache code of a plan's kernel configuration (warps, stages).
-static int plan_code(const FgPlan& q) { return q.WC * 16 + q.nstage; }
+static int plan_code(const FgPlan& q) { return (q.mma ? (1 << 20) + (q.npass << 10) : 0) + q.WC * 16 + q.nstage; }
 
 static rpca_status make_plan(rpca_ctx* c, FgPlan* P, int K, int B, bool same, int side, int xt = FG_X_F32) {
   const bool masked = c->bits != nullptr;
@@ -345,6 +374,85 @@ static rpca_status make_plan(rpca_ctx* c, FgPlan* P, int K, int B, bool same, in
       if (t < best) best = t;
     }
   }
+  // Tensor-core form (fg_mma.cu; float32 X, fg mode, K <= 8, unmasked): consumer warps x 32
+  // rows per pass, npass passes per CTA, BN (a multiple of 16) columns per CTA.  Measured on
+  // the 76800 x 1000, k = 5 pass it is slower than the CUDA-core form (152 against 87 us: its
+  // 32 x 16 TMA boxes alone cannot be fed above ~2.7 TB/s, and its compute alone takes
+  // ~125 us), so it is planned only on request: RPCA_FG_KERNEL=mma (=cuda: the CUDA-core
+  // form only, the default).
+  const char* kenv = getenv("RPCA_FG_KERNEL");
+  const bool only_mma = kenv && strcmp(kenv, "mma") == 0;
+  const FgVariant* mv = (same && side == 0 && B == K && xt == FG_X_F32) ? fg_mma_variant(K, masked) : nullptr;
+  if (only_mma && mv) cands.clear();
+  if (mv && only_mma && !(force_wc || force_ncs)) {
+    for (int WC : {8, 4}) for (int nst : {8, 6, 4}) {
+      const int rows_pass = 32 * WC;
+      if (WC > 4 && rows_pass / 2 >= c->m) continue;
+      const int maxsplit = std::max(1, (c->n + 15) / 16);
+      int last_ncs = -1;
+      for (int ncs_req = 1; ncs_req <= std::min(maxsplit, 32); ++ncs_req) {
+        int BN = (c->n + ncs_req - 1) / ncs_req;
+        BN = (BN + 15) / 16 * 16;
+        const int ncs = (c->n + BN - 1) / BN;
+        if (ncs == last_ncs) continue;
+        last_ncs = ncs;
+        const FgMmaSmem L = fg_mma_smem_layout(WC, BN, K, nst);
+        ++n_try;
+        if (L.total > c->max_smem) {
+          ++n_smem;
+          continue;
+        }
+        const int threads = (WC + 1) * 32;
+        if (!allow_smem(mv->fn, L.total)) {
+          ++n_attr;
+          continue;
+        }
+        int cps = 0;
+        cudaError_t oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cps, mv->fn, threads, L.total);
+        if (oe != cudaSuccess || cps < 1) {
+          if (oe != cudaSuccess) last_occ = oe;
+          cudaGetLastError();
+          ++n_occ;
+          continue;
+        }
+        for (int npass = 1; npass <= 256; npass *= 2) {
+          const int rows_cta = rows_pass * npass;
+          if (npass > 1 && rows_cta / 2 >= c->m) break;
+          const int nrb = (c->m + rows_cta - 1) / rows_cta;
+          const double tiles = (double)nrb * ncs;
+          const double tile_bytes = (double)rows_cta * BN * 4.0;
+          constexpr double SM_GBS = 20.0, HBM_GBS = 6700.0;
+          const double kt = std::ceil(tiles / c->nsm);
+          const double cw = std::min<double>(cps, kt);
+          const double waves = std::ceil(kt / cw);
+          const double rate = SM_GBS * std::min(1.0, cw * WC / 8.0);
+          double t = std::max(waves * cw * tile_bytes / rate, tiles * tile_bytes / HBM_GBS);
+          t += 2.0 * 4.0 * ((double)ncs * c->mpad * B + (double)nrb * c->n * B) / HBM_GBS;
+          FgPlan cand;
+          cand.valid = true;
+          cand.var = mv;
+          cand.K = K;
+          cand.B = B;
+          cand.same = same;
+          cand.side = side;
+          cand.masked = masked;
+          cand.R = 1;
+          cand.WC = WC;
+          cand.nrb = nrb;
+          cand.ncs = ncs;
+          cand.BN = BN;
+          cand.threads = threads;
+          cand.smem = L.total;
+          cand.cps = cps;
+          cand.nstage = nst;
+          cand.xt = xt;
+          cand.mma = true;
+          cand.npass = npass;
+          cands.push_back({t, cand});
+        }
+      }
+    }
+  }
   // A context that shares the GPU (grid_cap > 0) keeps the configurations within its CTA
   // budget, or the smallest grids when none is.
   if (c->grid_cap > 0 && !cands.empty()) {
@@ -376,13 +484,23 @@ static rpca_status make_plan(rpca_ctx* c, FgPlan* P, int K, int B, bool same, in
   int pick = 0;
   int cached_wc = 0, cached_ncs = 0;
   const bool measure = !(force_wc || force_ncs) && autotune_enabled() && c->opt.autotune && cands.size() > 1;
-  if (measure && plan_cache_get(key, &cached_wc, &cached_ncs)) {
+  if (measure && !kenv && plan_cache_get(key, &cached_wc, &cached_ncs)) {
     for (size_t i = 0; i < cands.size(); ++i)
       if (plan_code(cands[i].second) == cached_wc && cands[i].second.ncs == cached_ncs) pick = (int)i;
   } else if (measure) {
-    const int ntry = (int)std::min<size_t>(same ? 12 : 6, cands.size());
+    // The best few of each form by the model are timed.
+    const int per_form = same ? 8 : 6;
+    std::vector<int> tried;
+    int n_cuda = 0, n_mma = 0;
+    for (int i = 0; i < (int)cands.size(); ++i) {
+      int& cnt = cands[i].second.mma ? n_mma : n_cuda;
+      if (cnt < per_form) {
+        ++cnt;
+        tried.push_back(i);
+      }
+    }
     double best_ms = 1e300;
-    for (int i = 0; i < ntry; ++i) {
+    for (int i : tried) {
       FgPlan& q = cands[i].second;
       rpca_status s = finish_plan(c, &q);
       if (s != RPCA_OK) return s;
@@ -394,7 +512,7 @@ static rpca_status make_plan(rpca_ctx* c, FgPlan* P, int K, int B, bool same, in
         pick = i;
       }
     }
-    plan_cache_put(key, plan_code(cands[pick].second), cands[pick].second.ncs);
+    if (!kenv) plan_cache_put(key, plan_code(cands[pick].second), cands[pick].second.ncs);
   }
   FgPlan bp = cands[pick].second;
   rpca_status s = finish_plan(c, &bp);
@@ -467,6 +585,7 @@ rpca_status launch_fg(rpca_ctx* c, const FgPlan& P, const FgLaunch& L, cudaStrea
   a.ncs = P.ncs;
   a.BN = P.BN;
   a.nstage = P.nstage;
+  a.npass = P.npass;
   Workspace& w = plan_ws(c, P);
   a.PU = w.PU;
   a.PV = w.PV;
@@ -619,6 +738,15 @@ rpca_status rpca_plan_info(rpca_ctx* c, int which, int64_t* out) {
   const FgPlan& P = *Pp;
   const int64_t v[9] = {P.R, P.WC, P.nrb, P.ncs, P.BN, P.threads, (int64_t)P.smem, P.cps, P.nstage};
   for (int i = 0; i < 9; ++i) out[i] = v[i];
+  return RPCA_OK;
+}
+
+rpca_status rpca_plan_kernel(rpca_ctx* c, int which, int64_t* out) {
+  if (!c || !out || which < 0 || which > 2) return RPCA_EINVAL;
+  const FgPlan* Pp = which == 0 ? &eval_plan(c) : apply_plan(c, which == 1 ? c->k : 0, 1);
+  if (!Pp || !Pp->valid) return RPCA_EINVAL;
+  out[0] = Pp->large ? 2 : (Pp->mma ? 1 : 0);
+  out[1] = Pp->npass;
   return RPCA_OK;
 }
 

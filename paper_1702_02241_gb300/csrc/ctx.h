@@ -28,7 +28,9 @@ struct FgPlan {
   int nstage = 3;
   int xt = 0;       // storage type of X read by this plan (FG_X_*)
   bool large = false;  // k > 16: GEMMs + elementwise pass (largek.cu) instead of the fused kernel
-  CUtensorMap tmX;  // box {32 R rows, FG_BJ columns}
+  bool mma = false;    // tensor-core form (fg_mma.cu): WC warps x 32 rows per pass, npass passes
+  int npass = 1;
+  CUtensorMap tmX;  // box {32 R rows, FG_BJ columns}; tensor-core form: {32, 16}, 128-byte swizzle
   CUtensorMap tmM;  // bitmap box {WC * R words, FG_BJ columns}
 };
 

@@ -45,6 +45,7 @@ struct FgArgs {
   double* Ppsi;      // [nrb*ncs]        sum of psi over a CTA's tile
   int* err;          // device status word (error bits)
   const float* xscale;  // FP8 storage: per-column scales (x = stored value * scale)
+  int npass;         // tensor-core form: row passes of 32 * (consumer warps) rows per CTA
 };
 
 // Storage type of X read by an instantiation: float32, bfloat16, or FP8 E4M3 with a
@@ -53,7 +54,7 @@ enum { FG_X_F32 = 0, FG_X_BF16 = 1, FG_X_E4M3 = 2 };
 __host__ __device__ constexpr int fg_x_bytes(int xt) { return xt == FG_X_F32 ? 4 : (xt == FG_X_BF16 ? 2 : 1); }
 
 constexpr int FG_BJ = 4;      // columns per pipeline stage
-constexpr int FG_NSTAGE = 6;  // maximum pipeline depth
+constexpr int FG_NSTAGE = 8;  // maximum pipeline depth
 
 struct FgSmem {
   size_t x_off, m_off, v_off, cs_off, tr_off, sc_off, bar_off, scr_off, total;
@@ -94,6 +95,35 @@ __host__ __device__ inline FgSmem fg_smem_layout(int WC, int R, bool masked, int
   o += 2 * FG_NSTAGE * 8;
   L.scr_off = o;
   o += 32 * 8;
+  L.total = o + 1024;  // slack for aligning the base
+  return L;
+}
+
+// Shared-memory carve-up of the tensor-core form (fg_mma.cu), byte offsets from a 1024-byte
+// aligned base: X stages (one 2 KB box of 32 rows x 16 columns per consumer warp, 128-byte
+// swizzle), D^T U slabs per stage (16 columns x 8 per consumer warp), the slice's
+// (v, v, v', v') rows (per 16-column group, 8 x K float4), the CTA's column sums [K][BN], psi
+// scratch, mbarriers.
+struct FgMmaSmem {
+  size_t x_off, slab_off, vr_off, col_off, scr_off, bar_off, total;
+};
+__host__ __device__ inline FgMmaSmem fg_mma_smem_layout(int WC, int BN, int K, int nstage) {
+  FgMmaSmem L;
+  size_t o = 0;
+  const size_t ng = (size_t)(BN + 15) / 16;
+  L.x_off = o;
+  o += (size_t)nstage * WC * 2048;
+  L.slab_off = o;
+  o += (size_t)nstage * WC * 16 * 8 * 4;
+  L.vr_off = o;
+  o += ng * 8 * K * 16;
+  L.col_off = o;
+  o += (size_t)K * BN * 4;
+  o = (o + 15) & ~(size_t)15;
+  L.scr_off = o;
+  o += 32 * 8;
+  L.bar_off = o;
+  o += 2 * FG_NSTAGE * 8;
   L.total = o + 1024;  // slack for aligning the base
   return L;
 }

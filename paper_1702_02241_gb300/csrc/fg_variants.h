@@ -25,5 +25,9 @@ void fg_register_same_large(FgVariant (*tab)[2]);   // K = 9..16
 void fg_register_same_bf16(FgVariant (*tab)[2]);    // K = 1..8, X stored as bfloat16
 void fg_register_same_e4m3(FgVariant (*tab)[2]);    // K = 1..8, X stored as FP8 E4M3
 void fg_register_apply(FgVariant (*tab)[3][2]);     // K = 0, 8, 16; B = 8; three sides
+void fg_register_mma(FgVariant* tab);               // tensor-core form, K = 1..8, fg mode, float32 X
+
+// Tensor-core form of the fused kernel (fg_mma.cu) for forming rank K, or nullptr.
+const FgVariant* fg_mma_variant(int K, bool masked);
 
 }  // namespace rpca

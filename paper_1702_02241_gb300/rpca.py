@@ -105,6 +105,8 @@ def lib():
     L.rpca_last_error.restype = C.c_char_p
     L.rpca_plan_info.argtypes = [P, I, C.POINTER(C.c_int64)]
     L.rpca_plan_info.restype = I
+    L.rpca_plan_kernel.argtypes = [P, I, C.POINTER(C.c_int64)]
+    L.rpca_plan_kernel.restype = I
     L.rpca_profile.argtypes = [P, I]
     L.rpca_profile.restype = I
     L.rpca_profile_read.argtypes = [P, C.POINTER(C.c_double)]
@@ -180,7 +182,7 @@ def lib():
 
 
 EXPORTED = ["rpca_default_options", "rpca_create", "rpca_fg", "rpca_apply", "rpca_init_sketch", "rpca_solve",
-            "rpca_certificate", "rpca_destroy", "rpca_last_error", "rpca_version", "rpca_plan_info",
+            "rpca_certificate", "rpca_destroy", "rpca_last_error", "rpca_version", "rpca_plan_info", "rpca_plan_kernel",
             "rpca_profile", "rpca_profile_read", "rpca_solve_log", "rpca_solve_trials", "rpca_x_storage", "rpca_fg_noalloc", "rpca_create_batch",
             "rpca_solve_batch", "rpca_batch_context", "rpca_batch_size", "rpca_batch_last_error",
             "rpca_destroy_batch", "rpca_ws_nparam", "rpca_ws_create", "rpca_ws_set_params", "rpca_ws_get_params",
@@ -279,6 +281,12 @@ def rpca_plan_info(ctx, which=0) -> dict:
     _check(lib().rpca_plan_info(ctx, which, out), ctx)
     keys = ["R", "warps", "row_blocks", "col_splits", "cols_per_cta", "threads", "smem", "ctas_per_sm", "stages"]
     return dict(zip(keys, list(out)))
+
+
+def rpca_plan_kernel(ctx, which=0) -> dict:
+    out = (C.c_int64 * 2)()
+    _check(lib().rpca_plan_kernel(ctx, which, out), ctx)
+    return {"kernel": {0: "cuda-core", 1: "tensor-core", 2: "gemm"}[int(out[0])], "npass": int(out[1])}
 
 
 def rpca_profile(ctx, enable=True):
