@@ -610,7 +610,8 @@ rpca_status launch_fg(rpca_ctx* c, const FgPlan& P, const FgLaunch& L, cudaStrea
   }
   RPCA_CUDA(c, cudaLaunchKernel(P.var->fn, dim3(P.nrb * P.ncs), dim3(P.threads), args, P.smem, stream));
   if (timed) RPCA_CUDA(c, cudaEventRecord(ev[1], stream));
-  count_launches(c, L.fin_mode != FIN_APPLY ? 3 : 2);
+  const bool fuse_ls = L.ls_st != nullptr && L.fin_mode == FIN_FG;
+  count_launches(c, fuse_ls ? 2 : (L.fin_mode != FIN_APPLY ? 3 : 2));
   FinArgs f;
   f.m = c->m;
   f.n = c->n;
@@ -644,8 +645,12 @@ rpca_status launch_fg(rpca_ctx* c, const FgPlan& P, const FgLaunch& L, cudaStrea
   f.counter = c->ws.counter;
   f.out = L.out ? L.out : c->ws.out;
   if (timed) RPCA_CUDA(c, cudaEventRecord(ev[2], stream));
-  finalize_kernel<<<P.fin_grid, 256, 0, stream>>>(f);
-  if (L.fin_mode != FIN_APPLY) finalize_reduce_kernel<<<1, 256, 0, stream>>>(f, P.fin_grid);
+  if (fuse_ls) {
+    RPCA_CUDA(c, launch_finalize_ls(f, P.fin_grid, L, stream));
+  } else {
+    finalize_kernel<<<P.fin_grid, 256, 0, stream>>>(f);
+    if (L.fin_mode != FIN_APPLY) finalize_reduce_kernel<<<1, 256, 0, stream>>>(f, P.fin_grid);
+  }
   RPCA_CUDA(c, cudaGetLastError());
   if (timed) {
     RPCA_CUDA(c, cudaEventRecord(ev[3], stream));

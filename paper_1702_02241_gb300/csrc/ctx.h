@@ -49,6 +49,7 @@ struct Workspace {
 };
 
 struct SolverBuffers;  // solver.cu
+struct SolverState;    // solver.h
 struct CertBuffers;    // cert.cu
 struct LargeK;         // largek.cu
 struct ConvexBuffers;  // convex.cu
@@ -144,8 +145,15 @@ struct FgLaunch {
   const float* DV = nullptr;
   double* out = nullptr;
   double lam = -1.0;  // clip threshold override (< 0: the context's lam_S; +inf allowed)
+  // A line-search trial of the solver (fg mode, fused-kernel plans): the finalize stage, its
+  // sums and the line-search step run as one launch (finalize_ls_kernel, solver.cu).
+  SolverState* ls_st = nullptr;
+  cudaGraphConditionalHandle ls_h = 0;
+  int ls_in_graph = 0;
+  unsigned int* ls_ticket = nullptr;  // zero between launches (reset by the last block)
 };
 rpca_status launch_fg(rpca_ctx* c, const FgPlan& P, const FgLaunch& L, cudaStream_t stream);
+cudaError_t launch_finalize_ls(const FinArgs& f, int grid, const FgLaunch& L, cudaStream_t stream);  // solver.cu
 const FgPlan* apply_plan(rpca_ctx* c, int K, int side);  // forming rank >= K (0, 8 or 16), side
 rpca_status make_xq(rpca_ctx* c, int xt);                // narrow copy of X (xq.cu)
 rpca_status ws_learned_init(rpca_ctx* c, float* U, float* V, int* used);  // ws.cu

@@ -39,9 +39,13 @@ struct FinArgs {
   double* out;              // [4]: f, g.d, ||g||^2, ||x_t||^2
 };
 
-// Finalize grid: one thread per element of the m x B side, 64 elements (four groups of 64
-// threads splitting the row-block partials) per block on the n x B side.
-inline int fin_grid_u(int64_t m, int B) { return (int)std::max<int64_t>(1, (m * B + 255) / 256); }
+// Finalize grid: FIN_EPT elements per thread of the m x B side (256 threads per block), 64
+// elements (four groups of 64 threads splitting the row-block partials) per block on the
+// n x B side.
+constexpr int FIN_EPT = 4;
+inline int fin_grid_u(int64_t m, int B) {
+  return (int)std::max<int64_t>(1, (m * B + 256 * FIN_EPT - 1) / (256 * FIN_EPT));
+}
 inline int fin_grid_v(int64_t n, int B) { return (int)std::max<int64_t>(1, (n * B + 63) / 64); }
 
 __global__ void finalize_kernel(FinArgs a);

@@ -9,169 +9,19 @@
 // finish (atomic ticket) combines the per-block partials in index order, so the result is
 // bitwise reproducible.
 #include "common.cuh"
+#include "fin.cuh"
 #include "kernels.h"
 
 namespace rpca {
 
-// Deterministic block sum of three doubles per thread; results valid in thread 0.
-RPCA_DEV void block_sum3(double& x, double& y, double& z, double (*scr)[3]) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    x += __shfl_xor_sync(0xffffffffu, x, o);
-    y += __shfl_xor_sync(0xffffffffu, y, o);
-    z += __shfl_xor_sync(0xffffffffu, z, o);
-  }
-  __syncthreads();
-  if (lane == 0) {
-    scr[w][0] = x;
-    scr[w][1] = y;
-    scr[w][2] = z;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    x = y = z = 0.0;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
-      x += scr[i][0];
-      y += scr[i][1];
-      z += scr[i][2];
-    }
-  }
-}
-
-// Gradient assembly.  Blocks [0, a.gu) handle the m x B side, one thread per element: the
-// column-split partials of PU are summed (coalesced, loads unrolled) and G_U = lam_L U_t - PU
-// (fg) or D Bv = -PU (apply) is written.  The other blocks handle the n x B side, 64 elements
-// per block: four groups of 64 threads each sum every fourth row-block partial of PV
-// (coalesced across consecutive columns) and the groups are added in a fixed order.
-// Elementwise work is float32 (the partial sums are float32 already); each block's dot
-// products (||x_t||^2, g.d, ||g||^2) go to float64 for the fixed-order block sums.
 __global__ void __launch_bounds__(256) finalize_kernel(FinArgs a) {
-  __shared__ double scr[32][3];
-  __shared__ float vs[4][64];
-  __shared__ float alpha_s;
   if (a.gate != nullptr && *a.gate == 0) return;
-  // Conversions from float64 and 64-bit divisions run on the float64 pipe, which is narrow on
-  // this GPU: the step is converted once per block, indices use 32-bit unsigned division
-  // (m B and n B are below 2^31, checked when the context is created).
-  if (threadIdx.x == 0) alpha_s = a.alpha_dev ? (float)*a.alpha_dev : a.alpha;
-  __syncthreads();
-  const float alpha = alpha_s;
-  const float lam = a.lam_f;
-  const unsigned mB = (unsigned)a.m * (unsigned)a.B, nB = (unsigned)a.n * (unsigned)a.B;
-  float nrm_f = 0.f, gd_f = 0.f, gg_f = 0.f;
-  if ((int)blockIdx.x < a.gu) {
-    const unsigned e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (a.side != 2 && e < mB) {
-      const unsigned l = e / (unsigned)a.m, i = e - l * (unsigned)a.m;
-      const float* pu = a.PU + (int64_t)l * a.mpad + i;
-      const int64_t cstride = (int64_t)a.B * a.mpad;
-      float s = 0.f;
-#pragma unroll 8
-      for (int c = 0; c < a.ncs; ++c) s += pu[c * cstride];
-      float g, xt = 0.f, dir = 0.f;
-      if (a.mode != FIN_APPLY) {
-        xt = a.U[e];
-        if (a.dU) xt = fmaf(alpha, a.dU[e], xt);
-        g = a.mode == FIN_FG ? fmaf(lam, xt, -s) : -s;
-        if (a.Ut) a.Ut[e] = xt;
-        if (a.DU) dir = a.DU[e];
-      } else {
-        g = -s;
-      }
-      a.GU[e] = g;
-      nrm_f = xt * xt;
-      gd_f = g * dir;
-      gg_f = g * g;
-    }
-  } else {
-    const int q = threadIdx.x >> 6, t = threadIdx.x & 63;
-    const unsigned e2 = (blockIdx.x - a.gu) * 64 + t;
-    const bool live = a.side != 1 && e2 < nB;
-    unsigned l = 0, j = 0;
-    float s = 0.f;
-    if (live) {
-      l = e2 / (unsigned)a.n;
-      j = e2 - l * (unsigned)a.n;
-      const float* pv = a.PV + (int64_t)l * a.n + j;
-      const int64_t rstride = (int64_t)a.B * a.n;
-#pragma unroll 4
-      for (int r = q; r < a.nrb; r += 4) s += pv[r * rstride];
-    }
-    vs[q][t] = s;
-    __syncthreads();
-    if (q == 0 && live) {
-      s = (vs[0][t] + vs[1][t]) + (vs[2][t] + vs[3][t]);
-      float g, xt = 0.f, dir = 0.f;
-      if (a.mode != FIN_APPLY) {
-        xt = a.V[e2];
-        if (a.dV) xt = fmaf(alpha, a.dV[e2], xt);
-        g = a.mode == FIN_FG ? fmaf(lam, xt, s) : s;
-        if (a.Vt) a.Vt[e2] = xt;
-        if (a.DV) dir = a.DV[e2];
-      } else {
-        g = s;
-      }
-      a.GV[e2] = g;
-      nrm_f = xt * xt;
-      gd_f = g * dir;
-      gg_f = g * g;
-    }
-  }
-  if (a.mode == FIN_APPLY) return;
-  // Warp sums in float32 (float64 is slow on this GPU: a float64 tree over every thread of
-  // the grid costs more than the whole assembly), then float64 across the warps.
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    nrm_f += __shfl_xor_sync(0xffffffffu, nrm_f, o);
-    gd_f += __shfl_xor_sync(0xffffffffu, gd_f, o);
-    gg_f += __shfl_xor_sync(0xffffffffu, gg_f, o);
-  }
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane == 0) {
-    scr[w][0] = nrm_f;
-    scr[w][1] = gd_f;
-    scr[w][2] = gg_f;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double nrm = 0.0, gd = 0.0, gg = 0.0;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
-      nrm += scr[i][0];
-      gd += scr[i][1];
-      gg += scr[i][2];
-    }
-    a.blk[3 * blockIdx.x + 0] = nrm;
-    a.blk[3 * blockIdx.x + 1] = gd;
-    a.blk[3 * blockIdx.x + 2] = gg;
-  }
+  finalize_body(a);
 }
 
-// One block: fixed-order sums of the finalize partials and of the per-CTA psi sums.
-// out = {f, g.d, ||g||^2, ||x||^2}.
 __global__ void __launch_bounds__(256) finalize_reduce_kernel(FinArgs a, int nblocks) {
-  __shared__ double scr[32][3];
   if (a.gate != nullptr && *a.gate == 0) return;
-  double p0 = 0.0, p1 = 0.0, p2 = 0.0, ps = 0.0;
-#pragma unroll 4
-  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
-    p0 += a.blk[3 * b + 0];
-    p1 += a.blk[3 * b + 1];
-    p2 += a.blk[3 * b + 2];
-  }
-  block_sum3(p0, p1, p2, scr);
-  __syncthreads();
-#pragma unroll 4
-  for (int b = threadIdx.x; b < a.nctas; b += blockDim.x) ps += a.Ppsi[b];
-  double d1 = 0.0, d2 = 0.0;
-  block_sum3(ps, d1, d2, scr);
-  if (threadIdx.x == 0) {
-    a.out[0] = ps + 0.5 * a.lam_L * p0;
-    a.out[1] = p1;
-    a.out[2] = p2;
-    a.out[3] = p0;
-  }
+  finalize_reduce_body(a, nblocks);
 }
 
 // One warp per (word, column): bit b of word w of column j is mask(32 w + b, j) != 0.

@@ -29,6 +29,7 @@
 
 #include "common.cuh"
 #include "ctx.h"
+#include "fin.cuh"
 #include "solver.h"
 
 namespace rpca {
@@ -92,97 +93,137 @@ __device__ double zoom_trial(const LineSearch& L, double epsf) {
 }
 
 // One step of the line-search state machine after the trial at L.a has been evaluated
-// (st->out[0] = phi(a), st->out[1] = phi'(a)).
+// (st->out[0] = phi(a), st->out[1] = phi'(a)), run by one thread.
 // in_graph = 0: launched from the host-driven loop (no conditional node to set).
-__global__ void ls_step_kernel(SolverState* st, cudaGraphConditionalHandle h, int in_graph) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  LineSearch& L = st->ls;
-  if (!st->active || L.state != LS_RUNNING) {
+__device__ void ls_step_body(SolverState* st, cudaGraphConditionalHandle h, int in_graph) {
+  // One thread runs a chain of dependent decisions: it works on a local copy of the line
+  // search and of the scalars it reads (one batch of loads, independent of each other) and
+  // writes the copy back once, instead of a round trip to memory per field access.
+  const int active = st->active;
+  LineSearch L = st->ls;
+  if (!active || L.state != LS_RUNNING) {
     st->gate = 0;
     if (in_graph) cudaGraphSetConditional(h, 0);
     return;
   }
-  const double a = L.a, fa = st->out[0], ga = st->out[1];
+  const double a = L.a, fa = st->out[0], ga = st->out[1], gga = st->out[2];
+  const double ls_noise = st->ls_noise, gg_cur = st->gg;
+  const int evals = st->evals, tlog_n = st->tlog_n, iter = st->iter;
   L.evals += 1;
-  st->evals += 1;
+  st->evals = evals + 1;
   bool accept = false;
   // Sufficient decrease: the Armijo test, or -- once the objective differences are at the
   // noise level of f (|f(a) - f(0)| <= ls_noise |f(0)|) -- the approximate Wolfe test of
   // Hager & Zhang, phi'(a) <= (2 c1 - 1) phi'(0), which uses the (float64-accumulated)
   // directional derivative instead of the noisy function difference.
-  const double epsf = st->ls_noise * fabs(L.f0);
+  const double epsf = ls_noise * fabs(L.f0);
   const bool approx_ok = isfinite(fa) && fa <= L.f0 + epsf && ga <= (2.0 * LS_C1 - 1.0) * L.g0;
-  const double gga = st->out[2];
   {
-    double* rec = st->tlog[st->tlog_n % SOLVER_TLOG];
-    rec[0] = st->iter;
+    double* rec = st->tlog[tlog_n % SOLVER_TLOG];
+    rec[0] = iter;
     rec[1] = a;
     rec[2] = fa - L.f0;
     rec[3] = ga / fabs(L.g0);
     rec[4] = gga;
     rec[5] = L.phase;
     rec[6] = L.evals;
-    st->tlog_n += 1;
+    st->tlog_n = tlog_n + 1;
   }
   if (L.force) {  // the fallback trial (see below) is taken as it is
     L.state = LS_ACCEPTED;
     L.f_acc = fa;
-    st->gate = 0;
-    if (in_graph) cudaGraphSetConditional(h, 0u);
-    return;
-  }
-  if (isfinite(fa) && fa <= L.f0 + epsf && isfinite(gga) && gga < L.best_gg) {
-    L.best_gg = gga;
-    L.best_a = a;
-  }
-  const bool armijo_fail = !isfinite(fa) || (fa > L.f0 + LS_C1 * a * L.g0 && !approx_ok);
-  if (L.phase == 0) {  // bracketing (Alg. 3.5)
-    if (armijo_fail || (!L.first && fa > L.f_prev + epsf) || (fabs(ga) > -LS_C2 * L.g0 && ga >= 0.0)) {
-      // [a_prev, a] holds a point of the strong Wolfe conditions: phi'(a_prev) < 0 and phi
-      // there is within the sufficient-decrease band, while at a either phi rose or phi' >= 0.
-      L.lo = L.a_prev; L.flo = L.f_prev; L.glo = L.g_prev;
-      L.hi = a; L.fhi = fa; L.ghi = ga;
-      L.width_prev = 0.0;
-      L.phase = 1;
-    } else if (fabs(ga) <= -LS_C2 * L.g0) {
-      accept = true;
-    } else {
-      L.a_prev = a; L.f_prev = fa; L.g_prev = ga;
-      L.a = fmin(4.0 * a, LS_AMAX);
-      L.first = 0;
+  } else {
+    if (isfinite(fa) && fa <= L.f0 + epsf && isfinite(gga) && gga < L.best_gg) {
+      L.best_gg = gga;
+      L.best_a = a;
     }
-  } else {  // zoom (Alg. 3.6), with the bracket kept by the sign of phi' (Hager & Zhang)
-    const double w = L.hi - L.lo;
-    if (armijo_fail || fa > L.flo + epsf) {
-      L.hi = a; L.fhi = fa; L.ghi = ga;
-    } else if (fabs(ga) <= -LS_C2 * L.g0) {
-      accept = true;
-    } else if (ga >= 0.0) {
-      L.hi = a; L.fhi = fa; L.ghi = ga;
-    } else {
-      L.lo = a; L.flo = fa; L.glo = ga;
+    const bool armijo_fail = !isfinite(fa) || (fa > L.f0 + LS_C1 * a * L.g0 && !approx_ok);
+    if (L.phase == 0) {  // bracketing (Alg. 3.5)
+      if (armijo_fail || (!L.first && fa > L.f_prev + epsf) || (fabs(ga) > -LS_C2 * L.g0 && ga >= 0.0)) {
+        // [a_prev, a] holds a point of the strong Wolfe conditions: phi'(a_prev) < 0 and phi
+        // there is within the sufficient-decrease band, while at a either phi rose or phi' >= 0.
+        L.lo = L.a_prev; L.flo = L.f_prev; L.glo = L.g_prev;
+        L.hi = a; L.fhi = fa; L.ghi = ga;
+        L.width_prev = 0.0;
+        L.phase = 1;
+      } else if (fabs(ga) <= -LS_C2 * L.g0) {
+        accept = true;
+      } else {
+        L.a_prev = a; L.f_prev = fa; L.g_prev = ga;
+        L.a = fmin(4.0 * a, LS_AMAX);
+        L.first = 0;
+      }
+    } else {  // zoom (Alg. 3.6), with the bracket kept by the sign of phi' (Hager & Zhang)
+      const double w = L.hi - L.lo;
+      if (armijo_fail || fa > L.flo + epsf) {
+        L.hi = a; L.fhi = fa; L.ghi = ga;
+      } else if (fabs(ga) <= -LS_C2 * L.g0) {
+        accept = true;
+      } else if (ga >= 0.0) {
+        L.hi = a; L.fhi = fa; L.ghi = ga;
+      } else {
+        L.lo = a; L.flo = fa; L.glo = ga;
+      }
+      L.width_prev = w;
     }
-    L.width_prev = w;
-  }
-  if (accept) {
-    L.state = LS_ACCEPTED;
-    L.f_acc = fa;
-  } else if (L.evals >= LS_MAX_TRIALS - 1) {
-    // Out of trials (at the float32 noise floor the curvature test can stay out of reach):
-    // re-evaluate the trial with the smallest gradient among those that did not increase f
-    // beyond the noise level, if it improves on the current point, and accept it.
-    if (L.best_a > 0.0 && L.best_gg < st->gg) {
-      L.a = L.best_a;
-      L.force = 1;
-    } else {
-      L.state = LS_FAILED;
+    if (accept) {
+      L.state = LS_ACCEPTED;
+      L.f_acc = fa;
+    } else if (L.evals >= LS_MAX_TRIALS - 1) {
+      // Out of trials (at the float32 noise floor the curvature test can stay out of reach):
+      // re-evaluate the trial with the smallest gradient among those that did not increase f
+      // beyond the noise level, if it improves on the current point, and accept it.
+      if (L.best_a > 0.0 && L.best_gg < gg_cur) {
+        L.a = L.best_a;
+        L.force = 1;
+      } else {
+        L.state = LS_FAILED;
+      }
+    } else if (L.phase == 1) {
+      L.a = zoom_trial(L, epsf);
     }
-  } else if (L.phase == 1) {
-    L.a = zoom_trial(L, epsf);
   }
+  st->ls = L;
   const int running = L.state == LS_RUNNING;
   st->gate = running;
   if (in_graph) cudaGraphSetConditional(h, running ? 1u : 0u);
+}
+
+__global__ void ls_step_kernel(SolverState* st, cudaGraphConditionalHandle h, int in_graph) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  ls_step_body(st, h, in_graph);
+}
+
+// Second stage of a line-search trial in one launch: every block assembles its part of the
+// gradient (finalize_body), the last block to finish (ticket) forms the fixed-order sums
+// (finalize_reduce_body) and its thread 0 takes the line-search step on them.  The same
+// arithmetic in the same order as finalize_kernel + finalize_reduce_kernel + ls_step_kernel,
+// two fewer launches per trial.  With the gate closed (no search running) only the step runs,
+// which ends the graph's while loop.
+__global__ void __launch_bounds__(256) finalize_ls_kernel(FinArgs a, SolverState* st, cudaGraphConditionalHandle h,
+                                                          int in_graph, unsigned int* ticket) {
+  __shared__ bool is_last;
+  if (a.gate != nullptr && *a.gate == 0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) ls_step_body(st, h, in_graph);
+    return;
+  }
+  finalize_body(a);
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) is_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  finalize_reduce_body(a, (int)gridDim.x);
+  if (threadIdx.x == 0) {
+    *ticket = 0u;
+    ls_step_body(st, h, in_graph);
+  }
+}
+
+cudaError_t launch_finalize_ls(const FinArgs& f, int grid, const FgLaunch& L, cudaStream_t stream) {
+  finalize_ls_kernel<<<grid, 256, 0, stream>>>(f, L.ls_st, L.ls_h, L.ls_in_graph, L.ls_ticket);
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -841,7 +882,10 @@ static SolverArgs solver_args(rpca_ctx* c) {
   return a;
 }
 
-static FgLaunch trial_launch(rpca_ctx* c) {
+// A line-search trial at x + a d (a read on the device).  For fused-kernel plans the
+// line-search step is part of the finalize launch (in_graph: inside the iteration graph,
+// whose while node h it drives); the GEMM plans of ranks above 16 launch it separately.
+static FgLaunch trial_launch(rpca_ctx* c, cudaGraphConditionalHandle h = 0, int in_graph = 0) {
   SolverBuffers* b = c->sol;
   const int64_t mk = (int64_t)c->m * c->k;
   FgLaunch L;
@@ -858,6 +902,12 @@ static FgLaunch trial_launch(rpca_ctx* c) {
   L.DU = b->d;
   L.DV = b->d + mk;
   L.out = b->st->out;
+  if (!b->plan->large) {
+    L.ls_st = b->st;
+    L.ls_h = h;
+    L.ls_in_graph = in_graph;
+    L.ls_ticket = b->counter + 1 + DOTS_MAX_GRP;
+  }
   return L;
 }
 
@@ -920,13 +970,8 @@ static rpca_status ensure_solver(rpca_ctx* c) {
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     e = cudaStreamBeginCaptureToGraph(b->cap2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-      rpca_status s = launch_fg(c, *b->plan, trial_launch(c), b->cap2);
-      if (s == RPCA_OK) {
-        ls_step_kernel<<<1, 32, 0, b->cap2>>>(b->st, h, 1);
-        e = cudaGetLastError();
-      } else {
-        e = cudaErrorUnknown;
-      }
+      rpca_status s = launch_fg(c, *b->plan, trial_launch(c, h, 1), b->cap2);
+      e = s == RPCA_OK ? cudaGetLastError() : cudaErrorUnknown;
       cudaGraph_t body_out = nullptr;
       cudaError_t e2 = cudaStreamEndCapture(b->cap2, &body_out);
       if (e == cudaSuccess) e = e2;
@@ -994,8 +1039,10 @@ static rpca_status host_iteration(rpca_ctx* c) {
     if (!b->host->active || b->host->ls.state != LS_RUNNING) break;
     rpca_status s = launch_fg(c, *b->plan, trial_launch(c), c->stream);
     if (s != RPCA_OK) return s;
-    ls_step_kernel<<<1, 32, 0, c->stream>>>(b->st, 0, 0);
-    SOL_CUDA(cudaGetLastError());
+    if (b->plan->large) {
+      ls_step_kernel<<<1, 32, 0, c->stream>>>(b->st, 0, 0);
+      SOL_CUDA(cudaGetLastError());
+    }
   }
   SOL_CUDA(update_and_direction(b->mcap, solver_args(c), b->grid, c->stream));
   return RPCA_OK;
