@@ -57,29 +57,46 @@ RPCA_DEV void finalize_body(const FinArgs& a) {
   const unsigned mB = (unsigned)a.m * (unsigned)a.B, nB = (unsigned)a.n * (unsigned)a.B;
   float nrm_f = 0.f, gd_f = 0.f, gg_f = 0.f;
   if ((int)blockIdx.x < a.gu) {
+    // Loads of all FIN_EPT elements first, stores after: a store between them would order
+    // the next element's loads after it (the compiler cannot rule out aliasing).
+    float su[FIN_EPT], uu[FIN_EPT], du[FIN_EPT], dir[FIN_EPT];
+    const int64_t cstride = (int64_t)a.B * a.mpad;
+#pragma unroll
+    for (int u = 0; u < FIN_EPT; ++u) {
+      const unsigned e = (blockIdx.x + (unsigned)u * (unsigned)a.gu) * blockDim.x + threadIdx.x;
+      su[u] = 0.f;
+      uu[u] = 0.f;
+      du[u] = 0.f;
+      dir[u] = 0.f;
+      if (a.side != 2 && e < mB) {
+        const unsigned l = e / (unsigned)a.m, i = e - l * (unsigned)a.m;
+        const float* pu = a.PU + (int64_t)l * a.mpad + i;
+        float s = 0.f;
+#pragma unroll 8
+        for (int c = 0; c < a.ncs; ++c) s += pu[c * cstride];
+        su[u] = s;
+        if (a.mode != FIN_APPLY) {
+          uu[u] = a.U[e];
+          if (a.dU) du[u] = a.dU[e];
+          if (a.DU) dir[u] = a.DU[e];
+        }
+      }
+    }
 #pragma unroll
     for (int u = 0; u < FIN_EPT; ++u) {
       const unsigned e = (blockIdx.x + (unsigned)u * (unsigned)a.gu) * blockDim.x + threadIdx.x;
       if (a.side != 2 && e < mB) {
-        const unsigned l = e / (unsigned)a.m, i = e - l * (unsigned)a.m;
-        const float* pu = a.PU + (int64_t)l * a.mpad + i;
-        const int64_t cstride = (int64_t)a.B * a.mpad;
-        float s = 0.f;
-#pragma unroll 8
-        for (int c = 0; c < a.ncs; ++c) s += pu[c * cstride];
-        float g, xt = 0.f, dir = 0.f;
+        float g, xt = 0.f;
         if (a.mode != FIN_APPLY) {
-          xt = a.U[e];
-          if (a.dU) xt = fmaf(alpha, a.dU[e], xt);
-          g = a.mode == FIN_FG ? fmaf(lam, xt, -s) : -s;
+          xt = a.dU ? fmaf(alpha, du[u], uu[u]) : uu[u];
+          g = a.mode == FIN_FG ? fmaf(lam, xt, -su[u]) : -su[u];
           if (a.Ut) a.Ut[e] = xt;
-          if (a.DU) dir = a.DU[e];
         } else {
-          g = -s;
+          g = -su[u];
         }
         a.GU[e] = g;
         nrm_f = fmaf(xt, xt, nrm_f);
-        gd_f = fmaf(g, dir, gd_f);
+        gd_f = fmaf(g, dir[u], gd_f);
         gg_f = fmaf(g, g, gg_f);
       }
     }
@@ -94,7 +111,7 @@ RPCA_DEV void finalize_body(const FinArgs& a) {
       j = e2 - l * (unsigned)a.n;
       const float* pv = a.PV + (int64_t)l * a.n + j;
       const int64_t rstride = (int64_t)a.B * a.n;
-#pragma unroll 4
+#pragma unroll 8
       for (int r = q; r < a.nrb; r += 4) s += pv[r * rstride];
     }
     vs[q][t] = s;

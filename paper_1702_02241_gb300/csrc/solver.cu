@@ -723,9 +723,26 @@ __global__ void __launch_bounds__(256) lbfgs_accept_dots_kernel(SolverArgs a) {
 #pragma unroll
   for (int v = 0; v < 64; ++v) acc[v] = 0.f;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x) {
-    float gc, s = 0.f, y = 0.f;
+    // Every load of the element first -- all history slots (every slot lies inside the
+    // history buffers; only the live ones are summed) and the four vectors -- so that they
+    // are in flight together: the stores below would otherwise order the slot loads after
+    // them (one memory round trip more per element).  The slot the new pair goes to is the
+    // spare one, never live, so its stale value loaded here is not used.
+    float sv[NS], yv[NS];
+#pragma unroll
+    for (int j = 0; j < NS; ++j) {
+      sv[j] = a.S[(int64_t)j * N + e];
+      yv[j] = a.Y[(int64_t)j * N + e];
+    }
+    const float go = a.g[e];
+    float xo = 0.f, xn = 0.f, gn = 0.f;
     if (accepted) {
-      const float xo = a.x[e], xn = a.xt[e], go = a.g[e], gn = a.gt[e];
+      xo = a.x[e];
+      xn = a.xt[e];
+      gn = a.gt[e];
+    }
+    float gc = go, s = 0.f, y = 0.f;
+    if (accepted) {
       s = xn - xo;
       y = gn - go;
       a.S[sp * N + e] = s;
@@ -733,16 +750,6 @@ __global__ void __launch_bounds__(256) lbfgs_accept_dots_kernel(SolverArgs a) {
       a.x[e] = xn;
       a.g[e] = gn;
       gc = gn;
-    } else {
-      gc = a.g[e];
-    }
-    // All slots are loaded first (every slot lies inside the history buffers), so that the
-    // loads are in flight together; only the sums of the live slots are updated.
-    float sv[NS], yv[NS];
-#pragma unroll
-    for (int j = 0; j < NS; ++j) {
-      sv[j] = a.S[(int64_t)j * N + e];
-      yv[j] = a.Y[(int64_t)j * N + e];
     }
 #pragma unroll
     for (int j = 0; j < NS; ++j) {
