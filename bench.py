@@ -41,7 +41,7 @@ WORKLOAD = ("video 76800x1000 fp32 (320x240 frames x 1000, background rank 3, 3 
             "noise 0.01), k=5, full observation, cert_rel<=1e-4")
 # Iterations the device solve takes on this workload to reach cert_rel <= 1e-4 (measured; used
 # only to scale the oracle's per-iteration time in the reference arm and the CPU baseline).
-SOLVE_ITERS_HINT = 75
+SOLVE_ITERS_HINT = 65
 
 
 def parse_args():

@@ -35,7 +35,7 @@ __device__ inline void ts_reduce_partials_cta(const double* part, int nblocks, i
     const int o = t % nout, g = t / nout;
     double acc = 0.0;
     if (g < groups) {
-#pragma unroll 4
+#pragma unroll 16
       for (int b = g; b < nblocks; b += groups) acc += part[(int64_t)b * nout + o];
     }
     scratch[t] = acc;
@@ -48,7 +48,7 @@ __device__ inline void ts_reduce_partials_cta(const double* part, int nblocks, i
   } else {
     for (int o = t; o < nout; o += blockDim.x) {
       double s = 0.0;
-#pragma unroll 4
+#pragma unroll 16
       for (int b = 0; b < nblocks; ++b) s += part[(int64_t)b * nout + o];
       out[o] = s;
     }
