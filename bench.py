@@ -61,6 +61,18 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest of the ranks' values of x (the whole job's time per step: every rank solves
+    its own instances, the job ends with the slowest).  dist is torch.distributed with an
+    initialised process group, or None for one process."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -273,11 +285,7 @@ def run_ours(args):
     launches = int(prof[4])
     ms = e0.elapsed_time(e1)
     ok = all(r.status == rpca.RPCA_OK and r.cert.cert_rel <= 1e-4 for r in results)
-    t_solve = ms / 1e3 / args.steps
-    if pg is not None:
-        t = torch.tensor([t_solve], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        t_solve = float(t.item())
+    t_solve = max_over_ranks(ms / 1e3 / args.steps, pg, dev)
 
     # Fused objective/gradient kernel alone: CUDA events recorded by the library around each
     # launch on the stream it is launched on.
@@ -453,11 +461,7 @@ def run_batch(args):
         rpca.lib().rpca_profile_read(c, prof)
         rpca.lib().rpca_profile(c, 0)
         launches += int(prof[4])
-    t_step = e0.elapsed_time(e1) / 1e3 / args.steps
-    if pg is not None:
-        t = torch.tensor([t_step], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        t_step = float(t.item())
+    t_step = max_over_ranks(e0.elapsed_time(e1) / 1e3 / args.steps, pg, dev)
     st, res = results[-1]
     ok = all(r.status == rpca.RPCA_OK for r in res) and all(st_ == rpca.RPCA_OK for st_, _ in results)
     # Effective rate of the objective/gradient passes: algorithmic bytes of every pass of every

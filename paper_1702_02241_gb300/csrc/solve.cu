@@ -151,8 +151,20 @@ struct SolveJob {
   bool narrow = false, certified = false, done = false;
   double narrow_best = INFINITY;
   rpca_cert cert;
-  ~SolveJob() { delete timer; }
+  // Recorded after the last iterations launched: lets a host thread that steps many jobs
+  // skip the ones whose work is still running instead of blocking on them.
+  cudaEvent_t launched = nullptr;
+  ~SolveJob() {
+    delete timer;
+    if (launched) cudaEventDestroy(launched);
+  }
 };
+
+// Whether the iterations a job launched last have finished (errors count as finished, so that
+// the next step reports them).
+static bool job_ready(const SolveJob& j) {
+  return j.launched == nullptr || cudaEventQuery(j.launched) != cudaErrorNotReady;
+}
 
 static rpca_status job_start(SolveJob& j, rpca_ctx* c, float* U, float* V) {
   j.c = c;
@@ -301,6 +313,11 @@ static rpca_status job_step(SolveJob& j) {
     j.timer->begin(1);
     if ((s = solver_iterations(c, batch)) != RPCA_OK) return s;
     j.timer->end();
+    if (!j.launched && cudaEventCreateWithFlags(&j.launched, cudaEventDisableTiming) != cudaSuccess) {
+      j.launched = nullptr;
+      return cuda_err(c, cudaGetLastError(), "creating a job event");
+    }
+    if (cudaEventRecord(j.launched, c->stream) != cudaSuccess) return cuda_err(c, cudaGetLastError(), "job event");
     return RPCA_OK;
   }
 }
@@ -400,16 +417,22 @@ rpca_status solve_jobs(rpca_ctx* const* ctx, float* const* U, float* const* V, r
       live[q] = status[i] == RPCA_OK;
       remaining += live[q];
     }
+    // Step whichever jobs have finished their queued iterations; a job whose GPU work is still
+    // running is passed over rather than waited for, so that no finished job sits idle.
     while (remaining > 0) {
+      bool stepped = false;
       for (size_t q = 0; q < mine.size(); ++q) {
         if (!live[q]) continue;
         const int i = mine[q];
+        if (!job_ready(jobs[i])) continue;
+        stepped = true;
         status[i] = job_step(jobs[i]);
         if (status[i] != RPCA_OK || jobs[i].done) {
           live[q] = false;
           --remaining;
         }
       }
+      if (!stepped) std::this_thread::yield();
     }
     for (int i : mine)
       if (status[i] == RPCA_OK) status[i] = job_finish(jobs[i], res ? &res[i] : nullptr);
