@@ -88,6 +88,7 @@ struct CertBuffers {
   unsigned int* counter = nullptr;
   TsScratch ts;
   bool have_F0 = false;
+  double last_F = 0.0;  // F at the point of the last evaluation (its first four steps)
 };
 
 // ---------------------------------------------------------------------------------------------
@@ -645,64 +646,72 @@ static rpca_status apply_D(rpca_ctx* c, int side, const float* BV, const float* 
   return launch_fg(c, *P, L, c->stream);
 }
 
-rpca_status cert_compute(rpca_ctx* c, const float* U, const float* V, rpca_cert* out, bool full) {
+// reuse: the last call on this context evaluated the first four steps (F, Grams, t1, t2, t3 and
+// the range bases) at this same point and nothing has changed them since: go straight to the
+// spectral step (a solve that just found the cheap terms within the tolerance).
+rpca_status cert_compute(rpca_ctx* c, const float* U, const float* V, rpca_cert* out, bool full, bool reuse) {
   rpca_status s = ensure_cert(c);
   if (s != RPCA_OK) return s;
   CertBuffers* b = c->cert;
   const int64_t m = c->m, n = c->n;
   const int k = c->k;
   CertState* st = b->st;
-  cert_reset_kernel<<<1, 1, 0, c->stream>>>(st);
-  count_launches(c, 1);
-  // F(0) = phi(0) once per context (distance bound).
-  if (!b->have_F0) {
-    FgLaunch L0;
-    L0.U = b->zm;
-    L0.V = b->zn;
-    L0.GU = b->DV;
-    L0.GV = b->DtU;
-    L0.fin_mode = FIN_FG_RAW;
-    L0.out = c->ws.out + 4;
-    if ((s = launch_fg(c, c->fg_plan, L0, c->stream)) != RPCA_OK) return s;
-    double f0 = 0;
-    CERT_CUDA(cudaMemcpyAsync(&f0, c->ws.out + 4, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    CERT_CUDA(cudaStreamSynchronize(c->stream));
-    c->F0 = f0;
-    b->have_F0 = true;
-  }
-  // 1. F and the raw products.
-  FgLaunch L;
-  L.U = U;
-  L.V = V;
-  L.GU = b->DV;
-  L.GV = b->DtU;
-  L.fin_mode = FIN_FG_RAW;
-  L.out = c->ws.out;
-  if ((s = launch_fg(c, c->fg_plan, L, c->stream)) != RPCA_OK) return s;
-  // 2. Grams.
-  CERT_CUDA(ts_gram_c(c, U, m, k, U, m, k, m, st->G, b->ts, c->stream));
-  CERT_CUDA(cudaMemcpy2DAsync(st->AUU, CERT_KMAX * 8, st->G, k * 8, k * 8, k, cudaMemcpyDeviceToDevice, c->stream));
-  CERT_CUDA(ts_gram_c(c, V, n, k, V, n, k, n, st->G, b->ts, c->stream));
-  CERT_CUDA(cudaMemcpy2DAsync(st->AVV, CERT_KMAX * 8, st->G, k * 8, k * 8, k, cudaMemcpyDeviceToDevice, c->stream));
-  CERT_CUDA(ts_gram_c(c, U, m, k, b->DV, m, k, m, st->G, b->ts, c->stream));
-  CERT_CUDA(cudaMemcpy2DAsync(st->MUDV, CERT_KMAX * 8, st->G, k * 8, k * 8, k, cudaMemcpyDeviceToDevice, c->stream));
-  // 3. Small factorisations, t1.
-  cert_small_kernel<<<1, 256, 0, c->stream>>>(st, k, c->lam_L, c->ws.out);
-  count_launches(c, 1);
-  CERT_CUDA(cudaGetLastError());
-  // 4. t3 = ||DV T_V - U P2||^2, t2 = ||DtU T_U - V P3||^2.
-  const int rg = (int)std::min<int64_t>(2 * c->nsm, (std::max(m, n) + 255) / 256);
-  cert_resid_kernel<<<std::max(1, (int)std::min<int64_t>(rg, (m + 255) / 256)), 256, 0, c->stream>>>(
-      b->DV, U, m, k, st, 0, b->blk, b->counter, st);
-  count_launches(c, 1);
-  cert_resid_kernel<<<std::max(1, (int)std::min<int64_t>(rg, (n + 255) / 256)), 256, 0, c->stream>>>(
-      b->DtU, V, n, k, st, 1, b->blk, b->counter, st);
-  count_launches(c, 1);
-  CERT_CUDA(cudaGetLastError());
-  CERT_CUDA(cudaMemcpyAsync(b->host, st, sizeof(CertState), cudaMemcpyDeviceToHost, c->stream));
   double F = 0;
-  CERT_CUDA(cudaMemcpyAsync(&F, c->ws.out, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-  CERT_CUDA(cudaStreamSynchronize(c->stream));
+  if (reuse) {
+    F = b->last_F;
+  } else {
+    cert_reset_kernel<<<1, 1, 0, c->stream>>>(st);
+    count_launches(c, 1);
+    // F(0) = phi(0) once per context (distance bound).
+    if (!b->have_F0) {
+      FgLaunch L0;
+      L0.U = b->zm;
+      L0.V = b->zn;
+      L0.GU = b->DV;
+      L0.GV = b->DtU;
+      L0.fin_mode = FIN_FG_RAW;
+      L0.out = c->ws.out + 4;
+      if ((s = launch_fg(c, c->fg_plan, L0, c->stream)) != RPCA_OK) return s;
+      double f0 = 0;
+      CERT_CUDA(cudaMemcpyAsync(&f0, c->ws.out + 4, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+      CERT_CUDA(cudaStreamSynchronize(c->stream));
+      c->F0 = f0;
+      b->have_F0 = true;
+    }
+    // 1. F and the raw products.
+    FgLaunch L;
+    L.U = U;
+    L.V = V;
+    L.GU = b->DV;
+    L.GV = b->DtU;
+    L.fin_mode = FIN_FG_RAW;
+    L.out = c->ws.out;
+    if ((s = launch_fg(c, c->fg_plan, L, c->stream)) != RPCA_OK) return s;
+    // 2. Grams.
+    CERT_CUDA(ts_gram_c(c, U, m, k, U, m, k, m, st->G, b->ts, c->stream));
+    CERT_CUDA(cudaMemcpy2DAsync(st->AUU, CERT_KMAX * 8, st->G, k * 8, k * 8, k, cudaMemcpyDeviceToDevice, c->stream));
+    CERT_CUDA(ts_gram_c(c, V, n, k, V, n, k, n, st->G, b->ts, c->stream));
+    CERT_CUDA(cudaMemcpy2DAsync(st->AVV, CERT_KMAX * 8, st->G, k * 8, k * 8, k, cudaMemcpyDeviceToDevice, c->stream));
+    CERT_CUDA(ts_gram_c(c, U, m, k, b->DV, m, k, m, st->G, b->ts, c->stream));
+    CERT_CUDA(cudaMemcpy2DAsync(st->MUDV, CERT_KMAX * 8, st->G, k * 8, k * 8, k, cudaMemcpyDeviceToDevice, c->stream));
+    // 3. Small factorisations, t1.
+    cert_small_kernel<<<1, 256, 0, c->stream>>>(st, k, c->lam_L, c->ws.out);
+    count_launches(c, 1);
+    CERT_CUDA(cudaGetLastError());
+    // 4. t3 = ||DV T_V - U P2||^2, t2 = ||DtU T_U - V P3||^2.
+    const int rg = (int)std::min<int64_t>(2 * c->nsm, (std::max(m, n) + 255) / 256);
+    cert_resid_kernel<<<std::max(1, (int)std::min<int64_t>(rg, (m + 255) / 256)), 256, 0, c->stream>>>(
+        b->DV, U, m, k, st, 0, b->blk, b->counter, st);
+    count_launches(c, 1);
+    cert_resid_kernel<<<std::max(1, (int)std::min<int64_t>(rg, (n + 255) / 256)), 256, 0, c->stream>>>(
+        b->DtU, V, n, k, st, 1, b->blk, b->counter, st);
+    count_launches(c, 1);
+    CERT_CUDA(cudaGetLastError());
+    CERT_CUDA(cudaMemcpyAsync(b->host, st, sizeof(CertState), cudaMemcpyDeviceToHost, c->stream));
+    CERT_CUDA(cudaMemcpyAsync(&F, c->ws.out, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CERT_CUDA(cudaStreamSynchronize(c->stream));
+    b->last_F = F;
+  }
   const int r = b->host->r;
   int steps = 0;
   if (full) {
@@ -795,7 +804,7 @@ extern "C" rpca_status rpca_certificate(rpca_ctx* c, const float* U, const float
   if (!c) return RPCA_EINVAL;
   if (c->lk) return set_err(c, RPCA_EUNSUPPORTED, "the certificate is built for k <= 16");
   if (!U || !V || !out) return set_err(c, RPCA_EINVAL, "U, V and out are required");
-  return cert_compute(c, U, V, out, true);
+  return cert_compute(c, U, V, out, true, false);
 }
 
 extern "C" rpca_status rpca_perp_directions(rpca_ctx* c, int qmax, float* U, int64_t ldu, float* V, int64_t ldv,

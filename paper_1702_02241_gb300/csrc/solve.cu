@@ -18,7 +18,8 @@ rpca_status solver_prepare(rpca_ctx* c, const float* U, const float* V);
 rpca_status solver_iterations(rpca_ctx* c, int count);
 rpca_status solver_read_state(rpca_ctx* c, SolverState* out);
 const float* solver_point(rpca_ctx* c);
-rpca_status cert_compute(rpca_ctx* c, const float* U, const float* V, rpca_cert* out, bool full);
+rpca_status cert_compute(rpca_ctx* c, const float* U, const float* V, rpca_cert* out, bool full,
+                         bool reuse = false);
 rpca_status sketch_init(rpca_ctx* c, const float* Omega, float* U, float* V);
 
 // Counter-based normal variates: splitmix64 of (seed, index) -> two uniforms -> Box-Muller.
@@ -274,7 +275,8 @@ static rpca_status job_step(SolveJob& j) {
       ++j.cert_evals;
       bool rank_deficit = false;
       if (j.cert.cert_rel <= c->opt.cert_tol) {
-        if ((s = cert_compute(c, solver_point(c), solver_point(c) + j.mk, &j.cert, true)) != RPCA_OK) return s;
+        // Same point as the cheap evaluation just made: only the spectral step is added.
+        if ((s = cert_compute(c, solver_point(c), solver_point(c) + j.mk, &j.cert, true, true)) != RPCA_OK) return s;
         if (j.cert.cert_rel <= c->opt.cert_tol) j.certified = true;
         else rank_deficit = j.cert.t4 > 0.0;
       }
