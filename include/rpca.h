@@ -66,7 +66,9 @@ typedef struct {
   int lbfgs_mem;         /* L-BFGS memory (10, Sec. 5.1); 1..32 */
   int max_iter;          /* iteration cap of rpca_solve */
   double cert_tol;       /* stop when cert_rel <= cert_tol (1e-4) */
-  int cert_every;        /* evaluate the certificate every cert_every iterations (0 = only at the end) */
+  int cert_every;        /* first certificate check after cert_every iterations, later ones when the
+                            gradient norm predicts cert_tol is met (at most 2 cert_every apart); 0 = only
+                            at the end */
   int init;              /* rpca_init_kind */
   uint64_t seed;         /* seed of the device generator (sketch, random init) */
   rpca_dtype x_dtype;    /* storage of X the objective pass reads: RPCA_F32 (the caller's X),
@@ -166,8 +168,14 @@ RPCA_API rpca_status rpca_init_sketch(rpca_ctx *c, const float *Omega, float *U,
  * Minimises F with L-BFGS (memory opt.lbfgs_mem, Sec. 5.1) and a strong-Wolfe line search,
  * all on the device (direction, line search and its decisions are kernels inside a CUDA
  * graph; the host only polls a status word between graph launches).  U, V: in = the start
- * point when opt.init == RPCA_INIT_USER, out = the solution.  Stops at cert_rel <= cert_tol
- * (certificate every cert_every iterations), max_iter, gtol, or timeout.  res may be NULL.
+ * point when opt.init == RPCA_INIT_USER, out = the solution.  Stops at cert_rel <= cert_tol,
+ * max_iter, gtol, or timeout.  res may be NULL.  The certificate is first evaluated after
+ * cert_every iterations; after a check that did not certify, the ratio of cert_rel to the
+ * gradient norm at that point predicts cert_rel from the gradient norm (read every 5
+ * iterations), and the next check runs once the prediction meets cert_tol (at least 5 and at
+ * most 2 cert_every iterations after the last; the narrow-storage phase keeps checks every
+ * cert_every iterations).  A certificate that passes its cheap terms adds the spectral term
+ * at the same point.
  * Returns RPCA_OK when the certificate tolerance was met, RPCA_ENOTCONV otherwise.
  * With narrow storage the iterations first read the library's copy of X; when the
  * (float32) certificate stops halving between checks, or that phase's iteration stops, the
