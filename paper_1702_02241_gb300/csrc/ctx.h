@@ -65,7 +65,7 @@ struct rpca_ctx {
   double lam_L = 0, lam_S = 0;
   rpca_options opt;
   cudaStream_t stream = nullptr;
-  int grid_cap = 0;  // CTA budget of the objective/gradient launch (0: the whole GPU)
+  int grid_cap = 0;  // CTA budget of the objective/gradient and L-BFGS launches (0: the whole GPU)
   int device = 0, nsm = 0;
   size_t max_smem = 0;
   int mpad = 0;

@@ -940,7 +940,10 @@ static rpca_status ensure_solver(rpca_ctx* c) {
   SOL_CUDA(cudaMalloc(&b->st, sizeof(SolverState)));
   SOL_CUDA(cudaMemsetAsync(b->st, 0, sizeof(SolverState), c->stream));
   SOL_CUDA(cudaMallocHost(&b->host, sizeof(SolverState)));
-  const int64_t grid_cap = std::min<int64_t>(2LL * c->nsm, (int64_t)DOTS_GRP * DOTS_MAX_GRP);
+  // Two CTAs per SM, or the context's CTA budget when it shares the GPU with others (the
+  // batched form): a grid that fills every SM leaves no room for the other contexts' kernels.
+  int64_t grid_cap = std::min<int64_t>(2LL * c->nsm, (int64_t)DOTS_GRP * DOTS_MAX_GRP);
+  if (c->grid_cap > 0) grid_cap = std::min<int64_t>(grid_cap, c->grid_cap);
   b->grid = (int)std::max<int64_t>(1, std::min<int64_t>(grid_cap, (N + 255) / 256));
   SOL_CUDA(cudaMalloc(&b->blk, sizeof(double) * std::max<size_t>(7 * ((size_t)b->grid + 64) * (mcap + 2),
                                                                   64 * ((size_t)b->grid + DOTS_MAX_GRP))));
