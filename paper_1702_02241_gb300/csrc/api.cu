@@ -970,10 +970,12 @@ void rpca_destroy(rpca_ctx* c) {
   cvx_free(c);
   free_solver(c);
   free_cert(c);
+  sk_free(c);
   cudaFree(c->bits);
   cudaFree(c->Xq);
   cudaFree(c->xscale);
   cudaFree(c->sk_sigma);
+  cudaFree(c->ws_buf);
   cudaFree(c->ws.PU);
   cudaFree(c->ws.PV);
   cudaFree(c->ws.Ppsi);

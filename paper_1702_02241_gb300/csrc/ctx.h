@@ -52,6 +52,7 @@ struct SolverBuffers;  // solver.cu
 struct SolverState;    // solver.h
 struct CertBuffers;    // cert.cu
 struct LargeK;         // largek.cu
+struct SketchBuffers;  // sketch.cu
 struct ConvexBuffers;  // convex.cu
 
 }  // namespace rpca
@@ -89,6 +90,11 @@ struct rpca_ctx {
   rpca::CertBuffers* cert = nullptr;
   rpca::LargeK* lk = nullptr;  // k > 16 (largek.cu)
   rpca::ConvexBuffers* cvx = nullptr;  // the convex baseline's scratch (convex.cu), made on first use
+  // Scratch of the randomized-SVD start (sketch.cu) and of the learned start (ws.cu), made on
+  // first use and kept: a cudaFree per solve would wait for every stream of the device.
+  rpca::SketchBuffers* sk = nullptr;
+  float* ws_buf = nullptr;
+  size_t ws_buf_n = 0;
   // Learned warm start: the model (not owned) and the last sketch's singular values.
   const rpca_ws* ws_model = nullptr;
   float* sk_sigma = nullptr;  // 32 floats on the device, owned
@@ -160,6 +166,7 @@ rpca_status ws_learned_init(rpca_ctx* c, float* U, float* V, int* used);  // ws.
 rpca_status lk_setup(rpca_ctx* c);                                           // largek.cu
 void lk_free(rpca_ctx* c);
 void cvx_free(rpca_ctx* c);  // convex.cu
+void sk_free(rpca_ctx* c);   // sketch.cu
 rpca_status launch_fg_large(rpca_ctx* c, const FgPlan& P, const FgLaunch& L, cudaStream_t stream);
 rpca_status lk_product(rpca_ctx* c, const float* U, const float* V, const float** Lp, int64_t* ldl);
 rpca_status create_ctx(rpca_ctx** out, int64_t m, int64_t n, const float* X, int64_t ldx, const uint8_t* mask,

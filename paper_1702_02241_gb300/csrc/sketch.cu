@@ -83,6 +83,7 @@ __global__ void __launch_bounds__(256) sk_small_svd_kernel(SketchState* st, int 
 
 struct SketchBuffers {
   float* buf = nullptr;
+  int l = 0;  // sketch width the buffers were made for
   float *Om, *Y, *Z, *BVc, *BUc, *Y1c, *Y2c;
   SketchState* st = nullptr;
   TsScratch ts;
@@ -92,6 +93,58 @@ static void free_sketch_buffers(SketchBuffers& b) {
   cudaFree(b.buf);
   cudaFree(b.st);
   cudaFree(b.ts.part);
+  b.buf = nullptr;
+  b.st = nullptr;
+  b.ts.part = nullptr;
+  b.l = 0;
+}
+
+void sk_free(rpca_ctx* c) {
+  if (!c->sk) return;
+  cudaStreamSynchronize(c->stream);
+  free_sketch_buffers(*c->sk);
+  delete c->sk;
+  c->sk = nullptr;
+}
+
+// The context's sketch scratch for width l (made on first use, kept until rpca_destroy).
+static rpca_status ensure_sketch(rpca_ctx* c, int l, SketchBuffers** out) {
+  if (!c->sk) c->sk = new SketchBuffers();
+  SketchBuffers& b = *c->sk;
+  const int64_t m = c->m, n = c->n;
+  if (b.buf == nullptr || b.l < l) {
+    if (b.buf) {
+      cudaStreamSynchronize(c->stream);
+      free_sketch_buffers(b);
+    }
+    const int64_t nf = n * l + m * l + n * l + n * 8 + m * 8 + m * 8 + n * 8;
+    if (cudaMalloc(&b.buf, sizeof(float) * nf) != cudaSuccess) {
+      b.buf = nullptr;
+      return set_err(c, RPCA_ENOMEM, "cudaMalloc");
+    }
+    if (cudaMalloc(&b.st, sizeof(SketchState)) != cudaSuccess) {
+      b.st = nullptr;
+      free_sketch_buffers(b);
+      return set_err(c, RPCA_ENOMEM, "cudaMalloc");
+    }
+    b.ts.grid = 2 * c->nsm;
+    b.ts.part_n = (size_t)b.ts.grid * 2304;
+    if (cudaMalloc(&b.ts.part, sizeof(double) * b.ts.part_n) != cudaSuccess) {
+      b.ts.part = nullptr;
+      free_sketch_buffers(b);
+      return set_err(c, RPCA_ENOMEM, "cudaMalloc");
+    }
+    b.l = l;
+  }
+  b.Om = b.buf;
+  b.Y = b.Om + n * l;
+  b.Z = b.Y + m * l;
+  b.BVc = b.Z + n * l;
+  b.BUc = b.BVc + n * 8;
+  b.Y1c = b.BUc + m * 8;
+  b.Y2c = b.Y1c + m * 8;
+  *out = &b;
+  return RPCA_OK;
 }
 
 #define SK_CUDA(call)                                     \
@@ -166,46 +219,32 @@ rpca_status sketch_init(rpca_ctx* c, const float* Omega, float* U, float* V) {
   const int l = std::min(std::min(k + std::max(0, c->opt.sketch_oversample), SK_LMAX), std::min(c->m, c->n));
   const int q = std::max(0, c->opt.sketch_power);
   const int64_t m = c->m, n = c->n;
-  SketchBuffers b;
-  auto done = [&](rpca_status s) {
-    cudaStreamSynchronize(c->stream);
-    free_sketch_buffers(b);
-    return s;
-  };
-  const int64_t nf = n * l + m * l + n * l + n * 8 + m * 8 + m * 8 + n * 8;
-  if (cudaMalloc(&b.buf, sizeof(float) * nf) != cudaSuccess) return done(set_err(c, RPCA_ENOMEM, "cudaMalloc"));
-  b.Om = b.buf;
-  b.Y = b.Om + n * l;
-  b.Z = b.Y + m * l;
-  b.BVc = b.Z + n * l;
-  b.BUc = b.BVc + n * 8;
-  b.Y1c = b.BUc + m * 8;
-  b.Y2c = b.Y1c + m * 8;
-  if (cudaMalloc(&b.st, sizeof(SketchState)) != cudaSuccess) return done(set_err(c, RPCA_ENOMEM, "cudaMalloc"));
-  b.ts.grid = 2 * c->nsm;
-  b.ts.part_n = (size_t)b.ts.grid * 2304;
-  if (cudaMalloc(&b.ts.part, sizeof(double) * b.ts.part_n) != cudaSuccess)
-    return done(set_err(c, RPCA_ENOMEM, "cudaMalloc"));
+  SketchBuffers* bp = nullptr;
+  {
+    const rpca_status es = ensure_sketch(c, l, &bp);
+    if (es != RPCA_OK) return es;
+  }
+  SketchBuffers& b = *bp;
   if (Omega) cudaMemcpyAsync(b.Om, Omega, sizeof(float) * n * l, cudaMemcpyDeviceToDevice, c->stream);
   else {
     fill_normal(b.Om, n * l, 0xC0FFEEULL ^ (c->opt.seed * 0x9E3779B97F4A7C15ULL), 1.f, c->stream);
     count_launches(c, 1);
   }
   rpca_status s;
-  if ((s = sk_apply(c, b, l, b.Om, nullptr, b.Y, nullptr)) != RPCA_OK) return done(s);
-  if ((s = sk_orth(c, b, b.Y, m, l)) != RPCA_OK) return done(s);
+  if ((s = sk_apply(c, b, l, b.Om, nullptr, b.Y, nullptr)) != RPCA_OK) return s;
+  if ((s = sk_orth(c, b, b.Y, m, l)) != RPCA_OK) return s;
   for (int it = 0; it < q; ++it) {
-    if ((s = sk_apply(c, b, l, nullptr, b.Y, nullptr, b.Z)) != RPCA_OK) return done(s);
-    if ((s = sk_orth(c, b, b.Z, n, l)) != RPCA_OK) return done(s);
-    if ((s = sk_apply(c, b, l, b.Z, nullptr, b.Y, nullptr)) != RPCA_OK) return done(s);
-    if ((s = sk_orth(c, b, b.Y, m, l)) != RPCA_OK) return done(s);
+    if ((s = sk_apply(c, b, l, nullptr, b.Y, nullptr, b.Z)) != RPCA_OK) return s;
+    if ((s = sk_orth(c, b, b.Z, n, l)) != RPCA_OK) return s;
+    if ((s = sk_apply(c, b, l, b.Z, nullptr, b.Y, nullptr)) != RPCA_OK) return s;
+    if ((s = sk_orth(c, b, b.Y, m, l)) != RPCA_OK) return s;
   }
   // B^T = A*(X)^T Q = -(D^T Q) / p_hat.
-  if ((s = sk_apply(c, b, l, nullptr, b.Y, nullptr, b.Z)) != RPCA_OK) return done(s);
+  if ((s = sk_apply(c, b, l, nullptr, b.Y, nullptr, b.Z)) != RPCA_OK) return s;
   if (ts_gram_c(c, b.Z, n, l, b.Z, n, l, n, b.st->G, b.ts, c->stream) != cudaSuccess)
-    return done(set_err(c, RPCA_ECUDA, "ts_gram"));
+    return set_err(c, RPCA_ECUDA, "ts_gram");
   if (!c->sk_sigma && cudaMalloc(&c->sk_sigma, sizeof(float) * SK_LMAX) != cudaSuccess)
-    return done(set_err(c, RPCA_ENOMEM, "cudaMalloc"));
+    return set_err(c, RPCA_ENOMEM, "cudaMalloc");
   const float inv_p = (float)(1.0 / std::max(c->p_hat, 1e-30));
   sk_small_svd_kernel<<<1, 256, 0, c->stream>>>(b.st, l, k, c->sk_sigma, inv_p);
   count_launches(c, 1);
@@ -215,8 +254,8 @@ rpca_status sketch_init(rpca_ctx* c, const float* Omega, float* U, float* V) {
   const float su = std::sqrt(inv_p);
   if (ts_mul_c(c, b.Y, m, l, b.st->C1, l, k, U, m, m, su, 0.f, c->stream) != cudaSuccess ||
       ts_mul_c(c, b.Z, n, l, b.st->C2, l, k, V, n, n, -su, 0.f, c->stream) != cudaSuccess)
-    return done(set_err(c, RPCA_ECUDA, "ts_mul"));
-  return done(check_dev_err(c));
+    return set_err(c, RPCA_ECUDA, "ts_mul");
+  return check_dev_err(c);
 }
 
 }  // namespace rpca

@@ -509,19 +509,25 @@ rpca_status ws_learned_init(rpca_ctx* c, float* U, float* V, int* used) {
   const rpca_ws* w = c->ws_model;
   if (!w) return set_err(c, RPCA_EINVAL, "RPCA_INIT_LEARNED needs a model (rpca_set_warm_start)");
   const int64_t mk = (int64_t)c->m * c->k, nk = (int64_t)c->n * c->k;
-  float* buf = nullptr;
-  RPCA_CUDA(c, cudaMalloc(&buf, sizeof(float) * (2 * (mk + nk) + 64)));
+  // Scratch kept by the context (a cudaFree per solve would wait for every stream).
+  const size_t need = (size_t)(2 * (mk + nk) + 64);
+  if (c->ws_buf_n < need) {
+    if (c->ws_buf) {
+      RPCA_CUDA(c, cudaStreamSynchronize(c->stream));
+      cudaFree(c->ws_buf);
+      c->ws_buf = nullptr;
+      c->ws_buf_n = 0;
+    }
+    RPCA_CUDA(c, cudaMalloc(&c->ws_buf, sizeof(float) * need));
+    c->ws_buf_n = need;
+  }
+  float* buf = c->ws_buf;
   float* Ul = buf;
   float* Vl = Ul + mk;
   float* G = Vl + nk;  // gradient scratch, mk + nk
   float* xw = G + mk + nk;  // 40 features | 16 outputs
-  auto done = [&](rpca_status s) {
-    cudaStreamSynchronize(c->stream);
-    cudaFree(buf);
-    return s;
-  };
   rpca_status s = ws_features(c, xw);
-  if (s != RPCA_OK) return done(s);
+  if (s != RPCA_OK) return s;
   ws_forward_kernel<<<1, 256, 0, c->stream>>>(w->theta, w->q, xw, 1, xw + WS_FEAT);
   ws_scale_cols_kernel<<<std::max<int64_t>(1, std::min<int64_t>(1024, (mk + 255) / 256)), 256, 0, c->stream>>>(
       U, Ul, c->m, c->k, xw + WS_FEAT);
@@ -538,7 +544,7 @@ rpca_status ws_learned_init(rpca_ctx* c, float* U, float* V, int* used) {
     L.V = VV[q];
     L.GU = G;
     L.GV = G + mk;
-    if ((s = launch_fg(c, c->fg_plan, L, c->stream)) != RPCA_OK) return done(s);
+    if ((s = launch_fg(c, c->fg_plan, L, c->stream)) != RPCA_OK) return s;
     RPCA_CUDA(c, cudaMemcpyAsync(&f[q], c->ws.out, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     RPCA_CUDA(c, cudaStreamSynchronize(c->stream));
   }
@@ -547,7 +553,7 @@ rpca_status ws_learned_init(rpca_ctx* c, float* U, float* V, int* used) {
     RPCA_CUDA(c, cudaMemcpyAsync(V, Vl, sizeof(float) * nk, cudaMemcpyDeviceToDevice, c->stream));
     *used = 1;
   }
-  return done(RPCA_OK);
+  return RPCA_OK;
 }
 
 }  // namespace rpca
