@@ -84,7 +84,11 @@ rpca_status rpca_solve_batch(rpca_batch* b, float* const* U, float* const* V, rp
   cudaEventDestroy(ready);
   std::vector<rpca_result> local(count);
   std::vector<rpca_status> st(count, RPCA_OK);
-  int threads = (int)std::min(16u, std::max(1u, std::thread::hardware_concurrency()));
+  // Host threads stepping the solves: they mostly wait on their jobs' streams (a certificate
+  // evaluation blocks its thread for milliseconds while that thread's other jobs run dry), so
+  // more threads than cores pays: 256 instances took 2.83 s with 16 threads and 2.75 s with 64
+  // on a 16-core host.
+  int threads = (int)std::min(64u, 4u * std::max(1u, std::thread::hardware_concurrency()));
   if (const char* e = getenv("RPCA_BATCH_THREADS")) threads = std::max(1, atoi(e));
   rpca::solve_jobs(b->ctx.data(), U, V, local.data(), count, st.data(), threads);
   int notconv = 0;
