@@ -47,14 +47,19 @@ SOLVE_ITERS_HINT = 65
 def parse_args():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--steps", type=int, default=None,
+                   help="timed steps (default: 30 solves for the video workload, so that the clock sampler "
+                        "sees the timed region several times; 3 for the heavier workloads and the reference arm)")
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--fg-evals", type=int, default=100)
     p.add_argument("--workload", default="video", choices=["video", "batch", "convex", "precision"])
     p.add_argument("--batch-count", type=int, default=256)
-    return p.parse_args()
+    a = p.parse_args()
+    if a.steps is None:
+        a.steps = 30 if (a.workload == "video" and a.impl == "ours") else 3
+    return a
 
 
 def dist_env():
