@@ -92,10 +92,21 @@ typedef struct {
   double normL_F;  /* ||U V^T||_F */
   double F;        /* F(U, V) */
   double F_bound;  /* min(F(0), best F seen by this context) */
-  double gap_bound;/* cert * (||L||_F + F_bound / lam_L) >= F(L) - F* */
-  int rank_r;      /* numerical rank of U V^T (singular values > 1e-8 sigma_1) */
+  double gap_bound;/* cert * (||L||_F + F_bound / lam_L) + F_trunc >= G(L) - G*,
+                      G(L) = lam_L ||L||_* + phi(L) (the convex objective, Sec. 3.4) */
+  int rank_r;      /* numerical rank of U V^T used by the certificate: singular values
+                      > 1e-8 sigma_1, less the directions moved to the complement block
+                      (sigma_i <= 1e-3 sigma_1 with |lam_L + u_i^T D v_i| > lam_L / 2, or
+                      lam_L sigma_i <= 1e-12 F) */
   int krylov_steps;/* block Lanczos steps used for t4 */
   double sigma1_perp; /* largest singular value of P_U1perp D P_V1perp found */
+  double F_trunc;  /* 2 lam_L sum of the singular values moved to the complement block: the
+                      certificate is that of L with them truncated, and this bounds what the
+                      truncation adds to the optimality gap (not in the paper) */
+  double trunc_rel;/* F_trunc / (lam_L ||L||_F + F_bound), in the units of cert_rel:
+                      gap_bound = (cert_rel + trunc_rel)(lam_L ||L||_F + F_bound).  A point
+                      counts as certified at cert_tol only when cert_rel <= cert_tol and
+                      trunc_rel <= cert_tol. */
 } rpca_cert;
 
 typedef struct {
@@ -287,24 +298,24 @@ RPCA_API rpca_status rpca_solve_log(rpca_ctx *c, double *out, int max_rows, int 
  * 256 trials, copied out here): up to max_rows rows of 7 doubles, oldest first:
  * {iteration, trial step a, F(x + a d) - F(x), phi'(a) / |phi'(0)| (directional derivative
  * along d, relative), ||grad F(x + a d)||_F^2, phase (0 bracketing, 1 zoom), trial number}.
- * The line search is the strong-Wolfe search of Nocedal & Wright Alg. 3.5/3.6 that the
- * L-BFGS iteration of Sec. 3.3 uses.  *rows receives the number of rows written.
+ * The line search is the strong-Wolfe search of Nocedal & Wright Alg. 3.5/3.6 around the
+ * L-BFGS iteration of Sec. 5.1.  *rows receives the number of rows written.
  */
 RPCA_API rpca_status rpca_solve_trials(rpca_ctx *c, double *out, int max_rows, int *rows);
 
 /*
  * One objective/gradient evaluation, as rpca_fg (same formulas, same kernels), that
  * allocates nothing: for callers that cannot allocate device memory where they evaluate
- * (an application that owns all device memory through its own arena, code running while a
- * CUDA graph is captured, a plugin host).  The paper has no counterpart; this is an
- * interface of this library.  No context: X (m x n, ldx, 16-byte aligned, ldx a multiple
+ * (an application that owns all device memory through its own arena and allows no
+ * cudaMalloc or cudaFree on its hot path, a plugin host that hands the library only the
+ * buffers it owns).  The paper has no counterpart; this is an interface of this library.  No context: X (m x n, ldx, 16-byte aligned, ldx a multiple
  * of 4, fully observed -- no mask), k in [1, 16], lambda_L, lambda_S as in rpca_create; U,
  * V in; f (HOST pointer, may be NULL), gU, gV out.  The scratch comes from one file-scope
  * device array of 32 MiB that every GPU loading the library holds until exit; shapes whose
  * partial sums need more ((ncs m + nrb n) k floats plus a little) are rejected with
  * RPCA_EINVAL and a message (use rpca_fg).  X is not checked for non-finite values.  The
- * first call on a device looks up the array's device address (do that first call before
- * any stream capture).  The call synchronises the stream.  All calls share the array:
+ * first call on a device looks up the array's device address (make that first call before
+ * any stream capture).  The call waits for the stream before it returns.  All calls share the array:
  * calls that overlap on the GPU (other streams, other host threads) race and must be
  * serialised by the caller.  Errors: rpca_last_error(NULL).  No launch-configuration
  * timing is done, so it can be slower than rpca_fg.
@@ -315,6 +326,22 @@ RPCA_API rpca_status rpca_fg_noalloc(int64_t m, int64_t n, const float *X, int64
 
 /* Library version string. */
 RPCA_API const char *rpca_version(void);
+
+/*
+ * Failure injection, for tests of the failure paths (the paper has no counterpart).  Faults
+ * are made on the host side or by withholding work, never by a bad access on the GPU:
+ *   RPCA_FAULT_FG_STARVE (c required): the next `count` launches of the fused objective/
+ *     gradient kernel on c (CUDA-core form, outside CUDA graphs: rpca_fg, rpca_apply, the
+ *     certificate) run with their producer warp issuing no copies and a 1 ms limit on the
+ *     consumers' waits, which then run out; the call reports RPCA_ETIMEOUT, the status word is
+ *     cleared, no copy is left in flight and the context stays usable.
+ *   RPCA_FAULT_ALLOC (c ignored): the next `count` device allocations of context set-up
+ *     (rpca_create and the workspaces it sizes) fail as out of memory (RPCA_ENOMEM); the
+ *     partly built context is released.
+ * count = 0 clears the fault.  RPCA_EINVAL for an unknown kind or count < 0.
+ */
+enum { RPCA_FAULT_FG_STARVE = 1, RPCA_FAULT_ALLOC = 2 };
+RPCA_API rpca_status rpca_inject_fault(rpca_ctx *c, int kind, int count);
 
 /*
  * Unit singular vectors (u: device m floats, v: device n floats) of the largest singular value

@@ -34,7 +34,15 @@ Readings of the paper taken here (each is pinned by a test):
   L = 0).  Truncating it changes F by at most (lam_L + ||D||_2) sigma_i.
 * Distance bound: ||L - L*||_F <= ||L||_F + F_bound / lam_L with
   F_bound = min(F(0) = phi(0), best objective seen), and the optimality-gap bound
-  F(L) - F* <= cert * (||L||_F + F_bound / lam_L).
+  G(L) - G* <= cert * (||L||_F + F_bound / lam_L) + F_trunc, G(L) = lam_L ||L||_* + phi(L).
+* Cost of the truncation (not in the paper, which assumes exact ranks).  With T the directions
+  moved to the complement, L^ = L - sum_T sigma_i u_i v_i^T, E = lam_L Z + D, Z in the
+  subdifferential of ||.||_* at L^ and D = grad phi(L) (phi convex), every L' satisfies
+    G(L') >= G(L) + <E, L' - L> - lam_L sum_T sigma_i (1 - u_i^T W v_i),  ||W||_2 <= 1,
+  so G(L) - G* <= cert ||L - L*||_F + F_trunc with F_trunc = 2 lam_L sum_T sigma_i.  The
+  certificate reports F_trunc and trunc_rel = F_trunc / (lam_L ||L||_F + F_bound), the same
+  quantity in the units of cert_rel (gap_bound = (cert_rel + trunc_rel)(lam_L ||L||_F +
+  F_bound)); a point counts as certified at tolerance tol only when both are <= tol.
 """
 from __future__ import annotations
 
@@ -63,6 +71,12 @@ class Cert:
     F_bound: float
     gap_bound: float
     sigma_perp: np.ndarray  # leading singular values of P_U1perp D P_V1perp that were computed
+    F_trunc: float = 0.0    # 2 lam_L sum of the truncated singular values (bound on their cost)
+    trunc_rel: float = 0.0  # F_trunc / (lam_L ||L||_F + F_bound)
+
+    def certified(self, tol):
+        """Both the certificate and the truncation's cost within tol (relative units)."""
+        return self.cert_rel <= tol and self.trunc_rel <= tol
 
 
 def range_bases(U, V, tau=TAU):
@@ -126,8 +140,10 @@ def certificate(X, mask, U, V, lam_L, lam_S, F_best=None, tau=TAU, t4_method="au
         keep = ~((s1 <= DROP_TAU * s1[0]) & (np.abs(lam_L + b_diag) > 0.5 * lam_L))
         keep &= ~(lam_L * s1 <= NEG_TAU * F)
         U1, V1, s1_kept = U1[:, keep], V1[:, keep], s1[keep]
+        sig_dropped = float(np.sum(s1[~keep]))
     else:
         s1_kept = s1
+        sig_dropped = 0.0
     r = s1_kept.size
     DV1 = D @ V1
     UtD = U1.T @ D
@@ -145,10 +161,13 @@ def certificate(X, mask, U, V, lam_L, lam_S, F_best=None, tau=TAU, t4_method="au
     F0 = core.phi_of_R(-np.asarray(X, np.float64), mask, lam_S)
     F_bound = min(F0, F if F_best is None else min(F, F_best))
     normL = float(np.sqrt(np.sum(s1 ** 2)))
-    gap = cert * (normL + F_bound / lam_L)
+    F_trunc = 2.0 * lam_L * sig_dropped
+    scale = lam_L * normL + F_bound
+    trunc_rel = F_trunc / scale if scale > 0 else (0.0 if F_trunc == 0 else np.inf)
+    gap = cert * (normL + F_bound / lam_L) + F_trunc
     return Cert(cert=cert, cert_rel=cert / lam_L, t1=t1, t2=t2, t3=t3, t4=t4, rank_r=r,
                 normL_F=normL, F=float(F), F_bound=float(F_bound), gap_bound=float(gap),
-                sigma_perp=sp)
+                sigma_perp=sp, F_trunc=float(F_trunc), trunc_rel=float(trunc_rel))
 
 
 def perp_matrix(X, mask, U, V, lam_L, lam_S, tau=TAU):

@@ -2,6 +2,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <atomic>
 #include <climits>
 #include <cmath>
 #include <cstdio>
@@ -524,6 +525,20 @@ static rpca_status make_plan(rpca_ctx* c, FgPlan* P, int K, int B, bool same, in
 // Grows a workspace buffer.  Work already queued on the context's stream may still use the
 // old buffer (the stream may be non-blocking, which cudaFree's implicit synchronisation does
 // not cover), so the stream is drained first.
+// Device allocations of the context's set-up go through here so that a test can make the
+// next ones fail (rpca_inject_fault, RPCA_FAULT_ALLOC) without exhausting the GPU.
+static std::atomic<int> g_fault_alloc{0};
+cudaError_t dev_malloc(void** p, size_t bytes) {
+  int left = g_fault_alloc.load();
+  while (left > 0) {
+    if (g_fault_alloc.compare_exchange_weak(left, left - 1)) {
+      *p = nullptr;
+      return cudaErrorMemoryAllocation;
+    }
+  }
+  return cudaMalloc(p, bytes);
+}
+
 template <typename T>
 static rpca_status ensure(rpca_ctx* c, T** p, size_t* have, size_t need) {
   if (*have >= need) return RPCA_OK;
@@ -533,7 +548,7 @@ static rpca_status ensure(rpca_ctx* c, T** p, size_t* have, size_t need) {
   }
   *p = nullptr;
   *have = 0;
-  RPCA_CUDA(c, cudaMalloc(p, std::max<size_t>(need, 1) * sizeof(T)));
+  RPCA_CUDA(c, dev_malloc(reinterpret_cast<void**>(p), std::max<size_t>(need, 1) * sizeof(T)));
   *have = need;
   return RPCA_OK;
 }
@@ -567,6 +582,13 @@ const FgPlan* apply_plan(rpca_ctx* c, int K, int side) {
 rpca_status launch_fg(rpca_ctx* c, const FgPlan& P, const FgLaunch& L, cudaStream_t stream) {
   if (P.large) return launch_fg_large(c, P, L, stream);
   FgArgs a;
+  a.starve = 0;
+  a.wait_ns = 0;
+  if (c->fault_fg > 0 && !P.mma) {  // failure injection: this launch's copies are never issued
+    --c->fault_fg;
+    a.starve = 1;
+    a.wait_ns = 1000000ull;  // 1 ms
+  }
   a.m = c->m;
   a.n = c->n;
   a.mpad = c->mpad;
@@ -699,7 +721,21 @@ void rpca_default_options(rpca_options* o) {
   o->ls_noise = 1e-8;
 }
 
-const char* rpca_version(void) { return "rpca-gb300 0.1 (sm_103a)"; }
+const char* rpca_version(void) { return "rpca-gb300 0.2 (sm_103a)"; }
+
+rpca_status rpca_inject_fault(rpca_ctx* c, int kind, int count) {
+  if (count < 0) return set_err(c, RPCA_EINVAL, "count must be >= 0");
+  if (kind == RPCA_FAULT_FG_STARVE) {
+    if (!c) return set_err(nullptr, RPCA_EINVAL, "RPCA_FAULT_FG_STARVE needs a context");
+    c->fault_fg = count;
+    return RPCA_OK;
+  }
+  if (kind == RPCA_FAULT_ALLOC) {
+    rpca::g_fault_alloc.store(count);
+    return RPCA_OK;
+  }
+  return set_err(c, RPCA_EINVAL, "unknown fault kind");
+}
 
 rpca_status rpca_profile(rpca_ctx* c, int enable) {
   if (!c) return RPCA_EINVAL;
@@ -829,15 +865,15 @@ rpca_status create_ctx(rpca_ctx** out, int64_t m, int64_t n, const float* X, int
   if (cc_major != 10 || cc_minor != 3)
     return fail(set_err(c, RPCA_EUNSUPPORTED, "this library is built for sm_103a (GB300) only"));
 
-  if ((e = cudaMalloc(&c->ws.counter, 64)) != cudaSuccess) return fail(cuda_err(c, e, "cudaMalloc"));
-  if ((e = cudaMalloc(&c->ws.out, 8 * sizeof(double))) != cudaSuccess) return fail(cuda_err(c, e, "cudaMalloc"));
-  if ((e = cudaMalloc(&c->ws.err, 64)) != cudaSuccess) return fail(cuda_err(c, e, "cudaMalloc"));
+  if ((e = dev_malloc(reinterpret_cast<void**>(&c->ws.counter), 64)) != cudaSuccess) return fail(cuda_err(c, e, "cudaMalloc"));
+  if ((e = dev_malloc(reinterpret_cast<void**>(&c->ws.out), 8 * sizeof(double))) != cudaSuccess) return fail(cuda_err(c, e, "cudaMalloc"));
+  if ((e = dev_malloc(reinterpret_cast<void**>(&c->ws.err), 64)) != cudaSuccess) return fail(cuda_err(c, e, "cudaMalloc"));
   cudaMemsetAsync(c->ws.counter, 0, 64, c->stream);
   cudaMemsetAsync(c->ws.err, 0, 64, c->stream);
 
   // Validate X on the observed set.
   unsigned long long* cnt = nullptr;
-  if ((e = cudaMalloc(&cnt, 2 * sizeof(unsigned long long))) != cudaSuccess) return fail(cuda_err(c, e, "cudaMalloc"));
+  if ((e = dev_malloc(reinterpret_cast<void**>(&cnt), 2 * sizeof(unsigned long long))) != cudaSuccess) return fail(cuda_err(c, e, "cudaMalloc"));
   cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), c->stream);
   check_x_kernel<<<4 * c->nsm, 256, 0, c->stream>>>(X, ldx, mask, ldmask, c->m, c->n, cnt, cnt + 1);
   unsigned long long hc[2] = {0, 0};
@@ -850,7 +886,7 @@ rpca_status create_ctx(rpca_ctx** out, int64_t m, int64_t n, const float* X, int
 
   if (mask) {
     c->wpad = (int)(((m + 31) / 32 + 3) / 4 * 4);
-    if ((e = cudaMalloc(&c->bits, (size_t)c->wpad * n * 4)) != cudaSuccess) return fail(cuda_err(c, e, "cudaMalloc"));
+    if ((e = dev_malloc(reinterpret_cast<void**>(&c->bits), (size_t)c->wpad * n * 4)) != cudaSuccess) return fail(cuda_err(c, e, "cudaMalloc"));
     const int64_t warps = (int64_t)c->wpad * n;
     pack_mask_kernel<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, c->stream>>>(mask, ldmask, c->m, c->n, c->wpad,
                                                                                 c->bits);

@@ -21,7 +21,9 @@
 //     the fused kernel in apply mode; Ritz values from a float32 one-sided Jacobi SVD of the
 //     projected matrix T = P^T A Q; stops when the leading Ritz value and t4 settle.
 // Also F_bound = min(F(0), best F seen) and the gap bound cert * (||L||_F + F_bound/lam_L)
-// (Sec. 3.4, "Bounding the distance to the feasible set").
+// (Sec. 3.4, "Bounding the distance to the feasible set") plus F_trunc, the cost of the
+// directions of L that step 3 moves to the complement block (2 lam_L times their singular
+// values), and trunc_rel = F_trunc / (lam_L ||L||_F + F_bound).
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -49,6 +51,7 @@ struct CertState {
   double sig[CERT_KMAX];
   int r;
   double t1, t2, t3, t4, normL, sigma1;
+  double sig_drop;  // sum of the singular values of L moved to the complement block
   double G[(CERT_KMAX + LZ_TMAX) * LZ_B];    // Gram scratch (p x q)
   double G2[(CERT_KMAX + LZ_TMAX + LZ_B) * LZ_B];  // projection Gram [B | Y]^T Y
   double R[LZ_B * LZ_B], Rinv[LZ_B * LZ_B];
@@ -178,16 +181,22 @@ __global__ void __launch_bounds__(256) cert_small_kernel(CertState* st, int k, d
   // is then that of L with it truncated.  So is a direction whose nuclear-norm term is
   // negligible against the objective (lam_L sigma_i <= NEG_TAU F), which the relative test
   // cannot see when all of L is at the float32 rounding floor (a solution L = 0).
+  // Their singular values are summed: the truncation costs at most 2 lam_L sum sigma_i in the
+  // optimality gap (subgradient inequalities of phi at L and of the nuclear norm at the
+  // truncated point), which the host reports beside the certificate.
   __shared__ int keep[CERT_KMAX], rk;
   if (t == 0) {
     rk = 0;
+    double drop = 0.0;
     const double Fv = *Fp;
     for (int c = 0; c < r; ++c) {
       const bool tiny = sm[ordm[c]] <= DROP_TAU * sm[ordm[0]];
       const bool inactive = fabs(lam_L + Bs[c + c * CERT_KMAX]) > 0.5 * lam_L;
       const bool negligible = lam_L * sm[ordm[c]] <= NEG_TAU * Fv;
       if (!(tiny && inactive) && !negligible) keep[rk++] = c;
+      else drop += sm[ordm[c]];
     }
+    st->sig_drop = drop;
     if (rk < r) {
       for (int q = 0; q < rk; ++q) {
         for (int l = 0; l < k; ++l) {
@@ -788,7 +797,12 @@ rpca_status cert_compute(rpca_ctx* c, const float* U, const float* V, rpca_cert*
   o.F = F;
   if (F < c->F_best) c->F_best = F;
   o.F_bound = std::min(c->F0, c->F_best);
-  o.gap_bound = o.cert * (o.normL_F + o.F_bound / c->lam_L);
+  o.F_trunc = 2.0 * c->lam_L * h.sig_drop;
+  {
+    const double scale = c->lam_L * o.normL_F + o.F_bound;
+    o.trunc_rel = scale > 0.0 ? o.F_trunc / scale : (o.F_trunc > 0.0 ? INFINITY : 0.0);
+  }
+  o.gap_bound = o.cert * (o.normL_F + o.F_bound / c->lam_L) + o.F_trunc;
   o.rank_r = h.r;
   o.krylov_steps = steps;
   o.sigma1_perp = full ? h.sigma1 : 0.0;

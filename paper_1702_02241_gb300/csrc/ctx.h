@@ -111,6 +111,8 @@ struct rpca_ctx {
   int64_t prof_n[2] = {0, 0};
   int64_t launches = 0;
   int64_t graph_launches = 0;
+  // Failure injection (rpca_inject_fault): fused-kernel launches left to starve.
+  int fault_fg = 0;
 };
 
 namespace rpca {
@@ -122,6 +124,7 @@ rpca_status make_tmap(rpca_ctx* c, CUtensorMap* map, CUtensorMapDataType dt, con
                       int64_t d1, int64_t stride_bytes, int b0, int b1);
 rpca_status cuda_err(rpca_ctx* c, cudaError_t e, const char* what);
 rpca_status check_dev_err(rpca_ctx* c);
+cudaError_t dev_malloc(void** p, size_t bytes);  // cudaMalloc, or an injected failure
 
 // Returns from the calling function with RPCA_ECUDA (and the context's error text) on failure.
 #define RPCA_CUDA(c, call)                              \

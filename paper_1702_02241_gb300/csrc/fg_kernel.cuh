@@ -46,6 +46,10 @@ struct FgArgs {
   int* err;          // device status word (error bits)
   const float* xscale;  // FP8 storage: per-column scales (x = stored value * scale)
   int npass;         // tensor-core form: row passes of 32 * (consumer warps) rows per CTA
+  // Failure injection (rpca_inject_fault): the producer issues no copies, so the consumers'
+  // bounded waits run out (after wait_ns, 0 = the default limit) and report a status bit.
+  int starve;
+  unsigned long long wait_ns;
 };
 
 // Storage type of X read by an instantiation: float32, bfloat16, or FP8 E4M3 with a
@@ -211,7 +215,7 @@ __global__ void __launch_bounds__(288, 1) fg_kernel(const __grid_constant__ CUte
   __syncthreads();
 
   if (warp == WC) {  // ---------------- producer ----------------
-    if (lane == 0) {
+    if (lane == 0 && !a.starve) {
       prefetch_tmap(&tmX);
       if (MASKED) prefetch_tmap(&tmM);
       const uint64_t pol = l2_evict_first_policy();  // X and its bitmap are streamed once per pass
@@ -250,6 +254,7 @@ __global__ void __launch_bounds__(288, 1) fg_kernel(const __grid_constant__ CUte
   const int tid = threadIdx.x;
   const int wrow0 = row0 + warp * ROWS_W;
   const float alpha = a.alpha_dev ? (float)*a.alpha_dev : a.alpha;
+  const uint64_t wait_ns = a.wait_ns ? a.wait_ns : kWaitLimitNs;
 
   // Factor slice for this CTA's columns, as duplicated pairs (v, v) for the fp32x2 FMA.
   for (int idx = tid; idx < a.BN * KV; idx += nct) {
@@ -318,7 +323,7 @@ __global__ void __launch_bounds__(288, 1) fg_kernel(const __grid_constant__ CUte
 
   for (int c = 0; c < nchunks; ++c) {
     const int s = c % nst;
-    if (!failed && !mbar_wait_bounded(&full[s], (uint32_t)(c / nst) & 1u)) {
+    if (!failed && !mbar_wait_bounded(&full[s], (uint32_t)(c / nst) & 1u, wait_ns)) {
       failed = true;
       if (lane == 0) atomicOr(a.err, DEV_ERR_TIMEOUT_FULL);
     }

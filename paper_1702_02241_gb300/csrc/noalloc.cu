@@ -2,13 +2,14 @@
 //
 // Some callers cannot allocate device memory at the point where they evaluate the
 // objective: applications that own all device memory through their own arena and forbid
-// cudaMalloc on their hot path, code that runs while a CUDA graph is being captured (where
-// allocation calls are illegal), or hosts that load this library as a plugin with no
-// context of its own.  rpca_fg needs a context, and rpca_create allocates (partial-sum
-// buffers, the mask bitmap, the autotuner's trial buffers).  This entry point does the same
-// evaluation with the scratch it needs taken from one fixed device array declared in this
-// file (NOALLOC_SCRATCH_BYTES, reserved on every GPU that loads the library, until exit).
-// The caller passes X, the factors and the outputs.
+// cudaMalloc (and the device-wide synchronisation a cudaFree implies) on their hot path,
+// or hosts that load this library as a plugin and hand it only the buffers they own.
+// rpca_fg needs a context, and rpca_create allocates (partial-sum buffers, the mask bitmap,
+// the autotuner's trial buffers).  This entry point does the same evaluation with the
+// scratch it needs taken from one fixed device array declared in this file
+// (NOALLOC_SCRATCH_BYTES, reserved on every GPU that loads the library, until exit).
+// The caller passes X, the factors and the outputs.  The call waits for its stream before
+// it returns (it reads f and the status word back into host variables).
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -71,7 +72,8 @@ extern "C" rpca_status rpca_fg_noalloc(int64_t m, int64_t n, const float* X, int
   if (!v) return set_err_noctx(RPCA_EUNSUPPORTED, "no compiled kernel for this k");
 
   // Fixed launch configuration (no timing runs: they would need buffers): the widest CTA
-  // that the rows fill, two pipeline stages, enough column splits to cover the SMs once.
+  // that the rows fill, four pipeline stages (the depth rpca_fg's planner settles on for
+  // most shapes measured), enough column splits to cover the SMs once.
   int WC = 2;
   for (int w : {8, 4}) {
     if ((int64_t)w * 32 * v->R / 2 < m) {

@@ -22,6 +22,10 @@ rpca_status cert_compute(rpca_ctx* c, const float* U, const float* V, rpca_cert*
                          bool reuse = false);
 rpca_status sketch_init(rpca_ctx* c, const float* Omega, float* U, float* V);
 
+// A point is certified at tol when the Sec. 3.4 certificate meets it and so does the cost of
+// the directions the certificate truncated (same relative units).
+static inline bool cert_meets(const rpca_cert& q, double tol) { return q.cert_rel <= tol && q.trunc_rel <= tol; }
+
 // Counter-based normal variates: splitmix64 of (seed, index) -> two uniforms -> Box-Muller.
 __device__ __forceinline__ uint64_t splitmix64(uint64_t z) {
   z += 0x9e3779b97f4a7c15ull;
@@ -274,10 +278,10 @@ static rpca_status job_step(SolveJob& j) {
       if ((s = cert_compute(c, solver_point(c), solver_point(c) + j.mk, &j.cert, false)) != RPCA_OK) return s;
       ++j.cert_evals;
       bool rank_deficit = false;
-      if (j.cert.cert_rel <= c->opt.cert_tol) {
+      if (cert_meets(j.cert, c->opt.cert_tol)) {
         // Same point as the cheap evaluation just made: only the spectral step is added.
         if ((s = cert_compute(c, solver_point(c), solver_point(c) + j.mk, &j.cert, true, true)) != RPCA_OK) return s;
-        if (j.cert.cert_rel <= c->opt.cert_tol) j.certified = true;
+        if (cert_meets(j.cert, c->opt.cert_tol)) j.certified = true;
         else rank_deficit = j.cert.t4 > 0.0;
       }
       j.timer->end();
@@ -353,7 +357,7 @@ static rpca_status job_finish(SolveJob& j, rpca_result* res) {
   r.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - j.t0).count();
   // Ranks above 16 have no certificate here: the solver's gradient test decides.
   if (c->lk) r.status = j.st.stop == STOP_GTOL ? RPCA_OK : RPCA_ENOTCONV;
-  else r.status = j.cert.cert_rel <= c->opt.cert_tol ? RPCA_OK : RPCA_ENOTCONV;
+  else r.status = cert_meets(j.cert, c->opt.cert_tol) ? RPCA_OK : RPCA_ENOTCONV;
   if (r.F < c->F_best) c->F_best = r.F;
   if (res) *res = r;
   if (r.status != RPCA_OK) {
@@ -362,8 +366,8 @@ static rpca_status job_finish(SolveJob& j, rpca_result* res) {
       snprintf(buf, sizeof buf, "stopped after %d iterations (reason %d) before the gradient test (gtol %.1e)",
                r.iters, j.st.stop, c->opt.gtol);
     else
-      snprintf(buf, sizeof buf, "stopped after %d iterations (reason %d) with cert_rel %.3e > %.1e", r.iters,
-               j.st.stop, j.cert.cert_rel, c->opt.cert_tol);
+      snprintf(buf, sizeof buf, "stopped after %d iterations (reason %d) with cert_rel %.3e, trunc_rel %.3e (tol %.1e)",
+               r.iters, j.st.stop, j.cert.cert_rel, j.cert.trunc_rel, c->opt.cert_tol);
     set_err(c, RPCA_ENOTCONV, buf);
   }
   return r.status;

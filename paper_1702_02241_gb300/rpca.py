@@ -36,10 +36,14 @@ class rpca_cert(C.Structure):
     _fields_ = [("cert", C.c_double), ("cert_rel", C.c_double), ("t1", C.c_double), ("t2", C.c_double),
                 ("t3", C.c_double), ("t4", C.c_double), ("normL_F", C.c_double), ("F", C.c_double),
                 ("F_bound", C.c_double), ("gap_bound", C.c_double), ("rank_r", C.c_int),
-                ("krylov_steps", C.c_int), ("sigma1_perp", C.c_double)]
+                ("krylov_steps", C.c_int), ("sigma1_perp", C.c_double), ("F_trunc", C.c_double),
+                ("trunc_rel", C.c_double)]
 
     def asdict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+    def certified(self, tol):
+        return self.cert_rel <= tol and self.trunc_rel <= tol
 
 
 class rpca_fw_result(C.Structure):
@@ -177,6 +181,8 @@ def lib():
     L.rpca_gen_planted.restype = I
     L.rpca_philox4x32_10.argtypes = [P, I64, C.POINTER(C.c_uint32), C.c_uint64, P]
     L.rpca_philox4x32_10.restype = I
+    L.rpca_inject_fault.argtypes = [P, I, I]
+    L.rpca_inject_fault.restype = I
     _lib = L
     return L
 
@@ -189,7 +195,8 @@ EXPORTED = ["rpca_default_options", "rpca_create", "rpca_fg", "rpca_apply", "rpc
             "rpca_ws_predict", "rpca_ws_train_step", "rpca_ws_last_error", "rpca_ws_destroy",
             "rpca_set_warm_start", "rpca_sketch_spectrum", "rpca_ws_sample", "rpca_gen_planted",
             "rpca_philox4x32_10", "rpca_perp_direction", "rpca_perp_directions",
-            "rpca_solve_grow", "rpca_fw_solve", "rpca_aicc", "rpca_tsqr", "rpca_convex_solve"]
+            "rpca_solve_grow", "rpca_fw_solve", "rpca_aicc", "rpca_tsqr", "rpca_convex_solve",
+            "rpca_inject_fault"]
 
 
 class RpcaError(RuntimeError):
@@ -242,6 +249,15 @@ def rpca_fg(ctx, U, V, gU, gV, want_f=True):
     st = lib().rpca_fg(ctx, _ptr(U), _ptr(V), C.byref(f) if want_f else None, _ptr(gU), _ptr(gV))
     _check(st, ctx)
     return f.value
+
+
+RPCA_FAULT_FG_STARVE, RPCA_FAULT_ALLOC = 1, 2
+
+
+def rpca_inject_fault(ctx, kind, count):
+    """Failure injection for tests (see include/rpca.h): starve the next fused launches of
+    ctx, or fail the next device allocations of context set-up."""
+    _check(lib().rpca_inject_fault(ctx, kind, count), ctx)
 
 
 def rpca_fg_noalloc(m, n, X, ldx, k, lam_L, lam_S, U, V, gU, gV, stream=None):

@@ -75,3 +75,11 @@ def test_entry_points_reject_null_context(lib):
     assert lib.rpca_solve(None, None, None, None) == rpca.RPCA_EINVAL
     assert lib.rpca_certificate(None, None, None, None) == rpca.RPCA_EINVAL
     lib.rpca_destroy(None)
+
+
+def test_inject_fault_arguments_without_a_gpu(lib):
+    from paper_1702_02241_gb300 import rpca
+    assert lib.rpca_inject_fault(None, rpca.RPCA_FAULT_FG_STARVE, 1) == rpca.RPCA_EINVAL  # needs a context
+    assert lib.rpca_inject_fault(None, 99, 1) == rpca.RPCA_EINVAL
+    assert lib.rpca_inject_fault(None, rpca.RPCA_FAULT_ALLOC, -1) == rpca.RPCA_EINVAL
+    assert lib.rpca_inject_fault(None, rpca.RPCA_FAULT_ALLOC, 0) == rpca.RPCA_OK

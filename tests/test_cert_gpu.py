@@ -16,7 +16,7 @@ from oracle import certificate as ocert  # noqa: E402
 from oracle import lbfgs, sketch  # noqa: E402
 from paper_1702_02241_gb300 import gen  # noqa: E402
 
-from gpu_util import dev, make_problem  # noqa: E402
+from gpu_util import dev, host, make_problem  # noqa: E402
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -38,6 +38,10 @@ def compare(c, o, lam_L, t4_rel=1e-3):
     assert c.F == pytest.approx(o.F, rel=1e-6)
     assert c.F_bound <= o.F_bound * (1 + 1e-6)
     assert c.cert == pytest.approx(o.cert, rel=1e-3, abs=1e-3 * lam_L)
+    # Cost of the truncated directions (2 lam_L times their singular values) and its
+    # relative form; both zero when nothing was truncated.
+    assert c.F_trunc == pytest.approx(o.F_trunc, rel=1e-4, abs=1e-12 * lam_L * max(o.normL_F, 1.0))
+    assert c.trunc_rel == pytest.approx(o.trunc_rel, rel=1e-4, abs=1e-12)
 
 
 @pytest.mark.parametrize("m,n,k,masked", [(300, 200, 5, False), (257, 190, 3, True), (400, 130, 12, False)])
@@ -140,4 +144,57 @@ def test_certificate_of_rounding_floor_factors(zero_optimal):
     compare(c, o, lam_L)
     if zero_optimal:
         assert c.cert_rel == 0.0
+    P.close()
+
+
+def test_certificate_reports_the_cost_of_a_truncated_direction():
+    """A rank-3 point plus a tiny (5e-4 sigma_1) direction that is not stationary: both sides
+    move it to the complement block, report F_trunc = 2 lam_L sigma_4 and trunc_rel, and the
+    point does not count as certified at 1e-4 although cert_rel may."""
+    g = np.random.default_rng(31)
+    m, n = 1200, 300
+    X = np.asfortranarray(g.normal(size=(m, n)).astype(np.float32))
+    U, V = gen.factors(m, n, 4, seed=8, scale=0.5)
+    Q, _ = np.linalg.qr(np.c_[U[:, :3], g.normal(size=m)])
+    W, _ = np.linalg.qr(np.c_[V[:, :3], g.normal(size=n)])
+    s1 = np.linalg.svd(U[:, :3] @ V[:, :3].T, compute_uv=False)[0]
+    sig = 5e-4 * s1
+    U[:, 3] = math.sqrt(sig) * Q[:, 3]
+    V[:, 3] = math.sqrt(sig) * W[:, 3]
+    U, V = U.astype(np.float32), V.astype(np.float32)
+    lam_L, lam_S = 2.0, 0.5
+    P = make_problem(X, None, 4, lam_L, lam_S)
+    c = P.certificate(dev(U), dev(V))
+    o = ocert.certificate(X, None, U, V, lam_L, lam_S)
+    assert o.rank_r == 3 and o.F_trunc == pytest.approx(2 * lam_L * sig, rel=1e-3)
+    compare(c, o, lam_L)
+    assert c.gap_bound == pytest.approx(o.gap_bound, rel=1e-3)
+    assert not o.certified(1e-4) and not c.certified(1e-4)
+    P.close()
+
+
+def test_spectral_term_where_the_krylov_space_truncates():
+    """t4 > 0 at n = 1000: a planted rank-12 instance solved at k = 8, so that about four
+    directions of P_U1perp D P_V1perp exceed lam_L among 1000; block Lanczos (<= 256 dims)
+    spans a fraction of the space.  t4 and sigma_1 against the oracle's scipy svds at the
+    spectral step's 1e-3."""
+    from paper_1702_02241_gb300 import rpca
+    m, n, k = 20000, 1000, 8
+    lam_S = 1.0 / math.sqrt(m)
+    inst = gen.planted(m, n, rank=12, k=k, p_outlier=0.05, noise=1e-3,
+                       lam_L=2.0 * lam_S * (math.sqrt(m) + math.sqrt(n)), lam_S=lam_S, seed=5)
+    P = make_problem(inst.X, None, k, inst.lam_L, inst.lam_S, max_iter=300)
+    Ud, Vd = dev(np.zeros((m, k))), dev(np.zeros((n, k)))
+    try:
+        P.solve(Ud, Vd)
+    except rpca.RpcaError as e:            # a rank-8 solve of a rank-12 instance cannot certify
+        assert e.status == rpca.RPCA_ENOTCONV
+    U = host(Ud, m).astype(np.float32)
+    V = host(Vd, n).astype(np.float32)
+    c = P.certificate(dev(U), dev(V))
+    o = ocert.certificate(inst.X, None, U, V, inst.lam_L, inst.lam_S, t4_method="svds")
+    assert o.t4 > 1e-2 * inst.lam_L ** 2 and np.sum(o.sigma_perp > inst.lam_L) >= 2
+    assert c.krylov_steps * 8 < n
+    compare(c, o, inst.lam_L)
+    assert c.sigma1_perp == pytest.approx(o.sigma_perp[0], rel=1e-3)
     P.close()

@@ -46,6 +46,14 @@ def check(f, gU, gV, fo, GUo, GVo):
     G = np.concatenate([gU.ravel(), gV.ravel()])
     Go = np.concatenate([GUo.ravel(), GVo.ravel()])
     assert np.linalg.norm(G - Go) <= G_TOL * np.linalg.norm(Go), np.linalg.norm(G - Go) / np.linalg.norm(Go)
+    # Each block on its own: on a tall X the m x k block dominates the joint norm, so an
+    # error confined to the n x k block (D^T U, the cross-lane reduction) could hide there.
+    for a, b, name in ((gU, GUo, "gU"), (gV, GVo, "gV")):
+        nb = np.linalg.norm(b)
+        if nb > 0:
+            assert np.linalg.norm(a - b) <= G_TOL * nb, (name, np.linalg.norm(a - b) / nb)
+        else:
+            assert np.linalg.norm(a) == 0.0, name
 
 
 def random_case(m, n, k, seed, mask_p=None, lam_S=0.3, scale=0.5):

@@ -350,6 +350,47 @@ def test_certificate_moves_tiny_inactive_direction_to_complement():
     assert s.size == 4 and s[3] / s[0] < 1e-3
 
 
+@pytest.mark.parametrize("lam_S", [np.inf, 1.0 / math.sqrt(15)])
+def test_truncation_cost_bounds_the_gap_of_a_nonstationary_direction(lam_S):
+    """A deliberately non-stationary direction of size 5e-4 sigma_1 outside the optimum's
+    range is tiny and inactive, so the certificate truncates it; the gap it leaves, G(L) - G*
+    with G* from FISTA on the convex problem (Sec. 1, Eq. 4), stays below gap_bound once the
+    truncation's cost F_trunc = 2 lam_L sigma is added (convexity of phi and of the nuclear
+    norm), and the point does not count as certified at 1e-4.  In the least-squares case
+    (lam_S = inf, D = L - X changes only along the added direction) the certificate itself is
+    ~0 there, and the bound without F_trunc fails."""
+    m, n = 20, 15
+    g = np.random.default_rng(0)
+    L0 = g.normal(size=(m, 2)) @ g.normal(size=(2, n))
+    S0 = np.where(g.random((m, n)) < 0.1, g.choice([-3.0, 3.0], size=(m, n)), 0.0)
+    X = L0 + S0 + 0.01 * g.normal(size=(m, n))
+    lam_L = 0.8
+    Lc = convex.fista(X, None, lam_L, lam_S, iters=50000, tol=1e-15)
+    Gstar = core.convex_objective(X, None, Lc, lam_L, lam_S)
+    Uc, sc, Vct = np.linalg.svd(Lc)
+    r = int(np.sum(sc > 1e-8 * sc[0]))
+    assert 1 <= r < min(m, n)
+    U, V = convex.balanced_factors(Lc, r + 1)
+    assert ocert.certificate(X, None, U, V, lam_L, lam_S).certified(1e-6)
+    # The added direction: unit u, v orthogonal to the optimum's ranges, sigma = 5e-4 sigma_1.
+    u = Uc[:, r:] @ g.normal(size=m - r)
+    v = Vct[r:].T @ g.normal(size=n - r)
+    u, v = u / np.linalg.norm(u), v / np.linalg.norm(v)
+    sig = 5e-4 * sc[0]
+    U[:, r] = math.sqrt(sig) * u
+    V[:, r] = math.sqrt(sig) * v
+    c = ocert.certificate(X, None, U, V, lam_L, lam_S)
+    gap = core.convex_objective(X, None, U @ V.T, lam_L, lam_S) - Gstar
+    assert c.rank_r == r                                  # the direction went to the complement
+    assert c.F_trunc == pytest.approx(2.0 * lam_L * sig, rel=1e-9)
+    assert gap > 0.1 * lam_L * sig                        # it is not stationary
+    assert gap <= c.gap_bound
+    assert c.trunc_rel > 1e-4 and not c.certified(1e-4)
+    if lam_S == np.inf:
+        old = c.cert * (c.normL_F + c.F_bound / lam_L)    # the bound without the truncation
+        assert c.cert_rel < 1e-9 and old < 1e-3 * gap
+
+
 def test_certificate_of_rounding_floor_factors_is_that_of_zero():
     """Factors at the float32 rounding floor (|L| ~ 1e-44) when the solution is L = 0: every
     direction is negligible, r = 0, and the certificate equals the closed form at L = 0:
