@@ -263,11 +263,14 @@ RPCA_API rpca_status rpca_plan_info(rpca_ctx *c, int which, int64_t *out);
  * rpca_plan_info).  out[0] = 0: the CUDA-core kernel (every product on the fp32x2 FMA pipe);
  * 1: the tensor-core kernel (R^T = X - V U^T and D^T U as warp-level tf32 MMAs with a
  * three-term hi / lo split of every operand, D V on the FMA pipe; float32 X, fg mode,
- * k <= 8, no mask); 2: factor ranks above 16 (GEMMs around an elementwise pass).  out[1] =
+ * k <= 8, no mask); 2: factor ranks above 16 (GEMMs around an elementwise pass); 3: the
+ * tcgen05 kernel (U V^T as tf32 MMAs of the 5th-generation tensor cores, four-term hi / lo
+ * split, accumulated in tensor memory; D V and D^T U on the FMA pipe; float32 X, fg mode,
+ * k <= 6, no mask).  out[1] =
  * row passes per CTA of the tensor-core kernel (its CTA covers out[1] x 32 x warps rows;
  * 1 otherwise).  The CUDA-core form is the default (it is faster on the workloads measured);
- * the environment variable RPCA_FG_KERNEL=mma, set before rpca_create, plans the
- * tensor-core form where it applies.  RPCA_EINVAL for a NULL argument, which out of range,
+ * the environment variable RPCA_FG_KERNEL=mma (or =tc), set before rpca_create, plans the
+ * warp-level tensor-core form (or the tcgen05 form) where it applies.  RPCA_EINVAL for a NULL argument, which out of range,
  * or a plan that cannot be made.
  */
 RPCA_API rpca_status rpca_plan_kernel(rpca_ctx *c, int which, int64_t *out);
@@ -323,6 +326,25 @@ RPCA_API rpca_status rpca_solve_trials(rpca_ctx *c, double *out, int max_rows, i
 RPCA_API rpca_status rpca_fg_noalloc(int64_t m, int64_t n, const float *X, int64_t ldx, int k, double lambda_L,
                                      double lambda_S, const float *U, const float *V, double *f, float *gU,
                                      float *gV, void *cuda_stream);
+
+/*
+ * Row-partitioned evaluation (the multi-GPU form of the pass; Sec. 5.4 scales the video
+ * problem by its rows).  With X and U split by rows over G devices and V shared, F and its
+ * gradient separate: G_{U_g} = D_g V + lam_L U_g is complete on its device, and
+ *   G_V = sum_g D_g^T U_g + lam_L V,   F = sum_g (sum_{Omega_g} psi + lam_L/2 ||U_g||^2) + lam_L/2 ||V||^2.
+ * rpca_fg_rows runs on a context created for one row block X_g (its own m = m_g; X_g is the
+ * caller's pointer into X, 16-byte aligned, so the block starts at a row that is a multiple of
+ * 4 in a column-major X whose ld is a multiple of 4) and writes the shard's terms: gU (m_g x k,
+ * device) = D_g V + lam_L U_g, PV (n x k, device) = D_g^T U_g (no lam_L V), *f_part (host, may be
+ * NULL; the call then does not synchronise) = sum over the shard's observed entries of psi +
+ * lam_L/2 ||U_g||^2.  The caller sums PV and f_part over the shards (one all-reduce of n k + 1
+ * values per evaluation, by its own communicator), then rpca_fg_rows_finish (any shard's
+ * context, same n, k, lam_L) writes gV (n x k, device) = PV_sum + lam_L V and *f (host, may be
+ * NULL) = f_sum + lam_L/2 ||V||^2.  k <= 16.  The paper has no counterpart for the split itself.
+ */
+RPCA_API rpca_status rpca_fg_rows(rpca_ctx *c, const float *U, const float *V, double *f_part, float *gU, float *PV);
+RPCA_API rpca_status rpca_fg_rows_finish(rpca_ctx *c, const float *V, const float *PV_sum, double f_sum, double *f,
+                                         float *gV);
 
 /* Library version string. */
 RPCA_API const char *rpca_version(void);

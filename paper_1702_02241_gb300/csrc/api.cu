@@ -61,6 +61,7 @@ static FgVariant g_same[17][2];
 static FgVariant g_same_x[2][17][2];  // narrow storage of X: bfloat16, FP8 E4M3
 static FgVariant g_apply[3][3][2];
 static FgVariant g_mma[17];  // tensor-core form, unmasked, K = 1..8
+static FgVariant g_tc[17];   // tcgen05 form, unmasked, K = 1..6
 static std::once_flag g_once;
 
 static void init_tables() {
@@ -69,7 +70,9 @@ static void init_tables() {
     memset(g_same_x, 0, sizeof g_same_x);
     memset(g_apply, 0, sizeof g_apply);
     memset(g_mma, 0, sizeof g_mma);
+    memset(g_tc, 0, sizeof g_tc);
     fg_register_mma(g_mma);
+    fg_register_tc(g_tc);
     fg_register_same_small(g_same);
     fg_register_same_bf16(g_same_x[0]);
     fg_register_same_e4m3(g_same_x[1]);
@@ -100,6 +103,12 @@ const FgVariant* fg_mma_variant(int K, bool masked) {
   init_tables();
   if (masked || K < 1 || K > 8) return nullptr;
   return g_mma[K].fn ? &g_mma[K] : nullptr;
+}
+
+const FgVariant* fg_tc_variant(int K, bool masked) {
+  init_tables();
+  if (masked || K < 1 || K > 16) return nullptr;
+  return g_tc[K].fn ? &g_tc[K] : nullptr;
 }
 
 // ---- TMA descriptors -----------------------------------------------------------------------
@@ -294,7 +303,9 @@ static rpca_status time_plan(rpca_ctx* c, const FgPlan& q, double* ms) {
 // is kept (cached per shape in this process).  RPCA_PLAN="warps,splits" forces one
 // configuration; RPCA_AUTOTUNE=0 keeps the model's choice without timing.
 // Cache code of a plan's kernel configuration (warps, stages).
-static int plan_code(const FgPlan& q) { return (q.mma ? (1 << 20) + (q.npass << 10) : 0) + q.WC * 16 + q.nstage; }
+static int plan_code(const FgPlan& q) {
+  return (q.mma ? (1 << 20) + (q.npass << 10) : 0) + (q.tc ? (1 << 24) : 0) + q.WC * 16 + q.nstage;
+}
 
 static rpca_status make_plan(rpca_ctx* c, FgPlan* P, int K, int B, bool same, int side, int xt = FG_X_F32) {
   const bool masked = c->bits != nullptr;
@@ -454,6 +465,79 @@ static rpca_status make_plan(rpca_ctx* c, FgPlan* P, int K, int B, bool same, in
       }
     }
   }
+  // tcgen05 form (fg_tc.cu; float32 X, fg mode, K <= 6, unmasked): four consumer warps of 256
+  // rows (1024 rows per CTA), U V^T from tensor memory, the rest as the CUDA-core form.
+  // Planned on request (RPCA_FG_KERNEL=tc) or beside the CUDA-core form when the environment
+  // variable is unset and RPCA_FG_TC=1.
+  const bool only_tc = kenv && strcmp(kenv, "tc") == 0;
+  const char* tcenv = getenv("RPCA_FG_TC");
+  const bool with_tc = only_tc || (!kenv && tcenv && strcmp(tcenv, "1") == 0);
+  const FgVariant* tv = (same && side == 0 && B == K && xt == FG_X_F32) ? fg_tc_variant(K, masked) : nullptr;
+  if (only_tc && tv) cands.clear();
+  if (tv && with_tc && !(force_wc || force_ncs)) {
+    for (int nst : {6, 4, 3, 2}) {
+      const int BM = 4 * 32 * tv->R;
+      const int nrb = (c->m + BM - 1) / BM;
+      const int maxsplit = std::max(1, (c->n + FG_BJ - 1) / FG_BJ);
+      int last_ncs = -1;
+      for (int ncs_req = 1; ncs_req <= std::min(maxsplit, 256); ++ncs_req) {
+        int BN = (c->n + ncs_req - 1) / ncs_req;
+        BN = (BN + FG_BJ - 1) / FG_BJ * FG_BJ;
+        const int ncs = (c->n + BN - 1) / BN;
+        if (ncs == last_ncs) continue;
+        last_ncs = ncs;
+        const size_t smem = fg_tc_smem_bytes(BN, K, nst, tv->J);
+        ++n_try;
+        if (smem > c->max_smem) {
+          ++n_smem;
+          continue;
+        }
+        const int threads = 6 * 32;
+        if (!allow_smem(tv->fn, smem)) {
+          ++n_attr;
+          continue;
+        }
+        int cps = 0;
+        cudaError_t oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cps, tv->fn, threads, smem);
+        if (oe != cudaSuccess || cps < 1) {
+          if (oe != cudaSuccess) last_occ = oe;
+          cudaGetLastError();
+          ++n_occ;
+          continue;
+        }
+        cps = std::min(cps, 2);  // two CTAs of 256 TMEM columns per SM
+        const double tiles = (double)nrb * ncs;
+        const double tile_bytes = (double)BM * BN * 4.0;
+        constexpr double SM_GBS = 36.0, HBM_GBS = 6700.0;
+        const double kt = std::ceil(tiles / c->nsm);
+        const double cw = std::min<double>(cps, kt);
+        const double waves = std::ceil(kt / cw);
+        const double rate = SM_GBS * std::min(1.0, cw * 4 / 8.0);
+        double t = std::max(waves * cw * tile_bytes / rate, tiles * tile_bytes / HBM_GBS);
+        t += 2.0 * 4.0 * ((double)ncs * c->mpad * B + (double)nrb * c->n * B) / HBM_GBS;
+        FgPlan cand;
+        cand.valid = true;
+        cand.var = tv;
+        cand.K = K;
+        cand.B = B;
+        cand.same = same;
+        cand.side = side;
+        cand.masked = masked;
+        cand.R = tv->R;
+        cand.WC = 4;
+        cand.nrb = nrb;
+        cand.ncs = ncs;
+        cand.BN = BN;
+        cand.threads = threads;
+        cand.smem = smem;
+        cand.cps = cps;
+        cand.nstage = nst;
+        cand.xt = xt;
+        cand.tc = true;
+        cands.push_back({t, cand});
+      }
+    }
+  }
   // A context that shares the GPU (grid_cap > 0) keeps the configurations within its CTA
   // budget, or the smallest grids when none is.
   if (c->grid_cap > 0 && !cands.empty()) {
@@ -492,9 +576,9 @@ static rpca_status make_plan(rpca_ctx* c, FgPlan* P, int K, int B, bool same, in
     // The best few of each form by the model are timed.
     const int per_form = same ? 8 : 6;
     std::vector<int> tried;
-    int n_cuda = 0, n_mma = 0;
+    int n_cuda = 0, n_mma = 0, n_tc = 0;
     for (int i = 0; i < (int)cands.size(); ++i) {
-      int& cnt = cands[i].second.mma ? n_mma : n_cuda;
+      int& cnt = cands[i].second.mma ? n_mma : (cands[i].second.tc ? n_tc : n_cuda);
       if (cnt < per_form) {
         ++cnt;
         tried.push_back(i);
@@ -584,7 +668,7 @@ rpca_status launch_fg(rpca_ctx* c, const FgPlan& P, const FgLaunch& L, cudaStrea
   FgArgs a;
   a.starve = 0;
   a.wait_ns = 0;
-  if (c->fault_fg > 0 && !P.mma) {  // failure injection: this launch's copies are never issued
+  if (c->fault_fg > 0 && !P.mma && !P.tc) {  // failure injection: this launch's copies are never issued
     --c->fault_fg;
     a.starve = 1;
     a.wait_ns = 1000000ull;  // 1 ms
@@ -666,6 +750,7 @@ rpca_status launch_fg(rpca_ctx* c, const FgPlan& P, const FgLaunch& L, cudaStrea
   f.blk = w.blk;
   f.counter = c->ws.counter;
   f.out = L.out ? L.out : c->ws.out;
+  f.vpart = L.vpart;
   if (timed) RPCA_CUDA(c, cudaEventRecord(ev[2], stream));
   if (fuse_ls) {
     RPCA_CUDA(c, launch_finalize_ls(f, P.fin_grid, L, stream));
@@ -786,7 +871,7 @@ rpca_status rpca_plan_kernel(rpca_ctx* c, int which, int64_t* out) {
   if (!c || !out || which < 0 || which > 2) return RPCA_EINVAL;
   const FgPlan* Pp = which == 0 ? &eval_plan(c) : apply_plan(c, which == 1 ? c->k : 0, 1);
   if (!Pp || !Pp->valid) return RPCA_EINVAL;
-  out[0] = Pp->large ? 2 : (Pp->mma ? 1 : 0);
+  out[0] = Pp->large ? 2 : (Pp->mma ? 1 : (Pp->tc ? 3 : 0));
   out[1] = Pp->npass;
   return RPCA_OK;
 }

@@ -30,6 +30,7 @@ struct FgPlan {
   bool large = false;  // k > 16: GEMMs + elementwise pass (largek.cu) instead of the fused kernel
   bool mma = false;    // tensor-core form (fg_mma.cu): WC warps x 32 rows per pass, npass passes
   int npass = 1;
+  bool tc = false;     // tcgen05 form (fg_tc.cu): U V^T on the tensor cores, 4 consumer warps x 256 rows
   CUtensorMap tmX;  // box {32 R rows, FG_BJ columns}; tensor-core form: {32, 16}, 128-byte swizzle
   CUtensorMap tmM;  // bitmap box {WC * R words, FG_BJ columns}
 };
@@ -160,6 +161,7 @@ struct FgLaunch {
   cudaGraphConditionalHandle ls_h = 0;
   int ls_in_graph = 0;
   unsigned int* ls_ticket = nullptr;  // zero between launches (reset by the last block)
+  int vpart = 0;  // row shard: GV <- the raw partial D^T U, no V terms in the sums
 };
 rpca_status launch_fg(rpca_ctx* c, const FgPlan& P, const FgLaunch& L, cudaStream_t stream);
 cudaError_t launch_finalize_ls(const FinArgs& f, int grid, const FgLaunch& L, cudaStream_t stream);  // solver.cu

@@ -30,4 +30,9 @@ void fg_register_mma(FgVariant* tab);               // tensor-core form, K = 1..
 // Tensor-core form of the fused kernel (fg_mma.cu) for forming rank K, or nullptr.
 const FgVariant* fg_mma_variant(int K, bool masked);
 
+void fg_register_tc(FgVariant* tab);  // tcgen05 form, K = 1..6, fg mode, float32 X, unmasked
+// tcgen05 form (fg_tc.cu) for forming rank K, or nullptr; its shared memory for a plan.
+const FgVariant* fg_tc_variant(int K, bool masked);
+size_t fg_tc_smem_bytes(int BN, int K, int nstage, int J);
+
 }  // namespace rpca

@@ -119,7 +119,9 @@ RPCA_DEV void finalize_body(const FinArgs& a) {
     if (q == 0 && live) {
       s = (vs[0][t] + vs[1][t]) + (vs[2][t] + vs[3][t]);
       float g, xt = 0.f, dir = 0.f;
-      if (a.mode != FIN_APPLY) {
+      if (a.vpart) {
+        g = s;  // this row shard's D^T U; the shards' sum and lam_L V come later
+      } else if (a.mode != FIN_APPLY) {
         xt = a.V[e2];
         if (a.dV) xt = fmaf(alpha, a.dV[e2], xt);
         g = a.mode == FIN_FG ? fmaf(lam, xt, s) : s;
@@ -129,9 +131,11 @@ RPCA_DEV void finalize_body(const FinArgs& a) {
         g = s;
       }
       a.GV[e2] = g;
-      nrm_f = xt * xt;
-      gd_f = g * dir;
-      gg_f = g * g;
+      if (!a.vpart) {
+        nrm_f = xt * xt;
+        gd_f = g * dir;
+        gg_f = g * g;
+      }
     }
   }
   if (a.mode == FIN_APPLY) return;

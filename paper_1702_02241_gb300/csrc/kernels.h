@@ -37,6 +37,9 @@ struct FinArgs {
   double* blk;              // [3 * gridDim.x] block partials
   unsigned int* counter;    // zero between launches (reset by the last block)
   double* out;              // [4]: f, g.d, ||g||^2, ||x_t||^2
+  // Row shard of a partitioned problem (rpca_fg_rows): the n x B side writes the raw partial
+  // D^T U (no lam_L V) and adds nothing to the sums (V is shared by every shard).
+  int vpart;
 };
 
 // Finalize grid: FIN_EPT elements per thread of the m x B side (256 threads per block), 64

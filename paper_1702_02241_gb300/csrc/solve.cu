@@ -17,6 +17,7 @@ namespace rpca {
 rpca_status solver_prepare(rpca_ctx* c, const float* U, const float* V);
 rpca_status solver_iterations(rpca_ctx* c, int count);
 rpca_status solver_read_state(rpca_ctx* c, SolverState* out);
+rpca_status solver_read_scalars(rpca_ctx* c, SolverState* out);
 const float* solver_point(rpca_ctx* c);
 rpca_status cert_compute(rpca_ctx* c, const float* U, const float* V, rpca_cert* out, bool full,
                          bool reuse = false);
@@ -261,7 +262,7 @@ static rpca_status job_step(SolveJob& j) {
   rpca_ctx* c = j.c;
   rpca_status s;
   while (true) {
-    if ((s = solver_read_state(c, &j.st)) != RPCA_OK) return s;
+    if ((s = solver_read_scalars(c, &j.st)) != RPCA_OK) return s;
     const SolverState& st = j.st;
     if (!st.active || st.iter >= c->opt.max_iter - j.iter_base) {
       if (j.narrow && c->opt.refine_fp32 && st.iter < c->opt.max_iter - j.iter_base) {

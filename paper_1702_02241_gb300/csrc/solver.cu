@@ -8,7 +8,8 @@
 //   lbfgs_dots_kernel:    all inner products the two-loop recursion needs (one block row
 //                         per history slot); its last block runs the two-loop recursion on
 //                         those scalars (float64) and the stopping tests.
-//   lbfgs_direction_kernel:  d = c_g g + sum_j (c_s[j] s_j + c_y[j] y_j), and g.d.
+//   lbfgs_direction_kernel:  d = c_g g + sum_j (c_s[j] s_j + c_y[j] y_j) (g.d comes from the
+//                            Gram table).
 // The two-loop recursion (Nocedal & Wright Alg. 7.4) is evaluated on inner products only:
 // with q = g - sum a_j y_j and r = gamma q + sum c_j s_j, every dot it needs is a
 // combination of s_i.g, y_i.g, s_i.y_j and y_i.y_j, which are kept in a Gram table and
@@ -359,8 +360,13 @@ __device__ void iteration_finish(SolverState* st) {
   if (!(gd < 0.0)) {
     st->count = 0;
     two_loop_coefs(st);
+    gd = st->coef_g * st->gg;
   }
   LineSearch& L = st->ls;
+  // phi'(0) = g . d from the same inner products: d is a combination of g and the live
+  // pairs, so g . d needs no pass over the vectors.
+  L.g0 = gd;
+  L.g_prev = gd;
   L.a = st->count == 0 ? fmin(1.0, 1.0 / st->g1) : 1.0;
   L.f0 = st->f;
   L.a_prev = 0.0;
@@ -372,7 +378,7 @@ __device__ void iteration_finish(SolverState* st) {
   L.best_a = 0.0;
   L.best_gg = INFINITY;
   L.force = 0;
-  L.state = LS_RUNNING;
+  L.state = (gd < 0.0 && isfinite(gd)) ? LS_RUNNING : LS_FAILED;  // not a descent direction
 }
 
 // Accepting a step: s = x_t - x and y = g_t - g go to the spare history slot, x <- x_t,
@@ -471,7 +477,7 @@ __device__ void scalar_tail(SolverState* gst, const double* fin) {
   __syncthreads();
   if (threadIdx.x == 0) {
     iteration_finish(s);
-    s->gate = s->active;
+    s->gate = (s->active && s->ls.state == LS_RUNNING) ? 1 : 0;
   }
   __syncthreads();
   double* dst = reinterpret_cast<double*>(gst);
@@ -550,16 +556,12 @@ __global__ void __launch_bounds__(256) lbfgs_dots_kernel(SolverArgs a) {
   scalar_tail<NS>(st, fin);
 }
 
-// d = c_g g + sum over ring slots (c_s[j] s_j + c_y[j] y_j); then g.d in float64 starts the
-// line search (phi'(0)).
-// d = coef_g g + sum over live pairs (coef_s s_j + coef_y y_j) and phi'(0) = g . d.  Two
-// elements per thread (one for memory caps above 10) with every load in flight; g . d summed in float32 within a warp,
-// float64 across warps, blocks (two-level ticket tree as in the dots kernel).
+// d = coef_g g + sum over live pairs (coef_s s_j + coef_y y_j), elementwise: the line
+// search's phi'(0) = g . d is formed from the Gram table by the scalar part of the iteration.
+// Two elements per thread (one for memory caps above 10) with every load in flight.
 template <int MCAP>
 __global__ void __launch_bounds__(256) lbfgs_direction_kernel(SolverArgs a) {
   constexpr int NS = MCAP + 1;
-  __shared__ double scr[8];
-  __shared__ bool is_last;
   __shared__ float cs[NS], cy[NS];
   __shared__ float cg;
   SolverState* st = a.st;
@@ -573,7 +575,6 @@ __global__ void __launch_bounds__(256) lbfgs_direction_kernel(SolverArgs a) {
   if (threadIdx.x == 0) cg = (float)st->coef_g;
   __syncthreads();
   constexpr int EPT = NS <= 11 ? 2 : 1;  // elements per thread per pass (register budget)
-  float gd_f = 0.f;
   const int64_t N = a.N;
   for (int64_t e0 = (int64_t)blockIdx.x * blockDim.x * EPT + threadIdx.x; e0 < N;
        e0 += (int64_t)gridDim.x * blockDim.x * EPT) {
@@ -585,8 +586,9 @@ __global__ void __launch_bounds__(256) lbfgs_direction_kernel(SolverArgs a) {
       ge[u] = in ? a.g[e] : 0.f;
 #pragma unroll
       for (int j = 0; j < NS; ++j) {
-        sv[u][j] = in ? a.S[(int64_t)j * N + e] : 0.f;
-        yv[u][j] = in ? a.Y[(int64_t)j * N + e] : 0.f;
+        const bool use = in && ((live >> j) & 1ull);
+        sv[u][j] = use ? a.S[(int64_t)j * N + e] : 0.f;
+        yv[u][j] = use ? a.Y[(int64_t)j * N + e] : 0.f;
       }
     }
 #pragma unroll
@@ -600,56 +602,8 @@ __global__ void __launch_bounds__(256) lbfgs_direction_kernel(SolverArgs a) {
           dv = fmaf(cy[j], yv[u][j], dv);
         }
       }
-      if (e < N) {
-        a.d[e] = dv;
-        gd_f = fmaf(ge[u], dv, gd_f);
-      }
+      if (e < N) a.d[e] = dv;
     }
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) gd_f += __shfl_xor_sync(0xffffffffu, gd_f, o);
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  if (lane == 0) scr[w] = gd_f;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += scr[q];
-    a.blk[blockIdx.x] = t;
-  }
-  const int nb = (int)gridDim.x, grp = blockIdx.x / DOTS_GRP, ngrp = (nb + DOTS_GRP - 1) / DOTS_GRP;
-  const int gsize = min(DOTS_GRP, nb - grp * DOTS_GRP);
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) is_last = atomicAdd(a.counter + 1 + grp, 1u) == (unsigned)gsize - 1;
-  __syncthreads();
-  if (!is_last) return;
-  __threadfence();
-  // Both levels are summed by warp 0: one load per lane (two at the top), a fixed shuffle tree.
-  double* gblk = a.blk + nb;
-  if (threadIdx.x < 32) {
-    double t = lane < gsize ? __ldcg(&a.blk[grp * DOTS_GRP + lane]) : 0.0;
-    t = warp_sum_d(t);
-    if (lane == 0) {
-      gblk[grp] = t;
-      a.counter[1 + grp] = 0u;
-      __threadfence();
-      is_last = atomicAdd(a.counter, 1u) == (unsigned)ngrp - 1;
-    }
-  }
-  __syncthreads();
-  if (!is_last) return;
-  if (threadIdx.x < 32) {
-    __threadfence();
-    double t = 0.0;
-    for (int q = lane; q < ngrp; q += 32) t += __ldcg(&gblk[q]);
-    t = warp_sum_d(t);
-    if (lane != 0) return;
-    *a.counter = 0u;
-    LineSearch& L = st->ls;
-    L.g0 = t;
-    L.g_prev = t;
-    if (!(t < 0.0) || !isfinite(t)) L.state = LS_FAILED;  // not a descent direction
-    st->gate = (st->active && L.state == LS_RUNNING) ? 1 : 0;
   }
 }
 
@@ -1026,6 +980,21 @@ rpca_status solver_read_state(rpca_ctx* c, SolverState* out) {
   SOL_CUDA(cudaMemcpyAsync(b->host, b->st, sizeof(SolverState), cudaMemcpyDeviceToHost, c->stream));
   SOL_CUDA(cudaStreamSynchronize(c->stream));
   memcpy(out, b->host, sizeof(SolverState));
+  return RPCA_OK;
+}
+
+// The scalars the host's loop reads between graph launches (everything but the Gram tables
+// and the log rings): two small copies instead of the whole state.
+rpca_status solver_read_scalars(rpca_ctx* c, SolverState* out) {
+  SolverBuffers* b = c->sol;
+  const size_t a0 = offsetof(SolverState, SY), a1 = offsetof(SolverState, sg), a2 = offsetof(SolverState, log);
+  unsigned char* h = reinterpret_cast<unsigned char*>(b->host);
+  const unsigned char* d = reinterpret_cast<const unsigned char*>(b->st);
+  SOL_CUDA(cudaMemcpyAsync(h, d, a0, cudaMemcpyDeviceToHost, c->stream));
+  SOL_CUDA(cudaMemcpyAsync(h + a1, d + a1, a2 - a1, cudaMemcpyDeviceToHost, c->stream));
+  SOL_CUDA(cudaStreamSynchronize(c->stream));
+  memcpy(out, h, a0);
+  memcpy(reinterpret_cast<unsigned char*>(out) + a1, h + a1, a2 - a1);
   return RPCA_OK;
 }
 

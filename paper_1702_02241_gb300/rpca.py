@@ -181,6 +181,10 @@ def lib():
     L.rpca_gen_planted.restype = I
     L.rpca_philox4x32_10.argtypes = [P, I64, C.POINTER(C.c_uint32), C.c_uint64, P]
     L.rpca_philox4x32_10.restype = I
+    L.rpca_fg_rows.argtypes = [P, P, P, C.POINTER(C.c_double), P, P]
+    L.rpca_fg_rows.restype = I
+    L.rpca_fg_rows_finish.argtypes = [P, P, P, D, C.POINTER(C.c_double), P]
+    L.rpca_fg_rows_finish.restype = I
     L.rpca_inject_fault.argtypes = [P, I, I]
     L.rpca_inject_fault.restype = I
     _lib = L
@@ -196,7 +200,7 @@ EXPORTED = ["rpca_default_options", "rpca_create", "rpca_fg", "rpca_apply", "rpc
             "rpca_set_warm_start", "rpca_sketch_spectrum", "rpca_ws_sample", "rpca_gen_planted",
             "rpca_philox4x32_10", "rpca_perp_direction", "rpca_perp_directions",
             "rpca_solve_grow", "rpca_fw_solve", "rpca_aicc", "rpca_tsqr", "rpca_convex_solve",
-            "rpca_inject_fault"]
+            "rpca_inject_fault", "rpca_fg_rows", "rpca_fg_rows_finish"]
 
 
 class RpcaError(RuntimeError):
@@ -251,6 +255,20 @@ def rpca_fg(ctx, U, V, gU, gV, want_f=True):
     return f.value
 
 
+def rpca_fg_rows(ctx, U, V, gU, PV, want_f=True):
+    """This row shard's terms of F and the gradient; returns f_part (see include/rpca.h)."""
+    f = C.c_double(float("nan"))
+    _check(lib().rpca_fg_rows(ctx, _ptr(U), _ptr(V), C.byref(f) if want_f else None, _ptr(gU), _ptr(PV)), ctx)
+    return f.value
+
+
+def rpca_fg_rows_finish(ctx, V, PV_sum, f_sum, gV):
+    """gV = PV_sum + lam_L V; returns f = f_sum + lam_L/2 ||V||^2."""
+    f = C.c_double(float("nan"))
+    _check(lib().rpca_fg_rows_finish(ctx, _ptr(V), _ptr(PV_sum), float(f_sum), C.byref(f), _ptr(gV)), ctx)
+    return f.value
+
+
 RPCA_FAULT_FG_STARVE, RPCA_FAULT_ALLOC = 1, 2
 
 
@@ -302,7 +320,7 @@ def rpca_plan_info(ctx, which=0) -> dict:
 def rpca_plan_kernel(ctx, which=0) -> dict:
     out = (C.c_int64 * 2)()
     _check(lib().rpca_plan_kernel(ctx, which, out), ctx)
-    return {"kernel": {0: "cuda-core", 1: "tensor-core", 2: "gemm"}[int(out[0])], "npass": int(out[1])}
+    return {"kernel": {0: "cuda-core", 1: "tensor-core", 2: "gemm", 3: "tcgen05"}[int(out[0])], "npass": int(out[1])}
 
 
 def rpca_profile(ctx, enable=True):

@@ -162,7 +162,9 @@ def test_certificate_reports_the_cost_of_a_truncated_direction():
     U[:, 3] = math.sqrt(sig) * Q[:, 3]
     V[:, 3] = math.sqrt(sig) * W[:, 3]
     U, V = U.astype(np.float32), V.astype(np.float32)
-    lam_L, lam_S = 2.0, 0.5
+    # lam_L above the spectrum of D's projection (about 0.5 (sqrt(m) + sqrt(n)) here), so that
+    # t4 = 0 and the spectral step is exact; the point is the truncated direction.
+    lam_L, lam_S = 40.0, 0.5
     P = make_problem(X, None, 4, lam_L, lam_S)
     c = P.certificate(dev(U), dev(V))
     o = ocert.certificate(X, None, U, V, lam_L, lam_S)
