@@ -181,18 +181,39 @@ def ncu_traffic():
     return None
 
 
-def oracle_iteration_seconds(inst, iters=1):
-    """Wall time of `iters` oracle L-BFGS iterations (FP64 NumPy) on the full instance."""
+def oracle_solve_estimate(inst, warm_iters=1, sample_iters=5):
+    """The FP64 NumPy oracle on the full instance, timed by one procedure for both CPU legs:
+    its randomized-SVD start (the start the GPU solve takes: p = 10, q = 2, a seeded Gaussian
+    test matrix), then L-BFGS from that start; the first `warm_iters` iterations are not timed
+    (the first carries the line search's first-step rule), the next `sample_iters` are.
+    Returns (seconds of the start, median seconds per sampled iteration, objective/gradient
+    evaluations per sampled iteration)."""
     import numpy as np
 
-    from oracle import lbfgs
+    from oracle import lbfgs, sketch
     from paper_1702_02241_gb300 import gen
-    U0, V0 = gen.factors(inst.m, inst.n, inst.k, seed=3, scale=0.1)
-    t = time.perf_counter()
-    res = lbfgs.solve(inst.X, inst.mask, U0.astype(np.float64), V0.astype(np.float64), inst.lam_L, inst.lam_S,
-                      max_iter=iters, gtol=0.0)
-    el = time.perf_counter() - t
-    return el / max(res.iters, 1), res.evals / max(res.iters, 1)
+    t0 = time.perf_counter()
+    Om = gen.gaussian(inst.n, inst.k + 10, seed=11)
+    U0, V0 = sketch.rsvd_init(inst.X, inst.mask, inst.k, Om)
+    t_init = time.perf_counter() - t0
+    stamps = []
+
+    def cb(it, U, V, f):
+        stamps.append(time.perf_counter())
+        return False
+
+    stamps.append(time.perf_counter())
+    res = lbfgs.solve(inst.X, inst.mask, np.asarray(U0, np.float64), np.asarray(V0, np.float64), inst.lam_L,
+                      inst.lam_S, max_iter=warm_iters + sample_iters, gtol=0.0, callback=cb)
+    dt = [b - a for a, b in zip(stamps[:-1], stamps[1:])][warm_iters:]
+    per_iter = statistics.median(dt) if dt else float("nan")
+    return t_init, per_iter, res.evals / max(res.iters, 1)
+
+
+def oracle_sample_text(sample_iters, warm_iters):
+    return (f"FP64 NumPy oracle on the full 76800x1000 matrix from its randomized-SVD start: the start "
+            f"timed, then {sample_iters} L-BFGS iterations after {warm_iters} untimed (median per "
+            f"iteration) x {SOLVE_ITERS_HINT} iterations (the GPU solve's count)")
 
 
 def cores():
@@ -208,22 +229,20 @@ def run_reference(args):
         return 0
     from paper_1702_02241_gb300 import gen
     inst = gen.video_76800x1000(0)
-    for _ in range(args.warmup):
-        oracle_iteration_seconds(inst, 1)
-    per = []
-    for _ in range(args.steps):
-        s, _ = oracle_iteration_seconds(inst, 1)
-        per.append(s)
-    per_iter = statistics.median(per)
-    value = per_iter * SOLVE_ITERS_HINT
+    # One oracle run: warm-up iterations untimed, then one timed iteration per step (at least
+    # five in all), so that the whole run stays within a few minutes.
+    warm = max(1, args.warmup)
+    sample = max(5, args.steps)
+    t_init, per_iter, evals = oracle_solve_estimate(inst, warm, sample)
+    value = t_init + per_iter * SOLVE_ITERS_HINT
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_iter * 1e3, "higher_is_better": False,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "m": inst.m, "n": inst.n, "k": inst.k, "lam_L": inst.lam_L,
                        "lam_S": inst.lam_S},
             "cpu_baseline": {"value": value, "unit": "s", "cores": cores(), "kind": "oracle",
-                             "sample": f"one FP64 NumPy L-BFGS iteration on the full 76800x1000 matrix per step, "
-                                       f"median over {args.steps} steps, x {SOLVE_ITERS_HINT} iterations"},
+                             "sample": oracle_sample_text(sample, warm), "start_s": t_init,
+                             "per_iteration_s": per_iter, "evals_per_iteration": evals},
             "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -345,11 +364,11 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        per_iter, _ = oracle_iteration_seconds(inst, 2)
-        iters = int(statistics.median([r.iters for r in results])) if results else SOLVE_ITERS_HINT
-        cpu = {"value": per_iter * iters, "unit": "s", "cores": cores(), "kind": "oracle",
-               "sample": f"2 FP64 NumPy L-BFGS iterations on the full 76800x1000 matrix, per-iteration time "
-                         f"x {iters} iterations (the GPU solve's count)"}
+        # The same procedure as the reference arm (bench.py --impl reference).
+        t_init, per_iter, evals = oracle_solve_estimate(inst, 1, 5)
+        cpu = {"value": t_init + per_iter * SOLVE_ITERS_HINT, "unit": "s", "cores": cores(), "kind": "oracle",
+               "sample": oracle_sample_text(5, 1), "start_s": t_init, "per_iteration_s": per_iter,
+               "evals_per_iteration": evals}
 
     r0 = results[-1]
     line = {
@@ -683,6 +702,55 @@ PRECISION_WORKLOAD = ("video 110592x2000 (384x288 frames x 2000, background rank
                       "FP8 E4M3 (per-column scale) with float32 refinement")
 
 
+def narrow_phase_errors(inst, dtype, P32, U32, V32):
+    """Errors of the narrow-storage phase alone against the certified float32 solution
+    (U32, V32) of the same instance: relative objective (both objectives from the library's
+    float32 pass over X), ||L - L*||_F / ||L*||_F (from k x k Grams), and the symmetric
+    difference of the S supports {|X - L| > lam_S on Omega} over the observed entries (float32,
+    column chunks on the device).  Measurement only: the solve itself is the library's."""
+    import torch
+
+    from paper_1702_02241_gb300 import rpca
+    from paper_1702_02241_gb300.engine import Problem
+    m, n, k = inst.m, inst.n, inst.k
+    opt = rpca.rpca_default_options()
+    opt.init = rpca.RPCA_INIT_SKETCH
+    opt.max_iter = 3000
+    opt.cert_every = 0
+    opt.gtol = 1e-6
+    opt.x_dtype = dtype
+    opt.refine_fp32 = 0
+    P = Problem(inst.X, inst.mask, k, inst.lam_L, inst.lam_S, opt=opt, Xd=P32.Xd, Md=P32.Md)
+    U = torch.zeros((k, m), dtype=torch.float32, device="cuda")
+    V = torch.zeros((k, n), dtype=torch.float32, device="cuda")
+    t0 = time.perf_counter()
+    r = rpca.rpca_solve(P.ctx, U, V)
+    t_narrow = time.perf_counter() - t0
+    P.close()
+    gU, gV = torch.empty_like(U), torch.empty_like(V)
+    F_n = rpca.rpca_fg(P32.ctx, U, V, gU, gV)
+    F_s = rpca.rpca_fg(P32.ctx, U32, V32, gU, gV)
+    A = torch.cat([U, -U32], 0).double()
+    B = torch.cat([V, V32], 0).double()
+    d2 = float(((A @ A.T) * (B @ B.T)).sum())
+    s2 = float(((U32.double() @ U32.double().T) * (V32.double() @ V32.double().T)).sum())
+    lerr = (max(d2, 0.0) / s2) ** 0.5
+    diff = 0
+    obs = 0
+    lam = float(inst.lam_S)
+    for c0 in range(0, n, 128):
+        c1 = min(n, c0 + 128)
+        Xc = P32.Xd[c0:c1, :m].T
+        Mc = (P32.Md[c0:c1, :m].T != 0) if P32.Md is not None else torch.ones_like(Xc, dtype=torch.bool)
+        sa = ((Xc - U.T @ V[:, c0:c1]).abs() > lam) & Mc
+        sb = ((Xc - U32.T @ V32[:, c0:c1]).abs() > lam) & Mc
+        diff += int((sa ^ sb).sum())
+        obs += int(Mc.sum())
+    return {"iters": r.iters, "seconds": t_narrow, "objective_rel_err": abs(F_n - F_s) / abs(F_s),
+            "L_rel_err": lerr, "support_diff_frac": diff / max(obs, 1),
+            "reference": "certified float32 solve of the same instance (cert_rel <= 1e-4)"}
+
+
 def run_precision(args):
     """The precision form: one step = one solve to cert_rel <= 1e-4 on the masked video workload
     with X stored in float32, bfloat16 or E4M3 (the narrow forms iterate on the library's narrow
@@ -745,10 +813,19 @@ def run_precision(args):
         nbytes = m * n * xbytes + (m * n / 8.0) + 2 * (m + n) * k * 4  # X, bitmap, factors
         r = res[-1]
         per[name] = {"solve_s": t_solve, "iters": r.iters, "evals": r.evals, "cert_rel": r.cert.cert_rel,
-                     "certified": bool(r.status == rpca.RPCA_OK and r.cert.cert_rel <= 1e-4), "F": r.F,
+                     "certified": bool(r.status == rpca.RPCA_OK and r.cert.certified(1e-4)), "F": r.F,
                      "fg_kernel_ms": fg_ms, "fg_gbs": nbytes / (fg_ms / 1e3) / 1e9, "bytes_per_pass": nbytes}
-        P.close()
+        if name == "f32":
+            P32, U32, V32 = P, U, V  # the certified float32 solution: the reference point below
+        else:
+            P.close()
     clk = clocks.stop()
+    # The narrow phase alone (iterations on the narrow copy, no float32 refinement, stopped by
+    # its gradient test) against the certified float32 solution: the objective on float32 X
+    # (the library's pass), ||L - L*||_F / ||L*||_F and the S-support difference.
+    for name in ("bf16", "e4m3"):
+        per[name]["narrow_phase"] = narrow_phase_errors(inst, forms[name], P32, U32, V32)
+    P32.close()
     best = min(per, key=lambda q: per[q]["solve_s"])
     peak, peak_kind = load_peaks()
     line = {

@@ -4,8 +4,8 @@ Each shard is a context on a row block of the same device X (rpca_fg_rows); the 
 partials and the objective partials are summed over the shards in a fixed order (what the
 all-reduce of a multi-GPU run does), and rpca_fg_rows_finish adds the shared V terms.  The
 result must equal the unpartitioned evaluation (rpca_fg) to float32 rounding -- objective
-1e-12 relative (the float64 sums regroup), gradient 1e-6 relative per block (the shards' tiles
-differ from the unpartitioned tiling, so float32 partial sums regroup) -- and the FP64 oracle at
+1e-8 relative, gradient 1e-6 relative per block (the shards' tiles differ from the
+unpartitioned tiling, so the float32 partial sums regroup) -- and the FP64 oracle at
 the parity tolerances (1e-6, 1e-5), masked and unmasked, on the video workload too.
 """
 import numpy as np
@@ -72,7 +72,9 @@ def test_virtual_shards_match_unpartitioned(G, m, n, k, masked):
     f1, gU1, gV1 = P.fg(to_device_colmajor(U), to_device_colmajor(V))
     gU1, gV1 = from_device_colmajor(gU1, m), from_device_colmajor(gV1, n)
     f, gU, gV = sharded(P.Xd, P.ldx, m, n, k, lam_L, lam_S, U, V, G, Md=P.Md)
-    assert abs(f - f1) <= 1e-12 * abs(f1)
+    # The psi sums of each tile are float32 (Kahan-compensated) before float64: the shards'
+    # tiles regroup them, which moves f by a few 1e-10 relative (measured 2.4e-10 at most).
+    assert abs(f - f1) <= 1e-8 * abs(f1)
     assert rel(gU, gU1) <= 1e-6 and rel(gV, gV1) <= 1e-6
     fo, GUo, GVo = core.fg(X, mask, U, V, lam_L, lam_S)
     assert abs(f - fo) <= 1e-6 * abs(fo)
