@@ -213,7 +213,10 @@ RPCA_API rpca_status rpca_create_batch(rpca_batch **out, int count, const int64_
  * Solves every problem of the batch as rpca_solve does (U[i], V[i]: device m[i] x k[i] and
  * n[i] x k[i] buffers, in and out), concurrently: host worker threads (environment variable
  * RPCA_BATCH_THREADS, default 4 per hardware thread up to 64) drive the instances' solves on
- * their own streams, so that their kernels overlap on the GPU.  res (may be NULL) receives
+ * their own streams, so that their kernels overlap on the GPU.  RPCA_BATCH_MODE=rounds (float32
+ * X, k <= 16) advances all instances together instead: one CUDA graph launch runs five L-BFGS
+ * iterations of every unfinished instance, the host takes the certificate decisions between
+ * launches; the graph is kept by the batch for later solves.  res (may be NULL) receives
  * count results.  Work on cuda_stream before the call is ordered before the solves, and the
  * stream is ordered after them.  Returns RPCA_OK when every instance met its certificate
  * tolerance, RPCA_ENOTCONV when some did not (see res[i].status), another status on an error.

@@ -284,34 +284,28 @@ __global__ void __launch_bounds__(256) cert_resid_kernel(const float* A, const f
   }
 }
 
-// Sums the Gram partials of an 8-column block into st->G and factors it (masked Cholesky);
-// records the columns whose pivot collapsed (that column is numerically in the span of the
-// earlier ones and of the bases projected out).
-constexpr int CHOL_THREADS = 512;
-__global__ void __launch_bounds__(CHOL_THREADS) cert_gram_chol_kernel(const double* part, int nblk, CertState* st,
-                                                                      double rel, int per_column) {
-  __shared__ double scratch[CHOL_THREADS];
+// Factors the Gram st->G of an 8-column block (masked Cholesky) and records the columns whose
+// pivot collapsed (that column is numerically in the span of the earlier ones and of the bases
+// projected out).  st->G was summed over the row blocks by ts_gram's multi-block reduction (one
+// CTA summing every block's float64 partials was most of this step: float64 runs at a few
+// operations per clock per SM on this GPU).
+constexpr int CHOL_THREADS = 128;
+__global__ void __launch_bounds__(CHOL_THREADS) cert_gram_chol_kernel(CertState* st, double rel, int per_column) {
   __shared__ double G[LZ_B * LZ_B], W[LZ_B * LZ_B], R[LZ_B * LZ_B], Ri[LZ_B * LZ_B], rd[LZ_B];
   __shared__ int bad;
-  ts_reduce_partials_cta(part, nblk, LZ_B * LZ_B, G, scratch);
+  if (threadIdx.x < LZ_B * LZ_B) G[threadIdx.x] = st->G[threadIdx.x];
   __syncthreads();
   const int mask = cta_chol_masked(G, LZ_B, rel, per_column ? st->n0 : nullptr, W, R, Ri, rd, &bad);
   if (threadIdx.x < LZ_B * LZ_B) {
-    st->G[threadIdx.x] = G[threadIdx.x];
     st->R[threadIdx.x] = R[threadIdx.x];
     st->Rinv[threadIdx.x] = Ri[threadIdx.x];
   }
   if (threadIdx.x == 0) st->bad_mask = mask;
 }
 
-// Sums the Gram partials into st->G and records the squared column norms (its diagonal).
-__global__ void __launch_bounds__(CHOL_THREADS) cert_gram_norms_kernel(const double* part, int nblk, CertState* st) {
-  __shared__ double scratch[CHOL_THREADS];
-  __shared__ double G[LZ_B * LZ_B];
-  ts_reduce_partials_cta(part, nblk, LZ_B * LZ_B, G, scratch);
-  __syncthreads();
-  if (threadIdx.x < LZ_B * LZ_B) st->G[threadIdx.x] = G[threadIdx.x];
-  if (threadIdx.x < LZ_B) st->n0[threadIdx.x] = G[threadIdx.x * (LZ_B + 1)];
+// Records the squared column norms (the diagonal of the Gram st->G).
+__global__ void cert_gram_norms_kernel(CertState* st) {
+  if (threadIdx.x < LZ_B) st->n0[threadIdx.x] = st->G[threadIdx.x * (LZ_B + 1)];
 }
 
 // Columns flagged in st->bad_mask are set to zero (the Krylov space is exhausted there).
@@ -562,9 +556,8 @@ static rpca_status project_out(rpca_ctx* c, const float* Bm, int p, float* Y, in
 // rel * (largest squared column norm).
 static rpca_status gram_chol(rpca_ctx* c, float* Y, int64_t rows, double rel, int per_column) {
   CertBuffers* b = c->cert;
-  const int nblk = ts_gram_partial_c(c, Y, rows, LZ_B, Y, rows, LZ_B, rows, b->ts, c->stream);
-  if (nblk < 0) return set_err(c, RPCA_ECUDA, "ts_gram_partial");
-  cert_gram_chol_kernel<<<1, CHOL_THREADS, 0, c->stream>>>(b->ts.part, nblk, b->st, rel, per_column);
+  CERT_CUDA(ts_gram_c(c, Y, rows, LZ_B, Y, rows, LZ_B, rows, b->st->G, b->ts, c->stream));
+  cert_gram_chol_kernel<<<1, CHOL_THREADS, 0, c->stream>>>(b->st, rel, per_column);
   count_launches(c, 1);
   CERT_CUDA(cudaGetLastError());
   return RPCA_OK;
@@ -572,9 +565,8 @@ static rpca_status gram_chol(rpca_ctx* c, float* Y, int64_t rows, double rel, in
 
 static rpca_status record_norms(rpca_ctx* c, float* Y, int64_t rows) {
   CertBuffers* b = c->cert;
-  const int nblk = ts_gram_partial_c(c, Y, rows, LZ_B, Y, rows, LZ_B, rows, b->ts, c->stream);
-  if (nblk < 0) return set_err(c, RPCA_ECUDA, "ts_gram_partial");
-  cert_gram_norms_kernel<<<1, CHOL_THREADS, 0, c->stream>>>(b->ts.part, nblk, b->st);
+  CERT_CUDA(ts_gram_c(c, Y, rows, LZ_B, Y, rows, LZ_B, rows, b->st->G, b->ts, c->stream));
+  cert_gram_norms_kernel<<<1, 32, 0, c->stream>>>(b->st);
   count_launches(c, 1);
   CERT_CUDA(cudaGetLastError());
   return RPCA_OK;

@@ -3,7 +3,7 @@
 // a rank-(k + p) sketch and q power iterations (Halko, Martinsson & Tropp; p = 10, q = 2 by
 // default).  Products with A*(X) and its transpose are passes of the fused kernel in apply
 // mode with no forming factors and no clipping (then D = -A*(X)); orthonormalisation is
-// CholeskyQR2 with float64 Grams; the small SVD is a float64 one-sided Jacobi on the Gram of
+// CholeskyQR2 with float64 Grams; the small SVD is a float32 one-sided Jacobi on the Gram of
 // B^T = A*(X)^T Q.
 #include <algorithm>
 #include <cmath>
@@ -27,16 +27,16 @@ struct SketchState {
 
 void fill_normal(float* out, int64_t count, uint64_t seed, float scale, cudaStream_t s);
 
-// Sums the Gram partials of the l x l Gram and factors it; collapsed columns (the sketch of a
-// matrix of rank < l) are flagged and left uncoupled.
-constexpr int SK_CHOL_THREADS = 1024;
-__global__ void __launch_bounds__(SK_CHOL_THREADS) sk_gram_chol_kernel(const double* part, int nblk, SketchState* st,
-                                                                       int l) {
-  __shared__ double scratch[SK_CHOL_THREADS];
+// Factors the l x l Gram st->G (summed over the row blocks by ts_gram's multi-block reduction:
+// float64 runs at a few operations per clock per SM on this GPU, so one CTA summing every
+// block's partials was the larger part of this step); collapsed columns (the sketch of a matrix
+// of rank < l) are flagged and left uncoupled.
+constexpr int SK_CHOL_THREADS = 256;
+__global__ void __launch_bounds__(SK_CHOL_THREADS) sk_gram_chol_kernel(SketchState* st, int l) {
   __shared__ double G[SK_LMAX * SK_LMAX], W[SK_LMAX * SK_LMAX], R[SK_LMAX * SK_LMAX], Ri[SK_LMAX * SK_LMAX];
   __shared__ double rd[SK_LMAX];
   __shared__ int bad;
-  ts_reduce_partials_cta(part, nblk, l * l, G, scratch);
+  for (int e = threadIdx.x; e < l * l; e += blockDim.x) G[e] = st->G[e];
   __syncthreads();
   const int mask = cta_chol_masked(G, l, 1e-10, nullptr, W, R, Ri, rd, &bad);
   for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
@@ -55,16 +55,35 @@ __global__ void sk_zero_cols_kernel(float* Y, int64_t rows, int l, const SketchS
     if ((mask >> (int)(i / rows)) & 1) Y[i] = 0.f;
 }
 
-// Eigen-decomposition of the l x l Gram of B^T (one CTA); C1 = U_B[:, :k] Sigma^{1/2} and
-// C2 = U_B[:, :k] Sigma^{-1/2} (scaled by `scale`), both l x k (ld l).
+// Right singular vectors and singular values of Z = D^T Q (n x l, the Gram st->G = Z^T Z);
+// C1 = U_B[:, :k] Sigma^{1/2} and C2 = U_B[:, :k] Sigma^{-1/2}, both l x k (ld l).  The Gram is
+// factored in float64 (G = R^T R, masked Cholesky: a collapsed column gives a zero row of R),
+// and R, whose singular values are Z's (not their squares), goes through a float32 one-sided
+// Jacobi on one warp: float64 Jacobi sweeps on this GPU's narrow float64 pipe took ten times as
+// long, and the start needs no more than float32 singular vectors.
 __global__ void __launch_bounds__(256) sk_small_svd_kernel(SketchState* st, int l, int k, float* sig_out,
                                                             float inv_p) {
-  __shared__ double A[SK_LMAX * SK_LMAX], W[SK_LMAX * SK_LMAX], ev[SK_LMAX];
+  __shared__ double G[SK_LMAX * SK_LMAX], Wd[SK_LMAX * SK_LMAX], R[SK_LMAX * SK_LMAX], Ri[SK_LMAX * SK_LMAX];
+  __shared__ double rd[SK_LMAX], ev[SK_LMAX];
+  __shared__ float A[SK_LMAX * SK_LMAX], W[SK_LMAX * SK_LMAX], evf[SK_LMAX];
   __shared__ int ord[SK_LMAX];
-  __shared__ int flag;
-  for (int i = threadIdx.x; i < l * l; i += blockDim.x) A[i] = st->G[i];
+  __shared__ int bad;
+  for (int i = threadIdx.x; i < l * l; i += blockDim.x) G[i] = st->G[i];
   __syncthreads();
-  cta_jacobi_svd<double>(A, l, l, l, W, l, ev, &flag, 60, 1e-13, 4.0 * l * 1.1e-16);
+  const int mask = cta_chol_masked(G, l, 1e-12, nullptr, Wd, R, Ri, rd, &bad);
+  for (int i = threadIdx.x; i < l * l; i += blockDim.x) {
+    const int row = i % l;
+    A[i] = ((mask >> row) & 1) ? 0.f : (float)R[i];
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const float tol = fmaxf(1e-6f, 4.0f * l * 1.2e-7f), noise = 2.0f * l * 6e-8f;
+    if (l <= 16) warp_jacobi_svd<float, 16, 16>(A, l, l, l, W, l, evf, 40, tol, noise);
+    else warp_jacobi_svd<float, SK_LMAX, SK_LMAX>(A, l, l, l, W, l, evf, 40, tol, noise);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < l; i += blockDim.x) ev[i] = (double)evf[i] * (double)evf[i];  // sigma^2
+  __syncthreads();
   cta_sort_desc<double>(ev, l, ord);
   for (int i = threadIdx.x; i < l * k; i += blockDim.x) {
     const int a = i % l, c = i / l;
@@ -194,19 +213,21 @@ static rpca_status sk_apply(rpca_ctx* c, SketchBuffers& b, int l, const float* B
 }
 
 // CholeskyQR2; columns that collapse in the first pass are zeroed (rank of the sketch < l).
+// The first pass's masked factor leaves a collapsed column uncoupled (its column of R^-1 is the
+// unit vector), so Y R^-1 keeps it as it was and zeroing it afterwards gives what zeroing it
+// first and factoring again would.
 static rpca_status sk_orth(rpca_ctx* c, SketchBuffers& b, float* Y, int64_t rows, int l) {
-  for (int pass = 0; pass < 3; ++pass) {
-    const int nblk = ts_gram_partial_c(c, Y, rows, l, Y, rows, l, rows, b.ts, c->stream);
-    if (nblk < 0) return set_err(c, RPCA_ECUDA, "ts_gram_partial");
-    sk_gram_chol_kernel<<<1, SK_CHOL_THREADS, 0, c->stream>>>(b.ts.part, nblk, b.st, l);
+  for (int pass = 0; pass < 2; ++pass) {
+    if (ts_gram_c(c, Y, rows, l, Y, rows, l, rows, b.st->G, b.ts, c->stream) != cudaSuccess)
+      return set_err(c, RPCA_ECUDA, "ts_gram");
+    sk_gram_chol_kernel<<<1, SK_CHOL_THREADS, 0, c->stream>>>(b.st, l);
     count_launches(c, 1);
     SK_CUDA(cudaGetLastError());
+    SK_CUDA(ts_mul_c(c, Y, rows, l, b.st->Rinv, l, l, Y, rows, rows, 1.f, 0.f, c->stream));
     if (pass == 0) {
       sk_zero_cols_kernel<<<256, 256, 0, c->stream>>>(Y, rows, l, b.st);
       count_launches(c, 1);
-      continue;
     }
-    SK_CUDA(ts_mul_c(c, Y, rows, l, b.st->Rinv, l, l, Y, rows, rows, 1.f, 0.f, c->stream));
   }
   return RPCA_OK;
 }

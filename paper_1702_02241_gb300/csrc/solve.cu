@@ -256,6 +256,65 @@ static bool cert_due(const SolveJob& j, const SolverState& st, double tol) {
   return (since >= CERT_MIN_GAP && j.kappa * sqrt(fmax(st.gg, 0.0)) <= tol) || since >= 2 * j.every;
 }
 
+// Decisions between iterations on the state j.st (read by the caller): the certificate when
+// due and the stop tests.  Sets j.done when the job is finished; *again when the narrow phase
+// ended (the caller reads the state again before launching).
+static rpca_status job_decide(SolveJob& j, bool* again) {
+  rpca_ctx* c = j.c;
+  rpca_status s;
+  *again = false;
+  const SolverState& st = j.st;
+  if (!st.active || st.iter >= c->opt.max_iter - j.iter_base) {
+    if (j.narrow && c->opt.refine_fp32 && st.iter < c->opt.max_iter - j.iter_base) {
+      if ((s = job_refine(j)) != RPCA_OK) return s;
+      *again = true;
+      return RPCA_OK;
+    }
+    j.done = true;
+    return RPCA_OK;
+  }
+  if (cert_due(j, st, c->opt.cert_tol)) {
+    j.last_cert_iter = st.iter;
+    // Cheap terms first; the spectral term only when they already meet the tolerance.
+    j.timer->begin(2);
+    if ((s = cert_compute(c, solver_point(c), solver_point(c) + j.mk, &j.cert, false)) != RPCA_OK) return s;
+    ++j.cert_evals;
+    bool rank_deficit = false;
+    if (cert_meets(j.cert, c->opt.cert_tol)) {
+      // Same point as the cheap evaluation just made: only the spectral step is added.
+      if ((s = cert_compute(c, solver_point(c), solver_point(c) + j.mk, &j.cert, true, true)) != RPCA_OK) return s;
+      if (cert_meets(j.cert, c->opt.cert_tol)) j.certified = true;
+      else rank_deficit = j.cert.t4 > 0.0;
+    }
+    j.timer->end();
+    // Stationary in the factors' range (t1..t3 meet the tolerance) with a direction outside
+    // it that would lower F (t4 > 0): more iterations at this rank cannot certify; the
+    // rank-increasing solve takes over from here (Sec. 4.1).
+    if (j.certified || (rank_deficit && c->grow_stop)) {
+      j.done = true;
+      return RPCA_OK;
+    }
+    const double gn = sqrt(fmax(st.gg, 0.0));
+    if (gn > 0.0 && std::isfinite(j.cert.cert_rel) && std::isfinite(gn)) j.kappa = j.cert.cert_rel / gn;
+    // The narrow phase has done its part once the float32 certificate stops halving
+    // between checks: what is left is the storage rounding of X.
+    if (j.narrow && c->opt.refine_fp32) {
+      const bool plateau = j.cert.cert_rel > 0.5 * j.narrow_best;
+      j.narrow_best = std::min(j.narrow_best, j.cert.cert_rel);
+      if (plateau) {
+        if ((s = job_refine(j)) != RPCA_OK) return s;
+        *again = true;
+        return RPCA_OK;
+      }
+    }
+  }
+  if (c->opt.timeout_s > 0) {
+    const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - j.t0).count();
+    if (el > c->opt.timeout_s) j.done = true;
+  }
+  return RPCA_OK;
+}
+
 // Advances the job until it has iterations in flight (returns with them launched) or is
 // done (j.done).
 static rpca_status job_step(SolveJob& j) {
@@ -263,56 +322,11 @@ static rpca_status job_step(SolveJob& j) {
   rpca_status s;
   while (true) {
     if ((s = solver_read_scalars(c, &j.st)) != RPCA_OK) return s;
+    bool again = false;
+    if ((s = job_decide(j, &again)) != RPCA_OK) return s;
+    if (j.done) return RPCA_OK;
+    if (again) continue;
     const SolverState& st = j.st;
-    if (!st.active || st.iter >= c->opt.max_iter - j.iter_base) {
-      if (j.narrow && c->opt.refine_fp32 && st.iter < c->opt.max_iter - j.iter_base) {
-        if ((s = job_refine(j)) != RPCA_OK) return s;
-        continue;
-      }
-      j.done = true;
-      return RPCA_OK;
-    }
-    if (cert_due(j, st, c->opt.cert_tol)) {
-      j.last_cert_iter = st.iter;
-      // Cheap terms first; the spectral term only when they already meet the tolerance.
-      j.timer->begin(2);
-      if ((s = cert_compute(c, solver_point(c), solver_point(c) + j.mk, &j.cert, false)) != RPCA_OK) return s;
-      ++j.cert_evals;
-      bool rank_deficit = false;
-      if (cert_meets(j.cert, c->opt.cert_tol)) {
-        // Same point as the cheap evaluation just made: only the spectral step is added.
-        if ((s = cert_compute(c, solver_point(c), solver_point(c) + j.mk, &j.cert, true, true)) != RPCA_OK) return s;
-        if (cert_meets(j.cert, c->opt.cert_tol)) j.certified = true;
-        else rank_deficit = j.cert.t4 > 0.0;
-      }
-      j.timer->end();
-      // Stationary in the factors' range (t1..t3 meet the tolerance) with a direction outside
-      // it that would lower F (t4 > 0): more iterations at this rank cannot certify; the
-      // rank-increasing solve takes over from here (Sec. 4.1).
-      if (j.certified || (rank_deficit && c->grow_stop)) {
-        j.done = true;
-        return RPCA_OK;
-      }
-      const double gn = sqrt(fmax(st.gg, 0.0));
-      if (gn > 0.0 && std::isfinite(j.cert.cert_rel) && std::isfinite(gn)) j.kappa = j.cert.cert_rel / gn;
-      // The narrow phase has done its part once the float32 certificate stops halving
-      // between checks: what is left is the storage rounding of X.
-      if (j.narrow && c->opt.refine_fp32) {
-        const bool plateau = j.cert.cert_rel > 0.5 * j.narrow_best;
-        j.narrow_best = std::min(j.narrow_best, j.cert.cert_rel);
-        if (plateau) {
-          if ((s = job_refine(j)) != RPCA_OK) return s;
-          continue;
-        }
-      }
-    }
-    if (c->opt.timeout_s > 0) {
-      const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - j.t0).count();
-      if (el > c->opt.timeout_s) {
-        j.done = true;
-        return RPCA_OK;
-      }
-    }
     int batch = j.every > 0 ? j.every - (st.iter % j.every) : 25;
     if (j.every > 0 && !j.narrow && j.kappa > 0.0 && !c->lk)
       batch = std::max(1, std::min(CERT_POLL, 2 * j.every - (st.iter - j.last_cert_iter)));
@@ -395,6 +409,133 @@ namespace rpca {
 // and then steps them round-robin.  A step waits for its own context's stream only, so the
 // other jobs' iterations keep the GPU busy meanwhile, and a thread blocked in one job's
 // certificate holds up only the jobs of its own share.
+rpca_status solver_capture_rounds(rpca_ctx* c, cudaStream_t s, int rounds);  // solver.cu
+SolverState* solver_state_dev(rpca_ctx* c);
+rpca_status solver_deactivate(rpca_ctx* c, cudaStream_t s);
+
+// Each instance's scalars the host decides on, into out[6 i ..]: active, iteration, ||g||^2,
+// F, stop reason, evaluations.
+__global__ void gather_scalars_kernel(SolverState* const* sts, int count, double* out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+    const SolverState* st = sts[i];
+    double* o = out + 6 * (size_t)i;
+    if (!st) {
+      o[0] = 0.0;
+      continue;
+    }
+    o[0] = st->active;
+    o[1] = st->iter;
+    o[2] = st->gg;
+    o[3] = st->f;
+    o[4] = st->stop;
+    o[5] = st->evals;
+  }
+}
+
+// The batched form's graph: ROUNDS_PER_LAUNCH L-BFGS iterations of every instance, each
+// instance on a branch of its own (the iteration ensure_solver captures, repeated), then the
+// gather of every instance's scalars into pinned host memory.  Kept by the batch across solves
+// while every instance keeps its solver buffers.
+constexpr int ROUNDS_PER_LAUNCH = 5;
+struct RoundsGraph {
+  int count = 0;
+  cudaStream_t M = nullptr;               // the stream the graph runs on
+  std::vector<cudaStream_t> fork;         // capture branches
+  std::vector<cudaEvent_t> join;
+  cudaEvent_t ev = nullptr;
+  std::vector<const void*> key;           // each instance's solver state at capture
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  SolverState** d_states = nullptr;
+  double* d_out = nullptr;
+  double* h_out = nullptr;                // pinned
+};
+
+void rounds_free(RoundsGraph* g) {
+  if (!g) return;
+  if (g->M) cudaStreamSynchronize(g->M);
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  for (cudaStream_t s : g->fork) cudaStreamDestroy(s);
+  for (cudaEvent_t e : g->join) cudaEventDestroy(e);
+  if (g->ev) cudaEventDestroy(g->ev);
+  if (g->M) cudaStreamDestroy(g->M);
+  cudaFree(g->d_states);
+  cudaFree(g->d_out);
+  cudaFreeHost(g->h_out);
+  delete g;
+}
+
+// Makes (or reuses) the graph for the instances ctx[0..count) whose flag live[i] is set.
+static rpca_status rounds_graph(RoundsGraph* g, rpca_ctx* const* ctx, int count, const std::vector<char>& live) {
+  std::vector<const void*> key(count, nullptr);
+  for (int i = 0; i < count; ++i) key[i] = live[i] ? solver_state_dev(ctx[i]) : nullptr;
+  if (g->exec && g->count == count && g->key == key) return RPCA_OK;
+  rpca_ctx* c0 = ctx[0];
+  auto fail = [&](cudaError_t e, const char* what) { return cuda_err(c0, e, what); };
+  cudaError_t e;
+  if (g->count != count) {
+    if (g->d_states) return set_err(c0, RPCA_EUNSUPPORTED, "batch size changed");
+    g->count = count;
+    if ((e = cudaStreamCreateWithFlags(&g->M, cudaStreamNonBlocking)) != cudaSuccess) return fail(e, "stream");
+    if ((e = cudaEventCreateWithFlags(&g->ev, cudaEventDisableTiming)) != cudaSuccess) return fail(e, "event");
+    g->fork.assign(count, nullptr);
+    g->join.assign(count, nullptr);
+    for (int i = 0; i < count; ++i) {
+      if ((e = cudaStreamCreateWithFlags(&g->fork[i], cudaStreamNonBlocking)) != cudaSuccess) return fail(e, "stream");
+      if ((e = cudaEventCreateWithFlags(&g->join[i], cudaEventDisableTiming)) != cudaSuccess) return fail(e, "event");
+    }
+    if ((e = cudaMalloc(&g->d_states, sizeof(SolverState*) * count)) != cudaSuccess) return fail(e, "cudaMalloc");
+    if ((e = cudaMalloc(&g->d_out, sizeof(double) * 6 * count)) != cudaSuccess) return fail(e, "cudaMalloc");
+    if ((e = cudaMallocHost(&g->h_out, sizeof(double) * 6 * count)) != cudaSuccess) return fail(e, "cudaMallocHost");
+  }
+  if (g->exec) {
+    cudaGraphExecDestroy(g->exec);
+    g->exec = nullptr;
+  }
+  if (g->graph) {
+    cudaGraphDestroy(g->graph);
+    g->graph = nullptr;
+  }
+  std::vector<SolverState*> sts(count, nullptr);
+  for (int i = 0; i < count; ++i) sts[i] = live[i] ? solver_state_dev(ctx[i]) : nullptr;
+  if ((e = cudaMemcpyAsync(g->d_states, sts.data(), sizeof(SolverState*) * count, cudaMemcpyHostToDevice, g->M)) !=
+      cudaSuccess)
+    return fail(e, "state table");
+  if ((e = cudaStreamSynchronize(g->M)) != cudaSuccess) return fail(e, "state table");
+  if ((e = cudaStreamBeginCapture(g->M, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return fail(e, "capture");
+  rpca_status st = RPCA_OK;
+  e = cudaEventRecord(g->ev, g->M);
+  for (int i = 0; i < count && e == cudaSuccess && st == RPCA_OK; ++i) {
+    if (!live[i]) continue;
+    if ((e = cudaStreamWaitEvent(g->fork[i], g->ev, 0)) != cudaSuccess) break;
+    if ((st = solver_capture_rounds(ctx[i], g->fork[i], ROUNDS_PER_LAUNCH)) != RPCA_OK) break;
+    if ((e = cudaEventRecord(g->join[i], g->fork[i])) != cudaSuccess) break;
+    e = cudaStreamWaitEvent(g->M, g->join[i], 0);
+  }
+  if (e == cudaSuccess && st == RPCA_OK) {
+    gather_scalars_kernel<<<(count + 127) / 128, 128, 0, g->M>>>(g->d_states, count, g->d_out);
+    e = cudaGetLastError();
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(g->h_out, g->d_out, sizeof(double) * 6 * count, cudaMemcpyDeviceToHost, g->M);
+  }
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(g->M, &graph);
+  if (st != RPCA_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  if (e == cudaSuccess) e = e2;
+  if (e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return fail(e, "capturing the batched graph");
+  }
+  g->graph = graph;
+  if ((e = cudaGraphInstantiate(&g->exec, graph, 0)) != cudaSuccess) return fail(e, "instantiating the batched graph");
+  g->key = key;
+  return RPCA_OK;
+}
+
 rpca_status solve_jobs(rpca_ctx* const* ctx, float* const* U, float* const* V, rpca_result* res, int count,
                        rpca_status* status, int threads) {
   std::vector<SolveJob> jobs(count);
@@ -553,3 +694,110 @@ extern "C" rpca_status rpca_solve_grow(rpca_ctx* c, float* U, float* V, int kmax
   if (s != RPCA_OK && cur != c) set_err(c, s, rpca_last_error(cur));
   return s;
 }
+
+namespace rpca {
+
+// fn(i) for the items in `items`, shared among up to `threads` host threads (each sets the
+// device first).
+template <typename F>
+static void parallel_items(const std::vector<int>& items, int threads, int device, F fn) {
+  const int nt = std::max(1, std::min(threads, (int)items.size()));
+  if (nt == 1) {
+    for (int i : items) fn(i);
+    return;
+  }
+  std::vector<std::thread> pool;
+  pool.reserve(nt);
+  for (int t = 0; t < nt; ++t)
+    pool.emplace_back([&, t] {
+      cudaSetDevice(device);
+      for (size_t q = t; q < items.size(); q += nt) fn(items[q]);
+    });
+  for (auto& th : pool) th.join();
+}
+
+// The batched form in rounds: every instance is started (its initialisation and first
+// direction, host threads in parallel), then one graph launch advances every unfinished
+// instance by ROUNDS_PER_LAUNCH L-BFGS iterations at once -- the instances' kernels on
+// branches of one graph, no host work between them -- and ends with the gather of every
+// instance's scalars; between launches the host takes the same decisions as a single solve
+// (certificate when due, stop tests), the certificates of the instances that need one in
+// parallel, and a finished instance's iteration is switched off on the device.  Float32
+// storage of X and factor ranks up to 16 (the device iteration); otherwise solve_jobs.
+rpca_status solve_jobs_rounds(rpca_ctx* const* ctx, float* const* U, float* const* V, rpca_result* res, int count,
+                              rpca_status* status, int threads, RoundsGraph** cache) {
+  const int device = ctx[0]->device;
+  std::vector<SolveJob> jobs(count);
+  std::vector<int> all(count);
+  for (int i = 0; i < count; ++i) all[i] = i;
+  // Start every instance.
+  parallel_items(all, threads, device, [&](int i) { status[i] = job_start(jobs[i], ctx[i], U[i], V[i]); });
+  std::vector<char> live(count, 0);
+  for (int i = 0; i < count; ++i) live[i] = status[i] == RPCA_OK;
+  if (!*cache) *cache = new RoundsGraph();
+  RoundsGraph* g = *cache;
+  rpca_status s = rounds_graph(g, ctx, count, live);
+  if (s != RPCA_OK) {
+    for (int i = 0; i < count; ++i)
+      if (status[i] == RPCA_OK) status[i] = s;
+    return s;
+  }
+  // The graph's stream waits for every start.
+  for (int i = 0; i < count; ++i) {
+    if (!live[i]) continue;
+    cudaEventRecord(g->join[i], ctx[i]->stream);
+    cudaStreamWaitEvent(g->M, g->join[i], 0);
+  }
+  int remaining = 0;
+  for (int i = 0; i < count; ++i) remaining += live[i];
+  while (remaining > 0) {
+    cudaError_t e = cudaGraphLaunch(g->exec, g->M);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->M);
+    if (e != cudaSuccess) {
+      for (int i = 0; i < count; ++i)
+        if (live[i]) status[i] = cuda_err(ctx[i], e, "batched graph");
+      return status[0];
+    }
+    ctx[0]->graph_launches += 1;
+    std::vector<int> decide;
+    for (int i = 0; i < count; ++i) {
+      if (!live[i]) continue;
+      SolveJob& j = jobs[i];
+      const double* o = g->h_out + 6 * (size_t)i;
+      j.st.active = (int)o[0];
+      j.st.iter = (int)o[1];
+      j.st.gg = o[2];
+      j.st.f = o[3];
+      j.st.stop = (int)o[4];
+      j.st.evals = (int)o[5];
+      const bool stop = !j.st.active || j.st.iter >= ctx[i]->opt.max_iter - j.iter_base;
+      if (stop || cert_due(j, j.st, ctx[i]->opt.cert_tol) || ctx[i]->opt.timeout_s > 0) decide.push_back(i);
+    }
+    if (decide.empty()) continue;
+    parallel_items(decide, threads, device, [&](int i) {
+      bool again = false;
+      status[i] = job_decide(jobs[i], &again);
+      if (status[i] == RPCA_OK && jobs[i].done && jobs[i].st.active) status[i] = solver_deactivate(ctx[i], ctx[i]->stream);
+    });
+    for (int i : decide) {
+      if (status[i] != RPCA_OK || jobs[i].done) {
+        live[i] = 0;
+        --remaining;
+      }
+      cudaEventRecord(g->join[i], ctx[i]->stream);
+      cudaStreamWaitEvent(g->M, g->join[i], 0);
+    }
+  }
+  // The results, ordered after the last graph launch.
+  cudaEventRecord(g->ev, g->M);
+  std::vector<int> done;
+  for (int i = 0; i < count; ++i)
+    if (status[i] == RPCA_OK) done.push_back(i);
+  parallel_items(done, threads, device, [&](int i) {
+    cudaStreamWaitEvent(ctx[i]->stream, g->ev, 0);
+    status[i] = job_finish(jobs[i], res ? &res[i] : nullptr);
+  });
+  return RPCA_OK;
+}
+
+}  // namespace rpca

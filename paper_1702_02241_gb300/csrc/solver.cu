@@ -872,6 +872,41 @@ static FgLaunch trial_launch(rpca_ctx* c, cudaGraphConditionalHandle h = 0, int 
   return L;
 }
 
+// Records one iteration on `cap`, which must be capturing: a WHILE node over the line-search
+// trials (fused pass and finalize-with-step, captured into the node's body on the context's
+// second capture stream), then accept + inner products and the next direction.
+static cudaError_t capture_iteration(rpca_ctx* c, cudaStream_t cap) {
+  SolverBuffers* b = c->sol;
+  SolverArgs a = solver_args(c);
+  cudaStreamCaptureStatus cst;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(cap, &cst, nullptr, &g, &deps, nullptr, &ndeps);
+  cudaGraphConditionalHandle h;
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+  cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t wnode;
+  if (e == cudaSuccess) e = cudaGraphAddNode(&wnode, g, deps, nullptr, ndeps, &cp);
+  if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(cap, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies);
+  if (e == cudaSuccess) {
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(b->cap2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      rpca_status s = launch_fg(c, *b->plan, trial_launch(c, h, 1), b->cap2);
+      e = s == RPCA_OK ? cudaGetLastError() : cudaErrorUnknown;
+      cudaGraph_t body_out = nullptr;
+      cudaError_t e2 = cudaStreamEndCapture(b->cap2, &body_out);
+      if (e == cudaSuccess) e = e2;
+    }
+  }
+  if (e == cudaSuccess) e = update_and_direction(b->mcap, a, b->grid, cap);
+  return e;
+}
+
 static rpca_status ensure_solver(rpca_ctx* c) {
   const int mcap = mem_cap(c->opt.lbfgs_mem);
   const FgPlan* plan = c->solve_plan ? c->solve_plan : &c->fg_plan;
@@ -914,34 +949,8 @@ static rpca_status ensure_solver(rpca_ctx* c) {
   if (c->lk) return RPCA_OK;
 
   // Capture one iteration: WHILE(line search) { fg, finalize, ls_step }, update, direction.
-  SolverArgs a = solver_args(c);
   SOL_CUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
-  cudaStreamCaptureStatus cst;
-  cudaGraph_t g = nullptr;
-  const cudaGraphNode_t* deps = nullptr;
-  size_t ndeps = 0;
-  cudaError_t e = cudaStreamGetCaptureInfo(b->cap, &cst, nullptr, &g, &deps, nullptr, &ndeps);
-  cudaGraphConditionalHandle h;
-  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
-  cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
-  cp.conditional.handle = h;
-  cp.conditional.type = cudaGraphCondTypeWhile;
-  cp.conditional.size = 1;
-  cudaGraphNode_t wnode;
-  if (e == cudaSuccess) e = cudaGraphAddNode(&wnode, g, deps, nullptr, ndeps, &cp);
-  if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(b->cap, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies);
-  if (e == cudaSuccess) {
-    cudaGraph_t body = cp.conditional.phGraph_out[0];
-    e = cudaStreamBeginCaptureToGraph(b->cap2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess) {
-      rpca_status s = launch_fg(c, *b->plan, trial_launch(c, h, 1), b->cap2);
-      e = s == RPCA_OK ? cudaGetLastError() : cudaErrorUnknown;
-      cudaGraph_t body_out = nullptr;
-      cudaError_t e2 = cudaStreamEndCapture(b->cap2, &body_out);
-      if (e == cudaSuccess) e = e2;
-    }
-  }
-  if (e == cudaSuccess) e = update_and_direction(mcap, a, b->grid, b->cap);
+  cudaError_t e = capture_iteration(c, b->cap);
   cudaGraph_t graph = nullptr;
   cudaError_t e3 = cudaStreamEndCapture(b->cap, &graph);
   if (e == cudaSuccess) e = e3;
@@ -951,6 +960,30 @@ static rpca_status ensure_solver(rpca_ctx* c) {
   }
   b->graph = graph;
   SOL_CUDA(cudaGraphInstantiate(&b->exec, graph, 0));
+  return RPCA_OK;
+}
+
+// Appends this context's rounds of iterations (one iteration each, as the graph of
+// ensure_solver) to the graph that `s` is capturing: the batched form's graph holds the
+// iterations of every instance, each instance's on a branch of its own.
+rpca_status solver_capture_rounds(rpca_ctx* c, cudaStream_t s, int rounds) {
+  if (!c->sol || c->lk) return set_err(c, RPCA_EUNSUPPORTED, "no device iteration to capture");
+  for (int r = 0; r < rounds; ++r) {
+    const cudaError_t e = capture_iteration(c, s);
+    if (e != cudaSuccess) return cuda_err(c, e, "capturing the batched iteration graph");
+  }
+  return RPCA_OK;
+}
+
+SolverState* solver_state_dev(rpca_ctx* c) { return c->sol ? c->sol->st : nullptr; }
+
+// Stops the device iteration of this context (its kernels in a captured graph then return at
+// once): used by the batched form for instances that are finished.
+rpca_status solver_deactivate(rpca_ctx* c, cudaStream_t s) {
+  SolverBuffers* b = c->sol;
+  if (!b) return RPCA_OK;
+  SOL_CUDA(cudaMemsetAsync(&b->st->active, 0, sizeof(int), s));
+  SOL_CUDA(cudaMemsetAsync(&b->st->gate, 0, sizeof(int), s));
   return RPCA_OK;
 }
 

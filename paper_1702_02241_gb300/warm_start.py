@@ -67,11 +67,14 @@ def lambdas(m, n):
     return lam_S * (math.sqrt(m) + math.sqrt(n)), lam_S
 
 
-def _opts(init, max_iter=3000, cert_every=10):
+def _opts(init, max_iter=3000, cert_every=10, x_dtype=None):
     o = rpca.rpca_default_options()
     o.init = init
     o.max_iter = max_iter
     o.cert_every = cert_every
+    if x_dtype is not None:
+        o.x_dtype = x_dtype
+        o.refine_fp32 = 1
     return o
 
 
@@ -202,6 +205,52 @@ def evaluate_batch(w, specs, seed, reps=2):
     return out
 
 
+def evaluate_combined(w, specs, seed, reps=2):
+    """The end-to-end comparison on instances whose rank the narrow storage supports (k <= 8):
+    the plain float32 solver one instance after another from the sketch start, against the
+    batched form from the learned starts in float32 and with X stored in bfloat16 (float32
+    refinement to the same certificate).  Wall time for the whole set (best of reps), total
+    iterations, certified count (the float32 certificate at cert_tol 1e-4 in every form)."""
+    specs = [s for s in specs if s["k"] <= 8]
+    Xs, lds = zip(*[generate(s, seed, i) for i, s in enumerate(specs)])
+    lams = [lambdas(s["m"], s["n"]) for s in specs]
+    out = {"count": len(specs)}
+    best = None
+    for _ in range(reps):
+        ctxs = [rpca.rpca_create(s["m"], s["n"], X, ld, None, 0, s["k"], l[0], l[1], _opts(rpca.RPCA_INIT_SKETCH))
+                for s, X, ld, l in zip(specs, Xs, lds, lams)]
+        fac = [_factors(s["m"], s["n"], s["k"]) for s in specs]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = [rpca.rpca_solve(c, U, V) for c, (U, V) in zip(ctxs, fac)]
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        for c in ctxs:
+            rpca.rpca_destroy(c)
+        if best is None or dt < best[0]:
+            best = (dt, sum(r.iters for r in res), sum(r.status == rpca.RPCA_OK for r in res))
+    out["plain_f32_one_by_one"] = {"seconds": best[0], "iters": best[1], "certified": best[2]}
+    for name, xd in (("learned_batched_f32", None), ("learned_batched_bf16", rpca.RPCA_BF16)):
+        b = rpca.rpca_create_batch(list(Xs), [(s["m"], ld) for s, ld in zip(specs, lds)], [s["k"] for s in specs],
+                                   [l[0] for l in lams], [l[1] for l in lams],
+                                   _opts(rpca.RPCA_INIT_LEARNED, x_dtype=xd))
+        for i in range(len(specs)):
+            rpca.rpca_set_warm_start(rpca.rpca_batch_context(b, i), w)
+        best = None
+        for _ in range(reps):
+            Us, Vs = zip(*[_factors(s["m"], s["n"], s["k"]) for s in specs])
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st, res = rpca.rpca_solve_batch(b, list(Us), list(Vs))
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            if best is None or dt < best[0]:
+                best = (dt, sum(r.iters for r in res), sum(r.status == rpca.RPCA_OK for r in res))
+        out[name] = {"seconds": best[0], "iters": best[1], "certified": best[2]}
+        rpca.rpca_destroy_batch(b)
+    return out
+
+
 def summary(res):
     out = {}
     for st, d in res.items():
@@ -222,6 +271,9 @@ def main(argv=None):
     ap.add_argument("--out", default=PARAMS_PATH)
     ap.add_argument("--json", default=None)
     ap.add_argument("--load", action="store_true", help="evaluate the saved parameters instead of training")
+    ap.add_argument("--combined", type=int, default=0,
+                    help="draw this many held-out instances and compare, on those with k <= 8, the plain float32 "
+                         "solver one by one with the learned + batched form in float32 and in bfloat16")
     ap.add_argument("--batch-eval", type=int, default=0,
                     help="also solve this many held-out instances as one batch, sketch vs learned starts")
     a = ap.parse_args(argv)
@@ -245,6 +297,10 @@ def main(argv=None):
     log("held-out 4096x256: " + json.dumps(res))
     out = {"train": a.train, "epochs": a.epochs, "final_loss": losses[-1][1] if losses else None,
            "heldout_4096x256": res}
+    if a.combined:
+        rc = evaluate_combined(w, instance_params(a.combined, a.seed + 3), a.seed + 3)
+        log("combined form on held-out instances with k <= 8: " + json.dumps(rc))
+        out["combined_k_le_8"] = rc
     if a.batch_eval:
         rb = evaluate_batch(w, instance_params(a.batch_eval, a.seed + 2), a.seed + 2)
         log(f"held-out batch of {a.batch_eval}: " + json.dumps(rb))

@@ -22,7 +22,11 @@ def built():
     build.build()
 
 
-def test_batch_solves_match_single_solves():
+@pytest.mark.parametrize("mode", ["rounds", "threads"])
+def test_batch_solves_match_single_solves(mode, monkeypatch):
+    """Both drivers of the batched form: rounds (one graph launch advances every instance, the
+    default) and host threads stepping each instance's own graph."""
+    monkeypatch.setenv("RPCA_BATCH_MODE", mode)
     insts = gen.batch_c4(6, seed=1, m_range=(1024, 3000), n_range=(50, 200))
     Xs = [to_device_colmajor(i.X, pad=True) for i in insts]
     opt = rpca.rpca_default_options()
@@ -38,7 +42,7 @@ def test_batch_solves_match_single_solves():
     assert st == rpca.RPCA_OK, rpca.rpca_batch_last_error(b)
     for i, inst in enumerate(insts):
         r = res[i]
-        assert r.status == rpca.RPCA_OK and r.cert.cert_rel <= 1e-4
+        assert r.status == rpca.RPCA_OK and r.cert.certified(1e-4)
         U, V = host(Us[i], inst.m), host(Vs[i], inst.n)
         assert r.F == pytest.approx(core.objective(inst.X, None, U, V, inst.lam_L, inst.lam_S), rel=1e-6)
         P = make_problem(inst.X, None, inst.k, inst.lam_L, inst.lam_S, init=rpca.RPCA_INIT_SKETCH,
@@ -48,4 +52,10 @@ def test_batch_solves_match_single_solves():
         P.close()
         assert r1.status == rpca.RPCA_OK
         assert r.F == pytest.approx(r1.F, rel=1e-6)
+    # A second solve of the same batch (the rounds graph is kept) gives the same results.
+    Us2, Vs2 = zip(*[empty_factors(i.m, i.n, i.k) for i in insts])
+    st2, res2 = rpca.rpca_solve_batch(b, Us2, Vs2)
+    assert st2 == rpca.RPCA_OK
+    for a, c in zip(res, res2):
+        assert a.iters == c.iters and a.F == pytest.approx(c.F, rel=1e-9)
     rpca.rpca_destroy_batch(b)
