@@ -160,23 +160,20 @@ static rpca_status make_tmap_swz(rpca_ctx* c, CUtensorMap* map, CUtensorMapDataT
   return RPCA_OK;
 }
 
-// Raises a kernel's dynamic shared-memory limit to at least `bytes` (never lowers it, so
-// plans made earlier stay launchable).  False when the device cannot provide that much.
+// Raises a kernel's dynamic shared-memory limit to at least `bytes` (once per kernel and size;
+// the limit only ever grows, so a configuration planned earlier with more shared memory stays
+// launchable).  False when the device cannot give that much.
 bool allow_smem(const void* fn, size_t bytes) {
   static std::mutex mu;
-  static const void* fns[64];
-  static size_t lim[64];
-  static int nf = 0;
+  static std::map<const void*, size_t> lim;
   std::lock_guard<std::mutex> lock(mu);
-  int i = 0;
-  while (i < nf && fns[i] != fn) ++i;
-  if (i < nf && lim[i] >= bytes) return true;
+  auto it = lim.find(fn);
+  if (it != lim.end() && it->second >= bytes) return true;
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  if (i == nf && nf < 64) fns[nf++] = fn;
-  if (i < 64) lim[i] = bytes;
+  lim[fn] = bytes;
   return true;
 }
 
