@@ -97,6 +97,48 @@ RPCA_DEV void named_bar(int id, int nthreads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
+// ---- float-float sums ----------------------------------------------------------------------
+// An unevaluated sum hi + lo of two floats (about 44 significant bits), added with float32
+// operations only.  The fixed-order sums of partials across warps and blocks use it: on GB300
+// a float64 add takes 64 cycles and the float64 instructions of all warps on an SM quadrant
+// share one narrow unit, so float64 reduction trees were the longest part of the short
+// kernels of a solver iteration; a float-float add is ten float32 operations, four deep.
+struct ff2 {
+  float hi, lo;
+};
+RPCA_DEV ff2 ff_make(float x) { return {x, 0.f}; }
+// Knuth's two-sum of the high parts, the low parts added to its error, renormalised with
+// Dekker's fast two-sum.  (No products: nothing for the compiler to contract into an FMA.)
+RPCA_DEV ff2 ff_add(ff2 a, ff2 b) {
+  const float s = a.hi + b.hi;
+  const float v = s - a.hi;
+  const float e = ((a.hi - (s - v)) + (b.hi - v)) + (a.lo + b.lo);
+  const float hi = s + e;
+  return {hi, e - (hi - s)};
+}
+RPCA_DEV double ff_to_d(ff2 a) { return (double)a.hi + (double)a.lo; }
+RPCA_DEV ff2 ff_shfl_xor(ff2 a, int o) {
+  return {__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
+}
+// Butterfly sum over the warp; every lane's association differs, so take one lane's result.
+RPCA_DEV ff2 warp_ff_sum(ff2 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = ff_add(v, ff_shfl_xor(v, o));
+  return v;
+}
+// A float-float value kept in an 8-byte slot of a double buffer (block partials).
+RPCA_DEV void ff_store(double* slot, ff2 v) { *reinterpret_cast<float2*>(slot) = make_float2(v.hi, v.lo); }
+RPCA_DEV ff2 ff_load(const double* slot) {  // any state space (shared scratch)
+  const float2 t = *reinterpret_cast<const float2*>(slot);
+  return {t.x, t.y};
+}
+RPCA_DEV ff2 ff_load_cg(const double* slot) {  // global memory another block may have written
+  const float2 t = __ldcg(reinterpret_cast<const float2*>(slot));
+  return {t.x, t.y};
+}
+// A lane's Kahan pair (sum s, compensation c; the value is s - c) as a float-float value.
+RPCA_DEV ff2 ff_from_kahan(float s, float c) { return ff_add(ff_make(s), ff_make(-c)); }
+
 // ---- warp reduce-scatter of C floats over 32 lanes -----------------------------------
 // After the call every lane holds rs_count(C) fully reduced values v[0..), standing for the
 // original indices base + t.  Lanes that differ only in the bits of rs_dup_mask(C) hold the

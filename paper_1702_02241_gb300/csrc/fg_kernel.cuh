@@ -42,7 +42,7 @@ struct FgArgs {
   int nstage;        // pipeline depth (2 .. FG_NSTAGE)
   float* PU;         // [ncs][B][mpad]  -(D Bv) partial sums over a CTA's columns
   float* PV;         // [nrb][B][n]      D^T Bu partial sums over a CTA's rows
-  double* Ppsi;      // [nrb*ncs]        sum of psi over a CTA's tile
+  double* Ppsi;      // [nrb*ncs]        sum of psi over a CTA's tile (float-float pair, ff_store)
   int* err;          // device status word (error bits)
   const float* xscale;  // FP8 storage: per-column scales (x = stored value * scale)
   int npass;         // tensor-core form: row passes of 32 * (consumer warps) rows per CTA
@@ -485,14 +485,15 @@ __global__ void __launch_bounds__(288, 1) fg_kernel(const __grid_constant__ CUte
         *reinterpret_cast<float2*>(a.PU + ((size_t)cs * B + b) * a.mpad + i0) = gu[p][ROWSIDE ? b : 0];
     }
   }
-  // Sum of psi over the tile; column sums over the consumer warps in fixed order.
-  double psi_d = warp_sum_d((double)psi_s - (double)psi_c);
-  if (lane == 0) scr[warp] = psi_d;
+  // Sum of psi over the tile (float-float: lanes, then the consumer warps in fixed order);
+  // column sums over the consumer warps in fixed order.
+  const ff2 psi_w = warp_ff_sum(ff_from_kahan(psi_s, psi_c));
+  if (lane == 0) ff_store(&scr[warp], psi_w);
   named_bar(1, nct);
   if (tid == 0) {
-    double s = 0.0;
-    for (int w = 0; w < WC; ++w) s += scr[w];
-    a.Ppsi[blockIdx.x] = s;
+    ff2 s = ff_load(&scr[0]);
+    for (int w = 1; w < WC; ++w) s = ff_add(s, ff_load(&scr[w]));
+    ff_store(&a.Ppsi[blockIdx.x], s);
   }
   for (int idx = tid; idx < (COLSIDE ? ncols * B : 0); idx += nct) {
     const int b = idx / ncols, jl = idx - b * ncols;

@@ -375,14 +375,14 @@ __global__ void __launch_bounds__(288, 1) fg_mma_kernel(const __grid_constant__ 
     }
   }
 
-  // Sum of psi over the tile.
-  const double psi_d = warp_sum_d((double)psi_s - (double)psi_c);
-  if (lane == 0) scr[warp] = psi_d;
+  // Sum of psi over the tile (float-float: lanes, then the consumer warps in fixed order).
+  const ff2 psi_w = warp_ff_sum(ff_from_kahan(psi_s, psi_c));
+  if (lane == 0) ff_store(&scr[warp], psi_w);
   named_bar(1, nct);
   if (tid == 0) {
-    double sacc = 0.0;
-    for (int w = 0; w < WC; ++w) sacc += scr[w];
-    a.Ppsi[blockIdx.x] = sacc;
+    ff2 sacc = ff_load(&scr[0]);
+    for (int w = 1; w < WC; ++w) sacc = ff_add(sacc, ff_load(&scr[w]));
+    ff_store(&a.Ppsi[blockIdx.x], sacc);
   }
 }
 

@@ -476,14 +476,15 @@ __global__ void __launch_bounds__(TC_THREADS, 2) fg_tc_kernel(const __grid_const
       for (int b = 0; b < K; ++b) *reinterpret_cast<float2*>(a.PU + ((size_t)cs * K + b) * a.mpad + i0) = gu[p][b];
     }
   }
-  // Sum of psi over the tile; column sums over the consumer warps in fixed order.
-  double psi_d = warp_sum_d((double)psi_s - (double)psi_c);
-  if (lane == 0) scr[warp] = psi_d;
+  // Sum of psi over the tile (float-float: lanes, then the consumer warps in fixed order);
+  // column sums over the consumer warps in fixed order.
+  const ff2 psi_w = warp_ff_sum(ff_from_kahan(psi_s, psi_c));
+  if (lane == 0) ff_store(&scr[warp], psi_w);
   named_bar(1, nct);
   if (tid == 0) {
-    double sacc = 0.0;
-    for (int w = 0; w < TC_WC; ++w) sacc += scr[w];
-    a.Ppsi[blockIdx.x] = sacc;
+    ff2 sacc = ff_load(&scr[0]);
+    for (int w = 1; w < TC_WC; ++w) sacc = ff_add(sacc, ff_load(&scr[w]));
+    ff_store(&a.Ppsi[blockIdx.x], sacc);
   }
   for (int idx = tid; idx < ncols * K; idx += nct) {
     const int b = idx / ncols, jl = idx - b * ncols;

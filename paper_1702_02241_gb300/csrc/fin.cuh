@@ -9,32 +9,6 @@
 
 namespace rpca {
 
-// Deterministic block sum of three doubles per thread; results valid in thread 0.
-RPCA_DEV void block_sum3(double& x, double& y, double& z, double (*scr)[3]) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    x += __shfl_xor_sync(0xffffffffu, x, o);
-    y += __shfl_xor_sync(0xffffffffu, y, o);
-    z += __shfl_xor_sync(0xffffffffu, z, o);
-  }
-  __syncthreads();
-  if (lane == 0) {
-    scr[w][0] = x;
-    scr[w][1] = y;
-    scr[w][2] = z;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    x = y = z = 0.0;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
-      x += scr[i][0];
-      y += scr[i][1];
-      z += scr[i][2];
-    }
-  }
-}
-
 // Gradient assembly.  Blocks [0, a.gu) handle the m x B side, FIN_EPT elements per thread
 // (strided by the blocks of that side, so that each round is coalesced and all rounds' loads
 // are in flight together): the column-split partials of PU are summed and
@@ -42,9 +16,9 @@ RPCA_DEV void block_sum3(double& x, double& y, double& z, double (*scr)[3]) {
 // per block: four groups of 64 threads each sum every fourth row-block partial of PV
 // (coalesced across consecutive columns) and the groups are added in a fixed order.
 // Elementwise work is float32 (the partial sums are float32 already); each block's dot
-// products (||x_t||^2, g.d, ||g||^2) go to float64 for the fixed-order block sums.
+// products (||x_t||^2, g.d, ||g||^2) go to float-float for the fixed-order block sums.
 RPCA_DEV void finalize_body(const FinArgs& a) {
-  __shared__ double scr[32][3];
+  __shared__ float wsum[32][3];
   __shared__ float vs[4][64];
   __shared__ float alpha_s;
   // Conversions from float64 and 64-bit divisions run on the float64 pipe, which is narrow on
@@ -139,8 +113,8 @@ RPCA_DEV void finalize_body(const FinArgs& a) {
     }
   }
   if (a.mode == FIN_APPLY) return;
-  // Warp sums in float32 (float64 is slow on this GPU: a float64 tree over every thread of
-  // the grid costs more than the whole assembly), then float64 across the warps.
+  // Warp sums in float32, then the warps in float-float (a float64 sum over the warps, on
+  // thread 0, was the longest step of the assembly on GB300).
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     nrm_f += __shfl_xor_sync(0xffffffffu, nrm_f, o);
@@ -150,46 +124,51 @@ RPCA_DEV void finalize_body(const FinArgs& a) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   __syncthreads();
   if (lane == 0) {
-    scr[w][0] = nrm_f;
-    scr[w][1] = gd_f;
-    scr[w][2] = gg_f;
+    wsum[w][0] = nrm_f;
+    wsum[w][1] = gd_f;
+    wsum[w][2] = gg_f;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double nrm = 0.0, gd = 0.0, gg = 0.0;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
-      nrm += scr[i][0];
-      gd += scr[i][1];
-      gg += scr[i][2];
-    }
-    a.blk[3 * blockIdx.x + 0] = nrm;
-    a.blk[3 * blockIdx.x + 1] = gd;
-    a.blk[3 * blockIdx.x + 2] = gg;
+  if (threadIdx.x < 3) {
+    const int v = threadIdx.x;
+    ff2 t = ff_make(wsum[0][v]);
+    for (int i = 1; i < (int)(blockDim.x >> 5); ++i) t = ff_add(t, ff_make(wsum[i][v]));
+    ff_store(&a.blk[3 * blockIdx.x + v], t);
   }
 }
 
-// One block: fixed-order sums of the finalize partials and of the per-CTA psi sums.
+// One block: fixed-order sums of the finalize partials and of the per-CTA psi sums, in
+// float-float (each thread its blocks in order, a warp butterfly, the warps in order).
 // out = {f, g.d, ||g||^2, ||x||^2} (written by thread 0).
 RPCA_DEV void finalize_reduce_body(const FinArgs& a, int nblocks) {
-  __shared__ double scr[32][3];
-  double p0 = 0.0, p1 = 0.0, p2 = 0.0, ps = 0.0;
-#pragma unroll 4
+  __shared__ ff2 wred[32][4];
+  __shared__ double res[4];
+  ff2 p[4] = {ff_make(0.f), ff_make(0.f), ff_make(0.f), ff_make(0.f)};  // ||x||^2, g.d, ||g||^2, psi
   for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {  // L2 reads: other blocks may have just written
-    p0 += __ldcg(&a.blk[3 * b + 0]);
-    p1 += __ldcg(&a.blk[3 * b + 1]);
-    p2 += __ldcg(&a.blk[3 * b + 2]);
+#pragma unroll
+    for (int v = 0; v < 3; ++v) p[v] = ff_add(p[v], ff_load_cg(&a.blk[3 * b + v]));
   }
-  block_sum3(p0, p1, p2, scr);
+  for (int b = threadIdx.x; b < a.nctas; b += blockDim.x) p[3] = ff_add(p[3], ff_load_cg(&a.Ppsi[b]));
+#pragma unroll
+  for (int v = 0; v < 4; ++v) p[v] = warp_ff_sum(p[v]);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) {
+#pragma unroll
+    for (int v = 0; v < 4; ++v) wred[w][v] = p[v];
+  }
   __syncthreads();
-#pragma unroll 4
-  for (int b = threadIdx.x; b < a.nctas; b += blockDim.x) ps += __ldcg(&a.Ppsi[b]);
-  double d1 = 0.0, d2 = 0.0;
-  block_sum3(ps, d1, d2, scr);
+  if (threadIdx.x < 4) {
+    const int v = threadIdx.x;
+    ff2 t = wred[0][v];
+    for (int i = 1; i < (int)(blockDim.x >> 5); ++i) t = ff_add(t, wred[i][v]);
+    res[v] = ff_to_d(t);
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
-    a.out[0] = ps + 0.5 * a.lam_L * p0;
-    a.out[1] = p1;
-    a.out[2] = p2;
-    a.out[3] = p0;
+    a.out[0] = res[3] + 0.5 * a.lam_L * res[0];
+    a.out[1] = res[1];
+    a.out[2] = res[2];
+    a.out[3] = res[0];
   }
 }
 

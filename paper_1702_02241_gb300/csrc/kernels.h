@@ -16,7 +16,7 @@ struct FinArgs {
   int gu;  // blocks [0, gu) handle the m x B side; the rest the n x B side
   const float* PU;
   const float* PV;
-  const double* Ppsi;
+  const double* Ppsi;  // per-CTA psi sums of the fused pass, float-float pairs (ff_store)
   int mode;  // FIN_*
   int side;  // 0 both sides, 1 only the m x B side (GU), 2 only the n x B side (GV)
   const float* U;
@@ -34,7 +34,7 @@ struct FinArgs {
   float* Vt;
   const float* DU;  // optional direction for g.d
   const float* DV;
-  double* blk;              // [3 * gridDim.x] block partials
+  double* blk;              // [3 * gridDim.x] block partials (float-float pairs, ff_store)
   unsigned int* counter;    // zero between launches (reset by the last block)
   double* out;              // [4]: f, g.d, ||g||^2, ||x_t||^2
   // Row shard of a partitioned problem (rpca_fg_rows): the n x B side writes the raw partial

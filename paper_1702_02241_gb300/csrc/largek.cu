@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(LK_T) lk_resid_kernel(float* R, int64_t ldr, i
                                                         double* psi_part) {
   if (gate != nullptr && *gate == 0) return;
   __shared__ double scr[LK_T / 32];
-  double acc = 0.0;
+  float acc_s = 0.f, acc_c = 0.f;  // Kahan pair; float-float across lanes and warps
   const int64_t total = m * n;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t j = e / m, i = e - j * m;
@@ -58,15 +58,18 @@ __global__ void __launch_bounds__(LK_T) lk_resid_kernel(float* R, int64_t ldr, i
     const bool on = bits == nullptr || ((bits[(size_t)j * wpad + (i >> 5)] >> (i & 31)) & 1u);
     const float d = on ? fminf(fmaxf(r, -lam), lam) : 0.f;
     *p = d;
-    acc += (double)(d * (r - 0.5f * d));
+    const float y = d * (r - 0.5f * d) - acc_c;
+    const float t = acc_s + y;
+    acc_c = (t - acc_s) - y;
+    acc_s = t;
   }
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if ((threadIdx.x & 31) == 0) scr[threadIdx.x >> 5] = acc;
+  const ff2 w = warp_ff_sum(ff_from_kahan(acc_s, acc_c));
+  if ((threadIdx.x & 31) == 0) ff_store(&scr[threadIdx.x >> 5], w);
   __syncthreads();
   if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int w = 0; w < LK_T / 32; ++w) s += scr[w];
-    psi_part[blockIdx.x] = s;
+    ff2 s = ff_load(&scr[0]);
+    for (int q = 1; q < LK_T / 32; ++q) s = ff_add(s, ff_load(&scr[q]));
+    ff_store(&psi_part[blockIdx.x], s);
   }
 }
 

@@ -2,14 +2,15 @@
 // on the device.
 //
 // One iteration is one CUDA-graph launch:
-//   WHILE (line search running):  fg_kernel + finalize_kernel at x + a d,  ls_step_kernel
-//   lbfgs_accept_kernel:  accept the step (s = x_t - x, y = g_t - g into the history ring,
-//                         x <- x_t, g <- g_t).
-//   lbfgs_dots_kernel:    all inner products the two-loop recursion needs (one block row
-//                         per history slot); its last block runs the two-loop recursion on
-//                         those scalars (float64) and the stopping tests.
-//   lbfgs_direction_kernel:  d = c_g g + sum_j (c_s[j] s_j + c_y[j] y_j) (g.d comes from the
-//                            Gram table).
+//   WHILE (line search running):  fg_kernel at x + a d, then finalize_ls_kernel (gradient
+//                         assembly, the objective's sums and the line-search step)
+//   lbfgs_dots1_kernel:   all inner products the two-loop recursion needs, with the new pair
+//                         s = x_t - x, y = g_t - g formed on the fly; its last block runs the
+//                         scalar part (Gram table update, two-loop recursion, stopping tests,
+//                         the next line search's start)
+//   lbfgs_direction_kernel:  accept the step (the new pair into the history ring, x <- x_t,
+//                         g <- g_t) and d = c_g g + sum_j (c_s[j] s_j + c_y[j] y_j) (g.d comes
+//                         from the Gram table).
 // The two-loop recursion (Nocedal & Wright Alg. 7.4) is evaluated on inner products only:
 // with q = g - sum a_j y_j and r = gamma q + sum c_j s_j, every dot it needs is a
 // combination of s_i.g, y_i.g, s_i.y_j and y_i.y_j, which are kept in a Gram table and
@@ -19,9 +20,11 @@
 // with the approximate Wolfe conditions of Hager & Zhang (2005) for steps whose objective
 // change is below the float32 noise level of f.
 //
-// Products are formed in float32 and summed over a few elements per thread in float32;
-// all further sums, the Gram table, the two-loop scalars and the line-search arithmetic
-// are float64.
+// Products are formed in float32 and summed over a few elements per thread in float32; the
+// sums across warps and blocks are float-float (fixed order), the line-search arithmetic is
+// float64, the Gram table and the two-loop scalars float32 (a float64 operation takes 64
+// cycles on GB300, a float32 one 4, and the scalar part of an iteration is a chain of
+// dependent operations).
 #include <algorithm>
 #include <cstddef>
 #include <chrono>
@@ -35,7 +38,7 @@
 
 namespace rpca {
 
-constexpr double LS_C1 = 1e-4, LS_C2 = 0.9, LS_AMAX = 1e10, CURV_EPS = 1e-10;
+constexpr double LS_C1 = 1e-4, LS_C2 = 0.9, LS_AMAX = 1e10;
 constexpr int LS_MAX_TRIALS = 25;
 
 constexpr int DOTS_GRP = 16;      // blocks per group of the two-level reduction
@@ -201,7 +204,9 @@ __global__ void ls_step_kernel(SolverState* st, cudaGraphConditionalHandle h, in
 // arithmetic in the same order as finalize_kernel + finalize_reduce_kernel + ls_step_kernel,
 // two fewer launches per trial.  With the gate closed (no search running) only the step runs,
 // which ends the graph's while loop.
-__global__ void __launch_bounds__(256) finalize_ls_kernel(FinArgs a, SolverState* st, cudaGraphConditionalHandle h,
+// Four CTAs per SM (64 registers): the assembly needs few registers, the single thread that
+// takes the line-search step many, and the more of the grid one wave holds the better.
+__global__ void __launch_bounds__(256, 4) finalize_ls_kernel(FinArgs a, SolverState* st, cudaGraphConditionalHandle h,
                                                           int in_graph, unsigned int* ticket) {
   __shared__ bool is_last;
   if (a.gate != nullptr && *a.gate == 0) {
@@ -228,85 +233,48 @@ cudaError_t launch_finalize_ls(const FinArgs& f, int grid, const FgLaunch& L, cu
 }
 
 // ---------------------------------------------------------------------------------------------
-// Two-loop recursion on the Gram table (thread 0 of the last block of lbfgs_update_kernel).
-__device__ void two_loop_coefs(SolverState* st) {
-  const int n = st->count;
-  for (int j = 0; j < SOLVER_MAX_SLOTS; ++j) {
-    st->coef_s[j] = 0.0;
-    st->coef_y[j] = 0.0;
-  }
-  if (n == 0) {
-    st->coef_g = -1.0;
-    return;
-  }
-  double a[SOLVER_MAX_SLOTS], c[SOLVER_MAX_SLOTS], rho[SOLVER_MAX_SLOTS];
-  const int* id = st->ids;  // newest first
-  for (int i = 0; i < n; ++i) rho[i] = 1.0 / st->SY[id[i]][id[i]];  // independent divisions
-  for (int i = 0; i < n; ++i) {  // newest -> oldest
-    double t = st->sg[id[i]];
-    for (int j = 0; j < i; ++j) t -= a[j] * st->SY[id[i]][id[j]];
-    a[i] = t * rho[i];
-  }
-  const double gamma = st->SY[id[0]][id[0]] / st->YY[id[0]][id[0]];
-  for (int i = n - 1; i >= 0; --i) {  // oldest -> newest
-    double t = st->yg[id[i]];
-    for (int j = 0; j < n; ++j) t -= a[j] * st->YY[id[i]][id[j]];
-    t *= gamma;
-    for (int j = i + 1; j < n; ++j) t += c[j] * st->SY[id[j]][id[i]];
-    const double b = t * rho[i];
-    c[i] = a[i] - b;
-  }
-  st->coef_g = -gamma;
-  for (int i = 0; i < n; ++i) {
-    st->coef_y[id[i]] = gamma * a[i];
-    st->coef_s[id[i]] = -c[i];
-  }
-}
-
-// Scalar part of an iteration: ring update, stopping tests, next direction's coefficients
-// and the line-search start.  `v` holds the reduced inner products (layout: see below).
-// The scalar part of an iteration before the two-loop coefficients: the new pair enters
-// the Gram table (or the memory is reset after a failed search), the history dot products
-// are refreshed, the log record is written, and the stopping tests run.
+// The scalar part of an iteration before the two-loop coefficients (one thread): the new pair
+// enters the Gram table (or the memory is reset after a failed search), the history inner
+// products are refreshed, the log record is written, and the stopping tests run.  `v` holds
+// the reduced inner products in float64 and `vf` the same rounded to float32 (layout: see
+// lbfgs_dots_kernel).  Float64 is kept for f, ||g||^2 and the line search; the Gram table is
+// float32 (see SolverState), and no float64 square root or division is taken here.
+constexpr float CURV_EPS_F = 1e-10f;
 template <int NS>
-__device__ void iteration_update(SolverState* st, SolverState* logst, const double* v) {
+__device__ void iteration_update(SolverState* st, SolverState* logst, const double* v, const float* vf) {
   const int state = st->ls.state;
   int added = -1;  // slot of the pair added by this step, if any
   const double step = st->ls.a, trials = st->ls.evals;
+  st->acc_flag = state == LS_ACCEPTED;
   if (state == LS_ACCEPTED) {
     st->f = st->ls.f_acc;
     st->iter += 1;
     st->fails = 0;
-    const double sy = v[5 * NS + 2], yy = v[5 * NS + 3], ss = v[5 * NS + 4];
+    const float sy = vf[5 * NS + 2], yy = vf[5 * NS + 3], ss = vf[5 * NS + 4];
     const int sp = st->spare;
-    if (sy > CURV_EPS * sqrt(ss * yy) && yy > 0.0) {
+    if (sy > CURV_EPS_F * (sqrtf(ss) * sqrtf(yy)) && yy > 0.f) {  // curvature: s.y > eps |s| |y|
       for (int q = 0; q < st->count; ++q) {
         const int j = st->ids[q];
-        st->SY[sp][j] = v[5 * j + 3];  // s_new . y_j
-        st->SY[j][sp] = v[5 * j + 2];  // s_j . y_new
-        st->YY[sp][j] = v[5 * j + 4];
-        st->YY[j][sp] = v[5 * j + 4];
+        st->SY[sp][j] = vf[5 * j + 3];  // s_new . y_j
+        st->SY[j][sp] = vf[5 * j + 2];  // s_j . y_new
+        st->YY[sp][j] = vf[5 * j + 4];
+        st->YY[j][sp] = vf[5 * j + 4];
       }
       st->SY[sp][sp] = sy;
       st->YY[sp][sp] = yy;
-      int dropped = -1;
-      if (st->count == st->mem) dropped = st->ids[st->count - 1];
-      const int keep = st->count == st->mem ? st->count - 1 : st->count;
+      const bool full = st->count == st->mem;
+      const int dropped = full ? st->ids[st->count - 1] : -1;
+      const int keep = full ? st->count - 1 : st->count;
       for (int q = keep; q > 0; --q) st->ids[q] = st->ids[q - 1];
       st->ids[0] = sp;
       st->count = keep + 1;
       added = sp;
       if (dropped >= 0) {
         st->spare = dropped;
-      } else {
-        for (int cand = 0; cand < NS; ++cand) {
-          bool used = false;
-          for (int q = 0; q < st->count; ++q) used |= st->ids[q] == cand;
-          if (!used) {
-            st->spare = cand;
-            break;
-          }
-        }
+      } else {  // the lowest slot not in the ring (count <= mem < NS leaves one free)
+        unsigned long long used = 0;
+        for (int q = 0; q < st->count; ++q) used |= 1ull << st->ids[q];
+        st->spare = __ffsll((long long)~used) - 1;
       }
     }
   } else if (state == LS_FAILED) {
@@ -317,10 +285,11 @@ __device__ void iteration_update(SolverState* st, SolverState* logst, const doub
       st->active = 0;
     }
   }
+  st->acc_slot = added;
   for (int q = 0; q < st->count; ++q) {
     const int j = st->ids[q];
-    st->sg[j] = j == added ? v[5 * NS + 0] : v[5 * j + 0];
-    st->yg[j] = j == added ? v[5 * NS + 1] : v[5 * j + 1];
+    st->sg[j] = j == added ? vf[5 * NS + 0] : vf[5 * j + 0];
+    st->yg[j] = j == added ? vf[5 * NS + 1] : vf[5 * j + 1];
   }
   st->gg = v[5 * NS + 5];
   st->g1 = v[5 * NS + 6];
@@ -328,17 +297,18 @@ __device__ void iteration_update(SolverState* st, SolverState* logst, const doub
     double* rec = logst->log[logst->log_n % SOLVER_LOG];
     rec[0] = st->iter;
     rec[1] = st->f;
-    rec[2] = sqrt(st->gg);
+    rec[2] = sqrtf(vf[5 * NS + 5]);
     rec[3] = step;
     rec[4] = trials;
     rec[5] = state;
     rec[6] = st->count;
     logst->log_n += 1;
   }
+  const double glim = st->gtol * fmax(1.0, fabs(st->f));
   if (!isfinite(st->f) || !isfinite(st->gg)) {
     st->stop = STOP_NONFINITE;
     st->active = 0;
-  } else if (st->gtol > 0.0 && sqrt(st->gg) <= st->gtol * fmax(1.0, fabs(st->f))) {
+  } else if (st->gtol > 0.0 && st->gg <= glim * glim) {  // ||g|| <= gtol max(1, |f|)
     st->stop = STOP_GTOL;
     st->active = 0;
   } else if (st->iter >= st->max_iter) {
@@ -348,26 +318,41 @@ __device__ void iteration_update(SolverState* st, SolverState* logst, const doub
   if (st->f < st->best_f) st->best_f = st->f;
 }
 
-// The rest of the scalar part after the two-loop coefficients: the descent check and the
-// first trial of the next line search.
-__device__ void iteration_finish(SolverState* st) {
-  // Descent check on the Gram table; fall back to steepest descent otherwise.
-  double gd = st->coef_g * st->gg;
-  for (int q = 0; q < st->count; ++q) {
-    const int j = st->ids[q];
-    gd += st->coef_s[j] * st->sg[j] + st->coef_y[j] * st->yg[j];
+// The rest of the scalar part after the two-loop coefficients, run by one warp: the descent
+// check g.d < 0 on the Gram table (a fixed-order warp sum, lane 0's value taken), falling
+// back to steepest descent otherwise, and the first trial of the next line search.
+// gg: ||g||^2 in float32.
+__device__ void iteration_finish_warp(SolverState* st, float gg) {
+  const int lane = threadIdx.x & 31;
+  const int n = st->count;
+  float t = 0.f;
+  if (lane < n) {
+    const int j = st->ids[lane];
+    t = fmaf(st->coef_s[j], st->sg[j], st->coef_y[j] * st->yg[j]);
   }
-  if (!(gd < 0.0)) {
-    st->count = 0;
-    two_loop_coefs(st);
-    gd = st->coef_g * st->gg;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  float gd = __shfl_sync(0xffffffffu, fmaf(st->coef_g, gg, t), 0);
+  __syncwarp();
+  if (!(gd < 0.f)) {  // not a descent direction: reset the memory, steepest descent
+    for (int j = lane; j < SOLVER_MAX_SLOTS; j += 32) {
+      st->coef_s[j] = 0.f;
+      st->coef_y[j] = 0.f;
+    }
+    if (lane == 0) {
+      st->count = 0;
+      st->coef_g = -1.f;
+    }
+    gd = -gg;
   }
+  __syncwarp();
+  if (lane != 0) return;
   LineSearch& L = st->ls;
   // phi'(0) = g . d from the same inner products: d is a combination of g and the live
   // pairs, so g . d needs no pass over the vectors.
   L.g0 = gd;
   L.g_prev = gd;
-  L.a = st->count == 0 ? fmin(1.0, 1.0 / st->g1) : 1.0;
+  L.a = st->count == 0 ? (double)fminf(1.f, 1.f / (float)st->g1) : 1.0;
   L.f0 = st->f;
   L.a_prev = 0.0;
   L.f_prev = st->f;
@@ -378,22 +363,88 @@ __device__ void iteration_finish(SolverState* st) {
   L.best_a = 0.0;
   L.best_gg = INFINITY;
   L.force = 0;
-  L.state = (gd < 0.0 && isfinite(gd)) ? LS_RUNNING : LS_FAILED;  // not a descent direction
+  L.state = (gd < 0.f && isfinite(gd)) ? LS_RUNNING : LS_FAILED;  // not a descent direction
+  st->gate = (st->active && L.state == LS_RUNNING) ? 1 : 0;
 }
 
-// Accepting a step: s = x_t - x and y = g_t - g go to the spare history slot, x <- x_t,
-// g <- g_t.  Nothing happens unless the line search accepted.
-__global__ void __launch_bounds__(256) lbfgs_accept_kernel(SolverArgs a) {
-  SolverState* st = a.st;
-  if (!st->active || st->ls.state != LS_ACCEPTED) return;
-  const int64_t N = a.N, sp = st->spare;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x) {
-    const float xo = a.x[e], xn = a.xt[e], go = a.g[e], gn = a.gt[e];
-    a.S[sp * N + e] = xn - xo;
-    a.Y[sp * N + e] = gn - go;
-    a.x[e] = xn;
-    a.g[e] = gn;
+// The two-loop recursion (Nocedal & Wright Alg. 7.4) on the Gram table, run by one warp
+// (count <= 32): lane i holds history pair i (newest first).  Both loops are triangular
+// solves; at step j the lane that owns pair j finishes its coefficient, broadcasts it, and
+// every lane that still needs it adds its product -- one broadcast and one FMA per step
+// instead of a dependent dot product.  float32 throughout (see SolverState).
+__device__ void two_loop_coefs_warp(SolverState* st) {
+  const int lane = threadIdx.x & 31;
+  const int n = st->count;
+  for (int j = lane; j < SOLVER_MAX_SLOTS; j += 32) {
+    st->coef_s[j] = 0.f;
+    st->coef_y[j] = 0.f;
   }
+  __syncwarp();
+  if (n == 0) {
+    if (lane == 0) st->coef_g = -1.f;
+    __syncwarp();
+    return;
+  }
+  const bool mine = lane < n;
+  const int id = mine ? st->ids[lane] : 0;
+  const float rho = mine ? 1.f / st->SY[id][id] : 0.f;
+  const float sg = mine ? st->sg[id] : 0.f, yg = mine ? st->yg[id] : 0.f;
+  // Loop 1 (newest -> oldest): a_i = rho_i (sg_i - sum_{j < i} a_j s_i . y_j).
+  float acc = 0.f, a_mine = 0.f;
+  for (int j = 0; j < n; ++j) {
+    if (lane == j) a_mine = (sg - acc) * rho;
+    const float aj = __shfl_sync(0xffffffffu, a_mine, j);
+    const int idj = st->ids[j];
+    if (mine && lane > j) acc = fmaf(aj, st->SY[id][idj], acc);
+  }
+  const int i0 = st->ids[0];
+  const float gamma = st->SY[i0][i0] / st->YY[i0][i0];
+  // y_i . (sum_j a_j y_j), independent per lane.
+  float ay = 0.f;
+  for (int j = 0; j < n; ++j) {
+    const float aj = __shfl_sync(0xffffffffu, a_mine, j);
+    if (mine) ay = fmaf(aj, st->YY[id][st->ids[j]], ay);
+  }
+  // Loop 2 (oldest -> newest): c_i = a_i - rho_i (gamma (yg_i - ay_i) + sum_{j > i} c_j s_j . y_i).
+  float acc2 = 0.f, c_mine = 0.f;
+  for (int j = n - 1; j >= 0; --j) {
+    if (lane == j) c_mine = a_mine - fmaf(yg - ay, gamma, acc2) * rho;
+    const float cj = __shfl_sync(0xffffffffu, c_mine, j);
+    const int idj = st->ids[j];
+    if (mine && lane < j) acc2 = fmaf(cj, st->SY[idj][id], acc2);
+  }
+  __syncwarp();
+  if (mine) {
+    st->coef_y[id] = gamma * a_mine;
+    st->coef_s[id] = -c_mine;
+  }
+  if (lane == 0) st->coef_g = -gamma;
+  __syncwarp();
+}
+
+// The scalar part of an iteration, run by the last block of the dots reduction: the solver
+// state up to the log rings is copied to shared memory by the whole block, updated there
+// (one thread, then one warp: chains of dependent operations, which must not wait on global
+// memory), and copied back.
+constexpr int SOLVER_CORE_WORDS = (int)(offsetof(SolverState, log_n) / sizeof(double));
+static_assert(offsetof(SolverState, log_n) % sizeof(double) == 0, "solver core must be whole words");
+// fin: the reduced inner products in float64, finf: the same in float32 (shared memory).
+template <int NS>
+__device__ void scalar_tail(SolverState* gst, const double* fin, const float* finf) {
+  __shared__ double core[SOLVER_CORE_WORDS];
+  const double* src = reinterpret_cast<const double*>(gst);
+  for (int i = threadIdx.x; i < SOLVER_CORE_WORDS; i += blockDim.x) core[i] = __ldcg(src + i);
+  __syncthreads();
+  SolverState* s = reinterpret_cast<SolverState*>(core);
+  if (threadIdx.x == 0) iteration_update<NS>(s, gst, fin, finf);
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    two_loop_coefs_warp(s);
+    iteration_finish_warp(s, finf[5 * NS + 5]);
+  }
+  __syncthreads();
+  double* dst = reinterpret_cast<double*>(gst);
+  for (int i = threadIdx.x; i < SOLVER_CORE_WORDS; i += blockDim.x) dst[i] = core[i];
 }
 
 // Inner products.  Block row blockIdx.y = j < NS handles history slot j:
@@ -402,94 +453,13 @@ __global__ void __launch_bounds__(256) lbfgs_accept_kernel(SolverArgs a) {
 //   v[5 NS + 0..6] = s_new.g, y_new.g, s_new.y_new, y_new.y_new, s_new.s_new, g.g, |g|_1
 // Products in float32, summed in float32 over each thread's elements, float64 beyond.
 // The last block to finish runs the scalar part of the iteration.
-// two_loop_coefs run by one warp (count <= 32): lane i holds history pair i (newest first).
-// Both loops of the two-loop recursion are triangular solves; at step j the lane that owns
-// pair j finishes its coefficient, broadcasts it, and every lane that still needs it adds
-// its product -- one broadcast and one FMA per step instead of a dependent dot product.
-// The same terms as two_loop_coefs, each sum taken in the same index order (rounding differs
-// only in that the sum is formed before it is subtracted).
-__device__ void two_loop_coefs_warp(SolverState* st) {
-  const int lane = threadIdx.x & 31;
-  const int n = st->count;
-  for (int j = lane; j < SOLVER_MAX_SLOTS; j += 32) {
-    st->coef_s[j] = 0.0;
-    st->coef_y[j] = 0.0;
-  }
-  __syncwarp();
-  if (n == 0) {
-    if (lane == 0) st->coef_g = -1.0;
-    return;
-  }
-  const bool mine = lane < n;
-  const int id = mine ? st->ids[lane] : 0;
-  const double rho = mine ? 1.0 / st->SY[id][id] : 0.0;
-  const double sg = mine ? st->sg[id] : 0.0, yg = mine ? st->yg[id] : 0.0;
-  // Loop 1 (newest -> oldest): a_i = rho_i (sg_i - sum_{j < i} a_j s_i . y_j).
-  double acc = 0.0, a_mine = 0.0;
-  for (int j = 0; j < n; ++j) {
-    if (lane == j) a_mine = (sg - acc) * rho;
-    const double aj = __shfl_sync(0xffffffffu, a_mine, j);
-    const int idj = st->ids[j];
-    if (mine && lane > j) acc += aj * st->SY[id][idj];
-  }
-  const double gamma = st->SY[st->ids[0]][st->ids[0]] / st->YY[st->ids[0]][st->ids[0]];
-  // y_i . (sum_j a_j y_j), independent per lane.
-  double ay = 0.0;
-  for (int j = 0; j < n; ++j) {
-    const double aj = __shfl_sync(0xffffffffu, a_mine, j);
-    if (mine) ay += aj * st->YY[id][st->ids[j]];
-  }
-  // Loop 2 (oldest -> newest): c_i = a_i - rho_i (gamma (yg_i - ay_i) + sum_{j > i} c_j s_j . y_i).
-  double acc2 = 0.0, c_mine = 0.0;
-  for (int j = n - 1; j >= 0; --j) {
-    if (lane == j) {
-      const double t = (yg - ay) * gamma + acc2;
-      c_mine = a_mine - t * rho;
-    }
-    const double cj = __shfl_sync(0xffffffffu, c_mine, j);
-    const int idj = st->ids[j];
-    if (mine && lane < j) acc2 += cj * st->SY[idj][id];
-  }
-  __syncwarp();
-  if (mine) {
-    st->coef_y[id] = gamma * a_mine;
-    st->coef_s[id] = -c_mine;
-  }
-  if (lane == 0) st->coef_g = -gamma;
-}
-
-// The scalar part of an iteration, run by the last block of the dots reduction: the solver
-// state up to the log rings is copied to shared memory by the whole block, updated there by
-// one thread (a chain of dependent float64 operations, which must not wait on global
-// memory), and copied back.
-constexpr int SOLVER_CORE_WORDS = (int)(offsetof(SolverState, log_n) / sizeof(double));
-static_assert(offsetof(SolverState, log_n) % sizeof(double) == 0, "solver core must be whole words");
-template <int NS>
-__device__ void scalar_tail(SolverState* gst, const double* fin) {
-  __shared__ double core[SOLVER_CORE_WORDS];
-  const double* src = reinterpret_cast<const double*>(gst);
-  for (int i = threadIdx.x; i < SOLVER_CORE_WORDS; i += blockDim.x) core[i] = __ldcg(src + i);
-  __syncthreads();
-  SolverState* s = reinterpret_cast<SolverState*>(core);
-  if (threadIdx.x == 0) iteration_update<NS>(s, gst, fin);
-  __syncthreads();
-  if (threadIdx.x < 32) two_loop_coefs_warp(s);
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    iteration_finish(s);
-    s->gate = (s->active && s->ls.state == LS_RUNNING) ? 1 : 0;
-  }
-  __syncthreads();
-  double* dst = reinterpret_cast<double*>(gst);
-  for (int i = threadIdx.x; i < SOLVER_CORE_WORDS; i += blockDim.x) dst[i] = core[i];
-}
-
 template <int MCAP>
 __global__ void __launch_bounds__(256) lbfgs_dots_kernel(SolverArgs a) {
   constexpr int NS = MCAP + 1;
   constexpr int NV = 5 * NS + 7;
-  __shared__ double red[8][7];
+  __shared__ float red[8][7];
   __shared__ double fin[NV];
+  __shared__ float finf[NV];
   __shared__ bool is_last;
   SolverState* st = a.st;
   if (!st->active) return;
@@ -497,13 +467,18 @@ __global__ void __launch_bounds__(256) lbfgs_dots_kernel(SolverArgs a) {
   const bool accepted = st->ls.state == LS_ACCEPTED;
   bool live = false;
   for (int q = 0; q < st->count; ++q) live |= st->ids[q] == j;
-  const int64_t N = a.N, sp = st->spare;
+  const int64_t N = a.N;
   float acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   if (j < NS ? live : true) {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x) {
-      const float gc = a.g[e];
-      const float s = accepted ? a.S[sp * N + e] : 0.f;
-      const float y = accepted ? a.Y[sp * N + e] : 0.f;
+      const float go = a.g[e];
+      float gc = go, s = 0.f, y = 0.f;
+      if (accepted) {  // the new pair, formed on the fly (stored by the direction kernel)
+        const float xo = a.x[e], xn = a.xt[e], gn = a.gt[e];
+        s = xn - xo;
+        y = gn - go;
+        gc = gn;
+      }
       if (j < NS) {
         const float sj = a.S[(int64_t)j * N + e], yj = a.Y[(int64_t)j * N + e];
         acc[0] = fmaf(sj, gc, acc[0]);
@@ -526,15 +501,17 @@ __global__ void __launch_bounds__(256) lbfgs_dots_kernel(SolverArgs a) {
   const int nv = j < NS ? 5 : 7;
 #pragma unroll
   for (int v = 0; v < 7; ++v) {
-    const double t = warp_sum_d((double)acc[v]);
+    float t = acc[v];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
     if (lane == 0) red[w][v] = t;
   }
   __syncthreads();
   const int64_t bid = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
   if (threadIdx.x < nv) {
-    double t = 0.0;
-    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q][threadIdx.x];
-    a.blk[bid * 7 + threadIdx.x] = t;
+    ff2 t = ff_make(red[0][threadIdx.x]);
+    for (int q = 1; q < (int)(blockDim.x >> 5); ++q) t = ff_add(t, ff_make(red[q][threadIdx.x]));
+    ff_store(&a.blk[bid * 7 + threadIdx.x], t);
   }
   __threadfence();
   __syncthreads();
@@ -542,51 +519,71 @@ __global__ void __launch_bounds__(256) lbfgs_dots_kernel(SolverArgs a) {
   __syncthreads();
   if (!is_last) return;
   __threadfence();
-  // Fixed-order reduction over the x-blocks: warp w owns values w, w + 8, ...
+  // Fixed-order reduction over the x-blocks (float-float): warp w owns values w, w + 8, ...
   for (int v = w; v < NV; v += (int)(blockDim.x >> 5)) {
     const int row = v < 5 * NS ? v / 5 : NS;
     const int col = v < 5 * NS ? v - 5 * (v / 5) : v - 5 * NS;
-    double t = 0.0;
-    for (int b = lane; b < (int)gridDim.x; b += 32) t += __ldcg(&a.blk[((int64_t)row * gridDim.x + b) * 7 + col]);
-    t = warp_sum_d(t);
-    if (lane == 0) fin[v] = t;
+    ff2 t = ff_make(0.f);
+    for (int b = lane; b < (int)gridDim.x; b += 32) t = ff_add(t, ff_load_cg(&a.blk[((int64_t)row * gridDim.x + b) * 7 + col]));
+    t = warp_ff_sum(t);
+    if (lane == 0) {
+      fin[v] = ff_to_d(t);
+      finf[v] = t.hi + t.lo;
+    }
   }
   __syncthreads();
   if (threadIdx.x == 0) *a.counter = 0u;
-  scalar_tail<NS>(st, fin);
+  scalar_tail<NS>(st, fin, finf);
 }
 
-// d = coef_g g + sum over live pairs (coef_s s_j + coef_y y_j), elementwise: the line
-// search's phi'(0) = g . d is formed from the Gram table by the scalar part of the iteration.
-// Two elements per thread (one for memory caps above 10) with every load in flight.
+// The end of a step and the next direction, elementwise.  When the line search accepted
+// (acc_flag), s = x_t - x and y = g_t - g (the same float32 operations as in the inner
+// products) go to history slot acc_slot and x, g move to the trial point; then, while the
+// solver is active, d = coef_g g + sum over live pairs (coef_s s_j + coef_y y_j), the new pair
+// taken from registers.  The line search's phi'(0) = g . d is formed from the Gram table by
+// the scalar part of the iteration.  Two elements per thread (one for memory caps above 10)
+// with every load in flight; the last block (ticket) clears acc_flag.
 template <int MCAP>
-__global__ void __launch_bounds__(256) lbfgs_direction_kernel(SolverArgs a) {
+__global__ void __launch_bounds__(256, MCAP <= 10 ? 2 : 1) lbfgs_direction_kernel(SolverArgs a) {
   constexpr int NS = MCAP + 1;
   __shared__ float cs[NS], cy[NS];
   __shared__ float cg;
   SolverState* st = a.st;
-  if (!st->active) return;
+  const int acc = st->acc_flag, active = st->active;
+  if (!acc && !active) return;
+  const int slot = acc ? st->acc_slot : -1;
   uint64_t live = 0;
-  for (int q = 0; q < st->count; ++q) live |= 1ull << st->ids[q];
+  if (active)
+    for (int q = 0; q < st->count; ++q) live |= 1ull << st->ids[q];
+  const uint64_t load = slot >= 0 ? live & ~(1ull << slot) : live;
   if (threadIdx.x < NS) {
-    cs[threadIdx.x] = (float)st->coef_s[threadIdx.x];
-    cy[threadIdx.x] = (float)st->coef_y[threadIdx.x];
+    cs[threadIdx.x] = st->coef_s[threadIdx.x];
+    cy[threadIdx.x] = st->coef_y[threadIdx.x];
   }
-  if (threadIdx.x == 0) cg = (float)st->coef_g;
+  if (threadIdx.x == 0) cg = st->coef_g;
   __syncthreads();
   constexpr int EPT = NS <= 11 ? 2 : 1;  // elements per thread per pass (register budget)
   const int64_t N = a.N;
   for (int64_t e0 = (int64_t)blockIdx.x * blockDim.x * EPT + threadIdx.x; e0 < N;
        e0 += (int64_t)gridDim.x * blockDim.x * EPT) {
-    float ge[EPT], sv[EPT][NS], yv[EPT][NS];
+    float gn[EPT], xn[EPT], sn[EPT], yn[EPT], sv[EPT][NS], yv[EPT][NS];
 #pragma unroll
     for (int u = 0; u < EPT; ++u) {
       const int64_t e = e0 + u * blockDim.x;
       const bool in = e < N;
-      ge[u] = in ? a.g[e] : 0.f;
+      const float go = in ? a.g[e] : 0.f;
+      gn[u] = go;
+      xn[u] = sn[u] = yn[u] = 0.f;
+      if (acc && in) {
+        const float xo = a.x[e];
+        xn[u] = a.xt[e];
+        gn[u] = a.gt[e];
+        sn[u] = xn[u] - xo;
+        yn[u] = gn[u] - go;
+      }
 #pragma unroll
       for (int j = 0; j < NS; ++j) {
-        const bool use = in && ((live >> j) & 1ull);
+        const bool use = in && ((load >> j) & 1ull);
         sv[u][j] = use ? a.S[(int64_t)j * N + e] : 0.f;
         yv[u][j] = use ? a.Y[(int64_t)j * N + e] : 0.f;
       }
@@ -594,15 +591,33 @@ __global__ void __launch_bounds__(256) lbfgs_direction_kernel(SolverArgs a) {
 #pragma unroll
     for (int u = 0; u < EPT; ++u) {
       const int64_t e = e0 + u * blockDim.x;
-      float dv = cg * ge[u];
-#pragma unroll
-      for (int j = 0; j < NS; ++j) {
-        if ((live >> j) & 1ull) {
-          dv = fmaf(cs[j], sv[u][j], dv);
-          dv = fmaf(cy[j], yv[u][j], dv);
+      if (e >= N) continue;
+      if (acc) {
+        if (slot >= 0) {
+          a.S[(int64_t)slot * N + e] = sn[u];
+          a.Y[(int64_t)slot * N + e] = yn[u];
         }
+        a.x[e] = xn[u];
+        a.g[e] = gn[u];
       }
-      if (e < N) a.d[e] = dv;
+      if (active) {
+        float dv = cg * gn[u];
+#pragma unroll
+        for (int j = 0; j < NS; ++j) {
+          if ((live >> j) & 1ull) {
+            dv = fmaf(cs[j], j == slot ? sn[u] : sv[u][j], dv);
+            dv = fmaf(cy[j], j == slot ? yn[u] : yv[u][j], dv);
+          }
+        }
+        a.d[e] = dv;
+      }
+    }
+  }
+  if (acc) {  // every block has read acc_flag by the time the last one arrives
+    __syncthreads();
+    if (threadIdx.x == 0 && atomicAdd(a.counter + 2 + DOTS_MAX_GRP, 1u) == gridDim.x - 1) {
+      a.counter[2 + DOTS_MAX_GRP] = 0u;
+      st->acc_flag = 0;
     }
   }
 }
@@ -624,6 +639,8 @@ __global__ void solver_init_kernel(SolverState* st, int mem, int max_iter, doubl
   st->gtol = gtol;
   st->ls_noise = ls_noise;
   st->ls.state = LS_NONE;
+  st->acc_flag = 0;
+  st->acc_slot = -1;
   st->log_n = 0;
   st->tlog_n = 0;
 }
@@ -654,55 +671,47 @@ struct SolverBuffers {
 
 static int mem_cap(int mem) { return mem <= 4 ? 4 : (mem <= 10 ? 10 : (mem <= 16 ? 16 : 32)); }
 
-// Accept and dots in one pass (memory caps whose 5 (MCAP + 1) + 7 sums fit in 64 registers):
-// each element of x, g, x_t, g_t and of every live history pair is read once; the thread
-// keeps all the sums of its elements, a warp reduce-scatter leaves two per lane, the warps are
-// added in a fixed order, and the last block (ticket) adds the blocks in a fixed order and
-// runs the scalar part of the iteration.
+// Inner products in one pass (memory caps whose 5 (MCAP + 1) + 7 sums fit in 64 registers),
+// in the layout of lbfgs_dots_kernel.  Each element of x, g, x_t, g_t and of every live
+// history pair is read once and nothing is written, so the loads of successive elements can
+// be in flight together; when the line search accepted, s = x_t - x and y = g_t - g are
+// formed on the fly (the direction kernel stores them and moves x, g to the trial point).
+// The thread keeps all the sums of its elements, a warp reduce-scatter leaves two per lane,
+// the warps are added in a fixed order, the last block of each group of DOTS_GRP blocks adds
+// the group and the last group adds the groups (float-float throughout, fixed order); that
+// block runs the scalar part of the iteration.
 template <int MCAP>
-__global__ void __launch_bounds__(256) lbfgs_accept_dots_kernel(SolverArgs a) {
+__global__ void __launch_bounds__(256, 2) lbfgs_dots1_kernel(SolverArgs a) {
   constexpr int NS = MCAP + 1;
   constexpr int NV = 5 * NS + 7;
   static_assert(NV <= 64, "too many sums for the one-pass kernel");
-  __shared__ double red[8][64];
+  __shared__ float red[8][64];
   __shared__ double fin[64];
+  __shared__ float finf[64];
   __shared__ bool is_last;
   SolverState* st = a.st;
   if (!st->active) return;
   const bool accepted = st->ls.state == LS_ACCEPTED;
   unsigned int live = 0;
   for (int q = 0; q < st->count; ++q) live |= 1u << st->ids[q];
-  const int64_t N = a.N, sp = st->spare;
+  const int64_t N = a.N;
   float acc[64];
 #pragma unroll
   for (int v = 0; v < 64; ++v) acc[v] = 0.f;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x) {
-    // Every load of the element first -- all history slots (every slot lies inside the
-    // history buffers; only the live ones are summed) and the four vectors -- so that they
-    // are in flight together: the stores below would otherwise order the slot loads after
-    // them (one memory round trip more per element).  The slot the new pair goes to is the
-    // spare one, never live, so its stale value loaded here is not used.
     float sv[NS], yv[NS];
 #pragma unroll
     for (int j = 0; j < NS; ++j) {
-      sv[j] = a.S[(int64_t)j * N + e];
-      yv[j] = a.Y[(int64_t)j * N + e];
+      const bool use = (live >> j) & 1u;
+      sv[j] = use ? a.S[(int64_t)j * N + e] : 0.f;
+      yv[j] = use ? a.Y[(int64_t)j * N + e] : 0.f;
     }
     const float go = a.g[e];
-    float xo = 0.f, xn = 0.f, gn = 0.f;
-    if (accepted) {
-      xo = a.x[e];
-      xn = a.xt[e];
-      gn = a.gt[e];
-    }
     float gc = go, s = 0.f, y = 0.f;
     if (accepted) {
+      const float xo = a.x[e], xn = a.xt[e], gn = a.gt[e];
       s = xn - xo;
       y = gn - go;
-      a.S[sp * N + e] = s;
-      a.Y[sp * N + e] = y;
-      a.x[e] = xn;
-      a.g[e] = gn;
       gc = gn;
     }
 #pragma unroll
@@ -726,13 +735,13 @@ __global__ void __launch_bounds__(256) lbfgs_accept_dots_kernel(SolverArgs a) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   int base = 0;
   ReduceScatter<64, 16>::run(acc, lane, base);
-  red[w][base] = (double)acc[0];
-  red[w][base + 1] = (double)acc[1];
+  red[w][base] = acc[0];
+  red[w][base + 1] = acc[1];
   __syncthreads();
   if (threadIdx.x < NV) {
-    double t = 0.0;
-    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q][threadIdx.x];
-    a.blk[(int64_t)blockIdx.x * 64 + threadIdx.x] = t;
+    ff2 t = ff_make(red[0][threadIdx.x]);
+    for (int q = 1; q < (int)(blockDim.x >> 5); ++q) t = ff_add(t, ff_make(red[q][threadIdx.x]));
+    ff_store(&a.blk[(int64_t)blockIdx.x * 64 + threadIdx.x], t);
   }
   // Two-level ticket tree (one L2 round trip per level instead of one per block): the last
   // block of each group of DOTS_GRP blocks sums the group, the last group sums the groups.
@@ -745,12 +754,16 @@ __global__ void __launch_bounds__(256) lbfgs_accept_dots_kernel(SolverArgs a) {
   if (!is_last) return;
   __threadfence();
   double* gblk = a.blk + (int64_t)nb * 64;
-  if (threadIdx.x < 64) {
-    double t = 0.0;
+  if (threadIdx.x < NV) {
+    ff2 p[DOTS_GRP];
 #pragma unroll
     for (int u = 0; u < DOTS_GRP; ++u)
-      if (u < gsize) t += __ldcg(&a.blk[(int64_t)(grp * DOTS_GRP + u) * 64 + threadIdx.x]);
-    gblk[grp * 64 + threadIdx.x] = t;
+      p[u] = u < gsize ? ff_load_cg(&a.blk[(int64_t)(grp * DOTS_GRP + u) * 64 + threadIdx.x]) : ff_make(0.f);
+    ff2 t = p[0];
+#pragma unroll
+    for (int u = 1; u < DOTS_GRP; ++u)
+      if (u < gsize) t = ff_add(t, p[u]);
+    ff_store(&gblk[grp * 64 + threadIdx.x], t);
   }
   if (threadIdx.x == 0) a.counter[1 + grp] = 0u;
   __threadfence();
@@ -759,23 +772,23 @@ __global__ void __launch_bounds__(256) lbfgs_accept_dots_kernel(SolverArgs a) {
   __syncthreads();
   if (!is_last) return;
   __threadfence();
-  if (threadIdx.x < 64) {
-    double t = 0.0;
+  if (threadIdx.x < NV) {
+    ff2 t = ff_load_cg(&gblk[threadIdx.x]);
 #pragma unroll 8
-    for (int q = 0; q < ngrp; ++q) t += __ldcg(&gblk[q * 64 + threadIdx.x]);
-    fin[threadIdx.x] = t;
+    for (int q = 1; q < ngrp; ++q) t = ff_add(t, ff_load_cg(&gblk[q * 64 + threadIdx.x]));
+    fin[threadIdx.x] = ff_to_d(t);
+    finf[threadIdx.x] = t.hi + t.lo;
   }
   __syncthreads();
   if (threadIdx.x == 0) *a.counter = 0u;
-  scalar_tail<NS>(st, fin);
+  scalar_tail<NS>(st, fin, finf);
 }
 
 template <int MCAP>
 static cudaError_t launch_update(const SolverArgs& a, int grid, cudaStream_t s) {
   if constexpr (5 * (MCAP + 1) + 7 <= 64) {
-    lbfgs_accept_dots_kernel<MCAP><<<grid, 256, 0, s>>>(a);
+    lbfgs_dots1_kernel<MCAP><<<grid, 256, 0, s>>>(a);
   } else {
-    lbfgs_accept_kernel<<<grid, 256, 0, s>>>(a);
     const int gx = std::max(1, grid / (MCAP + 2));
     lbfgs_dots_kernel<MCAP><<<dim3(gx, MCAP + 2), 256, 0, s>>>(a);
   }
@@ -790,7 +803,7 @@ static cudaError_t launch_direction(const SolverArgs& a, int grid, cudaStream_t 
 }
 
 // Kernels launched by update_and_direction.
-static int update_launches(int mcap) { return 5 * (mcap + 1) + 7 <= 64 ? 2 : 3; }
+static int update_launches(int) { return 2; }
 
 static cudaError_t update_and_direction(int mcap, const SolverArgs& a, int grid, cudaStream_t s) {
   cudaError_t e;

@@ -33,11 +33,19 @@ struct SolverState {
   double out[4];  // finalize output of the last trial: f, g.d, ||g||^2, ||x||^2
   LineSearch ls;
   int mem, count, spare;
+  // Set by the scalar part when a line search has accepted its trial: the direction kernel
+  // then moves x, g to the trial point and stores the new pair in slot acc_slot (-1: the
+  // pair failed the curvature test and is not kept), and its last block clears acc_flag.
+  int acc_flag, acc_slot;
   int ids[SOLVER_MAX_SLOTS];  // history slots in the ring, newest first
-  double SY[SOLVER_MAX_SLOTS][SOLVER_MAX_SLOTS];  // s_i . y_j by slot
-  double YY[SOLVER_MAX_SLOTS][SOLVER_MAX_SLOTS];  // y_i . y_j by slot
-  double sg[SOLVER_MAX_SLOTS], yg[SOLVER_MAX_SLOTS];
-  double coef_g, coef_s[SOLVER_MAX_SLOTS], coef_y[SOLVER_MAX_SLOTS];
+  // The Gram table, the two-loop coefficients and the inner products they come from are
+  // float32: their inputs are float32 vectors, the direction is formed with float32
+  // coefficients, and a float64 operation costs 64 cycles on GB300 (a divide ~570), which
+  // made the two-loop recursion the longest step of an iteration.
+  float SY[SOLVER_MAX_SLOTS][SOLVER_MAX_SLOTS];  // s_i . y_j by slot
+  float YY[SOLVER_MAX_SLOTS][SOLVER_MAX_SLOTS];  // y_i . y_j by slot
+  float sg[SOLVER_MAX_SLOTS], yg[SOLVER_MAX_SLOTS];
+  float coef_g, coef_s[SOLVER_MAX_SLOTS], coef_y[SOLVER_MAX_SLOTS];
   int iter, evals, active, gate, stop, fails, max_iter;
   double gtol;
   double ls_noise;  // relative noise level of f for the approximate Wolfe test
