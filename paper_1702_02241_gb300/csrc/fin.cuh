@@ -12,14 +12,15 @@ namespace rpca {
 // Gradient assembly.  Blocks [0, a.gu) handle the m x B side, FIN_EPT elements per thread
 // (strided by the blocks of that side, so that each round is coalesced and all rounds' loads
 // are in flight together): the column-split partials of PU are summed and
-// G_U = lam_L U_t - PU (fg) or D Bv = -PU (apply) is written.  The other blocks handle the n x B side, 64 elements
-// per block: four groups of 64 threads each sum every fourth row-block partial of PV
-// (coalesced across consecutive columns) and the groups are added in a fixed order.
+// G_U = lam_L U_t - PU (fg) or D Bv = -PU (apply) is written.  The other blocks handle the n x B side, 32 elements
+// per block: eight groups of 32 threads each sum every eighth row-block partial of PV
+// (coalesced across consecutive columns, loaded FIN_VB at a time, all in flight) and the
+// groups are added in a fixed order.
 // Elementwise work is float32 (the partial sums are float32 already); each block's dot
 // products (||x_t||^2, g.d, ||g||^2) go to float-float for the fixed-order block sums.
 RPCA_DEV void finalize_body(const FinArgs& a) {
   __shared__ float wsum[32][3];
-  __shared__ float vs[4][64];
+  __shared__ float vs[8][32];
   __shared__ float alpha_s;
   // Conversions from float64 and 64-bit divisions run on the float64 pipe, which is narrow on
   // this GPU: the step is converted once per block, indices use 32-bit unsigned division
@@ -75,8 +76,8 @@ RPCA_DEV void finalize_body(const FinArgs& a) {
       }
     }
   } else {
-    const int q = threadIdx.x >> 6, t = threadIdx.x & 63;
-    const unsigned e2 = (blockIdx.x - a.gu) * 64 + t;
+    const int q = threadIdx.x >> 5, t = threadIdx.x & 31;
+    const unsigned e2 = (blockIdx.x - a.gu) * 32 + t;
     const bool live = a.side != 1 && e2 < nB;
     unsigned l = 0, j = 0;
     float s = 0.f;
@@ -85,13 +86,21 @@ RPCA_DEV void finalize_body(const FinArgs& a) {
       j = e2 - l * (unsigned)a.n;
       const float* pv = a.PV + (int64_t)l * a.n + j;
       const int64_t rstride = (int64_t)a.B * a.n;
-#pragma unroll 8
-      for (int r = q; r < a.nrb; r += 4) s += pv[r * rstride];
+      for (int r0 = q; r0 < a.nrb; r0 += 8 * FIN_VB) {
+        float tv[FIN_VB];
+#pragma unroll
+        for (int u = 0; u < FIN_VB; ++u) {
+          const int r = r0 + 8 * u;
+          tv[u] = r < a.nrb ? pv[r * rstride] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < FIN_VB; ++u) s += tv[u];
+      }
     }
     vs[q][t] = s;
     __syncthreads();
     if (q == 0 && live) {
-      s = (vs[0][t] + vs[1][t]) + (vs[2][t] + vs[3][t]);
+      s = ((vs[0][t] + vs[1][t]) + (vs[2][t] + vs[3][t])) + ((vs[4][t] + vs[5][t]) + (vs[6][t] + vs[7][t]));
       float g, xt = 0.f, dir = 0.f;
       if (a.vpart) {
         g = s;  // this row shard's D^T U; the shards' sum and lam_L V come later

@@ -42,14 +42,15 @@ struct FinArgs {
   int vpart;
 };
 
-// Finalize grid: FIN_EPT elements per thread of the m x B side (256 threads per block), 64
-// elements (four groups of 64 threads splitting the row-block partials) per block on the
-// n x B side.
+// Finalize grid: FIN_EPT elements per thread of the m x B side (256 threads per block), 32
+// elements (eight groups of 32 threads splitting the row-block partials, FIN_VB loads in
+// flight per thread) per block on the n x B side.
 constexpr int FIN_EPT = 4;
+constexpr int FIN_VB = 16;
 inline int fin_grid_u(int64_t m, int B) {
   return (int)std::max<int64_t>(1, (m * B + 256 * FIN_EPT - 1) / (256 * FIN_EPT));
 }
-inline int fin_grid_v(int64_t n, int B) { return (int)std::max<int64_t>(1, (n * B + 63) / 64); }
+inline int fin_grid_v(int64_t n, int B) { return (int)std::max<int64_t>(1, (n * B + 31) / 32); }
 
 __global__ void finalize_kernel(FinArgs a);
 __global__ void finalize_reduce_kernel(FinArgs a, int nblocks);

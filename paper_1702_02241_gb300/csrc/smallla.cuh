@@ -5,14 +5,18 @@
 
 namespace rpca {
 
-// Round-robin ("circle") schedule of ne players (ne even): pair k of round r.
+// Round-robin ("circle") schedule of ne players (ne even): pair k of round r (0 <= r < ne - 1,
+// 0 <= k < ne / 2).  Conditional subtractions instead of a modulo by a runtime value.
 RPCA_DEV void rr_pair(int r, int k, int ne, int& p, int& q) {
   if (k == 0) {
     p = ne - 1;
     q = r;
   } else {
-    p = (r + k) % (ne - 1);
-    q = (r - k + ne - 1) % (ne - 1);
+    const int m = ne - 1;
+    p = r + k;
+    if (p >= m) p -= m;
+    q = r - k;
+    if (q < 0) q += m;
   }
 }
 
@@ -42,9 +46,16 @@ RPCA_DEV bool jacobi_rotation(T al, T be, T ga, T& cs, T& sn) {
   const T sc = pow2_inv_scale(al + be);
   const float g = (float)(ga * sc);
   if (!(fabsf(g) >= 1e-30f && fabsf(g) <= 2.f)) return false;
+  // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)) from the approximate reciprocal and
+  // reciprocal square root (each a single instruction; the IEEE-rounded forms are call
+  // sequences, and a round of the CTA form is bound by instruction issue).  Above 2^32 the
+  // square root is |zeta| in float32 (and 1 + zeta^2 would overflow further up).
   const float zeta = __fdividef((float)((be - al) * sc), 2.f * g);
-  const float tf = copysignf(1.f, zeta) * __frcp_rn(fabsf(zeta) + __fsqrt_rn(fmaf(zeta, zeta, 1.f)));
-  const float csf = __frsqrt_rn(fmaf(tf, tf, 1.f));
+  const float az = fabsf(zeta);
+  const float z2 = fmaf(zeta, zeta, 1.f);
+  const float root = az < 4.0e9f ? z2 * rsqrtf(z2) : az;
+  const float tf = copysignf(__fdividef(1.f, az + root), zeta);
+  const float csf = rsqrtf(fmaf(tf, tf, 1.f));
   cs = (T)csf;
   sn = (T)(csf * tf);
   const T corr = T(1.5) - T(0.5) * (cs * cs + sn * sn);
@@ -162,9 +173,16 @@ __device__ int warp_jacobi_svd(T* A, int rows, int cols, int lda, T* V, int ldv,
     bool rotated = false;
     for (int r = 0; r < ne - 1; ++r) {
       int partner;
-      if (lane == ne - 1) partner = r;
-      else if (lane == r) partner = ne - 1;
-      else partner = (2 * r - lane + 2 * (ne - 1)) % (ne - 1);
+      if (lane == ne - 1) {
+        partner = r;
+      } else if (lane == r) {
+        partner = ne - 1;
+      } else {  // (2 r - lane) mod (ne - 1), by conditional subtractions
+        const int m = ne - 1;
+        partner = 2 * r - lane + 2 * m;
+        if (partner >= 2 * m) partner -= 2 * m;
+        if (partner >= m) partner -= m;
+      }
       const bool act = mine && partner < cols && lane < ne;
       const int src = act ? partner : lane;
       T b[RMAX];

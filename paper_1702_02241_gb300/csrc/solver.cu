@@ -671,40 +671,58 @@ struct SolverBuffers {
 
 static int mem_cap(int mem) { return mem <= 4 ? 4 : (mem <= 10 ? 10 : (mem <= 16 ? 16 : 32)); }
 
-// Inner products in one pass (memory caps whose 5 (MCAP + 1) + 7 sums fit in 64 registers),
-// in the layout of lbfgs_dots_kernel.  Each element of x, g, x_t, g_t and of every live
-// history pair is read once and nothing is written, so the loads of successive elements can
-// be in flight together; when the line search accepted, s = x_t - x and y = g_t - g are
-// formed on the fly (the direction kernel stores them and moves x, g to the trial point).
-// The thread keeps all the sums of its elements, a warp reduce-scatter leaves two per lane,
-// the warps are added in a fixed order, the last block of each group of DOTS_GRP blocks adds
-// the group and the last group adds the groups (float-float throughout, fixed order); that
-// block runs the scalar part of the iteration.
+// Inner products in one pass over the elements (memory caps whose 5 (MCAP + 1) + 7 sums fit
+// in 64), in the layout of lbfgs_dots_kernel.  The history slots are split between the two
+// block rows (blockIdx.y; one row when there are few slots): row 0 takes the first half of
+// the slots and the seven sums of the new pair and the gradient, row 1 the rest, so that a
+// thread holds at most 5 ceil(NS / 2) + 7 sums and four CTAs fit on an SM.  Each element of
+// x, g, x_t, g_t is read by both rows, every live history pair once, and nothing is written
+// (loads of successive elements can be in flight together); when the line search accepted,
+// s = x_t - x and y = g_t - g are formed on the fly (the direction kernel stores them and moves
+// x, g to the trial point).  A warp reduce-scatter leaves a few sums per lane, the warps are
+// added in a fixed order, the last block of each group of DOTS_GRP columns of blocks adds the
+// group and the last group adds the groups (float-float throughout, fixed order); that block
+// runs the scalar part of the iteration.
+template <int NS>
+struct Dots1Shape {
+  static constexpr int ROWS = NS > 6 ? 2 : 1;         // block rows
+  static constexpr int H = (NS + ROWS - 1) / ROWS;    // slots per row (at most)
+  static constexpr int C = ((5 * H + 7) + 7) & ~7;    // sums per thread, padded to a multiple of 8
+};
 template <int MCAP>
-__global__ void __launch_bounds__(256, 2) lbfgs_dots1_kernel(SolverArgs a) {
+__global__ void __launch_bounds__(256, 4) lbfgs_dots1_kernel(SolverArgs a) {
   constexpr int NS = MCAP + 1;
   constexpr int NV = 5 * NS + 7;
   static_assert(NV <= 64, "too many sums for the one-pass kernel");
-  __shared__ float red[8][64];
+  using Sh = Dots1Shape<NS>;
+  constexpr int C = Sh::C, H = Sh::H;
+  constexpr int RC = rs_count(C);
+  __shared__ float red[8][C];
   __shared__ double fin[64];
   __shared__ float finf[64];
   __shared__ bool is_last;
   SolverState* st = a.st;
   if (!st->active) return;
+  const int row = blockIdx.y;
+  const int j0 = row * H, nj = min(H, NS - j0);  // this row's slots [j0, j0 + nj)
+  const bool own_new = row == 0;                 // row 0 also sums the new pair and g
   const bool accepted = st->ls.state == LS_ACCEPTED;
   unsigned int live = 0;
   for (int q = 0; q < st->count; ++q) live |= 1u << st->ids[q];
+  live = (live >> j0) & ((1u << nj) - 1u);
   const int64_t N = a.N;
-  float acc[64];
+  const float* S0 = a.S + (int64_t)j0 * N;
+  const float* Y0 = a.Y + (int64_t)j0 * N;
+  float acc[C];
 #pragma unroll
-  for (int v = 0; v < 64; ++v) acc[v] = 0.f;
+  for (int v = 0; v < C; ++v) acc[v] = 0.f;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x) {
-    float sv[NS], yv[NS];
+    float sv[H], yv[H];
 #pragma unroll
-    for (int j = 0; j < NS; ++j) {
-      const bool use = (live >> j) & 1u;
-      sv[j] = use ? a.S[(int64_t)j * N + e] : 0.f;
-      yv[j] = use ? a.Y[(int64_t)j * N + e] : 0.f;
+    for (int jj = 0; jj < H; ++jj) {
+      const bool use = (live >> jj) & 1u;
+      sv[jj] = use ? S0[(int64_t)jj * N + e] : 0.f;
+      yv[jj] = use ? Y0[(int64_t)jj * N + e] : 0.f;
     }
     const float go = a.g[e];
     float gc = go, s = 0.f, y = 0.f;
@@ -715,41 +733,49 @@ __global__ void __launch_bounds__(256, 2) lbfgs_dots1_kernel(SolverArgs a) {
       gc = gn;
     }
 #pragma unroll
-    for (int j = 0; j < NS; ++j) {
-      if ((live >> j) & 1u) {
-        acc[5 * j + 0] = fmaf(sv[j], gc, acc[5 * j + 0]);
-        acc[5 * j + 1] = fmaf(yv[j], gc, acc[5 * j + 1]);
-        acc[5 * j + 2] = fmaf(sv[j], y, acc[5 * j + 2]);
-        acc[5 * j + 3] = fmaf(s, yv[j], acc[5 * j + 3]);
-        acc[5 * j + 4] = fmaf(y, yv[j], acc[5 * j + 4]);
+    for (int jj = 0; jj < H; ++jj) {
+      if ((live >> jj) & 1u) {
+        acc[5 * jj + 0] = fmaf(sv[jj], gc, acc[5 * jj + 0]);
+        acc[5 * jj + 1] = fmaf(yv[jj], gc, acc[5 * jj + 1]);
+        acc[5 * jj + 2] = fmaf(sv[jj], y, acc[5 * jj + 2]);
+        acc[5 * jj + 3] = fmaf(s, yv[jj], acc[5 * jj + 3]);
+        acc[5 * jj + 4] = fmaf(y, yv[jj], acc[5 * jj + 4]);
       }
     }
-    acc[5 * NS + 0] = fmaf(s, gc, acc[5 * NS + 0]);
-    acc[5 * NS + 1] = fmaf(y, gc, acc[5 * NS + 1]);
-    acc[5 * NS + 2] = fmaf(s, y, acc[5 * NS + 2]);
-    acc[5 * NS + 3] = fmaf(y, y, acc[5 * NS + 3]);
-    acc[5 * NS + 4] = fmaf(s, s, acc[5 * NS + 4]);
-    acc[5 * NS + 5] = fmaf(gc, gc, acc[5 * NS + 5]);
-    acc[5 * NS + 6] += fabsf(gc);
+    if (own_new) {
+      acc[5 * H + 0] = fmaf(s, gc, acc[5 * H + 0]);
+      acc[5 * H + 1] = fmaf(y, gc, acc[5 * H + 1]);
+      acc[5 * H + 2] = fmaf(s, y, acc[5 * H + 2]);
+      acc[5 * H + 3] = fmaf(y, y, acc[5 * H + 3]);
+      acc[5 * H + 4] = fmaf(s, s, acc[5 * H + 4]);
+      acc[5 * H + 5] = fmaf(gc, gc, acc[5 * H + 5]);
+      acc[5 * H + 6] += fabsf(gc);
+    }
   }
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   int base = 0;
-  ReduceScatter<64, 16>::run(acc, lane, base);
-  red[w][base] = acc[0];
-  red[w][base + 1] = acc[1];
+  ReduceScatter<C, 16>::run(acc, lane, base);
+#pragma unroll
+  for (int t = 0; t < RC; ++t) red[w][base + t] = acc[t];
   __syncthreads();
-  if (threadIdx.x < NV) {
-    ff2 t = ff_make(red[0][threadIdx.x]);
-    for (int q = 1; q < (int)(blockDim.x >> 5); ++q) t = ff_add(t, ff_make(red[q][threadIdx.x]));
-    ff_store(&a.blk[(int64_t)blockIdx.x * 64 + threadIdx.x], t);
+  // Local sum index u -> global layout v: slot sums 5 (j0 + jj) + c, the new pair's 5 NS + c.
+  const int nloc = 5 * nj + (own_new ? 7 : 0);
+  if (threadIdx.x < nloc) {
+    const int u = threadIdx.x;
+    const int ul = u < 5 * nj ? u : 5 * H + (u - 5 * nj);
+    const int v = u < 5 * nj ? 5 * j0 + u : 5 * NS + (u - 5 * nj);
+    ff2 t = ff_make(red[0][ul]);
+    for (int q = 1; q < (int)(blockDim.x >> 5); ++q) t = ff_add(t, ff_make(red[q][ul]));
+    ff_store(&a.blk[(int64_t)blockIdx.x * 64 + v], t);
   }
-  // Two-level ticket tree (one L2 round trip per level instead of one per block): the last
-  // block of each group of DOTS_GRP blocks sums the group, the last group sums the groups.
+  // Two-level ticket tree over the columns of blocks (both rows of a column write disjoint
+  // sums into its 64 slots): the last of the group's blocks sums the group, the last group
+  // sums the groups.
   const int nb = (int)gridDim.x, grp = blockIdx.x / DOTS_GRP, ngrp = (nb + DOTS_GRP - 1) / DOTS_GRP;
   const int gsize = min(DOTS_GRP, nb - grp * DOTS_GRP);
   __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) is_last = atomicAdd(a.counter + 1 + grp, 1u) == (unsigned)gsize - 1;
+  if (threadIdx.x == 0) is_last = atomicAdd(a.counter + 1 + grp, 1u) == (unsigned)(gsize * (int)gridDim.y) - 1;
   __syncthreads();
   if (!is_last) return;
   __threadfence();
@@ -787,7 +813,8 @@ __global__ void __launch_bounds__(256, 2) lbfgs_dots1_kernel(SolverArgs a) {
 template <int MCAP>
 static cudaError_t launch_update(const SolverArgs& a, int grid, cudaStream_t s) {
   if constexpr (5 * (MCAP + 1) + 7 <= 64) {
-    lbfgs_dots1_kernel<MCAP><<<grid, 256, 0, s>>>(a);
+    // Two blocks per SM per row of blocks: both rows fit at once (four CTAs per SM).
+    lbfgs_dots1_kernel<MCAP><<<dim3(grid, Dots1Shape<MCAP + 1>::ROWS), 256, 0, s>>>(a);
   } else {
     const int gx = std::max(1, grid / (MCAP + 2));
     lbfgs_dots_kernel<MCAP><<<dim3(gx, MCAP + 2), 256, 0, s>>>(a);
