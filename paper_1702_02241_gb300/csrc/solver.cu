@@ -41,6 +41,38 @@ namespace rpca {
 constexpr double LS_C1 = 1e-4, LS_C2 = 0.9, LS_AMAX = 1e10;
 constexpr int LS_MAX_TRIALS = 25;
 
+// Elements per thread and step of the inner-product pass, loaded as one vector.
+constexpr int DOTS_VEC = 2;
+
+template <int NV>
+__device__ __forceinline__ void vec_store(float* p, const float (&v)[NV]) {
+  if constexpr (NV == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  } else if constexpr (NV == 2) {
+    *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+  } else {
+    *p = v[0];
+  }
+}
+
+// n consecutive floats at p (16-byte aligned for n = 4, 8-byte for n = 2), or zeros when !use.
+template <int NV>
+__device__ __forceinline__ void vec_load(float (&out)[NV], const float* p, bool use) {
+  if constexpr (NV == 4) {
+    const float4 t = use ? *reinterpret_cast<const float4*>(p) : make_float4(0.f, 0.f, 0.f, 0.f);
+    out[0] = t.x;
+    out[1] = t.y;
+    out[2] = t.z;
+    out[3] = t.w;
+  } else if constexpr (NV == 2) {
+    const float2 t = use ? *reinterpret_cast<const float2*>(p) : make_float2(0.f, 0.f);
+    out[0] = t.x;
+    out[1] = t.y;
+  } else {
+    out[0] = use ? *p : 0.f;
+  }
+}
+
 constexpr int DOTS_GRP = 16;      // blocks per group of the two-level reduction
 constexpr int DOTS_MAX_GRP = 60;  // groups the counter buffer has room for
 
@@ -562,55 +594,51 @@ __global__ void __launch_bounds__(256, MCAP <= 10 ? 2 : 1) lbfgs_direction_kerne
   }
   if (threadIdx.x == 0) cg = st->coef_g;
   __syncthreads();
-  constexpr int EPT = NS <= 11 ? 2 : 1;  // elements per thread per pass (register budget)
+  // EPT consecutive elements per thread and step, each vector loaded and stored at once (the
+  // vectors are padded to a multiple of 4 elements); two for memory caps up to 10.
+  constexpr int EPT = NS <= 11 ? 2 : 1;
   const int64_t N = a.N;
-  for (int64_t e0 = (int64_t)blockIdx.x * blockDim.x * EPT + threadIdx.x; e0 < N;
-       e0 += (int64_t)gridDim.x * blockDim.x * EPT) {
-    float gn[EPT], xn[EPT], sn[EPT], yn[EPT], sv[EPT][NS], yv[EPT][NS];
+  for (int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * EPT; e < N;
+       e += (int64_t)gridDim.x * blockDim.x * EPT) {
+    float go[EPT], gn[EPT], xo[EPT], xn[EPT], sn[EPT], yn[EPT], sv[NS][EPT], yv[NS][EPT];
+    vec_load<EPT>(go, a.g + e, true);
+    vec_load<EPT>(xo, a.x + e, acc);
+    vec_load<EPT>(xn, a.xt + e, acc);
+    vec_load<EPT>(gn, a.gt + e, acc);
 #pragma unroll
-    for (int u = 0; u < EPT; ++u) {
-      const int64_t e = e0 + u * blockDim.x;
-      const bool in = e < N;
-      const float go = in ? a.g[e] : 0.f;
-      gn[u] = go;
-      xn[u] = sn[u] = yn[u] = 0.f;
-      if (acc && in) {
-        const float xo = a.x[e];
-        xn[u] = a.xt[e];
-        gn[u] = a.gt[e];
-        sn[u] = xn[u] - xo;
-        yn[u] = gn[u] - go;
-      }
-#pragma unroll
-      for (int j = 0; j < NS; ++j) {
-        const bool use = in && ((load >> j) & 1ull);
-        sv[u][j] = use ? a.S[(int64_t)j * N + e] : 0.f;
-        yv[u][j] = use ? a.Y[(int64_t)j * N + e] : 0.f;
-      }
+    for (int j = 0; j < NS; ++j) {
+      const bool use = (load >> j) & 1ull;
+      vec_load<EPT>(sv[j], a.S + (int64_t)j * N + e, use);
+      vec_load<EPT>(yv[j], a.Y + (int64_t)j * N + e, use);
     }
 #pragma unroll
     for (int u = 0; u < EPT; ++u) {
-      const int64_t e = e0 + u * blockDim.x;
-      if (e >= N) continue;
-      if (acc) {
-        if (slot >= 0) {
-          a.S[(int64_t)slot * N + e] = sn[u];
-          a.Y[(int64_t)slot * N + e] = yn[u];
-        }
-        a.x[e] = xn[u];
-        a.g[e] = gn[u];
+      sn[u] = xn[u] - xo[u];  // zero unless accepted
+      yn[u] = acc ? gn[u] - go[u] : 0.f;
+      if (!acc) gn[u] = go[u];
+    }
+    if (acc) {
+      if (slot >= 0) {
+        vec_store<EPT>(a.S + (int64_t)slot * N + e, sn);
+        vec_store<EPT>(a.Y + (int64_t)slot * N + e, yn);
       }
-      if (active) {
-        float dv = cg * gn[u];
+      vec_store<EPT>(a.x + e, xn);
+      vec_store<EPT>(a.g + e, gn);
+    }
+    if (active) {
+      float dv[EPT];
+#pragma unroll
+      for (int u = 0; u < EPT; ++u) {
+        dv[u] = cg * gn[u];
 #pragma unroll
         for (int j = 0; j < NS; ++j) {
           if ((live >> j) & 1ull) {
-            dv = fmaf(cs[j], j == slot ? sn[u] : sv[u][j], dv);
-            dv = fmaf(cy[j], j == slot ? yn[u] : yv[u][j], dv);
+            dv[u] = fmaf(cs[j], j == slot ? sn[u] : sv[j][u], dv[u]);
+            dv[u] = fmaf(cy[j], j == slot ? yn[u] : yv[j][u], dv[u]);
           }
         }
-        a.d[e] = dv;
       }
+      vec_store<EPT>(a.d + e, dv);
     }
   }
   if (acc) {  // every block has read acc_flag by the time the last one arrives
@@ -675,7 +703,7 @@ static int mem_cap(int mem) { return mem <= 4 ? 4 : (mem <= 10 ? 10 : (mem <= 16
 // in 64), in the layout of lbfgs_dots_kernel.  The history slots are split between the two
 // block rows (blockIdx.y; one row when there are few slots): row 0 takes the first half of
 // the slots and the seven sums of the new pair and the gradient, row 1 the rest, so that a
-// thread holds at most 5 ceil(NS / 2) + 7 sums and four CTAs fit on an SM.  Each element of
+// thread holds at most 5 ceil(NS / 2) + 7 sums and three CTAs fit on an SM.  Each element of
 // x, g, x_t, g_t is read by both rows, every live history pair once, and nothing is written
 // (loads of successive elements can be in flight together); when the line search accepted,
 // s = x_t - x and y = g_t - g are formed on the fly (the direction kernel stores them and moves
@@ -690,7 +718,7 @@ struct Dots1Shape {
   static constexpr int C = ((5 * H + 7) + 7) & ~7;    // sums per thread, padded to a multiple of 8
 };
 template <int MCAP>
-__global__ void __launch_bounds__(256, 4) lbfgs_dots1_kernel(SolverArgs a) {
+__global__ void __launch_bounds__(256, 3) lbfgs_dots1_kernel(SolverArgs a) {
   constexpr int NS = MCAP + 1;
   constexpr int NV = 5 * NS + 7;
   static_assert(NV <= 64, "too many sums for the one-pass kernel");
@@ -716,40 +744,47 @@ __global__ void __launch_bounds__(256, 4) lbfgs_dots1_kernel(SolverArgs a) {
   float acc[C];
 #pragma unroll
   for (int v = 0; v < C; ++v) acc[v] = 0.f;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x) {
-    float sv[H], yv[H];
+  // DOTS_VEC consecutive elements per thread and step, loaded as one vector each (the vectors
+  // are padded to a multiple of 4 elements): the pass reads from L2, where the number of
+  // requests in flight, not the bytes, sets the rate.
+  for (int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * DOTS_VEC; e < N;
+       e += (int64_t)gridDim.x * blockDim.x * DOTS_VEC) {
+    float sv[H][DOTS_VEC], yv[H][DOTS_VEC];
 #pragma unroll
     for (int jj = 0; jj < H; ++jj) {
       const bool use = (live >> jj) & 1u;
-      sv[jj] = use ? S0[(int64_t)jj * N + e] : 0.f;
-      yv[jj] = use ? Y0[(int64_t)jj * N + e] : 0.f;
+      vec_load<DOTS_VEC>(sv[jj], S0 + (int64_t)jj * N + e, use);
+      vec_load<DOTS_VEC>(yv[jj], Y0 + (int64_t)jj * N + e, use);
     }
-    const float go = a.g[e];
-    float gc = go, s = 0.f, y = 0.f;
-    if (accepted) {
-      const float xo = a.x[e], xn = a.xt[e], gn = a.gt[e];
-      s = xn - xo;
-      y = gn - go;
-      gc = gn;
-    }
+    float go[DOTS_VEC], xo[DOTS_VEC], xn[DOTS_VEC], gn[DOTS_VEC];
+    vec_load<DOTS_VEC>(go, a.g + e, true);
+    vec_load<DOTS_VEC>(xo, a.x + e, accepted);
+    vec_load<DOTS_VEC>(xn, a.xt + e, accepted);
+    vec_load<DOTS_VEC>(gn, a.gt + e, accepted);
 #pragma unroll
-    for (int jj = 0; jj < H; ++jj) {
-      if ((live >> jj) & 1u) {
-        acc[5 * jj + 0] = fmaf(sv[jj], gc, acc[5 * jj + 0]);
-        acc[5 * jj + 1] = fmaf(yv[jj], gc, acc[5 * jj + 1]);
-        acc[5 * jj + 2] = fmaf(sv[jj], y, acc[5 * jj + 2]);
-        acc[5 * jj + 3] = fmaf(s, yv[jj], acc[5 * jj + 3]);
-        acc[5 * jj + 4] = fmaf(y, yv[jj], acc[5 * jj + 4]);
+    for (int u = 0; u < DOTS_VEC; ++u) {
+      const float s = xn[u] - xo[u];  // zero unless accepted
+      const float y = accepted ? gn[u] - go[u] : 0.f;
+      const float gc = accepted ? gn[u] : go[u];
+#pragma unroll
+      for (int jj = 0; jj < H; ++jj) {
+        if ((live >> jj) & 1u) {
+          acc[5 * jj + 0] = fmaf(sv[jj][u], gc, acc[5 * jj + 0]);
+          acc[5 * jj + 1] = fmaf(yv[jj][u], gc, acc[5 * jj + 1]);
+          acc[5 * jj + 2] = fmaf(sv[jj][u], y, acc[5 * jj + 2]);
+          acc[5 * jj + 3] = fmaf(s, yv[jj][u], acc[5 * jj + 3]);
+          acc[5 * jj + 4] = fmaf(y, yv[jj][u], acc[5 * jj + 4]);
+        }
       }
-    }
-    if (own_new) {
-      acc[5 * H + 0] = fmaf(s, gc, acc[5 * H + 0]);
-      acc[5 * H + 1] = fmaf(y, gc, acc[5 * H + 1]);
-      acc[5 * H + 2] = fmaf(s, y, acc[5 * H + 2]);
-      acc[5 * H + 3] = fmaf(y, y, acc[5 * H + 3]);
-      acc[5 * H + 4] = fmaf(s, s, acc[5 * H + 4]);
-      acc[5 * H + 5] = fmaf(gc, gc, acc[5 * H + 5]);
-      acc[5 * H + 6] += fabsf(gc);
+      if (own_new) {
+        acc[5 * H + 0] = fmaf(s, gc, acc[5 * H + 0]);
+        acc[5 * H + 1] = fmaf(y, gc, acc[5 * H + 1]);
+        acc[5 * H + 2] = fmaf(s, y, acc[5 * H + 2]);
+        acc[5 * H + 3] = fmaf(y, y, acc[5 * H + 3]);
+        acc[5 * H + 4] = fmaf(s, s, acc[5 * H + 4]);
+        acc[5 * H + 5] = fmaf(gc, gc, acc[5 * H + 5]);
+        acc[5 * H + 6] += fabsf(gc);
+      }
     }
   }
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -813,8 +848,11 @@ __global__ void __launch_bounds__(256, 4) lbfgs_dots1_kernel(SolverArgs a) {
 template <int MCAP>
 static cudaError_t launch_update(const SolverArgs& a, int grid, cudaStream_t s) {
   if constexpr (5 * (MCAP + 1) + 7 <= 64) {
-    // Two blocks per SM per row of blocks: both rows fit at once (four CTAs per SM).
-    lbfgs_dots1_kernel<MCAP><<<dim3(grid, Dots1Shape<MCAP + 1>::ROWS), 256, 0, s>>>(a);
+    // Three CTAs per SM: with two rows, 3/4 of the solver grid (two CTAs per SM) per row, so
+    // that both rows fit in one wave.
+    constexpr int rows = Dots1Shape<MCAP + 1>::ROWS;
+    const int gx = rows == 2 ? std::max(1, grid * 3 / 4) : grid;
+    lbfgs_dots1_kernel<MCAP><<<dim3(gx, rows), 256, 0, s>>>(a);
   } else {
     const int gx = std::max(1, grid / (MCAP + 2));
     lbfgs_dots_kernel<MCAP><<<dim3(gx, MCAP + 2), 256, 0, s>>>(a);
@@ -956,9 +994,13 @@ static rpca_status ensure_solver(rpca_ctx* c) {
   c->sol = b;
   b->mcap = mcap;
   b->plan = plan;
-  b->N = (int64_t)(c->m + c->n) * c->k;
+  // [U | V] is (m + n) k floats; the vectors are padded with zeros to a multiple of 4 so
+  // that the elementwise kernels load aligned vectors.  The padding stays zero: nothing but
+  // the elementwise kernels writes it, and they write combinations of zeros there.
+  b->N = ((int64_t)(c->m + c->n) * c->k + 3) & ~(int64_t)3;
   const int64_t N = b->N;
   SOL_CUDA(cudaMalloc(&b->x, sizeof(float) * 5 * N));
+  SOL_CUDA(cudaMemsetAsync(b->x, 0, sizeof(float) * 5 * N, c->stream));
   b->g = b->x + N;
   b->xt = b->g + N;
   b->gt = b->xt + N;
