@@ -715,7 +715,7 @@ rpca_status launch_fg(rpca_ctx* c, const FgPlan& P, const FgLaunch& L, cudaStrea
   if (timed) RPCA_CUDA(c, cudaEventRecord(ev[1], stream));
   const bool fuse_ls = L.ls_st != nullptr && L.fin_mode == FIN_FG;
   count_launches(c, fuse_ls ? 2 : (L.fin_mode != FIN_APPLY ? 3 : 2));
-  FinArgs f;
+  FinArgs f{};  // every field not set below is zero (vpart, vec4, ...)
   f.m = c->m;
   f.n = c->n;
   f.B = P.B;
@@ -748,6 +748,7 @@ rpca_status launch_fg(rpca_ctx* c, const FgPlan& P, const FgLaunch& L, cudaStrea
   f.counter = c->ws.counter;
   f.out = L.out ? L.out : c->ws.out;
   f.vpart = L.vpart;
+  f.vec4 = fin_vec4(f);
   if (timed) RPCA_CUDA(c, cudaEventRecord(ev[2], stream));
   if (fuse_ls) {
     RPCA_CUDA(c, launch_finalize_ls(f, P.fin_grid, L, stream));

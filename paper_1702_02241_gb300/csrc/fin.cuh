@@ -31,7 +31,55 @@ RPCA_DEV void finalize_body(const FinArgs& a) {
   const float lam = a.lam_f;
   const unsigned mB = (unsigned)a.m * (unsigned)a.B, nB = (unsigned)a.n * (unsigned)a.B;
   float nrm_f = 0.f, gd_f = 0.f, gg_f = 0.f;
-  if ((int)blockIdx.x < a.gu) {
+  if ((int)blockIdx.x < a.gu && a.vec4) {
+    // Four consecutive elements per thread (one row range of one column: m is a multiple of
+    // 4), every array read and written as float4; the column-split partials are added in the
+    // same order as below.
+    const unsigned e = (blockIdx.x * blockDim.x + threadIdx.x) * 4u;
+    if (a.side != 2 && e < mB) {
+      const int64_t cstride = (int64_t)a.B * a.mpad;
+      const unsigned l = e / (unsigned)a.m, i = e - l * (unsigned)a.m;
+      const float* pu = a.PU + (int64_t)l * a.mpad + i;
+      float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 4
+      for (int c = 0; c < a.ncs; ++c) {
+        const float4 t = *reinterpret_cast<const float4*>(pu + c * cstride);
+        s.x += t.x;
+        s.y += t.y;
+        s.z += t.z;
+        s.w += t.w;
+      }
+      const float su[4] = {s.x, s.y, s.z, s.w};
+      float uu[4] = {0.f, 0.f, 0.f, 0.f}, du[4] = {0.f, 0.f, 0.f, 0.f}, dir[4] = {0.f, 0.f, 0.f, 0.f};
+      if (a.mode != FIN_APPLY) {
+        const float4 u4 = *reinterpret_cast<const float4*>(a.U + e);
+        uu[0] = u4.x, uu[1] = u4.y, uu[2] = u4.z, uu[3] = u4.w;
+        if (a.dU) {
+          const float4 d4 = *reinterpret_cast<const float4*>(a.dU + e);
+          du[0] = d4.x, du[1] = d4.y, du[2] = d4.z, du[3] = d4.w;
+        }
+        if (a.DU) {
+          const float4 d4 = *reinterpret_cast<const float4*>(a.DU + e);
+          dir[0] = d4.x, dir[1] = d4.y, dir[2] = d4.z, dir[3] = d4.w;
+        }
+      }
+      float xt[4] = {0.f, 0.f, 0.f, 0.f}, g[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (a.mode != FIN_APPLY) {
+          xt[u] = a.dU ? fmaf(alpha, du[u], uu[u]) : uu[u];
+          g[u] = a.mode == FIN_FG ? fmaf(lam, xt[u], -su[u]) : -su[u];
+        } else {
+          g[u] = -su[u];
+        }
+        nrm_f = fmaf(xt[u], xt[u], nrm_f);
+        gd_f = fmaf(g[u], dir[u], gd_f);
+        gg_f = fmaf(g[u], g[u], gg_f);
+      }
+      if (a.mode != FIN_APPLY && a.Ut) *reinterpret_cast<float4*>(a.Ut + e) = make_float4(xt[0], xt[1], xt[2], xt[3]);
+      *reinterpret_cast<float4*>(a.GU + e) = make_float4(g[0], g[1], g[2], g[3]);
+    }
+  } else if ((int)blockIdx.x < a.gu) {
     // Loads of all FIN_EPT elements first, stores after: a store between them would order
     // the next element's loads after it (the compiler cannot rule out aliasing).
     float su[FIN_EPT], uu[FIN_EPT], du[FIN_EPT], dir[FIN_EPT];

@@ -40,7 +40,16 @@ struct FinArgs {
   // Row shard of a partitioned problem (rpca_fg_rows): the n x B side writes the raw partial
   // D^T U (no lam_L V) and adds nothing to the sums (V is shared by every shard).
   int vpart;
+  // The m x B side in float4 (four consecutive elements per thread): set by fin_vec4 when m
+  // and mpad are multiples of 4 and every m x B array the assembly touches is 16-byte aligned.
+  int vec4;
 };
+
+inline bool fin_aligned16(const void* p) { return p == nullptr || (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+inline int fin_vec4(const FinArgs& f) {
+  return f.m % 4 == 0 && f.mpad % 4 == 0 && fin_aligned16(f.PU) && fin_aligned16(f.U) && fin_aligned16(f.dU) &&
+         fin_aligned16(f.DU) && fin_aligned16(f.Ut) && fin_aligned16(f.GU);
+}
 
 // Finalize grid: FIN_EPT elements per thread of the m x B side (256 threads per block), 32
 // elements (eight groups of 32 threads splitting the row-block partials, FIN_VB loads in

@@ -219,6 +219,7 @@ rpca_status launch_fg_large(rpca_ctx* c, const FgPlan& P, const FgLaunch& L, cud
   f.blk = c->ws.blk;
   f.counter = c->ws.counter;
   f.out = L.out ? L.out : c->ws.out;
+  f.vec4 = fin_vec4(f);
   finalize_kernel<<<P.fin_grid, 256, 0, stream>>>(f);
   finalize_reduce_kernel<<<1, 256, 0, stream>>>(f, P.fin_grid);
   count_launches(c, 2);

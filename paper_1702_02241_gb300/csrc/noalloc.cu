@@ -177,6 +177,7 @@ extern "C" rpca_status rpca_fg_noalloc(int64_t m, int64_t n, const float* X, int
   fa.blk = reinterpret_cast<double*>(base + off_blk);
   fa.counter = reinterpret_cast<unsigned int*>(base + off_ctr);
   fa.out = reinterpret_cast<double*>(base + off_out);
+  fa.vec4 = fin_vec4(fa);
   finalize_kernel<<<fin_grid, 256, 0, stream>>>(fa);
   finalize_reduce_kernel<<<1, 256, 0, stream>>>(fa, fin_grid);
   if ((e = cudaGetLastError()) != cudaSuccess) return set_err_noctx(RPCA_ECUDA, cudaGetErrorString(e));

@@ -42,7 +42,7 @@ constexpr double LS_C1 = 1e-4, LS_C2 = 0.9, LS_AMAX = 1e10;
 constexpr int LS_MAX_TRIALS = 25;
 
 // Elements per thread and step of the inner-product pass, loaded as one vector.
-constexpr int DOTS_VEC = 2;
+constexpr int DOTS_VEC = 4;
 
 template <int NV>
 __device__ __forceinline__ void vec_store(float* p, const float (&v)[NV]) {
@@ -703,7 +703,7 @@ static int mem_cap(int mem) { return mem <= 4 ? 4 : (mem <= 10 ? 10 : (mem <= 16
 // in 64), in the layout of lbfgs_dots_kernel.  The history slots are split between the two
 // block rows (blockIdx.y; one row when there are few slots): row 0 takes the first half of
 // the slots and the seven sums of the new pair and the gradient, row 1 the rest, so that a
-// thread holds at most 5 ceil(NS / 2) + 7 sums and three CTAs fit on an SM.  Each element of
+// thread holds at most 5 ceil(NS / 2) + 7 sums beside its four elements' loads.  Each element of
 // x, g, x_t, g_t is read by both rows, every live history pair once, and nothing is written
 // (loads of successive elements can be in flight together); when the line search accepted,
 // s = x_t - x and y = g_t - g are formed on the fly (the direction kernel stores them and moves
@@ -718,7 +718,7 @@ struct Dots1Shape {
   static constexpr int C = ((5 * H + 7) + 7) & ~7;    // sums per thread, padded to a multiple of 8
 };
 template <int MCAP>
-__global__ void __launch_bounds__(256, 3) lbfgs_dots1_kernel(SolverArgs a) {
+__global__ void __launch_bounds__(256, 2) lbfgs_dots1_kernel(SolverArgs a) {
   constexpr int NS = MCAP + 1;
   constexpr int NV = 5 * NS + 7;
   static_assert(NV <= 64, "too many sums for the one-pass kernel");
@@ -848,10 +848,10 @@ __global__ void __launch_bounds__(256, 3) lbfgs_dots1_kernel(SolverArgs a) {
 template <int MCAP>
 static cudaError_t launch_update(const SolverArgs& a, int grid, cudaStream_t s) {
   if constexpr (5 * (MCAP + 1) + 7 <= 64) {
-    // Three CTAs per SM: with two rows, 3/4 of the solver grid (two CTAs per SM) per row, so
-    // that both rows fit in one wave.
+    // Two CTAs per SM (float4 loads: 126 registers): with two rows, half the solver grid per
+    // row, so that both rows fit in one wave.
     constexpr int rows = Dots1Shape<MCAP + 1>::ROWS;
-    const int gx = rows == 2 ? std::max(1, grid * 3 / 4) : grid;
+    const int gx = rows == 2 ? std::max(1, grid / 2) : grid;
     lbfgs_dots1_kernel<MCAP><<<dim3(gx, rows), 256, 0, s>>>(a);
   } else {
     const int gx = std::max(1, grid / (MCAP + 2));
