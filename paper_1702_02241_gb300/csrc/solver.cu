@@ -265,89 +265,112 @@ cudaError_t launch_finalize_ls(const FinArgs& f, int grid, const FgLaunch& L, cu
 }
 
 // ---------------------------------------------------------------------------------------------
-// The scalar part of an iteration before the two-loop coefficients (one thread): the new pair
-// enters the Gram table (or the memory is reset after a failed search), the history inner
-// products are refreshed, the log record is written, and the stopping tests run.  `v` holds
-// the reduced inner products in float64 and `vf` the same rounded to float32 (layout: see
-// lbfgs_dots_kernel).  Float64 is kept for f, ||g||^2 and the line search; the Gram table is
-// float32 (see SolverState), and no float64 square root or division is taken here.
+// The scalar part of an iteration, run by one warp on the solver state in shared memory.
+// `v` holds the reduced inner products in float64 and `vf` the same rounded to float32 (layout:
+// see lbfgs_dots_kernel).  Float64 is kept for f, ||g||^2 and the line search; the Gram table
+// and the two-loop scalars are float32 (see SolverState), and no float64 square root or
+// division is taken.  Lane q works on history position q (newest first), so the table update
+// and the two-loop recursion are a few dependent steps per position instead of loops.
+//
+// Part 1: the new pair enters the Gram table (or the memory is reset after a failed search),
+// the history inner products are refreshed, the log record is written, and the stopping
+// tests run.
 constexpr float CURV_EPS_F = 1e-10f;
+constexpr unsigned FULL_MASK = 0xffffffffu;
 template <int NS>
-__device__ void iteration_update(SolverState* st, SolverState* logst, const double* v, const float* vf) {
+__device__ void iteration_update_warp(SolverState* st, SolverState* logst, const double* v, const float* vf) {
+  const int lane = threadIdx.x & 31;
   const int state = st->ls.state;
-  int added = -1;  // slot of the pair added by this step, if any
-  const double step = st->ls.a, trials = st->ls.evals;
-  st->acc_flag = state == LS_ACCEPTED;
+  const int count0 = st->count, sp = st->spare;
+  const int myid = lane < count0 ? st->ids[lane] : -1;  // history position `lane`, before the update
+  int added = -1;                                        // slot of the pair added by this step, if any
+  __syncwarp();
   if (state == LS_ACCEPTED) {
-    st->f = st->ls.f_acc;
-    st->iter += 1;
-    st->fails = 0;
     const float sy = vf[5 * NS + 2], yy = vf[5 * NS + 3], ss = vf[5 * NS + 4];
-    const int sp = st->spare;
     if (sy > CURV_EPS_F * (sqrtf(ss) * sqrtf(yy)) && yy > 0.f) {  // curvature: s.y > eps |s| |y|
-      for (int q = 0; q < st->count; ++q) {
-        const int j = st->ids[q];
-        st->SY[sp][j] = vf[5 * j + 3];  // s_new . y_j
-        st->SY[j][sp] = vf[5 * j + 2];  // s_j . y_new
-        st->YY[sp][j] = vf[5 * j + 4];
-        st->YY[j][sp] = vf[5 * j + 4];
+      if (lane < count0) {
+        st->SY[sp][myid] = vf[5 * myid + 3];  // s_new . y_j
+        st->SY[myid][sp] = vf[5 * myid + 2];  // s_j . y_new
+        st->YY[sp][myid] = vf[5 * myid + 4];
+        st->YY[myid][sp] = vf[5 * myid + 4];
       }
-      st->SY[sp][sp] = sy;
-      st->YY[sp][sp] = yy;
-      const bool full = st->count == st->mem;
-      const int dropped = full ? st->ids[st->count - 1] : -1;
-      const int keep = full ? st->count - 1 : st->count;
-      for (int q = keep; q > 0; --q) st->ids[q] = st->ids[q - 1];
-      st->ids[0] = sp;
-      st->count = keep + 1;
-      added = sp;
-      if (dropped >= 0) {
-        st->spare = dropped;
+      if (lane == 0) {
+        st->SY[sp][sp] = sy;
+        st->YY[sp][sp] = yy;
+      }
+      const bool full = count0 == st->mem;
+      const int keep = full ? count0 - 1 : count0;
+      const int prev = __shfl_up_sync(FULL_MASK, myid, 1);
+      const int newid = lane == 0 ? sp : prev;  // the ring shifts by one, the new pair in front
+      const int count = keep + 1;
+      int spare;
+      if (full) {
+        spare = __shfl_sync(FULL_MASK, myid, count0 - 1);  // the dropped oldest pair's slot
       } else {  // the lowest slot not in the ring (count <= mem < NS leaves one free)
-        unsigned long long used = 0;
-        for (int q = 0; q < st->count; ++q) used |= 1ull << st->ids[q];
-        st->spare = __ffsll((long long)~used) - 1;
+        const unsigned lo = __reduce_or_sync(FULL_MASK, lane < count && newid < 32 ? 1u << newid : 0u);
+        const unsigned hi = __reduce_or_sync(FULL_MASK, lane < count && newid >= 32 ? 1u << (newid - 32) : 0u);
+        spare = lo != 0xffffffffu ? __ffs(~lo) - 1 : 32 + __ffs(~hi) - 1;
       }
-    }
-  } else if (state == LS_FAILED) {
-    st->count = 0;  // reset the memory; the next direction is steepest descent
-    st->fails += 1;
-    if (st->fails >= 2) {
-      st->stop = STOP_LSFAIL;
-      st->active = 0;
+      if (lane < count) st->ids[lane] = newid;
+      if (lane == 0) {
+        st->count = count;
+        st->spare = spare;
+      }
+      added = sp;
     }
   }
-  st->acc_slot = added;
-  for (int q = 0; q < st->count; ++q) {
-    const int j = st->ids[q];
+  __syncwarp();
+  if (lane == 0) {
+    if (state == LS_ACCEPTED) {
+      st->f = st->ls.f_acc;
+      st->iter += 1;
+      st->fails = 0;
+    } else if (state == LS_FAILED) {
+      st->count = 0;  // reset the memory; the next direction is steepest descent
+      st->fails += 1;
+      if (st->fails >= 2) {
+        st->stop = STOP_LSFAIL;
+        st->active = 0;
+      }
+    }
+    st->acc_flag = state == LS_ACCEPTED;
+    st->acc_slot = added;
+  }
+  __syncwarp();
+  const int count = st->count;
+  if (lane < count) {
+    const int j = st->ids[lane];
     st->sg[j] = j == added ? vf[5 * NS + 0] : vf[5 * j + 0];
     st->yg[j] = j == added ? vf[5 * NS + 1] : vf[5 * j + 1];
   }
-  st->gg = v[5 * NS + 5];
-  st->g1 = v[5 * NS + 6];
-  if (state != LS_NONE) {
-    double* rec = logst->log[logst->log_n % SOLVER_LOG];
-    rec[0] = st->iter;
-    rec[1] = st->f;
-    rec[2] = sqrtf(vf[5 * NS + 5]);
-    rec[3] = step;
-    rec[4] = trials;
-    rec[5] = state;
-    rec[6] = st->count;
-    logst->log_n += 1;
+  if (lane == 0) {
+    st->gg = v[5 * NS + 5];
+    st->g1 = v[5 * NS + 6];
+    if (state != LS_NONE) {
+      double* rec = logst->log[logst->log_n % SOLVER_LOG];
+      rec[0] = st->iter;
+      rec[1] = st->f;
+      rec[2] = sqrtf(vf[5 * NS + 5]);
+      rec[3] = st->ls.a;
+      rec[4] = st->ls.evals;
+      rec[5] = state;
+      rec[6] = count;
+      logst->log_n += 1;
+    }
+    const double glim = st->gtol * fmax(1.0, fabs(st->f));
+    if (!isfinite(st->f) || !isfinite(st->gg)) {
+      st->stop = STOP_NONFINITE;
+      st->active = 0;
+    } else if (st->gtol > 0.0 && st->gg <= glim * glim) {  // ||g|| <= gtol max(1, |f|)
+      st->stop = STOP_GTOL;
+      st->active = 0;
+    } else if (st->iter >= st->max_iter) {
+      st->stop = STOP_MAXITER;
+      st->active = 0;
+    }
+    if (st->f < st->best_f) st->best_f = st->f;
   }
-  const double glim = st->gtol * fmax(1.0, fabs(st->f));
-  if (!isfinite(st->f) || !isfinite(st->gg)) {
-    st->stop = STOP_NONFINITE;
-    st->active = 0;
-  } else if (st->gtol > 0.0 && st->gg <= glim * glim) {  // ||g|| <= gtol max(1, |f|)
-    st->stop = STOP_GTOL;
-    st->active = 0;
-  } else if (st->iter >= st->max_iter) {
-    st->stop = STOP_MAXITER;
-    st->active = 0;
-  }
-  if (st->f < st->best_f) st->best_f = st->f;
+  __syncwarp();
 }
 
 // The rest of the scalar part after the two-loop coefficients, run by one warp: the descent
@@ -399,12 +422,14 @@ __device__ void iteration_finish_warp(SolverState* st, float gg) {
   st->gate = (st->active && L.state == LS_RUNNING) ? 1 : 0;
 }
 
-// The two-loop recursion (Nocedal & Wright Alg. 7.4) on the Gram table, run by one warp
-// (count <= 32): lane i holds history pair i (newest first).  Both loops are triangular
-// solves; at step j the lane that owns pair j finishes its coefficient, broadcasts it, and
-// every lane that still needs it adds its product -- one broadcast and one FMA per step
-// instead of a dependent dot product.  float32 throughout (see SolverState).
+// Part 2: the two-loop recursion (Nocedal & Wright Alg. 7.4) on the Gram table.  Both loops
+// are triangular solves: at step j the lane that owns pair j finishes its coefficient and
+// broadcasts it, and every lane that still needs it adds its product.  Each lane first loads
+// its row and column of the table (the entries it will use, in registers), so that a step is
+// one broadcast and one FMA.
+template <int NS>
 __device__ void two_loop_coefs_warp(SolverState* st) {
+  constexpr int MAXJ = NS - 1;  // history positions (count <= mem <= NS - 1)
   const int lane = threadIdx.x & 31;
   const int n = st->count;
   for (int j = lane; j < SOLVER_MAX_SLOTS; j += 32) {
@@ -419,31 +444,46 @@ __device__ void two_loop_coefs_warp(SolverState* st) {
   }
   const bool mine = lane < n;
   const int id = mine ? st->ids[lane] : 0;
+  float sy_row[MAXJ], sy_col[MAXJ], yy_row[MAXJ];
+#pragma unroll
+  for (int j = 0; j < MAXJ; ++j) {
+    const int idj = j < n ? st->ids[j] : 0;
+    sy_row[j] = mine && j < n ? st->SY[id][idj] : 0.f;  // s_id . y_j
+    sy_col[j] = mine && j < n ? st->SY[idj][id] : 0.f;  // s_j . y_id
+    yy_row[j] = mine && j < n ? st->YY[id][idj] : 0.f;
+  }
   const float rho = mine ? 1.f / st->SY[id][id] : 0.f;
   const float sg = mine ? st->sg[id] : 0.f, yg = mine ? st->yg[id] : 0.f;
-  // Loop 1 (newest -> oldest): a_i = rho_i (sg_i - sum_{j < i} a_j s_i . y_j).
-  float acc = 0.f, a_mine = 0.f;
-  for (int j = 0; j < n; ++j) {
-    if (lane == j) a_mine = (sg - acc) * rho;
-    const float aj = __shfl_sync(0xffffffffu, a_mine, j);
-    const int idj = st->ids[j];
-    if (mine && lane > j) acc = fmaf(aj, st->SY[id][idj], acc);
-  }
   const int i0 = st->ids[0];
   const float gamma = st->SY[i0][i0] / st->YY[i0][i0];
+  // Loop 1 (newest -> oldest): a_i = rho_i (sg_i - sum_{j < i} a_j s_i . y_j).
+  float acc = 0.f, a_mine = 0.f;
+#pragma unroll
+  for (int j = 0; j < MAXJ; ++j) {
+    if (j < n) {
+      if (lane == j) a_mine = (sg - acc) * rho;
+      const float aj = __shfl_sync(FULL_MASK, a_mine, j);
+      if (mine && lane > j) acc = fmaf(aj, sy_row[j], acc);
+    }
+  }
   // y_i . (sum_j a_j y_j), independent per lane.
   float ay = 0.f;
-  for (int j = 0; j < n; ++j) {
-    const float aj = __shfl_sync(0xffffffffu, a_mine, j);
-    if (mine) ay = fmaf(aj, st->YY[id][st->ids[j]], ay);
+#pragma unroll
+  for (int j = 0; j < MAXJ; ++j) {
+    if (j < n) {
+      const float aj = __shfl_sync(FULL_MASK, a_mine, j);
+      if (mine) ay = fmaf(aj, yy_row[j], ay);
+    }
   }
   // Loop 2 (oldest -> newest): c_i = a_i - rho_i (gamma (yg_i - ay_i) + sum_{j > i} c_j s_j . y_i).
   float acc2 = 0.f, c_mine = 0.f;
-  for (int j = n - 1; j >= 0; --j) {
-    if (lane == j) c_mine = a_mine - fmaf(yg - ay, gamma, acc2) * rho;
-    const float cj = __shfl_sync(0xffffffffu, c_mine, j);
-    const int idj = st->ids[j];
-    if (mine && lane < j) acc2 = fmaf(cj, st->SY[idj][id], acc2);
+#pragma unroll
+  for (int j = MAXJ - 1; j >= 0; --j) {
+    if (j < n) {
+      if (lane == j) c_mine = a_mine - fmaf(yg - ay, gamma, acc2) * rho;
+      const float cj = __shfl_sync(FULL_MASK, c_mine, j);
+      if (mine && lane < j) acc2 = fmaf(cj, sy_col[j], acc2);
+    }
   }
   __syncwarp();
   if (mine) {
@@ -455,9 +495,9 @@ __device__ void two_loop_coefs_warp(SolverState* st) {
 }
 
 // The scalar part of an iteration, run by the last block of the dots reduction: the solver
-// state up to the log rings is copied to shared memory by the whole block, updated there
-// (one thread, then one warp: chains of dependent operations, which must not wait on global
-// memory), and copied back.
+// state up to the log rings is copied to shared memory by the whole block, updated there by
+// one warp (chains of dependent operations, which must not wait on global memory), and
+// copied back.
 constexpr int SOLVER_CORE_WORDS = (int)(offsetof(SolverState, log_n) / sizeof(double));
 static_assert(offsetof(SolverState, log_n) % sizeof(double) == 0, "solver core must be whole words");
 // fin: the reduced inner products in float64, finf: the same in float32 (shared memory).
@@ -468,10 +508,9 @@ __device__ void scalar_tail(SolverState* gst, const double* fin, const float* fi
   for (int i = threadIdx.x; i < SOLVER_CORE_WORDS; i += blockDim.x) core[i] = __ldcg(src + i);
   __syncthreads();
   SolverState* s = reinterpret_cast<SolverState*>(core);
-  if (threadIdx.x == 0) iteration_update<NS>(s, gst, fin, finf);
-  __syncthreads();
   if (threadIdx.x < 32) {
-    two_loop_coefs_warp(s);
+    iteration_update_warp<NS>(s, gst, fin, finf);
+    two_loop_coefs_warp<NS>(s);
     iteration_finish_warp(s, finf[5 * NS + 5]);
   }
   __syncthreads();
