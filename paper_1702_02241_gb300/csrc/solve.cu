@@ -356,10 +356,11 @@ static rpca_status job_finish(SolveJob& j, rpca_result* res) {
     ++j.cert_evals;
   }
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_err(c, cudaGetLastError(), "rpca_solve");
-  // Fused kernel + finalize-and-line-search-step per while-body pass: one per trial, and one
-  // (early-exit) pass in every graph launch that ran no trial.
+  // Four kernels (fused pass, finalize and line-search step, inner products, direction) per
+  // pass of the iteration graph's while body: one pass per trial, and one (early-exit) pass in
+  // every graph launch that ran no trial.
   const int64_t gl = c->graph_launches - j.graph_launches0;
-  count_launches(c, 2LL * std::max<int64_t>(gl, (int64_t)(j.evals_base + j.st.evals) - 1));
+  if (gl > 0) count_launches(c, 4LL * std::max<int64_t>(gl, (int64_t)(j.evals_base + j.st.evals) - 1));
   rpca_result r;
   memset(&r, 0, sizeof r);
   j.timer->collect(&r.ms_init, &r.ms_iter, &r.ms_cert);

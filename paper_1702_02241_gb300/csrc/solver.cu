@@ -88,6 +88,8 @@ struct SolverArgs {
   float* Y;
   double* blk;
   unsigned int* counter;
+  cudaGraphConditionalHandle loop_h;  // the iteration graph's while node (in_graph)
+  int in_graph;
 };
 
 // ---------------------------------------------------------------------------------------------
@@ -512,6 +514,7 @@ __device__ void scalar_tail(SolverState* gst, const double* fin, const float* fi
     iteration_update_warp<NS>(s, gst, fin, finf);
     two_loop_coefs_warp<NS>(s);
     iteration_finish_warp(s, finf[5 * NS + 5]);
+    if (threadIdx.x == 0) s->dir_pending = 1;
   }
   __syncthreads();
   double* dst = reinterpret_cast<double*>(gst);
@@ -533,7 +536,7 @@ __global__ void __launch_bounds__(256) lbfgs_dots_kernel(SolverArgs a) {
   __shared__ float finf[NV];
   __shared__ bool is_last;
   SolverState* st = a.st;
-  if (!st->active) return;
+  if (!st->active || st->ls.state == LS_RUNNING) return;  // nothing to do while a search runs
   const int j = blockIdx.y;
   const bool accepted = st->ls.state == LS_ACCEPTED;
   bool live = false;
@@ -620,8 +623,15 @@ __global__ void __launch_bounds__(256, MCAP <= 10 ? 2 : 1) lbfgs_direction_kerne
   __shared__ float cs[NS], cy[NS];
   __shared__ float cg;
   SolverState* st = a.st;
-  const int acc = st->acc_flag, active = st->active;
-  if (!acc && !active) return;
+  const int acc = st->acc_flag, active = st->active, pending = st->dir_pending;
+  // In the iteration graph this is the last kernel of a trial: its first thread sets the
+  // loop condition from the state the scalar part left (final by now).
+  if (a.in_graph && blockIdx.x == 0 && threadIdx.x == 0) {
+    const int budget = st->loop_budget - 1;
+    st->loop_budget = budget;
+    cudaGraphSetConditional(a.loop_h, (active && st->iter < st->target && budget > 0) ? 1u : 0u);
+  }
+  if (!acc && !(active && pending)) return;
   const int slot = acc ? st->acc_slot : -1;
   uint64_t live = 0;
   if (active)
@@ -664,7 +674,7 @@ __global__ void __launch_bounds__(256, MCAP <= 10 ? 2 : 1) lbfgs_direction_kerne
       vec_store<EPT>(a.x + e, xn);
       vec_store<EPT>(a.g + e, gn);
     }
-    if (active) {
+    if (active && pending) {
       float dv[EPT];
 #pragma unroll
       for (int u = 0; u < EPT; ++u) {
@@ -680,12 +690,22 @@ __global__ void __launch_bounds__(256, MCAP <= 10 ? 2 : 1) lbfgs_direction_kerne
       vec_store<EPT>(a.d + e, dv);
     }
   }
-  if (acc) {  // every block has read acc_flag by the time the last one arrives
-    __syncthreads();
-    if (threadIdx.x == 0 && atomicAdd(a.counter + 2 + DOTS_MAX_GRP, 1u) == gridDim.x - 1) {
-      a.counter[2 + DOTS_MAX_GRP] = 0u;
-      st->acc_flag = 0;
-    }
+  // Every block has read the flags by the time the last one arrives.
+  __syncthreads();
+  if (threadIdx.x == 0 && atomicAdd(a.counter + 2 + DOTS_MAX_GRP, 1u) == gridDim.x - 1) {
+    a.counter[2 + DOTS_MAX_GRP] = 0u;
+    st->acc_flag = 0;
+    st->dir_pending = 0;
+  }
+}
+
+// The iteration target of the next graph launch: `count` iterations from the current one, in
+// at most as many passes as count searches of LS_MAX_TRIALS trials (plus the restart after a
+// failed search) can take.
+__global__ void set_chunk_kernel(SolverState* st, int count) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    st->target = st->iter + count;
+    st->loop_budget = (count + 2) * (LS_MAX_TRIALS + 2);
   }
 }
 
@@ -708,6 +728,9 @@ __global__ void solver_init_kernel(SolverState* st, int mem, int max_iter, doubl
   st->ls.state = LS_NONE;
   st->acc_flag = 0;
   st->acc_slot = -1;
+  st->dir_pending = 0;
+  st->target = 0;
+  st->loop_budget = 0;
   st->log_n = 0;
   st->tlog_n = 0;
 }
@@ -769,7 +792,7 @@ __global__ void __launch_bounds__(256, 2) lbfgs_dots1_kernel(SolverArgs a) {
   __shared__ float finf[64];
   __shared__ bool is_last;
   SolverState* st = a.st;
-  if (!st->active) return;
+  if (!st->active || st->ls.state == LS_RUNNING) return;  // nothing to do while a search runs
   const int row = blockIdx.y;
   const int j0 = row * H, nj = min(H, NS - j0);  // this row's slots [j0, j0 + nj)
   const bool own_new = row == 0;                 // row 0 also sums the new pair and g
@@ -957,6 +980,8 @@ static SolverArgs solver_args(rpca_ctx* c) {
   a.Y = b->Y;
   a.blk = b->blk;
   a.counter = b->counter;
+  a.loop_h = 0;
+  a.in_graph = 0;
   return a;
 }
 
@@ -989,9 +1014,12 @@ static FgLaunch trial_launch(rpca_ctx* c, cudaGraphConditionalHandle h = 0, int 
   return L;
 }
 
-// Records one iteration on `cap`, which must be capturing: a WHILE node over the line-search
-// trials (fused pass and finalize-with-step, captured into the node's body on the context's
-// second capture stream), then accept + inner products and the next direction.
+// Records the iteration loop on `cap`, which must be capturing: a WHILE node over line-search
+// trials, each trial the fused pass at x + a d, the assembly with the line-search step, the
+// inner products with the scalar part (which return at once while the search runs) and the
+// accepted step with the next direction (likewise); the direction kernel sets the loop
+// condition: active and iter < target.  One launch runs the iterations up to the target that
+// set_chunk_kernel recorded, with no return to the host and no graph launch per iteration.
 static cudaError_t capture_iteration(rpca_ctx* c, cudaStream_t cap) {
   SolverBuffers* b = c->sol;
   SolverArgs a = solver_args(c);
@@ -1013,14 +1041,16 @@ static cudaError_t capture_iteration(rpca_ctx* c, cudaStream_t cap) {
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     e = cudaStreamBeginCaptureToGraph(b->cap2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-      rpca_status s = launch_fg(c, *b->plan, trial_launch(c, h, 1), b->cap2);
+      rpca_status s = launch_fg(c, *b->plan, trial_launch(c), b->cap2);
       e = s == RPCA_OK ? cudaGetLastError() : cudaErrorUnknown;
+      a.loop_h = h;
+      a.in_graph = 1;
+      if (e == cudaSuccess) e = update_and_direction(b->mcap, a, b->grid, b->cap2);
       cudaGraph_t body_out = nullptr;
       cudaError_t e2 = cudaStreamEndCapture(b->cap2, &body_out);
       if (e == cudaSuccess) e = e2;
     }
   }
-  if (e == cudaSuccess) e = update_and_direction(b->mcap, a, b->grid, cap);
   return e;
 }
 
@@ -1069,7 +1099,7 @@ static rpca_status ensure_solver(rpca_ctx* c) {
   // Ranks above the fused kernel's call cuBLAS in their objective pass: host loop as well.
   if (c->lk) return RPCA_OK;
 
-  // Capture one iteration: WHILE(line search) { fg, finalize, ls_step }, update, direction.
+  // Capture the iteration loop: WHILE(active, iter < target) { fg, finalize + step, dots, direction }.
   SOL_CUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
   cudaError_t e = capture_iteration(c, b->cap);
   cudaGraph_t graph = nullptr;
@@ -1089,10 +1119,10 @@ static rpca_status ensure_solver(rpca_ctx* c) {
 // iterations of every instance, each instance's on a branch of its own.
 rpca_status solver_capture_rounds(rpca_ctx* c, cudaStream_t s, int rounds) {
   if (!c->sol || c->lk) return set_err(c, RPCA_EUNSUPPORTED, "no device iteration to capture");
-  for (int r = 0; r < rounds; ++r) {
-    const cudaError_t e = capture_iteration(c, s);
-    if (e != cudaSuccess) return cuda_err(c, e, "capturing the batched iteration graph");
-  }
+  set_chunk_kernel<<<1, 1, 0, s>>>(c->sol->st, rounds);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = capture_iteration(c, s);
+  if (e != cudaSuccess) return cuda_err(c, e, "capturing the batched iteration graph");
   return RPCA_OK;
 }
 
@@ -1187,14 +1217,16 @@ rpca_status solver_iterations(rpca_ctx* c, int count) {
       rpca_status s = host_iteration(c);
       if (s != RPCA_OK) return s;
     }
+    count_launches(c, (int64_t)update_launches(c->sol->mcap) * count);
   } else {
-    for (int i = 0; i < count; ++i) SOL_CUDA(cudaGraphLaunch(c->sol->exec, c->stream));
+    set_chunk_kernel<<<1, 1, 0, c->stream>>>(c->sol->st, count);
+    SOL_CUDA(cudaGetLastError());
+    SOL_CUDA(cudaGraphLaunch(c->sol->exec, c->stream));
+    c->graph_launches += 1;
+    // The while body's four kernels per pass are added from the trial count when the solve
+    // finishes.
+    count_launches(c, 1);
   }
-  c->graph_launches += count;
-  // Kernels inside: accept + dots (one kernel for small memory caps) + direction per launch;
-  // the while body (fused kernel, finalize, line-search step) is added from the trial count
-  // when the solve finishes.
-  count_launches(c, (int64_t)update_launches(c->sol->mcap) * count);
   return RPCA_OK;
 }
 

@@ -37,6 +37,13 @@ struct SolverState {
   // then moves x, g to the trial point and stores the new pair in slot acc_slot (-1: the
   // pair failed the curvature test and is not kept), and its last block clears acc_flag.
   int acc_flag, acc_slot;
+  // Set by the scalar part when it has formed new two-loop coefficients; the direction kernel
+  // then forms d and its last block clears it.
+  int dir_pending;
+  // The iteration graph loops over line-search trials while active and iter < target (set
+  // from the host's iteration count before each launch), and at most loop_budget passes: a
+  // bound that holds whatever the state, so that a launch always ends.
+  int target, loop_budget;
   int ids[SOLVER_MAX_SLOTS];  // history slots in the ring, newest first
   // The Gram table, the two-loop coefficients and the inner products they come from are
   // float32: their inputs are float32 vectors, the direction is formed with float32
