@@ -243,8 +243,20 @@ RPCA_API rpca_status rpca_x_storage(rpca_ctx *c, int *dtype, void *host_out, int
  */
 RPCA_API rpca_status rpca_certificate(rpca_ctx *c, const float *U, const float *V, rpca_cert *out);
 
-/* Releases the context and every buffer it owns (not X or the mask). NULL is allowed. */
+/*
+ * Releases the context and every buffer it owns (not X or the mask). NULL is allowed.  It
+ * waits for the device first; the context's device and pinned host blocks are then kept by
+ * the library (up to 4 GiB each) and handed to the next contexts, whose set-up then takes
+ * no cudaMalloc / cudaMallocHost.
+ */
 RPCA_API void rpca_destroy(rpca_ctx *c);
+
+/*
+ * Returns the device and pinned host memory the library keeps from destroyed contexts to the
+ * CUDA runtime, after waiting for the device.  Returns the bytes released.  Live contexts
+ * keep their own buffers.
+ */
+RPCA_API size_t rpca_release_memory(void);
 
 /* Message of the last failure on c (or of the last failed rpca_create when c is NULL). */
 RPCA_API const char *rpca_last_error(const rpca_ctx *c);

@@ -9,6 +9,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <unordered_map>
 #include <mutex>
 #include <tuple>
 #include <utility>
@@ -609,6 +610,72 @@ static rpca_status make_plan(rpca_ctx* c, FgPlan* P, int K, int B, bool same, in
 // Device allocations of the context's set-up go through here so that a test can make the
 // next ones fail (rpca_inject_fault, RPCA_FAULT_ALLOC) without exhausting the GPU.
 static std::atomic<int> g_fault_alloc{0};
+
+// Blocks of destroyed contexts are kept for the next ones: a context's set-up allocates some
+// twenty device buffers and two pinned host words, and each cudaMalloc / cudaFree costs tens of
+// microseconds (cudaFree also waits for the device), cudaMallocHost / cudaFreeHost more.
+// Freed blocks go to a free list keyed by their size class (powers of two up to 1 MiB, then
+// multiples of 1 MiB) and serve the next request of that class; at most kCacheMax bytes are
+// kept (beyond that a freed block is returned at once), and rpca_release_memory returns them
+// all.  A block is freed only after the work that used it has completed (callers synchronise
+// the context's stream, rpca_destroy the device).
+namespace {
+constexpr size_t kCacheMax = (size_t)4 << 30;
+size_t size_class(size_t bytes) {
+  if (bytes <= ((size_t)1 << 20)) {
+    size_t c = 256;
+    while (c < bytes) c <<= 1;
+    return c;
+  }
+  return (bytes + ((size_t)1 << 20) - 1) & ~(((size_t)1 << 20) - 1);
+}
+struct BlockCache {
+  std::mutex mu;
+  std::unordered_map<void*, size_t> live;              // block -> size class
+  std::unordered_map<size_t, std::vector<void*>> free;  // size class -> cached blocks
+  size_t cached = 0;
+};
+BlockCache& dev_cache() {
+  static BlockCache c;
+  return c;
+}
+BlockCache& host_cache() {
+  static BlockCache c;
+  return c;
+}
+void* cache_take(BlockCache& bc, size_t cls) {
+  std::lock_guard<std::mutex> lock(bc.mu);
+  auto it = bc.free.find(cls);
+  if (it == bc.free.end() || it->second.empty()) return nullptr;
+  void* p = it->second.back();
+  it->second.pop_back();
+  bc.cached -= cls;
+  bc.live[p] = cls;
+  return p;
+}
+// Keeps p for reuse (or releases it when the cache is full or p is not one of its blocks).
+template <typename Release>
+void cache_give(BlockCache& bc, void* p, Release release) {
+  if (!p) return;
+  std::unique_lock<std::mutex> lock(bc.mu);
+  auto it = bc.live.find(p);
+  if (it == bc.live.end()) {  // not ours (should not happen): release it directly
+    lock.unlock();
+    release(p);
+    return;
+  }
+  const size_t cls = it->second;
+  bc.live.erase(it);
+  if (bc.cached + cls <= kCacheMax) {
+    bc.free[cls].push_back(p);
+    bc.cached += cls;
+    return;
+  }
+  lock.unlock();
+  release(p);
+}
+}  // namespace
+
 cudaError_t dev_malloc(void** p, size_t bytes) {
   int left = g_fault_alloc.load();
   while (left > 0) {
@@ -617,7 +684,56 @@ cudaError_t dev_malloc(void** p, size_t bytes) {
       return cudaErrorMemoryAllocation;
     }
   }
-  return cudaMalloc(p, bytes);
+  const size_t cls = size_class(std::max<size_t>(bytes, 1));
+  if ((*p = cache_take(dev_cache(), cls)) != nullptr) return cudaSuccess;
+  const cudaError_t e = cudaMalloc(p, cls);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return e;
+  }
+  std::lock_guard<std::mutex> lock(dev_cache().mu);
+  dev_cache().live[*p] = cls;
+  return cudaSuccess;
+}
+
+void dev_free(void* p) {
+  cache_give(dev_cache(), p, [](void* q) { cudaFree(q); });
+}
+
+cudaError_t host_pinned_malloc(void** p, size_t bytes) {
+  const size_t cls = size_class(std::max<size_t>(bytes, 1));
+  if ((*p = cache_take(host_cache(), cls)) != nullptr) return cudaSuccess;
+  const cudaError_t e = cudaMallocHost(p, cls);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return e;
+  }
+  std::lock_guard<std::mutex> lock(host_cache().mu);
+  host_cache().live[*p] = cls;
+  return cudaSuccess;
+}
+
+void host_pinned_free(void* p) {
+  cache_give(host_cache(), p, [](void* q) { cudaFreeHost(q); });
+}
+
+// Releases every cached block; returns the bytes released.
+static size_t release_cached() {
+  size_t total = 0;
+  for (int h = 0; h < 2; ++h) {
+    BlockCache& bc = h ? host_cache() : dev_cache();
+    std::lock_guard<std::mutex> lock(bc.mu);
+    for (auto& kv : bc.free) {
+      for (void* q : kv.second) {
+        if (h) cudaFreeHost(q);
+        else cudaFree(q);
+        total += kv.first;
+      }
+    }
+    bc.free.clear();
+    bc.cached = 0;
+  }
+  return total;
 }
 
 template <typename T>
@@ -625,7 +741,7 @@ static rpca_status ensure(rpca_ctx* c, T** p, size_t* have, size_t need) {
   if (*have >= need) return RPCA_OK;
   if (*p) {
     RPCA_CUDA(c, cudaStreamSynchronize(c->stream));
-    cudaFree(*p);
+    dev_free(*p);
   }
   *p = nullptr;
   *have = 0;
@@ -962,7 +1078,7 @@ rpca_status create_ctx(rpca_ctx** out, int64_t m, int64_t n, const float* X, int
   unsigned long long hc[2] = {0, 0};
   cudaMemcpyAsync(hc, cnt, sizeof hc, cudaMemcpyDeviceToHost, c->stream);
   e = cudaStreamSynchronize(c->stream);
-  cudaFree(cnt);
+  dev_free(cnt);
   if (e != cudaSuccess) return fail(cuda_err(c, e, "validating X"));
   if (hc[0] != 0) return fail(set_err(c, RPCA_EINVAL, "X has non-finite observed entries"));
   c->p_hat = (double)hc[1] / ((double)m * (double)n);
@@ -1079,33 +1195,40 @@ rpca_status rpca_apply(rpca_ctx* c, const float* U, const float* V, int b, const
   return s;
 }
 
+size_t rpca_release_memory(void) {
+  cudaDeviceSynchronize();
+  return release_cached();
+}
+
 void rpca_destroy(rpca_ctx* c) {
   if (!c) return;
   for (rpca_ctx* g : c->grown)
     if (g) rpca_destroy(g);
   c->grown.clear();
   lk_free(c);
+  // Nothing of this context may still run when its blocks go back to the cache.
   cudaStreamSynchronize(c->stream);
+  cudaDeviceSynchronize();
   cvx_free(c);
   free_solver(c);
   free_cert(c);
   sk_free(c);
-  cudaFree(c->bits);
-  cudaFree(c->Xq);
-  cudaFree(c->xscale);
-  cudaFree(c->sk_sigma);
-  cudaFree(c->ws_buf);
-  cudaFree(c->ws.PU);
-  cudaFree(c->ws.PV);
-  cudaFree(c->ws.Ppsi);
-  cudaFree(c->ws.blk);
-  cudaFree(c->ws_ap.PU);
-  cudaFree(c->ws_ap.PV);
-  cudaFree(c->ws_ap.Ppsi);
-  cudaFree(c->ws_ap.blk);
-  cudaFree(c->ws.counter);
-  cudaFree(c->ws.out);
-  cudaFree(c->ws.err);
+  dev_free(c->bits);
+  dev_free(c->Xq);
+  dev_free(c->xscale);
+  dev_free(c->sk_sigma);
+  dev_free(c->ws_buf);
+  dev_free(c->ws.PU);
+  dev_free(c->ws.PV);
+  dev_free(c->ws.Ppsi);
+  dev_free(c->ws.blk);
+  dev_free(c->ws_ap.PU);
+  dev_free(c->ws_ap.PV);
+  dev_free(c->ws_ap.Ppsi);
+  dev_free(c->ws_ap.blk);
+  dev_free(c->ws.counter);
+  dev_free(c->ws.out);
+  dev_free(c->ws.err);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   delete c;
 }

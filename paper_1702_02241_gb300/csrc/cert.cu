@@ -455,14 +455,14 @@ void fill_normal(float* out, int64_t count, uint64_t seed, float scale, cudaStre
 void free_cert(rpca_ctx* c) {
   CertBuffers* b = c->cert;
   if (!b) return;
-  cudaFree(b->DV);
-  cudaFree(b->T);
-  cudaFree(b->ritz);
-  cudaFree(b->st);
-  cudaFree(b->blk);
-  cudaFree(b->counter);
-  cudaFree(b->ts.part);
-  cudaFreeHost(b->host);
+  dev_free(b->DV);
+  dev_free(b->T);
+  dev_free(b->ritz);
+  dev_free(b->st);
+  dev_free(b->blk);
+  dev_free(b->counter);
+  dev_free(b->ts.part);
+  host_pinned_free(b->host);
   delete b;
   c->cert = nullptr;
 }
@@ -482,7 +482,7 @@ static rpca_status ensure_cert(rpca_ctx* c) {
   const int zc = std::max<int>(LZ_B, (int)k);
   const int64_t nf = m * k + n * k + m * (CERT_KMAX + LZ_TMAX) + n * (CERT_KMAX + LZ_TMAX + LZ_B) + m * LZ_B +
                      n * LZ_B + m * b->Kp + n * b->Kp + m * zc + n * zc + m * LZ_B + 2 * LZ_TMAX * LZ_TMAX;
-  CERT_CUDA(cudaMalloc(&b->DV, sizeof(float) * nf));
+  CERT_CUDA(dev_alloc(&b->DV, sizeof(float) * nf));
   float* p = b->DV;
   p += m * k;
   b->DtU = p;
@@ -511,17 +511,17 @@ static rpca_status ensure_cert(rpca_ctx* c) {
   p += LZ_TMAX * LZ_TMAX;
   b->Tv = p;
   CERT_CUDA(cudaMemsetAsync(b->zm, 0, sizeof(float) * (m + n) * zc, c->stream));
-  CERT_CUDA(cudaMalloc(&b->T, sizeof(double) * LZ_TMAX * LZ_TMAX));
-  CERT_CUDA(cudaMalloc(&b->ritz, sizeof(double) * 2 * RITZ_TOPQ * LZ_TMAX));
-  CERT_CUDA(cudaMalloc(&b->st, sizeof(CertState)));
+  CERT_CUDA(dev_alloc(&b->T, sizeof(double) * LZ_TMAX * LZ_TMAX));
+  CERT_CUDA(dev_alloc(&b->ritz, sizeof(double) * 2 * RITZ_TOPQ * LZ_TMAX));
+  CERT_CUDA(dev_alloc(&b->st, sizeof(CertState)));
   CERT_CUDA(cudaMemsetAsync(b->st, 0, sizeof(CertState), c->stream));
-  CERT_CUDA(cudaMallocHost(&b->host, sizeof(CertState)));
-  CERT_CUDA(cudaMalloc(&b->blk, sizeof(double) * 4 * c->nsm));
-  CERT_CUDA(cudaMalloc(&b->counter, 64));
+  CERT_CUDA(host_pinned_alloc(&b->host, sizeof(CertState)));
+  CERT_CUDA(dev_alloc(&b->blk, sizeof(double) * 4 * c->nsm));
+  CERT_CUDA(dev_alloc(&b->counter, 64));
   CERT_CUDA(cudaMemsetAsync(b->counter, 0, 64, c->stream));
   b->ts.grid = 2 * c->nsm;
   b->ts.part_n = (size_t)b->ts.grid * 2304;
-  CERT_CUDA(cudaMalloc(&b->ts.part, sizeof(double) * b->ts.part_n));
+  CERT_CUDA(dev_alloc(&b->ts.part, sizeof(double) * b->ts.part_n));
   return RPCA_OK;
 }
 

@@ -125,7 +125,18 @@ rpca_status make_tmap(rpca_ctx* c, CUtensorMap* map, CUtensorMapDataType dt, con
                       int64_t d1, int64_t stride_bytes, int b0, int b1);
 rpca_status cuda_err(rpca_ctx* c, cudaError_t e, const char* what);
 rpca_status check_dev_err(rpca_ctx* c);
-cudaError_t dev_malloc(void** p, size_t bytes);  // cudaMalloc, or an injected failure
+cudaError_t dev_malloc(void** p, size_t bytes);  // cudaMalloc through the block cache, or an injected failure
+void dev_free(void* p);                          // back to the block cache (after the work using it is done)
+cudaError_t host_pinned_malloc(void** p, size_t bytes);  // cudaMallocHost through the block cache
+void host_pinned_free(void* p);
+template <typename T>
+inline cudaError_t dev_alloc(T** p, size_t bytes) {
+  return dev_malloc(reinterpret_cast<void**>(p), bytes);
+}
+template <typename T>
+inline cudaError_t host_pinned_alloc(T** p, size_t bytes) {
+  return host_pinned_malloc(reinterpret_cast<void**>(p), bytes);
+}
 
 // Returns from the calling function with RPCA_ECUDA (and the context's error text) on failure.
 #define RPCA_CUDA(c, call)                              \

@@ -109,9 +109,9 @@ struct SketchBuffers {
 };
 
 static void free_sketch_buffers(SketchBuffers& b) {
-  cudaFree(b.buf);
-  cudaFree(b.st);
-  cudaFree(b.ts.part);
+  dev_free(b.buf);
+  dev_free(b.st);
+  dev_free(b.ts.part);
   b.buf = nullptr;
   b.st = nullptr;
   b.ts.part = nullptr;
@@ -137,18 +137,18 @@ static rpca_status ensure_sketch(rpca_ctx* c, int l, SketchBuffers** out) {
       free_sketch_buffers(b);
     }
     const int64_t nf = n * l + m * l + n * l + n * 8 + m * 8 + m * 8 + n * 8;
-    if (cudaMalloc(&b.buf, sizeof(float) * nf) != cudaSuccess) {
+    if (dev_alloc(&b.buf, sizeof(float) * nf) != cudaSuccess) {
       b.buf = nullptr;
       return set_err(c, RPCA_ENOMEM, "cudaMalloc");
     }
-    if (cudaMalloc(&b.st, sizeof(SketchState)) != cudaSuccess) {
+    if (dev_alloc(&b.st, sizeof(SketchState)) != cudaSuccess) {
       b.st = nullptr;
       free_sketch_buffers(b);
       return set_err(c, RPCA_ENOMEM, "cudaMalloc");
     }
     b.ts.grid = 2 * c->nsm;
     b.ts.part_n = (size_t)b.ts.grid * 2304;
-    if (cudaMalloc(&b.ts.part, sizeof(double) * b.ts.part_n) != cudaSuccess) {
+    if (dev_alloc(&b.ts.part, sizeof(double) * b.ts.part_n) != cudaSuccess) {
       b.ts.part = nullptr;
       free_sketch_buffers(b);
       return set_err(c, RPCA_ENOMEM, "cudaMalloc");
@@ -264,7 +264,7 @@ rpca_status sketch_init(rpca_ctx* c, const float* Omega, float* U, float* V) {
   if ((s = sk_apply(c, b, l, nullptr, b.Y, nullptr, b.Z)) != RPCA_OK) return s;
   if (ts_gram_c(c, b.Z, n, l, b.Z, n, l, n, b.st->G, b.ts, c->stream) != cudaSuccess)
     return set_err(c, RPCA_ECUDA, "ts_gram");
-  if (!c->sk_sigma && cudaMalloc(&c->sk_sigma, sizeof(float) * SK_LMAX) != cudaSuccess)
+  if (!c->sk_sigma && dev_alloc(&c->sk_sigma, sizeof(float) * SK_LMAX) != cudaSuccess)
     return set_err(c, RPCA_ENOMEM, "cudaMalloc");
   const float inv_p = (float)(1.0 / std::max(c->p_hat, 1e-30));
   sk_small_svd_kernel<<<1, 256, 0, c->stream>>>(b.st, l, k, c->sk_sigma, inv_p);

@@ -950,12 +950,12 @@ void free_solver(rpca_ctx* c) {
   if (b->graph) cudaGraphDestroy(b->graph);
   if (b->cap) cudaStreamDestroy(b->cap);
   if (b->cap2) cudaStreamDestroy(b->cap2);
-  cudaFree(b->x);
-  cudaFree(b->S);
-  cudaFree(b->st);
-  cudaFree(b->blk);
-  cudaFree(b->counter);
-  cudaFreeHost(b->host);
+  dev_free(b->x);
+  dev_free(b->S);
+  dev_free(b->st);
+  dev_free(b->blk);
+  dev_free(b->counter);
+  host_pinned_free(b->host);
   delete b;
   c->sol = nullptr;
 }
@@ -1068,26 +1068,26 @@ static rpca_status ensure_solver(rpca_ctx* c) {
   // the elementwise kernels writes it, and they write combinations of zeros there.
   b->N = ((int64_t)(c->m + c->n) * c->k + 3) & ~(int64_t)3;
   const int64_t N = b->N;
-  SOL_CUDA(cudaMalloc(&b->x, sizeof(float) * 5 * N));
+  SOL_CUDA(dev_alloc(&b->x, sizeof(float) * 5 * N));
   SOL_CUDA(cudaMemsetAsync(b->x, 0, sizeof(float) * 5 * N, c->stream));
   b->g = b->x + N;
   b->xt = b->g + N;
   b->gt = b->xt + N;
   b->d = b->gt + N;
-  SOL_CUDA(cudaMalloc(&b->S, sizeof(float) * 2 * (mcap + 1) * N));
+  SOL_CUDA(dev_alloc(&b->S, sizeof(float) * 2 * (mcap + 1) * N));
   b->Y = b->S + (int64_t)(mcap + 1) * N;
   SOL_CUDA(cudaMemsetAsync(b->S, 0, sizeof(float) * 2 * (mcap + 1) * N, c->stream));
-  SOL_CUDA(cudaMalloc(&b->st, sizeof(SolverState)));
+  SOL_CUDA(dev_alloc(&b->st, sizeof(SolverState)));
   SOL_CUDA(cudaMemsetAsync(b->st, 0, sizeof(SolverState), c->stream));
-  SOL_CUDA(cudaMallocHost(&b->host, sizeof(SolverState)));
+  SOL_CUDA(host_pinned_alloc(&b->host, sizeof(SolverState)));
   // Two CTAs per SM, or the context's CTA budget when it shares the GPU with others (the
   // batched form): a grid that fills every SM leaves no room for the other contexts' kernels.
   int64_t grid_cap = std::min<int64_t>(2LL * c->nsm, (int64_t)DOTS_GRP * DOTS_MAX_GRP);
   if (c->grid_cap > 0) grid_cap = std::min<int64_t>(grid_cap, c->grid_cap);
   b->grid = (int)std::max<int64_t>(1, std::min<int64_t>(grid_cap, (N + 255) / 256));
-  SOL_CUDA(cudaMalloc(&b->blk, sizeof(double) * std::max<size_t>(7 * ((size_t)b->grid + 64) * (mcap + 2),
+  SOL_CUDA(dev_alloc(&b->blk, sizeof(double) * std::max<size_t>(7 * ((size_t)b->grid + 64) * (mcap + 2),
                                                                   64 * ((size_t)b->grid + DOTS_MAX_GRP))));
-  SOL_CUDA(cudaMalloc(&b->counter, sizeof(unsigned int) * (1 + DOTS_MAX_GRP + 3)));
+  SOL_CUDA(dev_alloc(&b->counter, sizeof(unsigned int) * (1 + DOTS_MAX_GRP + 3)));
   SOL_CUDA(cudaMemsetAsync(b->counter, 0, sizeof(unsigned int) * (1 + DOTS_MAX_GRP + 3), c->stream));
   SOL_CUDA(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
   SOL_CUDA(cudaStreamCreateWithFlags(&b->cap2, cudaStreamNonBlocking));

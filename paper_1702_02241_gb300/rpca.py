@@ -105,6 +105,8 @@ def lib():
     L.rpca_certificate.restype = I
     L.rpca_destroy.argtypes = [P]
     L.rpca_destroy.restype = None
+    L.rpca_release_memory.argtypes = []
+    L.rpca_release_memory.restype = C.c_size_t
     L.rpca_last_error.argtypes = [P]
     L.rpca_last_error.restype = C.c_char_p
     L.rpca_plan_info.argtypes = [P, I, C.POINTER(C.c_int64)]
@@ -192,7 +194,7 @@ def lib():
 
 
 EXPORTED = ["rpca_default_options", "rpca_create", "rpca_fg", "rpca_apply", "rpca_init_sketch", "rpca_solve",
-            "rpca_certificate", "rpca_destroy", "rpca_last_error", "rpca_version", "rpca_plan_info", "rpca_plan_kernel",
+            "rpca_certificate", "rpca_destroy", "rpca_release_memory", "rpca_last_error", "rpca_version", "rpca_plan_info", "rpca_plan_kernel",
             "rpca_profile", "rpca_profile_read", "rpca_solve_log", "rpca_solve_trials", "rpca_x_storage", "rpca_fg_noalloc", "rpca_create_batch",
             "rpca_solve_batch", "rpca_batch_context", "rpca_batch_size", "rpca_batch_last_error",
             "rpca_destroy_batch", "rpca_ws_nparam", "rpca_ws_create", "rpca_ws_set_params", "rpca_ws_get_params",
@@ -413,6 +415,11 @@ def rpca_destroy_batch(b):
 
 def rpca_destroy(ctx):
     lib().rpca_destroy(ctx)
+
+
+def rpca_release_memory() -> int:
+    """Returns the memory the library keeps from destroyed contexts; the bytes released."""
+    return int(lib().rpca_release_memory())
 
 
 # ---- Learned warm start -------------------------------------------------------------------
