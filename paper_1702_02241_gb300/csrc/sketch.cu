@@ -17,6 +17,7 @@
 namespace rpca {
 
 constexpr int SK_LMAX = 32;
+constexpr int SK_CHUNK = 8;  // columns per product pass (the chunk buffers' width)
 
 struct SketchState {
   double G[SK_LMAX * SK_LMAX];
@@ -102,7 +103,9 @@ __global__ void __launch_bounds__(256) sk_small_svd_kernel(SketchState* st, int 
 
 struct SketchBuffers {
   float* buf = nullptr;
-  int l = 0;  // sketch width the buffers were made for
+  int l = 0;   // sketch width the buffers were made for
+  int lp = 0;  // columns of Om, Y, Z: l rounded up to the products' chunk width
+  int lw = 0;  // the current call's l rounded up to its chunk width (<= lp)
   float *Om, *Y, *Z, *BVc, *BUc, *Y1c, *Y2c;
   SketchState* st = nullptr;
   TsScratch ts;
@@ -116,6 +119,7 @@ static void free_sketch_buffers(SketchBuffers& b) {
   b.st = nullptr;
   b.ts.part = nullptr;
   b.l = 0;
+  b.lp = 0;
 }
 
 void sk_free(rpca_ctx* c) {
@@ -131,12 +135,13 @@ static rpca_status ensure_sketch(rpca_ctx* c, int l, SketchBuffers** out) {
   if (!c->sk) c->sk = new SketchBuffers();
   SketchBuffers& b = *c->sk;
   const int64_t m = c->m, n = c->n;
-  if (b.buf == nullptr || b.l < l) {
+  const int lp = (l + SK_CHUNK - 1) / SK_CHUNK * SK_CHUNK;
+  if (b.buf == nullptr || b.l < l || b.lp < lp) {
     if (b.buf) {
       cudaStreamSynchronize(c->stream);
       free_sketch_buffers(b);
     }
-    const int64_t nf = n * l + m * l + n * l + n * 8 + m * 8 + m * 8 + n * 8;
+    const int64_t nf = (n + m + n) * (int64_t)lp + (n + m + m + n) * (int64_t)SK_CHUNK;
     if (dev_alloc(&b.buf, sizeof(float) * nf) != cudaSuccess) {
       b.buf = nullptr;
       return set_err(c, RPCA_ENOMEM, "cudaMalloc");
@@ -154,14 +159,16 @@ static rpca_status ensure_sketch(rpca_ctx* c, int l, SketchBuffers** out) {
       return set_err(c, RPCA_ENOMEM, "cudaMalloc");
     }
     b.l = l;
+    b.lp = lp;
   }
+  b.lw = lp;
   b.Om = b.buf;
-  b.Y = b.Om + n * l;
-  b.Z = b.Y + m * l;
-  b.BVc = b.Z + n * l;
-  b.BUc = b.BVc + n * 8;
-  b.Y1c = b.BUc + m * 8;
-  b.Y2c = b.Y1c + m * 8;
+  b.Y = b.Om + n * b.lp;
+  b.Z = b.Y + m * b.lp;
+  b.BVc = b.Z + n * b.lp;
+  b.BUc = b.BVc + n * SK_CHUNK;
+  b.Y1c = b.BUc + m * SK_CHUNK;
+  b.Y2c = b.Y1c + m * SK_CHUNK;
   *out = &b;
   return RPCA_OK;
 }
@@ -173,41 +180,44 @@ static rpca_status ensure_sketch(rpca_ctx* c, int l, SketchBuffers** out) {
   } while (0)
 
 // Y1 (m x l) = -A*(X) BV (BV n x l),  or  Y2 (n x l) = -A*(X)^T BU (BU m x l), in chunks of
-// 8 columns, each one pass of the one-sided apply kernel with no forming factors.
+// 8 columns, each one pass of the one-sided apply kernel with no forming factors.  A full
+// chunk writes its columns of Y in place; a ragged last chunk goes through a zero-padded copy.
 static rpca_status sk_apply(rpca_ctx* c, SketchBuffers& b, int l, const float* BV, const float* BU, float* Y1,
                             float* Y2) {
   const int side = BV ? 1 : 2;
   const FgPlan* P = apply_plan(c, 0, side);
   if (!P) return RPCA_EUNSUPPORTED;
+  constexpr int W = SK_CHUNK;
   const int64_t m = c->m, n = c->n;
-  for (int c0 = 0; c0 < l; c0 += 8) {
-    const int w = std::min(8, l - c0);
+  for (int c0 = 0; c0 < l; c0 += W) {
+    const int w = std::min(W, l - c0);
     const float* bv = BV ? BV + n * c0 : b.BVc;
     const float* bu = BU ? BU + m * c0 : b.BUc;
-    if (w < 8) {  // ragged last chunk: zero-padded copy
+    if (w < W) {  // ragged last chunk: zero-padded copy
       if (BV) {
-        SK_CUDA(cudaMemsetAsync(b.BVc, 0, sizeof(float) * n * 8, c->stream));
+        SK_CUDA(cudaMemsetAsync(b.BVc, 0, sizeof(float) * n * W, c->stream));
         SK_CUDA(cudaMemcpyAsync(b.BVc, bv, sizeof(float) * n * w, cudaMemcpyDeviceToDevice, c->stream));
         bv = b.BVc;
       } else {
-        SK_CUDA(cudaMemsetAsync(b.BUc, 0, sizeof(float) * m * 8, c->stream));
+        SK_CUDA(cudaMemsetAsync(b.BUc, 0, sizeof(float) * m * W, c->stream));
         SK_CUDA(cudaMemcpyAsync(b.BUc, bu, sizeof(float) * m * w, cudaMemcpyDeviceToDevice, c->stream));
         bu = b.BUc;
       }
     }
+    const bool direct = w == W;  // the product's W columns go straight to Y
     FgLaunch L;
     L.U = b.BUc;  // not read: no forming factors
     L.V = b.BVc;
     L.BU = bu;
     L.BV = bv;
     L.fin_mode = FIN_APPLY;
-    L.GU = b.Y1c;
-    L.GV = b.Y2c;
+    L.GU = (direct && Y1) ? Y1 + m * c0 : b.Y1c;
+    L.GV = (direct && Y2) ? Y2 + n * c0 : b.Y2c;
     L.lam = INFINITY;
     rpca_status s = launch_fg(c, *P, L, c->stream);
     if (s != RPCA_OK) return s;
-    if (Y1) SK_CUDA(cudaMemcpyAsync(Y1 + m * c0, b.Y1c, sizeof(float) * m * w, cudaMemcpyDeviceToDevice, c->stream));
-    if (Y2) SK_CUDA(cudaMemcpyAsync(Y2 + n * c0, b.Y2c, sizeof(float) * n * w, cudaMemcpyDeviceToDevice, c->stream));
+    if (!direct && Y1) SK_CUDA(cudaMemcpyAsync(Y1 + m * c0, b.Y1c, sizeof(float) * m * w, cudaMemcpyDeviceToDevice, c->stream));
+    if (!direct && Y2) SK_CUDA(cudaMemcpyAsync(Y2 + n * c0, b.Y2c, sizeof(float) * n * w, cudaMemcpyDeviceToDevice, c->stream));
   }
   return RPCA_OK;
 }
@@ -246,22 +256,31 @@ rpca_status sketch_init(rpca_ctx* c, const float* Omega, float* U, float* V) {
     if (es != RPCA_OK) return es;
   }
   SketchBuffers& b = *bp;
+  // Om, Y and Z carry lp >= l columns, a multiple of the products' chunk width: the extra
+  // columns are zero (so are their products), and every product is whole chunks written in
+  // place, without the padded copies of a ragged chunk.
+  const int lp = b.lw;
+  if (lp > l) {
+    SK_CUDA(cudaMemsetAsync(b.Om + n * l, 0, sizeof(float) * n * (lp - l), c->stream));
+    SK_CUDA(cudaMemsetAsync(b.Y + m * l, 0, sizeof(float) * m * (lp - l), c->stream));
+    SK_CUDA(cudaMemsetAsync(b.Z + n * l, 0, sizeof(float) * n * (lp - l), c->stream));
+  }
   if (Omega) cudaMemcpyAsync(b.Om, Omega, sizeof(float) * n * l, cudaMemcpyDeviceToDevice, c->stream);
   else {
     fill_normal(b.Om, n * l, 0xC0FFEEULL ^ (c->opt.seed * 0x9E3779B97F4A7C15ULL), 1.f, c->stream);
     count_launches(c, 1);
   }
   rpca_status s;
-  if ((s = sk_apply(c, b, l, b.Om, nullptr, b.Y, nullptr)) != RPCA_OK) return s;
+  if ((s = sk_apply(c, b, lp, b.Om, nullptr, b.Y, nullptr)) != RPCA_OK) return s;
   if ((s = sk_orth(c, b, b.Y, m, l)) != RPCA_OK) return s;
   for (int it = 0; it < q; ++it) {
-    if ((s = sk_apply(c, b, l, nullptr, b.Y, nullptr, b.Z)) != RPCA_OK) return s;
+    if ((s = sk_apply(c, b, lp, nullptr, b.Y, nullptr, b.Z)) != RPCA_OK) return s;
     if ((s = sk_orth(c, b, b.Z, n, l)) != RPCA_OK) return s;
-    if ((s = sk_apply(c, b, l, b.Z, nullptr, b.Y, nullptr)) != RPCA_OK) return s;
+    if ((s = sk_apply(c, b, lp, b.Z, nullptr, b.Y, nullptr)) != RPCA_OK) return s;
     if ((s = sk_orth(c, b, b.Y, m, l)) != RPCA_OK) return s;
   }
   // B^T = A*(X)^T Q = -(D^T Q) / p_hat.
-  if ((s = sk_apply(c, b, l, nullptr, b.Y, nullptr, b.Z)) != RPCA_OK) return s;
+  if ((s = sk_apply(c, b, lp, nullptr, b.Y, nullptr, b.Z)) != RPCA_OK) return s;
   if (ts_gram_c(c, b.Z, n, l, b.Z, n, l, n, b.st->G, b.ts, c->stream) != cudaSuccess)
     return set_err(c, RPCA_ECUDA, "ts_gram");
   if (!c->sk_sigma && dev_alloc(&c->sk_sigma, sizeof(float) * SK_LMAX) != cudaSuccess)
