@@ -496,8 +496,13 @@ def run_batch(args):
         pg.barrier()
     torch.cuda.synchronize()
     clocks.start()
+    # Launch counts from the contexts' counters (read before and after; per-launch event
+    # profiling stays off in the timed region).
+    prof = (rpca.C.c_double * 6)()
+    launches0 = 0
     for c in ctxs:
-        rpca.lib().rpca_profile(c, 1)
+        rpca.lib().rpca_profile_read(c, prof)
+        launches0 += int(prof[4])
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     results = []
@@ -508,11 +513,9 @@ def run_batch(args):
     if pg is not None:
         pg.barrier()
     clk = clocks.stop()
-    launches = 0
-    prof = (rpca.C.c_double * 6)()
+    launches = -launches0
     for c in ctxs:
         rpca.lib().rpca_profile_read(c, prof)
-        rpca.lib().rpca_profile(c, 0)
         launches += int(prof[4])
     t_step = max_over_ranks(e0.elapsed_time(e1) / 1e3 / args.steps, pg, dev)
     st, res = results[-1]

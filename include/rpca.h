@@ -211,17 +211,37 @@ RPCA_API rpca_status rpca_create_batch(rpca_batch **out, int count, const int64_
                                        void *cuda_stream);
 /*
  * Solves every problem of the batch as rpca_solve does (U[i], V[i]: device m[i] x k[i] and
- * n[i] x k[i] buffers, in and out), concurrently: host worker threads (environment variable
- * RPCA_BATCH_THREADS, default 4 per hardware thread up to 64) drive the instances' solves on
- * their own streams, so that their kernels overlap on the GPU.  RPCA_BATCH_MODE=rounds (float32
- * X, k <= 16) advances all instances together instead: one CUDA graph launch runs five L-BFGS
- * iterations of every unfinished instance, the host takes the certificate decisions between
- * launches; the graph is kept by the batch for later solves.  res (may be NULL) receives
- * count results.  Work on cuda_stream before the call is ordered before the solves, and the
- * stream is ordered after them.  Returns RPCA_OK when every instance met its certificate
- * tolerance, RPCA_ENOTCONV when some did not (see res[i].status), another status on an error.
+ * n[i] x k[i] buffers, in and out), concurrently, with one of three drivers:
+ *   RPCA_DRIVER_GROUPED (the default where every instance has float32 X, a factor rank
+ *     <= 16 and an L-BFGS memory <= 10): the line-search trials of all unfinished instances
+ *     run in shared launches, one launch of the fused objective/gradient pass per group of
+ *     instances of the same factor rank and block size plus one launch each of the gradient
+ *     assembly with the line-search step, the inner products with the two-loop scalars, and
+ *     the direction, every kernel finding its instance from a device table; chunks of five
+ *     trial rounds, between which the host takes each instance's decisions; an instance
+ *     whose certificate is due leaves the table while a host worker thread evaluates it on the
+ *     instance's stream, and the others keep iterating.  Each instance's iterates are those of
+ *     rpca_solve on its context (the same kernels on the same grids); the iteration at which
+ *     it stops can differ (decisions come after whole chunks of its trials).  res[i].ms_iter
+ *     counts the instance's own launches only (the shared ones are not divided among them).
+ *   RPCA_DRIVER_THREADS (RPCA_BATCH_MODE=threads, or where the grouped driver does not apply):
+ *     host worker threads (environment variable RPCA_BATCH_THREADS, default 4 per hardware
+ *     thread up to 64) drive the instances' solves on their own streams, so that their
+ *     kernels overlap on the GPU.
+ *   RPCA_DRIVER_ROUNDS (RPCA_BATCH_MODE=rounds; float32 X, k <= 16): one CUDA graph launch runs
+ *     five L-BFGS iterations of every unfinished instance, each instance's kernels on a branch
+ *     of their own; the host takes the certificate decisions between launches; the graph is
+ *     kept by the batch for later solves.
+ * Certificates (all drivers) are evaluated by host worker threads, up to RPCA_BATCH_THREADS at
+ * a time.  res (may be NULL) receives count results.  Work on cuda_stream before the call is
+ * ordered before the solves, and the stream is ordered after them.  Returns RPCA_OK when every
+ * instance met its certificate tolerance, RPCA_ENOTCONV when some did not (see res[i].status),
+ * another status on an error.
  */
 RPCA_API rpca_status rpca_solve_batch(rpca_batch *b, float *const *U, float *const *V, rpca_result *res);
+enum { RPCA_DRIVER_THREADS = 0, RPCA_DRIVER_ROUNDS = 1, RPCA_DRIVER_GROUPED = 2 };
+/* The driver of the batch's last rpca_solve_batch (RPCA_DRIVER_*), -1 before the first. */
+RPCA_API int rpca_batch_driver(const rpca_batch *b);
 RPCA_API rpca_ctx *rpca_batch_context(rpca_batch *b, int i); /* instance i's context (owned by b) */
 RPCA_API int rpca_batch_size(const rpca_batch *b);
 RPCA_API const char *rpca_batch_last_error(const rpca_batch *b);

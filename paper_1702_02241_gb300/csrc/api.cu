@@ -546,6 +546,13 @@ static rpca_status make_plan(rpca_ctx* c, FgPlan* P, int K, int B, bool same, in
                                [&](const std::pair<double, FgPlan>& cp) { return cp.second.nrb * cp.second.ncs > cap; }),
                 cands.end());
   }
+  // A batch instance (plan_wc > 0) keeps its fused-pass configurations at plan_wc consumer
+  // warps where it has any: instances of one factor rank then share one instantiation and
+  // block size, so that the grouped driver launches one fused pass for all of them.
+  if (c->plan_wc > 0 && same && side == 0) {
+    auto other = [&](const std::pair<double, FgPlan>& cp) { return cp.second.mma || cp.second.tc || cp.second.WC != c->plan_wc; };
+    if (!std::all_of(cands.begin(), cands.end(), other)) cands.erase(std::remove_if(cands.begin(), cands.end(), other), cands.end());
+  }
   if (cands.empty()) {
     char buf[256];
     snprintf(buf, sizeof buf,
@@ -776,16 +783,11 @@ const FgPlan* apply_plan(rpca_ctx* c, int K, int side) {
   return P;
 }
 
-rpca_status launch_fg(rpca_ctx* c, const FgPlan& P, const FgLaunch& L, cudaStream_t stream) {
-  if (P.large) return launch_fg_large(c, P, L, stream);
-  FgArgs a;
+// The arguments of one fused pass (a) and of its assembly (f) for launch L on plan P.
+void fg_launch_args(rpca_ctx* c, const FgPlan& P, const FgLaunch& L, FgArgs* ap, FinArgs* fp) {
+  FgArgs& a = *ap;
   a.starve = 0;
   a.wait_ns = 0;
-  if (c->fault_fg > 0 && !P.mma && !P.tc) {  // failure injection: this launch's copies are never issued
-    --c->fault_fg;
-    a.starve = 1;
-    a.wait_ns = 1000000ull;  // 1 ms
-  }
   a.m = c->m;
   a.n = c->n;
   a.mpad = c->mpad;
@@ -811,27 +813,8 @@ rpca_status launch_fg(rpca_ctx* c, const FgPlan& P, const FgLaunch& L, cudaStrea
   a.Ppsi = w.Ppsi;
   a.err = c->ws.err;
   a.xscale = c->xscale;
-  void* args[] = {(void*)&P.tmX, (void*)&P.tmM, (void*)&a};
-  // Event pairs bracket the two launches while profiling (never inside a graph capture).
-  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-  if (c->prof) cudaStreamIsCapturing(stream, &cap);
-  const bool timed = c->prof && cap == cudaStreamCaptureStatusNone;
-  if (timed) {
-    while (c->ev_pool.size() < c->ev_used + 4) {
-      cudaEvent_t e;
-      RPCA_CUDA(c, cudaEventCreate(&e));
-      c->ev_pool.push_back(e);
-    }
-    for (int i = 0; i < 4; ++i) ev[i] = c->ev_pool[c->ev_used + i];
-    c->ev_used += 4;
-    RPCA_CUDA(c, cudaEventRecord(ev[0], stream));
-  }
-  RPCA_CUDA(c, cudaLaunchKernel(P.var->fn, dim3(P.nrb * P.ncs), dim3(P.threads), args, P.smem, stream));
-  if (timed) RPCA_CUDA(c, cudaEventRecord(ev[1], stream));
-  const bool fuse_ls = L.ls_st != nullptr && L.fin_mode == FIN_FG;
-  count_launches(c, fuse_ls ? 2 : (L.fin_mode != FIN_APPLY ? 3 : 2));
-  FinArgs f{};  // every field not set below is zero (vpart, vec4, ...)
+  FinArgs& f = *fp;
+  f = FinArgs{};  // every field not set below is zero (vpart, vec4, ...)
   f.m = c->m;
   f.n = c->n;
   f.B = P.B;
@@ -865,6 +848,38 @@ rpca_status launch_fg(rpca_ctx* c, const FgPlan& P, const FgLaunch& L, cudaStrea
   f.out = L.out ? L.out : c->ws.out;
   f.vpart = L.vpart;
   f.vec4 = fin_vec4(f);
+}
+
+rpca_status launch_fg(rpca_ctx* c, const FgPlan& P, const FgLaunch& L, cudaStream_t stream) {
+  if (P.large) return launch_fg_large(c, P, L, stream);
+  FgArgs a;
+  FinArgs f;
+  fg_launch_args(c, P, L, &a, &f);
+  if (c->fault_fg > 0 && !P.mma && !P.tc) {  // failure injection: this launch's copies are never issued
+    --c->fault_fg;
+    a.starve = 1;
+    a.wait_ns = 1000000ull;  // 1 ms
+  }
+  void* args[] = {(void*)&P.tmX, (void*)&P.tmM, (void*)&a};
+  // Event pairs bracket the two launches while profiling (never inside a graph capture).
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (c->prof) cudaStreamIsCapturing(stream, &cap);
+  const bool timed = c->prof && cap == cudaStreamCaptureStatusNone;
+  if (timed) {
+    while (c->ev_pool.size() < c->ev_used + 4) {
+      cudaEvent_t e;
+      RPCA_CUDA(c, cudaEventCreate(&e));
+      c->ev_pool.push_back(e);
+    }
+    for (int i = 0; i < 4; ++i) ev[i] = c->ev_pool[c->ev_used + i];
+    c->ev_used += 4;
+    RPCA_CUDA(c, cudaEventRecord(ev[0], stream));
+  }
+  RPCA_CUDA(c, cudaLaunchKernel(P.var->fn, dim3(P.nrb * P.ncs), dim3(P.threads), args, P.smem, stream));
+  if (timed) RPCA_CUDA(c, cudaEventRecord(ev[1], stream));
+  const bool fuse_ls = L.ls_st != nullptr && L.fin_mode == FIN_FG;
+  count_launches(c, fuse_ls ? 2 : (L.fin_mode != FIN_APPLY ? 3 : 2));
   if (timed) RPCA_CUDA(c, cudaEventRecord(ev[2], stream));
   if (fuse_ls) {
     RPCA_CUDA(c, launch_finalize_ls(f, P.fin_grid, L, stream));
@@ -1006,7 +1021,7 @@ namespace rpca {
 // contexts that share the GPU with many others (the batched form).
 rpca_status create_ctx(rpca_ctx** out, int64_t m, int64_t n, const float* X, int64_t ldx, const uint8_t* mask,
                        int64_t ldmask, int k, double lambda_L, double lambda_S, const rpca_options* opt,
-                       void* cuda_stream, int grid_cap) {
+                       void* cuda_stream, int grid_cap, int plan_wc) {
   if (!out) return set_err(nullptr, RPCA_EINVAL, "out is NULL");
   *out = nullptr;
   // m and n up to 2^27: every (row or column) x (block of <= 16 columns) index fits 31 bits.
@@ -1045,6 +1060,7 @@ rpca_status create_ctx(rpca_ctx** out, int64_t m, int64_t n, const float* X, int
   c->opt = o;
   c->stream = static_cast<cudaStream_t>(cuda_stream);
   c->grid_cap = std::max(0, grid_cap);
+  c->plan_wc = std::max(0, plan_wc);
   c->mpad = (int)((m + 3) / 4 * 4);
   auto fail = [&](rpca_status s) {
     snprintf(g_create_err, sizeof g_create_err, "%s", c->err.c_str());

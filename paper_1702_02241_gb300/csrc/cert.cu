@@ -28,6 +28,8 @@
 #include <cmath>
 #include <cstring>
 
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 #include "ctx.h"
 #include "smallla.cuh"
@@ -424,13 +426,16 @@ __global__ void __launch_bounds__(32) cert_ritz_warp_kernel(CertState* st, const
 }
 
 // Larger d: the CTA form, in shared memory up to d = 96, else in global memory.
+// Projected matrices up to RITZ_SMEM_D on a side are rotated in shared memory (A and V, 200 KB
+// at 160); larger ones in global memory (measured 3.7 ms for d in [128, 160) there).
+constexpr int RITZ_SMEM_D = 160;
 __global__ void __launch_bounds__(1024) cert_ritz_kernel(CertState* st, const double* T, float* Ag, float* Vg, int d,
                                                           double lam_L, int final_step, double* ritz) {
   __shared__ float s[LZ_TMAX];
   __shared__ int ord[LZ_TMAX];
   __shared__ int flag;
   extern __shared__ float dyn[];
-  const bool in_smem = d <= 96;
+  const bool in_smem = d <= RITZ_SMEM_D;
   float* A = in_smem ? dyn : Ag;
   float* V = in_smem ? dyn + d * d : Vg;
   for (int i = threadIdx.x; i < d * d; i += blockDim.x) {
@@ -587,6 +592,326 @@ static rpca_status normalise(rpca_ctx* c, float* Y, int64_t rows) {
   return RPCA_OK;
 }
 
+// ---------------------------------------------------------------------------------------------
+// The orthonormalisation of orth_block in one launch: a thread-block cluster of up to OC_MAXC
+// CTAs, each owning a contiguous range of rows of Y (kept in its shared memory for the whole
+// launch, written back at the end).  A Gram product ([B | Y]^T Y, B^T Y or Y^T Y) is formed per
+// CTA with one warp per column of the left factor, each lane summing its rows in float32 with
+// sixteen loads in flight, the lanes added in float-float; the CTAs' partials are exchanged
+// through distributed shared memory and summed by every CTA in rank order (every CTA holds the
+// same Gram matrix), and each CTA updates its own rows, one thread per row.  The steps, pivot
+// rules and collapse handling are those of orth_block; nothing is read back by the host.  Used
+// while the rows fit OC_MAXC x OC_ROWS and p <= OC_PMAX.
+constexpr int OC_THREADS = 512;
+constexpr int OC_WARPS = OC_THREADS / 32;
+constexpr int OC_MAXC = 8;                           // CTAs per cluster (the portable limit)
+constexpr int OC_ROWS = 2560;                        // rows per CTA at most
+constexpr int OC_PMAX = CERT_KMAX + LZ_B * LZ_SMAX;  // basis columns at most
+constexpr int OC_NA = OC_PMAX + LZ_B;                // Gram rows at most ([B | Y])
+constexpr int OC_UNROLL = 16;                        // loads in flight per lane
+
+struct OrthArgs {
+  const float* B;    // rows x p basis (orthonormal columns), ld rows
+  int p;
+  float* Y;          // rows x LZ_B block, ld rows: in place
+  const float* src;  // Y starts as a copy of src (rows x LZ_B, ld rows; may be Y)
+  int64_t rows;
+  int rows_per;      // rows per CTA
+  uint64_t seed;     // refill of collapsed columns
+};
+
+struct OcSmem {
+  double* G;     // [OC_NA * LZ_B] the summed Gram, G[i * LZ_B + c]
+  float2* part;  // [2][OC_NA * LZ_B] this CTA's Gram partials (float-float)
+  float* Gf;     // [OC_PMAX * LZ_B] G rows < p as float32 for the update
+  float* Ys;     // [OC_ROWS][LZ_B] this CTA's rows of Y, row-major
+};
+inline size_t oc_smem_bytes() {
+  return sizeof(double) * OC_NA * LZ_B + sizeof(float2) * 2 * OC_NA * LZ_B + sizeof(float) * OC_PMAX * LZ_B +
+         sizeof(float) * (size_t)OC_ROWS * LZ_B;
+}
+__device__ inline OcSmem oc_layout(unsigned char* base) {
+  OcSmem L;
+  L.G = reinterpret_cast<double*>(base);
+  L.part = reinterpret_cast<float2*>(L.G + OC_NA * LZ_B);
+  L.Gf = reinterpret_cast<float*>(L.part + 2 * OC_NA * LZ_B);
+  L.Ys = L.Gf + OC_PMAX * LZ_B;
+  return L;
+}
+
+// Warp reduce-scatter of eight float-float sums: afterwards lane l with (l & 3) == 0 holds the
+// warp's total of sum number l >> 2.
+__device__ inline ff2 oc_warp_sum8(ff2 v[8], int lane) {
+  // xor 16: keep four of the eight (upper half of the lanes the upper four).
+  const bool h16 = lane & 16;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const ff2 send = h16 ? v[q] : v[q + 4];
+    const ff2 recv = ff_shfl_xor(send, 16);
+    v[q] = ff_add(h16 ? v[q + 4] : v[q], recv);
+  }
+  const bool h8 = lane & 8;
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const ff2 send = h8 ? v[q] : v[q + 2];
+    const ff2 recv = ff_shfl_xor(send, 8);
+    v[q] = ff_add(h8 ? v[q + 2] : v[q], recv);
+  }
+  const bool h4 = lane & 4;
+  {
+    const ff2 send = h4 ? v[0] : v[1];
+    const ff2 recv = ff_shfl_xor(send, 4);
+    v[0] = ff_add(h4 ? v[1] : v[0], recv);
+  }
+  v[0] = ff_add(v[0], ff_shfl_xor(v[0], 2));
+  v[0] = ff_add(v[0], ff_shfl_xor(v[0], 1));
+  return v[0];  // sum number (lane >> 4) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1) = lane >> 2
+}
+
+// Gram rows [nb columns of B | ny (0 or LZ_B) columns of Y]^T Y over this CTA's nr rows (from
+// row r0), summed over the cluster into L.G[i * LZ_B + c] (i < nb + ny).  buf alternates
+// between calls, so that one cluster barrier per call orders every CTA's reads of a buffer
+// before its next write.
+__device__ void oc_gram(const OrthArgs& a, const OcSmem& L, int nb, int ny, int64_t r0, int nr, int buf,
+                        cooperative_groups::cluster_group& cl) {
+  const int nA = nb + ny;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float2* mine = L.part + (size_t)buf * OC_NA * LZ_B;
+  for (int i = warp; i < nA; i += OC_WARPS) {
+    float acc[LZ_B];
+#pragma unroll
+    for (int c = 0; c < LZ_B; ++c) acc[c] = 0.f;
+    const float* col = i < nb ? a.B + (int64_t)i * a.rows + r0 : nullptr;
+    const int yc = i - nb;
+    for (int base = 0; base < nr; base += 32 * OC_UNROLL) {
+      float x[OC_UNROLL];
+#pragma unroll
+      for (int u = 0; u < OC_UNROLL; ++u) {
+        const int rl = base + u * 32 + lane;
+        x[u] = rl < nr ? (col ? __ldg(col + rl) : L.Ys[rl * LZ_B + yc]) : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < OC_UNROLL; ++u) {
+        const int rl = base + u * 32 + lane;
+        if (rl < nr) {
+          const float4 y0 = *reinterpret_cast<const float4*>(L.Ys + rl * LZ_B);
+          const float4 y1 = *reinterpret_cast<const float4*>(L.Ys + rl * LZ_B + 4);
+          acc[0] = fmaf(x[u], y0.x, acc[0]);
+          acc[1] = fmaf(x[u], y0.y, acc[1]);
+          acc[2] = fmaf(x[u], y0.z, acc[2]);
+          acc[3] = fmaf(x[u], y0.w, acc[3]);
+          acc[4] = fmaf(x[u], y1.x, acc[4]);
+          acc[5] = fmaf(x[u], y1.y, acc[5]);
+          acc[6] = fmaf(x[u], y1.z, acc[6]);
+          acc[7] = fmaf(x[u], y1.w, acc[7]);
+        }
+      }
+    }
+    ff2 v[LZ_B];
+#pragma unroll
+    for (int c = 0; c < LZ_B; ++c) v[c] = ff_make(acc[c]);
+    const ff2 t = oc_warp_sum8(v, lane);
+    if ((lane & 3) == 0) mine[i * LZ_B + (lane >> 2)] = make_float2(t.hi, t.lo);
+  }
+  cl.sync();
+  const int nc = (int)cl.num_blocks();
+  for (int e = threadIdx.x; e < nA * LZ_B; e += OC_THREADS) {
+    ff2 t = ff_make(0.f);
+    for (int q = 0; q < nc; ++q) {
+      const float2 v = cl.map_shared_rank(mine, q)[e];
+      t = ff_add(t, ff2{v.x, v.y});
+    }
+    L.G[e] = ff_to_d(t);
+    if (e < nb * LZ_B) L.Gf[e] = (float)L.G[e];  // B^T Y for oc_sub_basis
+  }
+  __syncthreads();
+}
+
+// Y -= B G[0:p] over this CTA's rows, one thread per row (G from the last oc_gram).
+__device__ void oc_sub_basis(const OrthArgs& a, const OcSmem& L, int64_t r0, int nr) {
+  for (int rl = threadIdx.x; rl < nr; rl += OC_THREADS) {
+    const float* brow = a.B + r0 + rl;
+    float s[LZ_B];
+#pragma unroll
+    for (int c = 0; c < LZ_B; ++c) s[c] = 0.f;
+    for (int i0 = 0; i0 < a.p; i0 += OC_UNROLL) {
+      float x[OC_UNROLL];
+#pragma unroll
+      for (int u = 0; u < OC_UNROLL; ++u) x[u] = i0 + u < a.p ? __ldg(brow + (int64_t)(i0 + u) * a.rows) : 0.f;
+#pragma unroll
+      for (int u = 0; u < OC_UNROLL; ++u) {
+        if (i0 + u < a.p) {
+          const float4 g0 = *reinterpret_cast<const float4*>(L.Gf + (i0 + u) * LZ_B);
+          const float4 g1 = *reinterpret_cast<const float4*>(L.Gf + (i0 + u) * LZ_B + 4);
+          s[0] = fmaf(x[u], g0.x, s[0]);
+          s[1] = fmaf(x[u], g0.y, s[1]);
+          s[2] = fmaf(x[u], g0.z, s[2]);
+          s[3] = fmaf(x[u], g0.w, s[3]);
+          s[4] = fmaf(x[u], g1.x, s[4]);
+          s[5] = fmaf(x[u], g1.y, s[5]);
+          s[6] = fmaf(x[u], g1.z, s[6]);
+          s[7] = fmaf(x[u], g1.w, s[7]);
+        }
+      }
+    }
+    float* y = L.Ys + rl * LZ_B;
+#pragma unroll
+    for (int c = 0; c < LZ_B; ++c) y[c] -= s[c];
+  }
+  __syncthreads();
+}
+
+// Y <- Y M over this CTA's rows, M an 8 x 8 matrix (column-major doubles in shared memory).
+__device__ void oc_mul_small(const OcSmem& L, const double* M, int nr) {
+  __shared__ float Mf[LZ_B * LZ_B];
+  if (threadIdx.x < LZ_B * LZ_B) Mf[threadIdx.x] = (float)M[threadIdx.x];
+  __syncthreads();
+  for (int rl = threadIdx.x; rl < nr; rl += OC_THREADS) {
+    float* y = L.Ys + rl * LZ_B;
+    float v[LZ_B], o[LZ_B];
+#pragma unroll
+    for (int j = 0; j < LZ_B; ++j) v[j] = y[j];
+#pragma unroll
+    for (int c = 0; c < LZ_B; ++c) {
+      float t = 0.f;
+#pragma unroll
+      for (int j = 0; j < LZ_B; ++j) t = fmaf(v[j], Mf[j + c * LZ_B], t);
+      o[c] = t;
+    }
+#pragma unroll
+    for (int c = 0; c < LZ_B; ++c) y[c] = o[c];
+  }
+  __syncthreads();
+}
+
+// Columns in `mask` of this CTA's rows: replaced by the counter-based values of
+// cert_refill_kernel (refill) or zeroed.
+__device__ void oc_fix_cols(const OrthArgs& a, const OcSmem& L, int mask, bool refill, int64_t r0, int nr) {
+  for (int e = threadIdx.x; e < nr * LZ_B; e += OC_THREADS) {
+    const int rl = e >> 3, c = e & 7;
+    if (!((mask >> c) & 1)) continue;
+    float v = 0.f;
+    if (refill) {
+      const int64_t i = r0 + rl + (int64_t)c * a.rows;
+      uint64_t z = a.seed * 0x9E3779B97F4A7C15ull + (uint64_t)i;
+      z += 0x9e3779b97f4a7c15ull;
+      z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+      z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+      z ^= z >> 31;
+      v = (float)((double)(z >> 11) * (1.0 / 9007199254740992.0) - 0.5);
+    }
+    L.Ys[e] = v;
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(OC_THREADS, 1) cert_orth_cluster_kernel(OrthArgs a) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  extern __shared__ __align__(16) unsigned char oc_raw[];
+  const OcSmem L = oc_layout(oc_raw);
+  __shared__ double H[LZ_B * LZ_B], W[LZ_B * LZ_B], R[LZ_B * LZ_B], Ri[LZ_B * LZ_B], rd[LZ_B], n0[LZ_B];
+  __shared__ int bad_s;
+  const int64_t r0 = (int64_t)cl.block_rank() * a.rows_per;
+  const int nr = (int)(r0 < a.rows ? (a.rows - r0 < a.rows_per ? a.rows - r0 : a.rows_per) : 0);
+  for (int e = threadIdx.x; e < nr * LZ_B; e += OC_THREADS) {  // this CTA's rows of Y (from src)
+    const int c = e / nr, rl = e - c * nr;
+    L.Ys[rl * LZ_B + c] = a.src[r0 + rl + (int64_t)c * a.rows];
+  }
+  __syncthreads();
+  int buf = 0;
+  const int p = a.p;
+  auto gram = [&](int nb, int ny) {
+    oc_gram(a, L, nb, ny, r0, nr, buf, cl);
+    buf ^= 1;
+  };
+  auto yty = [&]() {  // H = Y^T Y
+    gram(0, LZ_B);
+    if (threadIdx.x < LZ_B * LZ_B) H[threadIdx.x] = L.G[threadIdx.x];
+    __syncthreads();
+  };
+  auto project = [&]() {  // Y -= B (B^T Y)
+    if (p == 0) return;
+    gram(p, 0);
+    oc_sub_basis(a, L, r0, nr);
+  };
+  auto normalise = [&]() {  // Y <- Y R^{-1}, floor 1e-12 of the largest pivot
+    yty();
+    cta_chol_masked(H, LZ_B, 1e-12, nullptr, W, R, Ri, rd, &bad_s);
+    oc_mul_small(L, Ri, nr);
+  };
+  const double collapse = 1e-6;
+  // First projection with the column norms from the same pass ([B | Y]^T Y).
+  gram(p, LZ_B);
+  if (threadIdx.x < LZ_B) n0[threadIdx.x] = L.G[(p + threadIdx.x) * LZ_B + threadIdx.x];
+  __syncthreads();
+  if (p > 0) oc_sub_basis(a, L, r0, nr);
+  project();
+  yty();
+  int bad = cta_chol_masked(H, LZ_B, collapse, n0, W, R, Ri, rd, &bad_s);
+  if (bad != 0) {
+    // Collapsed columns: refilled with random values, projected again and zeroed if they
+    // collapse once more.
+    oc_fix_cols(a, L, bad, true, r0, nr);
+    yty();
+    if (threadIdx.x < LZ_B) n0[threadIdx.x] = H[threadIdx.x * (LZ_B + 1)];
+    __syncthreads();
+    project();
+    project();
+    yty();
+    bad = cta_chol_masked(H, LZ_B, collapse, n0, W, R, Ri, rd, &bad_s);
+    if (bad != 0) oc_fix_cols(a, L, bad, false, r0, nr);
+    normalise();
+  } else {
+    oc_mul_small(L, Ri, nr);
+  }
+  project();
+  normalise();
+  for (int e = threadIdx.x; e < nr * LZ_B; e += OC_THREADS) {
+    const int c = e / nr, rl = e - c * nr;
+    a.Y[r0 + rl + (int64_t)c * a.rows] = L.Ys[rl * LZ_B + c];
+  }
+  cl.sync();  // no CTA leaves while another may still read its partials
+}
+
+// Whether orth_block can run as one cluster launch for these sizes.
+static bool orth_cluster_fits(int64_t rows, int p) {
+  return rows >= 1 && rows <= (int64_t)OC_MAXC * OC_ROWS && p >= 0 && p <= OC_PMAX;
+}
+
+static rpca_status orth_block_cluster(rpca_ctx* c, const float* src, float* Y, int64_t rows, const float* Bm, int p,
+                                      uint64_t seed) {
+  static const bool attr_ok = [] {
+    return cudaFuncSetAttribute(cert_orth_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)oc_smem_bytes()) == cudaSuccess;
+  }();
+  if (!attr_ok) return set_err(c, RPCA_ECUDA, "shared memory of the cluster orthonormalisation");
+  const int nc = (int)std::min<int64_t>(OC_MAXC, std::max<int64_t>(1, (rows + 1023) / 1024));
+  OrthArgs a;
+  a.B = Bm;
+  a.p = p;
+  a.Y = Y;
+  a.src = src ? src : Y;
+  a.rows = rows;
+  a.rows_per = (int)((rows + nc - 1) / nc);
+  a.seed = seed;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nc);
+  cfg.blockDim = dim3(OC_THREADS);
+  cfg.dynamicSmemBytes = oc_smem_bytes();
+  cfg.stream = c->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = nc;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  CERT_CUDA(cudaLaunchKernelEx(&cfg, cert_orth_cluster_kernel, a));
+  count_launches(c, 1);
+  return RPCA_OK;
+}
+
 // Orthonormalises the block Y (rows x 8) against the basis B (rows x p; the fixed range
 // basis followed by the Krylov blocks, contiguous), by two passes of classical Gram-Schmidt
 // and CholeskyQR.  A column that loses all but 1e-3 of its norm to the projection and to the
@@ -629,6 +954,23 @@ static rpca_status orth_block(rpca_ctx* c, float* Y, int64_t rows, const float* 
   }
   if ((s = project_out(c, Bm, p, Y, rows)) != RPCA_OK) return s;
   return normalise(c, Y, rows);
+}
+
+// orth_block of Y (first a copy of src when src is not null): one launch of a single CTA for
+// up to OC_SINGLE rows, else the multi-launch form.  RPCA_CERT_CLUSTER=1 takes the cluster
+// launch wherever it fits (up to OC_MAXC x OC_ROWS rows), =0 never.  Measured on the
+// 256-instance batch (m up to 20000), the eight-CTA cluster kept the m-side blocks 2.5x longer
+// on the device than the multi-launch form (eight SMs stream the basis at a fraction of the
+// GPU's rate), although it made a quarter of the launches; the single CTA takes the small side.
+constexpr int64_t OC_SINGLE = 1024;
+static rpca_status orth_any(rpca_ctx* c, const float* src, float* Y, int64_t rows, const float* Bm, int p,
+                            uint64_t seed) {
+  const char* env = getenv("RPCA_CERT_CLUSTER");
+  const int mode = env ? (env[0] == '0' ? 0 : 2) : 1;  // 0 never, 1 single CTA only, 2 wherever it fits
+  if (mode > 0 && orth_cluster_fits(rows, p) && (mode == 2 || rows <= OC_SINGLE))
+    return orth_block_cluster(c, src, Y, rows, Bm, p, seed);
+  if (src && src != Y) CERT_CUDA(cudaMemcpyAsync(Y, src, sizeof(float) * rows * LZ_B, cudaMemcpyDeviceToDevice, c->stream));
+  return orth_block(c, Y, rows, Bm, p, seed);
 }
 
 // side 1: Y1 = D BV;  side 2: Y2 = D^T BU  (one pass over X each).
@@ -731,7 +1073,7 @@ rpca_status cert_compute(rpca_ctx* c, const float* U, const float* V, rpca_cert*
     count_launches(c, 1);
     fill_normal(b->Q, n * LZ_B, 0x5eedULL + (uint64_t)c->opt.seed, 1.f, c->stream);
     count_launches(c, 1);
-    if ((s = orth_block(c, b->Q, n, b->V1, r, 11)) != RPCA_OK) return s;
+    if ((s = orth_any(c, nullptr, b->Q, n, b->V1, r, 11)) != RPCA_OK) return s;
     // Krylov dimension cap: 256, or the dimension of the complement of range(V1).
     const int64_t room = std::max<int64_t>(1, std::min(m, n) - r);
     const int smax = (int)std::min<int64_t>(LZ_SMAX, (room + LZ_B - 1) / LZ_B);
@@ -742,8 +1084,7 @@ rpca_status cert_compute(rpca_ctx* c, const float* U, const float* V, rpca_cert*
       // projection on U1 is removed by orth_block, and T = P^T A Q_j = P^T D Q_j because the
       // columns of P are orthogonal to U1.
       if ((s = apply_D(c, 1, Qj, b->zm, b->Wraw, b->Z)) != RPCA_OK) return s;
-      CERT_CUDA(cudaMemcpyAsync(Pj, b->Wraw, sizeof(float) * m * LZ_B, cudaMemcpyDeviceToDevice, c->stream));
-      if ((s = orth_block(c, Pj, m, b->U1, r + j * LZ_B, 1000 + 2 * j)) != RPCA_OK) return s;
+      if ((s = orth_any(c, b->Wraw, Pj, m, b->U1, r + j * LZ_B, 1000 + 2 * j)) != RPCA_OK) return s;
       // Column block j of T = P^T A Q.
       CERT_CUDA(ts_gram_c(c, b->P, m, (j + 1) * LZ_B, b->Wraw, m, LZ_B, m, st->G, b->ts, c->stream));
       cert_store_T_kernel<<<1, 256, 0, c->stream>>>(st, b->T, (j + 1) * LZ_B, j * LZ_B);
@@ -755,9 +1096,9 @@ rpca_status cert_compute(rpca_ctx* c, const float* U, const float* V, rpca_cert*
         if (d <= 32) {
           cert_ritz_warp_kernel<<<1, 32, 0, c->stream>>>(st, b->T, d, c->lam_L, last ? 1 : 0, b->ritz);
         } else {
-          const size_t rsm = d <= 96 ? (size_t)2 * d * d * sizeof(float) : 0;
+          const size_t rsm = d <= RITZ_SMEM_D ? (size_t)2 * d * d * sizeof(float) : 0;
           CERT_CUDA(cudaFuncSetAttribute(cert_ritz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         2 * 96 * 96 * (int)sizeof(float)));
+                                         2 * RITZ_SMEM_D * RITZ_SMEM_D * (int)sizeof(float)));
           cert_ritz_kernel<<<1, 1024, rsm, c->stream>>>(st, b->T, b->Tw, b->Tv, d, c->lam_L, last ? 1 : 0, b->ritz);
         }
         count_launches(c, 1);
@@ -770,7 +1111,7 @@ rpca_status cert_compute(rpca_ctx* c, const float* U, const float* V, rpca_cert*
       // Q_{j+1} from A^T P_j = P_V1perp D^T P_j, orthogonal to V1 and Q_0..Q_j.
       float* Qn = b->Q + (int64_t)(j + 1) * LZ_B * n;
       if ((s = apply_D(c, 2, b->zn, Pj, b->W, Qn)) != RPCA_OK) return s;
-      if ((s = orth_block(c, Qn, n, b->V1, r + (j + 1) * LZ_B, 1001 + 2 * j)) != RPCA_OK) return s;
+      if ((s = orth_any(c, nullptr, Qn, n, b->V1, r + (j + 1) * LZ_B, 1001 + 2 * j)) != RPCA_OK) return s;
     }
   }
   CERT_CUDA(cudaMemcpyAsync(b->host, st, sizeof(CertState), cudaMemcpyDeviceToHost, c->stream));

@@ -91,6 +91,36 @@ RPCA_DEV void tma_load_2d_hint(void* dst, const CUtensorMap* map, int x, int y, 
 RPCA_DEV void prefetch_tmap(const CUtensorMap* map) {
   asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
 }
+// Grouped launches: entry q of a launch list owns the blocks [off[q], off[q + 1]) (off[0] = 0,
+// ascending); the entry that owns block `bid` is the last q with off[q] <= bid.
+RPCA_DEV int group_find(const int* __restrict__ off, int cnt, int bid) {
+  int lo = 0, hi = cnt - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(off + mid) <= bid) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Copies a kernel-argument struct from global to shared memory (8-byte words, one per thread;
+// the caller synchronises the block before reading it): grouped launches read their
+// instance's arguments there, as a plain launch reads its parameters, instead of holding
+// them in registers.
+template <class T>
+RPCA_DEV void args_to_shared(T* dst, const T* __restrict__ src) {
+  static_assert(sizeof(T) % 8 == 0 && sizeof(T) / 8 <= 96, "argument struct of whole words, at most 96");
+  if (threadIdx.x < sizeof(T) / 8)
+    reinterpret_cast<unsigned long long*>(dst)[threadIdx.x] =
+        __ldg(reinterpret_cast<const unsigned long long*>(src) + threadIdx.x);
+}
+
+// A tensor map in global memory that the host wrote (a copy before the launch) is made
+// visible to the tensor-map proxy before its first use by this thread.
+RPCA_DEV void fence_tensormap_acquire(const CUtensorMap* map) {
+  asm volatile("fence.proxy.tensormap::generic.acquire.sys [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(map))
+               : "memory");
+}
 
 // Named barrier over `nthreads` threads (ids 1..15; 0 is __syncthreads).
 RPCA_DEV void named_bar(int id, int nthreads) {

@@ -68,6 +68,7 @@ struct rpca_ctx {
   rpca_options opt;
   cudaStream_t stream = nullptr;
   int grid_cap = 0;  // CTA budget of the objective/gradient and L-BFGS launches (0: the whole GPU)
+  int plan_wc = 0;   // preferred consumer warps of the fg-mode fused pass (batch instances; 0: any)
   int device = 0, nsm = 0;
   size_t max_smem = 0;
   int mpad = 0;
@@ -112,6 +113,9 @@ struct rpca_ctx {
   int64_t prof_n[2] = {0, 0};
   int64_t launches = 0;
   int64_t graph_launches = 0;
+  // Set by the batched form's grouped iteration: the solver captures no iteration graph of
+  // its own for this context (one is captured when a later solve needs it).
+  bool no_iter_graph = false;
   // Failure injection (rpca_inject_fault): fused-kernel launches left to starve.
   int fault_fg = 0;
 };
@@ -175,6 +179,8 @@ struct FgLaunch {
   int vpart = 0;  // row shard: GV <- the raw partial D^T U, no V terms in the sums
 };
 rpca_status launch_fg(rpca_ctx* c, const FgPlan& P, const FgLaunch& L, cudaStream_t stream);
+// The arguments launch_fg passes to the fused pass and to its assembly (fused-kernel plans).
+void fg_launch_args(rpca_ctx* c, const FgPlan& P, const FgLaunch& L, FgArgs* a, FinArgs* f);
 cudaError_t launch_finalize_ls(const FinArgs& f, int grid, const FgLaunch& L, cudaStream_t stream);  // solver.cu
 const FgPlan* apply_plan(rpca_ctx* c, int K, int side);  // forming rank >= K (0, 8 or 16), side
 rpca_status make_xq(rpca_ctx* c, int xt);                // narrow copy of X (xq.cu)
@@ -187,7 +193,7 @@ rpca_status launch_fg_large(rpca_ctx* c, const FgPlan& P, const FgLaunch& L, cud
 rpca_status lk_product(rpca_ctx* c, const float* U, const float* V, const float** Lp, int64_t* ldl);
 rpca_status create_ctx(rpca_ctx** out, int64_t m, int64_t n, const float* X, int64_t ldx, const uint8_t* mask,
                        int64_t ldmask, int k, double lambda_L, double lambda_S, const rpca_options* opt,
-                       void* cuda_stream, int grid_cap);  // api.cu
+                       void* cuda_stream, int grid_cap, int plan_wc = 0);  // api.cu
 // The objective/gradient plan rpca_fg uses: the narrow copy's when there is one.
 inline const FgPlan& eval_plan(const rpca_ctx* c) { return c->xq_dt ? c->fg_plan_q : c->fg_plan; }
 inline void count_launches(rpca_ctx* c, int64_t n) { c->launches += n; }

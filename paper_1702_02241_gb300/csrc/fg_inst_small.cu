@@ -6,7 +6,8 @@ namespace rpca {
 
 template <int K, int R, int J>
 static void reg(FgVariant (*tab)[2]) {
-  tab[K][0] = FgVariant{(const void*)&fg_kernel<K, K, true, false, R, J>, R, J};
+  tab[K][0] = FgVariant{(const void*)&fg_kernel<K, K, true, false, R, J>, R, J,
+                        (const void*)&fg_group_kernel<K, K, true, false, R, J>};
   tab[K][1] = FgVariant{(const void*)&fg_kernel<K, K, true, true, R, J>, R, J};
 }
 

@@ -170,9 +170,11 @@ RPCA_DEV void lane_bit(int p, int e, int lane, int& word, int& bit) {
   }
 }
 
-template <int K, int B, bool SAME, bool MASKED, int R, int J, int SIDE = 0, int XT = FG_X_F32>
-__global__ void __launch_bounds__(288, 1) fg_kernel(const __grid_constant__ CUtensorMap tmX,
-                                                 const __grid_constant__ CUtensorMap tmM, FgArgs a) {
+// The pass over one tile: block `bid` of a grid of nrb x ncs tiles.  tmX, tmM: the tensor maps
+// (kernel parameters, or global memory written by the host before the launch: GMAP).
+template <int K, int B, bool SAME, bool MASKED, int R, int J, int SIDE, int XT, bool GMAP>
+__device__ __forceinline__ void fg_body(const CUtensorMap* tmX, const CUtensorMap* tmM, const FgArgs& a,
+                                        const int bid) {
   using T = FgTraits<K, B, SAME, R, J, SIDE>;
   constexpr int NP = T::NP, ROWS_W = T::ROWS_W, KV = T::KV, JB = T::JB;
   constexpr bool ROWSIDE = SIDE != 2, COLSIDE = SIDE != 1;  // which products are formed
@@ -184,7 +186,7 @@ __global__ void __launch_bounds__(288, 1) fg_kernel(const __grid_constant__ CUte
                                                        ~static_cast<uintptr_t>(1023));
   const int WC = (int)(blockDim.x >> 5) - 1;  // consumer warps; the last warp produces
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int rb = blockIdx.x % a.nrb, cs = blockIdx.x / a.nrb;
+  const int rb = bid % a.nrb, cs = bid / a.nrb;
   const int row0 = rb * WC * ROWS_W;
   const int col0 = cs * a.BN;
   const int ncols = min(a.BN, a.n - col0);
@@ -216,8 +218,12 @@ __global__ void __launch_bounds__(288, 1) fg_kernel(const __grid_constant__ CUte
 
   if (warp == WC) {  // ---------------- producer ----------------
     if (lane == 0 && !a.starve) {
-      prefetch_tmap(&tmX);
-      if (MASKED) prefetch_tmap(&tmM);
+      if constexpr (GMAP) {
+        fence_tensormap_acquire(tmX);
+        if (MASKED) fence_tensormap_acquire(tmM);
+      }
+      prefetch_tmap(tmX);
+      if (MASKED) prefetch_tmap(tmM);
       const uint64_t pol = l2_evict_first_policy();  // X and its bitmap are streamed once per pass
       int issued = 0;
       bool ok = true;
@@ -231,10 +237,10 @@ __global__ void __launch_bounds__(288, 1) fg_kernel(const __grid_constant__ CUte
         }
         mbar_arrive_expect_tx(&full[s], stage_bytes);
         for (int w = 0; w < WC; ++w)
-          tma_load_2d_hint(xs_all + ((size_t)s * WC + w) * xbox * XB, &tmX, row0 + w * ROWS_W, col0 + c * FG_BJ,
+          tma_load_2d_hint(xs_all + ((size_t)s * WC + w) * xbox * XB, tmX, row0 + w * ROWS_W, col0 + c * FG_BJ,
                            &full[s], pol);
         if constexpr (MASKED)
-          tma_load_2d_hint(ms_all + (size_t)s * mstage, &tmM, row0 / 32, col0 + c * FG_BJ, &full[s], pol);
+          tma_load_2d_hint(ms_all + (size_t)s * mstage, tmM, row0 / 32, col0 + c * FG_BJ, &full[s], pol);
         issued = c + 1;
       }
       // Wait (bounded) until every copy this thread issued has landed before leaving.
@@ -493,7 +499,7 @@ __global__ void __launch_bounds__(288, 1) fg_kernel(const __grid_constant__ CUte
   if (tid == 0) {
     ff2 s = ff_load(&scr[0]);
     for (int w = 1; w < WC; ++w) s = ff_add(s, ff_load(&scr[w]));
-    ff_store(&a.Ppsi[blockIdx.x], s);
+    ff_store(&a.Ppsi[bid], s);
   }
   for (int idx = tid; idx < (COLSIDE ? ncols * B : 0); idx += nct) {
     const int b = idx / ncols, jl = idx - b * ncols;
@@ -501,6 +507,35 @@ __global__ void __launch_bounds__(288, 1) fg_kernel(const __grid_constant__ CUte
     for (int w = 0; w < WC; ++w) sum += csum[((size_t)w * a.BN + jl) * B + b];
     a.PV[((size_t)rb * B + b) * a.n + col0 + jl] = sum;
   }
+}
+
+template <int K, int B, bool SAME, bool MASKED, int R, int J, int SIDE = 0, int XT = FG_X_F32>
+__global__ void __launch_bounds__(288, 1) fg_kernel(const __grid_constant__ CUtensorMap tmX,
+                                                 const __grid_constant__ CUtensorMap tmM, FgArgs a) {
+  fg_body<K, B, SAME, MASKED, R, J, SIDE, XT, false>(&tmX, &tmM, a, (int)blockIdx.x);
+}
+
+// Grouped form: the tiles of many independent problems in one launch.  Entry q of the launch's
+// list is instance ids[q], which owns the blocks [off[q], off[q + 1]) of the grid; its tensor
+// maps and arguments are the FgInst at the start of record ids[q] (records `stride` bytes
+// apart).  Every instance of a launch has the same instantiation and consumer-warp count
+// (blockDim), and the dynamic shared memory is the largest any of them needs.
+struct alignas(64) FgInst {
+  CUtensorMap tmX;
+  CUtensorMap tmM;
+  FgArgs a;
+};
+
+template <int K, int B, bool SAME, bool MASKED, int R, int J, int SIDE = 0, int XT = FG_X_F32>
+__global__ void __launch_bounds__(288, 1) fg_group_kernel(const unsigned char* __restrict__ rec, size_t stride,
+                                                       const int* __restrict__ ids, const int* __restrict__ off,
+                                                       int cnt) {
+  __shared__ FgArgs sa;
+  const int q = group_find(off, cnt, (int)blockIdx.x);
+  const FgInst* p = reinterpret_cast<const FgInst*>(rec + (size_t)__ldg(ids + q) * stride);
+  args_to_shared(&sa, &p->a);
+  __syncthreads();
+  fg_body<K, B, SAME, MASKED, R, J, SIDE, XT, true>(&p->tmX, &p->tmM, sa, (int)blockIdx.x - __ldg(off + q));
 }
 
 }  // namespace rpca

@@ -11,6 +11,9 @@ struct FgVariant {
   const void* fn;  // __global__ function pointer (nullptr: not compiled)
   int R;           // rows per lane
   int J;           // columns per reduction group
+  // Grouped form of the same instantiation (fg_group_kernel: many problems' tiles in one
+  // launch), nullptr when not compiled: fg mode, unmasked, float32 X.
+  const void* group = nullptr;
 };
 
 // Forming rank K (0..16), product width B, fg mode (B == K, operands = forming factors) or

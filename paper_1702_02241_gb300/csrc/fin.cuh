@@ -18,7 +18,8 @@ namespace rpca {
 // groups are added in a fixed order.
 // Elementwise work is float32 (the partial sums are float32 already); each block's dot
 // products (||x_t||^2, g.d, ||g||^2) go to float-float for the fixed-order block sums.
-RPCA_DEV void finalize_body(const FinArgs& a) {
+// bid: this block's index in the launch's grid of a.gu + fin_grid_v(n, B) blocks.
+RPCA_DEV void finalize_body(const FinArgs& a, const unsigned bid) {
   __shared__ float wsum[32][3];
   __shared__ float vs[8][32];
   __shared__ float alpha_s;
@@ -31,11 +32,11 @@ RPCA_DEV void finalize_body(const FinArgs& a) {
   const float lam = a.lam_f;
   const unsigned mB = (unsigned)a.m * (unsigned)a.B, nB = (unsigned)a.n * (unsigned)a.B;
   float nrm_f = 0.f, gd_f = 0.f, gg_f = 0.f;
-  if ((int)blockIdx.x < a.gu && a.vec4) {
+  if ((int)bid < a.gu && a.vec4) {
     // Four consecutive elements per thread (one row range of one column: m is a multiple of
     // 4), every array read and written as float4; the column-split partials are added in the
     // same order as below.
-    const unsigned e = (blockIdx.x * blockDim.x + threadIdx.x) * 4u;
+    const unsigned e = (bid * blockDim.x + threadIdx.x) * 4u;
     if (a.side != 2 && e < mB) {
       const int64_t cstride = (int64_t)a.B * a.mpad;
       const unsigned l = e / (unsigned)a.m, i = e - l * (unsigned)a.m;
@@ -79,14 +80,14 @@ RPCA_DEV void finalize_body(const FinArgs& a) {
       if (a.mode != FIN_APPLY && a.Ut) *reinterpret_cast<float4*>(a.Ut + e) = make_float4(xt[0], xt[1], xt[2], xt[3]);
       *reinterpret_cast<float4*>(a.GU + e) = make_float4(g[0], g[1], g[2], g[3]);
     }
-  } else if ((int)blockIdx.x < a.gu) {
+  } else if ((int)bid < a.gu) {
     // Loads of all FIN_EPT elements first, stores after: a store between them would order
     // the next element's loads after it (the compiler cannot rule out aliasing).
     float su[FIN_EPT], uu[FIN_EPT], du[FIN_EPT], dir[FIN_EPT];
     const int64_t cstride = (int64_t)a.B * a.mpad;
 #pragma unroll
     for (int u = 0; u < FIN_EPT; ++u) {
-      const unsigned e = (blockIdx.x + (unsigned)u * (unsigned)a.gu) * blockDim.x + threadIdx.x;
+      const unsigned e = (bid + (unsigned)u * (unsigned)a.gu) * blockDim.x + threadIdx.x;
       su[u] = 0.f;
       uu[u] = 0.f;
       du[u] = 0.f;
@@ -107,7 +108,7 @@ RPCA_DEV void finalize_body(const FinArgs& a) {
     }
 #pragma unroll
     for (int u = 0; u < FIN_EPT; ++u) {
-      const unsigned e = (blockIdx.x + (unsigned)u * (unsigned)a.gu) * blockDim.x + threadIdx.x;
+      const unsigned e = (bid + (unsigned)u * (unsigned)a.gu) * blockDim.x + threadIdx.x;
       if (a.side != 2 && e < mB) {
         float g, xt = 0.f;
         if (a.mode != FIN_APPLY) {
@@ -125,7 +126,7 @@ RPCA_DEV void finalize_body(const FinArgs& a) {
     }
   } else {
     const int q = threadIdx.x >> 5, t = threadIdx.x & 31;
-    const unsigned e2 = (blockIdx.x - a.gu) * 32 + t;
+    const unsigned e2 = (bid - a.gu) * 32 + t;
     const bool live = a.side != 1 && e2 < nB;
     unsigned l = 0, j = 0;
     float s = 0.f;
@@ -190,7 +191,7 @@ RPCA_DEV void finalize_body(const FinArgs& a) {
     const int v = threadIdx.x;
     ff2 t = ff_make(wsum[0][v]);
     for (int i = 1; i < (int)(blockDim.x >> 5); ++i) t = ff_add(t, ff_make(wsum[i][v]));
-    ff_store(&a.blk[3 * blockIdx.x + v], t);
+    ff_store(&a.blk[3 * bid + v], t);
   }
 }
 

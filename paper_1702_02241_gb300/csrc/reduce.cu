@@ -16,7 +16,7 @@ namespace rpca {
 
 __global__ void __launch_bounds__(256) finalize_kernel(FinArgs a) {
   if (a.gate != nullptr && *a.gate == 0) return;
-  finalize_body(a);
+  finalize_body(a, blockIdx.x);
 }
 
 __global__ void __launch_bounds__(256) finalize_reduce_kernel(FinArgs a, int nblocks) {

@@ -3,7 +3,10 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <condition_variable>
 #include <cstring>
+#include <deque>
+#include <mutex>
 #include <thread>
 #include <utility>
 #include <vector>
@@ -153,6 +156,10 @@ struct SolveJob {
   // Certificate scheduling: after the first check, the ratio kappa = cert_rel / ||grad F||
   // of the last check predicts cert_rel from the gradient norm the solver keeps on the device.
   double kappa = 0.0;
+  // A predicted check runs once kappa ||grad F|| <= margin * tol: below 1, the iterations run a
+  // little longer so that the check more often passes at once (the grouped driver, where an
+  // iteration is cheap next to a certificate).
+  double margin = 1.0;
   int init_used = 0;
   bool narrow = false, certified = false, done = false;
   double narrow_best = INFINITY;
@@ -251,9 +258,10 @@ constexpr int CERT_POLL = 5, CERT_MIN_GAP = 5;
 
 static bool cert_due(const SolveJob& j, const SolverState& st, double tol) {
   if (j.every <= 0 || j.c->lk || st.iter <= 0 || st.iter == j.last_cert_iter) return false;
-  if (j.narrow || !(j.kappa > 0.0)) return st.iter % j.every == 0;
+  // Fixed schedule: every `every` iterations from the last check (the first after `every`).
+  if (j.narrow || !(j.kappa > 0.0)) return st.iter >= std::max(0, j.last_cert_iter) + j.every;
   const int since = st.iter - j.last_cert_iter;
-  return (since >= CERT_MIN_GAP && j.kappa * sqrt(fmax(st.gg, 0.0)) <= tol) || since >= 2 * j.every;
+  return (since >= CERT_MIN_GAP && j.kappa * sqrt(fmax(st.gg, 0.0)) <= j.margin * tol) || since >= 2 * j.every;
 }
 
 // Decisions between iterations on the state j.st (read by the caller): the certificate when
@@ -597,6 +605,7 @@ rpca_status solve_jobs(rpca_ctx* const* ctx, float* const* U, float* const* V, r
   return RPCA_OK;
 }
 
+
 }  // namespace rpca
 
 extern "C" rpca_status rpca_perp_directions(rpca_ctx* c, int qmax, float* U, int64_t ldu, float* V, int64_t ldv,
@@ -801,4 +810,334 @@ rpca_status solve_jobs_rounds(rpca_ctx* const* ctx, float* const* U, float* cons
   return RPCA_OK;
 }
 
+// ---- The grouped form ----------------------------------------------------------------------
+// Every instance is started (initialisation and first direction, host threads in parallel);
+// then the group stream runs chunks of GROUP_ROUNDS trial rounds, each round one fused-pass
+// launch per group of instances with the same instantiation and block size and one launch
+// each of the assembly + line-search step, the inner products + scalar part and the direction
+// over all listed instances (solver_group_round), and ends with the gather of the listed
+// instances' scalars.  Between chunks the host takes each listed instance's decisions as a
+// single solve does: an instance whose certificate is due, or that stopped, leaves the list
+// and a worker thread evaluates its certificate on the instance's own stream while the
+// others keep iterating; it rejoins (or is finished) when the worker is done.  An instance
+// that stops inside a chunk idles there (its kernels return at once); it leaves the list at
+// the chunk's end.  An instance's trials run the same kernels' arithmetic on the same grids as
+// its own iteration graph, so its trajectory does not depend on the others; its decisions
+// come after whole chunks of its own trials.
+constexpr int GROUP_ROUNDS = 5;
+constexpr double GROUP_CERT_MARGIN = 0.5;
+
+struct GroupCache {
+  int count = 0;
+  cudaStream_t gs = nullptr;
+  cudaEvent_t chunk_ev = nullptr;
+  std::vector<cudaEvent_t> resume;  // per instance, on its own stream
+  unsigned char* d_rec = nullptr;
+  unsigned char* h_rec = nullptr;   // pinned
+  int* d_idx = nullptr;
+  int* h_idx = nullptr;             // pinned
+  size_t idx_cap = 0;
+  double* d_out = nullptr;
+  double* h_out = nullptr;          // pinned
+};
+
+void group_free(GroupCache* g) {
+  if (!g) return;
+  if (g->gs) cudaStreamSynchronize(g->gs);
+  for (cudaEvent_t e : g->resume)
+    if (e) cudaEventDestroy(e);
+  if (g->chunk_ev) cudaEventDestroy(g->chunk_ev);
+  if (g->gs) cudaStreamDestroy(g->gs);
+  dev_free(g->d_rec);
+  dev_free(g->d_idx);
+  dev_free(g->d_out);
+  host_pinned_free(g->h_rec);
+  host_pinned_free(g->h_idx);
+  host_pinned_free(g->h_out);
+  delete g;
+}
+
+static rpca_status group_setup(GroupCache* g, rpca_ctx* c0, int count) {
+  if (g->count == count) return RPCA_OK;
+  if (g->count != 0) return set_err(c0, RPCA_EUNSUPPORTED, "batch size changed");
+  auto fail = [&](cudaError_t e, const char* what) { return cuda_err(c0, e, what); };
+  cudaError_t e;
+  if ((e = cudaStreamCreateWithFlags(&g->gs, cudaStreamNonBlocking)) != cudaSuccess) return fail(e, "stream");
+  if ((e = cudaEventCreateWithFlags(&g->chunk_ev, cudaEventDisableTiming)) != cudaSuccess) return fail(e, "event");
+  g->resume.assign(count, nullptr);
+  for (int i = 0; i < count; ++i)
+    if ((e = cudaEventCreateWithFlags(&g->resume[i], cudaEventDisableTiming)) != cudaSuccess) return fail(e, "event");
+  const size_t rb = solver_group_stride() * (size_t)count;
+  if ((e = dev_alloc(&g->d_rec, rb)) != cudaSuccess) return fail(e, "records");
+  if ((e = host_pinned_alloc(&g->h_rec, rb)) != cudaSuccess) return fail(e, "records");
+  // Lists: per fused-pass group its ids and offsets (2 c_g + 1 entries), then the ids and three
+  // offset arrays of the other launches (4 n + 3): at most 7 count + 3 entries (a group per
+  // instance at most).
+  g->idx_cap = 7 * (size_t)count + 3;
+  if ((e = dev_alloc(&g->d_idx, sizeof(int) * g->idx_cap)) != cudaSuccess) return fail(e, "lists");
+  if ((e = host_pinned_alloc(&g->h_idx, sizeof(int) * g->idx_cap)) != cudaSuccess) return fail(e, "lists");
+  if ((e = dev_alloc(&g->d_out, sizeof(double) * 6 * count)) != cudaSuccess) return fail(e, "scalars");
+  if ((e = host_pinned_alloc(&g->h_out, sizeof(double) * 6 * count)) != cudaSuccess) return fail(e, "scalars");
+  g->count = count;
+  return RPCA_OK;
+}
+
+// Whether the grouped form can run this batch (every instance eligible, one device).
+bool group_eligible(rpca_ctx* const* ctx, int count) {
+  for (int i = 0; i < count; ++i)
+    if (!solver_group_eligible(ctx[i]) || ctx[i]->device != ctx[0]->device) return false;
+  return true;
+}
+
+rpca_status solve_jobs_grouped(rpca_ctx* const* ctx, float* const* U, float* const* V, rpca_result* res, int count,
+                               rpca_status* status, int threads, GroupCache** cache) {
+  const int device = ctx[0]->device;
+  if (!*cache) *cache = new GroupCache();
+  GroupCache* g = *cache;
+  rpca_status s = group_setup(g, ctx[0], count);
+  if (s != RPCA_OK) {
+    for (int i = 0; i < count; ++i) status[i] = s;
+    return s;
+  }
+  std::vector<SolveJob> jobs(count);
+  std::vector<int> all(count);
+  for (int i = 0; i < count; ++i) {
+    all[i] = i;
+    ctx[i]->no_iter_graph = true;
+  }
+  parallel_items(all, threads, device, [&](int i) { status[i] = job_start(jobs[i], ctx[i], U[i], V[i]); });
+  for (SolveJob& j : jobs) j.margin = GROUP_CERT_MARGIN;
+  // Records, and the group stream ordered after every start.
+  const size_t stride = solver_group_stride();
+  std::vector<GroupMember> mem(count);
+  std::vector<char> live(count, 0);  // 1: in the lists; 0: with a worker or finished
+  std::vector<char> finished(count, 0);
+  for (int i = 0; i < count; ++i) {
+    if (status[i] == RPCA_OK) status[i] = solver_group_member(ctx[i], g->h_rec + stride * i, &mem[i]);
+    if (status[i] != RPCA_OK) {
+      finished[i] = 1;
+      continue;
+    }
+    live[i] = 1;
+    cudaEventRecord(g->resume[i], ctx[i]->stream);
+    cudaStreamWaitEvent(g->gs, g->resume[i], 0);
+  }
+  // Fused-pass groups: instances with the same grouped instantiation and block size.
+  std::vector<std::pair<const void*, int>> gkey;
+  std::vector<size_t> gsmem;
+  std::vector<int> gof(count, -1);
+  for (int i = 0; i < count; ++i) {
+    if (!live[i]) continue;
+    const std::pair<const void*, int> key{mem[i].fg_fn, mem[i].fg_threads};
+    size_t q = 0;
+    while (q < gkey.size() && gkey[q] != key) ++q;
+    if (q == gkey.size()) {
+      gkey.push_back(key);
+      gsmem.push_back(0);
+    }
+    gof[i] = (int)q;
+    gsmem[q] = std::max(gsmem[q], mem[i].fg_smem);
+  }
+  for (size_t q = 0; q < gkey.size(); ++q)
+    if (!allow_smem(gkey[q].first, gsmem[q])) {
+      for (int i = 0; i < count; ++i)
+        if (live[i]) status[i] = set_err(ctx[i], RPCA_ECUDA, "shared memory of the grouped fused pass");
+      return RPCA_ECUDA;
+    }
+  cudaError_t e = cudaMemcpyAsync(g->d_rec, g->h_rec, stride * count, cudaMemcpyHostToDevice, g->gs);
+  if (e != cudaSuccess) {
+    for (int i = 0; i < count; ++i)
+      if (live[i]) status[i] = cuda_err(ctx[i], e, "records");
+    return status[0];
+  }
+
+  // Worker threads for the decisions (certificates) of instances that left the lists.
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<int> work, done_q;
+  bool quit = false;
+  const int nworkers = std::max(1, std::min(threads, count));
+  std::vector<std::thread> workers;
+  workers.reserve(nworkers);
+  for (int t = 0; t < nworkers; ++t)
+    workers.emplace_back([&] {
+      cudaSetDevice(device);
+      while (true) {
+        int i;
+        {
+          std::unique_lock<std::mutex> lk(mu);
+          cv_work.wait(lk, [&] { return quit || !work.empty(); });
+          if (work.empty()) return;
+          i = work.front();
+          work.pop_front();
+        }
+        bool again = false;
+        status[i] = job_decide(jobs[i], &again);
+        if (status[i] == RPCA_OK && jobs[i].done && jobs[i].st.active)
+          status[i] = solver_deactivate(ctx[i], ctx[i]->stream);
+        cudaEventRecord(g->resume[i], ctx[i]->stream);
+        {
+          std::lock_guard<std::mutex> lk(mu);
+          done_q.push_back(i);
+        }
+        cv_done.notify_one();
+      }
+    });
+
+  int64_t launches = 0;
+  int pending = 0;
+  std::vector<int> list;        // the listed instances of the current chunk
+  bool lists_stale = true;
+  std::vector<GroupFgList> fgl;
+  GroupRound R{};
+  rpca_status err = RPCA_OK;
+  while (err == RPCA_OK) {
+    // Decisions that finished: rejoin or finish.  With no instance left to iterate, wait for
+    // one; with none pending either, the batch is done.
+    {
+      std::unique_lock<std::mutex> lk(mu);
+      if (std::none_of(live.begin(), live.end(), [](char v) { return v != 0; })) {
+        if (pending == 0) break;
+        cv_done.wait(lk, [&] { return !done_q.empty(); });
+      }
+      while (!done_q.empty()) {
+        const int i = done_q.front();
+        done_q.pop_front();
+        --pending;
+        if (status[i] != RPCA_OK || jobs[i].done) {
+          finished[i] = 1;
+        } else {
+          live[i] = 1;
+          cudaStreamWaitEvent(g->gs, g->resume[i], 0);
+        }
+        lists_stale = true;
+      }
+    }
+    if (lists_stale) {
+      list.clear();
+      for (int i = 0; i < count; ++i)
+        if (live[i]) list.push_back(i);
+      if (list.empty()) continue;
+      // Lay out the lists in h_idx: per group ids, offsets; then ids and the three offsets.
+      int* h = g->h_idx;
+      size_t pos = 0;
+      fgl.assign(gkey.size(), GroupFgList{});
+      std::vector<size_t> gpos(gkey.size());
+      for (size_t q = 0; q < gkey.size(); ++q) {
+        int cnt = 0;
+        for (int i : list) cnt += gof[i] == (int)q;
+        GroupFgList& F = fgl[q];
+        F.fn = gkey[q].first;
+        F.threads = gkey[q].second;
+        F.smem = gsmem[q];
+        F.cnt = cnt;
+        F.ids = g->d_idx + pos;
+        F.off = g->d_idx + pos + cnt;
+        int* ids = h + pos;
+        int* off = h + pos + cnt;
+        int c = 0, b = 0;
+        off[0] = 0;
+        for (int i : list)
+          if (gof[i] == (int)q) {
+            ids[c] = i;
+            b += mem[i].fg_blocks;
+            off[++c] = b;
+          }
+        F.blocks = b;
+        pos += 2 * (size_t)cnt + 1;
+      }
+      const int n = (int)list.size();
+      int* ids = h + pos;
+      int* fo = ids + n;
+      int* dof = fo + n + 1;
+      int* rof = dof + n + 1;
+      fo[0] = dof[0] = rof[0] = 0;
+      for (int q = 0; q < n; ++q) {
+        const int i = list[q];
+        ids[q] = i;
+        fo[q + 1] = fo[q] + mem[i].fin_blocks;
+        dof[q + 1] = dof[q] + mem[i].dots_blocks;
+        rof[q + 1] = rof[q] + mem[i].dir_blocks;
+      }
+      R.rec = g->d_rec;
+      R.stride = stride;
+      R.fg = fgl.data();
+      R.nfg = (int)fgl.size();
+      R.cnt = n;
+      R.ids = g->d_idx + pos;
+      R.fin_off = R.ids + n;
+      R.dots_off = R.fin_off + n + 1;
+      R.dir_off = R.dots_off + n + 1;
+      R.fin_blocks = fo[n];
+      R.dots_blocks = dof[n];
+      R.dir_blocks = rof[n];
+      R.mcap = mem[list[0]].mcap;
+      pos += (size_t)n + 3 * ((size_t)n + 1);
+      if ((e = cudaMemcpyAsync(g->d_idx, h, sizeof(int) * pos, cudaMemcpyHostToDevice, g->gs)) != cudaSuccess) {
+        err = RPCA_ECUDA;
+        break;
+      }
+      lists_stale = false;
+    }
+    // One chunk of rounds, then the listed instances' scalars.
+    for (int r = 0; r < GROUP_ROUNDS && e == cudaSuccess; ++r) e = solver_group_round(R, g->gs, &launches);
+    if (e == cudaSuccess) e = solver_group_gather(g->d_rec, R.ids, R.cnt, g->d_out, g->gs);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(g->h_out, g->d_out, sizeof(double) * 6 * R.cnt, cudaMemcpyDeviceToHost, g->gs);
+    if (e == cudaSuccess) e = cudaEventRecord(g->chunk_ev, g->gs);
+    if (e == cudaSuccess) e = cudaEventSynchronize(g->chunk_ev);
+    if (e != cudaSuccess) {
+      err = RPCA_ECUDA;
+      break;
+    }
+    launches += 1;
+    for (int q = 0; q < (int)list.size(); ++q) {
+      const int i = list[q];
+      SolveJob& j = jobs[i];
+      const double* o = g->h_out + 6 * (size_t)q;
+      j.st.active = (int)o[0];
+      j.st.iter = (int)o[1];
+      j.st.gg = o[2];
+      j.st.f = o[3];
+      j.st.stop = (int)o[4];
+      j.st.evals = (int)o[5];
+      const bool stop = !j.st.active || j.st.iter >= ctx[i]->opt.max_iter - j.iter_base;
+      if (stop || cert_due(j, j.st, ctx[i]->opt.cert_tol) || ctx[i]->opt.timeout_s > 0) {
+        live[i] = 0;
+        lists_stale = true;
+        {
+          std::lock_guard<std::mutex> lk(mu);
+          work.push_back(i);
+          ++pending;
+        }
+        cv_work.notify_one();
+      }
+    }
+  }
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    quit = true;
+  }
+  cv_work.notify_all();
+  for (auto& th : workers) th.join();
+  count_launches(ctx[0], launches);
+  if (err != RPCA_OK) {
+    for (int i = 0; i < count; ++i) ctx[i]->no_iter_graph = false;
+    for (int i = 0; i < count; ++i)
+      if (status[i] == RPCA_OK) status[i] = cuda_err(ctx[i], e, "grouped iteration");
+    return status[0];
+  }
+  // Later solves of these contexts capture their own iteration graph again.
+  for (int i = 0; i < count; ++i) ctx[i]->no_iter_graph = false;
+  // The results, ordered after the last chunk.
+  cudaEventRecord(g->chunk_ev, g->gs);
+  std::vector<int> fin;
+  for (int i = 0; i < count; ++i)
+    if (status[i] == RPCA_OK) fin.push_back(i);
+  parallel_items(fin, threads, device, [&](int i) {
+    cudaStreamWaitEvent(ctx[i]->stream, g->chunk_ev, 0);
+    status[i] = job_finish(jobs[i], res ? &res[i] : nullptr);
+  });
+  return RPCA_OK;
+}
 }  // namespace rpca

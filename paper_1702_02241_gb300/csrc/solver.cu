@@ -33,6 +33,7 @@
 
 #include "common.cuh"
 #include "ctx.h"
+#include "fg_kernel.cuh"
 #include "fin.cuh"
 #include "solver.h"
 
@@ -240,25 +241,30 @@ __global__ void ls_step_kernel(SolverState* st, cudaGraphConditionalHandle h, in
 // which ends the graph's while loop.
 // Four CTAs per SM (64 registers): the assembly needs few registers, the single thread that
 // takes the line-search step many, and the more of the grid one wave holds the better.
-__global__ void __launch_bounds__(256, 4) finalize_ls_kernel(FinArgs a, SolverState* st, cudaGraphConditionalHandle h,
-                                                          int in_graph, unsigned int* ticket) {
+// Block bx of a grid of gx blocks.
+__device__ __forceinline__ void finalize_ls_body(const FinArgs& a, SolverState* st, cudaGraphConditionalHandle h,
+                                                 int in_graph, unsigned int* ticket, unsigned bx, unsigned gx) {
   __shared__ bool is_last;
   if (a.gate != nullptr && *a.gate == 0) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) ls_step_body(st, h, in_graph);
+    if (bx == 0 && threadIdx.x == 0) ls_step_body(st, h, in_graph);
     return;
   }
-  finalize_body(a);
+  finalize_body(a, bx);
   __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) is_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  if (threadIdx.x == 0) is_last = atomicAdd(ticket, 1u) == gx - 1;
   __syncthreads();
   if (!is_last) return;
   __threadfence();
-  finalize_reduce_body(a, (int)gridDim.x);
+  finalize_reduce_body(a, (int)gx);
   if (threadIdx.x == 0) {
     *ticket = 0u;
     ls_step_body(st, h, in_graph);
   }
+}
+__global__ void __launch_bounds__(256, 4) finalize_ls_kernel(FinArgs a, SolverState* st, cudaGraphConditionalHandle h,
+                                                          int in_graph, unsigned int* ticket) {
+  finalize_ls_body(a, st, h, in_graph, ticket, blockIdx.x, gridDim.x);
 }
 
 cudaError_t launch_finalize_ls(const FinArgs& f, int grid, const FgLaunch& L, cudaStream_t stream) {
@@ -617,8 +623,9 @@ __global__ void __launch_bounds__(256) lbfgs_dots_kernel(SolverArgs a) {
 // taken from registers.  The line search's phi'(0) = g . d is formed from the Gram table by
 // the scalar part of the iteration.  Two elements per thread (one for memory caps above 10)
 // with every load in flight; the last block (ticket) clears acc_flag.
+// Block bx of a grid of gx blocks.
 template <int MCAP>
-__global__ void __launch_bounds__(256, MCAP <= 10 ? 2 : 1) lbfgs_direction_kernel(SolverArgs a) {
+__device__ __forceinline__ void direction_body(const SolverArgs& a, const int bx, const int gx) {
   constexpr int NS = MCAP + 1;
   __shared__ float cs[NS], cy[NS];
   __shared__ float cg;
@@ -626,7 +633,7 @@ __global__ void __launch_bounds__(256, MCAP <= 10 ? 2 : 1) lbfgs_direction_kerne
   const int acc = st->acc_flag, active = st->active, pending = st->dir_pending;
   // In the iteration graph this is the last kernel of a trial: its first thread sets the
   // loop condition from the state the scalar part left (final by now).
-  if (a.in_graph && blockIdx.x == 0 && threadIdx.x == 0) {
+  if (a.in_graph && bx == 0 && threadIdx.x == 0) {
     const int budget = st->loop_budget - 1;
     st->loop_budget = budget;
     cudaGraphSetConditional(a.loop_h, (active && st->iter < st->target && budget > 0) ? 1u : 0u);
@@ -647,8 +654,8 @@ __global__ void __launch_bounds__(256, MCAP <= 10 ? 2 : 1) lbfgs_direction_kerne
   // vectors are padded to a multiple of 4 elements); two for memory caps up to 10.
   constexpr int EPT = NS <= 11 ? 2 : 1;
   const int64_t N = a.N;
-  for (int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * EPT; e < N;
-       e += (int64_t)gridDim.x * blockDim.x * EPT) {
+  for (int64_t e = ((int64_t)bx * blockDim.x + threadIdx.x) * EPT; e < N;
+       e += (int64_t)gx * blockDim.x * EPT) {
     float go[EPT], gn[EPT], xo[EPT], xn[EPT], sn[EPT], yn[EPT], sv[NS][EPT], yv[NS][EPT];
     vec_load<EPT>(go, a.g + e, true);
     vec_load<EPT>(xo, a.x + e, acc);
@@ -692,11 +699,16 @@ __global__ void __launch_bounds__(256, MCAP <= 10 ? 2 : 1) lbfgs_direction_kerne
   }
   // Every block has read the flags by the time the last one arrives.
   __syncthreads();
-  if (threadIdx.x == 0 && atomicAdd(a.counter + 2 + DOTS_MAX_GRP, 1u) == gridDim.x - 1) {
+  if (threadIdx.x == 0 && atomicAdd(a.counter + 2 + DOTS_MAX_GRP, 1u) == (unsigned)gx - 1) {
     a.counter[2 + DOTS_MAX_GRP] = 0u;
     st->acc_flag = 0;
     st->dir_pending = 0;
   }
+}
+
+template <int MCAP>
+__global__ void __launch_bounds__(256, MCAP <= 10 ? 2 : 1) lbfgs_direction_kernel(SolverArgs a) {
+  direction_body<MCAP>(a, blockIdx.x, gridDim.x);
 }
 
 // The iteration target of the next graph launch: `count` iterations from the current one, in
@@ -779,8 +791,9 @@ struct Dots1Shape {
   static constexpr int H = (NS + ROWS - 1) / ROWS;    // slots per row (at most)
   static constexpr int C = ((5 * H + 7) + 7) & ~7;    // sums per thread, padded to a multiple of 8
 };
+// Block (bx, by) of a grid of gx x gy blocks.
 template <int MCAP>
-__global__ void __launch_bounds__(256, 2) lbfgs_dots1_kernel(SolverArgs a) {
+__device__ __forceinline__ void dots1_body(const SolverArgs& a, const int bx, const int by, const int gx, const int gy) {
   constexpr int NS = MCAP + 1;
   constexpr int NV = 5 * NS + 7;
   static_assert(NV <= 64, "too many sums for the one-pass kernel");
@@ -793,7 +806,7 @@ __global__ void __launch_bounds__(256, 2) lbfgs_dots1_kernel(SolverArgs a) {
   __shared__ bool is_last;
   SolverState* st = a.st;
   if (!st->active || st->ls.state == LS_RUNNING) return;  // nothing to do while a search runs
-  const int row = blockIdx.y;
+  const int row = by;
   const int j0 = row * H, nj = min(H, NS - j0);  // this row's slots [j0, j0 + nj)
   const bool own_new = row == 0;                 // row 0 also sums the new pair and g
   const bool accepted = st->ls.state == LS_ACCEPTED;
@@ -809,8 +822,8 @@ __global__ void __launch_bounds__(256, 2) lbfgs_dots1_kernel(SolverArgs a) {
   // DOTS_VEC consecutive elements per thread and step, loaded as one vector each (the vectors
   // are padded to a multiple of 4 elements): the pass reads from L2, where the number of
   // requests in flight, not the bytes, sets the rate.
-  for (int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * DOTS_VEC; e < N;
-       e += (int64_t)gridDim.x * blockDim.x * DOTS_VEC) {
+  for (int64_t e = ((int64_t)bx * blockDim.x + threadIdx.x) * DOTS_VEC; e < N;
+       e += (int64_t)gx * blockDim.x * DOTS_VEC) {
     float sv[H][DOTS_VEC], yv[H][DOTS_VEC];
 #pragma unroll
     for (int jj = 0; jj < H; ++jj) {
@@ -863,16 +876,16 @@ __global__ void __launch_bounds__(256, 2) lbfgs_dots1_kernel(SolverArgs a) {
     const int v = u < 5 * nj ? 5 * j0 + u : 5 * NS + (u - 5 * nj);
     ff2 t = ff_make(red[0][ul]);
     for (int q = 1; q < (int)(blockDim.x >> 5); ++q) t = ff_add(t, ff_make(red[q][ul]));
-    ff_store(&a.blk[(int64_t)blockIdx.x * 64 + v], t);
+    ff_store(&a.blk[(int64_t)bx * 64 + v], t);
   }
   // Two-level ticket tree over the columns of blocks (both rows of a column write disjoint
   // sums into its 64 slots): the last of the group's blocks sums the group, the last group
   // sums the groups.
-  const int nb = (int)gridDim.x, grp = blockIdx.x / DOTS_GRP, ngrp = (nb + DOTS_GRP - 1) / DOTS_GRP;
+  const int nb = gx, grp = bx / DOTS_GRP, ngrp = (nb + DOTS_GRP - 1) / DOTS_GRP;
   const int gsize = min(DOTS_GRP, nb - grp * DOTS_GRP);
   __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) is_last = atomicAdd(a.counter + 1 + grp, 1u) == (unsigned)(gsize * (int)gridDim.y) - 1;
+  if (threadIdx.x == 0) is_last = atomicAdd(a.counter + 1 + grp, 1u) == (unsigned)(gsize * gy) - 1;
   __syncthreads();
   if (!is_last) return;
   __threadfence();
@@ -905,6 +918,11 @@ __global__ void __launch_bounds__(256, 2) lbfgs_dots1_kernel(SolverArgs a) {
   __syncthreads();
   if (threadIdx.x == 0) *a.counter = 0u;
   scalar_tail<NS>(st, fin, finf);
+}
+
+template <int MCAP>
+__global__ void __launch_bounds__(256, 2) lbfgs_dots1_kernel(SolverArgs a) {
+  dots1_body<MCAP>(a, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y);
 }
 
 template <int MCAP>
@@ -1054,10 +1072,13 @@ static cudaError_t capture_iteration(rpca_ctx* c, cudaStream_t cap) {
   return e;
 }
 
+static rpca_status capture_solver_graph(rpca_ctx* c);
+
 static rpca_status ensure_solver(rpca_ctx* c) {
   const int mcap = mem_cap(c->opt.lbfgs_mem);
   const FgPlan* plan = c->solve_plan ? c->solve_plan : &c->fg_plan;
-  if (c->sol && c->sol->mcap == mcap && c->sol->plan == plan) return RPCA_OK;
+  if (c->sol && c->sol->mcap == mcap && c->sol->plan == plan)
+    return c->sol->exec || c->no_iter_graph ? RPCA_OK : capture_solver_graph(c);
   free_solver(c);
   SolverBuffers* b = new SolverBuffers();
   c->sol = b;
@@ -1091,7 +1112,12 @@ static rpca_status ensure_solver(rpca_ctx* c) {
   SOL_CUDA(cudaMemsetAsync(b->counter, 0, sizeof(unsigned int) * (1 + DOTS_MAX_GRP + 3), c->stream));
   SOL_CUDA(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
   SOL_CUDA(cudaStreamCreateWithFlags(&b->cap2, cudaStreamNonBlocking));
+  // The grouped iteration of the batched form launches this instance's trials itself.
+  return c->no_iter_graph ? RPCA_OK : capture_solver_graph(c);
+}
 
+static rpca_status capture_solver_graph(rpca_ctx* c) {
+  SolverBuffers* b = c->sol;
   // RPCA_SOLVER_GRAPH=0 runs the same kernels from a host loop (one synchronisation per
   // line-search trial), for per-kernel profilers that do not see inside conditional graphs.
   if (const char* e = getenv("RPCA_SOLVER_GRAPH"))
@@ -1231,5 +1257,140 @@ rpca_status solver_iterations(rpca_ctx* c, int count) {
 }
 
 const float* solver_point(rpca_ctx* c) { return c->sol ? c->sol->x : nullptr; }
+
+// ---------------------------------------------------------------------------------------------
+// Grouped iteration.  Each instance's record holds what its own launches would pass: the
+// fused pass's tensor maps and arguments (FgInst, first, so that fg_group_kernel finds it at
+// the record's start), the solver's arguments, the assembly's arguments and ticket, and its
+// grid sizes (those of its own launches, so that a grouped trial sums in the same order).
+struct alignas(64) GroupRec {
+  FgInst fg;
+  SolverArgs a;
+  FinArgs f;
+  unsigned int* ticket;
+  int fin_grid, dots_gx, dir_grid;
+};
+
+// Three CTAs per SM: with the arguments read from memory instead of the constant bank the
+// line-search step needs more than 64 registers.
+__global__ void __launch_bounds__(256, 3) finalize_ls_group_kernel(const GroupRec* __restrict__ rec,
+                                                                const int* __restrict__ ids,
+                                                                const int* __restrict__ off, int cnt) {
+  __shared__ FinArgs sf;
+  const int q = group_find(off, cnt, (int)blockIdx.x);
+  const GroupRec* r = rec + __ldg(ids + q);
+  args_to_shared(&sf, &r->f);
+  __syncthreads();
+  finalize_ls_body(sf, r->a.st, 0, 0, r->ticket, blockIdx.x - (unsigned)__ldg(off + q), (unsigned)r->fin_grid);
+}
+
+template <int MCAP>
+__global__ void __launch_bounds__(256, 2) lbfgs_dots1_group_kernel(const GroupRec* __restrict__ rec,
+                                                                 const int* __restrict__ ids,
+                                                                 const int* __restrict__ off, int cnt) {
+  constexpr int rows = Dots1Shape<MCAP + 1>::ROWS;
+  __shared__ SolverArgs sa;
+  const int q = group_find(off, cnt, (int)blockIdx.x);
+  const GroupRec* r = rec + __ldg(ids + q);
+  args_to_shared(&sa, &r->a);
+  __syncthreads();
+  const int local = (int)blockIdx.x - __ldg(off + q), gx = r->dots_gx;
+  dots1_body<MCAP>(sa, local % gx, local / gx, gx, rows);
+}
+
+template <int MCAP>
+__global__ void __launch_bounds__(256, MCAP <= 10 ? 2 : 1) lbfgs_direction_group_kernel(
+    const GroupRec* __restrict__ rec, const int* __restrict__ ids, const int* __restrict__ off, int cnt) {
+  const int q = group_find(off, cnt, (int)blockIdx.x);
+  const GroupRec* r = rec + __ldg(ids + q);
+  direction_body<MCAP>(r->a, (int)blockIdx.x - __ldg(off + q), r->dir_grid);
+}
+
+__global__ void gather_group_kernel(const GroupRec* __restrict__ rec, const int* __restrict__ ids, int cnt,
+                                    double* out) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < cnt; q += gridDim.x * blockDim.x) {
+    const SolverState* st = rec[ids[q]].a.st;
+    double* o = out + 6 * (size_t)q;
+    o[0] = st->active;
+    o[1] = st->iter;
+    o[2] = st->gg;
+    o[3] = st->f;
+    o[4] = st->stop;
+    o[5] = st->evals;
+  }
+}
+
+size_t solver_group_stride() { return sizeof(GroupRec); }
+
+bool solver_group_eligible(rpca_ctx* c) {
+  const FgPlan& P = c->fg_plan;
+  return c->lk == nullptr && c->xq_dt == 0 && c->bits == nullptr && P.valid && !P.large && !P.mma && !P.tc &&
+         !P.masked && P.xt == FG_X_F32 && P.same && P.var != nullptr && P.var->group != nullptr &&
+         mem_cap(c->opt.lbfgs_mem) <= 10 && P.smem + sizeof(FgArgs) + 256 <= c->max_smem;  // + its static shared
+}
+
+rpca_status solver_group_member(rpca_ctx* c, void* rec_host, GroupMember* m) {
+  SolverBuffers* b = c->sol;
+  if (!b || !solver_group_eligible(c) || b->plan != &c->fg_plan)
+    return set_err(c, RPCA_EUNSUPPORTED, "this solve cannot join the grouped iteration");
+  GroupRec* r = static_cast<GroupRec*>(rec_host);
+  memset(static_cast<void*>(r), 0, sizeof *r);
+  const FgPlan& P = *b->plan;
+  const FgLaunch L = trial_launch(c);
+  fg_launch_args(c, P, L, &r->fg.a, &r->f);
+  r->fg.tmX = P.tmX;
+  r->fg.tmM = P.tmM;
+  r->a = solver_args(c);
+  r->ticket = L.ls_ticket;
+  r->fin_grid = P.fin_grid;
+  // The grids of launch_update / launch_direction for this instance.
+  const int rows = b->mcap == 4 ? Dots1Shape<5>::ROWS : Dots1Shape<11>::ROWS;
+  r->dots_gx = rows == 2 ? std::max(1, b->grid / 2) : b->grid;
+  r->dir_grid = (int)std::max<int64_t>(
+      1, std::min<int64_t>(std::min<int64_t>((b->N + 511) / 512, b->grid), (int64_t)DOTS_GRP * DOTS_MAX_GRP));
+  m->fg_fn = P.var->group;
+  m->fg_threads = P.threads;
+  m->fg_smem = P.smem;
+  m->fg_blocks = P.nrb * P.ncs;
+  m->fin_blocks = P.fin_grid;
+  m->dots_blocks = r->dots_gx * rows;
+  m->dir_blocks = r->dir_grid;
+  m->mcap = b->mcap;
+  return RPCA_OK;
+}
+
+cudaError_t solver_group_round(const GroupRound& R, cudaStream_t s, int64_t* launches) {
+  const unsigned char* rec = static_cast<const unsigned char*>(R.rec);
+  size_t stride = R.stride;
+  for (int g = 0; g < R.nfg; ++g) {
+    const GroupFgList& F = R.fg[g];
+    if (F.cnt <= 0) continue;
+    const int* ids = F.ids;
+    const int* off = F.off;
+    int cnt = F.cnt;
+    void* args[] = {(void*)&rec, (void*)&stride, (void*)&ids, (void*)&off, (void*)&cnt};
+    cudaError_t e = cudaLaunchKernel(F.fn, dim3(F.blocks), dim3(F.threads), args, F.smem, s);
+    if (e != cudaSuccess) return e;
+    ++*launches;
+  }
+  if (R.cnt <= 0) return cudaSuccess;
+  const GroupRec* gr = reinterpret_cast<const GroupRec*>(rec);
+  finalize_ls_group_kernel<<<R.fin_blocks, 256, 0, s>>>(gr, R.ids, R.fin_off, R.cnt);
+  if (R.mcap == 4) {
+    lbfgs_dots1_group_kernel<4><<<R.dots_blocks, 256, 0, s>>>(gr, R.ids, R.dots_off, R.cnt);
+    lbfgs_direction_group_kernel<4><<<R.dir_blocks, 256, 0, s>>>(gr, R.ids, R.dir_off, R.cnt);
+  } else {
+    lbfgs_dots1_group_kernel<10><<<R.dots_blocks, 256, 0, s>>>(gr, R.ids, R.dots_off, R.cnt);
+    lbfgs_direction_group_kernel<10><<<R.dir_blocks, 256, 0, s>>>(gr, R.ids, R.dir_off, R.cnt);
+  }
+  *launches += 3;
+  return cudaGetLastError();
+}
+
+cudaError_t solver_group_gather(const void* rec, const int* ids, int cnt, double* out, cudaStream_t s) {
+  if (cnt <= 0) return cudaSuccess;
+  gather_group_kernel<<<(cnt + 127) / 128, 128, 0, s>>>(static_cast<const GroupRec*>(rec), ids, cnt, out);
+  return cudaGetLastError();
+}
 
 }  // namespace rpca

@@ -1,6 +1,10 @@
 // Device-resident state of the L-BFGS solver (read by the host between graph launches).
 #pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
+
+#include "../../include/rpca.h"
 
 namespace rpca {
 
@@ -65,5 +69,55 @@ struct SolverState {
   int tlog_n;
   double tlog[SOLVER_TLOG][7];
 };
+
+// ---- Grouped iteration: the line-search trials of many instances in shared launches ----
+// A round advances every listed instance by one trial, as one pass of the iteration graph's
+// body does for one instance: the fused pass (one launch per group of instances that share
+// its instantiation and block size), then one launch each of the assembly with the
+// line-search step, the inner products with the scalar part, and the direction, over all
+// listed instances.  An instance's kernels read its record (tensor maps, arguments, its own
+// solver buffers and tickets), written once per solve.
+
+// Launch sizes of one instance in the grouped form.
+struct GroupMember {
+  const void* fg_fn = nullptr;  // grouped fused-pass instantiation
+  int fg_threads = 0;
+  size_t fg_smem = 0;
+  int fg_blocks = 0, fin_blocks = 0, dots_blocks = 0, dir_blocks = 0;
+  int mcap = 0;
+};
+// One fused-pass launch: cnt instances ids[] with block offsets off[] (cnt + 1 entries).
+struct GroupFgList {
+  const void* fn;
+  int threads;
+  size_t smem;
+  int blocks, cnt;
+  const int* ids;
+  const int* off;
+};
+struct GroupRound {
+  const void* rec;  // device records, `stride` bytes apart
+  size_t stride;
+  const GroupFgList* fg;
+  int nfg;
+  int cnt;  // the listed instances of the other three launches and their block offsets
+  const int* ids;
+  const int* fin_off;
+  const int* dots_off;
+  const int* dir_off;
+  int fin_blocks, dots_blocks, dir_blocks, mcap;
+};
+size_t solver_group_stride();
+// Whether a context's solve can take part (float32 X, unmasked, fused-kernel plan with a
+// grouped instantiation, memory cap <= 10); checked before the solve starts.
+bool solver_group_eligible(rpca_ctx* c);
+// Writes this context's record (host memory, solver_group_stride() bytes, 64-byte aligned)
+// and launch sizes; the solver must be prepared (its first direction launched).
+rpca_status solver_group_member(rpca_ctx* c, void* rec_host, GroupMember* m);
+// Launches one round on s; the kernel launches it made are added to *launches.
+cudaError_t solver_group_round(const GroupRound& r, cudaStream_t s, int64_t* launches);
+// The host's scalars of the listed instances into out[6 q ..]: active, iteration, ||g||^2, F,
+// stop reason, evaluations.
+cudaError_t solver_group_gather(const void* rec, const int* ids, int cnt, double* out, cudaStream_t s);
 
 }  // namespace rpca

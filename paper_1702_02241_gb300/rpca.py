@@ -133,6 +133,8 @@ def lib():
     L.rpca_batch_context.restype = P
     L.rpca_batch_size.argtypes = [P]
     L.rpca_batch_size.restype = I
+    L.rpca_batch_driver.argtypes = [P]
+    L.rpca_batch_driver.restype = I
     L.rpca_batch_last_error.argtypes = [P]
     L.rpca_batch_last_error.restype = C.c_char_p
     L.rpca_destroy_batch.argtypes = [P]
@@ -196,7 +198,7 @@ def lib():
 EXPORTED = ["rpca_default_options", "rpca_create", "rpca_fg", "rpca_apply", "rpca_init_sketch", "rpca_solve",
             "rpca_certificate", "rpca_destroy", "rpca_release_memory", "rpca_last_error", "rpca_version", "rpca_plan_info", "rpca_plan_kernel",
             "rpca_profile", "rpca_profile_read", "rpca_solve_log", "rpca_solve_trials", "rpca_x_storage", "rpca_fg_noalloc", "rpca_create_batch",
-            "rpca_solve_batch", "rpca_batch_context", "rpca_batch_size", "rpca_batch_last_error",
+            "rpca_solve_batch", "rpca_batch_context", "rpca_batch_size", "rpca_batch_driver", "rpca_batch_last_error",
             "rpca_destroy_batch", "rpca_ws_nparam", "rpca_ws_create", "rpca_ws_set_params", "rpca_ws_get_params",
             "rpca_ws_predict", "rpca_ws_train_step", "rpca_ws_last_error", "rpca_ws_destroy",
             "rpca_set_warm_start", "rpca_sketch_spectrum", "rpca_ws_sample", "rpca_gen_planted",
@@ -403,6 +405,14 @@ def rpca_batch_context(b, i):
 
 def rpca_batch_size(b):
     return lib().rpca_batch_size(b)
+
+
+RPCA_DRIVER_THREADS, RPCA_DRIVER_ROUNDS, RPCA_DRIVER_GROUPED = 0, 1, 2
+
+
+def rpca_batch_driver(b):
+    """The driver of the batch's last solve (RPCA_DRIVER_*), -1 before the first."""
+    return lib().rpca_batch_driver(b)
 
 
 def rpca_batch_last_error(b=None):

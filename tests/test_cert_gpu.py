@@ -44,8 +44,18 @@ def compare(c, o, lam_L, t4_rel=1e-3):
     assert c.trunc_rel == pytest.approx(o.trunc_rel, rel=1e-4, abs=1e-12)
 
 
-@pytest.mark.parametrize("m,n,k,masked", [(300, 200, 5, False), (257, 190, 3, True), (400, 130, 12, False)])
-def test_certificate_random_point(m, n, k, masked):
+@pytest.mark.parametrize("path", ["cluster", "default", "launches"])
+@pytest.mark.parametrize("m,n,k,masked", [(300, 200, 5, False), (257, 190, 3, True), (400, 130, 12, False),
+                                          (12000, 260, 6, False)])
+def test_certificate_random_point(m, n, k, masked, path, monkeypatch):
+    """The forms of the Lanczos block orthonormalisation: one thread-block-cluster launch
+    wherever the rows fit (RPCA_CERT_CLUSTER=1; 12000 rows take a cluster of eight CTAs), the
+    default (one CTA for up to 1024 rows, else the multi-launch form) and the multi-launch form
+    throughout (RPCA_CERT_CLUSTER=0)."""
+    if path == "default":
+        monkeypatch.delenv("RPCA_CERT_CLUSTER", raising=False)
+    else:
+        monkeypatch.setenv("RPCA_CERT_CLUSTER", "1" if path == "cluster" else "0")
     g = np.random.default_rng(m + k)
     X = np.asfortranarray(g.normal(size=(m, n)).astype(np.float32))
     mask = np.asfortranarray((g.random((m, n)) < 0.6).astype(np.uint8)) if masked else None
