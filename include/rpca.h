@@ -289,7 +289,7 @@ RPCA_API const char *rpca_last_error(const rpca_ctx *c);
  * out[0..8] = {rows per lane R, consumer warps per CTA, row blocks, column splits,
  * columns per CTA, threads per CTA, dynamic shared memory bytes, CTAs per SM, pipeline
  * stages}.
- * The planner can be overridden with the environment variable RPCA_PLAN="warps,splits".
+ * The planner can be overridden with the environment variable RPCA_PLAN="warps,splits[,stages]".
  */
 RPCA_API rpca_status rpca_plan_info(rpca_ctx *c, int which, int64_t *out);
 

@@ -298,7 +298,7 @@ static rpca_status time_plan(rpca_ctx* c, const FgPlan& q, double* ms) {
 // limited per SM by issue as much as by HBM), so the time is the larger of the busiest SM's
 // bytes (waves of cps tiles) at that rate and all bytes at the HBM rate, plus the write and
 // re-read of the partial sums.  The twelve best are then timed on the device and the fastest
-// is kept (cached per shape in this process).  RPCA_PLAN="warps,splits" forces one
+// is kept (cached per shape in this process).  RPCA_PLAN="warps,splits[,stages]" forces one
 // configuration; RPCA_AUTOTUNE=0 keeps the model's choice without timing.
 // Cache code of a plan's kernel configuration (warps, stages).
 static int plan_code(const FgPlan& q) {
@@ -313,11 +313,11 @@ static rpca_status make_plan(rpca_ctx* c, FgPlan* P, int K, int B, bool same, in
   const int CSB = side == 1 ? 0 : B;
   double best = 1e300;
   std::vector<std::pair<double, FgPlan>> cands;
-  int force_wc = 0, force_ncs = 0, n_smem = 0, n_attr = 0, n_occ = 0, n_try = 0;
+  int force_wc = 0, force_ncs = 0, force_nst = 0, n_smem = 0, n_attr = 0, n_occ = 0, n_try = 0;
   cudaError_t last_occ = cudaSuccess;
-  if (const char* env = getenv("RPCA_PLAN")) sscanf(env, "%d,%d", &force_wc, &force_ncs);
+  if (const char* env = getenv("RPCA_PLAN")) sscanf(env, "%d,%d,%d", &force_wc, &force_ncs, &force_nst);
   for (int WC : {8, 4, 2}) for (int nst : {6, 4, 2}) {
-    if (force_wc && WC != force_wc) continue;
+    if ((force_wc && WC != force_wc) || (force_nst && nst != force_nst)) continue;
     const int BM = WC * 32 * v->R;
     const int nrb = (c->m + BM - 1) / BM;
     if (WC > 2 && BM / 2 >= c->m) continue;  // a smaller CTA covers the rows

@@ -18,8 +18,11 @@
 //     the paper's ||U1^T D||^2 - ||U1^T D V1||^2, without its cancellation near optimum);
 //  5. t4: block Golub-Kahan-Lanczos (block 8, full re-orthogonalisation) on
 //     P_U1perp D P_V1perp, whose products D Q and D^T P each take one pass over X through
-//     the fused kernel in apply mode; Ritz values from a float32 one-sided Jacobi SVD of the
-//     projected matrix T = P^T A Q; stops when the leading Ritz value and t4 settle.
+//     the fused kernel in apply mode; after every block step from the second, the Ritz values
+//     of the projected matrix T = P^T A Q (float32 Householder bidiagonalisation, then
+//     bisection on Sturm counts for sigma_1 and the values above lam_L); stops when the
+//     leading Ritz value and t4 settle.  The leading Ritz vectors (rank increase) are formed
+//     on request by a one-sided Jacobi SVD of the same T.
 // Also F_bound = min(F(0), best F seen) and the gap bound cert * (||L||_F + F_bound/lam_L)
 // (Sec. 3.4, "Bounding the distance to the feasible set") plus F_trunc, the cost of the
 // directions of L that step 3 moves to the complement block (2 lam_L times their singular
@@ -343,8 +346,16 @@ __global__ void cert_store_T_kernel(const CertState* st, double* T, int p, int c
   }
 }
 
-__global__ void cert_zero_T_kernel(double* T) {
+// Start of a spectral step: T = 0 and the Lanczos loop's stopping state cleared.
+__global__ void cert_zero_T_kernel(double* T, CertState* st) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < LZ_TMAX * LZ_TMAX; i += gridDim.x * blockDim.x) T[i] = 0.0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    st->t4_prev = -1.0;
+    st->s1_prev = -1.0;
+    st->converged = 0;
+    st->ritz_d = 0;
+    st->ritz_q = 0;
+  }
 }
 
 __global__ void cert_reset_kernel(CertState* st) {
@@ -357,6 +368,23 @@ __global__ void cert_reset_kernel(CertState* st) {
   st->sigma1 = 0.0;
   st->ritz_d = 0;
   st->ritz_q = 0;
+}
+
+// Stopping tests of the Lanczos loop from the Ritz values of T[0:d, 0:d]: s1 the largest, t4
+// the sum of (sigma - lam_L)^2 over those above lam_L, `above` their count (one thread).
+__device__ void ritz_update(CertState* st, double s1, double t4, int above, int d, double lam_L, int final_step) {
+  // Settled: sigma_1 and t4 stopped moving, and the Ritz values above lam_L leave at least
+  // two blocks of the Krylov space to spare (otherwise more of them may be missing).
+  const bool settled = st->s1_prev >= 0.0 && fabs(s1 - st->s1_prev) <= 1e-5 * s1 &&
+                       fabs(t4 - st->t4_prev) <= 1e-4 * t4 + 1e-12 * lam_L * lam_L && above + 2 * LZ_B <= d;
+  // When the leading Ritz value has settled (to 1e-3) at half of lam_L or less, no singular
+  // value of the projected residual reaches lam_L: t4 = 0.
+  const bool clear = st->s1_prev >= 0.0 && fabs(s1 - st->s1_prev) <= 1e-3 * s1 && s1 <= 0.5 * lam_L;
+  st->converged = settled || clear || final_step;
+  st->t4_prev = t4;
+  st->s1_prev = s1;
+  st->t4 = t4;
+  st->sigma1 = s1;
 }
 
 // Ritz values of T[0:d, 0:d] (float32 one-sided Jacobi in global memory) -> t4 estimate,
@@ -387,21 +415,9 @@ __device__ void ritz_finish(CertState* st, const float* s, int* ord, int d, doub
       const double e = (double)s[i] - lam_L;
       if (e > 0.0) t4 += e * e;
     }
-    const double s1 = s[ord[0]];
     int above = 0;
     for (int i = 0; i < d; ++i) above += (double)s[i] > lam_L;
-    // Settled: sigma_1 and t4 stopped moving, and the Ritz values above lam_L leave at least
-    // two blocks of the Krylov space to spare (otherwise more of them may be missing).
-    const bool settled = st->s1_prev >= 0.0 && fabs(s1 - st->s1_prev) <= 1e-5 * s1 &&
-                         fabs(t4 - st->t4_prev) <= 1e-4 * t4 + 1e-12 * lam_L * lam_L && above + 2 * LZ_B <= d;
-    // When the leading Ritz value has settled (to 1e-3) at half of lam_L or less, no singular
-    // value of the projected residual reaches lam_L: t4 = 0.
-    const bool clear = st->s1_prev >= 0.0 && fabs(s1 - st->s1_prev) <= 1e-3 * s1 && s1 <= 0.5 * lam_L;
-    st->converged = settled || clear || final_step;
-    st->t4_prev = t4;
-    st->s1_prev = s1;
-    st->t4 = t4;
-    st->sigma1 = s1;
+    ritz_update(st, s[ord[0]], t4, above, d, lam_L, final_step);
   }
 }
 
@@ -445,6 +461,171 @@ __global__ void __launch_bounds__(1024) cert_ritz_kernel(CertState* st, const do
   __syncthreads();
   cta_jacobi_svd<float>(A, d, d, d, V, d, s, &flag, 40, ritz_tol(d), ritz_noise(d));
   ritz_finish(st, s, ord, d, lam_L, final_step, A, V, ritz);
+}
+
+// ---- Ritz values alone (the stopping tests after every Lanczos step) ----------------------
+// T (d x d, d <= RITZV_DMAX) is reduced to upper bidiagonal form B = H^T T G by Householder
+// reflections from the left (columns) and the right (rows) in float32 in shared memory (B has
+// T's singular values); those of B are located by bisection on Sturm counts of its
+// Golub-Kahan form, the symmetric tridiagonal of order 2d with zero diagonal and off-diagonal
+// (a_0, b_0, a_1, b_1, ..., a_{d-1}), whose eigenvalues are +-sigma_i.  Only sigma_1 and the
+// values above lam_L are located; the Ritz vectors are formed on request (ritz_vectors).
+constexpr int RITZV_DMAX = 128;
+constexpr int RITZV_THREADS = 256;
+
+// Sum over the block of one float per thread, the same value returned to every thread
+// (fixed order).  red holds one float per warp.
+__device__ float block_sum_all(float v, float* red) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  float t = 0.f;
+  for (int i = 0; i < nw; ++i) t += red[i];
+  __syncthreads();
+  return t;
+}
+
+// Number of singular values of the bidiagonal (a, b) that are >= s (s > 0): 2d minus the
+// negative pivots of the LDL^T factorisation of (Golub-Kahan form - s I).  Pivots smaller
+// than pivmin in magnitude are replaced by -pivmin (Kahan's safeguard).
+__device__ int gk_count_ge(const float* a, const float* b, int d, float s, float pivmin) {
+  float q = -s;
+  int neg = 1;
+  for (int i = 0; i < 2 * d - 1; ++i) {
+    const float e = (i & 1) ? b[i >> 1] : a[i >> 1];
+    if (fabsf(q) < pivmin) q = -pivmin;
+    q = -s - __fdividef(e * e, q);
+    neg += q < 0.f;
+  }
+  return 2 * d - neg;
+}
+
+// The (idx+1)-th largest singular value of the bidiagonal, bracketed in (lo, hi): 32-point
+// multisection by one warp (every lane counts at its own shift), until the bracket is a few
+// float32 units wide.
+__device__ float gk_kth_largest(const float* a, const float* b, int d, int idx, float lo, float hi, float pivmin) {
+  const int lane = threadIdx.x & 31;
+  for (int round = 0; round < 12 && hi - lo > 2.5e-7f * hi; ++round) {
+    const float w = (hi - lo) * (1.f / 33.f);
+    const float s = lo + w * (float)(lane + 1);
+    const unsigned msk = __ballot_sync(0xffffffffu, gk_count_ge(a, b, d, s, pivmin) >= idx + 1);
+    const int top = 32 - __clz(msk);  // shifts 1..top are at or below the value
+    const float nlo = top > 0 ? lo + w * (float)top : lo;
+    hi = top < 32 ? lo + w * (float)(top + 1) : hi;
+    lo = nlo;
+  }
+  return 0.5f * (lo + hi);
+}
+
+__global__ void __launch_bounds__(RITZV_THREADS) cert_ritz_values_kernel(CertState* st, const double* T, int d,
+                                                                         double lam_L, int final_step) {
+  extern __shared__ float A[];  // d x d, column-major, ld d
+  __shared__ float ad[RITZV_DMAX], bd[RITZV_DMAX], wv[RITZV_DMAX], sv[RITZV_DMAX];
+  __shared__ float red[RITZV_THREADS / 32];
+  __shared__ int n_above;
+  __shared__ float s1_sh;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  for (int i = tid; i < d * d; i += blockDim.x) {
+    const int r = i % d, c = i / d;
+    A[i] = (float)T[r + (int64_t)c * LZ_TMAX];
+  }
+  __syncthreads();
+  for (int k = 0; k < d; ++k) {
+    // Left reflection I - beta v v^T on rows k.., zeroing column k below the diagonal;
+    // v = A[k:, k] - alpha e_1 (kept in place below the diagonal, v_0 in a register).
+    float part = 0.f;
+    for (int i = k + tid; i < d; i += blockDim.x) part += A[i + k * d] * A[i + k * d];
+    float nrm2 = block_sum_all(part, red);
+    float akk = A[k + k * d];
+    if (nrm2 > 0.f) {
+      const float alpha = -copysignf(sqrtf(nrm2), akk);
+      const float v0 = akk - alpha;
+      const float beta = 2.f / (nrm2 - akk * akk + v0 * v0);
+      for (int j = k + 1 + warp; j < d; j += nw) {
+        float sum = 0.f;
+        for (int i = k + lane; i < d; i += 32) sum += (i == k ? v0 : A[i + k * d]) * A[i + j * d];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        if (lane == 0) wv[j] = beta * sum;
+      }
+      __syncthreads();
+      const int h = d - k;
+      for (int e = tid; e < h * (h - 1); e += blockDim.x) {
+        const int i = k + e % h, j = k + 1 + e / h;
+        A[i + j * d] -= (i == k ? v0 : A[i + k * d]) * wv[j];
+      }
+      if (tid == 0) ad[k] = alpha;
+    } else if (tid == 0) {
+      ad[k] = 0.f;
+    }
+    __syncthreads();
+    if (k + 1 == d) break;
+    // Right reflection on columns k+1.., zeroing row k beyond the superdiagonal.
+    part = 0.f;
+    for (int j = k + 1 + tid; j < d; j += blockDim.x) part += A[k + j * d] * A[k + j * d];
+    nrm2 = block_sum_all(part, red);
+    const float ak1 = A[k + (k + 1) * d];
+    if (nrm2 > 0.f) {
+      const float alpha = -copysignf(sqrtf(nrm2), ak1);
+      const float v0 = ak1 - alpha;
+      const float beta = 2.f / (nrm2 - ak1 * ak1 + v0 * v0);
+      for (int i = k + 1 + warp; i < d; i += nw) {
+        float sum = 0.f;
+        for (int j = k + 1 + lane; j < d; j += 32) sum += A[i + j * d] * (j == k + 1 ? v0 : A[k + j * d]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        if (lane == 0) wv[i] = beta * sum;
+      }
+      __syncthreads();
+      const int h = d - k - 1;
+      for (int e = tid; e < h * h; e += blockDim.x) {
+        const int i = k + 1 + e % h, j = k + 1 + e / h;
+        A[i + j * d] -= wv[i] * (j == k + 1 ? v0 : A[k + j * d]);
+      }
+      if (tid == 0) bd[k] = alpha;
+    } else if (tid == 0) {
+      bd[k] = 0.f;
+    }
+    __syncthreads();
+  }
+  if (tid == 0) bd[d - 1] = 0.f;
+  __syncthreads();
+  // Bracket: every eigenvalue of the Golub-Kahan form lies within its largest absolute row
+  // sum (Gershgorin); pivmin scales with its largest squared entry.
+  float hi = 0.f, e2 = 0.f;
+  for (int i = 0; i < d; ++i) {
+    const float bl = i > 0 ? fabsf(bd[i - 1]) : 0.f;
+    hi = fmaxf(hi, fmaxf(fabsf(ad[i]) + bl, fabsf(ad[i]) + fabsf(bd[i])));
+    e2 = fmaxf(e2, fmaxf(ad[i] * ad[i], bd[i] * bd[i]));
+  }
+  hi = hi * 1.0001f + 1e-30f;
+  const float pivmin = 1e-30f * fmaxf(1.f, e2);
+  if (tid == 0) n_above = (float)lam_L < hi ? gk_count_ge(ad, bd, d, (float)lam_L, pivmin) : 0;
+  __syncthreads();
+  const int na = n_above;
+  // The values above lam_L (one warp each), then sigma_1 if none is.
+  for (int idx = warp; idx < na; idx += nw) {
+    const float v = gk_kth_largest(ad, bd, d, idx, 0.f, hi, pivmin);
+    if (lane == 0) sv[idx] = v;
+  }
+  if (na == 0 && warp == 0) {
+    const float v = gk_kth_largest(ad, bd, d, 0, 0.f, hi, pivmin);
+    if (lane == 0) s1_sh = v;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double t4 = 0.0;
+    for (int i = 0; i < na; ++i) {
+      const double e = (double)sv[i] - lam_L;
+      if (e > 0.0) t4 += e * e;
+    }
+    const double s1 = na > 0 ? (double)sv[0] : (double)s1_sh;
+    ritz_update(st, s1, t4, na, d, lam_L, final_step);
+    st->ritz_d = d;
+    st->ritz_q = 0;  // Ritz vectors of this T not formed yet
+  }
 }
 
 __global__ void pad_copy_kernel(const float* src, int64_t rows, int k, float* dst, int kp) {
@@ -973,6 +1154,23 @@ static rpca_status orth_any(rpca_ctx* c, const float* src, float* Y, int64_t row
   return orth_block(c, Y, rows, Bm, p, seed);
 }
 
+// Leading Ritz pairs of the projected matrix T[0:d, 0:d] of the last spectral step (one-sided
+// Jacobi SVD: one warp up to d = 32, else one CTA), into CertBuffers::ritz and the state.
+static rpca_status ritz_vectors(rpca_ctx* c, int d) {
+  CertBuffers* b = c->cert;
+  if (d <= 32) {
+    cert_ritz_warp_kernel<<<1, 32, 0, c->stream>>>(b->st, b->T, d, c->lam_L, 1, b->ritz);
+  } else {
+    const size_t rsm = d <= RITZ_SMEM_D ? (size_t)2 * d * d * sizeof(float) : 0;
+    CERT_CUDA(cudaFuncSetAttribute(cert_ritz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   2 * RITZ_SMEM_D * RITZ_SMEM_D * (int)sizeof(float)));
+    cert_ritz_kernel<<<1, 1024, rsm, c->stream>>>(b->st, b->T, b->Tw, b->Tv, d, c->lam_L, 1, b->ritz);
+  }
+  count_launches(c, 1);
+  CERT_CUDA(cudaGetLastError());
+  return RPCA_OK;
+}
+
 // side 1: Y1 = D BV;  side 2: Y2 = D^T BU  (one pass over X each).
 static rpca_status apply_D(rpca_ctx* c, int side, const float* BV, const float* BU, float* Y1, float* Y2) {
   CertBuffers* b = c->cert;
@@ -1069,7 +1267,7 @@ rpca_status cert_compute(rpca_ctx* c, const float* U, const float* V, rpca_cert*
     count_launches(c, 1);
     pad_copy_kernel<<<256, 256, 0, c->stream>>>(V, n, k, b->Vp, b->Kp);
     count_launches(c, 1);
-    cert_zero_T_kernel<<<64, 256, 0, c->stream>>>(b->T);
+    cert_zero_T_kernel<<<64, 256, 0, c->stream>>>(b->T, st);
     count_launches(c, 1);
     fill_normal(b->Q, n * LZ_B, 0x5eedULL + (uint64_t)c->opt.seed, 1.f, c->stream);
     count_launches(c, 1);
@@ -1091,8 +1289,25 @@ rpca_status cert_compute(rpca_ctx* c, const float* U, const float* V, rpca_cert*
       count_launches(c, 1);
       steps = j + 1;
       const bool last = (j == smax - 1);
-      if (steps == 2 || steps == 4 || steps == 6 || (steps % 4) == 0 || last) {
-        const int d = steps * LZ_B;
+      const int d = steps * LZ_B;
+      // Up to RITZV_DMAX the Ritz values alone are located after every step from the second
+      // on (the vectors are formed on request, ritz_vectors); beyond it the Jacobi SVD (values
+      // and vectors) runs every fourth step.
+      if (d <= RITZV_DMAX && (steps >= 2 || last)) {
+        static const bool attr_ok = [] {
+          return cudaFuncSetAttribute(cert_ritz_values_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      RITZV_DMAX * RITZV_DMAX * (int)sizeof(float)) == cudaSuccess;
+        }();
+        if (!attr_ok) return set_err(c, RPCA_ECUDA, "shared memory of the Ritz-value kernel");
+        cert_ritz_values_kernel<<<1, RITZV_THREADS, (size_t)d * d * sizeof(float), c->stream>>>(st, b->T, d, c->lam_L,
+                                                                                               last ? 1 : 0);
+        count_launches(c, 1);
+        CERT_CUDA(cudaGetLastError());
+        int conv = 0;
+        CERT_CUDA(cudaMemcpyAsync(&conv, &st->converged, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        CERT_CUDA(cudaStreamSynchronize(c->stream));
+        if (conv) break;
+      } else if (d > RITZV_DMAX && ((steps % 4) == 0 || last)) {
         if (d <= 32) {
           cert_ritz_warp_kernel<<<1, 32, 0, c->stream>>>(st, b->T, d, c->lam_L, last ? 1 : 0, b->ritz);
         } else {
@@ -1165,6 +1380,14 @@ extern "C" rpca_status rpca_perp_directions(rpca_ctx* c, int qmax, float* U, int
   int dq[2] = {0, 0};
   double s[RITZ_TOPQ];
   CERT_CUDA(cudaMemcpyAsync(dq, &b->st->ritz_q, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CERT_CUDA(cudaStreamSynchronize(c->stream));
+  if (dq[1] >= 1 && dq[0] < 1) {
+    // The last spectral step located the Ritz values alone: form the leading pairs of its
+    // projected matrix now (Jacobi SVD of T, which the step left in place).
+    rpca_status rs = ritz_vectors(c, dq[1]);
+    if (rs != RPCA_OK) return rs;
+    CERT_CUDA(cudaMemcpyAsync(dq, &b->st->ritz_q, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  }
   CERT_CUDA(cudaMemcpyAsync(s, b->st->ritz_s, sizeof s, cudaMemcpyDeviceToHost, c->stream));
   CERT_CUDA(cudaStreamSynchronize(c->stream));
   const int q = std::min(std::min(qmax, dq[0]), RITZ_TOPQ), d = dq[1];
