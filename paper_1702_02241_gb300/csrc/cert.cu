@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(256) cert_small_kernel(CertState* st, int k, d
   __shared__ double M[CERT_KMAX * CERT_KMAX], Vm[CERT_KMAX * CERT_KMAX], sm[CERT_KMAX];
   __shared__ double Ru[CERT_KMAX * CERT_KMAX], Rv[CERT_KMAX * CERT_KMAX];
   __shared__ int ordu[CERT_KMAX], ordv[CERT_KMAX], ordm[CERT_KMAX];
-  __shared__ int flag, ku, kv;
+  __shared__ int flag, flag2, ku, kv;
   const int t = threadIdx.x;
   for (int i = t; i < k * k; i += blockDim.x) {
     const int a = i % k, b = i / k;
@@ -115,9 +115,16 @@ __global__ void __launch_bounds__(256) cert_small_kernel(CertState* st, int k, d
     Av[i] = st->AVV[a + b * CERT_KMAX];
   }
   __syncthreads();
-  // Symmetric PSD Grams: the one-sided Jacobi SVD is their eigen-decomposition.
-  cta_jacobi_svd<double>(Au, k, k, k, Wu, k, su, &flag, 60, 1e-13, 4.0 * k * 1.1e-16);
-  cta_jacobi_svd<double>(Av, k, k, k, Wv, k, sv, &flag, 60, 1e-13, 4.0 * k * 1.1e-16);
+  // Symmetric PSD Grams: the one-sided Jacobi SVD is their eigen-decomposition; the two run
+  // at once on the two halves of the CTA (named barriers 1 and 2).
+  {
+    const int hw = (int)(blockDim.x >> 6);
+    if ((int)(t >> 5) < hw)
+      group_jacobi_svd<double>(Au, k, k, k, Wu, k, su, &flag, 60, 1e-13, 4.0 * k * 1.1e-16, 0, hw, 1);
+    else
+      group_jacobi_svd<double>(Av, k, k, k, Wv, k, sv, &flag2, 60, 1e-13, 4.0 * k * 1.1e-16, hw, hw, 2);
+  }
+  __syncthreads();
   cta_sort_desc<double>(su, k, ordu);
   cta_sort_desc<double>(sv, k, ordv);
   if (t == 0) {
@@ -471,21 +478,7 @@ __global__ void __launch_bounds__(1024) cert_ritz_kernel(CertState* st, const do
 // (a_0, b_0, a_1, b_1, ..., a_{d-1}), whose eigenvalues are +-sigma_i.  Only sigma_1 and the
 // values above lam_L are located; the Ritz vectors are formed on request (ritz_vectors).
 constexpr int RITZV_DMAX = 128;
-constexpr int RITZV_THREADS = 256;
-
-// Sum over the block of one float per thread, the same value returned to every thread
-// (fixed order).  red holds one float per warp.
-__device__ float block_sum_all(float v, float* red) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  if (lane == 0) red[w] = v;
-  __syncthreads();
-  float t = 0.f;
-  for (int i = 0; i < nw; ++i) t += red[i];
-  __syncthreads();
-  return t;
-}
+constexpr int RITZV_THREADS = 128;
 
 // Number of singular values of the bidiagonal (a, b) that are >= s (s > 0): 2d minus the
 // negative pivots of the LDL^T factorisation of (Golub-Kahan form - s I).  Pivots smaller
@@ -521,72 +514,79 @@ __device__ float gk_kth_largest(const float* a, const float* b, int d, int idx, 
 
 __global__ void __launch_bounds__(RITZV_THREADS) cert_ritz_values_kernel(CertState* st, const double* T, int d,
                                                                          double lam_L, int final_step) {
-  extern __shared__ float A[];  // d x d, column-major, ld d
-  __shared__ float ad[RITZV_DMAX], bd[RITZV_DMAX], wv[RITZV_DMAX], sv[RITZV_DMAX];
-  __shared__ float red[RITZV_THREADS / 32];
+  extern __shared__ float A[];  // d x d, column-major, ld = d + 1 (odd: a row or a column
+                                // read by consecutive threads hits distinct banks)
+  __shared__ float ad[RITZV_DMAX], bd[RITZV_DMAX], sv[RITZV_DMAX];
+  __shared__ float hh[4];  // alpha, v_0, beta of the current reflection, and a skip flag
   __shared__ int n_above;
   __shared__ float s1_sh;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const int ld = d + 1;
   for (int i = tid; i < d * d; i += blockDim.x) {
     const int r = i % d, c = i / d;
-    A[i] = (float)T[r + (int64_t)c * LZ_TMAX];
+    A[r + c * ld] = (float)T[r + (int64_t)c * LZ_TMAX];
   }
   __syncthreads();
-  for (int k = 0; k < d; ++k) {
-    // Left reflection I - beta v v^T on rows k.., zeroing column k below the diagonal;
-    // v = A[k:, k] - alpha e_1 (kept in place below the diagonal, v_0 in a register).
-    float part = 0.f;
-    for (int i = k + tid; i < d; i += blockDim.x) part += A[i + k * d] * A[i + k * d];
-    float nrm2 = block_sum_all(part, red);
-    float akk = A[k + k * d];
+  // Reflection data from a vector x of length h with squared norm nrm2 and first entry x0:
+  // alpha = -sign(x0) ||x||, v = x - alpha e_1, beta = 2 / ||v||^2 (warp 0, lane 0).
+  auto reflector = [&](float nrm2, float x0, float* out_alpha) {
     if (nrm2 > 0.f) {
-      const float alpha = -copysignf(sqrtf(nrm2), akk);
-      const float v0 = akk - alpha;
-      const float beta = 2.f / (nrm2 - akk * akk + v0 * v0);
-      for (int j = k + 1 + warp; j < d; j += nw) {
-        float sum = 0.f;
-        for (int i = k + lane; i < d; i += 32) sum += (i == k ? v0 : A[i + k * d]) * A[i + j * d];
+      const float alpha = -copysignf(sqrtf(nrm2), x0);
+      const float v0 = x0 - alpha;
+      hh[0] = alpha;
+      hh[1] = v0;
+      hh[2] = 2.f / (nrm2 - x0 * x0 + v0 * v0);
+      hh[3] = 0.f;
+      *out_alpha = alpha;
+    } else {
+      hh[3] = 1.f;
+      *out_alpha = 0.f;
+    }
+  };
+  for (int k = 0; k < d; ++k) {
+    // Left reflection I - beta v v^T on rows k.. (v = A[k:, k] - alpha e_1, v_0 in hh[1]):
+    // thread j forms w_j = beta v^T A[k:, j] and updates its column j > k.
+    if (warp == 0) {
+      float part = 0.f;
+      for (int i = k + lane; i < d; i += 32) part += A[i + k * ld] * A[i + k * ld];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-        if (lane == 0) wv[j] = beta * sum;
+      for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+      if (lane == 0) reflector(part, A[k + k * ld], &ad[k]);
+    }
+    __syncthreads();
+    if (hh[3] == 0.f) {
+      const float v0 = hh[1], beta = hh[2];
+      for (int j = k + 1 + tid; j < d; j += blockDim.x) {
+        float* col = A + j * ld;
+        const float* vk = A + k * ld;
+        float w = v0 * col[k];
+        for (int i = k + 1; i < d; ++i) w = fmaf(vk[i], col[i], w);
+        w *= beta;
+        col[k] -= v0 * w;
+        for (int i = k + 1; i < d; ++i) col[i] = fmaf(-vk[i], w, col[i]);
       }
-      __syncthreads();
-      const int h = d - k;
-      for (int e = tid; e < h * (h - 1); e += blockDim.x) {
-        const int i = k + e % h, j = k + 1 + e / h;
-        A[i + j * d] -= (i == k ? v0 : A[i + k * d]) * wv[j];
-      }
-      if (tid == 0) ad[k] = alpha;
-    } else if (tid == 0) {
-      ad[k] = 0.f;
     }
     __syncthreads();
     if (k + 1 == d) break;
-    // Right reflection on columns k+1.., zeroing row k beyond the superdiagonal.
-    part = 0.f;
-    for (int j = k + 1 + tid; j < d; j += blockDim.x) part += A[k + j * d] * A[k + j * d];
-    nrm2 = block_sum_all(part, red);
-    const float ak1 = A[k + (k + 1) * d];
-    if (nrm2 > 0.f) {
-      const float alpha = -copysignf(sqrtf(nrm2), ak1);
-      const float v0 = ak1 - alpha;
-      const float beta = 2.f / (nrm2 - ak1 * ak1 + v0 * v0);
-      for (int i = k + 1 + warp; i < d; i += nw) {
-        float sum = 0.f;
-        for (int j = k + 1 + lane; j < d; j += 32) sum += A[i + j * d] * (j == k + 1 ? v0 : A[k + j * d]);
+    // Right reflection on columns k+1.. (v = A[k, k+1:] - alpha e_1): thread i forms
+    // w_i = beta A[i, k+1:] v and updates its row i > k.
+    if (warp == 0) {
+      float part = 0.f;
+      for (int j = k + 1 + lane; j < d; j += 32) part += A[k + j * ld] * A[k + j * ld];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-        if (lane == 0) wv[i] = beta * sum;
+      for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+      if (lane == 0) reflector(part, A[k + (k + 1) * ld], &bd[k]);
+    }
+    __syncthreads();
+    if (hh[3] == 0.f) {
+      const float v0 = hh[1], beta = hh[2];
+      for (int i = k + 1 + tid; i < d; i += blockDim.x) {
+        float w = A[i + (k + 1) * ld] * v0;
+        for (int j = k + 2; j < d; ++j) w = fmaf(A[i + j * ld], A[k + j * ld], w);
+        w *= beta;
+        A[i + (k + 1) * ld] -= w * v0;
+        for (int j = k + 2; j < d; ++j) A[i + j * ld] = fmaf(-w, A[k + j * ld], A[i + j * ld]);
       }
-      __syncthreads();
-      const int h = d - k - 1;
-      for (int e = tid; e < h * h; e += blockDim.x) {
-        const int i = k + 1 + e % h, j = k + 1 + e / h;
-        A[i + j * d] -= wv[i] * (j == k + 1 ? v0 : A[k + j * d]);
-      }
-      if (tid == 0) bd[k] = alpha;
-    } else if (tid == 0) {
-      bd[k] = 0.f;
     }
     __syncthreads();
   }
@@ -1296,11 +1296,11 @@ rpca_status cert_compute(rpca_ctx* c, const float* U, const float* V, rpca_cert*
       if (d <= RITZV_DMAX && (steps >= 2 || last)) {
         static const bool attr_ok = [] {
           return cudaFuncSetAttribute(cert_ritz_values_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      RITZV_DMAX * RITZV_DMAX * (int)sizeof(float)) == cudaSuccess;
+                                      RITZV_DMAX * (RITZV_DMAX + 1) * (int)sizeof(float)) == cudaSuccess;
         }();
         if (!attr_ok) return set_err(c, RPCA_ECUDA, "shared memory of the Ritz-value kernel");
-        cert_ritz_values_kernel<<<1, RITZV_THREADS, (size_t)d * d * sizeof(float), c->stream>>>(st, b->T, d, c->lam_L,
-                                                                                               last ? 1 : 0);
+        cert_ritz_values_kernel<<<1, RITZV_THREADS, (size_t)d * (d + 1) * sizeof(float), c->stream>>>(
+            st, b->T, d, c->lam_L, last ? 1 : 0);
         count_launches(c, 1);
         CERT_CUDA(cudaGetLastError());
         int conv = 0;

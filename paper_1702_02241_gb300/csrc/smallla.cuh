@@ -64,7 +64,9 @@ RPCA_DEV bool jacobi_rotation(T al, T be, T ga, T& cs, T& sn) {
   return true;
 }
 
-// One-sided Jacobi (Hestenes) SVD, executed by the whole CTA (blockDim multiple of 32).
+// One-sided Jacobi (Hestenes) SVD, executed by a group of gnw warps starting at warp gw0 that
+// synchronise on named barrier `bar` (0: the whole CTA, __syncthreads), or by the whole CTA
+// (cta_jacobi_svd).
 // A: rows x cols column-major (lda), overwritten by U * diag(sig) (columns in input order).
 // V: cols x cols (ldv), right singular vectors.  sig[j] = ||A_j||.  Returns the sweep count.
 // A pair is rotated while |a_p . a_q| > tol ||a_p|| ||a_q|| and |a_p . a_q| > noise (||a_p||^2 +
@@ -74,25 +76,30 @@ RPCA_DEV bool jacobi_rotation(T al, T be, T ga, T& cs, T& sn) {
 // smaller than its partner is rotated again in every sweep up to max_sweeps.
 // `flag` is one shared int.  Works in T = float or double.
 template <typename T>
-__device__ int cta_jacobi_svd(T* A, int rows, int cols, int lda, T* V, int ldv, T* sig, int* flag, int max_sweeps,
-                              T tol, T noise = T(0)) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+__device__ int group_jacobi_svd(T* A, int rows, int cols, int lda, T* V, int ldv, T* sig, int* flag, int max_sweeps,
+                                T tol, T noise, int gw0, int gnw, int bar) {
+  const int lane = threadIdx.x & 31, w = (int)(threadIdx.x >> 5) - gw0, nw = gnw;
+  const int gt = (int)threadIdx.x - gw0 * 32, gn = gnw * 32;  // thread index and count in the group
+  auto sync = [&]() {
+    if (bar == 0) __syncthreads();
+    else named_bar(bar, gn);
+  };
   // Butterfly width: the lanes that hold data (rows of A) or apply the rotation (rows of A,
   // rows of V = cols) must all get the sums, so the tree spans max(rows, cols) lanes.
   const int nact = rows > cols ? rows : cols;
   int top = 16;
   while (top > 1 && top >= nact) top >>= 1;
   if (nact > 32) top = 16;
-  for (int idx = threadIdx.x; idx < cols * cols; idx += blockDim.x) {
+  for (int idx = gt; idx < cols * cols; idx += gn) {
     const int i = idx % cols, j = idx / cols;
     V[i + (size_t)j * ldv] = (i == j) ? T(1) : T(0);
   }
-  __syncthreads();
+  sync();
   const int ne = cols + (cols & 1);
   int sweep = 0;
   for (; sweep < max_sweeps; ++sweep) {
-    if (threadIdx.x == 0) *flag = 0;
-    __syncthreads();
+    if (gt == 0) *flag = 0;
+    sync();
     for (int r = 0; r < ne - 1; ++r) {
       for (int k = w; k < ne / 2; k += nw) {
         int p, q;
@@ -132,18 +139,26 @@ __device__ int cta_jacobi_svd(T* A, int rows, int cols, int lda, T* V, int ldv, 
         }
         __syncwarp();
       }
-      __syncthreads();
+      sync();
     }
     if (*flag == 0) break;
-    __syncthreads();
+    sync();
   }
-  for (int j = threadIdx.x; j < cols; j += blockDim.x) {
+  for (int j = gt; j < cols; j += gn) {
     T s = 0;
     for (int i = 0; i < rows; ++i) s += A[i + (size_t)j * lda] * A[i + (size_t)j * lda];
     sig[j] = sqrt(s);
   }
-  __syncthreads();
+  sync();
   return sweep;
+}
+
+// The whole CTA.
+template <typename T>
+__device__ int cta_jacobi_svd(T* A, int rows, int cols, int lda, T* V, int ldv, T* sig, int* flag, int max_sweeps,
+                              T tol, T noise = T(0)) {
+  return group_jacobi_svd<T>(A, rows, cols, lda, V, ldv, sig, flag, max_sweeps, tol, noise, 0, (int)(blockDim.x >> 5),
+                             0);
 }
 
 // One-sided Jacobi (Hestenes) SVD of a small matrix by one warp: cols <= CMAX <= 32,
