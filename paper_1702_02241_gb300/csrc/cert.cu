@@ -1067,7 +1067,10 @@ static rpca_status orth_block_cluster(rpca_ctx* c, const float* src, float* Y, i
                                 (int)oc_smem_bytes()) == cudaSuccess;
   }();
   if (!attr_ok) return set_err(c, RPCA_ECUDA, "shared memory of the cluster orthonormalisation");
-  const int nc = (int)std::min<int64_t>(OC_MAXC, std::max<int64_t>(1, (rows + 1023) / 1024));
+  // About 128 rows per CTA: the basis Grams are latency-bound per CTA, so a block of up to a
+  // thousand rows spreads over up to eight SMs of one cluster (measured on the 1000-row side
+  // of the video workload: 1, 2, 4, 8 CTAs took the certificate from 3.24 to 3.13, 3.11, 3.08 ms).
+  const int nc = (int)std::min<int64_t>(OC_MAXC, std::max<int64_t>(1, (rows + 127) / 128));
   OrthArgs a;
   a.B = Bm;
   a.p = p;
@@ -1137,17 +1140,17 @@ static rpca_status orth_block(rpca_ctx* c, float* Y, int64_t rows, const float* 
   return normalise(c, Y, rows);
 }
 
-// orth_block of Y (first a copy of src when src is not null): one launch of a single CTA for
-// up to OC_SINGLE rows, else the multi-launch form.  RPCA_CERT_CLUSTER=1 takes the cluster
+// orth_block of Y (first a copy of src when src is not null): one cluster launch (up to eight
+// CTAs of about 128 rows) for up to OC_SINGLE rows, else the multi-launch form.  RPCA_CERT_CLUSTER=1 takes the cluster
 // launch wherever it fits (up to OC_MAXC x OC_ROWS rows), =0 never.  Measured on the
 // 256-instance batch (m up to 20000), the eight-CTA cluster kept the m-side blocks 2.5x longer
 // on the device than the multi-launch form (eight SMs stream the basis at a fraction of the
-// GPU's rate), although it made a quarter of the launches; the single CTA takes the small side.
+// GPU's rate), although it made a quarter of the launches; the cluster takes the small side.
 constexpr int64_t OC_SINGLE = 1024;
 static rpca_status orth_any(rpca_ctx* c, const float* src, float* Y, int64_t rows, const float* Bm, int p,
                             uint64_t seed) {
   const char* env = getenv("RPCA_CERT_CLUSTER");
-  const int mode = env ? (env[0] == '0' ? 0 : 2) : 1;  // 0 never, 1 single CTA only, 2 wherever it fits
+  const int mode = env ? (env[0] == '0' ? 0 : 2) : 1;  // 0 never, 1 small side only, 2 wherever it fits
   if (mode > 0 && orth_cluster_fits(rows, p) && (mode == 2 || rows <= OC_SINGLE))
     return orth_block_cluster(c, src, Y, rows, Bm, p, seed);
   if (src && src != Y) CERT_CUDA(cudaMemcpyAsync(Y, src, sizeof(float) * rows * LZ_B, cudaMemcpyDeviceToDevice, c->stream));
