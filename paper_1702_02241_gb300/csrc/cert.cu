@@ -1193,7 +1193,19 @@ static rpca_status apply_D(rpca_ctx* c, int side, const float* BV, const float* 
 // reuse: the last call on this context evaluated the first four steps (F, Grams, t1, t2, t3 and
 // the range bases) at this same point and nothing has changed them since: go straight to the
 // spectral step (a solve that just found the cheap terms within the tolerance).
-rpca_status cert_compute(rpca_ctx* c, const float* U, const float* V, rpca_cert* out, bool full, bool reuse) {
+// D V and D^T U from a gradient at the same point: G = D (V, U) + lam_L (U, V) (g, x: the
+// solver's vectors [U | V], the V part from offset mk).
+__global__ void cert_raw_from_grad_kernel(const float* g, const float* x, float lam, int64_t mk, int64_t nk, float* DV,
+                                          float* DtU) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < mk + nk; i += (int64_t)gridDim.x * blockDim.x) {
+    const float v = fmaf(-lam, x[i], g[i]);
+    if (i < mk) DV[i] = v;
+    else DtU[i - mk] = v;
+  }
+}
+
+rpca_status cert_compute(rpca_ctx* c, const float* U, const float* V, rpca_cert* out, bool full, bool reuse,
+                         const float* grad, const double* f_dev, double f_host) {
   rpca_status s = ensure_cert(c);
   if (s != RPCA_OK) return s;
   CertBuffers* b = c->cert;
@@ -1222,15 +1234,25 @@ rpca_status cert_compute(rpca_ctx* c, const float* U, const float* V, rpca_cert*
       c->F0 = f0;
       b->have_F0 = true;
     }
-    // 1. F and the raw products.
-    FgLaunch L;
-    L.U = U;
-    L.V = V;
-    L.GU = b->DV;
-    L.GV = b->DtU;
-    L.fin_mode = FIN_FG_RAW;
-    L.out = c->ws.out;
-    if ((s = launch_fg(c, c->fg_plan, L, c->stream)) != RPCA_OK) return s;
+    // 1. F and the raw products: one pass over X, or, given the gradient at this point (a
+    // solve's current iterate, [U | V] contiguous), D V = G_U - lam_L U and D^T U = G_V - lam_L V.
+    const double* Fp = grad ? f_dev : c->ws.out;
+    if (grad) {
+      const int64_t mk = m * k, nk = n * k;
+      cert_raw_from_grad_kernel<<<(int)std::min<int64_t>(4 * c->nsm, (mk + nk + 255) / 256), 256, 0, c->stream>>>(
+          grad, U, (float)c->lam_L, mk, nk, b->DV, b->DtU);
+      count_launches(c, 1);
+      CERT_CUDA(cudaGetLastError());
+    } else {
+      FgLaunch L;
+      L.U = U;
+      L.V = V;
+      L.GU = b->DV;
+      L.GV = b->DtU;
+      L.fin_mode = FIN_FG_RAW;
+      L.out = c->ws.out;
+      if ((s = launch_fg(c, c->fg_plan, L, c->stream)) != RPCA_OK) return s;
+    }
     // 2. Grams.
     CERT_CUDA(ts_gram_c(c, U, m, k, U, m, k, m, st->G, b->ts, c->stream));
     CERT_CUDA(cudaMemcpy2DAsync(st->AUU, CERT_KMAX * 8, st->G, k * 8, k * 8, k, cudaMemcpyDeviceToDevice, c->stream));
@@ -1239,7 +1261,7 @@ rpca_status cert_compute(rpca_ctx* c, const float* U, const float* V, rpca_cert*
     CERT_CUDA(ts_gram_c(c, U, m, k, b->DV, m, k, m, st->G, b->ts, c->stream));
     CERT_CUDA(cudaMemcpy2DAsync(st->MUDV, CERT_KMAX * 8, st->G, k * 8, k * 8, k, cudaMemcpyDeviceToDevice, c->stream));
     // 3. Small factorisations, t1.
-    cert_small_kernel<<<1, 256, 0, c->stream>>>(st, k, c->lam_L, c->ws.out);
+    cert_small_kernel<<<1, 256, 0, c->stream>>>(st, k, c->lam_L, Fp);
     count_launches(c, 1);
     CERT_CUDA(cudaGetLastError());
     // 4. t3 = ||DV T_V - U P2||^2, t2 = ||DtU T_U - V P3||^2.
@@ -1252,8 +1274,9 @@ rpca_status cert_compute(rpca_ctx* c, const float* U, const float* V, rpca_cert*
     count_launches(c, 1);
     CERT_CUDA(cudaGetLastError());
     CERT_CUDA(cudaMemcpyAsync(b->host, st, sizeof(CertState), cudaMemcpyDeviceToHost, c->stream));
-    CERT_CUDA(cudaMemcpyAsync(&F, c->ws.out, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if (!grad) CERT_CUDA(cudaMemcpyAsync(&F, c->ws.out, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CERT_CUDA(cudaStreamSynchronize(c->stream));
+    if (grad) F = f_host;
     b->last_F = F;
   }
   const int r = b->host->r;
@@ -1369,7 +1392,7 @@ extern "C" rpca_status rpca_certificate(rpca_ctx* c, const float* U, const float
   if (!c) return RPCA_EINVAL;
   if (c->lk) return set_err(c, RPCA_EUNSUPPORTED, "the certificate is built for k <= 16");
   if (!U || !V || !out) return set_err(c, RPCA_EINVAL, "U, V and out are required");
-  return cert_compute(c, U, V, out, true, false);
+  return cert_compute(c, U, V, out, true, false, nullptr, nullptr, 0.0);
 }
 
 extern "C" rpca_status rpca_perp_directions(rpca_ctx* c, int qmax, float* U, int64_t ldu, float* V, int64_t ldv,

@@ -23,7 +23,10 @@ rpca_status solver_read_state(rpca_ctx* c, SolverState* out);
 rpca_status solver_read_scalars(rpca_ctx* c, SolverState* out);
 const float* solver_point(rpca_ctx* c);
 rpca_status cert_compute(rpca_ctx* c, const float* U, const float* V, rpca_cert* out, bool full,
-                         bool reuse = false);
+                         bool reuse = false, const float* grad = nullptr, const double* f_dev = nullptr,
+                         double f_host = 0.0);
+const float* solver_gradient(rpca_ctx* c);
+const double* solver_f_device(rpca_ctx* c);
 rpca_status sketch_init(rpca_ctx* c, const float* Omega, float* U, float* V);
 
 // A point is certified at tol when the Sec. 3.4 certificate meets it and so does the cost of
@@ -285,7 +288,13 @@ static rpca_status job_decide(SolveJob& j, bool* again) {
     j.last_cert_iter = st.iter;
     // Cheap terms first; the spectral term only when they already meet the tolerance.
     j.timer->begin(2);
-    if ((s = cert_compute(c, solver_point(c), solver_point(c) + j.mk, &j.cert, false)) != RPCA_OK) return s;
+    // On float32 X the solver's gradient and objective at its iterate give the cheap terms'
+    // products without a pass over X.
+    const bool from_grad = !j.narrow;
+    if ((s = cert_compute(c, solver_point(c), solver_point(c) + j.mk, &j.cert, false, false,
+                          from_grad ? solver_gradient(c) : nullptr, from_grad ? solver_f_device(c) : nullptr,
+                          st.f)) != RPCA_OK)
+      return s;
     ++j.cert_evals;
     bool rank_deficit = false;
     if (cert_meets(j.cert, c->opt.cert_tol)) {

@@ -1257,6 +1257,9 @@ rpca_status solver_iterations(rpca_ctx* c, int count) {
 }
 
 const float* solver_point(rpca_ctx* c) { return c->sol ? c->sol->x : nullptr; }
+// The gradient at solver_point and the objective there (device copy in the solver state).
+const float* solver_gradient(rpca_ctx* c) { return c->sol ? c->sol->g : nullptr; }
+const double* solver_f_device(rpca_ctx* c) { return c->sol ? &c->sol->st->f : nullptr; }
 
 // ---------------------------------------------------------------------------------------------
 // Grouped iteration.  Each instance's record holds what its own launches would pass: the
