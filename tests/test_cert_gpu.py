@@ -210,3 +210,27 @@ def test_spectral_term_where_the_krylov_space_truncates():
     compare(c, o, inst.lam_L)
     assert c.sigma1_perp == pytest.approx(o.sigma_perp[0], rel=1e-3)
     P.close()
+
+
+@pytest.mark.parametrize("masked", [False, True])
+def test_solve_certificate_from_gradient_matches_full_pass(masked):
+    """Inside a solve the cheap terms take D V and D^T U from the solver's gradient at its
+    iterate (G - lam_L x) and F from its objective, with no pass over X.  A solve with a loose
+    tolerance certifies at a check and returns that certificate; it must equal rpca_certificate's
+    (which makes the pass) at the returned point, and the FP64 oracle's."""
+    from paper_1702_02241_gb300 import rpca
+    from gpu_util import empty_factors
+    inst = gen.planted_500x400(0)
+    mask = (np.random.default_rng(5).random(inst.X.shape) < 0.7).astype(np.uint8) if masked else None
+    P = make_problem(inst.X, mask, inst.k, inst.lam_L, inst.lam_S, init=rpca.RPCA_INIT_SKETCH, max_iter=400,
+                     cert_every=8, cert_tol=0.3)
+    U, V = empty_factors(inst.m, inst.n, inst.k)
+    res = P.solve(U, V)
+    assert res.status == rpca.RPCA_OK and res.iters < 400, (res.status, res.iters, res.cert.asdict())
+    assert res.cert.cert_rel > 1e-4  # stopped at a check well before convergence
+    full = P.certificate(U, V)
+    compare(res.cert, full, inst.lam_L)
+    Uh, Vh = host(U, inst.m), host(V, inst.n)
+    o = ocert.certificate(inst.X, mask, Uh.astype(np.float64), Vh.astype(np.float64), inst.lam_L, inst.lam_S)
+    compare(res.cert, o, inst.lam_L)
+    P.close()
