@@ -8,7 +8,9 @@ three moving foreground squares, noise sigma 0.01, k = 5, fully observed.  X is 
 HBM when the timed region starts (307 MB, larger than the 129 MB L2, so no L2 flush is
 needed between steps).  The JSON line also carries the fused objective/gradient kernel's
 roofline (HBM bound), the end-to-end time through the C ABI with host buffers, the FP64
-oracle's time on the host cores, and SM clocks sampled during the timed region.
+oracle's time on the host cores, and SM clocks sampled during the timed region; its
+metrics.forms holds short runs of the batched and precision forms (child processes of this
+script, skipped with --no-forms or --no-cpu-baseline).
 
 --impl reference times the FP64 CPU oracle (the only reference this method has) on the
 same workload, on a bounded sample: each step is one oracle L-BFGS iteration on the full
@@ -56,7 +58,10 @@ def parse_args():
                         "sees the timed region several times; 3 for the heavier workloads and the reference arm)")
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true",
+                   help="skip the oracle baseline (and the secondary forms' runs of the video line)")
+    p.add_argument("--no-forms", action="store_true",
+                   help="video line: skip the short runs of the batched and precision forms")
     p.add_argument("--fg-evals", type=int, default=100)
     p.add_argument("--workload", default="video", choices=["video", "batch", "convex", "precision"])
     p.add_argument("--batch-count", type=int, default=256)
@@ -428,12 +433,41 @@ def run_ours(args):
         "clocks": clk,
         "gpu_launches": launches,
     }
+    if rank == 0 and world == 1 and not (args.no_cpu_baseline or args.no_forms):
+        line["metrics"]["forms"] = secondary_forms()
     if rank == 0:
         print(json.dumps(line), flush=True)
     P.close()
     if pg is not None:
         pg.destroy_process_group()
     return 0
+
+
+def secondary_forms():
+    """Short runs of the batched form (256 instances) and of the precision form (110592x2000,
+    50 % mask, float32 / bfloat16 / E4M3 storage), each in a child process of this script with
+    its own timing (warm-up, CUDA events, clocks), summarised for the video line's metrics."""
+    runs = {"batch_256_instances": ["--workload", "batch", "--steps", "2", "--warmup", "2"],
+            "precision_110592x2000": ["--workload", "precision", "--steps", "2", "--warmup", "1"]}
+    out = {}
+    for name, extra in runs.items():
+        cmd = [sys.executable, os.path.abspath(__file__), "--no-cpu-baseline", "--no-forms"] + extra
+        try:
+            r = subprocess.run(cmd, capture_output=True, text=True, timeout=900)
+            lines = [json.loads(x) for x in r.stdout.splitlines() if x.startswith("{")]
+        except Exception as e:  # a failed secondary run leaves the main line valid
+            out[name] = {"error": f"{type(e).__name__}: {e}"}
+            continue
+        if r.returncode != 0 or not lines:
+            out[name] = {"error": f"exit {r.returncode}: {r.stderr.strip().splitlines()[-1:] or ''}"}
+            continue
+        d = lines[-1]
+        out[name] = {"value": d["value"], "unit": d["unit"], "valid": d.get("valid"), "steps": d["steps"],
+                     "warmup": d["warmup"], "workload": d["config"]["workload"],
+                     "e2e_s": (d.get("e2e") or {}).get("value"), "roofline_frac": d["roofline"]["frac"],
+                     "roofline_kernel": d["roofline"]["kernel"], "clocks": d.get("clocks"),
+                     "gpu_launches": d.get("gpu_launches"), "metrics": d.get("metrics")}
+    return out
 
 
 BATCH_WORKLOAD = ("{count} independent planted instances, m~U[1024,20000], n~U[50,600], k~U{{2..16}}, rank k//2, "
