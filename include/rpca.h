@@ -405,7 +405,9 @@ RPCA_API rpca_status rpca_inject_fault(rpca_ctx *c, int kind, int count);
  * of P_U1perp D P_V1perp at the point of this context's last full certificate (the spectral
  * term of Sec. 3.4), from its block-Lanczos bases; *sigma1 (may be NULL) = that singular value,
  * u^T D v = sigma1.  Needs a certificate with a spectral step (rpca_certificate, or the end of
- * rpca_solve) on this context.  Synchronous.
+ * rpca_solve) on this context.  The spectral step locates the Ritz values alone; the first call
+ * after it forms the leading Ritz pairs by a one-sided Jacobi SVD of its projected matrix (one
+ * launch, tens of microseconds), later calls reuse them.  Synchronous.
  */
 RPCA_API rpca_status rpca_perp_direction(rpca_ctx *c, float *u, float *v, double *sigma1);
 /* The q <= min(qmax, 16) leading pairs of the same: U (device, m x q, ld ldu >= m), V (device,
