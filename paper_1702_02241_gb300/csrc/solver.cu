@@ -188,8 +188,16 @@ __device__ void ls_step_body(SolverState* st, cudaGraphConditionalHandle h, int 
       } else if (fabs(ga) <= -LS_C2 * L.g0) {
         accept = true;
       } else {
+        // Extrapolation (Alg. 3.5 leaves the next trial in (a, a_max) open): the secant root of
+        // phi' through the last two trials -- the minimiser of the quadratic they define --
+        // when phi' rose toward zero, kept within [4 a, 100 a]; 4 a otherwise.
+        double t = 4.0 * a;
+        if (ga > L.g_prev && L.g_prev < 0.0) {
+          const double sec = a - ga * (a - L.a_prev) / (ga - L.g_prev);
+          if (isfinite(sec)) t = fmin(fmax(sec, 4.0 * a), 100.0 * a);
+        }
         L.a_prev = a; L.f_prev = fa; L.g_prev = ga;
-        L.a = fmin(4.0 * a, LS_AMAX);
+        L.a = fmin(t, LS_AMAX);
         L.first = 0;
       }
     } else {  // zoom (Alg. 3.6), with the bracket kept by the sign of phi' (Hager & Zhang)
