@@ -61,6 +61,7 @@ rpca_status check_dev_err(rpca_ctx* c) {
 static FgVariant g_same[17][2];
 static FgVariant g_same_x[2][17][2];  // narrow storage of X: bfloat16, FP8 E4M3
 static FgVariant g_apply[3][3][2];
+static FgVariant g_apply16[3][2];  // K = 0, B = 16, by side (1, 2) and mask
 static FgVariant g_mma[17];  // tensor-core form, unmasked, K = 1..8
 static FgVariant g_tc[17];   // tcgen05 form, unmasked, K = 1..6
 static std::once_flag g_once;
@@ -70,6 +71,7 @@ static void init_tables() {
     memset(g_same, 0, sizeof g_same);
     memset(g_same_x, 0, sizeof g_same_x);
     memset(g_apply, 0, sizeof g_apply);
+    memset(g_apply16, 0, sizeof g_apply16);
     memset(g_mma, 0, sizeof g_mma);
     memset(g_tc, 0, sizeof g_tc);
     fg_register_mma(g_mma);
@@ -79,6 +81,7 @@ static void init_tables() {
     fg_register_same_e4m3(g_same_x[1]);
     fg_register_same_large(g_same);
     fg_register_apply(g_apply);
+    fg_register_apply16(g_apply16);
   });
 }
 
@@ -92,6 +95,10 @@ const FgVariant* fg_variant(int K, int B, bool same, bool masked, int side, int 
   if (same) {
     if (K < 1 || K > 16 || B != K || side != 0) return nullptr;
     return g_same[K][masked ? 1 : 0].fn ? &g_same[K][masked ? 1 : 0] : nullptr;
+  }
+  if (B == 16 && K == 0 && (side == 1 || side == 2)) {
+    const FgVariant* v16 = &g_apply16[side][masked ? 1 : 0];
+    return v16->fn ? v16 : nullptr;
   }
   if (B != 8 || side < 0 || side > 2) return nullptr;
   const int slot = K == 0 ? 0 : (K == 8 ? 1 : (K == 16 ? 2 : -1));
@@ -779,6 +786,23 @@ const FgPlan* apply_plan(rpca_ctx* c, int K, int side) {
     const int KK = slot == 0 ? 0 : (slot == 1 ? 8 : 16);
     if (make_plan(c, P, KK, 8, false, side) != RPCA_OK) return nullptr;
     if (size_workspace(c, *P) != RPCA_OK) return nullptr;
+  }
+  return P;
+}
+
+// The sketch's 16-column product on side 1 or 2 (no forming factors), or nullptr when it has
+// no launch configuration (the sketch then takes 8 columns at a time).
+const FgPlan* apply_plan16(rpca_ctx* c, int side) {
+  if (side < 1 || side > 2 || c->ap16_none[side]) return nullptr;
+  FgPlan* P = &c->ap16_plan[side];
+  if (!P->valid) {
+    const std::string err = c->err;
+    if (make_plan(c, P, 0, 16, false, side) != RPCA_OK || size_workspace(c, *P) != RPCA_OK) {
+      P->valid = false;
+      c->ap16_none[side] = true;
+      c->err = err;  // not an error of the call: the 8-column form serves
+      return nullptr;
+    }
   }
   return P;
 }

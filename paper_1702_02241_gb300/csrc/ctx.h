@@ -86,6 +86,8 @@ struct rpca_ctx {
   rpca::FgPlan fg_plan_q;    // K = k, fg mode, narrow X
   const rpca::FgPlan* solve_plan = nullptr;  // the plan the solver's iteration uses
   rpca::FgPlan ap_plan[3][3];  // apply modes: forming rank 0 / 8 / 16 x side
+  rpca::FgPlan ap16_plan[3];   // the sketch's 16-column products, by side (1, 2)
+  bool ap16_none[3] = {false, false, false};  // no configuration for that side
   rpca::Workspace ws;          // partial sums of the objective/gradient plan (graph-captured)
   rpca::Workspace ws_ap;       // partial sums of the apply plans
   rpca::SolverBuffers* sol = nullptr;
@@ -183,6 +185,7 @@ rpca_status launch_fg(rpca_ctx* c, const FgPlan& P, const FgLaunch& L, cudaStrea
 void fg_launch_args(rpca_ctx* c, const FgPlan& P, const FgLaunch& L, FgArgs* a, FinArgs* f);
 cudaError_t launch_finalize_ls(const FinArgs& f, int grid, const FgLaunch& L, cudaStream_t stream);  // solver.cu
 const FgPlan* apply_plan(rpca_ctx* c, int K, int side);  // forming rank >= K (0, 8 or 16), side
+const FgPlan* apply_plan16(rpca_ctx* c, int side);       // K = 0, 16 columns (sketch), or nullptr
 rpca_status make_xq(rpca_ctx* c, int xt);                // narrow copy of X (xq.cu)
 rpca_status ws_learned_init(rpca_ctx* c, float* U, float* V, int* used);  // ws.cu
 rpca_status lk_setup(rpca_ctx* c);                                           // largek.cu

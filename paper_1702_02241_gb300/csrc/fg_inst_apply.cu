@@ -26,4 +26,17 @@ void fg_register_apply(FgVariant (*tab)[3][2]) {
   reg<16, 4, 1, 2>(tab, 2);
 }
 
+// The sketch's products with 16 columns at a time (no forming factors), one pass over X for
+// what two 8-column passes would do: tab[side][masked], sides 1 (D Bv) and 2 (D^T Bu).
+template <int SIDE>
+static void reg16(FgVariant (*tab)[2]) {
+  tab[SIDE][0] = FgVariant{(const void*)&fg_kernel<0, 16, false, false, 8, 1, SIDE>, 8, 1};
+  tab[SIDE][1] = FgVariant{(const void*)&fg_kernel<0, 16, false, true, 8, 1, SIDE>, 8, 1};
+}
+
+void fg_register_apply16(FgVariant (*tab)[2]) {
+  reg16<1>(tab);
+  reg16<2>(tab);
+}
+
 }  // namespace rpca

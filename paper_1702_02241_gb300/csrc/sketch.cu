@@ -180,16 +180,21 @@ static rpca_status ensure_sketch(rpca_ctx* c, int l, SketchBuffers** out) {
   } while (0)
 
 // Y1 (m x l) = -A*(X) BV (BV n x l),  or  Y2 (n x l) = -A*(X)^T BU (BU m x l), in chunks of
-// 8 columns, each one pass of the one-sided apply kernel with no forming factors.  A full
-// chunk writes its columns of Y in place; a ragged last chunk goes through a zero-padded copy.
+// 16 columns while at least 16 remain (one pass of the 16-column apply kernel, where it has a
+// launch configuration), then of 8 (the 8-column kernel), each one pass over X with no forming
+// factors.  A full chunk writes its columns of Y in place; a ragged last chunk (l not a
+// multiple of 8) goes through a zero-padded copy.
 static rpca_status sk_apply(rpca_ctx* c, SketchBuffers& b, int l, const float* BV, const float* BU, float* Y1,
                             float* Y2) {
   const int side = BV ? 1 : 2;
-  const FgPlan* P = apply_plan(c, 0, side);
-  if (!P) return RPCA_EUNSUPPORTED;
-  constexpr int W = SK_CHUNK;
+  const FgPlan* P8 = apply_plan(c, 0, side);
+  if (!P8) return RPCA_EUNSUPPORTED;
+  const FgPlan* P16 = l >= 16 ? apply_plan16(c, side) : nullptr;
   const int64_t m = c->m, n = c->n;
-  for (int c0 = 0; c0 < l; c0 += W) {
+  for (int c0 = 0; c0 < l;) {
+    const bool wide = P16 != nullptr && l - c0 >= 16;
+    const FgPlan* P = wide ? P16 : P8;
+    const int W = wide ? 16 : SK_CHUNK;
     const int w = std::min(W, l - c0);
     const float* bv = BV ? BV + n * c0 : b.BVc;
     const float* bu = BU ? BU + m * c0 : b.BUc;
@@ -218,6 +223,7 @@ static rpca_status sk_apply(rpca_ctx* c, SketchBuffers& b, int l, const float* B
     if (s != RPCA_OK) return s;
     if (!direct && Y1) SK_CUDA(cudaMemcpyAsync(Y1 + m * c0, b.Y1c, sizeof(float) * m * w, cudaMemcpyDeviceToDevice, c->stream));
     if (!direct && Y2) SK_CUDA(cudaMemcpyAsync(Y2 + n * c0, b.Y2c, sizeof(float) * n * w, cudaMemcpyDeviceToDevice, c->stream));
+    c0 += W;
   }
   return RPCA_OK;
 }
